@@ -1,0 +1,245 @@
+"""Upwind DG S_N transport discretization and sweep (oracle).
+
+Sec. "Transport Discretization": each discrete-ordinate flux psi_d lies in
+Y_p and the streaming + collision operator L is inverted by a transport
+sweep.  The paper defers the DG transport scheme to the solvers it cites,
+so this oracle states the standard upwind DG weak form: for ordinate d and
+element K find psi in Q_p(K) such that for all v in Q_p(K)
+
+    - int_K psi Omega_d . grad v + int_K sigma_t psi v
+    + sum_F int_F max(Omega_d . n, 0) psi v
+  = int_K s_d v - sum_F int_F min(Omega_d . n, 0) psi^up v,
+
+with n the outward normal of K, the sign taken pointwise at face
+quadrature points, psi^up the upwind neighbour's trace or the inflow
+function psibar on the domain boundary (Eq. inflow), and
+s_d = sigma_s/(4 pi) varphi + q_d (Eq. moment_coupled, first line).
+
+Elements are visited in a topological order of each ordinate's upwind
+graph (a neighbour is upwind if Omega_d . n < 0 at any point of the shared
+face); a cycle is an error (no lagging).  Each local system is solved by
+dense LU with partial pivoting.
+"""
+from __future__ import annotations
+
+import heapq
+import math
+
+import numpy as np
+
+from .fem import Element, face_corners, face_nodes, face_point, lagrange, tensor_basis
+from .quadrature import gauss_lobatto, level_symmetric_2d
+
+
+class CycleError(RuntimeError):
+    pass
+
+
+class Discretization:
+    """Mesh, finite elements, quadrature and per-element matrices."""
+
+    def __init__(self, nodes, elem_nodes, m: int, p: int, sn: int, sigma_t, sigma_s):
+        nodes = np.asarray(nodes, float)
+        elem_nodes = np.asarray(elem_nodes)
+        self.m, self.p, self.sn = m, p, sn
+        self.n = (p + 1) ** 2
+        self.ne = len(elem_nodes)
+        self.sigma_t = np.asarray(sigma_t, float)
+        self.sigma_s = np.asarray(sigma_s, float)
+        self.omega, self.wq = level_symmetric_2d(sn)
+        self.nd = len(self.wq)
+        self.elems = [Element(nodes[elem_nodes[e]], m, p) for e in range(self.ne)]
+        self.faces = [[el.face(f) for f in range(4)] for el in self.elems]
+        self.M = [el.mass() for el in self.elems]
+        st = [el.stream() for el in self.elems]
+        self.Gx = [g[0] for g in st]
+        self.Gy = [g[1] for g in st]
+        # connectivity from shared corner control points
+        owner = {}
+        for e in range(self.ne):
+            for f in range(4):
+                c0, c1 = face_corners(m, f)
+                key = frozenset((int(elem_nodes[e, c0]), int(elem_nodes[e, c1])))
+                owner.setdefault(key, []).append((e, f))
+        self.nbr = [[None] * 4 for _ in range(self.ne)]
+        for key, lst in owner.items():
+            if len(lst) == 2:
+                (e1, f1), (e2, f2) = lst
+                a1 = int(elem_nodes[e1, face_corners(m, f1)[0]])
+                a2 = int(elem_nodes[e2, face_corners(m, f2)[0]])
+                flip = a1 != a2
+                self.nbr[e1][f1] = (e2, f2, flip)
+                self.nbr[e2][f2] = (e1, f1, flip)
+            elif len(lst) > 2:
+                raise ValueError("non-manifold face")
+        self.bfaces = [(e, f) for e in range(self.ne) for f in range(4) if self.nbr[e][f] is None]
+        self.bindex = {ef: b for b, ef in enumerate(self.bfaces)}
+        # neighbour basis at this face's quadrature points (matching points)
+        self.Vnb = [[None] * 4 for _ in range(self.ne)]
+        gp, _ = gauss_lobatto(p + 1)
+        for e in range(self.ne):
+            for f in range(4):
+                if self.nbr[e][f] is None:
+                    continue
+                e2, f2, flip = self.nbr[e][f]
+                s = self.elems[e].fq_s
+                s2 = 1.0 - s if flip else s
+                xi2, eta2 = face_point(f2, s2)
+                V2, _ = tensor_basis(gp, xi2, eta2)
+                self.Vnb[e][f] = V2
+        # 1D Lagrange (face nodes) at face quadrature points, for inflow data
+        self.L1, _ = lagrange(gp, self.elems[0].fq_s) if self.ne else (None, None)
+
+    # -- upwind graph -------------------------------------------------------
+    def upwind_order(self, d: int):
+        """Topological order of the elements for ordinate d (smallest index
+        first among ready elements); raises CycleError on a cycle."""
+        if not hasattr(self, "_orders"):
+            self._orders = {}
+        if d not in self._orders:
+            self._orders[d] = self._topological_order(d)
+        return self._orders[d]
+
+    def _topological_order(self, d: int):
+        om = self.omega[d]
+        deps = [set() for _ in range(self.ne)]
+        for e in range(self.ne):
+            for f in range(4):
+                nb = self.nbr[e][f]
+                if nb is None:
+                    continue
+                a = self.faces[e][f]["nds"] @ om
+                if np.any(a < 0.0):
+                    deps[e].add(nb[0])
+        indeg = [len(s) for s in deps]
+        down = [[] for _ in range(self.ne)]
+        for e in range(self.ne):
+            for u in deps[e]:
+                down[u].append(e)
+        ready = [e for e in range(self.ne) if indeg[e] == 0]
+        heapq.heapify(ready)
+        order = []
+        while ready:
+            u = heapq.heappop(ready)
+            order.append(u)
+            for v in down[u]:
+                indeg[v] -= 1
+                if indeg[v] == 0:
+                    heapq.heappush(ready, v)
+        if len(order) != self.ne:
+            raise CycleError(f"upwind graph of ordinate {d} has a cycle")
+        return order
+
+    # -- local system -------------------------------------------------------
+    def local_matrix(self, e: int, d: int):
+        """A_{K,d}: streaming + collision + outflow face terms."""
+        ox, oy = self.omega[d]
+        A = self.sigma_t[e] * self.M[e] - ox * self.Gx[e] - oy * self.Gy[e]
+        for f in range(4):
+            fd = self.faces[e][f]
+            a = fd["nds"] @ self.omega[d]
+            A = A + fd["V"].T @ (np.maximum(a, 0.0)[:, None] * fd["V"])
+        return A
+
+    def upwind_values(self, e, f, d, psi, psibar):
+        """psi^up at the quadrature points of face f of element e."""
+        nb = self.nbr[e][f]
+        if nb is not None:
+            return self.Vnb[e][f] @ psi[nb[0]]
+        if psibar is None:
+            return np.zeros(len(self.elems[e].fq_s))
+        return self.L1 @ psibar[d][self.bindex[(e, f)]]
+
+    def sweep_ordinate(self, d: int, src, psibar=None):
+        """Solve L psi_d = src_d with inflow psibar; src: [ne][n] nodal
+        values of the total source for this ordinate; psibar: None (vacuum)
+        or [nd][n_bface][p+1] face-node values."""
+        psi = np.zeros((self.ne, self.n))
+        for e in self.upwind_order(d):
+            A = self.local_matrix(e, d)
+            b = self.M[e] @ src[e]
+            for f in range(4):
+                fd = self.faces[e][f]
+                a = fd["nds"] @ self.omega[d]
+                neg = np.minimum(a, 0.0)
+                if np.any(neg < 0.0):
+                    up = self.upwind_values(e, f, d, psi, psibar)
+                    b = b - fd["V"].T @ (neg * up)
+            psi[e] = np.linalg.solve(A, b)
+        return psi
+
+    def sweep(self, varphi, q, psibar=None):
+        """psi = L^{-1}(sigma_s/(4 pi) varphi + q) for all ordinates.
+
+        varphi: [ne][n] nodal scalar flux (or None for zero);
+        q: [ne][n] isotropic or [nd][ne][n] angular source per steradian.
+        Returns psi [nd][ne][n]."""
+        q = np.asarray(q, float)
+        out = np.zeros((self.nd, self.ne, self.n))
+        scat = np.zeros((self.ne, self.n))
+        if varphi is not None:
+            scat = (self.sigma_s / (4.0 * math.pi))[:, None] * np.asarray(varphi, float)
+        for d in range(self.nd):
+            qd = q if q.ndim == 2 else q[d]
+            out[d] = self.sweep_ordinate(d, scat + qd, psibar)
+        return out
+
+    # -- global assembly of one ordinate's DG system (brute force check) ------
+    def global_ordinate_matrix(self, d: int):
+        """Dense matrix of the whole single-ordinate DG system (all elements
+        coupled through upwind face terms): row block e, column block of the
+        upwind neighbour holds + int_F min(Omega.n,0) psi_nb v."""
+        n, ne = self.n, self.ne
+        A = np.zeros((ne * n, ne * n))
+        for e in range(ne):
+            A[e * n:(e + 1) * n, e * n:(e + 1) * n] = self.local_matrix(e, d)
+            for f in range(4):
+                nb = self.nbr[e][f]
+                if nb is None:
+                    continue
+                fd = self.faces[e][f]
+                neg = np.minimum(fd["nds"] @ self.omega[d], 0.0)
+                A[e * n:(e + 1) * n, nb[0] * n:(nb[0] + 1) * n] += fd["V"].T @ (neg[:, None] * self.Vnb[e][f])
+        return A
+
+    def global_ordinate_rhs(self, d: int, src, psibar=None):
+        n, ne = self.n, self.ne
+        b = np.zeros(ne * n)
+        zero = np.zeros((ne, n))
+        for e in range(ne):
+            b[e * n:(e + 1) * n] = self.M[e] @ src[e]
+            for f in range(4):
+                if self.nbr[e][f] is not None:
+                    continue
+                fd = self.faces[e][f]
+                neg = np.minimum(fd["nds"] @ self.omega[d], 0.0)
+                up = self.upwind_values(e, f, d, zero, psibar)
+                b[e * n:(e + 1) * n] -= fd["V"].T @ (neg * up)
+        return b
+
+    # -- helpers --------------------------------------------------------------
+    def interpolate(self, func):
+        """Nodal values [ne][n] of func(x, y) at the physical nodal points
+        (element map applied to the Gauss-Lobatto reference nodes)."""
+        gp, _ = gauss_lobatto(self.p + 1)
+        XI, ETA = np.meshgrid(gp, gp, indexing="xy")
+        out = np.zeros((self.ne, self.n))
+        for e, el in enumerate(self.elems):
+            x, _ = el.map(XI.ravel(), ETA.ravel())
+            out[e] = func(x[:, 0], x[:, 1])
+        return out
+
+    def l2_error(self, u, func):
+        """|| u - func ||_{L2(D)} with the element quadrature."""
+        s = 0.0
+        for e, el in enumerate(self.elems):
+            uq = el.V @ u[e]
+            ex = func(el.x[:, 0], el.x[:, 1])
+            s += np.sum(el.w * el.J * (uq - ex) ** 2)
+        return math.sqrt(s)
+
+    def integrate(self, u):
+        return float(sum(np.sum(el.w * el.J * (el.V @ u[e])) for e, el in enumerate(self.elems)))
+
+    def max_h(self):
+        return max(math.sqrt(el.area()) for el in self.elems)
