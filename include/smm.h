@@ -1,0 +1,184 @@
+/*
+ * smm.h -- C ABI of the GB300 second-moment-method (SMM) transport library.
+ *
+ * The library solves the mono-energetic, steady, fixed-source transport
+ * problem with isotropic scattering and inflow boundary conditions
+ * (paper Sec. "Moment Methods for Radiation Transport", Eqs. transport and
+ * inflow) by the SMM fixed-point iteration (Eqs. moment:smm_fp and
+ * fixed-point):
+ *
+ *     varphi^{k+1} = D^{-1} b( L^{-1}( sigma_s/(4 pi) varphi^k + q ) ),
+ *
+ * where L^{-1} is a high-order upwind DG S_N transport sweep on curved
+ * quadrilaterals (Sec. "Transport Discretization"), b(.) builds the
+ * interior penalty SMM right-hand side from the discrete closures
+ * (Eqs. correction_tensor_disc, bdr_correction_factor_disc, eb0_disc,
+ * broken_Tdiv, ipsmm) and D is the fixed, symmetric IP diffusion operator
+ * (Eq. ipsmm, left-hand side), solved by preconditioned CG.
+ *
+ * Conventions (all calls):
+ *  - Reference element [0,1]^2; nodal points on tensor Gauss-Lobatto points,
+ *    lexicographic with x fastest: i = iy*(k+1) + ix.  DG order p: n = (p+1)^2
+ *    nodal values per element.  Geometry order m: (m+1)^2 control points.
+ *  - Faces: 0 bottom (eta=0), 1 right (xi=1), 2 top (eta=1), 3 left (xi=0);
+ *    the face parameter s increases with the reference coordinate that
+ *    varies along the face.  Boundary faces are numbered by ascending
+ *    (element, face).
+ *  - Ordinates (level-symmetric LQ_N, N in {2,4,6,8,10,12}, N(N+2)/2 of them
+ *    in 2D) are numbered quadrant-major: (+,+), (-,+), (-,-), (+,-); within
+ *    a quadrant by the octant level triple (i,j,k), i then j ascending.
+ *    Weights sum to 4 pi.
+ *  - Host pointers ("host") are read during the call only; the caller keeps
+ *    ownership.  Device pointers ("dev") must be allocated by the caller on
+ *    the device of the handle's stream; the library never frees them.
+ *  - Every call returns an smm_status; nothing aborts or throws across the
+ *    ABI.  smm_last_error() gives a message for the calling thread's most
+ *    recent failure.  After SMM_ERR_CUDA the handle must only be destroyed.
+ *  - One handle per stream; calls on one handle are not thread safe.
+ */
+#ifndef SMM_H
+#define SMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smm_ctx* smm_handle;
+
+typedef enum {
+    SMM_OK = 0,
+    SMM_ERR_INVALID_ARG = 1,    /* bad size, NULL where required, unsupported order */
+    SMM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    SMM_ERR_OOM = 3,            /* device allocation failed */
+    SMM_ERR_MESH = 4,           /* non-positive Jacobian, broken connectivity */
+    SMM_ERR_CYCLE = 5,          /* an ordinate's upwind graph has a cycle, or a
+                                   face is inflow at some points and outflow at
+                                   others (no lagging is done) */
+    SMM_ERR_NONFINITE = 6,      /* NaN/Inf in an iterate */
+    SMM_ERR_NOT_CONVERGED = 7,  /* iteration limit reached; the iterate is kept */
+    SMM_ERR_DEVICE_TIMEOUT = 8  /* a bounded device-side wait expired */
+} smm_status;
+
+enum { SMM_SOURCE_ISOTROPIC = 0, SMM_SOURCE_ANGULAR = 1 };
+enum { SMM_INFLOW_VACUUM = 0, SMM_INFLOW_NODAL = 1 };
+enum { SMM_SWEEP_FP64 = 0, SMM_SWEEP_FP32_REFINED = 1 };
+
+typedef struct {
+    int32_t n_elem;             /* number of quadrilaterals */
+    int32_t geom_order;         /* m >= 1 */
+    int32_t n_nodes;            /* number of control points */
+    const double* nodes;        /* host [n_nodes][2] control point coordinates */
+    const int32_t* elem_nodes;  /* host [n_elem][(m+1)^2] control point ids,
+                                   lexicographic Gauss-Lobatto order; elements
+                                   must be positively oriented (J > 0) and
+                                   neighbours share face control points */
+} smm_mesh;
+
+typedef struct {
+    int32_t sweep_precision;    /* SMM_SWEEP_FP64 (default): local solves in
+                                   FP64.  SMM_SWEEP_FP32_REFINED: each sweep
+                                   solves for a correction in FP32 from an FP64
+                                   transport residual (moments, CG, checks stay
+                                   FP64). */
+    double tol_cg;              /* CG stop: ||r||_2 <= tol_cg ||b||_2 (default 1e-12) */
+    int32_t max_cg;             /* CG iteration cap per moment solve (default 20000) */
+    double kappa_scale;         /* multiplies the IP penalty (default 1) */
+    double spin_timeout_s;      /* bound on every device-side wait (default 2 s) */
+} smm_options;
+
+typedef struct {
+    int32_t n_elem, p, m, n_dof_elem, n_ord, n_bface, n_fq, n_levels;
+    int64_t n_angular;          /* n_elem * n_dof_elem * n_ord */
+} smm_info;
+
+typedef struct {
+    int32_t outer_iterations;
+    int32_t cg_total, cg_min, cg_max; /* CG iterations over the outer steps */
+    double last_diff;           /* max |varphi^{k+1} - varphi^k| of the last step */
+    double last_rel_diff;       /* last_diff / max |varphi^{k+1}| */
+    double ms_sweep, ms_moments, ms_rhs, ms_solve; /* accumulated phase times */
+} smm_stats;
+
+/* Fill *opt with the defaults listed above. */
+void smm_default_options(smm_options* opt);
+
+/* The library's level-symmetric quadrature for S_N order sn_order
+ * (paper: "Level Symmetric S_N", not printed; LQ_N construction).
+ * omega_out: host [n_ord][2] (may be NULL), w_out: host [n_ord] (may be
+ * NULL), n_ord_out: number of ordinates N(N+2)/2.
+ * Errors: SMM_ERR_INVALID_ARG for unsupported orders. */
+smm_status smm_quadrature(int32_t sn_order, double* omega_out, double* w_out, int32_t* n_ord_out);
+
+/* Build a solver: geometry factors, element and face matrices, upwind
+ * level lists per ordinate, the IP-SMM operator blocks and its block-Jacobi
+ * preconditioner; uploads everything to the device of cuda_stream (NULL =
+ * legacy default stream of the current device).
+ *   p: DG order 1..4.  sn_order: see smm_quadrature.
+ *   sigma_t, sigma_s: host [n_elem], piecewise constant, sigma_t > 0,
+ *     0 <= sigma_s <= sigma_t.
+ *   source_kind SMM_SOURCE_ISOTROPIC: q host [n_elem][n] nodal values per
+ *     steradian; SMM_SOURCE_ANGULAR: q host [n_ord][n_elem][n].
+ *   inflow_kind SMM_INFLOW_VACUUM: inflow ignored (may be NULL);
+ *     SMM_INFLOW_NODAL: inflow host [n_ord][n_bface][p+1], psibar at the face
+ *     nodal points in increasing s (used only where the ordinate enters).
+ *   opt: NULL for defaults.
+ * Errors: INVALID_ARG, MESH (J <= 0 at a quadrature point, a face shared by
+ * more than two elements), CYCLE (see above), OOM, CUDA. */
+smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order,
+                      const double* sigma_t, const double* sigma_s,
+                      int32_t source_kind, const double* q,
+                      int32_t inflow_kind, const double* inflow,
+                      const smm_options* opt, void* cuda_stream, smm_handle* out);
+
+smm_status smm_get_info(smm_handle h, smm_info* info);
+
+/* One transport sweep psi = L^{-1}(sigma_s/(4 pi) varphi + q) over all
+ * ordinates, followed by the angular moments and the boundary correction
+ * (Eqs. correction_tensor_disc, bdr_correction_factor_disc), kept in the
+ * handle.  phi_dev: dev [n_elem][n] FP64, or NULL for varphi = 0.
+ * In SMM_SWEEP_FP32_REFINED mode the sweep corrects the handle's current
+ * angular flux (zero after create) and repeated calls converge to the FP64
+ * result.  Errors: DEVICE_TIMEOUT, CUDA. */
+smm_status smm_sweep(smm_handle h, const double* phi_dev);
+
+/* Copy the moments of the last sweep.  moments_dev: dev [6][n_elem][n]
+ * (phi, Jx, Jy, Txx, Txy, Tyy), or NULL; beta_dev: dev [n_bface][n_fq]
+ * boundary correction beta at the face Gauss points, or NULL. */
+smm_status smm_moments(smm_handle h, double* moments_dev, double* beta_dev);
+
+/* Replace the handle's closures (the state a sweep would leave): used to
+ * solve the moment system with given T and beta (paper's isolated MMS
+ * study) and to restore a checkpoint.  Same layouts as smm_moments. */
+smm_status smm_set_moments(smm_handle h, const double* moments_dev, const double* beta_dev);
+
+/* Copy the angular flux of the last sweep: psi_dev dev [n_elem][n_ord][n] FP64. */
+smm_status smm_get_psi(smm_handle h, double* psi_dev);
+
+/* Solve the IP-SMM moment system (Eq. ipsmm) with the handle's closures by
+ * block-Jacobi preconditioned CG.  phi_dev: dev [n_elem][n], in: initial
+ * guess, out: solution.  cg_iters (host, may be NULL): iterations used.
+ * Errors: NOT_CONVERGED (phi_dev holds the last iterate), NONFINITE, CUDA. */
+smm_status smm_moment_solve(smm_handle h, double* phi_dev, int32_t* cg_iters);
+
+/* The SMM fixed-point iteration from the guess in phi_dev (dev [n_elem][n]):
+ * sweep, moments, right-hand side, moment solve, until
+ * max|varphi^{k+1}-varphi^k| < tol (relative == 0) or
+ * max|varphi^{k+1}-varphi^k| / max|varphi^{k+1}| < tol (relative != 0), or
+ * max_outer steps.  phi_dev receives the last iterate.  stats may be NULL.
+ * Errors: NOT_CONVERGED, NONFINITE, DEVICE_TIMEOUT, CUDA. */
+smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_outer,
+                       double* phi_dev, smm_stats* stats);
+
+smm_status smm_destroy(smm_handle h);
+
+/* Message of the calling thread's most recent error ("" if none); valid
+ * until the next call on that thread. */
+const char* smm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMM_H */

@@ -1,0 +1,7 @@
+"""GB300-native second-moment-method (SMM) transport: C-ABI library
+(libsmm.so, hand-written CUDA for sm_103a) and its thin Python binding."""
+from .smm import (Handle, SMMError, load_library, smm_create, smm_default_options, smm_destroy, smm_get_psi,
+                  smm_iterate, smm_moment_solve, smm_moments, smm_quadrature, smm_set_moments, smm_sweep)
+
+__all__ = ["Handle", "SMMError", "load_library", "smm_create", "smm_default_options", "smm_destroy", "smm_get_psi",
+           "smm_iterate", "smm_moment_solve", "smm_moments", "smm_quadrature", "smm_set_moments", "smm_sweep"]

@@ -1,0 +1,500 @@
+// C ABI of the SMM library (include/smm.h): handle, device buffers and the
+// outer fixed-point driver (paper Eqs. moment:smm_fp and fixed-point).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/smm.h"
+#include "kernels.cuh"
+#include "setup.hpp"
+
+namespace {
+
+thread_local std::string g_err;
+
+smm_status fail(smm_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define SMM_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(SMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+}  // namespace
+
+struct smm_ctx {
+    int ne = 0, m = 1, p = 1, p1 = 2, n = 4, nd = 0, nb = 0, nfq = 0, nlevels = 0, ntask = 0;
+    int src_angular = 0, has_inflow = 0;
+    bool fp32 = false;
+    smm_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0, sms = 1, sweep_grid = 1;
+    unsigned epoch = 0;
+    std::vector<void*> allocs;
+    // quadrature / connectivity
+    double *ox = nullptr, *oy = nullptr, *w = nullptr, *sigma_t = nullptr, *sigma_s = nullptr;
+    int32_t *tasks = nullptr, *nbr = nullptr, *nbr_face = nullptr, *nbr_flip = nullptr, *bface_id = nullptr;
+    int32_t *bface_elem = nullptr, *bface_face = nullptr;
+    int8_t* fdir = nullptr;
+    // sweep matrices
+    double *M = nullptr, *Gx = nullptr, *Gy = nullptr, *Fx = nullptr, *Fy = nullptr;
+    float *M32 = nullptr, *Gx32 = nullptr, *Gy32 = nullptr, *Fx32 = nullptr, *Fy32 = nullptr;
+    double *src = nullptr, *inflow = nullptr;
+    // state
+    double* psi = nullptr;         // [ne][nd][n] FP64
+    float* dpsi = nullptr;         // [ne][nd][n] FP32 correction (refined mode)
+    float* res = nullptr;          // [ne][nd][n] FP32 residual (refined mode)
+    unsigned* done = nullptr;
+    unsigned* ticket = nullptr;
+    int* err = nullptr;
+    double *mom = nullptr, *beta = nullptr;
+    // closures / rhs data
+    double *L1 = nullptr, *b_nhat = nullptr, *b_ds = nullptr, *b_eb0 = nullptr;
+    double *Kxx = nullptr, *Ks = nullptr, *Kyy = nullptr, *Dfx = nullptr, *Dfy = nullptr, *nds = nullptr;
+    double *bfixed = nullptr, *trace = nullptr, *rhs = nullptr;
+    // moment operator and CG
+    double *AdT = nullptr, *AoT = nullptr, *PinvT = nullptr;
+    double *r = nullptr, *z = nullptr, *pv = nullptr, *qv = nullptr, *part = nullptr, *scal = nullptr;
+    double *phi_prev = nullptr, *dpart = nullptr, *dout = nullptr;
+    int* ctl = nullptr;
+    int* nonfinite = nullptr;
+    int cg_nblk = 1;
+    // pinned host scratch
+    double* h_scal = nullptr;
+    int* h_int = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+
+    template <class T>
+    T* alloc(size_t count) {
+        if (count == 0) count = 1;
+        void* ptr = nullptr;
+        if (cudaMalloc(&ptr, count * sizeof(T)) != cudaSuccess) return nullptr;
+        allocs.push_back(ptr);
+        return (T*)ptr;
+    }
+    ~smm_ctx() {
+        for (void* ptr : allocs) cudaFree(ptr);
+        if (h_scal) cudaFreeHost(h_scal);
+        if (h_int) cudaFreeHost(h_int);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+template <class T>
+bool upload(smm_ctx* h, T*& dst, const std::vector<T>& src) {
+    dst = h->alloc<T>(src.size());
+    if (!dst) return false;
+    if (src.empty()) return true;
+    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+}
+
+template <class T>
+bool upload_f32(smm_ctx* h, float*& dst, const std::vector<T>& src) {
+    std::vector<float> tmp(src.begin(), src.end());
+    bool ok = upload(h, dst, tmp);
+    return ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
+}
+
+// transpose each n x n block ([blk][i][j] -> [blk][j][i])
+std::vector<double> transpose_blocks(const std::vector<double>& a, int n) {
+    std::vector<double> t(a.size());
+    const size_t nb = a.size() / ((size_t)n * n);
+    for (size_t b = 0; b < nb; ++b)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) t[b * n * n + (size_t)j * n + i] = a[b * n * n + (size_t)i * n + j];
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+void smm_default_options(smm_options* opt) {
+    if (!opt) return;
+    opt->sweep_precision = SMM_SWEEP_FP64;
+    opt->tol_cg = 1e-12;
+    opt->max_cg = 20000;
+    opt->kappa_scale = 1.0;
+    opt->spin_timeout_s = 2.0;
+}
+
+const char* smm_last_error(void) { return g_err.c_str(); }
+
+smm_status smm_quadrature(int32_t sn_order, double* omega_out, double* w_out, int32_t* n_ord_out) {
+    smm::Quadrature q;
+    if (!smm::level_symmetric(sn_order, q)) return fail(SMM_ERR_INVALID_ARG, "unsupported S_N order");
+    for (int d = 0; d < q.nd; ++d) {
+        if (omega_out) { omega_out[2 * d] = q.ox[d]; omega_out[2 * d + 1] = q.oy[d]; }
+        if (w_out) w_out[d] = q.w[d];
+    }
+    if (n_ord_out) *n_ord_out = q.nd;
+    return SMM_OK;
+}
+
+smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const double* sigma_t, const double* sigma_s,
+                      int32_t source_kind, const double* q, int32_t inflow_kind, const double* inflow,
+                      const smm_options* opt, void* cuda_stream, smm_handle* out) {
+    if (!out) return fail(SMM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!mesh) return fail(SMM_ERR_INVALID_ARG, "mesh is NULL");
+    if (source_kind != SMM_SOURCE_ISOTROPIC && source_kind != SMM_SOURCE_ANGULAR)
+        return fail(SMM_ERR_INVALID_ARG, "bad source kind");
+    if (inflow_kind != SMM_INFLOW_VACUUM && inflow_kind != SMM_INFLOW_NODAL)
+        return fail(SMM_ERR_INVALID_ARG, "bad inflow kind");
+    smm_options o;
+    smm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.sweep_precision != SMM_SWEEP_FP64 && o.sweep_precision != SMM_SWEEP_FP32_REFINED)
+        return fail(SMM_ERR_INVALID_ARG, "bad sweep precision");
+    if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0))
+        return fail(SMM_ERR_INVALID_ARG, "bad options");
+
+    smm::Input in;
+    in.ne = mesh->n_elem; in.m = mesh->geom_order; in.p = p; in.sn = sn_order; in.n_nodes = mesh->n_nodes;
+    in.nodes = mesh->nodes; in.elem_nodes = mesh->elem_nodes; in.sigma_t = sigma_t; in.sigma_s = sigma_s;
+    in.source_kind = source_kind; in.q = q; in.inflow_kind = inflow_kind; in.inflow = inflow;
+    in.kappa_scale = o.kappa_scale;
+    smm::Setup s;
+    std::string err;
+    int rc = smm::build_setup(in, s, err);
+    if (rc != 0) return fail((smm_status)rc, err);
+
+    smm_ctx* h = new smm_ctx();
+    h->opt = o;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->ne = s.ne; h->m = s.m; h->p = s.p; h->p1 = s.p1; h->n = s.n; h->nd = s.nd; h->nb = s.nb; h->nfq = s.nfq;
+    h->nlevels = s.nlevels; h->ntask = (int)s.tasks.size();
+    h->src_angular = source_kind == SMM_SOURCE_ANGULAR;
+    h->has_inflow = !s.inflow.empty();
+    h->fp32 = o.sweep_precision == SMM_SWEEP_FP32_REFINED;
+    auto bail = [&](smm_status st, const std::string& msg) { delete h; return fail(st, msg); };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(SMM_ERR_CUDA, "cudaGetDevice failed");
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+
+    bool ok = true;
+    ok &= upload(h, h->ox, s.quad.ox) && upload(h, h->oy, s.quad.oy) && upload(h, h->w, s.quad.w);
+    ok &= upload(h, h->sigma_t, s.sigma_t) && upload(h, h->sigma_s, s.sigma_s);
+    ok &= upload(h, h->tasks, s.tasks) && upload(h, h->fdir, s.fdir);
+    ok &= upload(h, h->nbr, s.nbr) && upload(h, h->nbr_face, s.nbr_face) && upload(h, h->nbr_flip, s.nbr_flip);
+    ok &= upload(h, h->bface_id, s.bface_id) && upload(h, h->bface_elem, s.bface_elem) && upload(h, h->bface_face, s.bface_face);
+    ok &= upload(h, h->M, s.M) && upload(h, h->Gx, s.Gx) && upload(h, h->Gy, s.Gy);
+    ok &= upload(h, h->Fx, s.Fx) && upload(h, h->Fy, s.Fy);
+    ok &= upload(h, h->src, s.src) && upload(h, h->inflow, s.inflow);
+    ok &= upload(h, h->L1, s.L1) && upload(h, h->b_nhat, s.b_nhat) && upload(h, h->b_ds, s.b_ds) && upload(h, h->b_eb0, s.b_eb0);
+    ok &= upload(h, h->Kxx, s.Kxx) && upload(h, h->Ks, s.Ks) && upload(h, h->Kyy, s.Kyy);
+    ok &= upload(h, h->Dfx, s.Dfx) && upload(h, h->Dfy, s.Dfy) && upload(h, h->nds, s.nds) && upload(h, h->bfixed, s.bfixed);
+    if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
+    {
+        std::vector<double> t = transpose_blocks(s.Adiag, s.n);
+        ok &= upload(h, h->AdT, t);
+        t = transpose_blocks(s.Aoff, s.n);
+        ok &= upload(h, h->AoT, t);
+        t = transpose_blocks(s.Pinv, s.n);
+        ok &= upload(h, h->PinvT, t);
+        ok &= cudaStreamSynchronize(h->stream) == cudaSuccess;
+    }
+    if (h->fp32) {
+        ok &= upload_f32(h, h->M32, s.M) && upload_f32(h, h->Gx32, s.Gx) && upload_f32(h, h->Gy32, s.Gy);
+        ok &= upload_f32(h, h->Fx32, s.Fx) && upload_f32(h, h->Fy32, s.Fy);
+    }
+    if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
+    const size_t nang = (size_t)s.ne * s.nd * s.n, nphi = (size_t)s.ne * s.n;
+    h->psi = h->alloc<double>(nang);
+    if (h->fp32) {
+        h->dpsi = h->alloc<float>(nang);
+        h->res = h->alloc<float>(nang);
+        if (!h->dpsi || !h->res) return bail(SMM_ERR_OOM, "device allocation failed");
+    }
+    h->done = h->alloc<unsigned>((size_t)s.ne * s.nd);
+    h->ticket = h->alloc<unsigned>(4);
+    h->err = h->alloc<int>(4);
+    h->mom = h->alloc<double>(6 * nphi);
+    h->beta = h->alloc<double>((size_t)s.nb * s.nfq);
+    h->trace = h->alloc<double>((size_t)s.ne * 4 * s.nfq * 3);
+    h->rhs = h->alloc<double>(nphi);
+    h->r = h->alloc<double>(nphi);
+    h->z = h->alloc<double>(nphi);
+    h->pv = h->alloc<double>(nphi);
+    h->qv = h->alloc<double>(nphi);
+    h->phi_prev = h->alloc<double>(nphi);
+    const int epb = smm::cg_threads_per_block(s.n) / s.n;
+    h->cg_nblk = (s.ne + epb - 1) / epb;
+    h->part = h->alloc<double>(3 * (size_t)h->cg_nblk);
+    h->scal = h->alloc<double>(8);
+    h->ctl = h->alloc<int>(8);
+    h->dpart = h->alloc<double>(2 * 256);
+    h->dout = h->alloc<double>(2);
+    h->nonfinite = h->alloc<int>(1);
+    if (!h->psi || !h->done || !h->ticket || !h->err || !h->mom || !h->beta || !h->trace || !h->rhs || !h->r || !h->z ||
+        !h->pv || !h->qv || !h->phi_prev || !h->part || !h->scal || !h->ctl || !h->dpart || !h->dout || !h->nonfinite)
+        return bail(SMM_ERR_OOM, "device allocation failed");
+    if (cudaMemsetAsync(h->psi, 0, nang * sizeof(double), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->done, 0, (size_t)s.ne * s.nd * sizeof(unsigned), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->err, 0, 4 * sizeof(int), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->mom, 0, 6 * nphi * sizeof(double), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->beta, 0, (size_t)std::max(1, s.nb * s.nfq) * sizeof(double), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->ctl, 0, 8 * sizeof(int), h->stream) != cudaSuccess)
+        return bail(SMM_ERR_CUDA, "cudaMemsetAsync failed");
+    if (h->fp32 && cudaMemsetAsync(h->dpsi, 0, nang * sizeof(float), h->stream) != cudaSuccess)
+        return bail(SMM_ERR_CUDA, "cudaMemsetAsync failed");
+    if (cudaMallocHost(&h->h_scal, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->h_int, 8 * sizeof(int)) != cudaSuccess)
+        return bail(SMM_ERR_OOM, "pinned allocation failed");
+    for (auto& e : h->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bail(SMM_ERR_CUDA, "cudaEventCreate failed");
+    const int bps = smm::sweep_blocks_per_sm(s.p, h->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE, h->fp32);
+    const long long want = ((long long)h->ntask + 7) / 8;
+    h->sweep_grid = (int)std::max(1LL, std::min<long long>((long long)h->sms * bps, want));
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(SMM_ERR_CUDA, "setup upload failed");
+    *out = h;
+    return SMM_OK;
+}
+
+smm_status smm_get_info(smm_handle h, smm_info* info) {
+    if (!h || !info) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
+    info->n_elem = h->ne; info->p = h->p; info->m = h->m; info->n_dof_elem = h->n; info->n_ord = h->nd;
+    info->n_bface = h->nb; info->n_fq = h->nfq; info->n_levels = h->nlevels;
+    info->n_angular = (int64_t)h->ne * h->n * h->nd;
+    return SMM_OK;
+}
+
+smm_status smm_destroy(smm_handle h) {
+    if (!h) return SMM_OK;
+    if (h->stream || true) cudaStreamSynchronize(h->stream);
+    delete h;
+    return SMM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// enqueue one sweep + moments + beta; no host synchronization
+smm_status enqueue_sweep(smm_handle h, const double* phi) {
+    SMM_CUDA(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream));
+    h->epoch += 1;
+    if (h->epoch == 0) {  // wrap: reset flags
+        SMM_CUDA(cudaMemsetAsync(h->done, 0, (size_t)h->ne * h->nd * sizeof(unsigned), h->stream));
+        h->epoch = 1;
+    }
+    const long long tmo = (long long)(h->opt.spin_timeout_s * 1e9);
+    if (!h->fp32) {
+        smm::SweepArgs<double> a{};
+        a.ne = h->ne; a.nd = h->nd; a.ntask = h->ntask; a.tasks = h->tasks; a.ox = h->ox; a.oy = h->oy;
+        a.sigma_t = h->sigma_t; a.sigma_s = h->sigma_s; a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy;
+        a.fdir = h->fdir; a.nbr = h->nbr; a.nbr_face = h->nbr_face; a.nbr_flip = h->nbr_flip; a.bface_id = h->bface_id;
+        a.phi = phi; a.src = h->src; a.src_angular = h->src_angular; a.inflow = h->has_inflow ? h->inflow : nullptr;
+        a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr; a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket;
+        a.err = h->err; a.timeout_ns = tmo;
+        smm::launch_sweep<double>(h->p, smm::SWEEP_SOURCE, a, h->sweep_grid, h->stream);
+    } else {
+        smm::ResidualArgs r{};
+        r.ne = h->ne; r.nd = h->nd; r.ntask = h->ntask; r.ox = h->ox; r.oy = h->oy; r.sigma_t = h->sigma_t;
+        r.sigma_s = h->sigma_s; r.M = h->M; r.Gx = h->Gx; r.Gy = h->Gy; r.Fx = h->Fx; r.Fy = h->Fy; r.fdir = h->fdir;
+        r.nbr = h->nbr; r.nbr_face = h->nbr_face; r.nbr_flip = h->nbr_flip; r.bface_id = h->bface_id; r.phi = phi;
+        r.src = h->src; r.src_angular = h->src_angular; r.inflow = h->has_inflow ? h->inflow : nullptr; r.psi = h->psi;
+        r.rhs = h->res;
+        smm::launch_residual(h->p, r, h->stream);
+        smm::SweepArgs<float> a{};
+        a.ne = h->ne; a.nd = h->nd; a.ntask = h->ntask; a.tasks = h->tasks; a.ox = h->ox; a.oy = h->oy;
+        a.sigma_t = h->sigma_t; a.sigma_s = h->sigma_s; a.M = h->M32; a.Gx = h->Gx32; a.Gy = h->Gy32; a.Fx = h->Fx32;
+        a.Fy = h->Fy32; a.fdir = h->fdir; a.nbr = h->nbr; a.nbr_face = h->nbr_face; a.nbr_flip = h->nbr_flip;
+        a.bface_id = h->bface_id; a.phi = nullptr; a.src = nullptr; a.src_angular = 0; a.inflow = nullptr; a.rhs = h->res;
+        a.psi = h->dpsi; a.psi_acc = h->psi; a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket; a.err = h->err;
+        a.timeout_ns = tmo;
+        smm::launch_sweep<float>(h->p, smm::SWEEP_RESIDUAL, a, h->sweep_grid, h->stream);
+    }
+    SMM_CUDA(cudaGetLastError());
+    return SMM_OK;
+}
+
+smm_status enqueue_moments(smm_handle h) {
+    smm::launch_moments(h->ne, h->nd, h->n, h->w, h->ox, h->oy, h->psi, h->mom, h->stream);
+    smm::launch_beta(h->nb, h->nd, h->n, h->p, h->nfq, h->bface_elem, h->bface_face, h->w, h->ox, h->oy, h->L1,
+                     h->b_nhat, h->b_eb0, h->psi, h->mom, h->beta, h->stream);
+    SMM_CUDA(cudaGetLastError());
+    return SMM_OK;
+}
+
+smm_status enqueue_rhs(smm_handle h) {
+    smm::launch_rhs(h->ne, h->n, h->p, h->nfq, h->mom, h->beta, h->bfixed, h->Kxx, h->Ks, h->Kyy, h->Dfx, h->Dfy, h->nds,
+                    h->L1, h->sigma_t, h->nbr, h->nbr_face, h->nbr_flip, h->bface_id, h->b_ds, h->trace, h->rhs,
+                    h->stream);
+    SMM_CUDA(cudaGetLastError());
+    return SMM_OK;
+}
+
+smm::CGArgs cg_args(smm_handle h, double* x) {
+    smm::CGArgs a{};
+    a.ne = h->ne; a.n = h->n; a.nrow = h->ne * h->n; a.nblk = h->cg_nblk;
+    a.AdT = h->AdT; a.AoT = h->AoT; a.PinvT = h->PinvT; a.nbr = h->nbr;
+    a.x = x; a.r = h->r; a.z = h->z; a.p = h->pv; a.q = h->qv; a.b = h->rhs; a.part = h->part; a.scal = h->scal;
+    a.ctl = h->ctl;
+    return a;
+}
+
+smm_status check_device_error(smm_handle h) {
+    SMM_CUDA(cudaMemcpyAsync(h->h_int, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->h_int[0] == smm::DEV_TIMEOUT) {
+        cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+        return fail(SMM_ERR_DEVICE_TIMEOUT, "a sweep dependency wait exceeded spin_timeout_s");
+    }
+    return SMM_OK;
+}
+
+// CG from the guess in x; host reads the control word every `chunk` iterations
+smm_status run_cg(smm_handle h, double* x, int* iters) {
+    smm::CGArgs a = cg_args(h, x);
+    SMM_CUDA(cudaMemsetAsync(h->ctl, 0, 8 * sizeof(int), h->stream));
+    smm::cg_start(a, h->opt.tol_cg, h->opt.max_cg, h->stream);
+    SMM_CUDA(cudaGetLastError());
+    int chunk = 8;
+    while (true) {
+        SMM_CUDA(cudaMemcpyAsync(h->h_int, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        SMM_CUDA(cudaStreamSynchronize(h->stream));
+        if (h->h_int[0]) break;
+        smm::cg_iterations(a, chunk, h->stream);
+        SMM_CUDA(cudaGetLastError());
+        chunk = std::min(chunk * 2, 64);
+    }
+    if (iters) *iters = h->h_int[1];
+    if (h->h_int[3]) return fail(SMM_ERR_NONFINITE, "non-finite value in the moment solve");
+    if (h->h_int[1] >= h->opt.max_cg) {
+        // converged exactly at the cap is still convergence
+        SMM_CUDA(cudaMemcpyAsync(h->h_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        SMM_CUDA(cudaStreamSynchronize(h->stream));
+        if (!(h->h_scal[2] <= h->h_scal[4])) return fail(SMM_ERR_NOT_CONVERGED, "CG iteration limit reached");
+    }
+    return SMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+smm_status smm_sweep(smm_handle h, const double* phi_dev) {
+    if (!h) return fail(SMM_ERR_INVALID_ARG, "NULL handle");
+    smm_status st = enqueue_sweep(h, phi_dev);
+    if (st != SMM_OK) return st;
+    st = enqueue_moments(h);
+    if (st != SMM_OK) return st;
+    return check_device_error(h);
+}
+
+smm_status smm_moments(smm_handle h, double* moments_dev, double* beta_dev) {
+    if (!h) return fail(SMM_ERR_INVALID_ARG, "NULL handle");
+    const size_t nphi = (size_t)h->ne * h->n;
+    if (moments_dev)
+        SMM_CUDA(cudaMemcpyAsync(moments_dev, h->mom, 6 * nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (beta_dev && h->nb)
+        SMM_CUDA(cudaMemcpyAsync(beta_dev, h->beta, (size_t)h->nb * h->nfq * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 h->stream));
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    return SMM_OK;
+}
+
+smm_status smm_set_moments(smm_handle h, const double* moments_dev, const double* beta_dev) {
+    if (!h || !moments_dev) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
+    const size_t nphi = (size_t)h->ne * h->n;
+    SMM_CUDA(cudaMemcpyAsync(h->mom, moments_dev, 6 * nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (h->nb) {
+        if (beta_dev)
+            SMM_CUDA(cudaMemcpyAsync(h->beta, beta_dev, (size_t)h->nb * h->nfq * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, h->stream));
+        else
+            SMM_CUDA(cudaMemsetAsync(h->beta, 0, (size_t)h->nb * h->nfq * sizeof(double), h->stream));
+    }
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    return SMM_OK;
+}
+
+smm_status smm_get_psi(smm_handle h, double* psi_dev) {
+    if (!h || !psi_dev) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
+    SMM_CUDA(cudaMemcpyAsync(psi_dev, h->psi, (size_t)h->ne * h->nd * h->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    return SMM_OK;
+}
+
+smm_status smm_moment_solve(smm_handle h, double* phi_dev, int32_t* cg_iters) {
+    if (!h || !phi_dev) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
+    smm_status st = enqueue_rhs(h);
+    if (st != SMM_OK) return st;
+    int it = 0;
+    st = run_cg(h, phi_dev, &it);
+    if (cg_iters) *cg_iters = it;
+    return st;
+}
+
+smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_outer, double* phi_dev,
+                       smm_stats* stats) {
+    if (!h || !phi_dev || !(tol > 0) || max_outer < 1) return fail(SMM_ERR_INVALID_ARG, "bad argument");
+    smm_stats local{};
+    local.cg_min = 1 << 30;
+    const size_t nphi = (size_t)h->ne * h->n;
+    smm_status result = SMM_ERR_NOT_CONVERGED;
+    for (int k = 1; k <= max_outer; ++k) {
+        SMM_CUDA(cudaMemcpyAsync(h->phi_prev, phi_dev, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        SMM_CUDA(cudaEventRecord(h->ev[0], h->stream));
+        smm_status st = enqueue_sweep(h, phi_dev);
+        if (st != SMM_OK) return st;
+        SMM_CUDA(cudaEventRecord(h->ev[1], h->stream));
+        st = enqueue_moments(h);
+        if (st != SMM_OK) return st;
+        SMM_CUDA(cudaEventRecord(h->ev[2], h->stream));
+        st = enqueue_rhs(h);
+        if (st != SMM_OK) return st;
+        SMM_CUDA(cudaEventRecord(h->ev[3], h->stream));
+        st = check_device_error(h);
+        if (st != SMM_OK) return st;
+        int it = 0;
+        st = run_cg(h, phi_dev, &it);
+        if (st != SMM_OK && st != SMM_ERR_NOT_CONVERGED) return st;
+        SMM_CUDA(cudaEventRecord(h->ev[4], h->stream));
+        SMM_CUDA(cudaMemsetAsync(h->nonfinite, 0, sizeof(int), h->stream));
+        smm::launch_diff((int)nphi, phi_dev, h->phi_prev, h->dpart, h->dout, h->nonfinite, h->stream);
+        SMM_CUDA(cudaMemcpyAsync(h->h_scal, h->dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        SMM_CUDA(cudaMemcpyAsync(h->h_int + 4, h->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        SMM_CUDA(cudaStreamSynchronize(h->stream));
+        float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
+        cudaEventElapsedTime(&t01, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&t12, h->ev[1], h->ev[2]);
+        cudaEventElapsedTime(&t23, h->ev[2], h->ev[3]);
+        cudaEventElapsedTime(&t34, h->ev[3], h->ev[4]);
+        local.ms_sweep += t01; local.ms_moments += t12; local.ms_rhs += t23; local.ms_solve += t34;
+        local.outer_iterations = k;
+        local.cg_total += it;
+        local.cg_min = std::min(local.cg_min, it);
+        local.cg_max = std::max(local.cg_max, it);
+        const double diff = h->h_scal[0], mx = h->h_scal[1];
+        local.last_diff = diff;
+        local.last_rel_diff = mx > 0 ? diff / mx : diff;
+        if (h->h_int[4]) {
+            if (stats) *stats = local;
+            return fail(SMM_ERR_NONFINITE, "non-finite scalar flux");
+        }
+        const double crit = relative ? local.last_rel_diff : diff;
+        if (crit < tol) {
+            result = SMM_OK;
+            break;
+        }
+    }
+    if (local.cg_min == (1 << 30)) local.cg_min = 0;
+    if (stats) *stats = local;
+    if (result != SMM_OK) return fail(result, "outer iteration limit reached");
+    return SMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Device kernels of the SMM hot path (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace smm {
+
+// Device error word values (first error wins).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NONFINITE = 2 };
+
+// Sweep modes: SOURCE solves L psi = sigma_s/(4pi) varphi + q with the
+// inflow data; RESIDUAL solves L delta = r (r given per element and
+// ordinate, homogeneous inflow) and accumulates delta into an FP64 flux.
+enum : int { SWEEP_SOURCE = 0, SWEEP_RESIDUAL = 1 };
+
+template <typename T>
+struct SweepArgs {
+    int ne, nd, ntask;
+    const int32_t* tasks;      // e*nd + d, sorted by upwind level
+    const double* ox;          // [nd]
+    const double* oy;          // [nd]
+    const double* sigma_t;     // [ne]
+    const double* sigma_s;     // [ne]
+    const T* M;                // [ne][n][n] row = test function
+    const T* Gx;
+    const T* Gy;
+    const T* Fx;               // [ne][4][p1][p1]
+    const T* Fy;
+    const int8_t* fdir;        // [ne][nd][4]
+    const int32_t* nbr;        // [ne][4]
+    const int32_t* nbr_face;
+    const int32_t* nbr_flip;
+    const int32_t* bface_id;
+    const double* phi;         // [ne][n] or nullptr (SOURCE)
+    const double* src;         // [ne][n] isotropic or [ne][nd][n] (SOURCE)
+    int src_angular;
+    const double* inflow;      // [nb][nd][p1] or nullptr (SOURCE)
+    const float* rhs;          // [ne][nd][n] (RESIDUAL)
+    T* psi;                    // [ne][nd][n] output, read by downwind tasks
+    double* psi_acc;           // RESIDUAL: psi_acc += psi
+    unsigned* done;            // [ne*nd] epoch flags
+    unsigned epoch;
+    unsigned* ticket;          // task counter, zero at launch
+    int* err;
+    long long timeout_ns;
+};
+
+struct ResidualArgs {
+    int ne, nd, ntask;
+    const double* ox;
+    const double* oy;
+    const double* sigma_t;
+    const double* sigma_s;
+    const double* M;
+    const double* Gx;
+    const double* Gy;
+    const double* Fx;
+    const double* Fy;
+    const int8_t* fdir;
+    const int32_t* nbr;
+    const int32_t* nbr_face;
+    const int32_t* nbr_flip;
+    const int32_t* bface_id;
+    const double* phi;
+    const double* src;
+    int src_angular;
+    const double* inflow;
+    const double* psi;         // [ne][nd][n] FP64 current iterate
+    float* rhs;                // [ne][nd][n] residual (out)
+};
+
+template <typename T>
+void launch_sweep(int p, int mode, const SweepArgs<T>& a, int grid, cudaStream_t s);
+void launch_residual(int p, const ResidualArgs& a, cudaStream_t s);
+int sweep_blocks_per_sm(int p, int mode, bool fp32);
+
+// moments and closures
+void launch_moments(int ne, int nd, int n, const double* w, const double* ox, const double* oy,
+                    const double* psi, double* mom, cudaStream_t s);
+void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_elem, const int32_t* bface_face,
+                 const double* w, const double* ox, const double* oy, const double* L1, const double* nhat,
+                 const double* eb0, const double* psi, const double* mom, double* beta, cudaStream_t s);
+void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
+                const double* Kxx, const double* Ks, const double* Kyy, const double* Dfx, const double* Dfy,
+                const double* nds, const double* L1, const double* sigma_t, const int32_t* nbr,
+                const int32_t* nbr_face, const int32_t* nbr_flip, const int32_t* bface_id, const double* b_ds,
+                double* trace, double* rhs, cudaStream_t s);
+
+// block-Jacobi PCG
+struct CGArgs {
+    int ne, n, nrow, nblk;     // nblk: blocks of the row kernels
+    const double* AdT;         // [ne][n][n] transposed (col-major per block)
+    const double* AoT;         // [ne][4][n][n] transposed
+    const double* PinvT;       // [ne][n][n] transposed
+    const int32_t* nbr;        // [ne][4]
+    double* x;
+    double* r;
+    double* z;
+    double* p;
+    double* q;
+    const double* b;
+    double* part;              // [3][nblk] partial sums
+    double* scal;              // [8]: rz, pq, rr, bb, thresh2, -, -, -
+    int* ctl;                  // [4]: done, iters, max_iters, nonfinite
+};
+void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s);
+void cg_iterations(const CGArgs& a, int count, cudaStream_t s);
+int cg_threads_per_block(int n);
+
+// outer step: diff = max|new - old|, max|new|, nonfinite check
+void launch_diff(int nrow, const double* a, const double* b, double* part, double* out, int* flag, cudaStream_t s);
+
+}  // namespace smm

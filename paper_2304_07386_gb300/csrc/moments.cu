@@ -1,0 +1,440 @@
+// Angular moments, SMM closures, IP-SMM right-hand side and the
+// block-Jacobi preconditioned CG of the moment system (FP64).
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace smm {
+
+namespace {
+
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block sum of v into out (thread 0 writes); deterministic order.
+__device__ double block_sum(double v, double* sh) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    v = warp_sum(v);
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) s += sh[i];
+    return s;  // valid in thread 0
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Moments (Eqs. correction_tensor_disc, broken_Tdiv): per element node,
+// phi = sum w psi, J = sum w Omega psi, T = sum w Omega Omega psi - phi/3 I.
+// One warp per element, lane = node; FP64 accumulation in ordinate order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) moments_kernel(int ne, int nd, int n, const double* __restrict__ w,
+                                                      const double* __restrict__ ox, const double* __restrict__ oy,
+                                                      const double* __restrict__ psi, double* __restrict__ mom) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < ne; e += warps) {
+        if (lane >= n) continue;
+        double phi = 0, jx = 0, jy = 0, pxx = 0, pxy = 0, pyy = 0;
+        const double* ps = psi + (size_t)e * nd * n + lane;
+        for (int d = 0; d < nd; ++d) {
+            const double v = __ldcg(ps + (size_t)d * n);
+            const double wv = w[d] * v, x = ox[d], y = oy[d];
+            phi += wv;
+            jx += wv * x;
+            jy += wv * y;
+            pxx += wv * x * x;
+            pxy += wv * x * y;
+            pyy += wv * y * y;
+        }
+        const size_t o = (size_t)e * n + lane, st = (size_t)ne * n;
+        mom[o] = phi;
+        mom[st + o] = jx;
+        mom[2 * st + o] = jy;
+        mom[3 * st + o] = pxx - phi / 3.0;
+        mom[4 * st + o] = pxy;
+        mom[5 * st + o] = pyy - phi / 3.0;
+    }
+}
+
+// beta(x_q) = sum_d w_d |Omega_d . n| psi_d(x_q) - E_b0(x_q) phi(x_q) at the
+// Gauss points of every boundary face (Eq. bdr_correction_factor_disc).
+__global__ void beta_kernel(int nb, int nd, int n, int p, int nfq, const int32_t* __restrict__ bface_elem,
+                            const int32_t* __restrict__ bface_face, const double* __restrict__ w,
+                            const double* __restrict__ ox, const double* __restrict__ oy, const double* __restrict__ L1,
+                            const double* __restrict__ nhat, const double* __restrict__ eb0,
+                            const double* __restrict__ psi, const double* __restrict__ mom, double* __restrict__ beta) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * nfq) return;
+    const int b = t / nfq, q = t - b * nfq;
+    const int e = bface_elem[b], f = bface_face[b];
+    const int p1 = p + 1;
+    int node[8];
+    for (int a = 0; a < p1; ++a)
+        node[a] = f == 0 ? a : (f == 1 ? a * p1 + p : (f == 2 ? p * p1 + a : a * p1));
+    const double nx = nhat[2 * t], ny = nhat[2 * t + 1];
+    double B = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        const double* ps = psi + ((size_t)e * nd + d) * n;
+        double v = 0.0;
+        for (int a = 0; a < p1; ++a) v += L1[q * p1 + a] * __ldcg(ps + node[a]);
+        B += w[d] * fabs(ox[d] * nx + oy[d] * ny) * v;
+    }
+    double phi = 0.0;
+    for (int a = 0; a < p1; ++a) phi += L1[q * p1 + a] * mom[(size_t)e * n + node[a]];
+    beta[t] = B - eb0[t] * phi;
+}
+
+// Face traces of the correction tensor per (element, face, Gauss point):
+// g = (div T . n ds)/sigma_t, and T n ds (2 components).
+__global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, const double* __restrict__ mom,
+                                 const double* __restrict__ Dfx, const double* __restrict__ Dfy,
+                                 const double* __restrict__ nds, const double* __restrict__ L1,
+                                 const double* __restrict__ sigma_t, double* __restrict__ tr) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ne * 4 * nfq) return;
+    const int q = t % nfq, f = (t / nfq) % 4, e = t / (4 * nfq);
+    const size_t st = (size_t)ne * n;
+    const double* txx = mom + 3 * st + (size_t)e * n;
+    const double* txy = mom + 4 * st + (size_t)e * n;
+    const double* tyy = mom + 5 * st + (size_t)e * n;
+    const double* dx = Dfx + (size_t)t * n;
+    const double* dy = Dfy + (size_t)t * n;
+    double divx = 0.0, divy = 0.0;
+    for (int j = 0; j < n; ++j) {
+        divx += dx[j] * txx[j] + dy[j] * txy[j];
+        divy += dx[j] * txy[j] + dy[j] * tyy[j];
+    }
+    const int p1 = p + 1;
+    double vxx = 0, vxy = 0, vyy = 0;
+    for (int a = 0; a < p1; ++a) {
+        const int nd_ = f == 0 ? a : (f == 1 ? a * p1 + p : (f == 2 ? p * p1 + a : a * p1));
+        const double l = L1[q * p1 + a];
+        vxx += l * txx[nd_];
+        vxy += l * txy[nd_];
+        vyy += l * tyy[nd_];
+    }
+    const double nx = nds[2 * t], ny = nds[2 * t + 1];
+    tr[3 * t] = (divx * nx + divy * ny) / sigma_t[e];
+    tr[3 * t + 1] = vxx * nx + vxy * ny;
+    tr[3 * t + 2] = vxy * nx + vyy * ny;
+}
+
+// IP-SMM right-hand side (Eq. ipsmm), element-centric, one thread per dof:
+// b = b_fixed - (1/sigma_t)(Kxx Txx + (Kxy+Kyx) Txy + Kyy Tyy)
+//   + sum_{interior f} sum_q [ l_a(s_q) (g_K - g_K')/2 + (grad phi_i/sigma_t) . (Tn_K + Tn_K')/2 ]
+//   - sum_{boundary f} sum_q ds_q l_a(s_q) beta_q
+__global__ void rhs_assemble_kernel(int ne, int n, int p, int nfq, const double* __restrict__ mom,
+                                    const double* __restrict__ beta, const double* __restrict__ bfixed,
+                                    const double* __restrict__ Kxx, const double* __restrict__ Ks,
+                                    const double* __restrict__ Kyy, const double* __restrict__ Dfx,
+                                    const double* __restrict__ Dfy, const double* __restrict__ L1,
+                                    const double* __restrict__ sigma_t, const int32_t* __restrict__ nbr,
+                                    const int32_t* __restrict__ nbr_face, const int32_t* __restrict__ nbr_flip,
+                                    const int32_t* __restrict__ bface_id, const double* __restrict__ b_ds,
+                                    const double* __restrict__ tr, double* __restrict__ rhs) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ne * n) return;
+    const int e = t / n, i = t - e * n;
+    const size_t st = (size_t)ne * n;
+    const double* txx = mom + 3 * st + (size_t)e * n;
+    const double* txy = mom + 4 * st + (size_t)e * n;
+    const double* tyy = mom + 5 * st + (size_t)e * n;
+    const size_t mo = ((size_t)e * n + i) * n;
+    double acc = bfixed[t];
+    for (int j = 0; j < n; ++j) acc += Kxx[mo + j] * txx[j] + Ks[mo + j] * txy[j] + Kyy[mo + j] * tyy[j];
+    const int p1 = p + 1, ix = i % p1, iy = i / p1;
+    const double hs = 0.5 / sigma_t[e];
+    for (int f = 0; f < 4; ++f) {
+        const bool on = (f == 0 && iy == 0) || (f == 1 && ix == p) || (f == 2 && iy == p) || (f == 3 && ix == 0);
+        const int fa = (f == 0 || f == 2) ? ix : iy;
+        const int e2 = nbr[e * 4 + f];
+        const size_t fo = ((size_t)e * 4 + f) * nfq;
+        if (e2 >= 0) {
+            const int f2 = nbr_face[e * 4 + f], flip = nbr_flip[e * 4 + f];
+            const size_t fo2 = ((size_t)e2 * 4 + f2) * nfq;
+            for (int q = 0; q < nfq; ++q) {
+                const int q2 = flip ? nfq - 1 - q : q;
+                const double* a1 = tr + 3 * (fo + q);
+                const double* a2 = tr + 3 * (fo2 + q2);
+                const double tjx = a1[1] + a2[1], tjy = a1[2] + a2[2];
+                acc += hs * (Dfx[(fo + q) * n + i] * tjx + Dfy[(fo + q) * n + i] * tjy);
+                if (on) acc += L1[q * p1 + fa] * 0.5 * (a1[0] - a2[0]);
+            }
+        } else if (on) {
+            const int b = bface_id[e * 4 + f];
+            for (int q = 0; q < nfq; ++q) acc -= b_ds[(size_t)b * nfq + q] * L1[q * p1 + fa] * beta[(size_t)b * nfq + q];
+        }
+    }
+    rhs[t] = acc;
+}
+
+void launch_moments(int ne, int nd, int n, const double* w, const double* ox, const double* oy, const double* psi,
+                    double* mom, cudaStream_t s) {
+    int grid = std::max(1, std::min((ne + 7) / 8, 65535));
+    moments_kernel<<<grid, 256, 0, s>>>(ne, nd, n, w, ox, oy, psi, mom);
+}
+
+void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_elem, const int32_t* bface_face,
+                 const double* w, const double* ox, const double* oy, const double* L1, const double* nhat,
+                 const double* eb0, const double* psi, const double* mom, double* beta, cudaStream_t s) {
+    const int tot = nb * nfq;
+    if (tot == 0) return;
+    beta_kernel<<<(tot + 127) / 128, 128, 0, s>>>(nb, nd, n, p, nfq, bface_elem, bface_face, w, ox, oy, L1, nhat, eb0,
+                                                  psi, mom, beta);
+}
+
+void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
+                const double* Kxx, const double* Ks, const double* Kyy, const double* Dfx, const double* Dfy,
+                const double* nds, const double* L1, const double* sigma_t, const int32_t* nbr, const int32_t* nbr_face,
+                const int32_t* nbr_flip, const int32_t* bface_id, const double* b_ds, double* trace, double* rhs,
+                cudaStream_t s) {
+    const int t1 = ne * 4 * nfq;
+    rhs_trace_kernel<<<(t1 + 255) / 256, 256, 0, s>>>(ne, n, p, nfq, mom, Dfx, Dfy, nds, L1, sigma_t, trace);
+    const int t2 = ne * n;
+    rhs_assemble_kernel<<<(t2 + 255) / 256, 256, 0, s>>>(ne, n, p, nfq, mom, beta, bfixed, Kxx, Ks, Kyy, Dfx, Dfy, L1,
+                                                         sigma_t, nbr, nbr_face, nbr_flip, bface_id, b_ds, trace, rhs);
+}
+
+// ---------------------------------------------------------------------------
+// Block-Jacobi PCG on the IP-SMM operator.  Operator blocks are stored
+// transposed ([e][j][i]) so that the threads of one element read contiguous
+// entries.  Blocks of threads cover whole elements (EPB elements x n rows).
+// Scalars are reduced deterministically: per-block partials, then every
+// block sums all partials in the same order.
+// ---------------------------------------------------------------------------
+int cg_threads_per_block(int n) { return std::max(1, 256 / n) * n; }
+
+namespace {
+
+__device__ double sum_partials(const double* part, int nblk, double* sh) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += part[i];
+    double s = block_sum(v, sh);
+    if (threadIdx.x == 0) sh[32] = s;
+    __syncthreads();
+    s = sh[32];
+    __syncthreads();
+    return s;
+}
+
+__device__ __forceinline__ double spmv_row(const CGArgs& a, const double* v, int e, int i) {
+    const int n = a.n;
+    const double* Ad = a.AdT + (size_t)e * n * n + i;
+    const double* ve = v + (size_t)e * n;
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc += Ad[(size_t)j * n] * ve[j];
+    for (int f = 0; f < 4; ++f) {
+        const int e2 = a.nbr[e * 4 + f];
+        if (e2 < 0) continue;
+        const double* Ao = a.AoT + ((size_t)e * 4 + f) * n * n + i;
+        const double* v2 = v + (size_t)e2 * n;
+        for (int j = 0; j < n; ++j) acc += Ao[(size_t)j * n] * v2[j];
+    }
+    return acc;
+}
+
+// r = b - A x ; z = P r ; p = z ; partials: rz, rr, bb
+__global__ void cg_init_kernel(CGArgs a) {
+    __shared__ double sh[40];
+    extern __shared__ double rs[];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    const bool act = e < a.ne;
+    double r = 0.0, bv = 0.0;
+    if (act) {
+        bv = a.b[(size_t)e * n + i];
+        r = bv - spmv_row(a, a.x, e, i);
+        a.r[(size_t)e * n + i] = r;
+    }
+    rs[threadIdx.x] = r;
+    __syncthreads();
+    double z = 0.0;
+    if (act) {
+        const double* P = a.PinvT + (size_t)e * n * n + i;
+        const double* re = rs + (threadIdx.x / n) * n;
+        for (int j = 0; j < n; ++j) z += P[(size_t)j * n] * re[j];
+        a.z[(size_t)e * n + i] = z;
+        a.p[(size_t)e * n + i] = z;
+    }
+    double s0 = block_sum(r * z, sh);
+    double s1 = block_sum(r * r, sh);
+    double s2 = block_sum(bv * bv, sh);
+    if (threadIdx.x == 0) {
+        a.part[blockIdx.x] = s0;
+        a.part[a.nblk + blockIdx.x] = s1;
+        a.part[2 * a.nblk + blockIdx.x] = s2;
+    }
+}
+
+__global__ void cg_init_scalars_kernel(CGArgs a, double tol2, int max_iters) {
+    __shared__ double sh[40];
+    double rz = sum_partials(a.part, a.nblk, sh);
+    double rr = sum_partials(a.part + a.nblk, a.nblk, sh);
+    double bb = sum_partials(a.part + 2 * a.nblk, a.nblk, sh);
+    if (threadIdx.x == 0) {
+        a.scal[0] = rz;
+        a.scal[2] = rr;
+        a.scal[3] = bb;
+        a.scal[4] = tol2 * bb;
+        a.ctl[1] = 0;
+        a.ctl[2] = max_iters;
+        a.ctl[3] = (isfinite(rz) && isfinite(rr) && isfinite(bb)) ? 0 : 1;
+        a.ctl[0] = (rr <= tol2 * bb || a.ctl[3]) ? 1 : 0;
+    }
+}
+
+// q = A p ; partial p.q
+__global__ void cg_spmv_kernel(CGArgs a) {
+    if (*(volatile int*)a.ctl) return;
+    __shared__ double sh[40];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    double pq = 0.0;
+    if (e < a.ne) {
+        const double qv = spmv_row(a, a.p, e, i);
+        a.q[(size_t)e * n + i] = qv;
+        pq = qv * a.p[(size_t)e * n + i];
+    }
+    double s = block_sum(pq, sh);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = s;
+}
+
+// alpha = rz / pq ; x += alpha p ; r -= alpha q ; z = P r ; partials r.z, r.r
+__global__ void cg_update_kernel(CGArgs a) {
+    if (*(volatile int*)a.ctl) return;
+    __shared__ double sh[40];
+    extern __shared__ double rs[];
+    const double pq = sum_partials(a.part, a.nblk, sh);
+    const double alpha = a.scal[0] / pq;
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    const bool act = e < a.ne;
+    double r = 0.0;
+    if (act) {
+        const size_t o = (size_t)e * n + i;
+        a.x[o] += alpha * a.p[o];
+        r = a.r[o] - alpha * a.q[o];
+        a.r[o] = r;
+    }
+    rs[threadIdx.x] = r;
+    __syncthreads();
+    double z = 0.0;
+    if (act) {
+        const double* P = a.PinvT + (size_t)e * n * n + i;
+        const double* re = rs + (threadIdx.x / n) * n;
+        for (int j = 0; j < n; ++j) z += P[(size_t)j * n] * re[j];
+        a.z[(size_t)e * n + i] = z;
+    }
+    double s0 = block_sum(r * z, sh);
+    double s1 = block_sum(r * r, sh);
+    if (threadIdx.x == 0) {
+        a.part[a.nblk + blockIdx.x] = s0;
+        a.part[2 * a.nblk + blockIdx.x] = s1;
+    }
+}
+
+// beta = rz_new / rz ; p = z + beta p ; convergence and iteration count
+__global__ void cg_direction_kernel(CGArgs a) {
+    if (*(volatile int*)a.ctl) return;
+    __shared__ double sh[40];
+    const double rz_new = sum_partials(a.part + a.nblk, a.nblk, sh);
+    const double rr = sum_partials(a.part + 2 * a.nblk, a.nblk, sh);
+    const double beta = rz_new / a.scal[0];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    if (e < a.ne) {
+        const size_t o = (size_t)e * n + i;
+        a.p[o] = a.z[o] + beta * a.p[o];
+    }
+    // every block has read scal[0] above; make the update visible only after
+    // all blocks are done with it: block 0 writes into a second slot, the
+    // finisher (last block) publishes.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned prev = atomicAdd((unsigned*)(a.ctl + 4), 1u);
+        if (prev == (unsigned)gridDim.x - 1) {
+            a.ctl[4] = 0;
+            a.scal[0] = rz_new;
+            a.scal[2] = rr;
+            const int it = a.ctl[1] + 1;
+            a.ctl[1] = it;
+            const bool bad = !(isfinite(rz_new) && isfinite(rr));
+            if (bad) a.ctl[3] = 1;
+            if (rr <= a.scal[4] || it >= a.ctl[2] || bad) a.ctl[0] = 1;
+            __threadfence();
+        }
+    }
+}
+
+// max |a - b| and max |a| over rows, plus a non-finite flag
+__global__ void diff_kernel(int nrow, const double* __restrict__ x, const double* __restrict__ y, double* part, int* flag) {
+    __shared__ double s1[32], s2[32];
+    double m1 = 0.0, m2 = 0.0;
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrow; i += gridDim.x * blockDim.x) {
+        const double v = x[i];
+        bad |= !isfinite(v);
+        m1 = fmax(m1, fabs(v - y[i]));
+        m2 = fmax(m2, fabs(v));
+    }
+    if (bad) atomicExch(flag, 1);
+    m1 = warp_max(m1);
+    m2 = warp_max(m2);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { s1[w] = m1; s2[w] = m2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { m1 = fmax(m1, s1[k]); m2 = fmax(m2, s2[k]); }
+        part[2 * blockIdx.x] = m1;
+        part[2 * blockIdx.x + 1] = m2;
+    }
+}
+
+__global__ void diff_final_kernel(int nblk, const double* part, double* out) {
+    if (threadIdx.x == 0) {
+        double m1 = 0.0, m2 = 0.0;
+        for (int k = 0; k < nblk; ++k) { m1 = fmax(m1, part[2 * k]); m2 = fmax(m2, part[2 * k + 1]); }
+        out[0] = m1;
+        out[1] = m2;
+    }
+}
+
+}  // namespace
+
+void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s) {
+    const int tpb = cg_threads_per_block(a.n);
+    cg_init_kernel<<<a.nblk, tpb, tpb * sizeof(double), s>>>(a);
+    cg_init_scalars_kernel<<<1, 256, 0, s>>>(a, tol * tol, max_iters);
+}
+
+void cg_iterations(const CGArgs& a, int count, cudaStream_t s) {
+    const int tpb = cg_threads_per_block(a.n);
+    for (int k = 0; k < count; ++k) {
+        cg_spmv_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        cg_update_kernel<<<a.nblk, tpb, tpb * sizeof(double), s>>>(a);
+        cg_direction_kernel<<<a.nblk, tpb, 0, s>>>(a);
+    }
+}
+
+void launch_diff(int nrow, const double* a, const double* b, double* part, double* out, int* flag, cudaStream_t s) {
+    const int nblk = 256;
+    diff_kernel<<<nblk, 256, 0, s>>>(nrow, a, b, part, flag);
+    diff_final_kernel<<<1, 32, 0, s>>>(nblk, part, out);
+}
+
+}  // namespace smm

@@ -1,0 +1,76 @@
+// Host-side setup of the SMM solver: quadrature, mapped Q_p elements on
+// curved quads, per-element sweep matrices, upwind ordering, and the
+// interior penalty SMM operator blocks.  Plain C++17, no CUDA.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace smm {
+
+struct Rule1D {
+    std::vector<double> x, w;
+};
+
+// Gauss-Legendre / Gauss-Lobatto rules on [0,1].
+Rule1D gauss_legendre01(int n);
+Rule1D gauss_lobatto01(int n);
+
+struct Quadrature {
+    int nd = 0;
+    std::vector<double> ox, oy, w;
+};
+
+// Level-symmetric LQ_N 2D set (weights sum to 4 pi); false if N unsupported.
+bool level_symmetric(int N, Quadrature& q);
+
+struct Input {
+    int ne = 0, m = 1, p = 1, sn = 4, n_nodes = 0;
+    const double* nodes = nullptr;       // [n_nodes][2]
+    const int32_t* elem_nodes = nullptr; // [ne][(m+1)^2]
+    const double* sigma_t = nullptr;     // [ne]
+    const double* sigma_s = nullptr;     // [ne]
+    int source_kind = 0;                 // 0 isotropic [ne][n], 1 angular [nd][ne][n]
+    const double* q = nullptr;
+    int inflow_kind = 0;                 // 0 vacuum, 1 nodal [nd][nb][p+1]
+    const double* inflow = nullptr;
+    double kappa_scale = 1.0;
+};
+
+struct Setup {
+    int ne = 0, m = 1, p = 1, p1 = 2, n = 4, nq = 0, nqv = 0, nfq = 0, nd = 0, nb = 0;
+    int nlevels = 0;
+    Quadrature quad;
+    // connectivity [ne][4]
+    std::vector<int32_t> nbr, nbr_face, nbr_flip, bface_id;
+    std::vector<int32_t> bface_elem, bface_face;  // [nb]
+    // sweep data
+    std::vector<double> sigma_t, sigma_s;
+    std::vector<double> M, Gx, Gy;                // [ne][n][n], row = test function
+    std::vector<double> Fx, Fy;                   // [ne][4][p1][p1]
+    std::vector<int8_t> fdir;                     // [ne][nd][4]: +1 out, -1 in, 0 none
+    std::vector<int32_t> level;                   // [nd][ne]
+    std::vector<int32_t> tasks;                   // e*nd + d sorted by (level, e, d)
+    std::vector<int32_t> level_start;             // [nlevels+1] offsets into tasks
+    std::vector<double> src;                      // [ne][nd][n] or [ne][n] (isotropic), per steradian
+    std::vector<double> inflow;                   // [nb][nd][p1] (empty = vacuum)
+    // face quadrature shared data
+    std::vector<double> L1;                       // [nfq][p1]
+    // boundary quadrature data
+    std::vector<double> b_nhat;                   // [nb][nfq][2]
+    std::vector<double> b_ds;                     // [nb][nfq]
+    std::vector<double> b_eb0;                    // [nb][nfq]
+    // moment system
+    std::vector<double> Adiag, Aoff, Pinv;        // [ne][n][n], [ne][4][n][n], [ne][n][n]
+    std::vector<double> Kxx, Ks, Kyy;             // [ne][n][n], scaled by -1/sigma_t
+    std::vector<double> Dfx, Dfy;                 // [ne][4][nfq][n]
+    std::vector<double> nds;                      // [ne][4][nfq][2]
+    std::vector<double> bfixed;                   // [ne][n]
+    std::vector<double> hK, area;
+};
+
+// Status codes match smm_status in include/smm.h.
+int build_setup(const Input& in, Setup& s, std::string& err);
+
+}  // namespace smm

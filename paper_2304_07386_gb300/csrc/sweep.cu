@@ -1,0 +1,323 @@
+// Persistent wavefront DG S_N sweep (paper Sec. "Transport Discretization").
+//
+// One warp per (element, ordinate) task; the row i of the local system is
+// held by lane i (n = (p+1)^2 <= 25 <= 32).  The local upwind DG operator
+//   A = sigma_t M - Omega_x Gx - Omega_y Gy + sum_{outflow f} (Omega_x Fx_f + Omega_y Fy_f)
+// is assembled on the fly from the element's angle-independent matrices, the
+// right-hand side b = M s - sum_{inflow f} (Omega_x Fx_f + Omega_y Fy_f) psi_up
+// takes the upwind neighbour's face values (or the inflow data), and A is
+// factored in registers by Gaussian elimination without pivoting (the
+// symmetric part of A is positive definite: x^T A x = 1/2 int_dK |Omega.n| x^2
+// + sigma_t |x|^2), broadcasting pivot rows with warp shuffles.
+//
+// Scheduling: tasks are sorted by upwind level; warps take tickets from a
+// global counter, so every task a warp waits for was claimed earlier by a
+// running warp.  A task waits (bounded in time) on its upwind neighbours'
+// epoch flags, and publishes its own flag with release semantics after its
+// outputs are written.
+#include "kernels.cuh"
+
+namespace smm {
+
+namespace {
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// Bounded wait until *flag == epoch.  False on timeout or when another warp
+// has already raised the error word.
+__device__ bool wait_epoch(const unsigned* flag, unsigned epoch, long long timeout_ns, const int* err) {
+    if (ld_acquire(flag) == epoch) return true;
+    const long long t0 = global_ns();
+    for (unsigned it = 1; it < (1u << 30); ++it) {
+        if (ld_acquire(flag) == epoch) return true;
+        if ((it & 31u) == 0) {
+            if (ld_volatile(err) != DEV_OK) return false;
+            if (global_ns() - t0 > timeout_ns) return false;
+        }
+        __nanosleep(32);
+    }
+    return false;
+}
+
+template <int P>
+__device__ __forceinline__ int face_node(int f, int a) {
+    constexpr int P1 = P + 1;
+    return f == 0 ? a : (f == 1 ? a * P1 + P : (f == 2 ? P * P1 + a : a * P1));
+}
+
+template <typename T> __device__ __forceinline__ T ldg_cg(const T* p) { return __ldcg(p); }
+
+}  // namespace
+
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
+    constexpr int P1 = P + 1, N = P1 * P1;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int row = lane < N ? lane : 0;  // lanes >= N shadow row 0 (results discarded)
+    const int ix = row % P1, iy = row / P1;
+    const int nd = a.nd;
+
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(a.ticket, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= a.ntask) break;
+        const int task = a.tasks[t];
+        const int e = task / nd, d = task - e * nd;
+        const T ox = (T)a.ox[d], oy = (T)a.oy[d];
+        const char4 dirs = *reinterpret_cast<const char4*>(a.fdir + ((size_t)e * nd + d) * 4);
+        const int dir[4] = {dirs.x, dirs.y, dirs.z, dirs.w};
+
+        // ---- wait for the upwind neighbours (lane f waits on face f) ----
+        bool ok = true;
+        if (lane < 4) {
+            const int f = lane;
+            const int df = f == 0 ? dir[0] : (f == 1 ? dir[1] : (f == 2 ? dir[2] : dir[3]));
+            const int nb = a.nbr[e * 4 + f];
+            if (df < 0 && nb >= 0) ok = wait_epoch(a.done + (size_t)nb * nd + d, a.epoch, a.timeout_ns, a.err);
+        }
+        ok = __all_sync(FULL, ok);
+        if (!ok) {
+            if (lane == 0) atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
+            break;
+        }
+
+        // ---- assemble row `row` of A and b ----
+        const T sig = (T)a.sigma_t[e];
+        const size_t mo = ((size_t)e * N + row) * N;
+        T A[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) A[j] = sig * a.M[mo + j] - ox * a.Gx[mo + j] - oy * a.Gy[mo + j];
+        T b;
+        if (MODE == SWEEP_SOURCE) {
+            const double c = a.sigma_s[e] * (1.0 / (4.0 * 3.14159265358979323846));
+            const double* q = a.src_angular ? a.src + ((size_t)e * nd + d) * N : a.src + (size_t)e * N;
+            T sj = 0;
+            if (lane < N) sj = (T)((a.phi ? c * a.phi[(size_t)e * N + lane] : 0.0) + q[lane]);
+            T acc = 0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc += a.M[mo + j] * __shfl_sync(FULL, sj, j);
+            b = acc;
+        } else {
+            b = (T)a.rhs[((size_t)e * nd + d) * N + row];
+        }
+
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const int df = dir[f];
+            const bool on = (f == 0 && iy == 0) || (f == 1 && ix == P) || (f == 2 && iy == P) || (f == 3 && ix == 0);
+            const int fa = (f == 0 || f == 2) ? ix : iy;  // position of this row on face f
+            const size_t fo = (((size_t)e * 4 + f) * P1 + fa) * P1;
+            if (df > 0 && on) {
+#pragma unroll
+                for (int c = 0; c < P1; ++c) {
+                    const T v = ox * a.Fx[fo + c] + oy * a.Fy[fo + c];
+#pragma unroll
+                    for (int j = 0; j < N; ++j)
+                        if (j == face_node<P>(f, c)) A[j] += v;
+                }
+            } else if (df < 0 && on) {
+                const int nb = a.nbr[e * 4 + f];
+                T acc = 0;
+                if (nb >= 0) {
+                    const int f2 = a.nbr_face[e * 4 + f];
+                    const int flip = a.nbr_flip[e * 4 + f];
+                    const T* up = a.psi + ((size_t)nb * nd + d) * N;
+#pragma unroll
+                    for (int c = 0; c < P1; ++c) {
+                        const int c2 = flip ? P - c : c;
+                        const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
+                        acc += (ox * a.Fx[fo + c] + oy * a.Fy[fo + c]) * ldg_cg(up + node);
+                    }
+                } else if (MODE == SWEEP_SOURCE && a.inflow) {
+                    const int bi = a.bface_id[e * 4 + f];
+                    const double* up = a.inflow + ((size_t)bi * nd + d) * P1;
+#pragma unroll
+                    for (int c = 0; c < P1; ++c) acc += (ox * a.Fx[fo + c] + oy * a.Fy[fo + c]) * (T)up[c];
+                }
+                b -= acc;
+            }
+        }
+
+        // ---- in-register LU without pivoting (row per lane) ----
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const T inv = T(1) / __shfl_sync(FULL, A[k], k);
+            const T l = A[k] * inv;
+            const bool below = lane > k;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                if (j > k) {
+                    const T akj = __shfl_sync(FULL, A[j], k);
+                    if (below) A[j] -= l * akj;
+                }
+            }
+            const T bk = __shfl_sync(FULL, b, k);
+            if (below) b -= l * bk;
+        }
+        // back substitution
+        T x = 0;
+#pragma unroll
+        for (int k = N - 1; k >= 0; --k) {
+            const T xk = __shfl_sync(FULL, b / A[k], k);
+            if (lane == k) x = xk;
+            if (lane < k) b -= A[k] * xk;
+        }
+
+        // ---- publish ----
+        if (lane < N) {
+            const size_t o = ((size_t)e * nd + d) * N + lane;
+            a.psi[o] = x;
+            if (MODE == SWEEP_RESIDUAL) a.psi_acc[o] += (double)x;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(a.done + task, a.epoch);
+    }
+}
+
+// FP64 transport residual r = b - A psi - (inflow terms) per (element,
+// ordinate), independent tasks, one warp each (row per lane).
+template <int P>
+__global__ void __launch_bounds__(256) residual_kernel(ResidualArgs a) {
+    constexpr int P1 = P + 1, N = P1 * P1;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int row = lane < N ? lane : 0;
+    const int ix = row % P1, iy = row / P1;
+    const int nd = a.nd;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < a.ntask; task += warps) {
+        const int e = task / nd, d = task - e * nd;
+        const double ox = a.ox[d], oy = a.oy[d];
+        const char4 dirs = *reinterpret_cast<const char4*>(a.fdir + (size_t)task * 4);
+        const int dir[4] = {dirs.x, dirs.y, dirs.z, dirs.w};
+        const double sig = a.sigma_t[e];
+        const double c = a.sigma_s[e] * (1.0 / (4.0 * 3.14159265358979323846));
+        const double* q = a.src_angular ? a.src + (size_t)task * N : a.src + (size_t)e * N;
+        const double* ps = a.psi + (size_t)task * N;
+        const double pj = lane < N ? ps[lane] : 0.0;
+        const double sj = lane < N ? (a.phi ? c * a.phi[(size_t)e * N + lane] : 0.0) + q[lane] - sig * pj : 0.0;
+        const size_t mo = ((size_t)e * N + row) * N;
+        double r = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const double sjj = __shfl_sync(FULL, sj, j);
+            const double pjj = __shfl_sync(FULL, pj, j);
+            r += a.M[mo + j] * sjj + (ox * a.Gx[mo + j] + oy * a.Gy[mo + j]) * pjj;
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const int df = dir[f];
+            if (df == 0) continue;
+            const bool on = (f == 0 && iy == 0) || (f == 1 && ix == P) || (f == 2 && iy == P) || (f == 3 && ix == 0);
+            if (!on) continue;
+            const int fa = (f == 0 || f == 2) ? ix : iy;
+            const size_t fo = (((size_t)e * 4 + f) * P1 + fa) * P1;
+            double acc = 0.0;
+            if (df > 0) {
+#pragma unroll
+                for (int cc = 0; cc < P1; ++cc) acc += (ox * a.Fx[fo + cc] + oy * a.Fy[fo + cc]) * ps[face_node<P>(f, cc)];
+            } else {
+                const int nb = a.nbr[e * 4 + f];
+                if (nb >= 0) {
+                    const int f2 = a.nbr_face[e * 4 + f], flip = a.nbr_flip[e * 4 + f];
+                    const double* up = a.psi + ((size_t)nb * nd + d) * N;
+#pragma unroll
+                    for (int cc = 0; cc < P1; ++cc) {
+                        const int c2 = flip ? P - cc : cc;
+                        const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
+                        acc += (ox * a.Fx[fo + cc] + oy * a.Fy[fo + cc]) * up[node];
+                    }
+                } else if (a.inflow) {
+                    const int bi = a.bface_id[e * 4 + f];
+                    const double* up = a.inflow + ((size_t)bi * nd + d) * P1;
+#pragma unroll
+                    for (int cc = 0; cc < P1; ++cc) acc += (ox * a.Fx[fo + cc] + oy * a.Fy[fo + cc]) * up[cc];
+                }
+            }
+            r -= acc;
+        }
+        if (lane < N) a.rhs[(size_t)task * N + lane] = (float)r;
+    }
+}
+
+template <typename T, int P, int MODE>
+static void launch_one(const SweepArgs<T>& a, int grid, cudaStream_t s) {
+    sweep_kernel<T, P, MODE><<<grid, 256, 0, s>>>(a);
+}
+
+template <typename T>
+void launch_sweep(int p, int mode, const SweepArgs<T>& a, int grid, cudaStream_t s) {
+#define SMM_SWEEP_CASE(PP)                                                              \
+    case PP:                                                                            \
+        if (mode == SWEEP_SOURCE) launch_one<T, PP, SWEEP_SOURCE>(a, grid, s);          \
+        else launch_one<T, PP, SWEEP_RESIDUAL>(a, grid, s);                             \
+        break;
+    switch (p) { SMM_SWEEP_CASE(1) SMM_SWEEP_CASE(2) SMM_SWEEP_CASE(3) SMM_SWEEP_CASE(4) default: break; }
+#undef SMM_SWEEP_CASE
+}
+
+template void launch_sweep<double>(int, int, const SweepArgs<double>&, int, cudaStream_t);
+template void launch_sweep<float>(int, int, const SweepArgs<float>&, int, cudaStream_t);
+
+int sweep_blocks_per_sm(int p, int mode, bool fp32) {
+    int nb = 0;
+#define SMM_OCC(T, PP, MM) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, PP, MM>, 256, 0)
+    switch (p * 4 + mode * 2 + (fp32 ? 1 : 0)) {
+        case 4: SMM_OCC(double, 1, 0); break;
+        case 5: SMM_OCC(float, 1, 0); break;
+        case 6: SMM_OCC(double, 1, 1); break;
+        case 7: SMM_OCC(float, 1, 1); break;
+        case 8: SMM_OCC(double, 2, 0); break;
+        case 9: SMM_OCC(float, 2, 0); break;
+        case 10: SMM_OCC(double, 2, 1); break;
+        case 11: SMM_OCC(float, 2, 1); break;
+        case 12: SMM_OCC(double, 3, 0); break;
+        case 13: SMM_OCC(float, 3, 0); break;
+        case 14: SMM_OCC(double, 3, 1); break;
+        case 15: SMM_OCC(float, 3, 1); break;
+        case 16: SMM_OCC(double, 4, 0); break;
+        case 17: SMM_OCC(float, 4, 0); break;
+        case 18: SMM_OCC(double, 4, 1); break;
+        case 19: SMM_OCC(float, 4, 1); break;
+        default: break;
+    }
+#undef SMM_OCC
+    return nb > 0 ? nb : 1;
+}
+
+void launch_residual(int p, const ResidualArgs& a, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long warps_needed = a.ntask;
+    int grid = (int)std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8);
+    if (grid < 1) grid = 1;
+    switch (p) {
+        case 1: residual_kernel<1><<<grid, 256, 0, s>>>(a); break;
+        case 2: residual_kernel<2><<<grid, 256, 0, s>>>(a); break;
+        case 3: residual_kernel<3><<<grid, 256, 0, s>>>(a); break;
+        case 4: residual_kernel<4><<<grid, 256, 0, s>>>(a); break;
+        default: break;
+    }
+}
+
+}  // namespace smm

@@ -1,0 +1,216 @@
+"""Thin ctypes binding of the SMM C ABI (include/smm.h).
+
+Argument marshalling only: every step of the hot path runs in libsmm.so.
+Host inputs are NumPy arrays; device buffers are CUDA torch tensors (FP64,
+contiguous) whose data pointers are passed through; the stream is torch's
+current stream unless one is given.  The binding raises if the library is
+missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsmm.so")
+
+SMM_OK = 0
+STATUS = {0: "SMM_OK", 1: "SMM_ERR_INVALID_ARG", 2: "SMM_ERR_CUDA", 3: "SMM_ERR_OOM", 4: "SMM_ERR_MESH",
+          5: "SMM_ERR_CYCLE", 6: "SMM_ERR_NONFINITE", 7: "SMM_ERR_NOT_CONVERGED", 8: "SMM_ERR_DEVICE_TIMEOUT"}
+SMM_SOURCE_ISOTROPIC, SMM_SOURCE_ANGULAR = 0, 1
+SMM_INFLOW_VACUUM, SMM_INFLOW_NODAL = 0, 1
+SMM_SWEEP_FP64, SMM_SWEEP_FP32_REFINED = 0, 1
+
+
+class smm_mesh(C.Structure):
+    _fields_ = [("n_elem", C.c_int32), ("geom_order", C.c_int32), ("n_nodes", C.c_int32),
+                ("nodes", C.POINTER(C.c_double)), ("elem_nodes", C.POINTER(C.c_int32))]
+
+
+class smm_options(C.Structure):
+    _fields_ = [("sweep_precision", C.c_int32), ("tol_cg", C.c_double), ("max_cg", C.c_int32),
+                ("kappa_scale", C.c_double), ("spin_timeout_s", C.c_double)]
+
+
+class smm_info(C.Structure):
+    _fields_ = [("n_elem", C.c_int32), ("p", C.c_int32), ("m", C.c_int32), ("n_dof_elem", C.c_int32),
+                ("n_ord", C.c_int32), ("n_bface", C.c_int32), ("n_fq", C.c_int32), ("n_levels", C.c_int32),
+                ("n_angular", C.c_int64)]
+
+
+class smm_stats(C.Structure):
+    _fields_ = [("outer_iterations", C.c_int32), ("cg_total", C.c_int32), ("cg_min", C.c_int32),
+                ("cg_max", C.c_int32), ("last_diff", C.c_double), ("last_rel_diff", C.c_double),
+                ("ms_sweep", C.c_double), ("ms_moments", C.c_double), ("ms_rhs", C.c_double),
+                ("ms_solve", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SMMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libsmm.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"libsmm.so not found at {p}: run __graft_entry__.build() first")
+    lib = C.CDLL(p)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    lib.smm_default_options.argtypes = [C.POINTER(smm_options)]
+    lib.smm_default_options.restype = None
+    lib.smm_last_error.restype = C.c_char_p
+    lib.smm_quadrature.argtypes = [C.c_int32, dp, dp, ip]
+    lib.smm_create.argtypes = [C.POINTER(smm_mesh), C.c_int32, C.c_int32, dp, dp, C.c_int32, dp, C.c_int32, dp,
+                               C.POINTER(smm_options), vp, C.POINTER(vp)]
+    lib.smm_get_info.argtypes = [vp, C.POINTER(smm_info)]
+    lib.smm_sweep.argtypes = [vp, vp]
+    lib.smm_moments.argtypes = [vp, vp, vp]
+    lib.smm_set_moments.argtypes = [vp, vp, vp]
+    lib.smm_get_psi.argtypes = [vp, vp]
+    lib.smm_moment_solve.argtypes = [vp, vp, ip]
+    lib.smm_iterate.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, vp, C.POINTER(smm_stats)]
+    lib.smm_destroy.argtypes = [vp]
+    for name in ("smm_quadrature", "smm_create", "smm_get_info", "smm_sweep", "smm_moments", "smm_set_moments",
+                 "smm_get_psi", "smm_moment_solve", "smm_iterate", "smm_destroy"):
+        getattr(lib, name).restype = C.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != SMM_OK:
+        raise SMMError(status, load_library().smm_last_error().decode())
+    return status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _devptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
+        raise ValueError("device buffers must be contiguous CUDA float64 tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def smm_default_options() -> smm_options:
+    o = smm_options()
+    load_library().smm_default_options(C.byref(o))
+    return o
+
+
+def smm_quadrature(sn_order: int):
+    """(omega [nd][2], weights [nd]) of the library's LQ_N set."""
+    lib = load_library()
+    nd = C.c_int32(0)
+    _check(lib.smm_quadrature(sn_order, None, None, C.byref(nd)))
+    om = np.zeros((nd.value, 2))
+    w = np.zeros(nd.value)
+    _check(lib.smm_quadrature(sn_order, _dptr(om), _dptr(w), C.byref(nd)))
+    return om, w
+
+
+class Handle:
+    """Owns one smm_handle; methods mirror the C calls."""
+
+    def __init__(self, ptr, stream_keepalive=None):
+        self.ptr = ptr
+        self._keep = stream_keepalive
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self):
+        if self.ptr:
+            load_library().smm_destroy(self.ptr)
+            self.ptr = None
+
+    def info(self) -> smm_info:
+        i = smm_info()
+        _check(load_library().smm_get_info(self.ptr, C.byref(i)))
+        return i
+
+
+def smm_create(nodes, elem_nodes, geom_order, p, sn_order, sigma_t, sigma_s, q, source_kind=None,
+               inflow=None, options: smm_options | None = None, stream=None) -> Handle:
+    """Build a solver.  nodes [n_nodes][2], elem_nodes [n_elem][(m+1)^2],
+    sigma_t/sigma_s [n_elem], q [n_elem][n] (isotropic) or [n_ord][n_elem][n],
+    inflow None or [n_ord][n_bface][p+1]; stream: a torch.cuda.Stream or None
+    (torch's current stream)."""
+    import torch
+
+    lib = load_library()
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    en = np.ascontiguousarray(elem_nodes, dtype=np.int32)
+    st = np.ascontiguousarray(sigma_t, dtype=np.float64)
+    ss = np.ascontiguousarray(sigma_s, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if source_kind is None:
+        source_kind = SMM_SOURCE_ANGULAR if q.ndim == 3 else SMM_SOURCE_ISOTROPIC
+    mesh = smm_mesh(len(en), geom_order, len(nodes), _dptr(nodes), en.ctypes.data_as(C.POINTER(C.c_int32)))
+    ik = SMM_INFLOW_VACUUM
+    inf_ptr = None
+    if inflow is not None:
+        inflow = np.ascontiguousarray(inflow, dtype=np.float64)
+        ik = SMM_INFLOW_NODAL
+        inf_ptr = _dptr(inflow)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_void_p()
+    _check(lib.smm_create(C.byref(mesh), p, sn_order, _dptr(st), _dptr(ss), source_kind, _dptr(q), ik, inf_ptr,
+                          C.byref(options) if options is not None else None, C.c_void_p(s.cuda_stream),
+                          C.byref(out)))
+    return Handle(out, s)
+
+
+def smm_sweep(h: Handle, phi=None):
+    _check(load_library().smm_sweep(h.ptr, _devptr(phi)))
+
+
+def smm_moments(h: Handle, moments=None, beta=None):
+    _check(load_library().smm_moments(h.ptr, _devptr(moments), _devptr(beta)))
+
+
+def smm_set_moments(h: Handle, moments, beta=None):
+    _check(load_library().smm_set_moments(h.ptr, _devptr(moments), _devptr(beta)))
+
+
+def smm_get_psi(h: Handle, psi):
+    _check(load_library().smm_get_psi(h.ptr, _devptr(psi)))
+
+
+def smm_moment_solve(h: Handle, phi) -> int:
+    it = C.c_int32(0)
+    _check(load_library().smm_moment_solve(h.ptr, _devptr(phi), C.byref(it)))
+    return it.value
+
+
+def smm_iterate(h: Handle, phi, tol: float, max_outer: int = 200, relative: bool = False, raise_on_error=True):
+    """Returns (status, stats dict)."""
+    st = smm_stats()
+    rc = load_library().smm_iterate(h.ptr, tol, int(relative), max_outer, _devptr(phi), C.byref(st))
+    if raise_on_error:
+        _check(rc)
+    return rc, st.as_dict()
+
+
+def smm_destroy(h: Handle):
+    h.destroy()

@@ -1,0 +1,177 @@
+"""GPU (C ABI, sm_103a kernels) vs. oracle parity.
+
+Tolerances: FP64 path 1e-11 relative (max norm over the array, relative to
+its max magnitude) per sweep and for the moments; 1e-9 on converged scalar
+fluxes.  The FP32-refined path is compared to the FP64 oracle at the
+tolerance its stopping test implies (stated in each test).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import smm_workloads as W
+from tests.parity_inputs import oracle_disc, problem, sources
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_07386_gb300 import build as B
+    B.build()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def make_gpu(prob, precision=0, **kw):
+    import paper_2304_07386_gb300 as P
+    om, w = P.smm_quadrature(prob["sn"])
+    q, inflow = sources(prob, om)
+    opt = P.smm_default_options()
+    opt.sweep_precision = precision
+    for k, v in kw.items():
+        setattr(opt, k, v)
+    mesh = prob["mesh"]
+    h = P.smm_create(mesh.nodes, mesh.elem_nodes, mesh.m, prob["p"], prob["sn"], prob["sigma_t"], prob["sigma_s"],
+                     q, inflow=inflow, options=opt)
+    return h
+
+
+def make_oracle(prob, kappa_scale=1.0):
+    from oracle.smm import SMMProblem
+    disc = oracle_disc(prob)
+    q, inflow = sources(prob, disc.omega)
+    return disc, SMMProblem(disc, q, inflow, kappa_scale), q, inflow
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+CASES = [
+    # (nx, ny, m, p, sn, seed, kind)
+    (5, 3, 2, 1, 4, 3, "mms"),
+    (4, 4, 2, 2, 8, 5, "mms"),
+    (3, 5, 3, 3, 4, 7, "mms"),
+    (3, 3, 3, 4, 4, 2, "mms"),
+    (1, 1, 1, 2, 6, None, "mms"),
+    (7, 1, 1, 1, 12, None, "iso"),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[:5])))
+def test_sweep_and_moments_fp64(case):
+    import paper_2304_07386_gb300 as P
+    from oracle import closures
+    nx, ny, m, p, sn, seed, kind = case
+    prob = problem(nx, ny, m=m, p=p, sn=sn, seed=seed, kind=kind, c=0.6)
+    h = make_gpu(prob)
+    disc, op, q, inflow = make_oracle(prob)
+    phi = W.mms_phi(prob["pos"][:, :, 0], prob["pos"][:, :, 1])
+    P.smm_sweep(h, dev(phi))
+    info = h.info()
+    psi_g = torch.zeros(info.n_elem * info.n_ord * info.n_dof_elem, dtype=torch.float64, device="cuda")
+    P.smm_get_psi(h, psi_g)
+    psi_g = psi_g.cpu().numpy().reshape(info.n_elem, info.n_ord, info.n_dof_elem).transpose(1, 0, 2)
+    psi_o = disc.sweep(phi, q, inflow)
+    assert rel(psi_g, psi_o) < 1e-11
+    mom = torch.zeros(6 * info.n_elem * info.n_dof_elem, dtype=torch.float64, device="cuda")
+    beta = torch.zeros(info.n_bface * info.n_fq, dtype=torch.float64, device="cuda")
+    P.smm_moments(h, mom, beta)
+    mom_o = closures.nodal_moments(disc, psi_o)
+    mom_g = mom.cpu().numpy().reshape(6, info.n_elem, info.n_dof_elem)
+    for c in range(6):
+        assert rel(mom_g[c], mom_o[c]) < 1e-11 or np.max(np.abs(mom_g[c] - mom_o[c])) < 1e-12 * np.max(np.abs(mom_o[0]))
+    beta_o = closures.beta(disc, psi_o)
+    assert np.max(np.abs(beta.cpu().numpy().reshape(beta_o.shape) - beta_o)) < 1e-11 * np.max(np.abs(mom_o[0]))
+
+
+@pytest.mark.parametrize("case", CASES[:4], ids=lambda c: "x".join(map(str, c[:5])))
+def test_moment_solve_fp64(case):
+    import paper_2304_07386_gb300 as P
+    from oracle import ipsmm
+    nx, ny, m, p, sn, seed, kind = case
+    prob = problem(nx, ny, m=m, p=p, sn=sn, seed=seed, kind=kind, c=0.6)
+    h = make_gpu(prob, tol_cg=1e-14)
+    disc, op, q, inflow = make_oracle(prob)
+    P.smm_sweep(h, None)
+    psi_o = disc.sweep(None, q, inflow)
+    x_o = ipsmm.solve(op.A, op.rhs_from_psi(psi_o))
+    phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+    P.smm_moment_solve(h, phi)
+    assert rel(phi.cpu().numpy(), x_o) < 1e-9
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2]], ids=lambda c: "x".join(map(str, c[:5])))
+def test_iterate_fp64_converged_flux(case):
+    import paper_2304_07386_gb300 as P
+    nx, ny, m, p, sn, seed, kind = case
+    prob = problem(nx, ny, m=m, p=p, sn=sn, seed=seed, kind=kind, c=0.6)
+    h = make_gpu(prob, tol_cg=1e-14)
+    disc, op, q, inflow = make_oracle(prob)
+    phi_o, k_o, _ = op.iterate(tol=1e-12)
+    phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+    rc, st = P.smm_iterate(h, phi, 1e-12, 200)
+    assert rel(phi.cpu().numpy(), phi_o.ravel()) < 1e-9
+    assert abs(st["outer_iterations"] - k_o) <= 1
+
+
+def test_fp32_refined_reaches_fp64_fixed_point():
+    """FP32 local solves corrected from an FP64 residual: the converged flux
+    matches the FP64 oracle to the 1e-10 relative stopping tolerance (x10)."""
+    import paper_2304_07386_gb300 as P
+    prob = problem(4, 4, m=2, p=2, sn=8, seed=5, kind="mms", c=0.6)
+    h = make_gpu(prob, precision=1, tol_cg=1e-14)
+    disc, op, q, inflow = make_oracle(prob)
+    phi_o, _, _ = op.iterate(tol=1e-13)
+    phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+    rc, st = P.smm_iterate(h, phi, 1e-10, 200, relative=True)
+    assert rel(phi.cpu().numpy(), phi_o.ravel()) < 1e-9
+
+
+def test_linear_solution_reproduced_on_gpu():
+    import paper_2304_07386_gb300 as P
+    prob = problem(4, 3, m=2, p=2, sn=4, seed=3, kind="linear", c=0.5)
+    h = make_gpu(prob, tol_cg=1e-14)
+    phi_ex = W.LIN_A + W.LIN_B * prob["pos"][:, :, 0] + W.LIN_C * prob["pos"][:, :, 1]
+    phi = torch.zeros(phi_ex.size, dtype=torch.float64, device="cuda")
+    P.smm_iterate(h, phi, 1e-13, 100)
+    assert np.max(np.abs(phi.cpu().numpy() - phi_ex.ravel())) < 1e-11
+
+
+def test_thick_diffusion_limit_counts_match_oracle():
+    import paper_2304_07386_gb300 as P
+    for eps in (1e-1, 1e-3):
+        prob = problem(8, 8, m=1, p=2, sn=4, sigt=1.0 / eps, c=(1.0 / eps - eps) * eps, kind="iso")
+        prob_q = np.full(prob["pos"].shape[:2], eps)
+        mesh = prob["mesh"]
+        opt = P.smm_default_options()
+        opt.tol_cg = 1e-14
+        h = P.smm_create(mesh.nodes, mesh.elem_nodes, 1, 2, 4, prob["sigma_t"], prob["sigma_s"], prob_q, options=opt)
+        disc, op, _, _ = make_oracle(prob)
+        from oracle.smm import SMMProblem
+        op = SMMProblem(disc, prob_q)
+        phi_o, k_o, _ = op.iterate(tol=1e-6)
+        phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+        rc, st = P.smm_iterate(h, phi, 1e-6, 100)
+        assert st["outer_iterations"] == k_o
+        assert rel(phi.cpu().numpy(), phi_o.ravel()) < 1e-8
+
+
+def test_cycle_rejected():
+    import paper_2304_07386_gb300 as P
+    mesh = W.structured_mesh(2, 1, m=2, domain=(0.0, 2.0, 0.0, 1.0))
+    nodes = mesh.nodes.copy()
+    k = np.argmin(np.hypot(nodes[:, 0] - 1.0, nodes[:, 1] - 0.5))
+    nodes[k, 0] = 1.2
+    with pytest.raises(P.SMMError) as ei:
+        P.smm_create(nodes, mesh.elem_nodes, 2, 1, 8, np.ones(2), np.zeros(2), np.ones((2, 4)))
+    assert ei.value.status == 5
