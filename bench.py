@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the SMM hot path on one GB300 (replicas on N GPUs).
+
+Workload: manufactured-solution transport on a curved mesh -- [0,1]^2,
+128x128 quads of geometry order 3 moved by the seeded sinusoidal map
+(amplitude 0.05), DG p=4 (25 dofs/element), level-symmetric S8 (40
+ordinates), sigma_t = 1, scattering ratio 0.9, MMS angular source and MMS
+inflow.  16,384,000 angular unknowns per sweep.
+
+A step is one SMM outer iteration through the C ABI (smm_iterate with
+max_outer = 1): FP64 transport residual, FP32 correction sweep, FP64 moments
+and boundary correction, IP-SMM right-hand side, block-Jacobi PCG to 1e-12,
+successive-difference check.  value = angular unknowns swept per second of
+whole steps (all ranks).  Inputs stay resident; L2 is flushed (256 MiB
+write) between timed steps.  Also reported: the plain FP64-sweep step, the
+time to a 1e-8 relative successive difference for both, the oracle on the
+host cores (cpu_baseline), and an end-to-end number with host buffers.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WL = dict(nx=128, m=3, p=4, sn=8, sigma_t=1.0, c=0.9, seed=0)
+WL_NAME = "mms-curved-128x128-m3-p4-S8-c0.9"
+METRIC = "sweep unknowns/s (elem*dof*angle)"
+CPU_SAMPLE_NX = 16
+
+
+def workload_inputs(nx, m, p, sn_omega, sigma_t, c, seed):
+    import numpy as np
+
+    import smm_workloads as W
+
+    mesh = W.structured_mesh(nx, m=m, perturb_seed=seed)
+    ne = mesh.n_elem
+    st = np.full(ne, sigma_t)
+    ss = st * c
+    pos = W.dg_node_positions(mesh, p)
+    fpos = W.face_node_positions(mesh, p, W.boundary_faces(mesh))
+    q = np.stack([W.mms_source(pos[:, :, 0], pos[:, :, 1], o[0], o[1], sigma_t, sigma_t * c) for o in sn_omega])
+    inflow = np.stack([W.mms_psi(fpos[:, :, 0], fpos[:, :, 1], o[0], o[1]) for o in sn_omega])
+    return mesh, st, ss, q, inflow
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (runs in a child process with one BLAS/OpenMP thread)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(seconds: float, nx: int) -> dict:
+    """Time oracle outer steps G(varphi) (sweep + closures + RHS + direct IP
+    solve) on an nx*nx mesh of the bench workload's kind for ~`seconds`."""
+    import numpy as np
+
+    from oracle.smm import SMMProblem
+    from oracle.transport import Discretization
+
+    from oracle.quadrature import level_symmetric_2d
+    om, _ = level_symmetric_2d(WL["sn"])
+    mesh, st, ss, q, inflow = workload_inputs(nx, WL["m"], WL["p"], om, WL["sigma_t"], WL["c"], WL["seed"])
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, WL["m"], WL["p"], WL["sn"], st, ss)
+    prob = SMMProblem(disc, q, inflow)
+    phi = np.zeros((disc.ne, disc.n))
+    times = []
+    t_end = time.perf_counter() + seconds
+    while len(times) < 2 or time.perf_counter() < t_end:
+        t0 = time.perf_counter()
+        phi, _ = prob.G(phi)
+        times.append(time.perf_counter() - t0)
+    unknowns = disc.ne * disc.n * disc.nd
+    med = statistics.median(times)
+    return dict(value=unknowns / med, unit="unknowns/s", cores=1, kind="oracle", steps=len(times),
+                seconds_per_step=med,
+                sample=f"oracle outer steps (sweep+closures+RHS+direct IP solve) on a {nx}x{nx} mesh of the same "
+                       f"kind (m={WL['m']}, p={WL['p']}, S{WL['sn']}, c={WL['c']}), median of {len(times)}")
+
+
+def run_oracle_child(seconds: float, nx: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_rate(%f, %d)))" % (ROOT, seconds, nx))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode:
+        return dict(error=r.stderr[-500:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=[], samples=0)
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def sweep_flops_per_task(p: int, mode_residual: bool) -> float:
+    """Algorithmic flops of one local solve (element x ordinate), n = (p+1)^2:
+    assembly 5 n^2 (sigma M - Ox Gx - Oy Gy), face blocks 4 faces x (p+1)^2 x 4,
+    elimination 2/3 n^3, right-hand side elimination + back substitution 2 n^2,
+    source product 2 n^2 (source mode only)."""
+    n = (p + 1) ** 2
+    f = 5 * n * n + 16 * (p + 1) ** 2 + (2.0 / 3.0) * n ** 3 + 2 * n * n
+    if not mode_residual:
+        f += 2 * n * n
+    return f
+
+
+def residual_flops_per_task(p: int) -> float:
+    """FP64 residual r = M(s - sigma psi) + Ox Gx psi + Oy Gy psi - faces: 6 n^2 + 16 (p+1)^2."""
+    n = (p + 1) ** 2
+    return 6 * n * n + 16 * (p + 1) ** 2
+
+
+def cg_bytes_per_iter(ne: int, n: int) -> float:
+    """HBM bytes of one PCG iteration: operator blocks (5 n^2 per element, FP64),
+    preconditioner blocks (n^2), and vector traffic (spmv: read p, write q;
+    update: read x,p,r,q, write x,r,z; direction: read z,p, write p)."""
+    return 8.0 * ne * (6 * n * n + 12 * n)
+
+
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2304_07386_gb300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2304_07386_gb300 import build as B
+    B.build()
+    om, _ = P.smm_quadrature(WL["sn"])
+    t_in = time.time()
+    mesh, st, ss, q, inflow = workload_inputs(WL["nx"], WL["m"], WL["p"], om, WL["sigma_t"], WL["c"], WL["seed"])
+    t_in = time.time() - t_in
+    stream = torch.cuda.Stream()
+
+    def create(precision):
+        opt = P.smm_default_options()
+        opt.sweep_precision = precision
+        opt.tol_cg = 1e-12
+        t0 = time.time()
+        h = P.smm_create(mesh.nodes, mesh.elem_nodes, WL["m"], WL["p"], WL["sn"], st, ss, q, inflow=inflow,
+                         options=opt, stream=stream)
+        return h, time.time() - t0
+
+    h, t_setup = create(P.SMM_SWEEP_FP32_REFINED)
+    info = h.info()
+    ne, n, nd = info.n_elem, info.n_dof_elem, info.n_ord
+    unknowns = info.n_angular
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
+    phi = torch.zeros(ne * n, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def step(handle, x):
+        rc, s = P.smm_iterate(handle, x, 1e-300, 1, relative=True, raise_on_error=False)
+        if rc not in (0, 7):
+            raise P.SMMError(rc, P.load_library().smm_last_error().decode())
+        return s
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(h, phi)
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        stats = []
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                stats.append(step(h, phi))
+                ev[k][1].record(stream)
+            barrier()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * unknowns / (ms * 1e-3)
+
+    def mean(key):
+        return sum(s[key] for s in stats) / len(stats)
+
+    ms_sweep, ms_res, ms_solve = mean("ms_sweep"), mean("ms_residual"), mean("ms_solve")
+    cg_it = mean("cg_total")
+    launches = int(sum(s["n_launches"] for s in stats))
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
+    fp64_peak = 1.25                               # TFLOP/s nominal GB300 FP64
+    tasks = ne * nd
+    sweep_tf = tasks * sweep_flops_per_task(WL["p"], True) / (ms_sweep * 1e-3) / 1e12
+    res_tf = tasks * residual_flops_per_task(WL["p"]) / (ms_res * 1e-3) / 1e12 if ms_res > 0 else 0.0
+    cg_gbs = cg_it * cg_bytes_per_iter(ne, n) / (ms_solve * 1e-3) / 1e9 if ms_solve > 0 else 0.0
+    rooflines = {
+        "sweep_fp32": dict(bound="alu", achieved=sweep_tf, peak=fp32_peak, unit="TFLOP/s", frac=sweep_tf / fp32_peak,
+                           traffic=None, ms=ms_sweep, peak_note="derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"),
+        "residual_fp64": dict(bound="alu", achieved=res_tf, peak=fp64_peak, unit="TFLOP/s", frac=res_tf / fp64_peak,
+                              traffic=None, ms=ms_res, peak_note="nominal GB300 FP64 rate"),
+        "pcg_fp64": dict(bound="hbm", achieved=cg_gbs, peak=hbm, unit="GB/s", frac=cg_gbs / hbm, traffic=None,
+                         ms=ms_solve, peak_note=f"{hbm_src} copy bandwidth"),
+    }
+    dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
+    roof = dict(rooflines[dom])
+    roof["kernel"] = dom
+
+    # end to end through the C ABI with host buffers: H2D of varphi^k, one outer
+    # step, D2H of varphi^{k+1}, all inside the timed region
+    host = torch.zeros(ne * n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for k in range(max(2, args.steps)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            phi.copy_(host, non_blocking=True)
+            step(h, phi)
+            host.copy_(phi, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+    e2e = dict(value=world * unknowns / (statistics.mean(e2e_ms) * 1e-3), unit="unknowns/s",
+               h2d_bytes_per_step=8 * ne * n, d2h_bytes_per_step=8 * ne * n)
+
+    extra = {}
+    if not args.quick:
+        # plain FP64-sweep step and the two solves to a 1e-8 relative difference
+        h64, _ = create(P.SMM_SWEEP_FP64)
+        phi64 = torch.zeros_like(phi)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                step(h64, phi64)
+            torch.cuda.synchronize()
+            ev64 = []
+            for k in range(max(2, min(args.steps, 5))):
+                flush.fill_(2.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s64 = step(h64, phi64)
+                b.record(stream)
+                b.synchronize()
+                ev64.append((a.elapsed_time(b), s64))
+        ms64 = statistics.mean(x for x, _ in ev64)
+        extra["plain_fp64_step"] = dict(value=unknowns / (ms64 * 1e-3), ms_per_step=ms64,
+                                        ms_sweep=statistics.mean(s["ms_sweep"] for _, s in ev64))
+
+        def solve(precision):
+            hh, _ = create(precision)
+            x = torch.zeros_like(phi)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                rc, s = P.smm_iterate(hh, x, 1e-8, 200, relative=True, raise_on_error=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            hh.destroy()
+            return dt, s, rc, x
+
+        t64, s64, rc64, x64 = solve(P.SMM_SWEEP_FP64)
+        t32, s32, rc32, x32 = solve(P.SMM_SWEEP_FP32_REFINED)
+        diff = float((x64 - x32).abs().max() / x64.abs().max())
+        extra["time_to_1e-8"] = dict(plain_fp64_s=t64, plain_outer=s64["outer_iterations"], plain_status=rc64,
+                                     fp32_refined_s=t32, fp32_outer=s32["outer_iterations"], fp32_status=rc32,
+                                     rel_diff_fp32_vs_fp64=diff, guess="zero (learned guess not built)")
+        h64.destroy()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = run_oracle_child(args.cpu_seconds, CPU_SAMPLE_NX)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 sweep + f64 residual/moments/CG", "data": "synthetic",
+            "config": {"workload": WL_NAME, "n_elem": ne, "p": WL["p"], "geom_order": WL["m"], "sn": WL["sn"],
+                       "n_ord": nd, "angular_unknowns": unknowns, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MiB write)", "sweep_precision": "fp32-refined",
+                       "cg_tol": 1e-12},
+            "roofline": roof, "roofline_all": rooflines, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "phases_ms": dict(residual=ms_res, sweep=ms_sweep, moments=mean("ms_moments"), rhs=mean("ms_rhs"),
+                              solve=ms_solve, cg_iters=cg_it),
+            "sweep_only": dict(value=unknowns / ((ms_sweep + ms_res) * 1e-3), unit="unknowns/s",
+                               note="residual + FP32 sweep kernels"),
+            "setup_s": t_setup, "inputs_s": t_in,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    h.destroy()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args) -> None:
+    """The oracle arm: the CPU oracle on the host cores, K timed steps of a
+    bounded sample (one outer step each), after W warm-up steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    import numpy as np
+
+    from oracle.quadrature import level_symmetric_2d
+    from oracle.smm import SMMProblem
+    from oracle.transport import Discretization
+
+    om, _ = level_symmetric_2d(WL["sn"])
+    nx = CPU_SAMPLE_NX
+    mesh, st, ss, q, inflow = workload_inputs(nx, WL["m"], WL["p"], om, WL["sigma_t"], WL["c"], WL["seed"])
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, WL["m"], WL["p"], WL["sn"], st, ss)
+    prob = SMMProblem(disc, q, inflow)
+    phi = np.zeros((disc.ne, disc.n))
+    for _ in range(args.warmup):
+        phi, _ = prob.G(phi)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        phi, _ = prob.G(phi)
+        t.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(t)
+    unknowns = disc.ne * disc.n * disc.nd
+    value = unknowns / (ms * 1e-3)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"oracle outer steps on a {nx}x{nx} mesh of the bench workload's kind (m={WL['m']}, p={WL['p']}, "
+              f"S{WL['sn']}); the full {WL['nx']}x{WL['nx']} workload is {(WL['nx'] // nx) ** 2}x larger")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WL_NAME, "sample_mesh": f"{nx}x{nx}", "angular_unknowns": unknowns},
+        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 and time-to-solution extras")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -98,7 +98,10 @@ typedef struct {
     int32_t cg_total, cg_min, cg_max; /* CG iterations over the outer steps */
     double last_diff;           /* max |varphi^{k+1} - varphi^k| of the last step */
     double last_rel_diff;       /* last_diff / max |varphi^{k+1}| */
-    double ms_sweep, ms_moments, ms_rhs, ms_solve; /* accumulated phase times */
+    double ms_residual;         /* FP64 transport residual kernel (refined mode) */
+    double ms_sweep;            /* sweep kernel alone */
+    double ms_moments, ms_rhs, ms_solve; /* moments + beta, RHS, CG (accumulated, ms) */
+    int64_t n_launches;         /* kernels this library launched during the call */
 } smm_stats;
 
 /* Fill *opt with the defaults listed above. */

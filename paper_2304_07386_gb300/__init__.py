@@ -1,7 +1,9 @@
 """GB300-native second-moment-method (SMM) transport: C-ABI library
 (libsmm.so, hand-written CUDA for sm_103a) and its thin Python binding."""
-from .smm import (Handle, SMMError, load_library, smm_create, smm_default_options, smm_destroy, smm_get_psi,
+from .smm import (SMM_INFLOW_NODAL, SMM_INFLOW_VACUUM, SMM_SOURCE_ANGULAR, SMM_SOURCE_ISOTROPIC, SMM_SWEEP_FP32_REFINED,
+                  SMM_SWEEP_FP64, Handle, SMMError, load_library, smm_create, smm_default_options, smm_destroy, smm_get_psi,
                   smm_iterate, smm_moment_solve, smm_moments, smm_quadrature, smm_set_moments, smm_sweep)
 
-__all__ = ["Handle", "SMMError", "load_library", "smm_create", "smm_default_options", "smm_destroy", "smm_get_psi",
+__all__ = ["SMM_INFLOW_NODAL", "SMM_INFLOW_VACUUM", "SMM_SOURCE_ANGULAR", "SMM_SOURCE_ISOTROPIC",
+           "SMM_SWEEP_FP32_REFINED", "SMM_SWEEP_FP64", "Handle", "SMMError", "load_library", "smm_create", "smm_default_options", "smm_destroy", "smm_get_psi",
            "smm_iterate", "smm_moment_solve", "smm_moments", "smm_quadrature", "smm_set_moments", "smm_sweep"]

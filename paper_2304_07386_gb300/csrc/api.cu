@@ -70,7 +70,8 @@ struct smm_ctx {
     // pinned host scratch
     double* h_scal = nullptr;
     int* h_int = nullptr;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    long long launches = 0;
 
     template <class T>
     T* alloc(size_t count) {
@@ -297,6 +298,7 @@ smm_status enqueue_sweep(smm_handle h, const double* phi) {
         a.phi = phi; a.src = h->src; a.src_angular = h->src_angular; a.inflow = h->has_inflow ? h->inflow : nullptr;
         a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr; a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket;
         a.err = h->err; a.timeout_ns = tmo;
+        SMM_CUDA(cudaEventRecord(h->ev[5], h->stream));
         smm::launch_sweep<double>(h->p, smm::SWEEP_SOURCE, a, h->sweep_grid, h->stream);
     } else {
         smm::ResidualArgs r{};
@@ -306,6 +308,8 @@ smm_status enqueue_sweep(smm_handle h, const double* phi) {
         r.src = h->src; r.src_angular = h->src_angular; r.inflow = h->has_inflow ? h->inflow : nullptr; r.psi = h->psi;
         r.rhs = h->res;
         smm::launch_residual(h->p, r, h->stream);
+        h->launches += 1;
+        SMM_CUDA(cudaEventRecord(h->ev[5], h->stream));
         smm::SweepArgs<float> a{};
         a.ne = h->ne; a.nd = h->nd; a.ntask = h->ntask; a.tasks = h->tasks; a.ox = h->ox; a.oy = h->oy;
         a.sigma_t = h->sigma_t; a.sigma_s = h->sigma_s; a.M = h->M32; a.Gx = h->Gx32; a.Gy = h->Gy32; a.Fx = h->Fx32;
@@ -315,6 +319,7 @@ smm_status enqueue_sweep(smm_handle h, const double* phi) {
         a.timeout_ns = tmo;
         smm::launch_sweep<float>(h->p, smm::SWEEP_RESIDUAL, a, h->sweep_grid, h->stream);
     }
+    h->launches += 1;
     SMM_CUDA(cudaGetLastError());
     return SMM_OK;
 }
@@ -323,6 +328,7 @@ smm_status enqueue_moments(smm_handle h) {
     smm::launch_moments(h->ne, h->nd, h->n, h->w, h->ox, h->oy, h->psi, h->mom, h->stream);
     smm::launch_beta(h->nb, h->nd, h->n, h->p, h->nfq, h->bface_elem, h->bface_face, h->w, h->ox, h->oy, h->L1,
                      h->b_nhat, h->b_eb0, h->psi, h->mom, h->beta, h->stream);
+    h->launches += h->nb > 0 ? 2 : 1;
     SMM_CUDA(cudaGetLastError());
     return SMM_OK;
 }
@@ -331,6 +337,7 @@ smm_status enqueue_rhs(smm_handle h) {
     smm::launch_rhs(h->ne, h->n, h->p, h->nfq, h->mom, h->beta, h->bfixed, h->Kxx, h->Ks, h->Kyy, h->Dfx, h->Dfy, h->nds,
                     h->L1, h->sigma_t, h->nbr, h->nbr_face, h->nbr_flip, h->bface_id, h->b_ds, h->trace, h->rhs,
                     h->stream);
+    h->launches += 2;
     SMM_CUDA(cudaGetLastError());
     return SMM_OK;
 }
@@ -359,6 +366,7 @@ smm_status run_cg(smm_handle h, double* x, int* iters) {
     smm::CGArgs a = cg_args(h, x);
     SMM_CUDA(cudaMemsetAsync(h->ctl, 0, 8 * sizeof(int), h->stream));
     smm::cg_start(a, h->opt.tol_cg, h->opt.max_cg, h->stream);
+    h->launches += 2;
     SMM_CUDA(cudaGetLastError());
     int chunk = 8;
     while (true) {
@@ -366,6 +374,7 @@ smm_status run_cg(smm_handle h, double* x, int* iters) {
         SMM_CUDA(cudaStreamSynchronize(h->stream));
         if (h->h_int[0]) break;
         smm::cg_iterations(a, chunk, h->stream);
+        h->launches += 3LL * chunk;
         SMM_CUDA(cudaGetLastError());
         chunk = std::min(chunk * 2, 64);
     }
@@ -443,6 +452,7 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
     if (!h || !phi_dev || !(tol > 0) || max_outer < 1) return fail(SMM_ERR_INVALID_ARG, "bad argument");
     smm_stats local{};
     local.cg_min = 1 << 30;
+    const long long launches0 = h->launches;
     const size_t nphi = (size_t)h->ne * h->n;
     smm_status result = SMM_ERR_NOT_CONVERGED;
     for (int k = 1; k <= max_outer; ++k) {
@@ -457,24 +467,31 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
         st = enqueue_rhs(h);
         if (st != SMM_OK) return st;
         SMM_CUDA(cudaEventRecord(h->ev[3], h->stream));
-        st = check_device_error(h);
-        if (st != SMM_OK) return st;
         int it = 0;
         st = run_cg(h, phi_dev, &it);
         if (st != SMM_OK && st != SMM_ERR_NOT_CONVERGED) return st;
         SMM_CUDA(cudaEventRecord(h->ev[4], h->stream));
         SMM_CUDA(cudaMemsetAsync(h->nonfinite, 0, sizeof(int), h->stream));
         smm::launch_diff((int)nphi, phi_dev, h->phi_prev, h->dpart, h->dout, h->nonfinite, h->stream);
+        h->launches += 2;
         SMM_CUDA(cudaMemcpyAsync(h->h_scal, h->dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         SMM_CUDA(cudaMemcpyAsync(h->h_int + 4, h->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        SMM_CUDA(cudaMemcpyAsync(h->h_int + 5, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         SMM_CUDA(cudaStreamSynchronize(h->stream));
-        float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
-        cudaEventElapsedTime(&t01, h->ev[0], h->ev[1]);
+        if (h->h_int[5] == smm::DEV_TIMEOUT) {
+            cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+            if (stats) *stats = local;
+            return fail(SMM_ERR_DEVICE_TIMEOUT, "a sweep dependency wait exceeded spin_timeout_s");
+        }
+        float t01 = 0, t12 = 0, t23 = 0, t34 = 0, t05 = 0;
+        cudaEventElapsedTime(&t05, h->ev[0], h->ev[5]);
+        cudaEventElapsedTime(&t01, h->ev[5], h->ev[1]);
         cudaEventElapsedTime(&t12, h->ev[1], h->ev[2]);
         cudaEventElapsedTime(&t23, h->ev[2], h->ev[3]);
         cudaEventElapsedTime(&t34, h->ev[3], h->ev[4]);
-        local.ms_sweep += t01; local.ms_moments += t12; local.ms_rhs += t23; local.ms_solve += t34;
+        local.ms_residual += t05; local.ms_sweep += t01; local.ms_moments += t12; local.ms_rhs += t23; local.ms_solve += t34;
         local.outer_iterations = k;
+        local.n_launches = h->launches - launches0;
         local.cg_total += it;
         local.cg_min = std::min(local.cg_min, it);
         local.cg_max = std::max(local.cg_max, it);

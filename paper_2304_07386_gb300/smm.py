@@ -43,8 +43,8 @@ class smm_info(C.Structure):
 class smm_stats(C.Structure):
     _fields_ = [("outer_iterations", C.c_int32), ("cg_total", C.c_int32), ("cg_min", C.c_int32),
                 ("cg_max", C.c_int32), ("last_diff", C.c_double), ("last_rel_diff", C.c_double),
-                ("ms_sweep", C.c_double), ("ms_moments", C.c_double), ("ms_rhs", C.c_double),
-                ("ms_solve", C.c_double)]
+                ("ms_residual", C.c_double), ("ms_sweep", C.c_double), ("ms_moments", C.c_double),
+                ("ms_rhs", C.c_double), ("ms_solve", C.c_double), ("n_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
