@@ -176,6 +176,36 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
 
 smm_status smm_destroy(smm_handle h);
 
+/* Allocation-free block-Jacobi preconditioned CG.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code that runs under another framework's allocator, inside
+ * a fixed memory budget, or on a path that must not touch the CUDA
+ * allocator.  It solves A x = b for a symmetric positive definite operator
+ * made of n x n blocks on an element graph (the layout smm uses for the
+ * IP-SMM operator) and allocates nothing: the CG vectors and reduction
+ * slots live in one fixed __device__ array of about 16.9 MB that every GPU
+ * which loads the library holds until the process exits.
+ *   n_elem, n: blocks of n unknowns (1 <= n <= 64); n_elem * n must not
+ *     exceed 524288 (else SMM_ERR_INVALID_ARG).
+ *   diag_blocks: dev [n_elem][n][n], off_blocks: dev [n_elem][4][n][n] (block
+ *     coupling element e to its neighbour across face f), pinv_blocks: dev
+ *     [n_elem][n][n] (inverse of each diagonal block); every block is stored
+ *     column-major: entry (i, j) at [j*n + i].
+ *   nbr: dev [n_elem][4] neighbour element ids, -1 where there is none.
+ *   b: dev [n_elem*n]; x: dev [n_elem*n], in: initial guess, out: solution.
+ *   Stops when ||r||_2 <= tol ||b||_2 or after max_iters iterations.
+ *   cuda_stream: stream of the current device (NULL = legacy default);
+ *   iters_out (host, may be NULL): iterations used.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents; calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialized by the caller.
+ * Errors: INVALID_ARG, NOT_CONVERGED (x holds the last iterate), NONFINITE, CUDA. */
+smm_status smm_block_pcg_noalloc(int32_t n_elem, int32_t n, const double* diag_blocks, const double* off_blocks,
+                                 const int32_t* nbr, const double* pinv_blocks, const double* b, double* x,
+                                 double tol, int32_t max_iters, void* cuda_stream, int32_t* iters_out);
+
 /* Message of the calling thread's most recent error ("" if none); valid
  * until the next call on that thread. */
 const char* smm_last_error(void);

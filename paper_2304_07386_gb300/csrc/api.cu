@@ -22,6 +22,12 @@ smm_status fail(smm_status s, const std::string& msg) {
     return s;
 }
 
+}  // namespace
+
+void smm::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+
 #define SMM_CUDA(call)                                                                        \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \

@@ -108,6 +108,9 @@ void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s);
 void cg_iterations(const CGArgs& a, int count, cudaStream_t s);
 int cg_threads_per_block(int n);
 
+// message returned by smm_last_error() for the calling thread
+void set_last_error(const char* msg);
+
 // outer step: diff = max|new - old|, max|new|, nonfinite check
 void launch_diff(int nrow, const double* a, const double* b, double* part, double* out, int* flag, cudaStream_t s);
 

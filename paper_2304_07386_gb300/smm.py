@@ -83,6 +83,8 @@ def load_library(path: str | None = None):
     lib.smm_moment_solve.argtypes = [vp, vp, ip]
     lib.smm_iterate.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, vp, C.POINTER(smm_stats)]
     lib.smm_destroy.argtypes = [vp]
+    lib.smm_block_pcg_noalloc.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, C.c_double, C.c_int32, vp, ip]
+    lib.smm_block_pcg_noalloc.restype = C.c_int
     for name in ("smm_quadrature", "smm_create", "smm_get_info", "smm_sweep", "smm_moments", "smm_set_moments",
                  "smm_get_psi", "smm_moment_solve", "smm_iterate", "smm_destroy"):
         getattr(lib, name).restype = C.c_int
@@ -214,3 +216,21 @@ def smm_iterate(h: Handle, phi, tol: float, max_outer: int = 200, relative: bool
 
 def smm_destroy(h: Handle):
     h.destroy()
+
+
+def smm_block_pcg_noalloc(diag_blocks, off_blocks, nbr, pinv_blocks, b, x, tol=1e-12, max_iters=20000,
+                          stream=None) -> int:
+    """Allocation-free block-Jacobi PCG (see include/smm.h).  Blocks are CUDA
+    float64 tensors [n_elem][n][n] / [n_elem][4][n][n], column-major per block;
+    nbr a CUDA int32 tensor [n_elem][4]; b, x CUDA float64 [n_elem*n]."""
+    import torch
+
+    n_elem, n = int(diag_blocks.shape[0]), int(diag_blocks.shape[1])
+    if not (nbr.is_cuda and nbr.is_contiguous() and nbr.dtype == torch.int32):
+        raise ValueError("nbr must be a contiguous CUDA int32 tensor")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    it = C.c_int32(0)
+    _check(load_library().smm_block_pcg_noalloc(n_elem, n, _devptr(diag_blocks), _devptr(off_blocks),
+                                                C.c_void_p(nbr.data_ptr()), _devptr(pinv_blocks), _devptr(b),
+                                                _devptr(x), tol, max_iters, C.c_void_p(s.cuda_stream), C.byref(it)))
+    return it.value
