@@ -64,6 +64,7 @@ typedef enum {
 enum { SMM_SOURCE_ISOTROPIC = 0, SMM_SOURCE_ANGULAR = 1 };
 enum { SMM_INFLOW_VACUUM = 0, SMM_INFLOW_NODAL = 1 };
 enum { SMM_SWEEP_FP64 = 0, SMM_SWEEP_FP32_REFINED = 1 };
+enum { SMM_PRECOND_BLOCK_JACOBI = 0, SMM_PRECOND_MULTIGRID = 1 };
 
 typedef struct {
     int32_t n_elem;             /* number of quadrilaterals */
@@ -86,6 +87,8 @@ typedef struct {
     int32_t max_cg;             /* CG iteration cap per moment solve (default 20000) */
     double kappa_scale;         /* multiplies the IP penalty (default 1) */
     double spin_timeout_s;      /* bound on every device-side wait (default 2 s) */
+    int32_t precond;            /* moment-solve preconditioner: SMM_PRECOND_MULTIGRID
+                                   (default) or SMM_PRECOND_BLOCK_JACOBI */
 } smm_options;
 
 typedef struct {
@@ -160,7 +163,10 @@ smm_status smm_set_moments(smm_handle h, const double* moments_dev, const double
 smm_status smm_get_psi(smm_handle h, double* psi_dev);
 
 /* Solve the IP-SMM moment system (Eq. ipsmm) with the handle's closures by
- * block-Jacobi preconditioned CG.  phi_dev: dev [n_elem][n], in: initial
+ * preconditioned CG: a symmetric multigrid V-cycle (damped element-block
+ * Jacobi on Y_p, Galerkin coarse level of continuous bilinear functions on
+ * the mesh vertices, smoothed aggregation below it, dense coarsest solve) or
+ * element-block Jacobi alone (options.precond).  phi_dev: dev [n_elem][n], in: initial
  * guess, out: solution.  cg_iters (host, may be NULL): iterations used.
  * Errors: NOT_CONVERGED (phi_dev holds the last iterate), NONFINITE, CUDA. */
 smm_status smm_moment_solve(smm_handle h, double* phi_dev, int32_t* cg_iters);

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/smm.h"
+#include "amg.hpp"
 #include "kernels.cuh"
 #include "setup.hpp"
 
@@ -73,6 +74,7 @@ struct smm_ctx {
     int* ctl = nullptr;
     int* nonfinite = nullptr;
     int cg_nblk = 1;
+    smm::MGPlan mg;
     // pinned host scratch
     double* h_scal = nullptr;
     int* h_int = nullptr;
@@ -134,6 +136,7 @@ void smm_default_options(smm_options* opt) {
     opt->max_cg = 20000;
     opt->kappa_scale = 1.0;
     opt->spin_timeout_s = 2.0;
+    opt->precond = SMM_PRECOND_MULTIGRID;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -164,7 +167,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     if (opt) o = *opt;
     if (o.sweep_precision != SMM_SWEEP_FP64 && o.sweep_precision != SMM_SWEEP_FP32_REFINED)
         return fail(SMM_ERR_INVALID_ARG, "bad sweep precision");
-    if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0))
+    if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0) ||
+        (o.precond != SMM_PRECOND_BLOCK_JACOBI && o.precond != SMM_PRECOND_MULTIGRID))
         return fail(SMM_ERR_INVALID_ARG, "bad options");
 
     smm::Input in;
@@ -260,6 +264,54 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         return bail(SMM_ERR_OOM, "pinned allocation failed");
     for (auto& e : h->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(SMM_ERR_CUDA, "cudaEventCreate failed");
+    if (o.precond == SMM_PRECOND_MULTIGRID) {
+        const int nc = (s.m + 1) * (s.m + 1);
+        std::vector<int> corners((size_t)s.ne * 4);
+        const int cidx[4] = {0, s.m, s.m * (s.m + 1), s.m * (s.m + 1) + s.m};
+        for (int e = 0; e < s.ne; ++e)
+            for (int c = 0; c < 4; ++c) corners[(size_t)e * 4 + c] = mesh->elem_nodes[(size_t)e * nc + cidx[c]];
+        std::vector<int> nbr(s.nbr.begin(), s.nbr.end());
+        smm::MGHierarchy H;
+        std::string merr;
+        if (!smm::build_multigrid(s.ne, s.n, s.Adiag, s.Aoff, s.Pinv, nbr, corners, smm::gauss_lobatto01(s.p1).x, H,
+                                  merr))
+            return bail(SMM_ERR_MESH, merr);
+        if ((int)H.lv.size() - 1 > 15) return bail(SMM_ERR_MESH, "multigrid: too many levels");
+        smm::MGPlan& P = h->mg;
+        P.enabled = true;
+        P.ne = s.ne; P.n = s.n; P.nu0 = 2; P.omega0 = H.omega0;
+        P.AdT = h->AdT; P.AoT = h->AoT; P.PinvT = h->PinvT; P.nbr = h->nbr;
+        P.x0 = h->alloc<double>(nphi); P.x0b = h->alloc<double>(nphi); P.res0 = h->alloc<double>(nphi);
+        P.nvert = H.nvert;
+        int *vid = nullptr, *vrp = nullptr, *vinc = nullptr;
+        double* w4 = nullptr;
+        ok &= upload(h, vid, H.vid) && upload(h, vrp, H.vrp) && upload(h, vinc, H.vinc) && upload(h, w4, H.w4);
+        P.vid = vid; P.vrp = vrp; P.vinc = vinc; P.w4 = w4;
+        P.nlev = (int)H.lv.size() - 1;
+        for (int l = 1; l <= P.nlev; ++l) {
+            const smm::MGLevel& L = H.lv[l];
+            smm::MGLevelDev& D = P.lv[l];
+            D.n = L.A.nrow;
+            D.omega = L.omega;
+            D.b = h->alloc<double>(D.n); D.x = h->alloc<double>(D.n); D.r = h->alloc<double>(D.n);
+            D.t = h->alloc<double>(D.n);
+            ok &= D.b && D.x && D.r && D.t;
+            if (l < P.nlev) {
+                int *arp, *aci, *prp, *pci, *rrp, *rci;
+                double *av, *dv, *pv, *rv;
+                ok &= upload(h, arp, L.A.rp) && upload(h, aci, L.A.ci) && upload(h, av, L.A.v) && upload(h, dv, L.dinv);
+                ok &= upload(h, prp, L.P.rp) && upload(h, pci, L.P.ci) && upload(h, pv, L.P.v);
+                ok &= upload(h, rrp, L.R.rp) && upload(h, rci, L.R.ci) && upload(h, rv, L.R.v);
+                D.Arp = arp; D.Aci = aci; D.Av = av; D.dinv = dv; D.Prp = prp; D.Pci = pci; D.Pv = pv;
+                D.Rrp = rrp; D.Rci = rci; D.Rv = rv;
+            }
+        }
+        double* cinv = nullptr;
+        ok &= upload(h, cinv, H.coarse_inv);
+        P.cinv = cinv;
+        ok &= P.x0 && P.x0b && P.res0 && cudaStreamSynchronize(h->stream) == cudaSuccess;
+        if (!ok) return bail(SMM_ERR_OOM, "multigrid upload failed");
+    }
     const int bps = smm::sweep_blocks_per_sm(s.p, h->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE, h->fp32);
     const long long want = ((long long)h->ntask + 7) / 8;
     h->sweep_grid = (int)std::max(1LL, std::min<long long>((long long)h->sms * bps, want));
@@ -371,18 +423,27 @@ smm_status check_device_error(smm_handle h) {
 smm_status run_cg(smm_handle h, double* x, int* iters) {
     smm::CGArgs a = cg_args(h, x);
     SMM_CUDA(cudaMemsetAsync(h->ctl, 0, 8 * sizeof(int), h->stream));
-    smm::cg_start(a, h->opt.tol_cg, h->opt.max_cg, h->stream);
-    h->launches += 2;
+    const bool mg = h->mg.enabled;
+    if (mg) {
+        h->launches += smm::cgx_start(a, h->opt.tol_cg, h->opt.max_cg, h->mg, h->stream);
+    } else {
+        smm::cg_start(a, h->opt.tol_cg, h->opt.max_cg, h->stream);
+        h->launches += 2;
+    }
     SMM_CUDA(cudaGetLastError());
-    int chunk = 8;
+    int chunk = mg ? 4 : 8;
     while (true) {
         SMM_CUDA(cudaMemcpyAsync(h->h_int, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         SMM_CUDA(cudaStreamSynchronize(h->stream));
         if (h->h_int[0]) break;
-        smm::cg_iterations(a, chunk, h->stream);
-        h->launches += 3LL * chunk;
+        if (mg) {
+            h->launches += smm::cgx_iterations(a, chunk, h->mg, h->stream);
+        } else {
+            smm::cg_iterations(a, chunk, h->stream);
+            h->launches += 3LL * chunk;
+        }
         SMM_CUDA(cudaGetLastError());
-        chunk = std::min(chunk * 2, 64);
+        chunk = std::min(chunk * 2, mg ? 16 : 64);
     }
     if (iters) *iters = h->h_int[1];
     if (h->h_int[3]) return fail(SMM_ERR_NONFINITE, "non-finite value in the moment solve");

@@ -104,7 +104,35 @@ struct CGArgs {
     double* scal;              // [8]: rz, pq, rr, bb, thresh2, -, -, -
     int* ctl;                  // [4]: done, iters, max_iters, nonfinite
 };
+// multigrid preconditioner (device side of an MGHierarchy)
+struct MGLevelDev {
+    int n = 0;                                   // unknowns on this level
+    const int* Arp = nullptr; const int* Aci = nullptr; const double* Av = nullptr;
+    const double* dinv = nullptr;
+    double omega = 0.0;
+    const int* Prp = nullptr; const int* Pci = nullptr; const double* Pv = nullptr;  // to level l+1
+    const int* Rrp = nullptr; const int* Rci = nullptr; const double* Rv = nullptr;
+    double* b = nullptr; double* x = nullptr; double* r = nullptr; double* t = nullptr;
+};
+struct MGPlan {
+    bool enabled = false;
+    int ne = 0, n = 0, nu0 = 2;
+    double omega0 = 0.0;
+    const double* AdT = nullptr; const double* AoT = nullptr; const double* PinvT = nullptr;
+    const int32_t* nbr = nullptr;
+    double* x0 = nullptr; double* x0b = nullptr; double* res0 = nullptr;   // [ne*n]
+    int nvert = 0;
+    const int* vid = nullptr; const double* w4 = nullptr; const int* vrp = nullptr; const int* vinc = nullptr;
+    int nlev = 0;                                 // levels 1..nlev (nlev = coarsest, dense)
+    MGLevelDev lv[16];
+    const double* cinv = nullptr;
+};
+// z = V-cycle(r); returns the number of kernel launches; ctl (nullable): skip when set
+int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s);
+
 void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s);
+int cgx_start(const CGArgs& a, double tol, int max_iters, const MGPlan& mg, cudaStream_t s);
+int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s);
 void cg_iterations(const CGArgs& a, int count, cudaStream_t s);
 int cg_threads_per_block(int n);
 

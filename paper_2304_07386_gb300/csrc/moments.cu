@@ -2,6 +2,7 @@
 // block-Jacobi preconditioned CG of the moment system (FP64).
 #include <algorithm>
 
+#include "blockops.cuh"
 #include "kernels.cuh"
 
 namespace smm {
@@ -232,19 +233,7 @@ __device__ double sum_partials(const double* part, int nblk, double* sh) {
 }
 
 __device__ __forceinline__ double spmv_row(const CGArgs& a, const double* v, int e, int i) {
-    const int n = a.n;
-    const double* Ad = a.AdT + (size_t)e * n * n + i;
-    const double* ve = v + (size_t)e * n;
-    double acc = 0.0;
-    for (int j = 0; j < n; ++j) acc += Ad[(size_t)j * n] * ve[j];
-    for (int f = 0; f < 4; ++f) {
-        const int e2 = a.nbr[e * 4 + f];
-        if (e2 < 0) continue;
-        const double* Ao = a.AoT + ((size_t)e * 4 + f) * n * n + i;
-        const double* v2 = v + (size_t)e2 * n;
-        for (int j = 0; j < n; ++j) acc += Ao[(size_t)j * n] * v2[j];
-    }
-    return acc;
+    return block_row(a.AdT, a.AoT, a.nbr, a.n, v, e, i);
 }
 
 // r = b - A x ; z = P r ; p = z ; partials: rz, rr, bb
@@ -381,6 +370,76 @@ __global__ void cg_direction_kernel(CGArgs a) {
     }
 }
 
+// ---- CG with an external preconditioner (multigrid) ----
+// r = b - A x ; partials rr -> part[nblk], bb -> part[2 nblk]
+__global__ void cgx_init_r_kernel(CGArgs a) {
+    __shared__ double sh[40];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    double r = 0.0, bv = 0.0;
+    if (e < a.ne) {
+        bv = a.b[(size_t)e * n + i];
+        r = bv - spmv_row(a, a.x, e, i);
+        a.r[(size_t)e * n + i] = r;
+    }
+    double s1 = block_sum(r * r, sh);
+    double s2 = block_sum(bv * bv, sh);
+    if (threadIdx.x == 0) {
+        a.part[a.nblk + blockIdx.x] = s1;
+        a.part[2 * a.nblk + blockIdx.x] = s2;
+    }
+}
+
+// p = z ; partial rz -> part[0]
+__global__ void cgx_init_p_kernel(CGArgs a) {
+    __shared__ double sh[40];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    double rz = 0.0;
+    if (e < a.ne) {
+        const size_t o = (size_t)e * n + i;
+        const double z = a.z[o];
+        a.p[o] = z;
+        rz = z * a.r[o];
+    }
+    double s = block_sum(rz, sh);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = s;
+}
+
+// alpha = rz / pq ; x += alpha p ; r -= alpha q ; partial rr -> part[2 nblk]
+__global__ void cgx_update_kernel(CGArgs a) {
+    if (*(volatile int*)a.ctl) return;
+    __shared__ double sh[40];
+    const double pq = sum_partials(a.part, a.nblk, sh);
+    const double alpha = a.scal[0] / pq;
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    double r = 0.0;
+    if (e < a.ne) {
+        const size_t o = (size_t)e * n + i;
+        a.x[o] += alpha * a.p[o];
+        r = a.r[o] - alpha * a.q[o];
+        a.r[o] = r;
+    }
+    double s = block_sum(r * r, sh);
+    if (threadIdx.x == 0) a.part[2 * a.nblk + blockIdx.x] = s;
+}
+
+// partial r.z -> part[nblk]
+__global__ void cgx_rz_kernel(CGArgs a) {
+    if (*(volatile int*)a.ctl) return;
+    __shared__ double sh[40];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    double rz = 0.0;
+    if (e < a.ne) {
+        const size_t o = (size_t)e * n + i;
+        rz = a.r[o] * a.z[o];
+    }
+    double s = block_sum(rz, sh);
+    if (threadIdx.x == 0) a.part[a.nblk + blockIdx.x] = s;
+}
+
 // max |a - b| and max |a| over rows, plus a non-finite flag
 __global__ void diff_kernel(int nrow, const double* __restrict__ x, const double* __restrict__ y, double* part, int* flag) {
     __shared__ double s1[32], s2[32];
@@ -420,6 +479,29 @@ void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s) {
     const int tpb = cg_threads_per_block(a.n);
     cg_init_kernel<<<a.nblk, tpb, tpb * sizeof(double), s>>>(a);
     cg_init_scalars_kernel<<<1, 256, 0, s>>>(a, tol * tol, max_iters);
+}
+
+int cgx_start(const CGArgs& a, double tol, int max_iters, const MGPlan& mg, cudaStream_t s) {
+    const int tpb = cg_threads_per_block(a.n);
+    cgx_init_r_kernel<<<a.nblk, tpb, 0, s>>>(a);
+    const int l = mg_apply(mg, a.r, a.z, nullptr, s);
+    cgx_init_p_kernel<<<a.nblk, tpb, 0, s>>>(a);
+    cg_init_scalars_kernel<<<1, 256, 0, s>>>(a, tol * tol, max_iters);
+    return 3 + l;
+}
+
+int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s) {
+    const int tpb = cg_threads_per_block(a.n);
+    int launches = 0;
+    for (int k = 0; k < count; ++k) {
+        cg_spmv_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        cgx_update_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        launches += 2 + mg_apply(mg, a.r, a.z, a.ctl, s);
+        cgx_rz_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        cg_direction_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        launches += 2;
+    }
+    return launches;
 }
 
 void cg_iterations(const CGArgs& a, int count, cudaStream_t s) {
