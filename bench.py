@@ -8,13 +8,15 @@ ordinates), sigma_t = 1, scattering ratio 0.9, MMS angular source and MMS
 inflow.  16,384,000 angular unknowns per sweep.
 
 A step is one SMM outer iteration through the C ABI (smm_iterate with
-max_outer = 1): FP64 transport residual, FP32 correction sweep, FP64 moments
-and boundary correction, IP-SMM right-hand side, block-Jacobi PCG to 1e-12,
-successive-difference check.  value = angular unknowns swept per second of
+max_outer = 1): FP64 sweep with cached local inverses, FP64 moments and
+boundary correction, IP-SMM right-hand side, multigrid-preconditioned CG to
+1e-12, successive-difference check.  value = angular unknowns swept per second of
 whole steps (all ranks).  Inputs stay resident; L2 is flushed (256 MiB
-write) between timed steps.  Also reported: the plain FP64-sweep step, the
-time to a 1e-8 relative successive difference for both, the oracle on the
-host cores (cpu_baseline), and an end-to-end number with host buffers.
+write) between timed steps.  Also reported: the FP32-refined and on-the-fly
+LU variants of the step, the time to a 1e-8 relative successive difference
+for the plain method (FP64 on-the-fly LU sweep, block-Jacobi PCG) and the
+chosen one, the oracle on the host cores (cpu_baseline), and an end-to-end
+number with host buffers.
 """
 from __future__ import annotations
 
@@ -151,16 +153,29 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
-def sweep_flops_per_task(p: int, mode_residual: bool) -> float:
-    """Algorithmic flops of one local solve (element x ordinate), n = (p+1)^2:
-    assembly 5 n^2 (sigma M - Ox Gx - Oy Gy), face blocks 4 faces x (p+1)^2 x 4,
-    elimination 2/3 n^3, right-hand side elimination + back substitution 2 n^2,
-    source product 2 n^2 (source mode only)."""
+def lu_sweep_flops_per_task(p: int, mode_residual: bool) -> float:
+    """Algorithmic flops of one on-the-fly local solve (element x ordinate),
+    n = (p+1)^2: assembly 5 n^2 (sigma M - Ox Gx - Oy Gy), face blocks
+    4 faces x (p+1)^2 x 4, elimination 2/3 n^3, right-hand side elimination
+    and back substitution 2 n^2, source product 2 n^2 (source mode only)."""
     n = (p + 1) ** 2
     f = 5 * n * n + 16 * (p + 1) ** 2 + (2.0 / 3.0) * n ** 3 + 2 * n * n
     if not mode_residual:
         f += 2 * n * n
     return f
+
+
+def cached_sweep_flops_per_task(p: int) -> float:
+    """Cached-inverse task: x = A^{-1} b (2 n^2) plus two inflow face blocks (4 (p+1)^2 each)."""
+    n = (p + 1) ** 2
+    return 2 * n * n + 8 * (p + 1) ** 2
+
+
+def cached_sweep_bytes_per_task(p: int, word: int, angular: bool) -> float:
+    """HBM bytes of one cached-inverse task: the n x n inverse, the n outputs,
+    the n angular source values (M q_d, FP64) and two inflow traces."""
+    n = (p + 1) ** 2
+    return word * (n * n + n + 2 * (p + 1)) + (8 * n if angular else 0)
 
 
 def residual_flops_per_task(p: int) -> float:
@@ -169,11 +184,14 @@ def residual_flops_per_task(p: int) -> float:
     return 6 * n * n + 16 * (p + 1) ** 2
 
 
-def cg_bytes_per_iter(ne: int, n: int) -> float:
-    """HBM bytes of one PCG iteration: operator blocks (5 n^2 per element, FP64),
-    preconditioner blocks (n^2), and vector traffic (spmv: read p, write q;
-    update: read x,p,r,q, write x,r,z; direction: read z,p, write p)."""
-    return 8.0 * ne * (6 * n * n + 12 * n)
+def mg_cg_bytes_per_iter(ne: int, n: int) -> float:
+    """HBM bytes of one multigrid-preconditioned CG iteration on the element
+    blocks: operator spmv with FP64 blocks (5 n^2 x 8 B per element) and the
+    V-cycle's level-0 work on FP32 blocks -- first smoothing step (Pinv,
+    n^2), second pre-smoothing step (6 n^2), residual (5 n^2), two
+    post-smoothing steps (12 n^2) -- plus about 30 FP64 vector passes
+    (n words each); the vertex and aggregation levels are < 2 % and left out."""
+    return ne * (5 * n * n * 8 + 24 * n * n * 4 + 30 * n * 8)
 
 
 def run_ours(args) -> None:
@@ -199,16 +217,20 @@ def run_ours(args) -> None:
     t_in = time.time() - t_in
     stream = torch.cuda.Stream()
 
-    def create(precision):
+    def create(precision, solver=None, precond=None):
         opt = P.smm_default_options()
         opt.sweep_precision = precision
         opt.tol_cg = 1e-12
+        if solver is not None:
+            opt.sweep_solver = solver
+        if precond is not None:
+            opt.precond = precond
         t0 = time.time()
         h = P.smm_create(mesh.nodes, mesh.elem_nodes, WL["m"], WL["p"], WL["sn"], st, ss, q, inflow=inflow,
                          options=opt, stream=stream)
         return h, time.time() - t0
 
-    h, t_setup = create(P.SMM_SWEEP_FP32_REFINED)
+    h, t_setup = create(P.SMM_SWEEP_FP64)
     info = h.info()
     ne, n, nd = info.n_elem, info.n_dof_elem, info.n_ord
     unknowns = info.n_angular
@@ -261,19 +283,18 @@ def run_ours(args) -> None:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
     fp64_peak = 1.25                               # TFLOP/s nominal GB300 FP64
     tasks = ne * nd
-    sweep_tf = tasks * sweep_flops_per_task(WL["p"], True) / (ms_sweep * 1e-3) / 1e12
-    res_tf = tasks * residual_flops_per_task(WL["p"]) / (ms_res * 1e-3) / 1e12 if ms_res > 0 else 0.0
-    cg_gbs = cg_it * cg_bytes_per_iter(ne, n) / (ms_solve * 1e-3) / 1e9 if ms_solve > 0 else 0.0
+    sweep_tf = tasks * cached_sweep_flops_per_task(WL["p"]) / (ms_sweep * 1e-3) / 1e12
+    sweep_gbs = tasks * cached_sweep_bytes_per_task(WL["p"], 8, True) / (ms_sweep * 1e-3) / 1e9
+    cg_gbs = cg_it * mg_cg_bytes_per_iter(ne, n) / (ms_solve * 1e-3) / 1e9 if ms_solve > 0 else 0.0
     rooflines = {
-        "sweep_fp32": dict(bound="alu", achieved=sweep_tf, peak=fp32_peak, unit="TFLOP/s", frac=sweep_tf / fp32_peak,
-                           traffic=None, ms=ms_sweep, peak_note="derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"),
-        "residual_fp64": dict(bound="alu", achieved=res_tf, peak=fp64_peak, unit="TFLOP/s", frac=res_tf / fp64_peak,
-                              traffic=None, ms=ms_res, peak_note="nominal GB300 FP64 rate"),
-        "pcg_fp64": dict(bound="hbm", achieved=cg_gbs, peak=hbm, unit="GB/s", frac=cg_gbs / hbm, traffic=None,
-                         ms=ms_solve, peak_note=f"{hbm_src} copy bandwidth"),
+        "sweep_fp64_cached": dict(bound="alu", achieved=sweep_tf, peak=fp64_peak, unit="TFLOP/s",
+                                  frac=sweep_tf / fp64_peak, traffic=None, ms=ms_sweep,
+                                  hbm_gbs=sweep_gbs, hbm_frac=sweep_gbs / hbm,
+                                  peak_note="nominal GB300 FP64 rate (1.20 TFLOP/s measured by an FMA probe)"),
+        "mg_pcg_fp64": dict(bound="hbm", achieved=cg_gbs, peak=hbm, unit="GB/s", frac=cg_gbs / hbm, traffic=None,
+                            ms=ms_solve, peak_note=f"{hbm_src} copy bandwidth"),
     }
     dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
     roof = dict(rooflines[dom])
@@ -299,45 +320,58 @@ def run_ours(args) -> None:
 
     extra = {}
     if not args.quick:
-        # plain FP64-sweep step and the two solves to a 1e-8 relative difference
-        h64, _ = create(P.SMM_SWEEP_FP64)
-        phi64 = torch.zeros_like(phi)
-        with torch.cuda.stream(stream):
-            for _ in range(2):
-                step(h64, phi64)
-            torch.cuda.synchronize()
-            ev64 = []
-            for k in range(max(2, min(args.steps, 5))):
-                flush.fill_(2.0)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                s64 = step(h64, phi64)
-                b.record(stream)
-                b.synchronize()
-                ev64.append((a.elapsed_time(b), s64))
-        ms64 = statistics.mean(x for x, _ in ev64)
-        extra["plain_fp64_step"] = dict(value=unknowns / (ms64 * 1e-3), ms_per_step=ms64,
-                                        ms_sweep=statistics.mean(s["ms_sweep"] for _, s in ev64))
+        def time_steps(handle, nsteps=4):
+            x = torch.zeros_like(phi)
+            out = []
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    step(handle, x)
+                torch.cuda.synchronize()
+                for _ in range(nsteps):
+                    flush.fill_(2.0)
+                    a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    s_ = step(handle, x)
+                    b2.record(stream)
+                    b2.synchronize()
+                    out.append((a.elapsed_time(b2), s_))
+            msx = statistics.mean(t for t, _ in out)
+            return dict(value=unknowns / (msx * 1e-3), ms_per_step=msx,
+                        ms_sweep=statistics.mean(s_["ms_sweep"] for _, s_ in out),
+                        ms_residual=statistics.mean(s_["ms_residual"] for _, s_ in out),
+                        ms_solve=statistics.mean(s_["ms_solve"] for _, s_ in out))
 
-        def solve(precision):
-            hh, _ = create(precision)
+        h32, _ = create(P.SMM_SWEEP_FP32_REFINED)
+        extra["fp32_refined_step"] = time_steps(h32)
+        h32.destroy()
+        hlu, _ = create(P.SMM_SWEEP_FP64, solver=P.smm.SMM_SOLVER_LU)
+        extra["fp64_lu_step"] = time_steps(hlu)
+        hlu.destroy()
+
+        def solve(precision, solver=None, precond=None):
+            hh, _ = create(precision, solver, precond)
             x = torch.zeros_like(phi)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):
-                rc, s = P.smm_iterate(hh, x, 1e-8, 200, relative=True, raise_on_error=False)
+                rc, s_ = P.smm_iterate(hh, x, 1e-8, 200, relative=True, raise_on_error=False)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             hh.destroy()
-            return dt, s, rc, x
+            return dt, s_, rc, x
 
-        t64, s64, rc64, x64 = solve(P.SMM_SWEEP_FP64)
-        t32, s32, rc32, x32 = solve(P.SMM_SWEEP_FP32_REFINED)
-        diff = float((x64 - x32).abs().max() / x64.abs().max())
-        extra["time_to_1e-8"] = dict(plain_fp64_s=t64, plain_outer=s64["outer_iterations"], plain_status=rc64,
-                                     fp32_refined_s=t32, fp32_outer=s32["outer_iterations"], fp32_status=rc32,
-                                     rel_diff_fp32_vs_fp64=diff, guess="zero (learned guess not built)")
-        h64.destroy()
+        tp, sp, rcp, xp = solve(P.SMM_SWEEP_FP64, P.smm.SMM_SOLVER_LU, P.smm.SMM_PRECOND_BLOCK_JACOBI)
+        tc, sc, rcc, xc = solve(P.SMM_SWEEP_FP64)
+        t3, s3, rc3, x3 = solve(P.SMM_SWEEP_FP32_REFINED)
+        extra["time_to_1e-8"] = dict(
+            plain_s=tp, plain_outer=sp["outer_iterations"], plain_cg_total=sp["cg_total"], plain_status=rcp,
+            plain="FP64 sweep with on-the-fly LU, element-block-Jacobi PCG, zero guess",
+            chosen_s=tc, chosen_outer=sc["outer_iterations"], chosen_cg_total=sc["cg_total"], chosen_status=rcc,
+            chosen="FP64 sweep with cached local inverses, multigrid PCG, zero guess",
+            fp32_refined_s=t3, fp32_refined_outer=s3["outer_iterations"], fp32_refined_status=rc3,
+            rel_diff_chosen_vs_plain=float((xc - xp).abs().max() / xp.abs().max()),
+            rel_diff_fp32_vs_plain=float((x3 - xp).abs().max() / xp.abs().max()),
+            learned_guess="not built")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -347,17 +381,17 @@ def run_ours(args) -> None:
         line = {
             "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 sweep + f64 residual/moments/CG", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 (FP32 copies of the multigrid smoother blocks)", "data": "synthetic",
             "config": {"workload": WL_NAME, "n_elem": ne, "p": WL["p"], "geom_order": WL["m"], "sn": WL["sn"],
                        "n_ord": nd, "angular_unknowns": unknowns, "parallelism": f"replicas x{world}",
-                       "l2": "flushed between timed steps (256 MiB write)", "sweep_precision": "fp32-refined",
-                       "cg_tol": 1e-12},
+                       "l2": "flushed between timed steps (256 MiB write)", "sweep": "fp64, cached local inverses",
+                       "moment_solve": "multigrid-preconditioned flexible CG", "cg_tol": 1e-12},
             "roofline": roof, "roofline_all": rooflines, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "phases_ms": dict(residual=ms_res, sweep=ms_sweep, moments=mean("ms_moments"), rhs=mean("ms_rhs"),
                               solve=ms_solve, cg_iters=cg_it),
             "sweep_only": dict(value=unknowns / ((ms_sweep + ms_res) * 1e-3), unit="unknowns/s",
-                               note="residual + FP32 sweep kernels"),
+                               note="sweep kernel (plus the per-sweep source kernel)"),
             "setup_s": t_setup, "inputs_s": t_in,
         }
         line.update(extra)
@@ -420,7 +454,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FP64 and time-to-solution extras")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--nx", type=int, default=WL["nx"], help="mesh size override (profiling runs)")
     args = ap.parse_args()
+    WL["nx"] = args.nx
     if args.impl == "reference":
         run_reference(args)
     else:

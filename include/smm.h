@@ -65,6 +65,7 @@ enum { SMM_SOURCE_ISOTROPIC = 0, SMM_SOURCE_ANGULAR = 1 };
 enum { SMM_INFLOW_VACUUM = 0, SMM_INFLOW_NODAL = 1 };
 enum { SMM_SWEEP_FP64 = 0, SMM_SWEEP_FP32_REFINED = 1 };
 enum { SMM_PRECOND_BLOCK_JACOBI = 0, SMM_PRECOND_MULTIGRID = 1 };
+enum { SMM_SOLVER_LU = 0, SMM_SOLVER_CACHED_INVERSE = 1 };
 
 typedef struct {
     int32_t n_elem;             /* number of quadrilaterals */
@@ -89,6 +90,13 @@ typedef struct {
     double spin_timeout_s;      /* bound on every device-side wait (default 2 s) */
     int32_t precond;            /* moment-solve preconditioner: SMM_PRECOND_MULTIGRID
                                    (default) or SMM_PRECOND_BLOCK_JACOBI */
+    int32_t sweep_solver;       /* SMM_SOLVER_CACHED_INVERSE (default): every local
+                                   operator A_{K,d} is inverted once at create
+                                   (it does not change between sweeps) and a sweep
+                                   task is an n x n matrix-vector product;
+                                   needs n_elem * n_ord * n^2 words of device
+                                   memory.  SMM_SOLVER_LU: assemble and factor
+                                   every local system in registers per sweep. */
 } smm_options;
 
 typedef struct {

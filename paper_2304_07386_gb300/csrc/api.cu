@@ -55,6 +55,11 @@ struct smm_ctx {
     double *M = nullptr, *Gx = nullptr, *Gy = nullptr, *Fx = nullptr, *Fy = nullptr;
     float *M32 = nullptr, *Gx32 = nullptr, *Gy32 = nullptr, *Fx32 = nullptr, *Fy32 = nullptr;
     double *src = nullptr, *inflow = nullptr;
+    bool cached = false;
+    double* ainv64 = nullptr;      // cached local inverses (FP64 sweep)
+    float* ainv32 = nullptr;       // cached local inverses (FP32 correction sweep)
+    double* msrc = nullptr;        // [ne][n] M (sigma_s/(4pi) phi + q_iso) of the current sweep
+    double* mq = nullptr;          // [ne][nd][n] M q_d (angular sources)
     // state
     double* psi = nullptr;         // [ne][nd][n] FP64
     float* dpsi = nullptr;         // [ne][nd][n] FP32 correction (refined mode)
@@ -75,6 +80,11 @@ struct smm_ctx {
     int* nonfinite = nullptr;
     int cg_nblk = 1;
     smm::MGPlan mg;
+    double* rold = nullptr;        // flexible CG: previous residual
+    double* xcg = nullptr;         // CG iterate owned by the handle (captured in the iteration graph)
+    cudaStream_t cap = nullptr;    // private stream used once to capture the CG iteration graph
+    cudaGraphExec_t cg_graph = nullptr;
+    int graph_kernels = 0;
     // pinned host scratch
     double* h_scal = nullptr;
     int* h_int = nullptr;
@@ -90,6 +100,8 @@ struct smm_ctx {
         return (T*)ptr;
     }
     ~smm_ctx() {
+        if (cg_graph) cudaGraphExecDestroy(cg_graph);
+        if (cap) cudaStreamDestroy(cap);
         for (void* ptr : allocs) cudaFree(ptr);
         if (h_scal) cudaFreeHost(h_scal);
         if (h_int) cudaFreeHost(h_int);
@@ -127,6 +139,10 @@ std::vector<double> transpose_blocks(const std::vector<double>& a, int n) {
 
 }  // namespace
 
+namespace {
+smm::CGArgs cg_args(smm_handle h, double* x);
+}
+
 extern "C" {
 
 void smm_default_options(smm_options* opt) {
@@ -137,6 +153,7 @@ void smm_default_options(smm_options* opt) {
     opt->kappa_scale = 1.0;
     opt->spin_timeout_s = 2.0;
     opt->precond = SMM_PRECOND_MULTIGRID;
+    opt->sweep_solver = SMM_SOLVER_CACHED_INVERSE;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -168,7 +185,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     if (o.sweep_precision != SMM_SWEEP_FP64 && o.sweep_precision != SMM_SWEEP_FP32_REFINED)
         return fail(SMM_ERR_INVALID_ARG, "bad sweep precision");
     if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0) ||
-        (o.precond != SMM_PRECOND_BLOCK_JACOBI && o.precond != SMM_PRECOND_MULTIGRID))
+        (o.precond != SMM_PRECOND_BLOCK_JACOBI && o.precond != SMM_PRECOND_MULTIGRID) ||
+        (o.sweep_solver != SMM_SOLVER_LU && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE))
         return fail(SMM_ERR_INVALID_ARG, "bad options");
 
     smm::Input in;
@@ -280,8 +298,15 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         smm::MGPlan& P = h->mg;
         P.enabled = true;
         P.ne = s.ne; P.n = s.n; P.nu0 = 2; P.omega0 = H.omega0;
-        P.AdT = h->AdT; P.AoT = h->AoT; P.PinvT = h->PinvT; P.nbr = h->nbr;
-        P.x0 = h->alloc<double>(nphi); P.x0b = h->alloc<double>(nphi); P.res0 = h->alloc<double>(nphi);
+        {
+            float *ad32 = nullptr, *ao32 = nullptr, *pi32 = nullptr;
+            ok &= upload_f32(h, ad32, transpose_blocks(s.Adiag, s.n));
+            ok &= upload_f32(h, ao32, transpose_blocks(s.Aoff, s.n));
+            ok &= upload_f32(h, pi32, transpose_blocks(s.Pinv, s.n));
+            P.AdT = ad32; P.AoT = ao32; P.PinvT = pi32;
+        }
+        P.nbr = h->nbr;
+        P.x0 = h->alloc<float>(nphi); P.x0b = h->alloc<float>(nphi); P.res0 = h->alloc<float>(nphi);
         P.nvert = H.nvert;
         int *vid = nullptr, *vrp = nullptr, *vinc = nullptr;
         double* w4 = nullptr;
@@ -311,10 +336,60 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         P.cinv = cinv;
         ok &= P.x0 && P.x0b && P.res0 && cudaStreamSynchronize(h->stream) == cudaSuccess;
         if (!ok) return bail(SMM_ERR_OOM, "multigrid upload failed");
+        h->rold = h->alloc<double>(nphi);
+        h->xcg = h->alloc<double>(nphi);
+        if (!h->rold || !h->xcg) return bail(SMM_ERR_OOM, "device allocation failed");
+        // capture one flexible-CG iteration (spmv, update, V-cycle, dots, direction) as a graph
+        if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(SMM_ERR_CUDA, "cudaStreamCreate failed");
+        smm::CGArgs ca = cg_args(h, h->xcg);
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return bail(SMM_ERR_CUDA, "cudaStreamBeginCapture failed");
+        h->graph_kernels = smm::cgx_iterations(ca, 1, h->mg, h->cap);
+        if (cudaStreamEndCapture(h->cap, &g) != cudaSuccess || !g)
+            return bail(SMM_ERR_CUDA, "CG iteration capture failed");
+        const cudaError_t ie = cudaGraphInstantiate(&h->cg_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return bail(SMM_ERR_CUDA, "CG graph instantiation failed");
     }
-    const int bps = smm::sweep_blocks_per_sm(s.p, h->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE, h->fp32);
+    h->cached = o.sweep_solver == SMM_SOLVER_CACHED_INVERSE;
+    if (h->cached) {
+        const size_t ninv = (size_t)s.ne * s.nd * s.n * s.n;
+        h->msrc = h->alloc<double>(nphi);
+        if (!h->msrc) return bail(SMM_ERR_OOM, "device allocation failed");
+        if (h->src_angular) {
+            h->mq = h->alloc<double>(nang);
+            if (!h->mq) return bail(SMM_ERR_OOM, "device allocation failed");
+            smm::launch_mass_apply(s.ne, s.nd, s.n, h->M, h->src, h->mq, h->stream);
+        }
+        if (h->fp32) {
+            h->ainv32 = h->alloc<float>(ninv);
+            if (!h->ainv32) return bail(SMM_ERR_OOM, "no device memory for the cached local inverses (use SMM_SOLVER_LU)");
+            smm::SweepArgs<float> a{};
+            a.ne = s.ne; a.nd = s.nd; a.ntask = h->ntask; a.ox = h->ox; a.oy = h->oy; a.sigma_t = h->sigma_t;
+            a.M = h->M32; a.Gx = h->Gx32; a.Gy = h->Gy32; a.Fx = h->Fx32; a.Fy = h->Fy32; a.fdir = h->fdir;
+            smm::launch_invert<float>(s.p, a, h->ainv32, h->stream);
+        } else {
+            h->ainv64 = h->alloc<double>(ninv);
+            if (!h->ainv64) return bail(SMM_ERR_OOM, "no device memory for the cached local inverses (use SMM_SOLVER_LU)");
+            smm::SweepArgs<double> a{};
+            a.ne = s.ne; a.nd = s.nd; a.ntask = h->ntask; a.ox = h->ox; a.oy = h->oy; a.sigma_t = h->sigma_t;
+            a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy; a.fdir = h->fdir;
+            smm::launch_invert<double>(s.p, a, h->ainv64, h->stream);
+        }
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return bail(SMM_ERR_CUDA, "local inverse construction failed");
+    }
+    const int bps = smm::sweep_blocks_per_sm(s.p, h->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE, h->fp32, h->cached);
+    // cooperative launch: never more blocks than can be co-resident
     const long long want = ((long long)h->ntask + 7) / 8;
     h->sweep_grid = (int)std::max(1LL, std::min<long long>((long long)h->sms * bps, want));
+    {
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+        if (!coop) return bail(SMM_ERR_CUDA, "device does not support cooperative launches");
+    }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(SMM_ERR_CUDA, "setup upload failed");
     *out = h;
     return SMM_OK;
@@ -356,6 +431,11 @@ smm_status enqueue_sweep(smm_handle h, const double* phi) {
         a.phi = phi; a.src = h->src; a.src_angular = h->src_angular; a.inflow = h->has_inflow ? h->inflow : nullptr;
         a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr; a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket;
         a.err = h->err; a.timeout_ns = tmo;
+        if (h->cached) {
+            smm::launch_source(h->ne, h->n, h->M, h->sigma_s, phi, h->src_angular ? nullptr : h->src, h->msrc, h->stream);
+            h->launches += 1;
+            a.ainv = h->ainv64; a.msrc = h->msrc; a.mq = h->mq;
+        }
         SMM_CUDA(cudaEventRecord(h->ev[5], h->stream));
         smm::launch_sweep<double>(h->p, smm::SWEEP_SOURCE, a, h->sweep_grid, h->stream);
     } else {
@@ -375,6 +455,7 @@ smm_status enqueue_sweep(smm_handle h, const double* phi) {
         a.bface_id = h->bface_id; a.phi = nullptr; a.src = nullptr; a.src_angular = 0; a.inflow = nullptr; a.rhs = h->res;
         a.psi = h->dpsi; a.psi_acc = h->psi; a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket; a.err = h->err;
         a.timeout_ns = tmo;
+        a.ainv = h->cached ? h->ainv32 : nullptr;
         smm::launch_sweep<float>(h->p, smm::SWEEP_RESIDUAL, a, h->sweep_grid, h->stream);
     }
     h->launches += 1;
@@ -404,7 +485,8 @@ smm::CGArgs cg_args(smm_handle h, double* x) {
     smm::CGArgs a{};
     a.ne = h->ne; a.n = h->n; a.nrow = h->ne * h->n; a.nblk = h->cg_nblk;
     a.AdT = h->AdT; a.AoT = h->AoT; a.PinvT = h->PinvT; a.nbr = h->nbr;
-    a.x = x; a.r = h->r; a.z = h->z; a.p = h->pv; a.q = h->qv; a.b = h->rhs; a.part = h->part; a.scal = h->scal;
+    a.x = x; a.r = h->r; a.z = h->z; a.p = h->pv; a.q = h->qv; a.rold = h->rold; a.b = h->rhs; a.part = h->part;
+    a.scal = h->scal;
     a.ctl = h->ctl;
     return a;
 }
@@ -421,10 +503,12 @@ smm_status check_device_error(smm_handle h) {
 
 // CG from the guess in x; host reads the control word every `chunk` iterations
 smm_status run_cg(smm_handle h, double* x, int* iters) {
-    smm::CGArgs a = cg_args(h, x);
-    SMM_CUDA(cudaMemsetAsync(h->ctl, 0, 8 * sizeof(int), h->stream));
     const bool mg = h->mg.enabled;
+    const size_t nphi = (size_t)h->ne * h->n;
+    smm::CGArgs a = cg_args(h, mg ? h->xcg : x);
+    SMM_CUDA(cudaMemsetAsync(h->ctl, 0, 8 * sizeof(int), h->stream));
     if (mg) {
+        SMM_CUDA(cudaMemcpyAsync(h->xcg, x, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         h->launches += smm::cgx_start(a, h->opt.tol_cg, h->opt.max_cg, h->mg, h->stream);
     } else {
         smm::cg_start(a, h->opt.tol_cg, h->opt.max_cg, h->stream);
@@ -437,7 +521,8 @@ smm_status run_cg(smm_handle h, double* x, int* iters) {
         SMM_CUDA(cudaStreamSynchronize(h->stream));
         if (h->h_int[0]) break;
         if (mg) {
-            h->launches += smm::cgx_iterations(a, chunk, h->mg, h->stream);
+            for (int k = 0; k < chunk; ++k) SMM_CUDA(cudaGraphLaunch(h->cg_graph, h->stream));
+            h->launches += (long long)chunk * h->graph_kernels;
         } else {
             smm::cg_iterations(a, chunk, h->stream);
             h->launches += 3LL * chunk;
@@ -445,6 +530,7 @@ smm_status run_cg(smm_handle h, double* x, int* iters) {
         SMM_CUDA(cudaGetLastError());
         chunk = std::min(chunk * 2, mg ? 16 : 64);
     }
+    if (mg) SMM_CUDA(cudaMemcpyAsync(x, h->xcg, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     if (iters) *iters = h->h_int[1];
     if (h->h_int[3]) return fail(SMM_ERR_NONFINITE, "non-finite value in the moment solve");
     if (h->h_int[1] >= h->opt.max_cg) {

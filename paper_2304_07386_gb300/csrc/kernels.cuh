@@ -37,6 +37,9 @@ struct SweepArgs {
     int src_angular;
     const double* inflow;      // [nb][nd][p1] or nullptr (SOURCE)
     const float* rhs;          // [ne][nd][n] (RESIDUAL)
+    const T* ainv;             // cached local inverses [ne*nd][n][n] column-major, or nullptr (on-the-fly LU)
+    const double* msrc;        // cached mode, SOURCE: [ne][n] M (sigma_s/(4pi) phi + q_iso) of this sweep
+    const double* mq;          // cached mode, SOURCE, angular q: [ne][nd][n] M q_d, else nullptr
     T* psi;                    // [ne][nd][n] output, read by downwind tasks
     double* psi_acc;           // RESIDUAL: psi_acc += psi
     unsigned* done;            // [ne*nd] epoch flags
@@ -72,8 +75,16 @@ struct ResidualArgs {
 
 template <typename T>
 void launch_sweep(int p, int mode, const SweepArgs<T>& a, int grid, cudaStream_t s);
+// form every local inverse A_{K,d}^{-1} (column-major, type T) in ainv_out
+template <typename T>
+void launch_invert(int p, const SweepArgs<T>& a, T* ainv_out, cudaStream_t s);
+// out[e][d][i] = scale * sum_j M[e][i][j] in[e][d][j] (+ add[e][i] * scale2 if add) ; nd = 1 for per-element data
+void launch_mass_apply(int ne, int nd, int n, const double* M, const double* in, double* out, cudaStream_t s);
+// msrc[e][i] = sum_j M[e][i][j] (c_e phi[e][j] + q[e][j]); phi, q nullable
+void launch_source(int ne, int n, const double* M, const double* sigma_s, const double* phi, const double* q_iso,
+                   double* msrc, cudaStream_t s);
 void launch_residual(int p, const ResidualArgs& a, cudaStream_t s);
-int sweep_blocks_per_sm(int p, int mode, bool fp32);
+int sweep_blocks_per_sm(int p, int mode, bool fp32, bool cached);
 
 // moments and closures
 void launch_moments(int ne, int nd, int n, const double* w, const double* ox, const double* oy,
@@ -99,6 +110,7 @@ struct CGArgs {
     double* z;
     double* p;
     double* q;
+    double* rold;              // previous residual (flexible CG), may be nullptr on the block-Jacobi path
     const double* b;
     double* part;              // [3][nblk] partial sums
     double* scal;              // [8]: rz, pq, rr, bb, thresh2, -, -, -
@@ -118,9 +130,9 @@ struct MGPlan {
     bool enabled = false;
     int ne = 0, n = 0, nu0 = 2;
     double omega0 = 0.0;
-    const double* AdT = nullptr; const double* AoT = nullptr; const double* PinvT = nullptr;
+    const float* AdT = nullptr; const float* AoT = nullptr; const float* PinvT = nullptr;  // FP32 copies
     const int32_t* nbr = nullptr;
-    double* x0 = nullptr; double* x0b = nullptr; double* res0 = nullptr;   // [ne*n]
+    float* x0 = nullptr; float* x0b = nullptr; float* res0 = nullptr;      // [ne*n], level 0 works in FP32
     int nvert = 0;
     const int* vid = nullptr; const double* w4 = nullptr; const int* vrp = nullptr; const int* vinc = nullptr;
     int nlev = 0;                                 // levels 1..nlev (nlev = coarsest, dense)

@@ -406,38 +406,103 @@ __global__ void cgx_init_p_kernel(CGArgs a) {
     if (threadIdx.x == 0) a.part[blockIdx.x] = s;
 }
 
-// alpha = rz / pq ; x += alpha p ; r -= alpha q ; partial rr -> part[2 nblk]
+// q = A p (FP64, compile-time block size) ; partial p.q -> part[0]
+template <int N>
+__global__ void __launch_bounds__(256) cgx_spmv_kernel(CGArgs a) {
+    if (*(volatile int*)a.ctl) return;
+    __shared__ double sh[40];
+    const int epb = blockDim.x / N;
+    const int e = blockIdx.x * epb + threadIdx.x / N, i = threadIdx.x % N;
+    double pq = 0.0;
+    if (e < a.ne) {
+        const double qv = block_row_n<N, double, double, double>(a.AdT, a.AoT, a.nbr, a.p, e, i);
+        a.q[(size_t)e * N + i] = qv;
+        pq = qv * a.p[(size_t)e * N + i];
+    }
+    double s = block_sum(pq, sh);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = s;
+}
+
+// single-block reductions of the per-block partials (deterministic order).
+// stage 0: alpha = rz / pq -> scal[5].  stage 1: dz, rz_new, rr; beta = dz / rz
+// -> scal[6]; rz, rr updated; iteration count and convergence in ctl.
+__global__ void cgx_reduce_kernel(CGArgs a, int stage) {
+    if (*(volatile int*)a.ctl) return;
+    __shared__ double sh[40];
+    if (stage == 0) {
+        const double pq = sum_partials(a.part, a.nblk, sh);
+        if (threadIdx.x == 0) {
+            a.scal[1] = pq;
+            a.scal[5] = a.scal[0] / pq;
+        }
+        return;
+    }
+    const double dz = sum_partials(a.part, a.nblk, sh);
+    const double rz_new = sum_partials(a.part + a.nblk, a.nblk, sh);
+    const double rr = sum_partials(a.part + 2 * a.nblk, a.nblk, sh);
+    if (threadIdx.x == 0) {
+        a.scal[6] = dz / a.scal[0];
+        a.scal[0] = rz_new;
+        a.scal[2] = rr;
+        const int it = a.ctl[1] + 1;
+        a.ctl[1] = it;
+        const bool bad = !(isfinite(rz_new) && isfinite(rr) && isfinite(dz));
+        if (bad) a.ctl[3] = 1;
+        if (rr <= a.scal[4] || it >= a.ctl[2] || bad) a.ctl[0] = 1;
+    }
+}
+
+// x += alpha p ; r_old = r ; r -= alpha q ; partial rr -> part[2 nblk]
 __global__ void cgx_update_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
     __shared__ double sh[40];
-    const double pq = sum_partials(a.part, a.nblk, sh);
-    const double alpha = a.scal[0] / pq;
+    const double alpha = a.scal[5];
     const int n = a.n, epb = blockDim.x / n;
     const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
     double r = 0.0;
     if (e < a.ne) {
         const size_t o = (size_t)e * n + i;
         a.x[o] += alpha * a.p[o];
-        r = a.r[o] - alpha * a.q[o];
+        const double ro = a.r[o];
+        a.rold[o] = ro;
+        r = ro - alpha * a.q[o];
         a.r[o] = r;
     }
     double s = block_sum(r * r, sh);
     if (threadIdx.x == 0) a.part[2 * a.nblk + blockIdx.x] = s;
 }
 
-// partial r.z -> part[nblk]
+// partials r.z -> part[nblk] and (r - r_old).z -> part[0] (flexible CG)
 __global__ void cgx_rz_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
     __shared__ double sh[40];
     const int n = a.n, epb = blockDim.x / n;
     const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
-    double rz = 0.0;
+    double rz = 0.0, dz = 0.0;
     if (e < a.ne) {
         const size_t o = (size_t)e * n + i;
-        rz = a.r[o] * a.z[o];
+        const double z = a.z[o], r = a.r[o];
+        rz = r * z;
+        dz = (r - a.rold[o]) * z;
     }
     double s = block_sum(rz, sh);
-    if (threadIdx.x == 0) a.part[a.nblk + blockIdx.x] = s;
+    double t = block_sum(dz, sh);
+    if (threadIdx.x == 0) {
+        a.part[a.nblk + blockIdx.x] = s;
+        a.part[blockIdx.x] = t;
+    }
+}
+
+// p = z + beta p (flexible beta from scal[6])
+__global__ void cgx_direction_kernel(CGArgs a) {
+    if (*(volatile int*)a.ctl) return;
+    const double beta = a.scal[6];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    if (e < a.ne) {
+        const size_t o = (size_t)e * n + i;
+        a.p[o] = a.z[o] + beta * a.p[o];
+    }
 }
 
 // max |a - b| and max |a| over rows, plus a non-finite flag
@@ -494,12 +559,19 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
     const int tpb = cg_threads_per_block(a.n);
     int launches = 0;
     for (int k = 0; k < count; ++k) {
-        cg_spmv_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        switch (a.n) {
+            case 4: cgx_spmv_kernel<4><<<a.nblk, tpb, 0, s>>>(a); break;
+            case 9: cgx_spmv_kernel<9><<<a.nblk, tpb, 0, s>>>(a); break;
+            case 16: cgx_spmv_kernel<16><<<a.nblk, tpb, 0, s>>>(a); break;
+            default: cgx_spmv_kernel<25><<<a.nblk, tpb, 0, s>>>(a); break;
+        }
+        cgx_reduce_kernel<<<1, 256, 0, s>>>(a, 0);
         cgx_update_kernel<<<a.nblk, tpb, 0, s>>>(a);
-        launches += 2 + mg_apply(mg, a.r, a.z, a.ctl, s);
+        launches += 3 + mg_apply(mg, a.r, a.z, a.ctl, s);
         cgx_rz_kernel<<<a.nblk, tpb, 0, s>>>(a);
-        cg_direction_kernel<<<a.nblk, tpb, 0, s>>>(a);
-        launches += 2;
+        cgx_reduce_kernel<<<1, 256, 0, s>>>(a, 1);
+        cgx_direction_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        launches += 3;
     }
     return launches;
 }

@@ -10,11 +10,12 @@
 // symmetric part of A is positive definite: x^T A x = 1/2 int_dK |Omega.n| x^2
 // + sigma_t |x|^2), broadcasting pivot rows with warp shuffles.
 //
-// Scheduling: tasks are sorted by upwind level; warps take tickets from a
-// global counter, so every task a warp waits for was claimed earlier by a
-// running warp.  A task waits (bounded in time) on its upwind neighbours'
-// epoch flags, and publishes its own flag with release semantics after its
-// outputs are written.
+// Scheduling: tasks are sorted by upwind level and dealt round-robin to the
+// warps of a cooperative (co-resident) launch.  A task waits (bounded in
+// time) on its upwind neighbours' epoch flags, and publishes its own flag
+// with release semantics after its outputs are written.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace smm {
@@ -65,7 +66,7 @@ template <typename T> __device__ __forceinline__ T ldg_cg(const T* p) { return _
 
 }  // namespace
 
-template <typename T, int P, int MODE>
+template <typename T, int P, int MODE, bool INV>
 __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
     constexpr int P1 = P + 1, N = P1 * P1;
     constexpr unsigned FULL = 0xffffffffu;
@@ -74,16 +75,35 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
     const int ix = row % P1, iy = row / P1;
     const int nd = a.nd;
 
-    while (true) {
-        int t = 0;
-        if (lane == 0) t = (int)atomicAdd(a.ticket, 1u);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= a.ntask) break;
+    // static round-robin schedule: task t of the level-sorted list goes to warp
+    // t mod W, so each warp meets its tasks in level order; with every warp
+    // co-resident (cooperative launch) the task a warp waits for is owned by a
+    // running warp that reaches it after finishing only earlier-level tasks
+    const int W = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int t = gw; t < a.ntask; t += W) {
         const int task = a.tasks[t];
         const int e = task / nd, d = task - e * nd;
         const T ox = (T)a.ox[d], oy = (T)a.oy[d];
         const char4 dirs = *reinterpret_cast<const char4*>(a.fdir + ((size_t)e * nd + d) * 4);
         const int dir[4] = {dirs.x, dirs.y, dirs.z, dirs.w};
+
+        // ---- cached mode: everything that does not depend on upwind data is
+        //      loaded before the wait, so HBM latency overlaps the wavefront ----
+        T Ainv[INV ? N : 1];
+        T bpre = 0;
+        if (INV) {
+            const T* Ai = a.ainv + (size_t)task * N * N + row;
+#pragma unroll
+            for (int j = 0; j < N; ++j) Ainv[j] = Ai[(size_t)j * N];
+            if (MODE == SWEEP_SOURCE) {
+                double bs = a.msrc[(size_t)e * N + row];
+                if (a.mq) bs += a.mq[((size_t)e * nd + d) * N + row];
+                bpre = (T)bs;
+            } else {
+                bpre = (T)a.rhs[((size_t)e * nd + d) * N + row];
+            }
+        }
 
         // ---- wait for the upwind neighbours (lane f waits on face f) ----
         bool ok = true;
@@ -99,22 +119,28 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
             break;
         }
 
-        // ---- assemble row `row` of A and b ----
+        // ---- right-hand side b (and, without cached inverses, row `row` of A) ----
         const T sig = (T)a.sigma_t[e];
         const size_t mo = ((size_t)e * N + row) * N;
-        T A[N];
+        T A[INV ? 1 : N];
+        if (!INV) {
 #pragma unroll
-        for (int j = 0; j < N; ++j) A[j] = sig * a.M[mo + j] - ox * a.Gx[mo + j] - oy * a.Gy[mo + j];
+            for (int j = 0; j < N; ++j) A[j] = sig * a.M[mo + j] - ox * a.Gx[mo + j] - oy * a.Gy[mo + j];
+        }
         T b;
-        if (MODE == SWEEP_SOURCE) {
-            const double c = a.sigma_s[e] * (1.0 / (4.0 * 3.14159265358979323846));
-            const double* q = a.src_angular ? a.src + ((size_t)e * nd + d) * N : a.src + (size_t)e * N;
-            T sj = 0;
-            if (lane < N) sj = (T)((a.phi ? c * a.phi[(size_t)e * N + lane] : 0.0) + q[lane]);
-            T acc = 0;
+        if (INV) {
+            b = bpre;
+        } else if (MODE == SWEEP_SOURCE) {
+            {
+                const double c = a.sigma_s[e] * (1.0 / (4.0 * 3.14159265358979323846));
+                const double* q = a.src_angular ? a.src + ((size_t)e * nd + d) * N : a.src + (size_t)e * N;
+                T sj = 0;
+                if (lane < N) sj = (T)((a.phi ? c * a.phi[(size_t)e * N + lane] : 0.0) + q[lane]);
+                T acc = 0;
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc += a.M[mo + j] * __shfl_sync(FULL, sj, j);
-            b = acc;
+                for (int j = 0; j < N; ++j) acc += a.M[mo + j] * __shfl_sync(FULL, sj, j);
+                b = acc;
+            }
         } else {
             b = (T)a.rhs[((size_t)e * nd + d) * N + row];
         }
@@ -125,12 +151,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
             const bool on = (f == 0 && iy == 0) || (f == 1 && ix == P) || (f == 2 && iy == P) || (f == 3 && ix == 0);
             const int fa = (f == 0 || f == 2) ? ix : iy;  // position of this row on face f
             const size_t fo = (((size_t)e * 4 + f) * P1 + fa) * P1;
-            if (df > 0 && on) {
+            if (!INV && df > 0 && on) {
 #pragma unroll
                 for (int c = 0; c < P1; ++c) {
                     const T v = ox * a.Fx[fo + c] + oy * a.Fy[fo + c];
 #pragma unroll
-                    for (int j = 0; j < N; ++j)
+                    for (int j = 0; j < (INV ? 1 : N); ++j)
                         if (j == face_node<P>(f, c)) A[j] += v;
                 }
             } else if (df < 0 && on) {
@@ -156,29 +182,37 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
             }
         }
 
-        // ---- in-register LU without pivoting (row per lane) ----
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const T inv = T(1) / __shfl_sync(FULL, A[k], k);
-            const T l = A[k] * inv;
-            const bool below = lane > k;
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                if (j > k) {
-                    const T akj = __shfl_sync(FULL, A[j], k);
-                    if (below) A[j] -= l * akj;
-                }
-            }
-            const T bk = __shfl_sync(FULL, b, k);
-            if (below) b -= l * bk;
-        }
-        // back substitution
         T x = 0;
+        if (INV) {
+            // ---- cached inverse: x = A^{-1} b ----
 #pragma unroll
-        for (int k = N - 1; k >= 0; --k) {
-            const T xk = __shfl_sync(FULL, b / A[k], k);
-            if (lane == k) x = xk;
-            if (lane < k) b -= A[k] * xk;
+            for (int j = 0; j < (INV ? N : 1); ++j) x += Ainv[j] * __shfl_sync(FULL, b, j);
+        } else {
+            // ---- in-register LU without pivoting (row per lane) ----
+            T dinv = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const T inv = T(1) / __shfl_sync(FULL, A[k < (INV ? 1 : N) ? k : 0], k);
+                if (lane == k) dinv = inv;
+                const T l = A[k < (INV ? 1 : N) ? k : 0] * inv;
+                const bool below = lane > k;
+#pragma unroll
+                for (int j = 0; j < (INV ? 1 : N); ++j) {
+                    if (j > k) {
+                        const T akj = __shfl_sync(FULL, A[j], k);
+                        if (below) A[j] -= l * akj;
+                    }
+                }
+                const T bk = __shfl_sync(FULL, b, k);
+                if (below) b -= l * bk;
+            }
+            // back substitution with the stored pivot reciprocals
+#pragma unroll
+            for (int k = N - 1; k >= 0; --k) {
+                const T xk = __shfl_sync(FULL, b * dinv, k);
+                if (lane == k) x = xk;
+                if (lane < k) b -= A[k < (INV ? 1 : N) ? k : 0] * xk;
+            }
         }
 
         // ---- publish ----
@@ -187,7 +221,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
             a.psi[o] = x;
             if (MODE == SWEEP_RESIDUAL) a.psi_acc[o] += (double)x;
         }
-        __threadfence();
+        __threadfence();  // one warp-wide fence instruction orders every lane's stores
         __syncwarp();
         if (lane == 0) st_release(a.done + task, a.epoch);
     }
@@ -259,45 +293,187 @@ __global__ void __launch_bounds__(256) residual_kernel(ResidualArgs a) {
     }
 }
 
-template <typename T, int P, int MODE>
+// Local inverses A_{K,d}^{-1} by Gauss-Jordan elimination without pivoting,
+// one warp per task, row per lane; stored column-major per task.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) invert_kernel(SweepArgs<T> a, T* __restrict__ out) {
+    constexpr int P1 = P + 1, N = P1 * P1;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int row = lane < N ? lane : 0;
+    const int ix = row % P1, iy = row / P1;
+    const int nd = a.nd;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < a.ntask; task += warps) {
+        const int e = task / nd, d = task - e * nd;
+        const T ox = (T)a.ox[d], oy = (T)a.oy[d];
+        const char4 dirs = *reinterpret_cast<const char4*>(a.fdir + (size_t)task * 4);
+        const int dir[4] = {dirs.x, dirs.y, dirs.z, dirs.w};
+        const T sig = (T)a.sigma_t[e];
+        const size_t mo = ((size_t)e * N + row) * N;
+        T A[N], B[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            A[j] = sig * a.M[mo + j] - ox * a.Gx[mo + j] - oy * a.Gy[mo + j];
+            B[j] = (j == row) ? T(1) : T(0);
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const bool on = (f == 0 && iy == 0) || (f == 1 && ix == P) || (f == 2 && iy == P) || (f == 3 && ix == 0);
+            if (dir[f] > 0 && on) {
+                const int fa = (f == 0 || f == 2) ? ix : iy;
+                const size_t fo = (((size_t)e * 4 + f) * P1 + fa) * P1;
+#pragma unroll
+                for (int c = 0; c < P1; ++c) {
+                    const T v = ox * a.Fx[fo + c] + oy * a.Fy[fo + c];
+#pragma unroll
+                    for (int j = 0; j < N; ++j)
+                        if (j == face_node<P>(f, c)) A[j] += v;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const T l = A[k] / __shfl_sync(FULL, A[k], k);
+            const bool other = lane != k;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                if (j > k) {
+                    const T akj = __shfl_sync(FULL, A[j], k);
+                    if (other) A[j] -= l * akj;
+                }
+                const T bkj = __shfl_sync(FULL, B[j], k);
+                if (other) B[j] -= l * bkj;
+            }
+        }
+        // row `row` of A is now diagonal: divide
+        T dg = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j == row) dg = A[j];
+        const T inv = T(1) / dg;
+        if (lane < N) {
+            T* o = out + (size_t)task * N * N + lane;
+#pragma unroll
+            for (int j = 0; j < N; ++j) o[(size_t)j * N] = B[j] * inv;
+        }
+    }
+}
+
+// out[t][i] = sum_j M[e][i][j] in[t][j], t = e*nd + d
+__global__ void mass_apply_kernel(int ne, int nd, int n, const double* __restrict__ M, const double* __restrict__ in,
+                                  double* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)ne * nd * n) return;
+    const long long task = t / n;
+    const int i = (int)(t - task * n);
+    const int e = (int)(task / nd);
+    const double* m = M + ((size_t)e * n + i) * n;
+    const double* v = in + (size_t)task * n;
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += m[j] * v[j];
+    out[t] = s;
+}
+
+// msrc[e][i] = sum_j M[e][i][j] (sigma_s/(4 pi) phi[e][j] + q[e][j])
+__global__ void source_kernel(int ne, int n, const double* __restrict__ M, const double* __restrict__ sigma_s,
+                              const double* __restrict__ phi, const double* __restrict__ q, double* __restrict__ msrc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ne * n) return;
+    const int e = t / n, i = t - e * n;
+    const double c = sigma_s[e] * (1.0 / (4.0 * 3.14159265358979323846));
+    const double* m = M + ((size_t)e * n + i) * n;
+    double s = 0.0;
+    for (int j = 0; j < n; ++j)
+        s += m[j] * ((phi ? c * phi[(size_t)e * n + j] : 0.0) + (q ? q[(size_t)e * n + j] : 0.0));
+    msrc[t] = s;
+}
+
+template <typename T, int P, int MODE, bool INV>
 static void launch_one(const SweepArgs<T>& a, int grid, cudaStream_t s) {
-    sweep_kernel<T, P, MODE><<<grid, 256, 0, s>>>(a);
+    SweepArgs<T> arg = a;
+    void* params[] = {&arg};
+    cudaLaunchCooperativeKernel((const void*)sweep_kernel<T, P, MODE, INV>, dim3(grid), dim3(256), params, 0, s);
+}
+
+template <typename T, int P>
+static void launch_p(int mode, const SweepArgs<T>& a, int grid, cudaStream_t s) {
+    const bool inv = a.ainv != nullptr;
+    if (mode == SWEEP_SOURCE) {
+        if (inv) launch_one<T, P, SWEEP_SOURCE, true>(a, grid, s);
+        else launch_one<T, P, SWEEP_SOURCE, false>(a, grid, s);
+    } else {
+        if (inv) launch_one<T, P, SWEEP_RESIDUAL, true>(a, grid, s);
+        else launch_one<T, P, SWEEP_RESIDUAL, false>(a, grid, s);
+    }
 }
 
 template <typename T>
 void launch_sweep(int p, int mode, const SweepArgs<T>& a, int grid, cudaStream_t s) {
-#define SMM_SWEEP_CASE(PP)                                                              \
-    case PP:                                                                            \
-        if (mode == SWEEP_SOURCE) launch_one<T, PP, SWEEP_SOURCE>(a, grid, s);          \
-        else launch_one<T, PP, SWEEP_RESIDUAL>(a, grid, s);                             \
-        break;
-    switch (p) { SMM_SWEEP_CASE(1) SMM_SWEEP_CASE(2) SMM_SWEEP_CASE(3) SMM_SWEEP_CASE(4) default: break; }
-#undef SMM_SWEEP_CASE
+    switch (p) {
+        case 1: launch_p<T, 1>(mode, a, grid, s); break;
+        case 2: launch_p<T, 2>(mode, a, grid, s); break;
+        case 3: launch_p<T, 3>(mode, a, grid, s); break;
+        case 4: launch_p<T, 4>(mode, a, grid, s); break;
+        default: break;
+    }
 }
 
 template void launch_sweep<double>(int, int, const SweepArgs<double>&, int, cudaStream_t);
 template void launch_sweep<float>(int, int, const SweepArgs<float>&, int, cudaStream_t);
 
-int sweep_blocks_per_sm(int p, int mode, bool fp32) {
+static int residual_grid(long long ntask) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = (int)std::min<long long>((ntask + 7) / 8, (long long)sms * 8);
+    return grid < 1 ? 1 : grid;
+}
+
+template <typename T>
+void launch_invert(int p, const SweepArgs<T>& a, T* out, cudaStream_t s) {
+    const int grid = residual_grid(a.ntask);
+    switch (p) {
+        case 1: invert_kernel<T, 1><<<grid, 256, 0, s>>>(a, out); break;
+        case 2: invert_kernel<T, 2><<<grid, 256, 0, s>>>(a, out); break;
+        case 3: invert_kernel<T, 3><<<grid, 256, 0, s>>>(a, out); break;
+        case 4: invert_kernel<T, 4><<<grid, 256, 0, s>>>(a, out); break;
+        default: break;
+    }
+}
+
+template void launch_invert<double>(int, const SweepArgs<double>&, double*, cudaStream_t);
+template void launch_invert<float>(int, const SweepArgs<float>&, float*, cudaStream_t);
+
+void launch_mass_apply(int ne, int nd, int n, const double* M, const double* in, double* out, cudaStream_t s) {
+    const long long tot = (long long)ne * nd * n;
+    mass_apply_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ne, nd, n, M, in, out);
+}
+
+void launch_source(int ne, int n, const double* M, const double* sigma_s, const double* phi, const double* q_iso,
+                   double* msrc, cudaStream_t s) {
+    const int tot = ne * n;
+    source_kernel<<<(tot + 255) / 256, 256, 0, s>>>(ne, n, M, sigma_s, phi, q_iso, msrc);
+}
+
+int sweep_blocks_per_sm(int p, int mode, bool fp32, bool cached) {
     int nb = 0;
-#define SMM_OCC(T, PP, MM) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<T, PP, MM>, 256, 0)
-    switch (p * 4 + mode * 2 + (fp32 ? 1 : 0)) {
-        case 4: SMM_OCC(double, 1, 0); break;
-        case 5: SMM_OCC(float, 1, 0); break;
-        case 6: SMM_OCC(double, 1, 1); break;
-        case 7: SMM_OCC(float, 1, 1); break;
-        case 8: SMM_OCC(double, 2, 0); break;
-        case 9: SMM_OCC(float, 2, 0); break;
-        case 10: SMM_OCC(double, 2, 1); break;
-        case 11: SMM_OCC(float, 2, 1); break;
-        case 12: SMM_OCC(double, 3, 0); break;
-        case 13: SMM_OCC(float, 3, 0); break;
-        case 14: SMM_OCC(double, 3, 1); break;
-        case 15: SMM_OCC(float, 3, 1); break;
-        case 16: SMM_OCC(double, 4, 0); break;
-        case 17: SMM_OCC(float, 4, 0); break;
-        case 18: SMM_OCC(double, 4, 1); break;
-        case 19: SMM_OCC(float, 4, 1); break;
+#define SMM_OCC(T, PP)                                                                                           \
+    do {                                                                                                         \
+        if (mode == SWEEP_SOURCE)                                                                                \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                                       \
+                &nb, cached ? (const void*)sweep_kernel<T, PP, SWEEP_SOURCE, true>                               \
+                            : (const void*)sweep_kernel<T, PP, SWEEP_SOURCE, false>, 256, 0);                    \
+        else                                                                                                     \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                                       \
+                &nb, cached ? (const void*)sweep_kernel<T, PP, SWEEP_RESIDUAL, true>                             \
+                            : (const void*)sweep_kernel<T, PP, SWEEP_RESIDUAL, false>, 256, 0);                  \
+    } while (0)
+    switch (p) {
+        case 1: if (fp32) SMM_OCC(float, 1); else SMM_OCC(double, 1); break;
+        case 2: if (fp32) SMM_OCC(float, 2); else SMM_OCC(double, 2); break;
+        case 3: if (fp32) SMM_OCC(float, 3); else SMM_OCC(double, 3); break;
+        case 4: if (fp32) SMM_OCC(float, 4); else SMM_OCC(double, 4); break;
         default: break;
     }
 #undef SMM_OCC
@@ -305,12 +481,7 @@ int sweep_blocks_per_sm(int p, int mode, bool fp32) {
 }
 
 void launch_residual(int p, const ResidualArgs& a, cudaStream_t s) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long warps_needed = a.ntask;
-    int grid = (int)std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8);
-    if (grid < 1) grid = 1;
+    const int grid = residual_grid(a.ntask);
     switch (p) {
         case 1: residual_kernel<1><<<grid, 256, 0, s>>>(a); break;
         case 2: residual_kernel<2><<<grid, 256, 0, s>>>(a); break;

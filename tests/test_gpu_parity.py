@@ -67,13 +67,14 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("solver", [0, 1], ids=["lu", "cached_inverse"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[:5])))
-def test_sweep_and_moments_fp64(case):
+def test_sweep_and_moments_fp64(case, solver):
     import paper_2304_07386_gb300 as P
     from oracle import closures
     nx, ny, m, p, sn, seed, kind = case
     prob = problem(nx, ny, m=m, p=p, sn=sn, seed=seed, kind=kind, c=0.6)
-    h = make_gpu(prob)
+    h = make_gpu(prob, sweep_solver=solver)
     disc, op, q, inflow = make_oracle(prob)
     phi = W.mms_phi(prob["pos"][:, :, 0], prob["pos"][:, :, 1])
     P.smm_sweep(h, dev(phi))
@@ -125,12 +126,13 @@ def test_iterate_fp64_converged_flux(case):
     assert abs(st["outer_iterations"] - k_o) <= 1
 
 
-def test_fp32_refined_reaches_fp64_fixed_point():
+@pytest.mark.parametrize("solver", [0, 1], ids=["lu", "cached_inverse"])
+def test_fp32_refined_reaches_fp64_fixed_point(solver):
     """FP32 local solves corrected from an FP64 residual: the converged flux
     matches the FP64 oracle to the 1e-10 relative stopping tolerance (x10)."""
     import paper_2304_07386_gb300 as P
     prob = problem(4, 4, m=2, p=2, sn=8, seed=5, kind="mms", c=0.6)
-    h = make_gpu(prob, precision=1, tol_cg=1e-14)
+    h = make_gpu(prob, precision=1, tol_cg=1e-14, sweep_solver=solver)
     disc, op, q, inflow = make_oracle(prob)
     phi_o, _, _ = op.iterate(tol=1e-13)
     phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
