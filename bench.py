@@ -217,8 +217,9 @@ def run_ours(args) -> None:
     t_in = time.time() - t_in
     stream = torch.cuda.Stream()
 
-    def create(precision, solver=None, precond=None):
+    def create(precision, solver=None, precond=None, anderson=0):
         opt = P.smm_default_options()
+        opt.anderson_depth = anderson
         opt.sweep_precision = precision
         opt.tol_cg = 1e-12
         if solver is not None:
@@ -348,8 +349,8 @@ def run_ours(args) -> None:
         extra["fp64_lu_step"] = time_steps(hlu)
         hlu.destroy()
 
-        def solve(precision, solver=None, precond=None):
-            hh, _ = create(precision, solver, precond)
+        def solve(precision, solver=None, precond=None, anderson=0):
+            hh, _ = create(precision, solver, precond, anderson)
             x = torch.zeros_like(phi)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -362,6 +363,7 @@ def run_ours(args) -> None:
 
         tp, sp, rcp, xp = solve(P.SMM_SWEEP_FP64, P.smm.SMM_SOLVER_LU, P.smm.SMM_PRECOND_BLOCK_JACOBI)
         tc, sc, rcc, xc = solve(P.SMM_SWEEP_FP64)
+        ta, sa, rca, xa = solve(P.SMM_SWEEP_FP64, anderson=2)
         t3, s3, rc3, x3 = solve(P.SMM_SWEEP_FP32_REFINED)
         extra["time_to_1e-8"] = dict(
             plain_s=tp, plain_outer=sp["outer_iterations"], plain_cg_total=sp["cg_total"], plain_status=rcp,
@@ -369,6 +371,8 @@ def run_ours(args) -> None:
             chosen_s=tc, chosen_outer=sc["outer_iterations"], chosen_cg_total=sc["cg_total"], chosen_status=rcc,
             chosen="FP64 sweep with cached local inverses, multigrid PCG, zero guess",
             fp32_refined_s=t3, fp32_refined_outer=s3["outer_iterations"], fp32_refined_status=rc3,
+            anderson2_s=ta, anderson2_outer=sa["outer_iterations"], anderson2_cg_total=sa["cg_total"],
+            anderson2_status=rca, rel_diff_anderson2_vs_plain=float((xa - xp).abs().max() / xp.abs().max()),
             rel_diff_chosen_vs_plain=float((xc - xp).abs().max() / xp.abs().max()),
             rel_diff_fp32_vs_plain=float((x3 - xp).abs().max() / xp.abs().max()),
             learned_guess="not built")

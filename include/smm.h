@@ -97,6 +97,11 @@ typedef struct {
                                    needs n_elem * n_ord * n^2 words of device
                                    memory.  SMM_SOLVER_LU: assemble and factor
                                    every local system in registers per sweep. */
+    int32_t anderson_depth;     /* smm_iterate: 0 (default) plain fixed point
+                                   varphi^{k+1} = G(varphi^k); 1..5 Anderson
+                                   acceleration of that depth (paper Sec. "The
+                                   Moment Method Algorithm"; depth 2 in its
+                                   crooked-pipe runs), with moment-sized history */
 } smm_options;
 
 typedef struct {

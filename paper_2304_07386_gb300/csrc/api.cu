@@ -60,6 +60,9 @@ struct smm_ctx {
     float* ainv32 = nullptr;       // cached local inverses (FP32 correction sweep)
     double* msrc = nullptr;        // [ne][n] M (sigma_s/(4pi) phi + q_iso) of the current sweep
     double* mq = nullptr;          // [ne][nd][n] M q_d (angular sources)
+    // Anderson acceleration: rings of G(x_k) and f_k = G(x_k) - x_k (depth + 1 slots)
+    std::vector<double*> aaG, aaF;
+    double *aa_part = nullptr, *aa_out = nullptr;
     // state
     double* psi = nullptr;         // [ne][nd][n] FP64
     float* dpsi = nullptr;         // [ne][nd][n] FP32 correction (refined mode)
@@ -154,6 +157,7 @@ void smm_default_options(smm_options* opt) {
     opt->spin_timeout_s = 2.0;
     opt->precond = SMM_PRECOND_MULTIGRID;
     opt->sweep_solver = SMM_SOLVER_CACHED_INVERSE;
+    opt->anderson_depth = 0;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -186,7 +190,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         return fail(SMM_ERR_INVALID_ARG, "bad sweep precision");
     if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0) ||
         (o.precond != SMM_PRECOND_BLOCK_JACOBI && o.precond != SMM_PRECOND_MULTIGRID) ||
-        (o.sweep_solver != SMM_SOLVER_LU && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE))
+        (o.sweep_solver != SMM_SOLVER_LU && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) || o.anderson_depth < 0 ||
+        o.anderson_depth > 5)
         return fail(SMM_ERR_INVALID_ARG, "bad options");
 
     smm::Input in;
@@ -277,7 +282,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         return bail(SMM_ERR_CUDA, "cudaMemsetAsync failed");
     if (h->fp32 && cudaMemsetAsync(h->dpsi, 0, nang * sizeof(float), h->stream) != cudaSuccess)
         return bail(SMM_ERR_CUDA, "cudaMemsetAsync failed");
-    if (cudaMallocHost(&h->h_scal, 8 * sizeof(double)) != cudaSuccess ||
+    if (cudaMallocHost(&h->h_scal, 32 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&h->h_int, 8 * sizeof(int)) != cudaSuccess)
         return bail(SMM_ERR_OOM, "pinned allocation failed");
     for (auto& e : h->ev)
@@ -352,6 +357,16 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         const cudaError_t ie = cudaGraphInstantiate(&h->cg_graph, g, 0);
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) return bail(SMM_ERR_CUDA, "CG graph instantiation failed");
+    }
+    if (o.anderson_depth > 0) {
+        for (int k = 0; k <= o.anderson_depth; ++k) {
+            h->aaG.push_back(h->alloc<double>(nphi));
+            h->aaF.push_back(h->alloc<double>(nphi));
+            if (!h->aaG.back() || !h->aaF.back()) return bail(SMM_ERR_OOM, "device allocation failed");
+        }
+        h->aa_part = h->alloc<double>(21 * 256);
+        h->aa_out = h->alloc<double>(32);
+        if (!h->aa_part || !h->aa_out) return bail(SMM_ERR_OOM, "device allocation failed");
     }
     h->cached = o.sweep_solver == SMM_SOLVER_CACHED_INVERSE;
     if (h->cached) {
@@ -542,6 +557,73 @@ smm_status run_cg(smm_handle h, double* x, int* iters) {
     return SMM_OK;
 }
 
+// Anderson acceleration of x = G(x) (depth m): with f_j = G(x_j) - x_j,
+// x_{k+1} = G(x_k) - sum_j gamma_j (G_{k-j} - G_{k-j-1}) where gamma minimizes
+// || f_k - sum_j gamma_j (f_{k-j} - f_{k-j-1}) ||_2 (normal equations from a
+// Gram matrix reduced on the device).  phi holds G(x_k) on entry and
+// h->phi_prev holds x_k; phi receives x_{k+1}.
+smm_status anderson_step(smm_handle h, int k, double* phi) {
+    const int m = h->opt.anderson_depth;
+    const int slots = m + 1;
+    const size_t nphi = (size_t)h->ne * h->n;
+    const int cur = (k - 1) % slots;
+    SMM_CUDA(cudaMemcpyAsync(h->aaG[cur], phi, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    smm::launch_axpby((int)nphi, 1.0, phi, -1.0, h->phi_prev, h->aaF[cur], h->stream);
+    h->launches += 1;
+    const int mk = std::min(m, k - 1);
+    if (mk == 0) return SMM_OK;  // x_{k+1} = G(x_k), already in phi
+    smm::VecSet vs{};
+    vs.nv = mk + 1;
+    for (int j = 0; j <= mk; ++j) vs.v[j] = h->aaF[(cur - j + slots) % slots];
+    smm::launch_gram((int)nphi, vs, h->aa_part, h->aa_out, h->stream);
+    h->launches += 2;
+    SMM_CUDA(cudaMemcpyAsync(h->h_scal, h->aa_out, 21 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    // R[a][b] = f_a . f_b for the vectors of vs (packed upper triangle, row-major)
+    double R[6][6];
+    {
+        int t = 0;
+        for (int x = 0; x < 6; ++x)
+            for (int y = x; y < 6; ++y) {
+                R[x][y] = R[y][x] = h->h_scal[t];
+                ++t;
+            }
+    }
+    // dF_i = vs[i] - vs[i+1]:  H_ij = dF_i . dF_j,  g_i = dF_i . f_k
+    double H[5][6];
+    for (int i = 0; i < mk; ++i) {
+        for (int j = 0; j < mk; ++j) H[i][j] = R[i][j] - R[i][j + 1] - R[i + 1][j] + R[i + 1][j + 1];
+        H[i][mk] = R[i][0] - R[i + 1][0];
+    }
+    double tr = 0.0;
+    for (int i = 0; i < mk; ++i) tr += H[i][i];
+    for (int i = 0; i < mk; ++i) H[i][i] += 1e-13 * tr;
+    for (int c = 0; c < mk; ++c) {  // Gaussian elimination with partial pivoting
+        int piv = c;
+        for (int r = c + 1; r < mk; ++r)
+            if (std::fabs(H[r][c]) > std::fabs(H[piv][c])) piv = r;
+        if (piv != c)
+            for (int j = 0; j <= mk; ++j) std::swap(H[c][j], H[piv][j]);
+        if (H[c][c] == 0.0) return SMM_OK;  // degenerate history: keep the plain update
+        for (int r = c + 1; r < mk; ++r) {
+            const double l = H[r][c] / H[c][c];
+            for (int j = c; j <= mk; ++j) H[r][j] -= l * H[c][j];
+        }
+    }
+    smm::MixArgs mx{};
+    mx.m = mk;
+    for (int i = mk - 1; i >= 0; --i) {
+        double s = H[i][mk];
+        for (int j = i + 1; j < mk; ++j) s -= H[i][j] * mx.gamma[j];
+        mx.gamma[i] = s / H[i][i];
+    }
+    for (int j = 0; j <= mk; ++j) mx.G[j] = h->aaG[(cur - j + slots) % slots];
+    smm::launch_anderson_mix((int)nphi, mx, phi, h->stream);
+    h->launches += 1;
+    SMM_CUDA(cudaGetLastError());
+    return SMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -659,6 +741,10 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
         if (crit < tol) {
             result = SMM_OK;
             break;
+        }
+        if (h->opt.anderson_depth > 0) {
+            smm_status as = anderson_step(h, k, phi_dev);
+            if (as != SMM_OK) return as;
         }
     }
     if (local.cg_min == (1 << 30)) local.cg_min = 0;

@@ -148,6 +148,23 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
 void cg_iterations(const CGArgs& a, int count, cudaStream_t s);
 int cg_threads_per_block(int n);
 
+// Anderson acceleration helpers: Gram matrix of up to 6 vectors (21 pairwise
+// dots, deterministic two-stage reduction) and the mixing update
+struct VecSet {
+    const double* v[6];
+    int nv;
+};
+void launch_gram(int nrow, const VecSet& vs, double* part, double* out, cudaStream_t s);
+// x = G[0] - sum_j gamma[j] (G[j] - G[j+1]), j = 0..m-1 (G[0] newest)
+struct MixArgs {
+    const double* G[6];
+    double gamma[5];
+    int m;
+};
+void launch_anderson_mix(int nrow, const MixArgs& a, double* x, cudaStream_t s);
+// out = alpha x + beta y
+void launch_axpby(int nrow, double alpha, const double* x, double beta, const double* y, double* out, cudaStream_t s);
+
 // message returned by smm_last_error() for the calling thread
 void set_last_error(const char* msg);
 

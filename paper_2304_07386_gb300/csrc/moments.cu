@@ -585,6 +585,67 @@ void cg_iterations(const CGArgs& a, int count, cudaStream_t s) {
     }
 }
 
+namespace {
+
+constexpr int kGramBlocks = 256;
+
+__global__ void gram_kernel(int nrow, VecSet vs, double* part) {
+    __shared__ double sh[40];
+    double acc[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) acc[k] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrow; i += gridDim.x * blockDim.x) {
+        double x[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) x[a] = a < vs.nv ? vs.v[a][i] : 0.0;
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = a; b < 6; ++b) acc[k++] += x[a] * x[b];
+    }
+    for (int k = 0; k < 21; ++k) {
+        const double s = block_sum(acc[k], sh);
+        if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void gram_final_kernel(int nblk, const double* part, double* out) {
+    const int k = threadIdx.x;
+    if (k >= 21) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[k * nblk + b];
+    out[k] = s;
+}
+
+__global__ void axpby_kernel(int nrow, double alpha, const double* x, double beta, const double* y, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nrow) out[i] = alpha * x[i] + beta * y[i];
+}
+
+__global__ void anderson_mix_kernel(int nrow, MixArgs a, double* x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrow) return;
+    double v = a.G[0][i];
+    for (int j = 0; j < a.m; ++j) v -= a.gamma[j] * (a.G[j][i] - a.G[j + 1][i]);
+    x[i] = v;
+}
+
+}  // namespace
+
+void launch_gram(int nrow, const VecSet& vs, double* part, double* out, cudaStream_t s) {
+    gram_kernel<<<kGramBlocks, 256, 0, s>>>(nrow, vs, part);
+    gram_final_kernel<<<1, 32, 0, s>>>(kGramBlocks, part, out);
+}
+
+void launch_axpby(int nrow, double alpha, const double* x, double beta, const double* y, double* out, cudaStream_t s) {
+    axpby_kernel<<<(nrow + 255) / 256, 256, 0, s>>>(nrow, alpha, x, beta, y, out);
+}
+
+void launch_anderson_mix(int nrow, const MixArgs& a, double* x, cudaStream_t s) {
+    anderson_mix_kernel<<<(nrow + 255) / 256, 256, 0, s>>>(nrow, a, x);
+}
+
 void launch_diff(int nrow, const double* a, const double* b, double* part, double* out, int* flag, cudaStream_t s) {
     const int nblk = 256;
     diff_kernel<<<nblk, 256, 0, s>>>(nrow, a, b, part, flag);

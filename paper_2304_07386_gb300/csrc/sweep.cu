@@ -159,26 +159,34 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
                     for (int j = 0; j < (INV ? 1 : N); ++j)
                         if (j == face_node<P>(f, c)) A[j] += v;
                 }
-            } else if (df < 0 && on) {
-                const int nb = a.nbr[e * 4 + f];
-                T acc = 0;
-                if (nb >= 0) {
-                    const int f2 = a.nbr_face[e * 4 + f];
-                    const int flip = a.nbr_flip[e * 4 + f];
-                    const T* up = a.psi + ((size_t)nb * nd + d) * N;
-#pragma unroll
-                    for (int c = 0; c < P1; ++c) {
-                        const int c2 = flip ? P - c : c;
+            } else if (df < 0) {
+                // inflow face (warp-uniform branch): the (p+1)^2 products
+                // coef[a][c] * psi_up[c] are spread over lanes (a, c), summed
+                // over c within each group of p+1 lanes, and handed to the lane
+                // of face node a -- every lane does useful FP64 work
+                const int la = lane / P1, lc = lane - (lane / P1) * P1;
+                T term = 0;
+                if (lane < P1 * P1) {
+                    const size_t fo2 = ((size_t)e * 4 + f) * P1 * P1 + la * P1 + lc;
+                    const T coef = ox * a.Fx[fo2] + oy * a.Fy[fo2];
+                    const int nb = a.nbr[e * 4 + f];
+                    T upv = 0;
+                    if (nb >= 0) {
+                        const int f2 = a.nbr_face[e * 4 + f];
+                        const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
                         const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
-                        acc += (ox * a.Fx[fo + c] + oy * a.Fy[fo + c]) * ldg_cg(up + node);
+                        upv = ldg_cg(a.psi + ((size_t)nb * nd + d) * N + node);
+                    } else if (MODE == SWEEP_SOURCE && a.inflow) {
+                        const int bi = a.bface_id[e * 4 + f];
+                        upv = (T)a.inflow[((size_t)bi * nd + d) * P1 + lc];
                     }
-                } else if (MODE == SWEEP_SOURCE && a.inflow) {
-                    const int bi = a.bface_id[e * 4 + f];
-                    const double* up = a.inflow + ((size_t)bi * nd + d) * P1;
-#pragma unroll
-                    for (int c = 0; c < P1; ++c) acc += (ox * a.Fx[fo + c] + oy * a.Fy[fo + c]) * (T)up[c];
+                    term = coef * upv;
                 }
-                b -= acc;
+                T sum = term;
+#pragma unroll
+                for (int k = 1; k < P1; ++k) sum += __shfl_down_sync(FULL, term, k);
+                const T v = __shfl_sync(FULL, sum, fa * P1);
+                if (on) b -= v;
             }
         }
 

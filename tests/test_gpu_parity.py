@@ -194,3 +194,22 @@ def test_multigrid_cuts_cg_iterations():
         sols.append(phi.cpu().numpy())
     assert its[1] * 8 < its[0], its
     assert rel(sols[1], sols[0]) < 1e-9
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_anderson_reaches_oracle_fixed_point(depth):
+    """Anderson-accelerated SMM (the paper's outer solver) converges to the same
+    fixed point as the oracle's plain iteration, in no more outer steps than
+    the plain GPU iteration."""
+    import paper_2304_07386_gb300 as P
+    prob = problem(6, 5, m=2, p=2, sn=4, seed=2, kind="mms", c=0.95)
+    disc, op, q, inflow = make_oracle(prob)
+    phi_o, _, _ = op.iterate(tol=1e-13)
+    its = []
+    for d in (0, depth):
+        h = make_gpu(prob, tol_cg=1e-14, anderson_depth=d)
+        phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+        rc, st = P.smm_iterate(h, phi, 1e-11, 200)
+        assert rel(phi.cpu().numpy(), phi_o.ravel()) < 1e-9
+        its.append(st["outer_iterations"])
+    assert its[1] <= its[0], its
