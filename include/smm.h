@@ -195,6 +195,36 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
 
 smm_status smm_destroy(smm_handle h);
 
+/* ---- Batched problems ----
+ * Many problems of uneven mesh size, order p and S_N order swept in one
+ * cooperative launch: their level-sorted task lists are merged level by level
+ * and every task dispatches on its problem's p.  Problems keep their own
+ * state; only the sweep is shared.  The launch shape (threads per block,
+ * resident blocks per SM) is autotuned on live sweeps at creation. */
+typedef struct smm_batch_ctx* smm_batch;
+
+/* handles: n problems created with the same sweep_precision, sweep_solver,
+ * device and stream; they must outlive the batch.  Creation runs a few
+ * sweeps with varphi = 0 to tune the launch (the handles' sweep state
+ * changes as by smm_sweep).  Errors: INVALID_ARG, OOM, CUDA, DEVICE_TIMEOUT. */
+smm_status smm_batch_create(int32_t n, const smm_handle* handles, smm_batch* out);
+
+/* Chosen launch shape and the tuned time of one batched sweep (ms). */
+smm_status smm_batch_schedule(smm_batch b, int32_t* grid, int32_t* block, double* tuned_ms, int64_t* n_tasks);
+
+/* One sweep of every problem (as smm_sweep for each) in one launch.
+ * phi_dev: host array of n device pointers (entries NULL for varphi = 0). */
+smm_status smm_batch_sweep(smm_batch b, const double* const* phi_dev);
+
+/* smm_iterate for every problem, sharing the batched sweep: each outer step
+ * runs one batched sweep, then each unconverged problem's moment solve.
+ * phi_dev: host array of n device pointers (guesses in, iterates out);
+ * stats: NULL or n entries.  Errors as smm_iterate. */
+smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t max_outer, double* const* phi_dev,
+                             smm_stats* stats);
+
+smm_status smm_batch_destroy(smm_batch b);
+
 /* Allocation-free block-Jacobi preconditioned CG.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- code that runs under another framework's allocator, inside

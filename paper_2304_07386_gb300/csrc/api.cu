@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/smm.h"
@@ -60,6 +61,7 @@ struct smm_ctx {
     float* ainv32 = nullptr;       // cached local inverses (FP32 correction sweep)
     double* msrc = nullptr;        // [ne][n] M (sigma_s/(4pi) phi + q_iso) of the current sweep
     double* mq = nullptr;          // [ne][nd][n] M q_d (angular sources)
+    std::vector<int32_t> tasks_host, level_start;  // level-sorted task list (for batching)
     // Anderson acceleration: rings of G(x_k) and f_k = G(x_k) - x_k (depth + 1 slots)
     std::vector<double*> aaG, aaF;
     double *aa_part = nullptr, *aa_out = nullptr;
@@ -209,6 +211,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->stream = (cudaStream_t)cuda_stream;
     h->ne = s.ne; h->m = s.m; h->p = s.p; h->p1 = s.p1; h->n = s.n; h->nd = s.nd; h->nb = s.nb; h->nfq = s.nfq;
     h->nlevels = s.nlevels; h->ntask = (int)s.tasks.size();
+    h->tasks_host = s.tasks;
+    h->level_start = s.level_start;
     h->src_angular = source_kind == SMM_SOURCE_ANGULAR;
     h->has_inflow = !s.inflow.empty();
     h->fp32 = o.sweep_precision == SMM_SWEEP_FP32_REFINED;
@@ -430,29 +434,31 @@ smm_status smm_destroy(smm_handle h) {
 namespace {
 
 // enqueue one sweep + moments + beta; no host synchronization
-smm_status enqueue_sweep(smm_handle h, const double* phi) {
-    SMM_CUDA(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream));
+// Bump the flag epoch, launch the per-sweep pre-kernels (FP64: source
+// products for cached inverses; FP32-refined: the FP64 transport residual) and
+// fill the sweep arguments.  Shared by the single and the batched sweep.
+template <typename T>
+smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) {
     h->epoch += 1;
     if (h->epoch == 0) {  // wrap: reset flags
         SMM_CUDA(cudaMemsetAsync(h->done, 0, (size_t)h->ne * h->nd * sizeof(unsigned), h->stream));
         h->epoch = 1;
     }
-    const long long tmo = (long long)(h->opt.spin_timeout_s * 1e9);
-    if (!h->fp32) {
-        smm::SweepArgs<double> a{};
-        a.ne = h->ne; a.nd = h->nd; a.ntask = h->ntask; a.tasks = h->tasks; a.ox = h->ox; a.oy = h->oy;
-        a.sigma_t = h->sigma_t; a.sigma_s = h->sigma_s; a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy;
-        a.fdir = h->fdir; a.nbr = h->nbr; a.nbr_face = h->nbr_face; a.nbr_flip = h->nbr_flip; a.bface_id = h->bface_id;
+    a = smm::SweepArgs<T>{};
+    a.ne = h->ne; a.nd = h->nd; a.ntask = h->ntask; a.p = h->p; a.tasks = h->tasks; a.ox = h->ox; a.oy = h->oy;
+    a.sigma_t = h->sigma_t; a.sigma_s = h->sigma_s;
+    a.fdir = h->fdir; a.nbr = h->nbr; a.nbr_face = h->nbr_face; a.nbr_flip = h->nbr_flip; a.bface_id = h->bface_id;
+    a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket; a.err = h->err;
+    a.timeout_ns = (long long)(h->opt.spin_timeout_s * 1e9);
+    if constexpr (std::is_same<T, double>::value) {
+        a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy;
         a.phi = phi; a.src = h->src; a.src_angular = h->src_angular; a.inflow = h->has_inflow ? h->inflow : nullptr;
-        a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr; a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket;
-        a.err = h->err; a.timeout_ns = tmo;
+        a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr;
         if (h->cached) {
             smm::launch_source(h->ne, h->n, h->M, h->sigma_s, phi, h->src_angular ? nullptr : h->src, h->msrc, h->stream);
             h->launches += 1;
             a.ainv = h->ainv64; a.msrc = h->msrc; a.mq = h->mq;
         }
-        SMM_CUDA(cudaEventRecord(h->ev[5], h->stream));
-        smm::launch_sweep<double>(h->p, smm::SWEEP_SOURCE, a, h->sweep_grid, h->stream);
     } else {
         smm::ResidualArgs r{};
         r.ne = h->ne; r.nd = h->nd; r.ntask = h->ntask; r.ox = h->ox; r.oy = h->oy; r.sigma_t = h->sigma_t;
@@ -462,15 +468,28 @@ smm_status enqueue_sweep(smm_handle h, const double* phi) {
         r.rhs = h->res;
         smm::launch_residual(h->p, r, h->stream);
         h->launches += 1;
-        SMM_CUDA(cudaEventRecord(h->ev[5], h->stream));
-        smm::SweepArgs<float> a{};
-        a.ne = h->ne; a.nd = h->nd; a.ntask = h->ntask; a.tasks = h->tasks; a.ox = h->ox; a.oy = h->oy;
-        a.sigma_t = h->sigma_t; a.sigma_s = h->sigma_s; a.M = h->M32; a.Gx = h->Gx32; a.Gy = h->Gy32; a.Fx = h->Fx32;
-        a.Fy = h->Fy32; a.fdir = h->fdir; a.nbr = h->nbr; a.nbr_face = h->nbr_face; a.nbr_flip = h->nbr_flip;
-        a.bface_id = h->bface_id; a.phi = nullptr; a.src = nullptr; a.src_angular = 0; a.inflow = nullptr; a.rhs = h->res;
-        a.psi = h->dpsi; a.psi_acc = h->psi; a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket; a.err = h->err;
-        a.timeout_ns = tmo;
+        a.M = h->M32; a.Gx = h->Gx32; a.Gy = h->Gy32; a.Fx = h->Fx32; a.Fy = h->Fy32;
+        a.phi = nullptr; a.src = nullptr; a.src_angular = 0; a.inflow = nullptr; a.rhs = h->res;
+        a.psi = h->dpsi; a.psi_acc = h->psi;
         a.ainv = h->cached ? h->ainv32 : nullptr;
+    }
+    SMM_CUDA(cudaGetLastError());
+    return SMM_OK;
+}
+
+// enqueue one sweep (pre-kernels + the wavefront kernel); no host synchronization
+smm_status enqueue_sweep(smm_handle h, const double* phi) {
+    if (!h->fp32) {
+        smm::SweepArgs<double> a;
+        smm_status st = prepare_sweep(h, phi, a);
+        if (st != SMM_OK) return st;
+        SMM_CUDA(cudaEventRecord(h->ev[5], h->stream));
+        smm::launch_sweep<double>(h->p, smm::SWEEP_SOURCE, a, h->sweep_grid, h->stream);
+    } else {
+        smm::SweepArgs<float> a;
+        smm_status st = prepare_sweep(h, phi, a);
+        if (st != SMM_OK) return st;
+        SMM_CUDA(cudaEventRecord(h->ev[5], h->stream));
         smm::launch_sweep<float>(h->p, smm::SWEEP_RESIDUAL, a, h->sweep_grid, h->stream);
     }
     h->launches += 1;
@@ -750,6 +769,225 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
     if (local.cg_min == (1 << 30)) local.cg_min = 0;
     if (stats) *stats = local;
     if (result != SMM_OK) return fail(result, "outer iteration limit reached");
+    return SMM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched sweeps: many problems (uneven mesh size, order p and S_N) in one
+// cooperative launch over a merged, level-sorted (problem, task) list.
+// ---------------------------------------------------------------------------
+struct smm_batch_ctx {
+    std::vector<smm_handle> hs;
+    bool fp32 = false, cached = false;
+    cudaStream_t stream = nullptr;
+    int ntask = 0, grid = 1, block = 256, sms = 1;
+    double tuned_ms = 0.0;
+    int2* tasks = nullptr;
+    void* args_dev = nullptr;
+    void* args_host = nullptr;  // pinned
+    size_t args_bytes = 0;
+    int* err = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ~smm_batch_ctx() {
+        if (tasks) cudaFree(tasks);
+        if (args_dev) cudaFree(args_dev);
+        if (args_host) cudaFreeHost(args_host);
+        if (err) cudaFree(err);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+template <typename T>
+smm_status batch_enqueue(smm_batch b, const double* const* phis) {
+    auto* host = static_cast<smm::SweepArgs<T>*>(b->args_host);
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        smm_status st = prepare_sweep<T>(b->hs[i], phis ? phis[i] : nullptr, host[i]);
+        if (st != SMM_OK) return st;
+        host[i].err = b->err;
+    }
+    SMM_CUDA(cudaMemcpyAsync(b->args_dev, b->args_host, b->args_bytes, cudaMemcpyHostToDevice, b->stream));
+    SMM_CUDA(smm::launch_batch_sweep<T>(b->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE, b->cached,
+                                         static_cast<const smm::SweepArgs<T>*>(b->args_dev), b->tasks, b->ntask,
+                                         b->grid, b->block, b->stream));
+    b->hs[0]->launches += 1;
+    return SMM_OK;
+}
+
+smm_status batch_sweep_all(smm_batch b, const double* const* phis) {
+    smm_status st = b->fp32 ? batch_enqueue<float>(b, phis) : batch_enqueue<double>(b, phis);
+    if (st != SMM_OK) return st;
+    for (smm_handle h : b->hs) {
+        st = enqueue_moments(h);
+        if (st != SMM_OK) return st;
+    }
+    int e = 0;
+    SMM_CUDA(cudaMemcpyAsync(&e, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    SMM_CUDA(cudaStreamSynchronize(b->stream));
+    if (e == smm::DEV_TIMEOUT) {
+        cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
+        return fail(SMM_ERR_DEVICE_TIMEOUT, "a batched sweep dependency wait exceeded spin_timeout_s");
+    }
+    return SMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+smm_status smm_batch_create(int32_t n, const smm_handle* handles, smm_batch* out) {
+    if (!out || n < 1 || !handles) return fail(SMM_ERR_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!handles[i]) return fail(SMM_ERR_INVALID_ARG, "NULL handle in batch");
+    smm_handle h0 = handles[0];
+    for (int i = 1; i < n; ++i) {
+        if (handles[i]->fp32 != h0->fp32 || handles[i]->cached != h0->cached)
+            return fail(SMM_ERR_INVALID_ARG, "batched problems must share sweep_precision and sweep_solver");
+        if (handles[i]->stream != h0->stream || handles[i]->device != h0->device)
+            return fail(SMM_ERR_INVALID_ARG, "batched problems must share the device and the stream");
+    }
+    auto* b = new smm_batch_ctx();
+    auto bail = [&](smm_status st, const std::string& msg) { delete b; return fail(st, msg); };
+    b->hs.assign(handles, handles + n);
+    b->fp32 = h0->fp32;
+    b->cached = h0->cached;
+    b->stream = h0->stream;
+    b->sms = h0->sms;
+    // merged task list: level by level, problem by problem
+    int maxlev = 0;
+    for (smm_handle h : b->hs) maxlev = std::max(maxlev, h->nlevels);
+    std::vector<int2> merged;
+    for (int l = 0; l < maxlev; ++l)
+        for (int i = 0; i < n; ++i) {
+            smm_handle h = b->hs[i];
+            if (l >= h->nlevels) continue;
+            for (int t = h->level_start[l]; t < h->level_start[l + 1]; ++t) merged.push_back(make_int2(i, h->tasks_host[t]));
+        }
+    b->ntask = (int)merged.size();
+    b->args_bytes = (size_t)n * (b->fp32 ? sizeof(smm::SweepArgs<float>) : sizeof(smm::SweepArgs<double>));
+    if (cudaMalloc(&b->tasks, merged.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&b->args_dev, b->args_bytes) != cudaSuccess || cudaMallocHost(&b->args_host, b->args_bytes) != cudaSuccess ||
+        cudaMalloc(&b->err, sizeof(int)) != cudaSuccess)
+        return bail(SMM_ERR_OOM, "batch allocation failed");
+    if (cudaMemcpyAsync(b->tasks, merged.data(), merged.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess)
+        return bail(SMM_ERR_CUDA, "batch upload failed");
+    for (auto& e : b->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bail(SMM_ERR_CUDA, "cudaEventCreate failed");
+    // autotune the launch shape (threads per block x resident fraction) on live sweeps
+    const int mode = b->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE;
+    double best = 1e300;
+    int best_grid = 1, best_block = 256;
+    for (int block : {256, 128}) {
+        const int bps = smm::batch_blocks_per_sm(mode, b->fp32, b->cached, block);
+        if (bps < 1) continue;
+        for (int frac : {1, 2}) {
+            const long long want = ((long long)b->ntask * 32 + block - 1) / block;
+            b->grid = (int)std::max(1LL, std::min<long long>((long long)b->sms * bps / frac, want));
+            b->block = block;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                if (cudaEventRecord(b->ev[0], b->stream) != cudaSuccess) return bail(SMM_ERR_CUDA, "event");
+                smm_status st = b->fp32 ? batch_enqueue<float>(b, nullptr) : batch_enqueue<double>(b, nullptr);
+                if (st != SMM_OK) { delete b; return st; }
+                if (cudaEventRecord(b->ev[1], b->stream) != cudaSuccess || cudaEventSynchronize(b->ev[1]) != cudaSuccess)
+                    return bail(SMM_ERR_CUDA, "batched sweep failed during tuning");
+                cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+            }
+            int e = 0;
+            cudaMemcpy(&e, b->err, sizeof(int), cudaMemcpyDeviceToHost);
+            if (e != 0) return bail(SMM_ERR_DEVICE_TIMEOUT, "batched sweep wait expired during tuning");
+            if (ms < best) { best = ms; best_grid = b->grid; best_block = block; }
+        }
+    }
+    b->grid = best_grid;
+    b->block = best_block;
+    b->tuned_ms = best;
+    *out = b;
+    return SMM_OK;
+}
+
+smm_status smm_batch_schedule(smm_batch b, int32_t* grid, int32_t* block, double* tuned_ms, int64_t* n_tasks) {
+    if (!b) return fail(SMM_ERR_INVALID_ARG, "NULL batch");
+    if (grid) *grid = b->grid;
+    if (block) *block = b->block;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    if (n_tasks) *n_tasks = b->ntask;
+    return SMM_OK;
+}
+
+smm_status smm_batch_sweep(smm_batch b, const double* const* phi_dev) {
+    if (!b) return fail(SMM_ERR_INVALID_ARG, "NULL batch");
+    return batch_sweep_all(b, phi_dev);
+}
+
+smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t max_outer, double* const* phi_dev,
+                             smm_stats* stats) {
+    if (!b || !phi_dev || !(tol > 0) || max_outer < 1) return fail(SMM_ERR_INVALID_ARG, "bad argument");
+    const int n = (int)b->hs.size();
+    std::vector<smm_stats> st(n);
+    std::vector<char> done(n, 0);
+    for (auto& s : st) s.cg_min = 1 << 30;
+    std::vector<const double*> phis(phi_dev, phi_dev + n);
+    int remaining = n;
+    for (int k = 1; k <= max_outer && remaining > 0; ++k) {
+        for (int i = 0; i < n; ++i) {
+            smm_handle h = b->hs[i];
+            SMM_CUDA(cudaMemcpyAsync(h->phi_prev, phi_dev[i], (size_t)h->ne * h->n * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, b->stream));
+        }
+        smm_status s = batch_sweep_all(b, phis.data());
+        if (s != SMM_OK) return s;
+        for (int i = 0; i < n; ++i) {
+            if (done[i]) continue;
+            smm_handle h = b->hs[i];
+            s = enqueue_rhs(h);
+            if (s != SMM_OK) return s;
+            int it = 0;
+            s = run_cg(h, phi_dev[i], &it);
+            if (s != SMM_OK && s != SMM_ERR_NOT_CONVERGED) return s;
+            const size_t nphi = (size_t)h->ne * h->n;
+            SMM_CUDA(cudaMemsetAsync(h->nonfinite, 0, sizeof(int), h->stream));
+            smm::launch_diff((int)nphi, phi_dev[i], h->phi_prev, h->dpart, h->dout, h->nonfinite, h->stream);
+            SMM_CUDA(cudaMemcpyAsync(h->h_scal, h->dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            SMM_CUDA(cudaMemcpyAsync(h->h_int + 4, h->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            SMM_CUDA(cudaStreamSynchronize(h->stream));
+            if (h->h_int[4]) return fail(SMM_ERR_NONFINITE, "non-finite scalar flux in a batched problem");
+            smm_stats& q = st[i];
+            q.outer_iterations = k;
+            q.cg_total += it;
+            q.cg_min = std::min(q.cg_min, it);
+            q.cg_max = std::max(q.cg_max, it);
+            q.last_diff = h->h_scal[0];
+            q.last_rel_diff = h->h_scal[1] > 0 ? h->h_scal[0] / h->h_scal[1] : h->h_scal[0];
+            const double crit = relative ? q.last_rel_diff : q.last_diff;
+            if (crit < tol) {
+                done[i] = 1;
+                --remaining;
+            } else if (h->opt.anderson_depth > 0) {
+                s = anderson_step(h, k, phi_dev[i]);
+                if (s != SMM_OK) return s;
+            }
+        }
+    }
+    for (auto& s : st)
+        if (s.cg_min == (1 << 30)) s.cg_min = 0;
+    if (stats)
+        for (int i = 0; i < n; ++i) stats[i] = st[i];
+    if (remaining > 0) return fail(SMM_ERR_NOT_CONVERGED, "outer iteration limit reached for some batched problems");
+    return SMM_OK;
+}
+
+smm_status smm_batch_destroy(smm_batch b) {
+    if (!b) return SMM_OK;
+    cudaStreamSynchronize(b->stream);
+    delete b;
     return SMM_OK;
 }
 

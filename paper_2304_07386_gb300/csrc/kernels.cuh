@@ -16,7 +16,7 @@ enum : int { SWEEP_SOURCE = 0, SWEEP_RESIDUAL = 1 };
 
 template <typename T>
 struct SweepArgs {
-    int ne, nd, ntask;
+    int ne, nd, ntask, p;
     const int32_t* tasks;      // e*nd + d, sorted by upwind level
     const double* ox;          // [nd]
     const double* oy;          // [nd]
@@ -75,6 +75,11 @@ struct ResidualArgs {
 
 template <typename T>
 void launch_sweep(int p, int mode, const SweepArgs<T>& a, int grid, cudaStream_t s);
+// many problems in one cooperative launch; tasks: (problem, task) pairs sorted by level
+template <typename T>
+cudaError_t launch_batch_sweep(int mode, bool cached, const SweepArgs<T>* args, const int2* tasks, int ntask, int grid,
+                               int block, cudaStream_t s);
+int batch_blocks_per_sm(int mode, bool fp32, bool cached, int block);
 // form every local inverse A_{K,d}^{-1} (column-major, type T) in ainv_out
 template <typename T>
 void launch_invert(int p, const SweepArgs<T>& a, T* ainv_out, cudaStream_t s);

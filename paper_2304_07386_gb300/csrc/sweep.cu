@@ -66,23 +66,17 @@ template <typename T> __device__ __forceinline__ T ldg_cg(const T* p) { return _
 
 }  // namespace
 
+// One (element, ordinate) task of one problem, executed by a whole warp.
+// Returns false if a dependency wait gave up.
 template <typename T, int P, int MODE, bool INV>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
+__device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task) {
     constexpr int P1 = P + 1, N = P1 * P1;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int row = lane < N ? lane : 0;  // lanes >= N shadow row 0 (results discarded)
     const int ix = row % P1, iy = row / P1;
     const int nd = a.nd;
-
-    // static round-robin schedule: task t of the level-sorted list goes to warp
-    // t mod W, so each warp meets its tasks in level order; with every warp
-    // co-resident (cooperative launch) the task a warp waits for is owned by a
-    // running warp that reaches it after finishing only earlier-level tasks
-    const int W = (gridDim.x * blockDim.x) >> 5;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (int t = gw; t < a.ntask; t += W) {
-        const int task = a.tasks[t];
+    {
         const int e = task / nd, d = task - e * nd;
         const T ox = (T)a.ox[d], oy = (T)a.oy[d];
         const char4 dirs = *reinterpret_cast<const char4*>(a.fdir + ((size_t)e * nd + d) * 4);
@@ -116,7 +110,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
         ok = __all_sync(FULL, ok);
         if (!ok) {
             if (lane == 0) atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
-            break;
+            return false;
         }
 
         // ---- right-hand side b (and, without cached inverses, row `row` of A) ----
@@ -232,6 +226,42 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
         __threadfence();  // one warp-wide fence instruction orders every lane's stores
         __syncwarp();
         if (lane == 0) st_release(a.done + task, a.epoch);
+    }
+    return true;
+}
+
+// Static round-robin schedule: task t of the level-sorted list goes to warp
+// t mod W, so each warp meets its tasks in level order; with every warp
+// co-resident (cooperative launch) the task a warp waits for is owned by a
+// running warp that reaches it after finishing only earlier-level tasks.
+template <typename T, int P, int MODE, bool INV>
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
+    const int W = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int t = gw; t < a.ntask; t += W)
+        if (!sweep_task<T, P, MODE, INV>(a, a.tasks[t])) break;
+}
+
+// Many problems in one launch: the merged list holds (problem, task) pairs
+// sorted by each problem's own upwind level, and each task dispatches on its
+// problem's order p.  The same schedule argument holds: a task's upwind tasks
+// belong to its problem, sit at lower levels and so earlier in the list.
+template <typename T, int MODE, bool INV>
+__global__ void __launch_bounds__(256) batch_sweep_kernel(const SweepArgs<T>* __restrict__ args,
+                                                          const int2* __restrict__ tasks, int ntask) {
+    const int W = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int t = gw; t < ntask; t += W) {
+        const int2 it = tasks[t];
+        const SweepArgs<T>& a = args[it.x];
+        bool ok = true;
+        switch (a.p) {
+            case 1: ok = sweep_task<T, 1, MODE, INV>(a, it.y); break;
+            case 2: ok = sweep_task<T, 2, MODE, INV>(a, it.y); break;
+            case 3: ok = sweep_task<T, 3, MODE, INV>(a, it.y); break;
+            default: ok = sweep_task<T, 4, MODE, INV>(a, it.y); break;
+        }
+        if (!ok) break;
     }
 }
 
@@ -436,6 +466,51 @@ static int residual_grid(long long ntask) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int grid = (int)std::min<long long>((ntask + 7) / 8, (long long)sms * 8);
     return grid < 1 ? 1 : grid;
+}
+
+template <typename T, int MODE, bool INV>
+static cudaError_t launch_batch_one(const SweepArgs<T>* args, const int2* tasks, int ntask, int grid, int block,
+                                   cudaStream_t s) {
+    void* params[] = {(void*)&args, (void*)&tasks, (void*)&ntask};
+    return cudaLaunchCooperativeKernel((const void*)batch_sweep_kernel<T, MODE, INV>, dim3(grid), dim3(block),
+                                       params, 0, s);
+}
+
+template <typename T>
+cudaError_t launch_batch_sweep(int mode, bool cached, const SweepArgs<T>* args, const int2* tasks, int ntask, int grid,
+                               int block, cudaStream_t s) {
+    if (mode == SWEEP_SOURCE)
+        return cached ? launch_batch_one<T, SWEEP_SOURCE, true>(args, tasks, ntask, grid, block, s)
+                      : launch_batch_one<T, SWEEP_SOURCE, false>(args, tasks, ntask, grid, block, s);
+    return cached ? launch_batch_one<T, SWEEP_RESIDUAL, true>(args, tasks, ntask, grid, block, s)
+                  : launch_batch_one<T, SWEEP_RESIDUAL, false>(args, tasks, ntask, grid, block, s);
+}
+
+template cudaError_t launch_batch_sweep<double>(int, bool, const SweepArgs<double>*, const int2*, int, int, int,
+                                                cudaStream_t);
+template cudaError_t launch_batch_sweep<float>(int, bool, const SweepArgs<float>*, const int2*, int, int, int,
+                                               cudaStream_t);
+
+int batch_blocks_per_sm(int mode, bool fp32, bool cached, int block) {
+    int nb = 0;
+    const void* f = nullptr;
+    if (fp32) {
+        if (mode == SWEEP_SOURCE)
+            f = cached ? (const void*)batch_sweep_kernel<float, SWEEP_SOURCE, true>
+                       : (const void*)batch_sweep_kernel<float, SWEEP_SOURCE, false>;
+        else
+            f = cached ? (const void*)batch_sweep_kernel<float, SWEEP_RESIDUAL, true>
+                       : (const void*)batch_sweep_kernel<float, SWEEP_RESIDUAL, false>;
+    } else {
+        if (mode == SWEEP_SOURCE)
+            f = cached ? (const void*)batch_sweep_kernel<double, SWEEP_SOURCE, true>
+                       : (const void*)batch_sweep_kernel<double, SWEEP_SOURCE, false>;
+        else
+            f = cached ? (const void*)batch_sweep_kernel<double, SWEEP_RESIDUAL, true>
+                       : (const void*)batch_sweep_kernel<double, SWEEP_RESIDUAL, false>;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, 0);
+    return nb;
 }
 
 template <typename T>

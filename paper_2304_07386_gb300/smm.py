@@ -86,6 +86,13 @@ def load_library(path: str | None = None):
     lib.smm_moment_solve.argtypes = [vp, vp, ip]
     lib.smm_iterate.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, vp, C.POINTER(smm_stats)]
     lib.smm_destroy.argtypes = [vp]
+    lib.smm_batch_create.argtypes = [C.c_int32, C.POINTER(vp), C.POINTER(vp)]
+    lib.smm_batch_schedule.argtypes = [vp, ip, ip, dp, C.POINTER(C.c_int64)]
+    lib.smm_batch_sweep.argtypes = [vp, C.POINTER(vp)]
+    lib.smm_batch_iterate.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, C.POINTER(vp), C.POINTER(smm_stats)]
+    lib.smm_batch_destroy.argtypes = [vp]
+    for name in ("smm_batch_create", "smm_batch_schedule", "smm_batch_sweep", "smm_batch_iterate", "smm_batch_destroy"):
+        getattr(lib, name).restype = C.c_int
     lib.smm_block_pcg_noalloc.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, C.c_double, C.c_int32, vp, ip]
     lib.smm_block_pcg_noalloc.restype = C.c_int
     for name in ("smm_quadrature", "smm_create", "smm_get_info", "smm_sweep", "smm_moments", "smm_set_moments",
@@ -237,3 +244,55 @@ def smm_block_pcg_noalloc(diag_blocks, off_blocks, nbr, pinv_blocks, b, x, tol=1
                                                 C.c_void_p(nbr.data_ptr()), _devptr(pinv_blocks), _devptr(b),
                                                 _devptr(x), tol, max_iters, C.c_void_p(s.cuda_stream), C.byref(it)))
     return it.value
+
+
+class Batch:
+    """Owns an smm_batch; keeps its problems' handles alive."""
+
+    def __init__(self, ptr, handles):
+        self.ptr = ptr
+        self.handles = list(handles)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self):
+        if self.ptr:
+            load_library().smm_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def schedule(self):
+        g, b, n = C.c_int32(0), C.c_int32(0), C.c_int64(0)
+        ms = C.c_double(0.0)
+        _check(load_library().smm_batch_schedule(self.ptr, C.byref(g), C.byref(b), C.byref(ms), C.byref(n)))
+        return dict(grid=g.value, block=b.value, tuned_ms=ms.value, n_tasks=n.value)
+
+
+def _ptr_array(tensors):
+    arr = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else _devptr(t).value
+    return arr
+
+
+def smm_batch_create(handles) -> Batch:
+    arr = (C.c_void_p * len(handles))(*[h.ptr.value if isinstance(h.ptr, C.c_void_p) else h.ptr for h in handles])
+    out = C.c_void_p()
+    _check(load_library().smm_batch_create(len(handles), arr, C.byref(out)))
+    return Batch(out, handles)
+
+
+def smm_batch_sweep(b: Batch, phis=None):
+    arr = _ptr_array(phis if phis is not None else [None] * len(b.handles))
+    _check(load_library().smm_batch_sweep(b.ptr, arr))
+
+
+def smm_batch_iterate(b: Batch, phis, tol: float, max_outer: int = 200, relative: bool = False):
+    arr = _ptr_array(phis)
+    st = (smm_stats * len(phis))()
+    rc = load_library().smm_batch_iterate(b.ptr, tol, int(relative), max_outer, arr, st)
+    _check(rc)
+    return [s.as_dict() for s in st]

@@ -213,3 +213,57 @@ def test_anderson_reaches_oracle_fixed_point(depth):
         assert rel(phi.cpu().numpy(), phi_o.ravel()) < 1e-9
         its.append(st["outer_iterations"])
     assert its[1] <= its[0], its
+
+
+BATCH = [
+    # (nx, ny, m, p, sn, seed)
+    (4, 4, 1, 1, 4, None),
+    (6, 5, 2, 2, 8, 3),
+    (3, 3, 3, 3, 4, 7),
+    (5, 4, 2, 4, 6, 2),
+    (7, 3, 1, 2, 12, None),
+]
+
+
+@pytest.mark.parametrize("precision,solver", [(0, 1), (0, 0), (1, 1)], ids=["fp64_cached", "fp64_lu", "fp32_cached"])
+def test_batched_sweep_matches_single_problems(precision, solver):
+    """Uneven problems (mesh size, p, S_N, geometry order) in one launch give
+    the same angular fluxes as their single sweeps."""
+    import paper_2304_07386_gb300 as P
+    probs = [problem(nx, ny, m=m, p=p, sn=sn, seed=seed, kind="mms", c=0.6) for (nx, ny, m, p, sn, seed) in BATCH]
+    phis = [dev(W.mms_phi(pr["pos"][:, :, 0], pr["pos"][:, :, 1]).ravel()) for pr in probs]
+    singles, hs = [], []
+    for pr, ph in zip(probs, phis):
+        h = make_gpu(pr, precision=precision, sweep_solver=solver)
+        P.smm_sweep(h, ph)
+        info = h.info()
+        buf = torch.zeros(info.n_elem * info.n_ord * info.n_dof_elem, dtype=torch.float64, device="cuda")
+        P.smm_get_psi(h, buf)
+        singles.append(buf.cpu().numpy())
+        hs.append(make_gpu(pr, precision=precision, sweep_solver=solver))
+    b = P.smm.smm_batch_create(hs)
+    sched = b.schedule()
+    assert sched["n_tasks"] == sum(h.info().n_elem * h.info().n_ord for h in hs)
+    # (the refined FP32 sweep corrects the flux left by the tuning sweeps; both
+    # it and the single sweep approximate the same FP64 result to FP32 accuracy)
+    P.smm.smm_batch_sweep(b, phis)
+    for h, ref in zip(hs, singles):
+        info = h.info()
+        buf = torch.zeros(info.n_elem * info.n_ord * info.n_dof_elem, dtype=torch.float64, device="cuda")
+        P.smm_get_psi(h, buf)
+        tol = 1e-13 if precision == 0 else 1e-6
+        assert rel(buf.cpu().numpy(), ref) < tol
+
+
+def test_batched_iterate_matches_oracle():
+    import paper_2304_07386_gb300 as P
+    probs = [problem(nx, ny, m=m, p=p, sn=sn, seed=seed, kind="mms", c=0.6) for (nx, ny, m, p, sn, seed) in BATCH[:3]]
+    hs = [make_gpu(pr, tol_cg=1e-14) for pr in probs]
+    b = P.smm.smm_batch_create(hs)
+    phis = [torch.zeros(h.info().n_elem * h.info().n_dof_elem, dtype=torch.float64, device="cuda") for h in hs]
+    stats = P.smm.smm_batch_iterate(b, phis, 1e-12, 100)
+    for pr, ph, st in zip(probs, phis, stats):
+        disc, op, q, inflow = make_oracle(pr)
+        ref, k, _ = op.iterate(tol=1e-12)
+        assert rel(ph.cpu().numpy(), ref.ravel()) < 1e-9
+        assert abs(st["outer_iterations"] - k) <= 1
