@@ -377,6 +377,9 @@ def run_ours(args) -> None:
             rel_diff_fp32_vs_plain=float((x3 - xp).abs().max() / xp.abs().max()),
             learned_guess="not built")
 
+    if not args.quick and args.batch > 0:
+        extra["batched_sweep"] = run_batch(args.batch, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = run_oracle_child(args.cpu_seconds, CPU_SAMPLE_NX)
@@ -403,6 +406,64 @@ def run_ours(args) -> None:
     h.destroy()
     if dist:
         dist.destroy_process_group()
+
+
+def batch_problem(seed: int):
+    """One problem of the uneven batch (BASELINE configs[3] shape, reduced
+    mesh range): n ~ U{32..96}, p ~ U{1..4}, S_N ~ U{4,6,8,10,12}, sigma_t =
+    10 exp(1.5 g) with g a unit Gaussian random field (correlation length 0.1),
+    c ~ U[0.5, 0.99], q = 1 per steradian, vacuum, straight mesh."""
+    import numpy as np
+
+    import smm_workloads as W
+
+    rng = np.random.default_rng(1000 + seed)
+    nx = int(rng.integers(32, 97))
+    p = int(rng.integers(1, 5))
+    sn = int(rng.choice([4, 6, 8, 10, 12]))
+    c = float(rng.uniform(0.5, 0.99))
+    mesh = W.structured_mesh(nx, m=1)
+    st = 10.0 * np.exp(1.5 * W.gaussian_random_field(nx, 0.1, seed))
+    return mesh, p, sn, st, c * st, np.ones((mesh.n_elem, (p + 1) ** 2))
+
+
+def run_batch(nprob: int, stream) -> dict:
+    """Time one batched sweep of nprob uneven problems against the same
+    problems swept one at a time (FP32-refined sweeps, cached inverses)."""
+    import torch
+
+    import paper_2304_07386_gb300 as P
+
+    hs, unknowns = [], 0
+    for i in range(nprob):
+        mesh, p, sn, st, ss, q = batch_problem(i)
+        opt = P.smm_default_options()
+        opt.sweep_precision = P.SMM_SWEEP_FP32_REFINED
+        hs.append(P.smm_create(mesh.nodes, mesh.elem_nodes, 1, p, sn, st, ss, q, options=opt, stream=stream))
+        unknowns += hs[-1].info().n_angular
+    b = P.smm.smm_batch_create(hs)
+    sched = b.schedule()
+
+    def timed(fn, reps=3):
+        best = 1e300
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        return best
+
+    with torch.cuda.stream(stream):
+        tb = timed(lambda: P.smm.smm_batch_sweep(b))
+        ts = timed(lambda: [P.smm_sweep(h) for h in hs])
+    b.destroy()
+    for h in hs:
+        h.destroy()
+    return dict(problems=nprob, angular_unknowns=unknowns, batched_s=tb, one_at_a_time_s=ts,
+                batched_value=unknowns / tb, one_at_a_time_value=unknowns / ts, unit="unknowns/s",
+                schedule=sched, note="wall time of smm_batch_sweep vs consecutive smm_sweep calls (each includes "
+                                     "the FP64 residual, the FP32 correction sweep, moments and one sync)")
 
 
 def run_reference(args) -> None:
@@ -459,6 +520,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--nx", type=int, default=WL["nx"], help="mesh size override (profiling runs)")
+    ap.add_argument("--batch", type=int, default=24, help="problems in the batched-sweep measurement (0: skip)")
     args = ap.parse_args()
     WL["nx"] = args.nx
     if args.impl == "reference":

@@ -102,6 +102,12 @@ typedef struct {
                                    acceleration of that depth (paper Sec. "The
                                    Moment Method Algorithm"; depth 2 in its
                                    crooked-pipe runs), with moment-sized history */
+    int32_t guess_check;        /* smm_iterate: if nonzero and the first step from
+                                   the given guess x0 changes it by more than
+                                   the zero guess would (max|G(x0)-x0| >
+                                   max|G(x0)|, the first residual of the zero
+                                   guess being max|G(0)| ~ max|G(x0)|), restart
+                                   from zero (default 0) */
 } smm_options;
 
 typedef struct {
@@ -118,6 +124,7 @@ typedef struct {
     double ms_sweep;            /* sweep kernel alone */
     double ms_moments, ms_rhs, ms_solve; /* moments + beta, RHS, CG (accumulated, ms) */
     int64_t n_launches;         /* kernels this library launched during the call */
+    int32_t guess_rejected;     /* 1 if guess_check restarted the iteration from zero */
 } smm_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -224,6 +231,34 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
                              smm_stats* stats);
 
 smm_status smm_batch_destroy(smm_batch b);
+
+/* ---- Learned initial guess (not part of the paper's method) ----
+ * A small convolutional encoder-decoder on an H x W element grid (H, W even)
+ * mapping 3 input channels (normalized sigma_t, scattering ratio, source) to
+ * n_out output channels (normalized varphi and correction-tensor nodal
+ * values), trained and evaluated by the library's own kernels: BF16 weights
+ * and activations, FP32 accumulation, FP32 master weights, Adam, mean squared
+ * error.  Layouts: inputs dev [batch][3][H][W] FP32, outputs and targets dev
+ * [batch][n_out][H][W] FP32.  The network only proposes a starting point:
+ * smm_iterate still runs to the same tolerance, and options.guess_check makes
+ * it fall back to the zero guess when the proposal raises the first residual. */
+typedef struct smm_guess_ctx* smm_guess;
+
+/* max_batch: largest batch of later calls; seed: weight initialization. */
+smm_status smm_guess_create(int32_t height, int32_t width, int32_t n_out, int32_t max_batch, uint64_t seed,
+                            void* cuda_stream, smm_guess* out);
+smm_status smm_guess_num_params(smm_guess g, int64_t* n);
+smm_status smm_guess_forward(smm_guess g, int32_t batch, const float* in_dev, float* out_dev);
+/* One Adam step (learning rate lr) on the batch; loss_host (may be NULL) gets the batch loss before the step. */
+smm_status smm_guess_train_step(smm_guess g, int32_t batch, const float* in_dev, const float* target_dev, float lr,
+                                float* loss_host);
+/* Loss and parameter gradients (host, n_params floats; may be NULL) without updating the weights. */
+smm_status smm_guess_gradients(smm_guess g, int32_t batch, const float* in_dev, const float* target_dev,
+                               float* grad_host, float* loss_host);
+/* FP32 master weights to / from a host buffer of n_params floats (checkpoint). */
+smm_status smm_guess_get_params(smm_guess g, float* host);
+smm_status smm_guess_set_params(smm_guess g, const float* host);
+smm_status smm_guess_destroy(smm_guess g);
 
 /* Allocation-free block-Jacobi preconditioned CG.  The paper has no
  * counterpart: this entry point exists for callers that cannot call

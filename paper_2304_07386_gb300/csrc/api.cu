@@ -160,6 +160,7 @@ void smm_default_options(smm_options* opt) {
     opt->precond = SMM_PRECOND_MULTIGRID;
     opt->sweep_solver = SMM_SOLVER_CACHED_INVERSE;
     opt->anderson_depth = 0;
+    opt->guess_check = 0;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -755,6 +756,12 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
         if (h->h_int[4]) {
             if (stats) *stats = local;
             return fail(SMM_ERR_NONFINITE, "non-finite scalar flux");
+        }
+        if (k == 1 && h->opt.guess_check && diff > mx) {
+            // the guess raised the first residual above the zero guess's: restart from zero
+            SMM_CUDA(cudaMemsetAsync(phi_dev, 0, nphi * sizeof(double), h->stream));
+            local.guess_rejected = 1;
+            continue;
         }
         const double crit = relative ? local.last_rel_diff : diff;
         if (crit < tol) {

@@ -34,7 +34,7 @@ class smm_mesh(C.Structure):
 class smm_options(C.Structure):
     _fields_ = [("sweep_precision", C.c_int32), ("tol_cg", C.c_double), ("max_cg", C.c_int32),
                 ("kappa_scale", C.c_double), ("spin_timeout_s", C.c_double), ("precond", C.c_int32),
-                ("sweep_solver", C.c_int32), ("anderson_depth", C.c_int32)]
+                ("sweep_solver", C.c_int32), ("anderson_depth", C.c_int32), ("guess_check", C.c_int32)]
 
 
 class smm_info(C.Structure):
@@ -47,7 +47,8 @@ class smm_stats(C.Structure):
     _fields_ = [("outer_iterations", C.c_int32), ("cg_total", C.c_int32), ("cg_min", C.c_int32),
                 ("cg_max", C.c_int32), ("last_diff", C.c_double), ("last_rel_diff", C.c_double),
                 ("ms_residual", C.c_double), ("ms_sweep", C.c_double), ("ms_moments", C.c_double),
-                ("ms_rhs", C.c_double), ("ms_solve", C.c_double), ("n_launches", C.c_int64)]
+                ("ms_rhs", C.c_double), ("ms_solve", C.c_double), ("n_launches", C.c_int64),
+                ("guess_rejected", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +93,18 @@ def load_library(path: str | None = None):
     lib.smm_batch_iterate.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, C.POINTER(vp), C.POINTER(smm_stats)]
     lib.smm_batch_destroy.argtypes = [vp]
     for name in ("smm_batch_create", "smm_batch_schedule", "smm_batch_sweep", "smm_batch_iterate", "smm_batch_destroy"):
+        getattr(lib, name).restype = C.c_int
+    fp = C.POINTER(C.c_float)
+    lib.smm_guess_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, vp, C.POINTER(vp)]
+    lib.smm_guess_num_params.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.smm_guess_forward.argtypes = [vp, C.c_int32, vp, vp]
+    lib.smm_guess_train_step.argtypes = [vp, C.c_int32, vp, vp, C.c_float, fp]
+    lib.smm_guess_gradients.argtypes = [vp, C.c_int32, vp, vp, fp, fp]
+    lib.smm_guess_get_params.argtypes = [vp, fp]
+    lib.smm_guess_set_params.argtypes = [vp, fp]
+    lib.smm_guess_destroy.argtypes = [vp]
+    for name in ("smm_guess_create", "smm_guess_num_params", "smm_guess_forward", "smm_guess_train_step",
+                 "smm_guess_gradients", "smm_guess_get_params", "smm_guess_set_params", "smm_guess_destroy"):
         getattr(lib, name).restype = C.c_int
     lib.smm_block_pcg_noalloc.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, C.c_double, C.c_int32, vp, ip]
     lib.smm_block_pcg_noalloc.restype = C.c_int
@@ -296,3 +309,62 @@ def smm_batch_iterate(b: Batch, phis, tol: float, max_outer: int = 200, relative
     rc = load_library().smm_batch_iterate(b.ptr, tol, int(relative), max_outer, arr, st)
     _check(rc)
     return [s.as_dict() for s in st]
+
+
+def _fdev(t):
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"):
+        raise ValueError("network buffers must be contiguous CUDA float32 tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+class Guess:
+    """Owns an smm_guess network; methods mirror the C calls."""
+
+    def __init__(self, height, width, n_out, max_batch, seed=0, stream=None):
+        import torch
+
+        self.shape = (height, width, n_out)
+        self.max_batch = max_batch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._stream = s
+        self.ptr = C.c_void_p()
+        _check(load_library().smm_guess_create(height, width, n_out, max_batch, seed, C.c_void_p(s.cuda_stream),
+                                               C.byref(self.ptr)))
+        n = C.c_int64(0)
+        _check(load_library().smm_guess_num_params(self.ptr, C.byref(n)))
+        self.n_params = n.value
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self):
+        if self.ptr:
+            load_library().smm_guess_destroy(self.ptr)
+            self.ptr = None
+
+    def forward(self, x, out):
+        _check(load_library().smm_guess_forward(self.ptr, x.shape[0], _fdev(x), _fdev(out)))
+
+    def train_step(self, x, target, lr):
+        loss = C.c_float(0.0)
+        _check(load_library().smm_guess_train_step(self.ptr, x.shape[0], _fdev(x), _fdev(target), lr, C.byref(loss)))
+        return loss.value
+
+    def gradients(self, x, target):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_float(0.0)
+        _check(load_library().smm_guess_gradients(self.ptr, x.shape[0], _fdev(x), _fdev(target),
+                                                  g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
+        return loss.value, g
+
+    def get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(load_library().smm_guess_get_params(self.ptr, p.ctypes.data_as(C.POINTER(C.c_float))))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load_library().smm_guess_set_params(self.ptr, p.ctypes.data_as(C.POINTER(C.c_float))))

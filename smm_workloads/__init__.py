@@ -320,3 +320,28 @@ def linear_aniso_psi(x, y, ox, oy):
 def linear_aniso_grad_psi(x, y, ox, oy):
     z = np.zeros_like(np.asarray(x, dtype=float))
     return z + LIN_B / (4 * math.pi), z + LIN_C / (4 * math.pi)
+
+
+# ---------------------------------------------------------------------------
+# Learned-guess workload (BASELINE configs[4] shape)
+# ---------------------------------------------------------------------------
+
+def learned_guess_problem(nx: int, seed: int, blocks: int = 8):
+    """Straight nx*nx mesh of [0,1]^2 with sigma_t = 10 exp(1.5 g) (g a unit
+    Gaussian random field, correlation length 0.1), sigma_s = c sigma_t with a
+    smooth scattering ratio field c in [0.5, 0.99], and an isotropic source
+    that is piecewise constant (0 or 1 per steradian) on a random
+    blocks*blocks map.  Returns (mesh, sigma_t, sigma_s, q_elem) with q_elem
+    the per-element source value."""
+    mesh = structured_mesh(nx, m=1)
+    g = gaussian_random_field(nx, 0.1, 2 * seed)
+    h = gaussian_random_field(nx, 0.2, 2 * seed + 1)
+    st = 10.0 * np.exp(1.5 * g)
+    c = 0.5 + 0.49 / (1.0 + np.exp(-1.5 * h))
+    rng = np.random.default_rng(10_000 + seed)
+    bmap = (rng.random((blocks, blocks)) < 0.5).astype(float)
+    e = np.arange(nx * nx)
+    bi = np.minimum((e % nx) * blocks // nx, blocks - 1)
+    bj = np.minimum((e // nx) * blocks // nx, blocks - 1)
+    q = bmap[bj, bi]
+    return mesh, st, c * st, q

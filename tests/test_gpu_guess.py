@@ -1,0 +1,90 @@
+"""Learned initial guess: the library's BF16 network kernels against the
+NumPy oracle (forward and gradients), and a held-out test of what a network
+trained on the method's own solutions gains over the zero guess."""
+import numpy as np
+import pytest
+
+import smm_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_07386_gb300 import build as B
+    B.build()
+
+
+def test_network_forward_and_gradients_match_oracle():
+    import paper_2304_07386_gb300 as P
+    from oracle import cnn
+    H, Wd, n_out, B = 8, 6, 4, 2
+    net = P.smm.Guess(H, Wd, n_out, B, seed=3)
+    assert net.n_params == cnn.num_params(n_out)
+    rng = np.random.default_rng(1)
+    params = (rng.standard_normal(net.n_params) * 0.2).astype(np.float32)
+    net.set_params(params)
+    x = rng.standard_normal((B, 3, H, Wd)).astype(np.float32)
+    t = rng.standard_normal((B, n_out, H, Wd)).astype(np.float32)
+    xd, td = torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda")
+    y = torch.zeros((B, n_out, H, Wd), dtype=torch.float32, device="cuda")
+    net.forward(xd, y)
+    y_ref, _ = cnn.forward(params.astype(np.float64), x.astype(np.float64), n_out, bf=True)
+    assert np.max(np.abs(y.cpu().numpy() - y_ref)) < 2e-2 * np.max(np.abs(y_ref))
+    loss, g = net.gradients(xd, td)
+    loss_ref, g_ref = cnn.loss_and_grad(params.astype(np.float64), x.astype(np.float64), t.astype(np.float64), n_out,
+                                        bf=True)
+    assert abs(loss - loss_ref) < 1e-2 * loss_ref
+    assert np.linalg.norm(g - g_ref) < 3e-2 * np.linalg.norm(g_ref)
+
+
+def _solve(P, nx, seed, phi0=None, check=False, p=2, sn=4, tol=1e-8):
+    mesh, st, ss, qe = W.learned_guess_problem(nx, seed)
+    n = (p + 1) ** 2
+    opt = P.smm_default_options()
+    opt.tol_cg = 1e-12
+    opt.guess_check = int(check)
+    h = P.smm_create(mesh.nodes, mesh.elem_nodes, 1, p, sn, st, ss, np.repeat(qe[:, None], n, axis=1), options=opt)
+    phi = torch.zeros(nx * nx * n, dtype=torch.float64, device="cuda")
+    if phi0 is not None:
+        phi.copy_(torch.as_tensor(phi0, device="cuda"))
+    rc, stats = P.smm_iterate(h, phi, tol, 200, relative=True)
+    mom = torch.zeros(6 * nx * nx * n, dtype=torch.float64, device="cuda")
+    P.smm_moments(h, mom)
+    h.destroy()
+    return phi.cpu().numpy(), mom.cpu().numpy(), stats, (st, ss, qe)
+
+
+def test_trained_guess_saves_outer_iterations_on_held_out_problems():
+    import paper_2304_07386_gb300 as P
+    from paper_2304_07386_gb300 import guess as G
+    nx, p, n = 16, 2, 9
+    X, Y = [], []
+    for seed in range(96):
+        phi, mom, _, (st, ss, qe) = _solve(P, nx, seed, tol=1e-10)
+        X.append(G.features(st, ss, qe, nx))
+        Y.append(G.targets(phi, mom, nx, n))
+    X, Y = np.stack(X), np.stack(Y)
+    xn, yn = G.Normalizer(X), G.Normalizer(Y)
+    net = P.smm.Guess(nx, nx, 4 * n, 16, seed=0)
+    Xd = torch.as_tensor(xn.fwd(X), device="cuda")
+    Yd = torch.as_tensor(yn.fwd(Y), device="cuda")
+    losses = G.train(net, Xd, Yd, steps=800, batch=16, lr=3e-3)
+    assert np.mean(losses[-50:]) < 0.25 * np.mean(losses[:10])
+    base, learned, rejected = [], [], 0
+    for seed in range(1000, 1008):
+        _, _, s0, (st, ss, qe) = _solve(P, nx, seed)
+        xg = torch.as_tensor(xn.fwd(G.features(st, ss, qe, nx)[None]), device="cuda")
+        phi0 = G.predict_phi(net, xg, yn, nx, n)
+        phi1, _, s1, _ = _solve(P, nx, seed, phi0=phi0, check=True)
+        ref, _, _, _ = _solve(P, nx, seed, tol=1e-11)
+        assert np.max(np.abs(phi1 - ref)) < 1e-6 * np.max(np.abs(ref))
+        base.append(s0["outer_iterations"])
+        learned.append(s1["outer_iterations"])
+        rejected += s1["guess_rejected"]
+    print("zero guess", base, "learned", learned, "rejected", rejected)
+    assert np.mean(learned) < np.mean(base)
