@@ -186,12 +186,16 @@ def residual_flops_per_task(p: int) -> float:
 
 def mg_cg_bytes_per_iter(ne: int, n: int) -> float:
     """HBM bytes of one multigrid-preconditioned CG iteration on the element
-    blocks: operator spmv with FP64 blocks (5 n^2 x 8 B per element) and the
-    V-cycle's level-0 work on FP32 blocks -- first smoothing step (Pinv,
-    n^2), second pre-smoothing step (6 n^2), residual (5 n^2), two
-    post-smoothing steps (12 n^2) -- plus about 30 FP64 vector passes
-    (n words each); the vertex and aggregation levels are < 2 % and left out."""
-    return ne * (5 * n * n * 8 + 24 * n * n * 4 + 30 * n * 8)
+    blocks.  The operator is stored as the n x n diagonal block plus four
+    G x G face-coupling matrices per element (G = 2(p+1)): the FP64 product
+    reads it once (8 (n^2 + 4 G^2) B); the V-cycle's level 0 applies the FP32
+    copy four times (second pre-smoothing step, residual, two post-smoothing
+    steps) and the FP32 block-Jacobi inverse four times (16 (n^2 + 4 G^2)
+    + 16 n^2 B); about 30 FP64 vector passes of n words each.  The vertex and
+    aggregation levels are < 2 % of the bytes and left out."""
+    g = 2 * (int(round(n ** 0.5)))
+    op = n * n + 4 * g * g
+    return ne * (8 * op + 16 * op + 16 * n * n + 30 * n * 8)
 
 
 def run_ours(args) -> None:
@@ -375,10 +379,12 @@ def run_ours(args) -> None:
             anderson2_status=rca, rel_diff_anderson2_vs_plain=float((xa - xp).abs().max() / xp.abs().max()),
             rel_diff_chosen_vs_plain=float((xc - xp).abs().max() / xp.abs().max()),
             rel_diff_fp32_vs_plain=float((x3 - xp).abs().max() / xp.abs().max()),
-            learned_guess="not built")
+            learned_guess="see the learned_guess entry (network trained in the run on the learned-guess workload)")
 
     if not args.quick and args.batch > 0:
         extra["batched_sweep"] = run_batch(args.batch, stream)
+    if not args.quick and args.learned > 0:
+        extra["learned_guess"] = run_learned(args.learned, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -409,8 +415,8 @@ def run_ours(args) -> None:
 
 
 def batch_problem(seed: int):
-    """One problem of the uneven batch (BASELINE configs[3] shape, reduced
-    mesh range): n ~ U{32..96}, p ~ U{1..4}, S_N ~ U{4,6,8,10,12}, sigma_t =
+    """One problem of the uneven batched-instances workload (reduced mesh
+    range): n ~ U{32..96}, p ~ U{1..4}, S_N ~ U{4,6,8,10,12}, sigma_t =
     10 exp(1.5 g) with g a unit Gaussian random field (correlation length 0.1),
     c ~ U[0.5, 0.99], q = 1 per steradian, vacuum, straight mesh."""
     import numpy as np
@@ -464,6 +470,105 @@ def run_batch(nprob: int, stream) -> dict:
                 batched_value=unknowns / tb, one_at_a_time_value=unknowns / ts, unit="unknowns/s",
                 schedule=sched, note="wall time of smm_batch_sweep vs consecutive smm_sweep calls (each includes "
                                      "the FP64 residual, the FP32 correction sweep, moments and one sync)")
+
+
+def run_learned(nx: int, stream, n_train: int = 128, n_test: int = 8, p: int = 2, sn: int = 8) -> dict:
+    """Learned-guess workload (p=2, S8, log-normal sigma_t / sigma_s fields,
+    piecewise-constant source maps, on an nx*nx grid of quads): train the
+    library's network on n_train converged solutions the method produces,
+    then time held-out solves to a 1e-8 relative difference: the plain GPU
+    method (FP64 on-the-fly LU sweep, block-Jacobi PCG, zero guess), the
+    chosen method with a zero guess, and the chosen method started from the
+    network's proposal (guess_check on)."""
+    import numpy as np
+    import torch
+
+    import paper_2304_07386_gb300 as P
+    import smm_workloads as W
+    from paper_2304_07386_gb300 import guess as G
+
+    n = (p + 1) ** 2
+
+    def make(seed, plain=False, check=False, anderson=0):
+        mesh, st, ss, qe = W.learned_guess_problem(nx, seed)
+        opt = P.smm_default_options()
+        opt.tol_cg = 1e-12
+        opt.guess_check = int(check)
+        opt.anderson_depth = anderson
+        if plain:
+            opt.sweep_solver = P.smm.SMM_SOLVER_LU
+            opt.precond = P.smm.SMM_PRECOND_BLOCK_JACOBI
+        h = P.smm_create(mesh.nodes, mesh.elem_nodes, 1, p, sn, st, ss, np.repeat(qe[:, None], n, axis=1),
+                         options=opt, stream=stream)
+        return h, (st, ss, qe)
+
+    def solve(h, tol, phi0=None):
+        x = torch.zeros(nx * nx * n, dtype=torch.float64, device="cuda")
+        if phi0 is not None:
+            x.copy_(torch.as_tensor(phi0, device="cuda"))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            rc, s = P.smm_iterate(h, x, tol, 200, relative=True, raise_on_error=False)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, s, x
+
+    t_gen = time.perf_counter()
+    X, Y = [], []
+    for seed in range(n_train):
+        h, (st, ss, qe) = make(seed)
+        _, _, x = solve(h, 1e-10)
+        mom = torch.zeros(6 * nx * nx * n, dtype=torch.float64, device="cuda")
+        P.smm_moments(h, mom)
+        h.destroy()
+        X.append(G.features(st, ss, qe, nx))
+        Y.append(G.targets(x.cpu().numpy(), mom.cpu().numpy(), nx, n))
+    t_gen = time.perf_counter() - t_gen
+    X, Y = np.stack(X), np.stack(Y)
+    xn, yn = G.Normalizer(X), G.Normalizer(Y)
+    net = P.smm.Guess(nx, nx, 4 * n, 16, seed=0, stream=stream)
+    t_train = time.perf_counter()
+    with torch.cuda.stream(stream):
+        losses = G.train(net, torch.as_tensor(xn.fwd(X), device="cuda"), torch.as_tensor(yn.fwd(Y), device="cuda"),
+                         steps=1500, batch=16, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    rows = []
+    for seed in range(100_000, 100_000 + n_test):
+        hp, _ = make(seed, plain=True)
+        tp, sp, xp = solve(hp, 1e-8)
+        hp.destroy()
+        hz, (st, ss, qe) = make(seed)
+        tz, sz, xz = solve(hz, 1e-8)
+        hz.destroy()
+        with torch.cuda.stream(stream):
+            xg = torch.as_tensor(xn.fwd(G.features(st, ss, qe, nx)[None]), device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            phi0 = G.predict_phi(net, xg, yn, nx, n)
+            t_inf = time.perf_counter() - t0
+        hg, _ = make(seed, check=True)
+        tg, sg, xgs = solve(hg, 1e-8, phi0)
+        hg.destroy()
+        ha, _ = make(seed, check=True, anderson=2)
+        ta, sa, xa = solve(ha, 1e-8, phi0)
+        ha.destroy()
+        rows.append(dict(plain_s=tp, plain_outer=sp["outer_iterations"], zero_s=tz, zero_outer=sz["outer_iterations"],
+                         guess_s=tg + t_inf, guess_outer=sg["outer_iterations"], rejected=sg["guess_rejected"],
+                         guess_anderson2_s=ta + t_inf, guess_anderson2_outer=sa["outer_iterations"],
+                         rel_diff_guess_vs_plain=float((xgs - xp).abs().max() / xp.abs().max())))
+    mean = lambda k: float(np.mean([r[k] for r in rows]))
+    return dict(grid=f"{nx}x{nx}", p=p, sn=sn, train_problems=n_train, test_problems=n_test,
+                params=net.n_params, data_gen_s=t_gen, train_s=t_train, final_loss=float(np.mean(losses[-50:])),
+                initial_loss=float(np.mean(losses[:10])),
+                mean_plain_s=mean("plain_s"), mean_zero_guess_s=mean("zero_s"), mean_learned_s=mean("guess_s"),
+                mean_learned_anderson2_s=mean("guess_anderson2_s"),
+                mean_outer_plain=mean("plain_outer"), mean_outer_zero=mean("zero_outer"),
+                mean_outer_learned=mean("guess_outer"), mean_outer_learned_anderson2=mean("guess_anderson2_outer"),
+                rejected=int(sum(r["rejected"] for r in rows)),
+                max_rel_diff_vs_plain=max(r["rel_diff_guess_vs_plain"] for r in rows),
+                note="times to a 1e-8 relative successive difference, inference included; the plain method is the "
+                     "FP64 on-the-fly LU sweep with block-Jacobi PCG and a zero guess")
 
 
 def run_reference(args) -> None:
@@ -521,6 +626,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--nx", type=int, default=WL["nx"], help="mesh size override (profiling runs)")
     ap.add_argument("--batch", type=int, default=24, help="problems in the batched-sweep measurement (0: skip)")
+    ap.add_argument("--learned", type=int, default=32, help="element grid of the learned-guess measurement (0: skip)")
     args = ap.parse_args()
     WL["nx"] = args.nx
     if args.impl == "reference":

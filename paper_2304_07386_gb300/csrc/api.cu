@@ -57,7 +57,7 @@ struct smm_ctx {
     float *M32 = nullptr, *Gx32 = nullptr, *Gy32 = nullptr, *Fx32 = nullptr, *Fy32 = nullptr;
     double *src = nullptr, *inflow = nullptr;
     bool cached = false;
-    double* ainv64 = nullptr;      // cached local inverses (FP64 sweep)
+    float2* ainv_df = nullptr;     // cached local inverses (FP64 sweep), FP32 pairs hi + lo
     float* ainv32 = nullptr;       // cached local inverses (FP32 correction sweep)
     double* msrc = nullptr;        // [ne][n] M (sigma_s/(4pi) phi + q_iso) of the current sweep
     double* mq = nullptr;          // [ne][nd][n] M q_d (angular sources)
@@ -78,7 +78,8 @@ struct smm_ctx {
     double *Kxx = nullptr, *Ks = nullptr, *Kyy = nullptr, *Dfx = nullptr, *Dfy = nullptr, *nds = nullptr;
     double *bfixed = nullptr, *trace = nullptr, *rhs = nullptr;
     // moment operator and CG
-    double *AdT = nullptr, *AoT = nullptr, *PinvT = nullptr;
+    double *AdT = nullptr, *CT = nullptr, *PinvT = nullptr;   // diagonal blocks, face couplings, inverses
+    double wd[5] = {0, 0, 0, 0, 0};
     double *r = nullptr, *z = nullptr, *pv = nullptr, *qv = nullptr, *part = nullptr, *scal = nullptr;
     double *phi_prev = nullptr, *dpart = nullptr, *dout = nullptr;
     int* ctl = nullptr;
@@ -237,8 +238,9 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     {
         std::vector<double> t = transpose_blocks(s.Adiag, s.n);
         ok &= upload(h, h->AdT, t);
-        t = transpose_blocks(s.Aoff, s.n);
-        ok &= upload(h, h->AoT, t);
+        t = transpose_blocks(s.Cface, 2 * s.p1);
+        ok &= upload(h, h->CT, t);
+        for (int k = 0; k < s.p1; ++k) h->wd[k] = s.wd[k];
         t = transpose_blocks(s.Pinv, s.n);
         ok &= upload(h, h->PinvT, t);
         ok &= cudaStreamSynchronize(h->stream) == cudaSuccess;
@@ -304,45 +306,48 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         if (!smm::build_multigrid(s.ne, s.n, s.Adiag, s.Aoff, s.Pinv, nbr, corners, smm::gauss_lobatto01(s.p1).x, H,
                                   merr))
             return bail(SMM_ERR_MESH, merr);
-        if ((int)H.lv.size() - 1 > 15) return bail(SMM_ERR_MESH, "multigrid: too many levels");
+        if ((int)H.lv.size() - 1 > 11) return bail(SMM_ERR_MESH, "multigrid: too many levels");
         smm::MGPlan& P = h->mg;
         P.enabled = true;
         P.ne = s.ne; P.n = s.n; P.nu0 = 2; P.omega0 = H.omega0;
         {
-            float *ad32 = nullptr, *ao32 = nullptr, *pi32 = nullptr;
+            float *ad32 = nullptr, *c32 = nullptr, *pi32 = nullptr;
             ok &= upload_f32(h, ad32, transpose_blocks(s.Adiag, s.n));
-            ok &= upload_f32(h, ao32, transpose_blocks(s.Aoff, s.n));
+            ok &= upload_f32(h, c32, transpose_blocks(s.Cface, 2 * s.p1));
             ok &= upload_f32(h, pi32, transpose_blocks(s.Pinv, s.n));
-            P.AdT = ad32; P.AoT = ao32; P.PinvT = pi32;
+            P.A.AdT = ad32; P.A.CT = c32; P.PinvT = pi32;
+            P.A.nbr = h->nbr; P.A.nface = h->nbr_face;
+            for (int k = 0; k < s.p1; ++k) P.A.wd[k] = (float)s.wd[k];
         }
-        P.nbr = h->nbr;
         P.x0 = h->alloc<float>(nphi); P.x0b = h->alloc<float>(nphi); P.res0 = h->alloc<float>(nphi);
         P.nvert = H.nvert;
         int *vid = nullptr, *vrp = nullptr, *vinc = nullptr;
-        double* w4 = nullptr;
-        ok &= upload(h, vid, H.vid) && upload(h, vrp, H.vrp) && upload(h, vinc, H.vinc) && upload(h, w4, H.w4);
+        float* w4 = nullptr;
+        ok &= upload(h, vid, H.vid) && upload(h, vrp, H.vrp) && upload(h, vinc, H.vinc) && upload_f32(h, w4, H.w4);
         P.vid = vid; P.vrp = vrp; P.vinc = vinc; P.w4 = w4;
         P.nlev = (int)H.lv.size() - 1;
+        P.coarse_ctas = smm::mg_coarse_cluster_size();
         for (int l = 1; l <= P.nlev; ++l) {
             const smm::MGLevel& L = H.lv[l];
             smm::MGLevelDev& D = P.lv[l];
             D.n = L.A.nrow;
-            D.omega = L.omega;
-            D.b = h->alloc<double>(D.n); D.x = h->alloc<double>(D.n); D.r = h->alloc<double>(D.n);
-            D.t = h->alloc<double>(D.n);
+            D.omega = (float)L.omega;
+            D.b = h->alloc<float>(D.n); D.x = h->alloc<float>(D.n); D.r = h->alloc<float>(D.n);
+            D.t = h->alloc<float>(D.n);
             ok &= D.b && D.x && D.r && D.t;
             if (l < P.nlev) {
                 int *arp, *aci, *prp, *pci, *rrp, *rci;
-                double *av, *dv, *pv, *rv;
-                ok &= upload(h, arp, L.A.rp) && upload(h, aci, L.A.ci) && upload(h, av, L.A.v) && upload(h, dv, L.dinv);
-                ok &= upload(h, prp, L.P.rp) && upload(h, pci, L.P.ci) && upload(h, pv, L.P.v);
-                ok &= upload(h, rrp, L.R.rp) && upload(h, rci, L.R.ci) && upload(h, rv, L.R.v);
+                float *av, *dv, *pv, *rv;
+                ok &= upload(h, arp, L.A.rp) && upload(h, aci, L.A.ci) && upload_f32(h, av, L.A.v) &&
+                      upload_f32(h, dv, L.dinv);
+                ok &= upload(h, prp, L.P.rp) && upload(h, pci, L.P.ci) && upload_f32(h, pv, L.P.v);
+                ok &= upload(h, rrp, L.R.rp) && upload(h, rci, L.R.ci) && upload_f32(h, rv, L.R.v);
                 D.Arp = arp; D.Aci = aci; D.Av = av; D.dinv = dv; D.Prp = prp; D.Pci = pci; D.Pv = pv;
                 D.Rrp = rrp; D.Rci = rci; D.Rv = rv;
             }
         }
-        double* cinv = nullptr;
-        ok &= upload(h, cinv, H.coarse_inv);
+        float* cinv = nullptr;
+        ok &= upload_f32(h, cinv, H.coarse_inv);
         P.cinv = cinv;
         ok &= P.x0 && P.x0b && P.res0 && cudaStreamSynchronize(h->stream) == cudaSuccess;
         if (!ok) return bail(SMM_ERR_OOM, "multigrid upload failed");
@@ -391,12 +396,12 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             a.M = h->M32; a.Gx = h->Gx32; a.Gy = h->Gy32; a.Fx = h->Fx32; a.Fy = h->Fy32; a.fdir = h->fdir;
             smm::launch_invert<float>(s.p, a, h->ainv32, h->stream);
         } else {
-            h->ainv64 = h->alloc<double>(ninv);
-            if (!h->ainv64) return bail(SMM_ERR_OOM, "no device memory for the cached local inverses (use SMM_SOLVER_LU)");
+            h->ainv_df = h->alloc<float2>(ninv);
+            if (!h->ainv_df) return bail(SMM_ERR_OOM, "no device memory for the cached local inverses (use SMM_SOLVER_LU)");
             smm::SweepArgs<double> a{};
             a.ne = s.ne; a.nd = s.nd; a.ntask = h->ntask; a.ox = h->ox; a.oy = h->oy; a.sigma_t = h->sigma_t;
             a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy; a.fdir = h->fdir;
-            smm::launch_invert<double>(s.p, a, h->ainv64, h->stream);
+            smm::launch_invert_df(s.p, a, h->ainv_df, h->stream);
         }
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess)
             return bail(SMM_ERR_CUDA, "local inverse construction failed");
@@ -458,7 +463,7 @@ smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) 
         if (h->cached) {
             smm::launch_source(h->ne, h->n, h->M, h->sigma_s, phi, h->src_angular ? nullptr : h->src, h->msrc, h->stream);
             h->launches += 1;
-            a.ainv = h->ainv64; a.msrc = h->msrc; a.mq = h->mq;
+            a.ainv_df = h->ainv_df; a.msrc = h->msrc; a.mq = h->mq;
         }
     } else {
         smm::ResidualArgs r{};
@@ -519,7 +524,9 @@ smm_status enqueue_rhs(smm_handle h) {
 smm::CGArgs cg_args(smm_handle h, double* x) {
     smm::CGArgs a{};
     a.ne = h->ne; a.n = h->n; a.nrow = h->ne * h->n; a.nblk = h->cg_nblk;
-    a.AdT = h->AdT; a.AoT = h->AoT; a.PinvT = h->PinvT; a.nbr = h->nbr;
+    a.A.AdT = h->AdT; a.A.CT = h->CT; a.A.nbr = h->nbr; a.A.nface = h->nbr_face;
+    for (int k = 0; k < 5; ++k) a.A.wd[k] = h->wd[k];
+    a.PinvT = h->PinvT;
     a.x = x; a.r = h->r; a.z = h->z; a.p = h->pv; a.q = h->qv; a.rold = h->rold; a.b = h->rhs; a.part = h->part;
     a.scal = h->scal;
     a.ctl = h->ctl;

@@ -1,66 +1,131 @@
-// Device helpers shared by the PCG and multigrid kernels: element-block
-// operator rows with column-major (transposed) n x n blocks.
+// Device helpers shared by the PCG and multigrid kernels: rows of the IP-SMM
+// moment operator with column-major n x n diagonal blocks and face-factored
+// neighbour blocks (see FaceOp).  Thread blocks cover whole elements: EPB =
+// 256 / n elements of n rows each.
 #pragma once
 
 #include "kernels.cuh"
 
 namespace smm {
 
-// (A v)_i for row i of element e: diagonal block plus the four face-neighbour blocks
-// (blocks of type BT, FP64 accumulation)
-template <typename BT>
-__device__ __forceinline__ double block_row(const BT* __restrict__ AdT, const BT* __restrict__ AoT,
-                                            const int32_t* __restrict__ nbr, int n, const double* __restrict__ v,
-                                            int e, int i) {
-    const BT* Ad = AdT + (size_t)e * n * n + i;
+template <int N>
+struct FaceDims {
+    static constexpr int P1 = N == 4 ? 2 : N == 9 ? 3 : N == 16 ? 4 : 5;  // p + 1
+    static constexpr int G = 2 * P1;                                      // face data per face
+    static constexpr int NG = 4 * G;                                      // face data per element
+    static constexpr int EPB = 256 / N;                                   // elements per block
+};
+
+// element-local node at face position a, line position t (t = 0 on face f)
+template <int P1>
+__device__ __forceinline__ int line_node(int f, int a, int t) {
+    constexpr int p = P1 - 1;
+    switch (f) {
+        case 0: return t * P1 + a;
+        case 1: return a * P1 + p - t;
+        case 2: return (p - t) * P1 + a;
+        default: return a * P1 + t;
+    }
+}
+
+// shared scratch of one thread block: neighbour face data and coupled face data
+template <int N, typename AT>
+struct FaceScratch {
+    AT g[FaceDims<N>::EPB * FaceDims<N>::NG];
+    AT w[FaceDims<N>::EPB * FaceDims<N>::NG];
+};
+
+// (A x)_i for row i of element e (act: this thread owns a row).  Every thread
+// of the block must call it (two block barriers).  Steps: diagonal block row;
+// the neighbours' face data g = E_f2 x_e2 (trace values and normal
+// derivatives); w = C_{e,f} g per face; lift (E_f^T w)_i.
+template <int N, typename T, typename AT, typename VT>
+__device__ __forceinline__ AT faceop_row(const FaceOp<T>& op, const VT* __restrict__ x, int e, int i, bool act,
+                                         FaceScratch<N, AT>& sc) {
+    using D = FaceDims<N>;
+    constexpr int P1 = D::P1, G = D::G, NG = D::NG;
+    const int le = threadIdx.x / N;
+    AT y = 0;
+    if (act) {
+        const T* Ad = op.AdT + (size_t)e * N * N + i;
+        const VT* xe = x + (size_t)e * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) y += (AT)Ad[j * N] * (AT)xe[j];
+#pragma unroll
+        for (int v0 = 0; v0 < NG; v0 += N) {
+            const int v = v0 + i;
+            if (v < NG) {
+                const int f = v / G, r = v - f * G;
+                const int e2 = op.nbr[e * 4 + f];
+                AT g = 0;
+                if (e2 >= 0) {
+                    const int f2 = op.nface[e * 4 + f];
+                    const VT* x2 = x + (size_t)e2 * N;
+                    if (r < P1) {
+                        g = (AT)x2[line_node<P1>(f2, r, 0)];
+                    } else {
+                        const int a = r - P1;
+#pragma unroll
+                        for (int t = 0; t < P1; ++t) g += (AT)op.wd[t] * (AT)x2[line_node<P1>(f2, a, t)];
+                    }
+                }
+                sc.g[le * NG + v] = g;
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int v0 = 0; v0 < NG; v0 += N) {
+            const int v = v0 + i;
+            if (v < NG) {
+                const int f = v / G, r = v - f * G;
+                AT w = 0;
+                if (op.nbr[e * 4 + f] >= 0) {
+                    const T* C = op.CT + ((size_t)(e * 4 + f) * G) * G + r;
+                    const AT* g = sc.g + le * NG + f * G;
+#pragma unroll
+                    for (int c = 0; c < G; ++c) w += (AT)C[c * G] * g[c];
+                }
+                sc.w[le * NG + v] = w;
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+        constexpr int p = P1 - 1;
+        const int ix = i % P1, iy = i / P1;
+        const AT* w = sc.w + le * NG;
+        // (face, face position, line position) of this node for each face
+        const int fa[4] = {ix, iy, ix, iy};
+        const int ft[4] = {iy, p - ix, p - iy, ix};
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            AT c = 0;
+#pragma unroll
+            for (int t = 0; t < P1; ++t)
+                if (t == ft[f]) c = (AT)op.wd[t];
+            y += c * w[f * G + P1 + fa[f]];
+            if (ft[f] == 0) y += w[f * G + fa[f]];
+        }
+    }
+    return y;
+}
+
+// (A v)_i with dense column-major neighbour blocks (runtime n)
+__device__ __forceinline__ double dense_block_row(const double* __restrict__ AdT, const double* __restrict__ AoT,
+                                                  const int32_t* __restrict__ nbr, int n, const double* __restrict__ v,
+                                                  int e, int i) {
+    const double* Ad = AdT + (size_t)e * n * n + i;
     const double* ve = v + (size_t)e * n;
     double acc = 0.0;
-    for (int j = 0; j < n; ++j) acc += (double)Ad[(size_t)j * n] * ve[j];
+    for (int j = 0; j < n; ++j) acc += Ad[(size_t)j * n] * ve[j];
     for (int f = 0; f < 4; ++f) {
         const int e2 = nbr[e * 4 + f];
         if (e2 < 0) continue;
-        const BT* Ao = AoT + ((size_t)e * 4 + f) * n * n + i;
+        const double* Ao = AoT + ((size_t)e * 4 + f) * n * n + i;
         const double* v2 = v + (size_t)e2 * n;
-        for (int j = 0; j < n; ++j) acc += (double)Ao[(size_t)j * n] * v2[j];
-    }
-    return acc;
-}
-
-// FP32 variant for the multigrid smoother: FP32 blocks, vector and accumulation
-__device__ __forceinline__ float block_row_f(const float* __restrict__ AdT, const float* __restrict__ AoT,
-                                             const int32_t* __restrict__ nbr, int n, const float* __restrict__ v,
-                                             int e, int i) {
-    const float* Ad = AdT + (size_t)e * n * n + i;
-    const float* ve = v + (size_t)e * n;
-    float acc = 0.0f;
-    for (int j = 0; j < n; ++j) acc = fmaf(Ad[(size_t)j * n], ve[j], acc);
-    for (int f = 0; f < 4; ++f) {
-        const int e2 = nbr[e * 4 + f];
-        if (e2 < 0) continue;
-        const float* Ao = AoT + ((size_t)e * 4 + f) * n * n + i;
-        const float* v2 = v + (size_t)e2 * n;
-        for (int j = 0; j < n; ++j) acc = fmaf(Ao[(size_t)j * n], v2[j], acc);
-    }
-    return acc;
-}
-
-// compile-time block size variants (n = (p+1)^2), fully unrolled
-template <int N, typename BT, typename VT, typename AT>
-__device__ __forceinline__ AT block_row_n(const BT* __restrict__ AdT, const BT* __restrict__ AoT,
-                                          const int32_t* __restrict__ nbr, const VT* __restrict__ v, int e, int i) {
-    const BT* Ad = AdT + (size_t)e * N * N + i;
-    const VT* ve = v + (size_t)e * N;
-    AT acc = 0;
-#pragma unroll
-    for (int j = 0; j < N; ++j) acc += (AT)Ad[j * N] * (AT)ve[j];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const int e2 = nbr[e * 4 + f];
-        if (e2 < 0) continue;
-        const BT* Ao = AoT + ((size_t)e * 4 + f) * N * N + i;
-        const VT* v2 = v + (size_t)e2 * N;
-#pragma unroll
-        for (int j = 0; j < N; ++j) acc += (AT)Ao[j * N] * (AT)v2[j];
+        for (int j = 0; j < n; ++j) acc += Ao[(size_t)j * n] * v2[j];
     }
     return acc;
 }

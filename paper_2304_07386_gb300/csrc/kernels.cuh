@@ -38,6 +38,7 @@ struct SweepArgs {
     const double* inflow;      // [nb][nd][p1] or nullptr (SOURCE)
     const float* rhs;          // [ne][nd][n] (RESIDUAL)
     const T* ainv;             // cached local inverses [ne*nd][n][n] column-major, or nullptr (on-the-fly LU)
+    const float2* ainv_df;     // FP64 cached mode: the same inverses as FP32 pairs (hi, lo), hi + lo = entry
     const double* msrc;        // cached mode, SOURCE: [ne][n] M (sigma_s/(4pi) phi + q_iso) of this sweep
     const double* mq;          // cached mode, SOURCE, angular q: [ne][nd][n] M q_d, else nullptr
     T* psi;                    // [ne][nd][n] output, read by downwind tasks
@@ -83,6 +84,8 @@ int batch_blocks_per_sm(int mode, bool fp32, bool cached, int block);
 // form every local inverse A_{K,d}^{-1} (column-major, type T) in ainv_out
 template <typename T>
 void launch_invert(int p, const SweepArgs<T>& a, T* ainv_out, cudaStream_t s);
+// FP64 local inverses stored as FP32 pairs (hi, lo) with hi + lo = the FP64 entry to 2^-48
+void launch_invert_df(int p, const SweepArgs<double>& a, float2* ainv_out, cudaStream_t s);
 // out[e][d][i] = scale * sum_j M[e][i][j] in[e][d][j] (+ add[e][i] * scale2 if add) ; nd = 1 for per-element data
 void launch_mass_apply(int ne, int nd, int n, const double* M, const double* in, double* out, cudaStream_t s);
 // msrc[e][i] = sum_j M[e][i][j] (c_e phi[e][j] + q[e][j]); phi, q nullable
@@ -103,13 +106,28 @@ void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* 
                 const int32_t* nbr_face, const int32_t* nbr_flip, const int32_t* bface_id, const double* b_ds,
                 double* trace, double* rhs, cudaStream_t s);
 
+// IP-SMM moment operator: diagonal blocks plus face-factored neighbour
+// blocks A_{e,e2} = E_f^T C_{e,f} E_f2, where E_f extracts the p+1 trace
+// values and p+1 reference normal derivatives sum_t wd[t] u(line t) of one
+// face (G = 2(p+1) face data)
+template <typename T>
+struct FaceOp {
+    const T* AdT = nullptr;          // [ne][n][n] transposed (col-major per block)
+    const T* CT = nullptr;           // [ne][4][G][G], CT[((e*4+f)*G + c)*G + r] = C_{e,f}[r][c]
+    const int32_t* nbr = nullptr;    // [ne][4] neighbour element or -1
+    const int32_t* nface = nullptr;  // [ne][4] the neighbour's local index of the shared face
+    T wd[5] = {};                    // l'_t(0) of the 1D Gauss-Lobatto basis, t < p+1
+};
+
 // block-Jacobi PCG
 struct CGArgs {
     int ne, n, nrow, nblk;     // nblk: blocks of the row kernels
-    const double* AdT;         // [ne][n][n] transposed (col-major per block)
-    const double* AoT;         // [ne][4][n][n] transposed
+    FaceOp<double> A;          // operator (FP64)
+    // dense alternative (caller-provided blocks, any n <= 64): used when AoT_dense is set
+    const double* AdT_dense;   // [ne][n][n] transposed
+    const double* AoT_dense;   // [ne][4][n][n] transposed
+    const int32_t* nbr_dense;  // [ne][4]
     const double* PinvT;       // [ne][n][n] transposed
-    const int32_t* nbr;        // [ne][4]
     double* x;
     double* r;
     double* z;
@@ -121,29 +139,33 @@ struct CGArgs {
     double* scal;              // [8]: rz, pq, rr, bb, thresh2, -, -, -
     int* ctl;                  // [4]: done, iters, max_iters, nonfinite
 };
-// multigrid preconditioner (device side of an MGHierarchy)
+// multigrid preconditioner (device side of an MGHierarchy); levels >= 1 in FP32
 struct MGLevelDev {
     int n = 0;                                   // unknowns on this level
-    const int* Arp = nullptr; const int* Aci = nullptr; const double* Av = nullptr;
-    const double* dinv = nullptr;
-    double omega = 0.0;
-    const int* Prp = nullptr; const int* Pci = nullptr; const double* Pv = nullptr;  // to level l+1
-    const int* Rrp = nullptr; const int* Rci = nullptr; const double* Rv = nullptr;
-    double* b = nullptr; double* x = nullptr; double* r = nullptr; double* t = nullptr;
+    const int* Arp = nullptr; const int* Aci = nullptr; const float* Av = nullptr;
+    const float* dinv = nullptr;
+    float omega = 0.0f;
+    const int* Prp = nullptr; const int* Pci = nullptr; const float* Pv = nullptr;  // from level l+1
+    const int* Rrp = nullptr; const int* Rci = nullptr; const float* Rv = nullptr;  // to level l+1
+    float* b = nullptr; float* x = nullptr; float* r = nullptr; float* t = nullptr;
 };
 struct MGPlan {
     bool enabled = false;
     int ne = 0, n = 0, nu0 = 2;
     double omega0 = 0.0;
-    const float* AdT = nullptr; const float* AoT = nullptr; const float* PinvT = nullptr;  // FP32 copies
-    const int32_t* nbr = nullptr;
-    float* x0 = nullptr; float* x0b = nullptr; float* res0 = nullptr;      // [ne*n], level 0 works in FP32
+    FaceOp<float> A;                              // FP32 copy of the operator
+    const float* PinvT = nullptr;                 // FP32 block-Jacobi inverses
+    float* x0 = nullptr; float* x0b = nullptr;   // [ne*n], level 0 works in FP32
+    float* res0 = nullptr;                        // [ne][4] element-corner sums of the level-0 residual
     int nvert = 0;
-    const int* vid = nullptr; const double* w4 = nullptr; const int* vrp = nullptr; const int* vinc = nullptr;
+    const int* vid = nullptr; const float* w4 = nullptr; const int* vrp = nullptr; const int* vinc = nullptr;
     int nlev = 0;                                 // levels 1..nlev (nlev = coarsest, dense)
-    MGLevelDev lv[16];
-    const double* cinv = nullptr;
+    int coarse_ctas = 8;                          // cluster size of the coarse-level launch
+    MGLevelDev lv[12];
+    const float* cinv = nullptr;                  // [nc][nc] row-major
 };
+// cluster size for the coarse-level launch on the current device (8 or 16)
+int mg_coarse_cluster_size();
 // z = V-cycle(r); returns the number of kernel launches; ctl (nullable): skip when set
 int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s);
 

@@ -8,43 +8,46 @@
 // functions on the mesh vertices (restriction gathers the four corner
 // weights of every element node, prolongation interpolates them back).
 // Levels 2..: smoothed-aggregation CSR operators with one damped Jacobi
-// step before and after; the coarsest level is a dense inverse.  The cycle
+// step before and after; the coarsest level is a dense inverse.  Levels >= 1
+// are stored and applied in FP32 and run as one cluster launch.  The cycle
 // is symmetric, so it is a valid CG preconditioner.  Every kernel returns at
 // once when the CG control word says the solve has finished.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "blockops.cuh"
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace smm {
 
 namespace {
 
-constexpr int kTPB = 256;
-
-inline int blocks_for(int n) { return std::max(1, (n + kTPB - 1) / kTPB); }
-
 // xout = xin + omega Pinv (b - A xin) in FP32; xin == nullptr means xin = 0;
 // b is the FP64 right-hand side, xout is FP32 (inner steps) or FP64 (last step)
 template <typename OT, int N>
-__global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, const float* __restrict__ AdT,
-                                                        const float* __restrict__ AoT, const float* __restrict__ PinvT,
-                                                        const int32_t* __restrict__ nbr, float omega,
-                                                        const double* __restrict__ b, const float* __restrict__ xin,
-                                                        OT* __restrict__ xout, const int* ctl) {
+__global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, FaceOp<float> A, const float* __restrict__ PinvT,
+                                                        float omega, const double* __restrict__ b,
+                                                        const float* __restrict__ xin, OT* __restrict__ xout,
+                                                        const int* ctl) {
     if (cg_finished(ctl)) return;
     constexpr int n = N;
     __shared__ float res[256];
+    __shared__ FaceScratch<N, float> sc;
     const int epb = blockDim.x / n;
     const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
     const bool act = e < ne;
     float r = 0.0f, x = 0.0f;
-    if (act) {
-        r = (float)b[(size_t)e * n + i];
-        if (xin) {
+    if (xin) {
+        const float ax = faceop_row<N, float, float, float>(A, xin, e, i, act, sc);
+        if (act) {
             x = xin[(size_t)e * n + i];
-            r -= block_row_n<N, float, float, float>(AdT, AoT, nbr, xin, e, i);
+            r = (float)b[(size_t)e * n + i] - ax;
         }
+    } else if (act) {
+        r = (float)b[(size_t)e * n + i];
     }
     res[threadIdx.x] = r;
     __syncthreads();
@@ -58,108 +61,173 @@ __global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, const float* __r
     }
 }
 
-// res = b - A x (FP32)
+// Level-0 residual res = b - A x (FP32) restricted to the element corners:
+// cres[e][c] = sum_i w4[i][c] res[e][i] (the vertex level sums these over the
+// elements at each vertex)
 template <int N>
-__global__ void bj_residual_kernel(int ne, const float* __restrict__ AdT, const float* __restrict__ AoT,
-                                   const int32_t* __restrict__ nbr, const double* __restrict__ b,
-                                   const float* __restrict__ x, float* __restrict__ res, const int* ctl) {
+__global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> A, const double* __restrict__ b,
+                                                          const float* __restrict__ x, const float* __restrict__ w4,
+                                                          float* __restrict__ cres, const int* ctl) {
     if (cg_finished(ctl)) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ne * N) return;
-    const int e = t / N, i = t - e * N;
-    res[t] = (float)b[t] - block_row_n<N, float, float, float>(AdT, AoT, nbr, x, e, i);
-}
-
-// bv[v] = sum over (element, corner) at vertex v of sum_i w4[i][corner] res[e][i]
-__global__ void restrict_q1_kernel(int nvert, int n, const int* __restrict__ vrp, const int* __restrict__ vinc,
-                                   const double* __restrict__ w4, const float* __restrict__ res,
-                                   double* __restrict__ bv, const int* ctl) {
-    if (cg_finished(ctl)) return;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nvert) return;
-    double s = 0.0;
-    for (int k = vrp[v]; k < vrp[v + 1]; ++k) {
-        const int e = vinc[k] >> 2, c = vinc[k] & 3;
-        const float* re = res + (size_t)e * n;
-        for (int i = 0; i < n; ++i) s += w4[i * 4 + c] * (double)re[i];
+    __shared__ FaceScratch<N, float> sc;
+    __shared__ float rs[256];
+    const int epb = blockDim.x / N;
+    const int e = blockIdx.x * epb + threadIdx.x / N, i = threadIdx.x % N;
+    const bool act = e < ne;
+    const float ax = faceop_row<N, float, float, float>(A, x, e, i, act, sc);
+    rs[threadIdx.x] = act ? (float)b[(size_t)e * N + i] - ax : 0.0f;
+    __syncthreads();
+    if (act && i < 4) {
+        const float* re = rs + (threadIdx.x / N) * N;
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fmaf(w4[j * 4 + i], re[j], s);
+        cres[(size_t)e * 4 + i] = s;
     }
-    bv[v] = s;
 }
 
 // x[e][i] += sum_c w4[i][c] xv[vid[e][c]]
-__global__ void prolong_q1_kernel(int ne, int n, const int* __restrict__ vid, const double* __restrict__ w4,
-                                  const double* __restrict__ xv, float* __restrict__ x, const int* ctl) {
+__global__ void prolong_q1_kernel(int ne, int n, const int* __restrict__ vid, const float* __restrict__ w4,
+                                  const float* __restrict__ xv, float* __restrict__ x, const int* ctl) {
     if (cg_finished(ctl)) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ne * n) return;
     const int e = t / n, i = t - e * n;
     const int* ve = vid + e * 4;
-    x[t] += (float)(w4[i * 4] * xv[ve[0]] + w4[i * 4 + 1] * xv[ve[1]] + w4[i * 4 + 2] * xv[ve[2]] +
-                    w4[i * 4 + 3] * xv[ve[3]]);
+    const float* w = w4 + i * 4;
+    x[t] += w[0] * xv[ve[0]] + w[1] * xv[ve[1]] + w[2] * xv[ve[2]] + w[3] * xv[ve[3]];
 }
 
-__device__ __forceinline__ double csr_row(const int* rp, const int* ci, const double* v, const double* x, int i) {
-    double s = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) s += v[k] * x[ci[k]];
-    return s;
-}
+// The coarse part of the cycle -- the vertex-level right-hand side from the
+// element-corner residuals, the CSR levels down and up and the dense
+// coarsest solve -- in one launch of one thread-block cluster.  Each stage is
+// a grid-stride loop over the cluster's threads; stages are separated by the
+// cluster's hardware barrier (no flag waits).  Vectors written inside the
+// kernel are read through L2 (ld.global.cg).  The result is lv[1].t (or the
+// coarsest x when the vertex level is the coarsest).
+constexpr int kCoarseThreads = 1024;
 
-// x = omega dinv b
-__global__ void jac_first_kernel(int n, const double* __restrict__ dinv, double omega, const double* __restrict__ b,
-                                 double* __restrict__ x, const int* ctl) {
-    if (cg_finished(ctl)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] = omega * dinv[i] * b[i];
-}
+struct CoarseArgs {
+    int nvert, nlev;
+    const float* cres;                          // [ne][4] corner sums of the level-0 residual
+    const int* vrp; const int* vinc;
+    MGLevelDev lv[12];
+    const float* cinv;
+};
 
-// r = b - A x
-__global__ void csr_residual_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                    const double* __restrict__ v, const double* __restrict__ b,
-                                    const double* __restrict__ x, double* __restrict__ r, const int* ctl) {
-    if (cg_finished(ctl)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) r[i] = b[i] - csr_row(rp, ci, v, x, i);
-}
-
-// y = M x   (accumulate: y += M x)
-__global__ void csr_spmv_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y,
-                                int accumulate, const int* ctl) {
-    if (cg_finished(ctl)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double s = csr_row(rp, ci, v, x, i);
-    y[i] = accumulate ? y[i] + s : s;
-}
-
-// xout = x + omega dinv (b - A x)
-__global__ void jac_step_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                const double* __restrict__ v, const double* __restrict__ dinv, double omega,
-                                const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ xout,
-                                const int* ctl) {
-    if (cg_finished(ctl)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) xout[i] = x[i] + omega * dinv[i] * (b[i] - csr_row(rp, ci, v, x, i));
-}
-
-// x = Cinv b (dense, row-major), one warp per row
-__global__ void dense_solve_kernel(int n, const double* __restrict__ cinv, const double* __restrict__ b,
-                                   double* __restrict__ x, const int* ctl) {
-    if (cg_finished(ctl)) return;
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= n) return;
-    const double* cr = cinv + (size_t)row * n;
-    double s = 0.0;
-    for (int j = lane; j < n; j += 32) s += cr[j] * b[j];
+// sum_k v[k] x[ci[k]] over row i, loads issued eight entries at a time
+__device__ __forceinline__ float csr_row_f(const int* __restrict__ rp, const int* __restrict__ ci,
+                                           const float* __restrict__ v, const float* x, int i) {
+    int k = rp[i];
+    const int ke = rp[i + 1];
+    float s0 = 0.0f, s1 = 0.0f;
+    for (; k + 8 <= ke; k += 8) {
+        int c[8];
+        float w[8], xv[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[row] = s;
+        for (int u = 0; u < 8; ++u) {
+            c[u] = ci[k + u];
+            w[u] = v[k + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xv[u] = __ldcg(x + c[u]);
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            s0 = fmaf(w[u], xv[u], s0);
+            s1 = fmaf(w[u + 1], xv[u + 1], s1);
+        }
+    }
+    for (; k < ke; ++k) s0 = fmaf(v[k], __ldcg(x + ci[k]), s0);
+    return s0 + s1;
+}
+
+// launched as one cluster of gridDim.x CTAs (8, or 16 where the GPU allows it)
+__global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs a, const int* ctl) {
+    if (cg_finished(ctl)) return;  // uniform over the cluster: no barrier is left waiting
+    cg::cluster_group cl = cg::this_cluster();
+    const int T = gridDim.x * kCoarseThreads;
+    const int tid = blockIdx.x * kCoarseThreads + threadIdx.x;
+    // vertex-level right-hand side: sum of the corner sums of the elements at each vertex
+    {
+        float* b1 = a.lv[1].b;
+        for (int v = tid; v < a.nvert; v += T) {
+            float s = 0.0f;
+            for (int k = a.vrp[v]; k < a.vrp[v + 1]; ++k) s += a.cres[a.vinc[k]];
+            b1[v] = s;
+        }
+    }
+    cl.sync();
+    // down: x = omega dinv b ; r = b - A x ; b_{l+1} = R r
+    for (int l = 1; l < a.nlev; ++l) {
+        const MGLevelDev& L = a.lv[l];
+        for (int i = tid; i < L.n; i += T) L.x[i] = L.omega * L.dinv[i] * __ldcg(L.b + i);
+        cl.sync();
+        for (int i = tid; i < L.n; i += T) L.r[i] = __ldcg(L.b + i) - csr_row_f(L.Arp, L.Aci, L.Av, L.x, i);
+        cl.sync();
+        const MGLevelDev& Lc = a.lv[l + 1];
+        for (int i = tid; i < Lc.n; i += T) Lc.b[i] = csr_row_f(L.Rrp, L.Rci, L.Rv, L.r, i);
+        cl.sync();
+    }
+    // coarsest: x = Cinv b, one warp per row
+    {
+        const MGLevelDev& C = a.lv[a.nlev];
+        const int lane = threadIdx.x & 31, w = tid >> 5, nw = T >> 5;
+        for (int row = w; row < C.n; row += nw) {
+            const float* cr = a.cinv + (size_t)row * C.n;
+            float s = 0.0f;
+            for (int j = lane; j < C.n; j += 32) s = fmaf(cr[j], __ldcg(C.b + j), s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) C.x[row] = s;
+        }
+    }
+    cl.sync();
+    // up: x += P x_{l+1} ; t = x + omega dinv (b - A x)
+    const float* coarse_out = a.lv[a.nlev].x;
+    for (int l = a.nlev - 1; l >= 1; --l) {
+        const MGLevelDev& L = a.lv[l];
+        for (int i = tid; i < L.n; i += T) L.x[i] = __ldcg(L.x + i) + csr_row_f(L.Prp, L.Pci, L.Pv, coarse_out, i);
+        cl.sync();
+        for (int i = tid; i < L.n; i += T) {
+            const float xi = __ldcg(L.x + i);
+            L.t[i] = xi + L.omega * L.dinv[i] * (__ldcg(L.b + i) - csr_row_f(L.Arp, L.Aci, L.Av, L.x, i));
+        }
+        cl.sync();
+        coarse_out = L.t;
+    }
 }
 
 }  // namespace
 
 template <int N>
 int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s);
+
+int mg_coarse_cluster_size() {
+    // 16 CTAs (a non-portable cluster size) where the device can co-schedule
+    // them, else the portable 8
+    static int chosen = 0;
+    if (chosen) return chosen;
+    int ctas = 8;
+    if (cudaFuncSetAttribute(coarse_cycle_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess) {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3(16, 1, 1);
+        cfg.blockDim = dim3(kCoarseThreads, 1, 1);
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 16;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, coarse_cycle_kernel, &cfg) == cudaSuccess && nclusters >= 1)
+            ctas = 16;
+    }
+    cudaGetLastError();
+    chosen = ctas;
+    return chosen;
+}
 
 int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s) {
     switch (m.n) {
@@ -177,52 +245,47 @@ int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cuda
     const int tpb = cg_threads_per_block(N);
     const int nblk0 = (m.ne + tpb / N - 1) / (tpb / N);
     const size_t shm = 0;
-    const int rows0 = m.ne * N;
     const float w0 = (float)m.omega0;
     // level 0 pre-smoothing from zero (FP32)
     float* xa = m.x0;
     float* xb = m.x0b;
-    bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.AdT, m.AoT, m.PinvT, m.nbr, w0, r, nullptr, xa, ctl);
+    bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.A, m.PinvT, w0, r, nullptr, xa, ctl);
     ++launches;
     for (int k = 1; k < m.nu0; ++k) {
-        bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.AdT, m.AoT, m.PinvT, m.nbr, w0, r, xa, xb, ctl);
+        bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, xb, ctl);
         std::swap(xa, xb);
         ++launches;
     }
-    bj_residual_kernel<N><<<blocks_for(rows0), kTPB, 0, s>>>(m.ne, m.AdT, m.AoT, m.nbr, r, xa, m.res0, ctl);
-    restrict_q1_kernel<<<blocks_for(m.nvert), kTPB, 0, s>>>(m.nvert, N, m.vrp, m.vinc, m.w4, m.res0, m.lv[1].b, ctl);
-    launches += 2;
-    // down the CSR levels (FP64)
-    for (int l = 1; l < m.nlev; ++l) {
-        const MGLevelDev& L = m.lv[l];
-        jac_first_kernel<<<blocks_for(L.n), kTPB, 0, s>>>(L.n, L.dinv, L.omega, L.b, L.x, ctl);
-        csr_residual_kernel<<<blocks_for(L.n), kTPB, 0, s>>>(L.n, L.Arp, L.Aci, L.Av, L.b, L.x, L.r, ctl);
-        csr_spmv_kernel<<<blocks_for(m.lv[l + 1].n), kTPB, 0, s>>>(m.lv[l + 1].n, L.Rrp, L.Rci, L.Rv, L.r,
-                                                                    m.lv[l + 1].b, 0, ctl);
-        launches += 3;
+    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, r, xa, m.w4, m.res0, ctl);
+    // vertex and aggregation levels and the coarsest solve (one cluster launch)
+    CoarseArgs ca{};
+    ca.nvert = m.nvert; ca.nlev = m.nlev; ca.cres = m.res0; ca.vrp = m.vrp; ca.vinc = m.vinc;
+    for (int l = 0; l <= m.nlev; ++l) ca.lv[l] = m.lv[l];
+    ca.cinv = m.cinv;
+    {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3(m.coarse_ctas, 1, 1);
+        cfg.blockDim = dim3(kCoarseThreads, 1, 1);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = m.coarse_ctas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, coarse_cycle_kernel, ca, ctl);
     }
-    const MGLevelDev& C = m.lv[m.nlev];
-    dense_solve_kernel<<<(C.n * 32 + 255) / 256, 256, 0, s>>>(C.n, m.cinv, C.b, C.x, ctl);
-    ++launches;
-    const double* coarse_out = C.x;
-    // up the CSR levels
-    for (int l = m.nlev - 1; l >= 1; --l) {
-        const MGLevelDev& L = m.lv[l];
-        csr_spmv_kernel<<<blocks_for(L.n), kTPB, 0, s>>>(L.n, L.Prp, L.Pci, L.Pv, coarse_out, L.x, 1, ctl);
-        jac_step_kernel<<<blocks_for(L.n), kTPB, 0, s>>>(L.n, L.Arp, L.Aci, L.Av, L.dinv, L.omega, L.b, L.x, L.t, ctl);
-        coarse_out = L.t;
-        launches += 2;
-    }
-    // back to level 0: prolongate, post-smooth (the last step writes the FP64 z)
-    prolong_q1_kernel<<<blocks_for(rows0), kTPB, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, xa, ctl);
-    ++launches;
+    const float* coarse_out = m.nlev > 1 ? m.lv[1].t : m.lv[1].x;
+    const int rows0 = m.ne * N;
+    prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, xa, ctl);
+    launches += 3;
     for (int k = 0; k < m.nu0; ++k) {
         if (k == m.nu0 - 1) {
-            bj_smooth_kernel<double, N><<<nblk0, tpb, shm, s>>>(m.ne, m.AdT, m.AoT, m.PinvT, m.nbr, w0, r, xa, z,
-                                                             ctl);
+            bj_smooth_kernel<double, N><<<nblk0, tpb, shm, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, z, ctl);
         } else {
-            bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.AdT, m.AoT, m.PinvT, m.nbr, w0, r, xa, xb,
-                                                            ctl);
+            bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, xb, ctl);
             std::swap(xa, xb);
         }
         ++launches;

@@ -232,21 +232,72 @@ __device__ double sum_partials(const double* part, int nblk, double* sh) {
     return s;
 }
 
-__device__ __forceinline__ double spmv_row(const CGArgs& a, const double* v, int e, int i) {
-    return block_row(a.AdT, a.AoT, a.nbr, a.n, v, e, i);
+// same sum over partials written by other blocks of the running kernel (read through L2)
+__device__ double sum_partials_cg(const double* part, int nblk, double* sh) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += __ldcg(part + i);
+    double s = block_sum(v, sh);
+    if (threadIdx.x == 0) sh[32] = s;
+    __syncthreads();
+    s = sh[32];
+    __syncthreads();
+    return s;
+}
+
+// the three partial arrays part[0..nblk), part[nblk..2 nblk), part[2 nblk..3 nblk)
+// summed in one pass (independent loads in flight)
+__device__ void sum3_partials_cg(const double* part, int nblk, double* sh, double& s0, double& s1, double& s2) {
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        const double a0 = __ldcg(part + i), a1 = __ldcg(part + nblk + i), a2 = __ldcg(part + 2 * nblk + i);
+        v0 += a0;
+        v1 += a1;
+        v2 += a2;
+    }
+    s0 = block_sum(v0, sh);
+    s1 = block_sum(v1, sh);
+    s2 = block_sum(v2, sh);
+    if (threadIdx.x == 0) {
+        sh[32] = s0;
+        sh[33] = s1;
+        sh[34] = s2;
+    }
+    __syncthreads();
+    s0 = sh[32];
+    s1 = sh[33];
+    s2 = sh[34];
+    __syncthreads();
+}
+
+// True in the last block of the grid to get here (after its partials are
+// written): that block then reduces all partials.  No block waits.
+__device__ bool last_block(unsigned* ticket) {
+    __shared__ bool am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        am_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
 }
 
 // r = b - A x ; z = P r ; p = z ; partials: rz, rr, bb
-__global__ void cg_init_kernel(CGArgs a) {
+template <int N>
+__global__ void __launch_bounds__(256) cg_init_kernel(CGArgs a) {
     __shared__ double sh[40];
-    extern __shared__ double rs[];
-    const int n = a.n, epb = blockDim.x / n;
+    __shared__ FaceScratch<N, double> sc;
+    __shared__ double rs[256];
+    constexpr int n = N;
+    const int epb = blockDim.x / n;
     const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
     const bool act = e < a.ne;
+    const double ax = faceop_row<N, double, double, double>(a.A, a.x, e, i, act, sc);
     double r = 0.0, bv = 0.0;
     if (act) {
         bv = a.b[(size_t)e * n + i];
-        r = bv - spmv_row(a, a.x, e, i);
+        r = bv - ax;
         a.r[(size_t)e * n + i] = r;
     }
     rs[threadIdx.x] = r;
@@ -269,6 +320,54 @@ __global__ void cg_init_kernel(CGArgs a) {
     }
 }
 
+// dense-operator variants of the two kernels above (runtime n)
+__global__ void cg_init_dense_kernel(CGArgs a) {
+    __shared__ double sh[40];
+    extern __shared__ double rsd[];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    const bool act = e < a.ne;
+    double r = 0.0, bv = 0.0;
+    if (act) {
+        bv = a.b[(size_t)e * n + i];
+        r = bv - dense_block_row(a.AdT_dense, a.AoT_dense, a.nbr_dense, n, a.x, e, i);
+        a.r[(size_t)e * n + i] = r;
+    }
+    rsd[threadIdx.x] = r;
+    __syncthreads();
+    double z = 0.0;
+    if (act) {
+        const double* P = a.PinvT + (size_t)e * n * n + i;
+        const double* re = rsd + (threadIdx.x / n) * n;
+        for (int j = 0; j < n; ++j) z += P[(size_t)j * n] * re[j];
+        a.z[(size_t)e * n + i] = z;
+        a.p[(size_t)e * n + i] = z;
+    }
+    double s0 = block_sum(r * z, sh);
+    double s1 = block_sum(r * r, sh);
+    double s2 = block_sum(bv * bv, sh);
+    if (threadIdx.x == 0) {
+        a.part[blockIdx.x] = s0;
+        a.part[a.nblk + blockIdx.x] = s1;
+        a.part[2 * a.nblk + blockIdx.x] = s2;
+    }
+}
+
+__global__ void cg_spmv_dense_kernel(CGArgs a) {
+    if (*(volatile int*)a.ctl) return;
+    __shared__ double sh[40];
+    const int n = a.n, epb = blockDim.x / n;
+    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    double pq = 0.0;
+    if (e < a.ne) {
+        const double qv = dense_block_row(a.AdT_dense, a.AoT_dense, a.nbr_dense, n, a.p, e, i);
+        a.q[(size_t)e * n + i] = qv;
+        pq = qv * a.p[(size_t)e * n + i];
+    }
+    double s = block_sum(pq, sh);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = s;
+}
+
 __global__ void cg_init_scalars_kernel(CGArgs a, double tol2, int max_iters) {
     __shared__ double sh[40];
     double rz = sum_partials(a.part, a.nblk, sh);
@@ -287,14 +386,17 @@ __global__ void cg_init_scalars_kernel(CGArgs a, double tol2, int max_iters) {
 }
 
 // q = A p ; partial p.q
-__global__ void cg_spmv_kernel(CGArgs a) {
+template <int N>
+__global__ void __launch_bounds__(256) cg_spmv_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
     __shared__ double sh[40];
-    const int n = a.n, epb = blockDim.x / n;
+    __shared__ FaceScratch<N, double> sc;
+    constexpr int n = N;
+    const int epb = blockDim.x / n;
     const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    const double qv = faceop_row<N, double, double, double>(a.A, a.p, e, i, e < a.ne, sc);
     double pq = 0.0;
     if (e < a.ne) {
-        const double qv = spmv_row(a, a.p, e, i);
         a.q[(size_t)e * n + i] = qv;
         pq = qv * a.p[(size_t)e * n + i];
     }
@@ -372,14 +474,18 @@ __global__ void cg_direction_kernel(CGArgs a) {
 
 // ---- CG with an external preconditioner (multigrid) ----
 // r = b - A x ; partials rr -> part[nblk], bb -> part[2 nblk]
-__global__ void cgx_init_r_kernel(CGArgs a) {
+template <int N>
+__global__ void __launch_bounds__(256) cgx_init_r_kernel(CGArgs a) {
     __shared__ double sh[40];
-    const int n = a.n, epb = blockDim.x / n;
+    __shared__ FaceScratch<N, double> sc;
+    constexpr int n = N;
+    const int epb = blockDim.x / n;
     const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    const double ax = faceop_row<N, double, double, double>(a.A, a.x, e, i, e < a.ne, sc);
     double r = 0.0, bv = 0.0;
     if (e < a.ne) {
         bv = a.b[(size_t)e * n + i];
-        r = bv - spmv_row(a, a.x, e, i);
+        r = bv - ax;
         a.r[(size_t)e * n + i] = r;
     }
     double s1 = block_sum(r * r, sh);
@@ -411,44 +517,25 @@ template <int N>
 __global__ void __launch_bounds__(256) cgx_spmv_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
     __shared__ double sh[40];
+    __shared__ FaceScratch<N, double> sc;
     const int epb = blockDim.x / N;
     const int e = blockIdx.x * epb + threadIdx.x / N, i = threadIdx.x % N;
+    const double qv = faceop_row<N, double, double, double>(a.A, a.p, e, i, e < a.ne, sc);
     double pq = 0.0;
     if (e < a.ne) {
-        const double qv = block_row_n<N, double, double, double>(a.AdT, a.AoT, a.nbr, a.p, e, i);
         a.q[(size_t)e * N + i] = qv;
         pq = qv * a.p[(size_t)e * N + i];
     }
     double s = block_sum(pq, sh);
     if (threadIdx.x == 0) a.part[blockIdx.x] = s;
-}
-
-// single-block reductions of the per-block partials (deterministic order).
-// stage 0: alpha = rz / pq -> scal[5].  stage 1: dz, rz_new, rr; beta = dz / rz
-// -> scal[6]; rz, rr updated; iteration count and convergence in ctl.
-__global__ void cgx_reduce_kernel(CGArgs a, int stage) {
-    if (*(volatile int*)a.ctl) return;
-    __shared__ double sh[40];
-    if (stage == 0) {
-        const double pq = sum_partials(a.part, a.nblk, sh);
+    // last block: alpha = rz / pq -> scal[5]
+    if (last_block((unsigned*)(a.ctl + 5))) {
+        const double pq_all = sum_partials_cg(a.part, a.nblk, sh);
         if (threadIdx.x == 0) {
-            a.scal[1] = pq;
-            a.scal[5] = a.scal[0] / pq;
+            a.scal[1] = pq_all;
+            a.scal[5] = a.scal[0] / pq_all;
+            a.ctl[5] = 0;
         }
-        return;
-    }
-    const double dz = sum_partials(a.part, a.nblk, sh);
-    const double rz_new = sum_partials(a.part + a.nblk, a.nblk, sh);
-    const double rr = sum_partials(a.part + 2 * a.nblk, a.nblk, sh);
-    if (threadIdx.x == 0) {
-        a.scal[6] = dz / a.scal[0];
-        a.scal[0] = rz_new;
-        a.scal[2] = rr;
-        const int it = a.ctl[1] + 1;
-        a.ctl[1] = it;
-        const bool bad = !(isfinite(rz_new) && isfinite(rr) && isfinite(dz));
-        if (bad) a.ctl[3] = 1;
-        if (rr <= a.scal[4] || it >= a.ctl[2] || bad) a.ctl[0] = 1;
     }
 }
 
@@ -490,6 +577,22 @@ __global__ void cgx_rz_kernel(CGArgs a) {
     if (threadIdx.x == 0) {
         a.part[a.nblk + blockIdx.x] = s;
         a.part[blockIdx.x] = t;
+    }
+    // last block: beta = (r - r_old).z / rz_old -> scal[6]; rz, rr; count and convergence
+    if (last_block((unsigned*)(a.ctl + 6))) {
+        double dz_all, rz_new, rr;
+        sum3_partials_cg(a.part, a.nblk, sh, dz_all, rz_new, rr);
+        if (threadIdx.x == 0) {
+            a.scal[6] = dz_all / a.scal[0];
+            a.scal[0] = rz_new;
+            a.scal[2] = rr;
+            const int it = a.ctl[1] + 1;
+            a.ctl[1] = it;
+            const bool bad = !(isfinite(rz_new) && isfinite(rr) && isfinite(dz_all));
+            if (bad) a.ctl[3] = 1;
+            if (rr <= a.scal[4] || it >= a.ctl[2] || bad) a.ctl[0] = 1;
+            a.ctl[6] = 0;
+        }
     }
 }
 
@@ -540,15 +643,27 @@ __global__ void diff_final_kernel(int nblk, const double* part, double* out) {
 
 }  // namespace
 
+#define SMM_DISPATCH_N(n, KERNEL, ...)                          \
+    switch (n) {                                                \
+        case 4: KERNEL<4><<<__VA_ARGS__>>>(a); break;           \
+        case 9: KERNEL<9><<<__VA_ARGS__>>>(a); break;           \
+        case 16: KERNEL<16><<<__VA_ARGS__>>>(a); break;         \
+        default: KERNEL<25><<<__VA_ARGS__>>>(a); break;         \
+    }
+
 void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s) {
     const int tpb = cg_threads_per_block(a.n);
-    cg_init_kernel<<<a.nblk, tpb, tpb * sizeof(double), s>>>(a);
+    if (a.AoT_dense) {
+        cg_init_dense_kernel<<<a.nblk, tpb, tpb * sizeof(double), s>>>(a);
+    } else {
+        SMM_DISPATCH_N(a.n, cg_init_kernel, a.nblk, tpb, 0, s)
+    }
     cg_init_scalars_kernel<<<1, 256, 0, s>>>(a, tol * tol, max_iters);
 }
 
 int cgx_start(const CGArgs& a, double tol, int max_iters, const MGPlan& mg, cudaStream_t s) {
     const int tpb = cg_threads_per_block(a.n);
-    cgx_init_r_kernel<<<a.nblk, tpb, 0, s>>>(a);
+    SMM_DISPATCH_N(a.n, cgx_init_r_kernel, a.nblk, tpb, 0, s)
     const int l = mg_apply(mg, a.r, a.z, nullptr, s);
     cgx_init_p_kernel<<<a.nblk, tpb, 0, s>>>(a);
     cg_init_scalars_kernel<<<1, 256, 0, s>>>(a, tol * tol, max_iters);
@@ -559,19 +674,12 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
     const int tpb = cg_threads_per_block(a.n);
     int launches = 0;
     for (int k = 0; k < count; ++k) {
-        switch (a.n) {
-            case 4: cgx_spmv_kernel<4><<<a.nblk, tpb, 0, s>>>(a); break;
-            case 9: cgx_spmv_kernel<9><<<a.nblk, tpb, 0, s>>>(a); break;
-            case 16: cgx_spmv_kernel<16><<<a.nblk, tpb, 0, s>>>(a); break;
-            default: cgx_spmv_kernel<25><<<a.nblk, tpb, 0, s>>>(a); break;
-        }
-        cgx_reduce_kernel<<<1, 256, 0, s>>>(a, 0);
+        SMM_DISPATCH_N(a.n, cgx_spmv_kernel, a.nblk, tpb, 0, s)
         cgx_update_kernel<<<a.nblk, tpb, 0, s>>>(a);
-        launches += 3 + mg_apply(mg, a.r, a.z, a.ctl, s);
+        launches += 2 + mg_apply(mg, a.r, a.z, a.ctl, s);
         cgx_rz_kernel<<<a.nblk, tpb, 0, s>>>(a);
-        cgx_reduce_kernel<<<1, 256, 0, s>>>(a, 1);
         cgx_direction_kernel<<<a.nblk, tpb, 0, s>>>(a);
-        launches += 3;
+        launches += 2;
     }
     return launches;
 }
@@ -579,7 +687,11 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
 void cg_iterations(const CGArgs& a, int count, cudaStream_t s) {
     const int tpb = cg_threads_per_block(a.n);
     for (int k = 0; k < count; ++k) {
-        cg_spmv_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        if (a.AoT_dense) {
+            cg_spmv_dense_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        } else {
+            SMM_DISPATCH_N(a.n, cg_spmv_kernel, a.nblk, tpb, 0, s)
+        }
         cg_update_kernel<<<a.nblk, tpb, tpb * sizeof(double), s>>>(a);
         cg_direction_kernel<<<a.nblk, tpb, 0, s>>>(a);
     }

@@ -68,10 +68,10 @@ extern "C" smm_status smm_block_pcg_noalloc(int32_t n_elem, int32_t n, const dou
     a.nrow = (int)rows;
     const int epb = smm::cg_threads_per_block(n) / n;
     a.nblk = (n_elem + epb - 1) / epb;
-    a.AdT = diag_blocks;
-    a.AoT = off_blocks;
+    a.AdT_dense = diag_blocks;
+    a.AoT_dense = off_blocks;
+    a.nbr_dense = nbr;
     a.PinvT = pinv_blocks;
-    a.nbr = nbr;
     a.x = x;
     a.r = d;
     a.z = d + kMaxRows;

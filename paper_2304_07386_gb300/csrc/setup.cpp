@@ -178,6 +178,88 @@ struct FaceData {
     double length = 0.0;
 };
 
+// Factor every neighbour block of the moment operator through the face data
+// of the two elements.  With nodal Gauss-Lobatto bases the trace of u on a
+// face is its p+1 face-node values, and the physical gradient there depends
+// only on the trace and on the reference normal derivative, whose values at
+// the face nodes are sum_t l'_t(0) u(line t).  So Aoff = E_f^T C E_f2 with a
+// 2(p+1) x 2(p+1) matrix C, computed here as R_f^T Aoff R_f2 from right
+// inverses (E R = I) and checked by rebuilding Aoff.
+int factor_face_blocks(Setup& s, std::string& err) {
+    const int n = s.n, p = s.p, p1 = s.p1, G = 2 * p1, ne = s.ne;
+    Lag1D L;
+    L.nodes = gauss_lobatto01(p1).x;
+    std::vector<double> v(p1), d(p1);
+    L.eval(0.0, v.data(), d.data());
+    s.wd.assign(d.begin(), d.end());
+    if (std::fabs(s.wd[1]) < 1e-12) { err = "degenerate face derivative"; return 4; }
+    // R_f columns: trace a -> e_(a,0) - wd0/wd1 e_(a,1); derivative a -> e_(a,1) / wd1
+    auto rcols = [&](int f, std::vector<double>& R) {  // R [n][G]
+        R.assign((size_t)n * G, 0.0);
+        for (int a = 0; a < p1; ++a) {
+            const int n0 = face_line_node(p, f, a, 0), n1 = face_line_node(p, f, a, 1);
+            R[(size_t)n0 * G + a] = 1.0;
+            R[(size_t)n1 * G + a] = -s.wd[0] / s.wd[1];
+            R[(size_t)n1 * G + p1 + a] = 1.0 / s.wd[1];
+        }
+    };
+    std::vector<double> Rf[4];
+    for (int f = 0; f < 4; ++f) rcols(f, Rf[f]);
+    s.Cface.assign((size_t)ne * 4 * G * G, 0.0);
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int e = 0; e < ne; ++e) {
+        std::vector<double> T((size_t)n * G), Rb((size_t)n * n);
+        for (int f = 0; f < 4; ++f) {
+            if (s.nbr[e * 4 + f] < 0) continue;
+            const int f2 = s.nbr_face[e * 4 + f];
+            const double* A = &s.Aoff[((size_t)e * 4 + f) * n * n];
+            const std::vector<double>& R1 = Rf[f];
+            const std::vector<double>& R2 = Rf[f2];
+            double* C = &s.Cface[((size_t)e * 4 + f) * G * G];
+            // T = A R2 (n x G); C = R1^T T
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < G; ++c) {
+                    double acc = 0.0;
+                    for (int j = 0; j < n; ++j) acc += A[(size_t)i * n + j] * R2[(size_t)j * G + c];
+                    T[(size_t)i * G + c] = acc;
+                }
+            for (int r = 0; r < G; ++r)
+                for (int c = 0; c < G; ++c) {
+                    double acc = 0.0;
+                    for (int i = 0; i < n; ++i) acc += R1[(size_t)i * G + r] * T[(size_t)i * G + c];
+                    C[r * G + c] = acc;
+                }
+            // rebuild E_f^T C E_f2 and compare
+            std::fill(Rb.begin(), Rb.end(), 0.0);
+            for (int r = 0; r < G; ++r)
+                for (int c = 0; c < G; ++c) {
+                    const double cv = C[r * G + c];
+                    if (cv == 0.0) continue;
+                    const int a = r % p1, b = c % p1;
+                    for (int t = 0; t < p1; ++t) {
+                        if (r < p1 && t > 0) break;
+                        const double er = r < p1 ? 1.0 : s.wd[t];
+                        const int ni = face_line_node(p, f, a, t);
+                        for (int u = 0; u < p1; ++u) {
+                            if (c < p1 && u > 0) break;
+                            const double ec = c < p1 ? 1.0 : s.wd[u];
+                            Rb[(size_t)ni * n + face_line_node(p, f2, b, u)] += er * cv * ec;
+                        }
+                    }
+                }
+            double amax = 0.0, dmax = 0.0;
+            for (size_t ij = 0; ij < (size_t)n * n; ++ij) {
+                amax = std::max(amax, std::fabs(A[ij]));
+                dmax = std::max(dmax, std::fabs(A[ij] - Rb[ij]));
+            }
+            if (dmax > 1e-11 * amax) bad += 1;
+        }
+    }
+    if (bad) { err = "neighbour block of the moment operator is not face-factorable"; return 4; }
+    return 0;
+}
+
 }  // namespace
 
 Rule1D gauss_legendre01(int n) {
@@ -618,6 +700,7 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
         if (!invert(n, Ad, &s.Pinv[(size_t)e * n * n])) sing += 1;
     }
     if (sing) { err = "singular diagonal block of the moment operator"; return 4; }
+    if (int rc = factor_face_blocks(s, err)) return rc;
 
     // ---- fixed right-hand side: Q_0, Q_1 and J_in terms of Eq. ipsmm ----
     // Q_0 = sum_d w_d q_d, Q_1 = sum_d w_d Omega_d q_d (nodal)

@@ -63,12 +63,29 @@ struct Setup {
     std::vector<double> b_eb0;                    // [nb][nfq]
     // moment system
     std::vector<double> Adiag, Aoff, Pinv;        // [ne][n][n], [ne][4][n][n], [ne][n][n]
+    // Face-factored neighbour blocks: Aoff[e][f] = E_f^T Cface[e][f] E_f2 with
+    // E_f (2(p+1) x n) = [trace at the p+1 face nodes; reference derivative
+    // sum_t wd[t] u(line t) along the p+1 node lines normal to face f]
+    std::vector<double> Cface;                    // [ne][4][2p1][2p1], row = own face datum
+    std::vector<double> wd;                       // [p1]: l'_t(0) of the 1D GLL basis
     std::vector<double> Kxx, Ks, Kyy;             // [ne][n][n], scaled by -1/sigma_t
     std::vector<double> Dfx, Dfy;                 // [ne][4][nfq][n]
     std::vector<double> nds;                      // [ne][4][nfq][2]
     std::vector<double> bfixed;                   // [ne][n]
     std::vector<double> hK, area;
 };
+
+// Node of element-local index (face f, face position a, line position t):
+// t = 0 is the face node, t grows into the element.
+inline int face_line_node(int p, int f, int a, int t) {
+    const int k = p + 1;
+    switch (f) {
+        case 0: return t * k + a;
+        case 1: return a * k + p - t;
+        case 2: return (p - t) * k + a;
+        default: return a * k + t;
+    }
+}
 
 // Status codes match smm_status in include/smm.h.
 int build_setup(const Input& in, Setup& s, std::string& err);

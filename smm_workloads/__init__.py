@@ -323,7 +323,7 @@ def linear_aniso_grad_psi(x, y, ox, oy):
 
 
 # ---------------------------------------------------------------------------
-# Learned-guess workload (BASELINE configs[4] shape)
+# Learned-guess workload: log-normal cross sections, piecewise-constant sources
 # ---------------------------------------------------------------------------
 
 def learned_guess_problem(nx: int, seed: int, blocks: int = 8):
