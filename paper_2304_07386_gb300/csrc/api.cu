@@ -79,6 +79,8 @@ struct smm_ctx {
     double *bfixed = nullptr, *trace = nullptr, *rhs = nullptr;
     // moment operator and CG
     double *AdT = nullptr, *CT = nullptr, *PinvT = nullptr;   // diagonal blocks, face couplings, inverses
+    float2 *AdT2 = nullptr, *CT2 = nullptr;                    // the same as FP32 pairs (flexible-CG product)
+    float2* p2 = nullptr;                                       // CG direction as FP32 pairs
     double wd[5] = {0, 0, 0, 0, 0};
     double *r = nullptr, *z = nullptr, *pv = nullptr, *qv = nullptr, *part = nullptr, *scal = nullptr;
     double *phi_prev = nullptr, *dpart = nullptr, *dout = nullptr;
@@ -134,6 +136,16 @@ bool upload_f32(smm_ctx* h, float*& dst, const std::vector<T>& src) {
 }
 
 // transpose each n x n block ([blk][i][j] -> [blk][j][i])
+// FP32 pairs (hi, lo) with hi + lo = v to 2^-48
+std::vector<float2> to_pairs(const std::vector<double>& v) {
+    std::vector<float2> out(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        const float hi = (float)v[i];
+        out[i] = make_float2(hi, (float)(v[i] - (double)hi));
+    }
+    return out;
+}
+
 std::vector<double> transpose_blocks(const std::vector<double>& a, int n) {
     std::vector<double> t(a.size());
     const size_t nb = a.size() / ((size_t)n * n);
@@ -238,8 +250,10 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     {
         std::vector<double> t = transpose_blocks(s.Adiag, s.n);
         ok &= upload(h, h->AdT, t);
+        ok &= upload(h, h->AdT2, to_pairs(t));
         t = transpose_blocks(s.Cface, 2 * s.p1);
         ok &= upload(h, h->CT, t);
+        ok &= upload(h, h->CT2, to_pairs(t));
         for (int k = 0; k < s.p1; ++k) h->wd[k] = s.wd[k];
         t = transpose_blocks(s.Pinv, s.n);
         ok &= upload(h, h->PinvT, t);
@@ -268,6 +282,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->z = h->alloc<double>(nphi);
     h->pv = h->alloc<double>(nphi);
     h->qv = h->alloc<double>(nphi);
+    h->p2 = h->alloc<float2>(nphi);
     h->phi_prev = h->alloc<double>(nphi);
     const int epb = smm::cg_threads_per_block(s.n) / s.n;
     h->cg_nblk = (s.ne + epb - 1) / epb;
@@ -278,7 +293,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->dout = h->alloc<double>(2);
     h->nonfinite = h->alloc<int>(1);
     if (!h->psi || !h->done || !h->ticket || !h->err || !h->mom || !h->beta || !h->trace || !h->rhs || !h->r || !h->z ||
-        !h->pv || !h->qv || !h->phi_prev || !h->part || !h->scal || !h->ctl || !h->dpart || !h->dout || !h->nonfinite)
+        !h->pv || !h->qv || !h->p2 || !h->phi_prev || !h->part || !h->scal || !h->ctl || !h->dpart || !h->dout || !h->nonfinite)
         return bail(SMM_ERR_OOM, "device allocation failed");
     if (cudaMemsetAsync(h->psi, 0, nang * sizeof(double), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->done, 0, (size_t)s.ne * s.nd * sizeof(unsigned), h->stream) != cudaSuccess ||
@@ -526,6 +541,12 @@ smm::CGArgs cg_args(smm_handle h, double* x) {
     a.ne = h->ne; a.n = h->n; a.nrow = h->ne * h->n; a.nblk = h->cg_nblk;
     a.A.AdT = h->AdT; a.A.CT = h->CT; a.A.nbr = h->nbr; a.A.nface = h->nbr_face;
     for (int k = 0; k < 5; ++k) a.A.wd[k] = h->wd[k];
+    a.A2.AdT = h->AdT2; a.A2.CT = h->CT2; a.A2.nbr = h->nbr; a.A2.nface = h->nbr_face;
+    for (int k = 0; k < 5; ++k) {
+        const float hi = (float)h->wd[k];
+        a.A2.wd[k] = make_float2(hi, (float)(h->wd[k] - (double)hi));
+    }
+    a.p2 = h->p2;
     a.PinvT = h->PinvT;
     a.x = x; a.r = h->r; a.z = h->z; a.p = h->pv; a.q = h->qv; a.rold = h->rold; a.b = h->rhs; a.part = h->part;
     a.scal = h->scal;

@@ -4,6 +4,7 @@
 // 256 / n elements of n rows each.
 #pragma once
 
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace smm {
@@ -110,6 +111,101 @@ __device__ __forceinline__ AT faceop_row(const FaceOp<T>& op, const VT* __restri
         }
     }
     return y;
+}
+
+template <int N>
+struct FaceScratchDF {
+    float2 g[FaceDims<N>::EPB * FaceDims<N>::NG];
+    float2 w[FaceDims<N>::EPB * FaceDims<N>::NG];
+};
+
+// faceop_row with the operator and x as FP32 pairs, pair arithmetic
+// throughout (see dfloat.cuh); the row value is returned in FP64
+template <int N>
+__device__ __forceinline__ double faceop_row_df(const FaceOpDF& op, const float2* __restrict__ x, int e, int i,
+                                                bool act, FaceScratchDF<N>& sc) {
+    using D = FaceDims<N>;
+    constexpr int P1 = D::P1, G = D::G, NG = D::NG;
+    const int le = threadIdx.x / N;
+    float ys = 0.0f, yc = 0.0f;
+    if (act) {
+        const float2* Ad = op.AdT + (size_t)e * N * N + i;
+        const float2* xe = x + (size_t)e * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const float2 a = Ad[j * N], v = xe[j];
+            df_acc(ys, yc, a.x, a.y, v.x, v.y);
+        }
+#pragma unroll
+        for (int v0 = 0; v0 < NG; v0 += N) {
+            const int v = v0 + i;
+            if (v < NG) {
+                const int f = v / G, r = v - f * G;
+                const int e2 = op.nbr[e * 4 + f];
+                float2 g = make_float2(0.0f, 0.0f);
+                if (e2 >= 0) {
+                    const int f2 = op.nface[e * 4 + f];
+                    const float2* x2 = x + (size_t)e2 * N;
+                    if (r < P1) {
+                        g = x2[line_node<P1>(f2, r, 0)];
+                    } else {
+                        const int a = r - P1;
+                        float gs = 0.0f, gc = 0.0f;
+#pragma unroll
+                        for (int t = 0; t < P1; ++t) {
+                            const float2 xv = x2[line_node<P1>(f2, a, t)];
+                            df_acc(gs, gc, op.wd[t].x, op.wd[t].y, xv.x, xv.y);
+                        }
+                        g = df_norm(gs, gc);
+                    }
+                }
+                sc.g[le * NG + v] = g;
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int v0 = 0; v0 < NG; v0 += N) {
+            const int v = v0 + i;
+            if (v < NG) {
+                const int f = v / G, r = v - f * G;
+                float ws = 0.0f, wc = 0.0f;
+                if (op.nbr[e * 4 + f] >= 0) {
+                    const float2* C = op.CT + ((size_t)(e * 4 + f) * G) * G + r;
+                    const float2* g = sc.g + le * NG + f * G;
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        const float2 cv = C[c * G], gv = g[c];
+                        df_acc(ws, wc, cv.x, cv.y, gv.x, gv.y);
+                    }
+                }
+                sc.w[le * NG + v] = df_norm(ws, wc);
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+        constexpr int p = P1 - 1;
+        const int ix = i % P1, iy = i / P1;
+        const float2* w = sc.w + le * NG;
+        const int fa[4] = {ix, iy, ix, iy};
+        const int ft[4] = {iy, p - ix, p - iy, ix};
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            float2 cf = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int t = 0; t < P1; ++t)
+                if (t == ft[f]) cf = op.wd[t];
+            const float2 wv = w[f * G + P1 + fa[f]];
+            df_acc(ys, yc, cf.x, cf.y, wv.x, wv.y);
+            if (ft[f] == 0) {
+                const float2 wt = w[f * G + fa[f]];
+                df_add(ys, yc, wt.x, wt.y);
+            }
+        }
+    }
+    return df_to_double(ys, yc);
 }
 
 // (A v)_i with dense column-major neighbour blocks (runtime n)

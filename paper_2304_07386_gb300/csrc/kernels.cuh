@@ -119,10 +119,21 @@ struct FaceOp {
     T wd[5] = {};                    // l'_t(0) of the 1D Gauss-Lobatto basis, t < p+1
 };
 
+// the same operator with every entry stored as an FP32 pair (hi, lo)
+struct FaceOpDF {
+    const float2* AdT = nullptr;
+    const float2* CT = nullptr;
+    const int32_t* nbr = nullptr;
+    const int32_t* nface = nullptr;
+    float2 wd[5] = {};
+};
+
 // block-Jacobi PCG
 struct CGArgs {
     int ne, n, nrow, nblk;     // nblk: blocks of the row kernels
     FaceOp<double> A;          // operator (FP64)
+    FaceOpDF A2;               // operator as FP32 pairs (flexible-CG product), AdT == nullptr if absent
+    float2* p2;                // flexible CG: the direction p as FP32 pairs, kept with p
     // dense alternative (caller-provided blocks, any n <= 64): used when AoT_dense is set
     const double* AdT_dense;   // [ne][n][n] transposed
     const double* AoT_dense;   // [ne][4][n][n] transposed

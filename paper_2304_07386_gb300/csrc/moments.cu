@@ -506,6 +506,7 @@ __global__ void cgx_init_p_kernel(CGArgs a) {
         const size_t o = (size_t)e * n + i;
         const double z = a.z[o];
         a.p[o] = z;
+        a.p2[o] = df_make(z);
         rz = z * a.r[o];
     }
     double s = block_sum(rz, sh);
@@ -517,10 +518,10 @@ template <int N>
 __global__ void __launch_bounds__(256) cgx_spmv_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
     __shared__ double sh[40];
-    __shared__ FaceScratch<N, double> sc;
+    __shared__ FaceScratchDF<N> sc;
     const int epb = blockDim.x / N;
     const int e = blockIdx.x * epb + threadIdx.x / N, i = threadIdx.x % N;
-    const double qv = faceop_row<N, double, double, double>(a.A, a.p, e, i, e < a.ne, sc);
+    const double qv = faceop_row_df<N>(a.A2, a.p2, e, i, e < a.ne, sc);
     double pq = 0.0;
     if (e < a.ne) {
         a.q[(size_t)e * N + i] = qv;
@@ -604,7 +605,9 @@ __global__ void cgx_direction_kernel(CGArgs a) {
     const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
     if (e < a.ne) {
         const size_t o = (size_t)e * n + i;
-        a.p[o] = a.z[o] + beta * a.p[o];
+        const double pn = a.z[o] + beta * a.p[o];
+        a.p[o] = pn;
+        a.p2[o] = df_make(pn);
     }
 }
 

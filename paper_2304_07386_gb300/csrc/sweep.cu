@@ -16,6 +16,7 @@
 // with release semantics after its outputs are written.
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace smm {
@@ -64,31 +65,6 @@ __device__ __forceinline__ int face_node(int f, int a) {
 
 template <typename T> __device__ __forceinline__ T ldg_cg(const T* p) { return __ldcg(p); }
 
-// ---- FP32-pair ("double-float") arithmetic for the FP64 cached sweep ----
-// A value is hi + lo with |lo| <= ulp(hi)/2.  GB300 runs FP32 FMAs about 60x
-// faster than FP64 ones, so the n-term product with the cached inverse is
-// done as a compensated dot product on FP32 pairs: each product's rounding
-// error is recovered exactly with an FMA (Dekker's product), the running sum's
-// with Knuth's TwoSum, and the errors are accumulated separately (the
-// Ogita-Rump-Oishi Dot2 scheme extended to pair inputs).  The result agrees
-// with FP64 to ~1e-14 relative for these well-conditioned local solves.
-__device__ __forceinline__ void df_split(double v, float& hi, float& lo) {
-    hi = __double2float_rn(v);
-    lo = __double2float_rn(v - (double)hi);
-}
-
-// (s, c) += (ah + al) * (xh + xl), the al * xl term dropped (2^-48 relative)
-__device__ __forceinline__ void df_acc(float& s, float& c, float ah, float al, float xh, float xl) {
-    const float ph = __fmul_rn(ah, xh);
-    float t = __fmaf_rn(ah, xh, -ph);  // exact rounding error of ah * xh
-    t = __fmaf_rn(ah, xl, t);
-    t = __fmaf_rn(al, xh, t);
-    const float sn = __fadd_rn(s, ph);  // TwoSum(s, ph)
-    const float bp = __fsub_rn(sn, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bp)), __fsub_rn(ph, bp));
-    c = __fadd_rn(c, __fadd_rn(err, t));
-    s = sn;
-}
 
 }  // namespace
 
