@@ -108,6 +108,9 @@ typedef struct {
                                    max|G(x0)|, the first residual of the zero
                                    guess being max|G(0)| ~ max|G(x0)|), restart
                                    from zero (default 0) */
+    int32_t mg_smooth_steps;    /* multigrid preconditioner: damped block-Jacobi
+                                   steps on the DG level before and after the
+                                   coarse correction, 1..4 (default 2) */
 } smm_options;
 
 typedef struct {

@@ -174,6 +174,7 @@ void smm_default_options(smm_options* opt) {
     opt->sweep_solver = SMM_SOLVER_CACHED_INVERSE;
     opt->anderson_depth = 0;
     opt->guess_check = 0;
+    opt->mg_smooth_steps = 2;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -207,7 +208,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0) ||
         (o.precond != SMM_PRECOND_BLOCK_JACOBI && o.precond != SMM_PRECOND_MULTIGRID) ||
         (o.sweep_solver != SMM_SOLVER_LU && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) || o.anderson_depth < 0 ||
-        o.anderson_depth > 5)
+        o.anderson_depth > 5 || o.mg_smooth_steps < 1 || o.mg_smooth_steps > 4)
         return fail(SMM_ERR_INVALID_ARG, "bad options");
 
     smm::Input in;
@@ -324,7 +325,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         if ((int)H.lv.size() - 1 > 11) return bail(SMM_ERR_MESH, "multigrid: too many levels");
         smm::MGPlan& P = h->mg;
         P.enabled = true;
-        P.ne = s.ne; P.n = s.n; P.nu0 = 2; P.omega0 = H.omega0;
+        P.ne = s.ne; P.n = s.n; P.nu0 = o.mg_smooth_steps; P.omega0 = H.omega0;
         {
             float *ad32 = nullptr, *c32 = nullptr, *pi32 = nullptr;
             ok &= upload_f32(h, ad32, transpose_blocks(s.Adiag, s.n));
@@ -357,6 +358,13 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
                       upload_f32(h, dv, L.dinv);
                 ok &= upload(h, prp, L.P.rp) && upload(h, pci, L.P.ci) && upload_f32(h, pv, L.P.v);
                 ok &= upload(h, rrp, L.R.rp) && upload(h, rci, L.R.ci) && upload_f32(h, rv, L.R.v);
+                std::vector<double> asv(L.A.v.size());
+                for (int i = 0; i < L.A.nrow; ++i)
+                    for (int k = L.A.rp[i]; k < L.A.rp[i + 1]; ++k)
+                        asv[k] = L.A.v[k] * L.omega * L.dinv[L.A.ci[k]];
+                float* asd = nullptr;
+                ok &= upload_f32(h, asd, asv);
+                D.Asv = asd;
                 D.Arp = arp; D.Aci = aci; D.Av = av; D.dinv = dv; D.Prp = prp; D.Pci = pci; D.Pv = pv;
                 D.Rrp = rrp; D.Rci = rci; D.Rv = rv;
             }

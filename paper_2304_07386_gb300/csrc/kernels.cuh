@@ -154,6 +154,7 @@ struct CGArgs {
 struct MGLevelDev {
     int n = 0;                                   // unknowns on this level
     const int* Arp = nullptr; const int* Aci = nullptr; const float* Av = nullptr;
+    const float* Asv = nullptr;                  // A diag(omega dinv): the values of A scaled by column
     const float* dinv = nullptr;
     float omega = 0.0f;
     const int* Prp = nullptr; const int* Pci = nullptr; const float* Pv = nullptr;  // from level l+1

@@ -115,30 +115,42 @@ struct CoarseArgs {
     const float* cinv;
 };
 
-// sum_k v[k] x[ci[k]] over row i, loads issued eight entries at a time
-__device__ __forceinline__ float csr_row_f(const int* __restrict__ rp, const int* __restrict__ ci,
-                                           const float* __restrict__ v, const float* x, int i) {
-    int k = rp[i];
-    const int ke = rp[i + 1];
-    float s0 = 0.0f, s1 = 0.0f;
-    for (; k + 8 <= ke; k += 8) {
-        int c[8];
-        float w[8], xv[8];
+// rows i and j (j < 0: none) of a CSR matrix times x, with the loads of the two
+// rows interleaved so a thread holding two rows waits about as long as one
+__device__ __forceinline__ void csr_row2_f(const int* __restrict__ rp, const int* __restrict__ ci,
+                                           const float* __restrict__ v, const float* x, int i, int j, float& si,
+                                           float& sj) {
+    int ki = rp[i], kj = j >= 0 ? rp[j] : 0;
+    const int ei = rp[i + 1], ej = j >= 0 ? rp[j + 1] : 0;
+    float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+    while (ki < ei || kj < ej) {
+        int c[8], d[8];
+        float w[8], u[8], xv[8], yv[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            c[u] = ci[k + u];
-            w[u] = v[k + u];
+        for (int q = 0; q < 8; ++q) {
+            const bool oi = ki + q < ei, oj = kj + q < ej;
+            c[q] = oi ? ci[ki + q] : 0;
+            w[q] = oi ? v[ki + q] : 0.0f;
+            d[q] = oj ? ci[kj + q] : 0;
+            u[q] = oj ? v[kj + q] : 0.0f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) xv[u] = __ldcg(x + c[u]);
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-            s0 = fmaf(w[u], xv[u], s0);
-            s1 = fmaf(w[u + 1], xv[u + 1], s1);
+        for (int q = 0; q < 8; ++q) {
+            xv[q] = ki + q < ei ? __ldcg(x + c[q]) : 0.0f;
+            yv[q] = kj + q < ej ? __ldcg(x + d[q]) : 0.0f;
         }
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            a0 = fmaf(w[q], xv[q], a0);
+            a1 = fmaf(w[q + 1], xv[q + 1], a1);
+            b0 = fmaf(u[q], yv[q], b0);
+            b1 = fmaf(u[q + 1], yv[q + 1], b1);
+        }
+        ki += 8;
+        kj += 8;
     }
-    for (; k < ke; ++k) s0 = fmaf(v[k], __ldcg(x + ci[k]), s0);
-    return s0 + s1;
+    si = a0 + a1;
+    sj = b0 + b1;
 }
 
 // launched as one cluster of gridDim.x CTAs (8, or 16 where the GPU allows it)
@@ -157,15 +169,33 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
         }
     }
     cl.sync();
-    // down: x = omega dinv b ; r = b - A x ; b_{l+1} = R r
+    // down: x = omega dinv b ; r = b - A x ; b_{l+1} = R r.  The residual is
+    // formed as b - As b with As = A diag(omega dinv) (stored), so x and r come
+    // out of one pass over b.
     for (int l = 1; l < a.nlev; ++l) {
         const MGLevelDev& L = a.lv[l];
-        for (int i = tid; i < L.n; i += T) L.x[i] = L.omega * L.dinv[i] * __ldcg(L.b + i);
-        cl.sync();
-        for (int i = tid; i < L.n; i += T) L.r[i] = __ldcg(L.b + i) - csr_row_f(L.Arp, L.Aci, L.Av, L.x, i);
+        for (int i = tid; i < L.n; i += 2 * T) {
+            const int j = i + T < L.n ? i + T : -1;
+            float si, sj;
+            csr_row2_f(L.Arp, L.Aci, L.Asv, L.b, i, j, si, sj);
+            const float bi = __ldcg(L.b + i);
+            L.r[i] = bi - si;
+            L.x[i] = L.omega * L.dinv[i] * bi;
+            if (j >= 0) {
+                const float bj = __ldcg(L.b + j);
+                L.r[j] = bj - sj;
+                L.x[j] = L.omega * L.dinv[j] * bj;
+            }
+        }
         cl.sync();
         const MGLevelDev& Lc = a.lv[l + 1];
-        for (int i = tid; i < Lc.n; i += T) Lc.b[i] = csr_row_f(L.Rrp, L.Rci, L.Rv, L.r, i);
+        for (int i = tid; i < Lc.n; i += 2 * T) {
+            const int j = i + T < Lc.n ? i + T : -1;
+            float si, sj;
+            csr_row2_f(L.Rrp, L.Rci, L.Rv, L.r, i, j, si, sj);
+            Lc.b[i] = si;
+            if (j >= 0) Lc.b[j] = sj;
+        }
         cl.sync();
     }
     // coarsest: x = Cinv b, one warp per row
@@ -186,11 +216,20 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
     const float* coarse_out = a.lv[a.nlev].x;
     for (int l = a.nlev - 1; l >= 1; --l) {
         const MGLevelDev& L = a.lv[l];
-        for (int i = tid; i < L.n; i += T) L.x[i] = __ldcg(L.x + i) + csr_row_f(L.Prp, L.Pci, L.Pv, coarse_out, i);
+        for (int i = tid; i < L.n; i += 2 * T) {
+            const int j = i + T < L.n ? i + T : -1;
+            float si, sj;
+            csr_row2_f(L.Prp, L.Pci, L.Pv, coarse_out, i, j, si, sj);
+            L.x[i] = __ldcg(L.x + i) + si;
+            if (j >= 0) L.x[j] = __ldcg(L.x + j) + sj;
+        }
         cl.sync();
-        for (int i = tid; i < L.n; i += T) {
-            const float xi = __ldcg(L.x + i);
-            L.t[i] = xi + L.omega * L.dinv[i] * (__ldcg(L.b + i) - csr_row_f(L.Arp, L.Aci, L.Av, L.x, i));
+        for (int i = tid; i < L.n; i += 2 * T) {
+            const int j = i + T < L.n ? i + T : -1;
+            float si, sj;
+            csr_row2_f(L.Arp, L.Aci, L.Av, L.x, i, j, si, sj);
+            L.t[i] = __ldcg(L.x + i) + L.omega * L.dinv[i] * (__ldcg(L.b + i) - si);
+            if (j >= 0) L.t[j] = __ldcg(L.x + j) + L.omega * L.dinv[j] * (__ldcg(L.b + j) - sj);
         }
         cl.sync();
         coarse_out = L.t;
