@@ -59,8 +59,12 @@ struct smm_ctx {
     bool cached = false;
     float2* ainv_df = nullptr;     // cached local inverses (FP64 sweep), FP32 pairs hi + lo
     float* ainv32 = nullptr;       // cached local inverses (FP32 correction sweep)
-    double* msrc = nullptr;        // [ne][n] M (sigma_s/(4pi) phi + q_iso) of the current sweep
-    double* mq = nullptr;          // [ne][nd][n] M q_d (angular sources)
+    // FP64 cached sweep, FP32-pair inputs: M (sigma_s/(4pi) phi + q_iso) of the current sweep [ne][n],
+    // M q_d [ne][nd][n] (angular sources), cosines [nd], face matrices, inflow; psi as pairs
+    float2* msrc2 = nullptr;
+    float2* mq2 = nullptr;
+    float2 *ox2 = nullptr, *oy2 = nullptr, *Fx2 = nullptr, *Fy2 = nullptr, *inflow2 = nullptr;
+    float2* psi2 = nullptr;
     std::vector<int32_t> tasks_host, level_start;  // level-sorted task list (for batching)
     // Anderson acceleration: rings of G(x_k) and f_k = G(x_k) - x_k (depth + 1 slots)
     std::vector<double*> aaG, aaF;
@@ -404,12 +408,21 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->cached = o.sweep_solver == SMM_SOLVER_CACHED_INVERSE;
     if (h->cached) {
         const size_t ninv = (size_t)s.ne * s.nd * s.n * s.n;
-        h->msrc = h->alloc<double>(nphi);
-        if (!h->msrc) return bail(SMM_ERR_OOM, "device allocation failed");
+        h->msrc2 = h->alloc<float2>(nphi);
+        if (!h->msrc2) return bail(SMM_ERR_OOM, "device allocation failed");
         if (h->src_angular) {
-            h->mq = h->alloc<double>(nang);
-            if (!h->mq) return bail(SMM_ERR_OOM, "device allocation failed");
-            smm::launch_mass_apply(s.ne, s.nd, s.n, h->M, h->src, h->mq, h->stream);
+            h->mq2 = h->alloc<float2>(nang);
+            if (!h->mq2) return bail(SMM_ERR_OOM, "device allocation failed");
+            smm::launch_mass_apply(s.ne, s.nd, s.n, h->M, h->src, h->mq2, h->stream);
+        }
+        if (!h->fp32) {
+            bool okp = upload(h, h->ox2, to_pairs(s.quad.ox)) && upload(h, h->oy2, to_pairs(s.quad.oy)) &&
+                       upload(h, h->Fx2, to_pairs(s.Fx)) && upload(h, h->Fy2, to_pairs(s.Fy));
+            if (okp && !s.inflow.empty()) okp = upload(h, h->inflow2, to_pairs(s.inflow));
+            h->psi2 = h->alloc<float2>(nang);
+            if (!okp || !h->psi2) return bail(SMM_ERR_OOM, "device allocation failed");
+            if (cudaMemsetAsync(h->psi2, 0, nang * sizeof(float2), h->stream) != cudaSuccess)
+                return bail(SMM_ERR_CUDA, "cudaMemsetAsync failed");
         }
         if (h->fp32) {
             h->ainv32 = h->alloc<float>(ninv);
@@ -484,9 +497,12 @@ smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) 
         a.phi = phi; a.src = h->src; a.src_angular = h->src_angular; a.inflow = h->has_inflow ? h->inflow : nullptr;
         a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr;
         if (h->cached) {
-            smm::launch_source(h->ne, h->n, h->M, h->sigma_s, phi, h->src_angular ? nullptr : h->src, h->msrc, h->stream);
+            smm::launch_source(h->ne, h->n, h->M, h->sigma_s, phi, h->src_angular ? nullptr : h->src, h->msrc2,
+                               h->stream);
             h->launches += 1;
-            a.ainv_df = h->ainv_df; a.msrc = h->msrc; a.mq = h->mq;
+            a.ainv_df = h->ainv_df; a.msrc2 = h->msrc2; a.mq2 = h->mq2;
+            a.ox2 = h->ox2; a.oy2 = h->oy2; a.Fx2 = h->Fx2; a.Fy2 = h->Fy2;
+            a.inflow2 = h->has_inflow ? h->inflow2 : nullptr; a.psi2 = h->psi2;
         }
     } else {
         smm::ResidualArgs r{};

@@ -39,6 +39,16 @@ struct SweepArgs {
     const float* rhs;          // [ne][nd][n] (RESIDUAL)
     const T* ainv;             // cached local inverses [ne*nd][n][n] column-major, or nullptr (on-the-fly LU)
     const float2* ainv_df;     // FP64 cached mode: the same inverses as FP32 pairs (hi, lo), hi + lo = entry
+    // FP64 cached mode, pair copies: M (s + q_iso) of this sweep [ne][n], M q_d [ne][nd][n] or nullptr,
+    // ordinate cosines [nd], face matrices [ne][4][p1][p1], inflow [nb][nd][p1] or nullptr
+    const float2* msrc2;
+    const float2* mq2;
+    const float2* ox2;
+    const float2* oy2;
+    const float2* Fx2;
+    const float2* Fy2;
+    const float2* inflow2;
+    float2* psi2;              // FP64 cached mode: psi as pairs (read by downwind tasks and the moments)
     const double* msrc;        // cached mode, SOURCE: [ne][n] M (sigma_s/(4pi) phi + q_iso) of this sweep
     const double* mq;          // cached mode, SOURCE, angular q: [ne][nd][n] M q_d, else nullptr
     T* psi;                    // [ne][nd][n] output, read by downwind tasks
@@ -87,10 +97,10 @@ void launch_invert(int p, const SweepArgs<T>& a, T* ainv_out, cudaStream_t s);
 // FP64 local inverses stored as FP32 pairs (hi, lo) with hi + lo = the FP64 entry to 2^-48
 void launch_invert_df(int p, const SweepArgs<double>& a, float2* ainv_out, cudaStream_t s);
 // out[e][d][i] = scale * sum_j M[e][i][j] in[e][d][j] (+ add[e][i] * scale2 if add) ; nd = 1 for per-element data
-void launch_mass_apply(int ne, int nd, int n, const double* M, const double* in, double* out, cudaStream_t s);
+void launch_mass_apply(int ne, int nd, int n, const double* M, const double* in, float2* out, cudaStream_t s);
 // msrc[e][i] = sum_j M[e][i][j] (c_e phi[e][j] + q[e][j]); phi, q nullable
 void launch_source(int ne, int n, const double* M, const double* sigma_s, const double* phi, const double* q_iso,
-                   double* msrc, cudaStream_t s);
+                   float2* msrc, cudaStream_t s);
 void launch_residual(int p, const ResidualArgs& a, cudaStream_t s);
 int sweep_blocks_per_sm(int p, int mode, bool fp32, bool cached);
 

@@ -104,19 +104,29 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
 #pragma unroll
                 for (int j = 0; j < (DF ? 1 : N); ++j) Ainv[j] = Ai[(size_t)j * N];
             }
-            if (MODE == SWEEP_SOURCE) {
+            if constexpr (DF) {
+                // b_pre = M s (+ M q_d) as pairs, y0 = A^{-1} b_pre
+                float2 bp;
+                if (MODE == SWEEP_SOURCE) {
+                    bp = a.msrc2[(size_t)e * N + row];
+                    if (a.mq2) {
+                        const float2 qv = a.mq2[((size_t)e * nd + d) * N + row];
+                        float s0 = bp.x, c0 = bp.y;
+                        df_add(s0, c0, qv.x, qv.y);
+                        bp = df_norm(s0, c0);
+                    }
+                } else {
+                    bp = make_float2(a.rhs[((size_t)e * nd + d) * N + row], 0.0f);
+                }
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    df_acc(ys, yc, Adf[j].x, Adf[j].y, __shfl_sync(FULL, bp.x, j), __shfl_sync(FULL, bp.y, j));
+            } else if (MODE == SWEEP_SOURCE) {
                 double bs = a.msrc[(size_t)e * N + row];
                 if (a.mq) bs += a.mq[((size_t)e * nd + d) * N + row];
                 bpre = (T)bs;
             } else {
                 bpre = (T)a.rhs[((size_t)e * nd + d) * N + row];
-            }
-            if constexpr (DF) {
-                float bh, bl;
-                df_split((double)bpre, bh, bl);
-#pragma unroll
-                for (int j = 0; j < N; ++j)
-                    df_acc(ys, yc, Adf[j].x, Adf[j].y, __shfl_sync(FULL, bh, j), __shfl_sync(FULL, bl, j));
             }
         }
 
@@ -174,6 +184,43 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                     for (int j = 0; j < (INV ? 1 : N); ++j)
                         if (j == face_node<P>(f, c)) A[j] += v;
                 }
+            } else if (DF && df < 0) {
+                // inflow face in pairs: lane (a, c) forms coef[a][c] u[c] with
+                // coef = Omega_x Fx + Omega_y Fy, the p+1 lanes of group a sum
+                // over c, and every row adds -A^{-1}[row][node(f, a)] v_a
+                const int la = lane / P1, lc = lane - (lane / P1) * P1;
+                float ts = 0.0f, tc = 0.0f;
+                if (lane < P1 * P1) {
+                    const size_t fo2 = ((size_t)e * 4 + f) * P1 * P1 + la * P1 + lc;
+                    const float2 fx = a.Fx2[fo2], fy = a.Fy2[fo2], o2x = a.ox2[d], o2y = a.oy2[d];
+                    float cs = 0.0f, cc = 0.0f;
+                    df_acc(cs, cc, o2x.x, o2x.y, fx.x, fx.y);
+                    df_acc(cs, cc, o2y.x, o2y.y, fy.x, fy.y);
+                    const float2 coef = df_norm(cs, cc);
+                    const int nb = a.nbr[e * 4 + f];
+                    float2 u = make_float2(0.0f, 0.0f);
+                    if (nb >= 0) {
+                        const int f2 = a.nbr_face[e * 4 + f];
+                        const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
+                        const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
+                        u = __ldcg(a.psi2 + ((size_t)nb * nd + d) * N + node);
+                    } else if (MODE == SWEEP_SOURCE && a.inflow2) {
+                        const int bi = a.bface_id[e * 4 + f];
+                        u = a.inflow2[((size_t)bi * nd + d) * P1 + lc];
+                    }
+                    df_acc(ts, tc, coef.x, coef.y, u.x, u.y);
+                }
+                const float2 t = df_norm(ts, tc);
+                float vs = t.x, vc = t.y;
+#pragma unroll
+                for (int k = 1; k < P1; ++k)
+                    df_add(vs, vc, __shfl_down_sync(FULL, t.x, k), __shfl_down_sync(FULL, t.y, k));
+                const float2 v = df_norm(vs, vc);
+#pragma unroll
+                for (int aa = 0; aa < P1; ++aa) {
+                    const float2 col = Adf[face_node<P>(f, aa)];
+                    df_acc(ys, yc, -col.x, -col.y, __shfl_sync(FULL, v.x, aa * P1), __shfl_sync(FULL, v.y, aa * P1));
+                }
             } else if (df < 0) {
                 // inflow face (warp-uniform branch): the (p+1)^2 products
                 // coef[a][c] * psi_up[c] are spread over lanes (a, c), summed
@@ -200,19 +247,8 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                 T sum = term;
 #pragma unroll
                 for (int k = 1; k < P1; ++k) sum += __shfl_down_sync(FULL, term, k);
-                if constexpr (DF) {
-                    // x -= sum_a A^{-1}[row][node(f, a)] v_a, v_a held by lane a (p+1)
-                    float vh, vl;
-                    df_split((double)sum, vh, vl);
-#pragma unroll
-                    for (int aa = 0; aa < P1; ++aa) {
-                        const float2 col = Adf[face_node<P>(f, aa)];
-                        df_acc(ys, yc, -col.x, -col.y, __shfl_sync(FULL, vh, aa * P1), __shfl_sync(FULL, vl, aa * P1));
-                    }
-                } else {
-                    const T v = __shfl_sync(FULL, sum, fa * P1);
-                    if (on) b -= v;
-                }
+                const T v = __shfl_sync(FULL, sum, fa * P1);
+                if (on) b -= v;
             }
         }
 
@@ -257,6 +293,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         if (lane < N) {
             const size_t o = ((size_t)e * nd + d) * N + lane;
             a.psi[o] = x;
+            if constexpr (DF) a.psi2[o] = df_norm(ys, yc);
             if (MODE == SWEEP_RESIDUAL) a.psi_acc[o] += (double)x;
         }
         __threadfence();  // one warp-wide fence instruction orders every lane's stores
@@ -444,9 +481,9 @@ __global__ void __launch_bounds__(256) invert_kernel(SweepArgs<T> a, T* __restri
     }
 }
 
-// out[t][i] = sum_j M[e][i][j] in[t][j], t = e*nd + d
+// out[t][i] = sum_j M[e][i][j] in[t][j], t = e*nd + d (FP64 sum, stored as an FP32 pair)
 __global__ void mass_apply_kernel(int ne, int nd, int n, const double* __restrict__ M, const double* __restrict__ in,
-                                  double* __restrict__ out) {
+                                  float2* __restrict__ out) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)ne * nd * n) return;
     const long long task = t / n;
@@ -456,12 +493,12 @@ __global__ void mass_apply_kernel(int ne, int nd, int n, const double* __restric
     const double* v = in + (size_t)task * n;
     double s = 0.0;
     for (int j = 0; j < n; ++j) s += m[j] * v[j];
-    out[t] = s;
+    out[t] = df_make(s);
 }
 
-// msrc[e][i] = sum_j M[e][i][j] (sigma_s/(4 pi) phi[e][j] + q[e][j])
+// msrc[e][i] = sum_j M[e][i][j] (sigma_s/(4 pi) phi[e][j] + q[e][j]) (FP64 sum, stored as an FP32 pair)
 __global__ void source_kernel(int ne, int n, const double* __restrict__ M, const double* __restrict__ sigma_s,
-                              const double* __restrict__ phi, const double* __restrict__ q, double* __restrict__ msrc) {
+                              const double* __restrict__ phi, const double* __restrict__ q, float2* __restrict__ msrc) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ne * n) return;
     const int e = t / n, i = t - e * n;
@@ -470,7 +507,7 @@ __global__ void source_kernel(int ne, int n, const double* __restrict__ M, const
     double s = 0.0;
     for (int j = 0; j < n; ++j)
         s += m[j] * ((phi ? c * phi[(size_t)e * n + j] : 0.0) + (q ? q[(size_t)e * n + j] : 0.0));
-    msrc[t] = s;
+    msrc[t] = df_make(s);
 }
 
 template <typename T, int P, int MODE, bool INV>
@@ -585,13 +622,13 @@ void launch_invert_df(int p, const SweepArgs<double>& a, float2* out, cudaStream
 template void launch_invert<double>(int, const SweepArgs<double>&, double*, cudaStream_t);
 template void launch_invert<float>(int, const SweepArgs<float>&, float*, cudaStream_t);
 
-void launch_mass_apply(int ne, int nd, int n, const double* M, const double* in, double* out, cudaStream_t s) {
+void launch_mass_apply(int ne, int nd, int n, const double* M, const double* in, float2* out, cudaStream_t s) {
     const long long tot = (long long)ne * nd * n;
     mass_apply_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ne, nd, n, M, in, out);
 }
 
 void launch_source(int ne, int n, const double* M, const double* sigma_s, const double* phi, const double* q_iso,
-                   double* msrc, cudaStream_t s) {
+                   float2* msrc, cudaStream_t s) {
     const int tot = ne * n;
     source_kernel<<<(tot + 255) / 256, 256, 0, s>>>(ne, n, M, sigma_s, phi, q_iso, msrc);
 }
