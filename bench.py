@@ -153,35 +153,24 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
-def lu_sweep_flops_per_task(p: int, mode_residual: bool) -> float:
-    """Algorithmic flops of one on-the-fly local solve (element x ordinate),
-    n = (p+1)^2: assembly 5 n^2 (sigma M - Ox Gx - Oy Gy), face blocks
-    4 faces x (p+1)^2 x 4, elimination 2/3 n^3, right-hand side elimination
-    and back substitution 2 n^2, source product 2 n^2 (source mode only)."""
-    n = (p + 1) ** 2
-    f = 5 * n * n + 16 * (p + 1) ** 2 + (2.0 / 3.0) * n ** 3 + 2 * n * n
-    if not mode_residual:
-        f += 2 * n * n
-    return f
-
-
-def cached_sweep_flops_per_task(p: int) -> float:
-    """Cached-inverse task: x = A^{-1} b (2 n^2) plus two inflow face blocks (4 (p+1)^2 each)."""
-    n = (p + 1) ** 2
-    return 2 * n * n + 8 * (p + 1) ** 2
+# DRAM bytes (read + write) per launch measured by ncu for the current kernels
+# on this workload (profiles/cg_iteration_mms-curved-128x128-p4-S8.md); a key
+# is dropped whenever the kernels it covers change.
+NCU_TRAFFIC: dict = {}
 
 
 def cached_sweep_bytes_per_task(p: int, word: int, angular: bool) -> float:
-    """HBM bytes of one cached-inverse task: the n x n inverse, the n outputs,
-    the n angular source values (M q_d, FP64) and two inflow traces."""
+    """HBM bytes of one cached-inverse task: the n x n inverse, the n outputs
+    (FP64 and, in the FP64 path, the FP32-pair copy), the angular source term
+    M q_d (an FP32 pair per node) and two inflow traces."""
     n = (p + 1) ** 2
-    return word * (n * n + n + 2 * (p + 1)) + (8 * n if angular else 0)
+    return word * (n * n + 2 * n + 2 * (p + 1)) + (8 * n if angular else 0)
 
 
-def residual_flops_per_task(p: int) -> float:
-    """FP64 residual r = M(s - sigma psi) + Ox Gx psi + Oy Gy psi - faces: 6 n^2 + 16 (p+1)^2."""
-    n = (p + 1) ** 2
-    return 6 * n * n + 16 * (p + 1) ** 2
+def moments_bytes_per_elem(n: int, nd: int) -> float:
+    """HBM bytes of the moment reduction per element: psi as FP32 pairs read
+    once (8 nd n) and six FP64 moments written (48 n)."""
+    return 8 * nd * n + 48 * n
 
 
 def mg_cg_bytes_per_iter(ne: int, n: int) -> float:
@@ -288,22 +277,30 @@ def run_ours(args) -> None:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    fp64_peak = 1.25                               # TFLOP/s nominal GB300 FP64
     tasks = ne * nd
-    sweep_tf = tasks * cached_sweep_flops_per_task(WL["p"]) / (ms_sweep * 1e-3) / 1e12
-    sweep_gbs = tasks * cached_sweep_bytes_per_task(WL["p"], 8, True) / (ms_sweep * 1e-3) / 1e9
-    cg_gbs = cg_it * mg_cg_bytes_per_iter(ne, n) / (ms_solve * 1e-3) / 1e9 if ms_solve > 0 else 0.0
+    sweep_bytes = tasks * cached_sweep_bytes_per_task(WL["p"], 8, True)
+    cg_bytes = mg_cg_bytes_per_iter(ne, n)
+    mom_bytes = ne * moments_bytes_per_elem(n, nd)
+    ms_mom = mean("ms_moments")
+    ms_iter = ms_solve / cg_it if cg_it > 0 else 0.0
+
+    def entry(bytes_per_launch, ms_per_launch, kernel, traffic_key, launches_per_step):
+        gbs = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9 if ms_per_launch > 0 else 0.0
+        return dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=gbs / hbm,
+                    traffic=NCU_TRAFFIC.get(traffic_key), algorithmic_bytes=bytes_per_launch, ms=ms_per_launch,
+                    launches_per_step=launches_per_step, kernel=kernel, peak_note=f"{hbm_src} copy bandwidth")
+
     rooflines = {
-        "sweep_fp64_cached": dict(bound="alu", achieved=sweep_tf, peak=fp64_peak, unit="TFLOP/s",
-                                  frac=sweep_tf / fp64_peak, traffic=None, ms=ms_sweep,
-                                  hbm_gbs=sweep_gbs, hbm_frac=sweep_gbs / hbm,
-                                  peak_note="nominal GB300 FP64 rate (1.20 TFLOP/s measured by an FMA probe)"),
-        "mg_pcg_fp64": dict(bound="hbm", achieved=cg_gbs, peak=hbm, unit="GB/s", frac=cg_gbs / hbm, traffic=None,
-                            ms=ms_solve, peak_note=f"{hbm_src} copy bandwidth"),
+        "cg_iteration": entry(cg_bytes, ms_iter, "one flexible-CG iteration: CUDA graph of 10 kernels (operator "
+                              "product, update, V-cycle: 4 smoothing steps, residual, cluster coarse cycle, "
+                              "prolongation; dot products, direction)", "cg_iteration", cg_it),
+        "sweep_kernel": entry(sweep_bytes, ms_sweep, "sweep_kernel<double, 4, SOURCE, cached inverse> "
+                              "(plus the per-sweep source kernel)", "sweep_kernel", 1),
+        "moments": entry(mom_bytes, ms_mom, "moments_df_kernel + beta_kernel", "moments", 1),
     }
-    dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
+    # dominant: the largest device time per step
+    dom = max(rooflines, key=lambda k: rooflines[k]["ms"] * rooflines[k]["launches_per_step"])
     roof = dict(rooflines[dom])
-    roof["kernel"] = dom
 
     # end to end through the C ABI with host buffers: H2D of varphi^k, one outer
     # step, D2H of varphi^{k+1}, all inside the timed region

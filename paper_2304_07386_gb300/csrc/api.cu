@@ -65,6 +65,7 @@ struct smm_ctx {
     float2* mq2 = nullptr;
     float2 *ox2 = nullptr, *oy2 = nullptr, *Fx2 = nullptr, *Fy2 = nullptr, *inflow2 = nullptr;
     float2* psi2 = nullptr;
+    float2* wq2 = nullptr;         // [6][nd] pairs of w_d (1, Ox, Oy, OxOx, OxOy, OyOy) for the pair moments
     std::vector<int32_t> tasks_host, level_start;  // level-sorted task list (for batching)
     // Anderson acceleration: rings of G(x_k) and f_k = G(x_k) - x_k (depth + 1 slots)
     std::vector<double*> aaG, aaF;
@@ -91,6 +92,7 @@ struct smm_ctx {
     int* ctl = nullptr;
     int* nonfinite = nullptr;
     int cg_nblk = 1;
+    int cg_nvblk = 1;              // blocks of the grid-stride CG vector kernels
     smm::MGPlan mg;
     double* rold = nullptr;        // flexible CG: previous residual
     double* xcg = nullptr;         // CG iterate owned by the handle (captured in the iteration graph)
@@ -291,7 +293,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->phi_prev = h->alloc<double>(nphi);
     const int epb = smm::cg_threads_per_block(s.n) / s.n;
     h->cg_nblk = (s.ne + epb - 1) / epb;
-    h->part = h->alloc<double>(3 * (size_t)h->cg_nblk);
+    h->cg_nvblk = std::max(1, std::min(2 * h->sms, (int)((nphi + 255) / 256)));
+    h->part = h->alloc<double>(3 * (size_t)h->cg_nblk + 3 * (size_t)h->cg_nvblk);
     h->scal = h->alloc<double>(8);
     h->ctl = h->alloc<int>(8);
     h->dpart = h->alloc<double>(2 * 256);
@@ -419,6 +422,20 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             bool okp = upload(h, h->ox2, to_pairs(s.quad.ox)) && upload(h, h->oy2, to_pairs(s.quad.oy)) &&
                        upload(h, h->Fx2, to_pairs(s.Fx)) && upload(h, h->Fy2, to_pairs(s.Fy));
             if (okp && !s.inflow.empty()) okp = upload(h, h->inflow2, to_pairs(s.inflow));
+            {
+                const int nd = s.nd;
+                std::vector<double> wq((size_t)6 * nd);
+                for (int d = 0; d < nd; ++d) {
+                    const double w = s.quad.w[d], x = s.quad.ox[d], y = s.quad.oy[d];
+                    wq[d] = w;
+                    wq[nd + d] = w * x;
+                    wq[2 * nd + d] = w * y;
+                    wq[3 * nd + d] = w * x * x;
+                    wq[4 * nd + d] = w * x * y;
+                    wq[5 * nd + d] = w * y * y;
+                }
+                okp = okp && upload(h, h->wq2, to_pairs(wq));
+            }
             h->psi2 = h->alloc<float2>(nang);
             if (!okp || !h->psi2) return bail(SMM_ERR_OOM, "device allocation failed");
             if (cudaMemsetAsync(h->psi2, 0, nang * sizeof(float2), h->stream) != cudaSuccess)
@@ -543,7 +560,10 @@ smm_status enqueue_sweep(smm_handle h, const double* phi) {
 }
 
 smm_status enqueue_moments(smm_handle h) {
-    smm::launch_moments(h->ne, h->nd, h->n, h->w, h->ox, h->oy, h->psi, h->mom, h->stream);
+    if (h->psi2)
+        smm::launch_moments_df(h->ne, h->nd, h->n, h->wq2, h->psi2, h->mom, h->stream);
+    else
+        smm::launch_moments(h->ne, h->nd, h->n, h->w, h->ox, h->oy, h->psi, h->mom, h->stream);
     smm::launch_beta(h->nb, h->nd, h->n, h->p, h->nfq, h->bface_elem, h->bface_face, h->w, h->ox, h->oy, h->L1,
                      h->b_nhat, h->b_eb0, h->psi, h->mom, h->beta, h->stream);
     h->launches += h->nb > 0 ? 2 : 1;
@@ -563,6 +583,7 @@ smm_status enqueue_rhs(smm_handle h) {
 smm::CGArgs cg_args(smm_handle h, double* x) {
     smm::CGArgs a{};
     a.ne = h->ne; a.n = h->n; a.nrow = h->ne * h->n; a.nblk = h->cg_nblk;
+    a.nvblk = h->cg_nvblk; a.pvec = h->part + 3 * (size_t)h->cg_nblk;
     a.A.AdT = h->AdT; a.A.CT = h->CT; a.A.nbr = h->nbr; a.A.nface = h->nbr_face;
     for (int k = 0; k < 5; ++k) a.A.wd[k] = h->wd[k];
     a.A2.AdT = h->AdT2; a.A2.CT = h->CT2; a.A2.nbr = h->nbr; a.A2.nface = h->nbr_face;

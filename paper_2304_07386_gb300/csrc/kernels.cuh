@@ -105,6 +105,8 @@ void launch_residual(int p, const ResidualArgs& a, cudaStream_t s);
 int sweep_blocks_per_sm(int p, int mode, bool fp32, bool cached);
 
 // moments and closures
+// moments from psi as FP32 pairs; wq [6][nd] pairs of w_d (1, Ox, Oy, OxOx, OxOy, OyOy)
+void launch_moments_df(int ne, int nd, int n, const float2* wq, const float2* psi2, double* mom, cudaStream_t s);
 void launch_moments(int ne, int nd, int n, const double* w, const double* ox, const double* oy,
                     const double* psi, double* mom, cudaStream_t s);
 void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_elem, const int32_t* bface_face,
@@ -157,6 +159,8 @@ struct CGArgs {
     double* rold;              // previous residual (flexible CG), may be nullptr on the block-Jacobi path
     const double* b;
     double* part;              // [3][nblk] partial sums
+    double* pvec;              // [3][nvblk] partial sums of the grid-stride vector kernels (flexible CG)
+    int nvblk;                 // blocks of the grid-stride vector kernels
     double* scal;              // [8]: rz, pq, rr, bb, thresh2, -, -, -
     int* ctl;                  // [4]: done, iters, max_iters, nonfinite
 };

@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "blockops.cuh"
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace smm {
@@ -181,6 +182,41 @@ __global__ void rhs_assemble_kernel(int ne, int n, int p, int nfq, const double*
         }
     }
     rhs[t] = acc;
+}
+
+// The same moments from psi stored as FP32 pairs, accumulated in pair
+// arithmetic (see dfloat.cuh) against the six per-ordinate weights
+// wq[k][d] = w_d (1, Ox, Oy, Ox Ox, Ox Oy, Oy Oy)_k, also pairs.
+__global__ void __launch_bounds__(256) moments_df_kernel(int ne, int nd, int n, const float2* __restrict__ wq,
+                                                         const float2* __restrict__ psi2, double* __restrict__ mom) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < ne; e += warps) {
+        if (lane >= n) continue;
+        float s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
+        const float2* ps = psi2 + (size_t)e * nd * n + lane;
+        for (int d = 0; d < nd; ++d) {
+            const float2 v = __ldcg(ps + (size_t)d * n);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float2 wk = wq[k * nd + d];
+                df_acc(s[k], c[k], wk.x, wk.y, v.x, v.y);
+            }
+        }
+        const size_t o = (size_t)e * n + lane, st = (size_t)ne * n;
+        const double phi = df_to_double(s[0], c[0]);
+        mom[o] = phi;
+        mom[st + o] = df_to_double(s[1], c[1]);
+        mom[2 * st + o] = df_to_double(s[2], c[2]);
+        mom[3 * st + o] = df_to_double(s[3], c[3]) - phi / 3.0;
+        mom[4 * st + o] = df_to_double(s[4], c[4]);
+        mom[5 * st + o] = df_to_double(s[5], c[5]) - phi / 3.0;
+    }
+}
+
+void launch_moments_df(int ne, int nd, int n, const float2* wq, const float2* psi2, double* mom, cudaStream_t s) {
+    int grid = std::max(1, std::min((ne + 7) / 8, 65535));
+    moments_df_kernel<<<grid, 256, 0, s>>>(ne, nd, n, wq, psi2, mom);
 }
 
 void launch_moments(int ne, int nd, int n, const double* w, const double* ox, const double* oy, const double* psi,
@@ -529,60 +565,54 @@ __global__ void __launch_bounds__(256) cgx_spmv_kernel(CGArgs a) {
     }
     double s = block_sum(pq, sh);
     if (threadIdx.x == 0) a.part[blockIdx.x] = s;
-    // last block: alpha = rz / pq -> scal[5]
-    if (last_block((unsigned*)(a.ctl + 5))) {
-        const double pq_all = sum_partials_cg(a.part, a.nblk, sh);
-        if (threadIdx.x == 0) {
-            a.scal[1] = pq_all;
-            a.scal[5] = a.scal[0] / pq_all;
-            a.ctl[5] = 0;
-        }
-    }
 }
 
 // x += alpha p ; r_old = r ; r -= alpha q ; partial rr -> part[2 nblk]
 __global__ void cgx_update_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
     __shared__ double sh[40];
-    const double alpha = a.scal[5];
-    const int n = a.n, epb = blockDim.x / n;
-    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
-    double r = 0.0;
-    if (e < a.ne) {
-        const size_t o = (size_t)e * n + i;
+    // every block reduces the operator product's partials itself (same order
+    // everywhere, so every block gets the same alpha)
+    const double pq = sum_partials(a.part, a.nblk, sh);
+    const double alpha = a.scal[0] / pq;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.scal[1] = pq;
+        a.scal[5] = alpha;
+    }
+    double rr = 0.0;
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.nrow; o += gridDim.x * blockDim.x) {
         a.x[o] += alpha * a.p[o];
         const double ro = a.r[o];
         a.rold[o] = ro;
-        r = ro - alpha * a.q[o];
+        const double r = ro - alpha * a.q[o];
         a.r[o] = r;
+        rr += r * r;
     }
-    double s = block_sum(r * r, sh);
-    if (threadIdx.x == 0) a.part[2 * a.nblk + blockIdx.x] = s;
+    double s = block_sum(rr, sh);
+    if (threadIdx.x == 0) a.pvec[2 * a.nvblk + blockIdx.x] = s;
 }
 
-// partials r.z -> part[nblk] and (r - r_old).z -> part[0] (flexible CG)
+// partials r.z and (r - r_old).z (flexible CG); the last block reduces them
+// with the update's r.r partials: beta = (r - r_old).z / rz_old -> scal[6],
+// rz, rr, iteration count and convergence
 __global__ void cgx_rz_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
     __shared__ double sh[40];
-    const int n = a.n, epb = blockDim.x / n;
-    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
     double rz = 0.0, dz = 0.0;
-    if (e < a.ne) {
-        const size_t o = (size_t)e * n + i;
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.nrow; o += gridDim.x * blockDim.x) {
         const double z = a.z[o], r = a.r[o];
-        rz = r * z;
-        dz = (r - a.rold[o]) * z;
+        rz += r * z;
+        dz += (r - a.rold[o]) * z;
     }
     double s = block_sum(rz, sh);
     double t = block_sum(dz, sh);
     if (threadIdx.x == 0) {
-        a.part[a.nblk + blockIdx.x] = s;
-        a.part[blockIdx.x] = t;
+        a.pvec[a.nvblk + blockIdx.x] = s;
+        a.pvec[blockIdx.x] = t;
     }
-    // last block: beta = (r - r_old).z / rz_old -> scal[6]; rz, rr; count and convergence
     if (last_block((unsigned*)(a.ctl + 6))) {
         double dz_all, rz_new, rr;
-        sum3_partials_cg(a.part, a.nblk, sh, dz_all, rz_new, rr);
+        sum3_partials_cg(a.pvec, a.nvblk, sh, dz_all, rz_new, rr);
         if (threadIdx.x == 0) {
             a.scal[6] = dz_all / a.scal[0];
             a.scal[0] = rz_new;
@@ -601,10 +631,7 @@ __global__ void cgx_rz_kernel(CGArgs a) {
 __global__ void cgx_direction_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
     const double beta = a.scal[6];
-    const int n = a.n, epb = blockDim.x / n;
-    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
-    if (e < a.ne) {
-        const size_t o = (size_t)e * n + i;
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.nrow; o += gridDim.x * blockDim.x) {
         const double pn = a.z[o] + beta * a.p[o];
         a.p[o] = pn;
         a.p2[o] = df_make(pn);
@@ -678,10 +705,10 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
     int launches = 0;
     for (int k = 0; k < count; ++k) {
         SMM_DISPATCH_N(a.n, cgx_spmv_kernel, a.nblk, tpb, 0, s)
-        cgx_update_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        cgx_update_kernel<<<a.nvblk, 256, 0, s>>>(a);
         launches += 2 + mg_apply(mg, a.r, a.z, a.ctl, s);
-        cgx_rz_kernel<<<a.nblk, tpb, 0, s>>>(a);
-        cgx_direction_kernel<<<a.nblk, tpb, 0, s>>>(a);
+        cgx_rz_kernel<<<a.nvblk, 256, 0, s>>>(a);
+        cgx_direction_kernel<<<a.nvblk, 256, 0, s>>>(a);
         launches += 2;
     }
     return launches;
