@@ -66,6 +66,7 @@ enum { SMM_INFLOW_VACUUM = 0, SMM_INFLOW_NODAL = 1 };
 enum { SMM_SWEEP_FP64 = 0, SMM_SWEEP_FP32_REFINED = 1 };
 enum { SMM_PRECOND_BLOCK_JACOBI = 0, SMM_PRECOND_MULTIGRID = 1 };
 enum { SMM_SOLVER_LU = 0, SMM_SOLVER_CACHED_INVERSE = 1 };
+enum { SMM_MOMENT_IP = 0, SMM_MOMENT_CG = 1 };
 
 typedef struct {
     int32_t n_elem;             /* number of quadrilaterals */
@@ -111,6 +112,18 @@ typedef struct {
     int32_t mg_smooth_steps;    /* multigrid preconditioner: damped block-Jacobi
                                    steps on the DG level before and after the
                                    coarse correction, 1..4 (default 2) */
+    int32_t moment_discretization; /* SMM_MOMENT_IP (default): interior penalty
+                                   moment system on the DG space (paper Eq.
+                                   ipsmm).  SMM_MOMENT_CG: the continuous
+                                   finite element system (Sec. "Discontinuous
+                                   Galerkin and Continuous Finite Element"):
+                                   Eq. ipsmm with test and trial space V_p,
+                                   solved by flexible CG with a V-cycle of
+                                   point-Jacobi smoothing on the continuous
+                                   nodes (any `precond`); varphi is still
+                                   passed as DG nodal values, and the solve
+                                   returns P varphi (equal values at shared
+                                   nodes). */
 } smm_options;
 
 typedef struct {

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsmm.so")
-UNITS = ["setup.cpp", "amg.cpp", "sweep.cu", "moments.cu", "mg.cu", "api.cu", "cnn.cu", "noalloc.cu"]
-HEADERS = [os.path.join(CSRC, h) for h in ("kernels.cuh", "setup.hpp", "amg.hpp", "blockops.cuh")] + [os.path.join(ROOT, "include", "smm.h")]
+UNITS = ["setup.cpp", "amg.cpp", "sweep.cu", "moments.cu", "mg.cu", "cgsmm.cu", "api.cu", "cnn.cu", "noalloc.cu"]
+HEADERS = [os.path.join(CSRC, h) for h in ("kernels.cuh", "setup.hpp", "amg.hpp", "blockops.cuh", "dfloat.cuh")] + [os.path.join(ROOT, "include", "smm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp", "-I", os.path.join(ROOT, "include")]
 

@@ -205,8 +205,10 @@ bool build_multigrid(int ne, int n, const std::vector<double>& Adiag, const std:
                      const std::vector<double>& gll, MGHierarchy& mg, std::string& err, int coarse_max) {
     mg = MGHierarchy();
     const size_t nn = (size_t)n * n;
-    // ---- level-0 block-Jacobi damping: lambda_max(Pinv A) by power iteration ----
-    {
+    // ---- level-0 block-Jacobi damping: lambda_max(Pinv A) by power iteration
+    //      (skipped when no block inverses are given: a continuous-space
+    //      operator, whose level 0 the caller smooths itself) ----
+    if (!Pinv.empty()) {
         const size_t N = (size_t)ne * n;
         std::vector<double> x(N), y(N), z(N);
         for (size_t i = 0; i < N; ++i) x[i] = 1.0 + 0.5 * std::sin(0.7 * (double)i + 0.3);
@@ -301,7 +303,7 @@ bool build_multigrid(int ne, int n, const std::vector<double>& Adiag, const std:
                 for (int k = 0; k < 4; ++k) rows[mg.vid[e * 4 + a]].push_back({mg.vid[e * 4 + k], g[a * 4 + k]});
             for (int f = 0; f < 4; ++f) {
                 const int e2 = nbr[e * 4 + f];
-                if (e2 < 0) continue;
+                if (e2 < 0 || Aoff.empty()) continue;
                 galerkin4(&Aoff[((size_t)e * 4 + f) * nn], g);
                 for (int a = 0; a < 4; ++a)
                     for (int k = 0; k < 4; ++k) rows[mg.vid[e * 4 + a]].push_back({mg.vid[e2 * 4 + k], g[a * 4 + k]});

@@ -39,7 +39,9 @@ struct MGHierarchy {
     int ncoarse = 0;
 };
 
-// Adiag/Aoff/Pinv: row-major blocks as in Setup; nbr [ne][4]; corner_ids
+// Adiag/Aoff/Pinv: row-major blocks as in Setup (Aoff empty: no neighbour
+// blocks, as for the continuous-space operator; Pinv empty: no level-0
+// block-Jacobi damping estimate, omega0 stays 0); nbr [ne][4]; corner_ids
 // [ne][4] control-point ids of the element corners (c00, c10, c01, c11);
 // gll: the p+1 Gauss-Lobatto points of [0,1].
 bool build_multigrid(int ne, int n, const std::vector<double>& Adiag, const std::vector<double>& Aoff,

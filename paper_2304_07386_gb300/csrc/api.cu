@@ -93,7 +93,11 @@ struct smm_ctx {
     int* nonfinite = nullptr;
     int cg_nblk = 1;
     int cg_nvblk = 1;              // blocks of the grid-stride CG vector kernels
+    int cg_pmax = 1;               // room per partial-sum array
     smm::MGPlan mg;
+    smm::CGCPlan cgc;              // continuous (CG) moment system, when selected
+    double* bc = nullptr;          // its right-hand side P^T b_IP [nglob]
+    double* xc = nullptr;          // its CG iterate [nglob]
     double* rold = nullptr;        // flexible CG: previous residual
     double* xcg = nullptr;         // CG iterate owned by the handle (captured in the iteration graph)
     cudaStream_t cap = nullptr;    // private stream used once to capture the CG iteration graph
@@ -165,6 +169,8 @@ std::vector<double> transpose_blocks(const std::vector<double>& a, int n) {
 
 namespace {
 smm::CGArgs cg_args(smm_handle h, double* x);
+smm::CGArgs cgc_args(smm_handle h);
+smm_status setup_cg_moment_system(smm_handle h, const smm::Setup& s);
 }
 
 extern "C" {
@@ -181,6 +187,7 @@ void smm_default_options(smm_options* opt) {
     opt->anderson_depth = 0;
     opt->guess_check = 0;
     opt->mg_smooth_steps = 2;
+    opt->moment_discretization = SMM_MOMENT_IP;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -214,7 +221,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0) ||
         (o.precond != SMM_PRECOND_BLOCK_JACOBI && o.precond != SMM_PRECOND_MULTIGRID) ||
         (o.sweep_solver != SMM_SOLVER_LU && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) || o.anderson_depth < 0 ||
-        o.anderson_depth > 5 || o.mg_smooth_steps < 1 || o.mg_smooth_steps > 4)
+        o.anderson_depth > 5 || o.mg_smooth_steps < 1 || o.mg_smooth_steps > 4 ||
+        (o.moment_discretization != SMM_MOMENT_IP && o.moment_discretization != SMM_MOMENT_CG))
         return fail(SMM_ERR_INVALID_ARG, "bad options");
 
     smm::Input in;
@@ -222,6 +230,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     in.nodes = mesh->nodes; in.elem_nodes = mesh->elem_nodes; in.sigma_t = sigma_t; in.sigma_s = sigma_s;
     in.source_kind = source_kind; in.q = q; in.inflow_kind = inflow_kind; in.inflow = inflow;
     in.kappa_scale = o.kappa_scale;
+    in.moment_cg = o.moment_discretization == SMM_MOMENT_CG;
     smm::Setup s;
     std::string err;
     int rc = smm::build_setup(in, s, err);
@@ -294,7 +303,9 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     const int epb = smm::cg_threads_per_block(s.n) / s.n;
     h->cg_nblk = (s.ne + epb - 1) / epb;
     h->cg_nvblk = std::max(1, std::min(2 * h->sms, (int)((nphi + 255) / 256)));
-    h->part = h->alloc<double>(3 * (size_t)h->cg_nblk + 3 * (size_t)h->cg_nvblk);
+    // partial sums: [3][max(element blocks, continuous-node blocks)] then [3][vector blocks]
+    h->cg_pmax = std::max(h->cg_nblk, std::max(1, (s.nglob + 255) / 256));
+    h->part = h->alloc<double>(3 * (size_t)h->cg_pmax + 3 * (size_t)h->cg_nvblk);
     h->scal = h->alloc<double>(8);
     h->ctl = h->alloc<int>(8);
     h->dpart = h->alloc<double>(2 * 256);
@@ -317,7 +328,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         return bail(SMM_ERR_OOM, "pinned allocation failed");
     for (auto& e : h->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(SMM_ERR_CUDA, "cudaEventCreate failed");
-    if (o.precond == SMM_PRECOND_MULTIGRID) {
+    const bool cgm = o.moment_discretization == SMM_MOMENT_CG;
+    if (o.precond == SMM_PRECOND_MULTIGRID || cgm) {
         const int nc = (s.m + 1) * (s.m + 1);
         std::vector<int> corners((size_t)s.ne * 4);
         const int cidx[4] = {0, s.m, s.m * (s.m + 1), s.m * (s.m + 1) + s.m};
@@ -326,14 +338,18 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         std::vector<int> nbr(s.nbr.begin(), s.nbr.end());
         smm::MGHierarchy H;
         std::string merr;
-        if (!smm::build_multigrid(s.ne, s.n, s.Adiag, s.Aoff, s.Pinv, nbr, corners, smm::gauss_lobatto01(s.p1).x, H,
-                                  merr))
-            return bail(SMM_ERR_MESH, merr);
+        // the continuous system's hierarchy starts from its element blocks (no
+        // neighbour blocks, no level-0 block smoother)
+        const bool okmg = cgm ? smm::build_multigrid(s.ne, s.n, s.Kcg, {}, {}, nbr, corners,
+                                                     smm::gauss_lobatto01(s.p1).x, H, merr)
+                              : smm::build_multigrid(s.ne, s.n, s.Adiag, s.Aoff, s.Pinv, nbr, corners,
+                                                     smm::gauss_lobatto01(s.p1).x, H, merr);
+        if (!okmg) return bail(SMM_ERR_MESH, merr);
         if ((int)H.lv.size() - 1 > 11) return bail(SMM_ERR_MESH, "multigrid: too many levels");
         smm::MGPlan& P = h->mg;
         P.enabled = true;
         P.ne = s.ne; P.n = s.n; P.nu0 = o.mg_smooth_steps; P.omega0 = H.omega0;
-        {
+        if (!cgm) {
             float *ad32 = nullptr, *c32 = nullptr, *pi32 = nullptr;
             ok &= upload_f32(h, ad32, transpose_blocks(s.Adiag, s.n));
             ok &= upload_f32(h, c32, transpose_blocks(s.Cface, 2 * s.p1));
@@ -342,7 +358,10 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             P.A.nbr = h->nbr; P.A.nface = h->nbr_face;
             for (int k = 0; k < s.p1; ++k) P.A.wd[k] = (float)s.wd[k];
         }
-        P.x0 = h->alloc<float>(nphi); P.x0b = h->alloc<float>(nphi); P.res0 = h->alloc<float>(nphi);
+        if (!cgm) {
+            P.x0 = h->alloc<float>(nphi); P.x0b = h->alloc<float>(nphi); P.res0 = h->alloc<float>(nphi);
+            ok &= P.x0 && P.x0b && P.res0;
+        }
         P.nvert = H.nvert;
         int *vid = nullptr, *vrp = nullptr, *vinc = nullptr;
         float* w4 = nullptr;
@@ -379,19 +398,27 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         float* cinv = nullptr;
         ok &= upload_f32(h, cinv, H.coarse_inv);
         P.cinv = cinv;
-        ok &= P.x0 && P.x0b && P.res0 && cudaStreamSynchronize(h->stream) == cudaSuccess;
+        ok &= cudaStreamSynchronize(h->stream) == cudaSuccess;
         if (!ok) return bail(SMM_ERR_OOM, "multigrid upload failed");
         h->rold = h->alloc<double>(nphi);
         h->xcg = h->alloc<double>(nphi);
         if (!h->rold || !h->xcg) return bail(SMM_ERR_OOM, "device allocation failed");
+        if (cgm) {
+            smm_status cst = setup_cg_moment_system(h, s);
+            if (cst != SMM_OK) {
+                delete h;
+                return cst;
+            }
+        }
         // capture one flexible-CG iteration (spmv, update, V-cycle, dots, direction) as a graph
         if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
             return bail(SMM_ERR_CUDA, "cudaStreamCreate failed");
-        smm::CGArgs ca = cg_args(h, h->xcg);
+        smm::CGArgs ca = cgm ? cgc_args(h) : cg_args(h, h->xcg);
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return bail(SMM_ERR_CUDA, "cudaStreamBeginCapture failed");
-        h->graph_kernels = smm::cgx_iterations(ca, 1, h->mg, h->cap);
+        h->graph_kernels = cgm ? smm::cgc_iteration(ca, h->cgc, h->mg, h->cap)
+                               : smm::cgx_iterations(ca, 1, h->mg, h->cap);
         if (cudaStreamEndCapture(h->cap, &g) != cudaSuccess || !g)
             return bail(SMM_ERR_CUDA, "CG iteration capture failed");
         const cudaError_t ie = cudaGraphInstantiate(&h->cg_graph, g, 0);
@@ -580,10 +607,90 @@ smm_status enqueue_rhs(smm_handle h) {
     return SMM_OK;
 }
 
+// Arguments of the flexible CG on the continuous system (nglob unknowns)
+smm::CGArgs cgc_args(smm_handle h) {
+    smm::CGArgs a = cg_args(h, h->xc);
+    a.nrow = h->cgc.nglob;
+    a.nblk = h->cgc.nblk_node;
+    a.b = h->bc;
+    return a;
+}
+
+// Device data of the continuous moment system (Sec. 5.1): element blocks,
+// node numbering and incidences, diagonal and point-Jacobi damping
+smm_status setup_cg_moment_system(smm_handle h, const smm::Setup& s) {
+    const int ne = s.ne, n = s.n, ng = s.nglob;
+    const size_t nn = (size_t)n * n;
+    smm::CGCPlan& c = h->cgc;
+    c.ne = ne; c.n = n; c.nglob = ng; c.nu = h->opt.mg_smooth_steps;
+    c.nblk_node = std::max(1, (ng + 255) / 256);
+    // assembled diagonal and the largest eigenvalue of D^{-1} A by power iteration
+    std::vector<double> diag(ng, 0.0);
+    for (int e = 0; e < ne; ++e)
+        for (int i = 0; i < n; ++i) diag[s.gid[(size_t)e * n + i]] += s.Kcg[(size_t)e * nn + (size_t)i * n + i];
+    std::vector<double> dinv(ng), minv_d(ng);
+    for (int g = 0; g < ng; ++g) {
+        if (!(diag[g] > 0)) return fail(SMM_ERR_MESH, "continuous moment system: non-positive diagonal");
+        dinv[g] = 1.0 / diag[g];
+        minv_d[g] = 1.0 / (double)(s.grp[g + 1] - s.grp[g]);
+    }
+    {
+        std::vector<double> x(ng), ye((size_t)ne * n), y(ng);
+        for (int g = 0; g < ng; ++g) x[g] = 1.0 + 0.5 * std::sin(0.7 * (double)g + 0.3);
+        double lam = 1.0;
+        for (int it = 0; it < 30; ++it) {
+#pragma omp parallel for schedule(static)
+            for (int e = 0; e < ne; ++e)
+                for (int i = 0; i < n; ++i) {
+                    double acc = 0.0;
+                    for (int j = 0; j < n; ++j) acc += s.Kcg[(size_t)e * nn + (size_t)i * n + j] * x[s.gid[(size_t)e * n + j]];
+                    ye[(size_t)e * n + i] = acc;
+                }
+            double xy = 0.0, xdx = 0.0, nrm = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : xy, xdx)
+            for (int g = 0; g < ng; ++g) {
+                double acc = 0.0;
+                for (int k = s.grp[g]; k < s.grp[g + 1]; ++k) acc += ye[s.ginc[k]];
+                y[g] = acc;
+                xy += x[g] * acc;
+                xdx += x[g] * x[g] * diag[g];
+            }
+            lam = xy / xdx;
+            for (int g = 0; g < ng; ++g) {
+                y[g] *= dinv[g];
+                nrm += y[g] * y[g];
+            }
+            nrm = std::sqrt(nrm);
+            for (int g = 0; g < ng; ++g) x[g] = y[g] / nrm;
+        }
+        c.omega = (4.0 / 3.0) / (1.05 * lam);
+    }
+    bool ok = true;
+    double *KT = nullptr, *dv = nullptr;
+    int *gid = nullptr, *grp = nullptr, *ginc = nullptr, *gown = nullptr;
+    float* minv = nullptr;
+    ok &= upload(h, KT, transpose_blocks(s.Kcg, n)) && upload(h, dv, dinv);
+    ok &= upload(h, gid, s.gid) && upload(h, grp, s.grp) && upload(h, ginc, s.ginc) && upload(h, gown, s.gown);
+    ok &= upload_f32(h, minv, minv_d);
+    c.KT = KT; c.dinv = dv; c.gid = gid; c.grp = grp; c.ginc = ginc; c.gown = gown; c.minv = minv;
+    c.ye = h->alloc<double>((size_t)ne * n);
+    c.xa = h->alloc<double>(ng);
+    c.xb = h->alloc<double>(ng);
+    c.res = h->alloc<double>(ng);
+    c.cres = h->alloc<float>((size_t)ne * 4);
+    h->bc = h->alloc<double>(ng);
+    h->xc = h->alloc<double>(ng);
+    ok &= c.ye && c.xa && c.xb && c.res && c.cres && h->bc && h->xc;
+    ok &= cudaStreamSynchronize(h->stream) == cudaSuccess;
+    if (!ok) return fail(SMM_ERR_OOM, "continuous moment system: device allocation or upload failed");
+    c.enabled = true;
+    return SMM_OK;
+}
+
 smm::CGArgs cg_args(smm_handle h, double* x) {
     smm::CGArgs a{};
     a.ne = h->ne; a.n = h->n; a.nrow = h->ne * h->n; a.nblk = h->cg_nblk;
-    a.nvblk = h->cg_nvblk; a.pvec = h->part + 3 * (size_t)h->cg_nblk;
+    a.nvblk = h->cg_nvblk; a.pvec = h->part + 3 * (size_t)h->cg_pmax;
     a.A.AdT = h->AdT; a.A.CT = h->CT; a.A.nbr = h->nbr; a.A.nface = h->nbr_face;
     for (int k = 0; k < 5; ++k) a.A.wd[k] = h->wd[k];
     a.A2.AdT = h->AdT2; a.A2.CT = h->CT2; a.A2.nbr = h->nbr; a.A2.nface = h->nbr_face;
@@ -611,11 +718,17 @@ smm_status check_device_error(smm_handle h) {
 
 // CG from the guess in x; host reads the control word every `chunk` iterations
 smm_status run_cg(smm_handle h, double* x, int* iters) {
+    const bool cgm = h->cgc.enabled;
     const bool mg = h->mg.enabled;
     const size_t nphi = (size_t)h->ne * h->n;
-    smm::CGArgs a = cg_args(h, mg ? h->xcg : x);
+    smm::CGArgs a = cgm ? cgc_args(h) : cg_args(h, mg ? h->xcg : x);
     SMM_CUDA(cudaMemsetAsync(h->ctl, 0, 8 * sizeof(int), h->stream));
-    if (mg) {
+    if (cgm) {
+        // continuous system: b = P^T b_IP, initial guess from the DG iterate
+        smm::cgc_gather(h->cgc, h->rhs, h->bc, h->stream);
+        smm::cgc_pick(h->cgc, x, h->xc, h->stream);
+        h->launches += 2 + smm::cgc_start(a, h->cgc, h->mg, h->opt.tol_cg, h->opt.max_cg, h->stream);
+    } else if (mg) {
         SMM_CUDA(cudaMemcpyAsync(h->xcg, x, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         h->launches += smm::cgx_start(a, h->opt.tol_cg, h->opt.max_cg, h->mg, h->stream);
     } else {
@@ -638,7 +751,12 @@ smm_status run_cg(smm_handle h, double* x, int* iters) {
         SMM_CUDA(cudaGetLastError());
         chunk = std::min(chunk * 2, mg ? 16 : 64);
     }
-    if (mg) SMM_CUDA(cudaMemcpyAsync(x, h->xcg, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (cgm) {
+        smm::cgc_expand(h->cgc, h->xc, x, h->stream);  // the DG nodal values P varphi
+        h->launches += 1;
+    } else if (mg) {
+        SMM_CUDA(cudaMemcpyAsync(x, h->xcg, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
     if (iters) *iters = h->h_int[1];
     if (h->h_int[3]) return fail(SMM_ERR_NONFINITE, "non-finite value in the moment solve");
     if (h->h_int[1] >= h->opt.max_cg) {

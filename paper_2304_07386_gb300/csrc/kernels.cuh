@@ -192,10 +192,47 @@ struct MGPlan {
 };
 // cluster size for the coarse-level launch on the current device (8 or 16)
 int mg_coarse_cluster_size();
+// the coarse part of the V-cycle (vertex level from element-corner residual
+// sums cres [ne][4], aggregation levels, coarsest solve) as one cluster
+// launch; returns the vertex-level correction (device pointer, nvert floats)
+const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* ctl, cudaStream_t s);
 // z = V-cycle(r); returns the number of kernel launches; ctl (nullable): skip when set
 int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s);
 
 void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s);
+void launch_cgx_update(const CGArgs& a, cudaStream_t s);
+void launch_cgx_rz(const CGArgs& a, cudaStream_t s);
+void launch_cgx_direction(const CGArgs& a, cudaStream_t s);
+void launch_cg_init_scalars(const CGArgs& a, double tol, int max_iters, cudaStream_t s);
+
+// Continuous (CG) moment system, Sec. 5.1: element blocks on the continuous
+// node numbering, a V-cycle with point-Jacobi smoothing on the continuous
+// nodes over the same vertex / aggregation levels
+struct CGCPlan {
+    bool enabled = false;
+    int ne = 0, n = 0, nglob = 0, nu = 2, nblk_node = 1;
+    double omega = 0.0;                           // damping of the point-Jacobi smoother
+    const double* KT = nullptr;                   // [ne][n][n] column-major element blocks
+    const int* gid = nullptr;                     // [ne][n] global node of each element node
+    const int* grp = nullptr;                     // [nglob+1] element nodes of each global node (CSR)
+    const int* ginc = nullptr;                    // [ne*n]
+    const int* gown = nullptr;                    // [nglob] first element node of each global node
+    const float* minv = nullptr;                  // [nglob] 1 / number of element nodes
+    const double* dinv = nullptr;                 // [nglob] 1 / diag(A_CG)
+    double* ye = nullptr;                         // [ne][n] element products
+    double* xa = nullptr;                         // [nglob] V-cycle iterates
+    double* xb = nullptr;
+    double* res = nullptr;                        // [nglob] level-0 residual
+    float* cres = nullptr;                        // [ne][4] its element-corner restriction
+};
+// b = P^T b_dg (sum over the element nodes of each global node)
+void cgc_gather(const CGCPlan& c, const double* b_dg, double* b, cudaStream_t s);
+// dg = P x ; x = value of each global node's first element node
+void cgc_expand(const CGCPlan& c, const double* x, double* dg, cudaStream_t s);
+void cgc_pick(const CGCPlan& c, const double* dg, double* x, cudaStream_t s);
+// flexible CG on the continuous system: a.nrow = nglob, a.nblk = c.nblk_node
+int cgc_start(const CGArgs& a, const CGCPlan& c, const MGPlan& mg, double tol, int max_iters, cudaStream_t s);
+int cgc_iteration(const CGArgs& a, const CGCPlan& c, const MGPlan& mg, cudaStream_t s);
 int cgx_start(const CGArgs& a, double tol, int max_iters, const MGPlan& mg, cudaStream_t s);
 int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s);
 void cg_iterations(const CGArgs& a, int count, cudaStream_t s);

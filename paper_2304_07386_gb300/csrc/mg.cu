@@ -268,6 +268,27 @@ int mg_coarse_cluster_size() {
     return chosen;
 }
 
+const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* ctl, cudaStream_t s) {
+    CoarseArgs ca{};
+    ca.nvert = m.nvert; ca.nlev = m.nlev; ca.cres = cres; ca.vrp = m.vrp; ca.vinc = m.vinc;
+    for (int l = 0; l <= m.nlev; ++l) ca.lv[l] = m.lv[l];
+    ca.cinv = m.cinv;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(m.coarse_ctas, 1, 1);
+    cfg.blockDim = dim3(kCoarseThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = m.coarse_ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, coarse_cycle_kernel, ca, ctl);
+    return m.nlev > 1 ? m.lv[1].t : m.lv[1].x;
+}
+
 int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s) {
     switch (m.n) {
         case 4: return mg_apply_n<4>(m, r, z, ctl, s);
@@ -297,26 +318,7 @@ int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cuda
     }
     bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, r, xa, m.w4, m.res0, ctl);
     // vertex and aggregation levels and the coarsest solve (one cluster launch)
-    CoarseArgs ca{};
-    ca.nvert = m.nvert; ca.nlev = m.nlev; ca.cres = m.res0; ca.vrp = m.vrp; ca.vinc = m.vinc;
-    for (int l = 0; l <= m.nlev; ++l) ca.lv[l] = m.lv[l];
-    ca.cinv = m.cinv;
-    {
-        cudaLaunchConfig_t cfg{};
-        cudaLaunchAttribute attr[1];
-        cfg.gridDim = dim3(m.coarse_ctas, 1, 1);
-        cfg.blockDim = dim3(kCoarseThreads, 1, 1);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = m.coarse_ctas;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, coarse_cycle_kernel, ca, ctl);
-    }
-    const float* coarse_out = m.nlev > 1 ? m.lv[1].t : m.lv[1].x;
+    const float* coarse_out = launch_coarse_cycle(m, m.res0, ctl, s);
     const int rows0 = m.ne * N;
     prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, xa, ctl);
     launches += 3;

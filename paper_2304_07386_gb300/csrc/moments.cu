@@ -681,6 +681,15 @@ __global__ void diff_final_kernel(int nblk, const double* part, double* out) {
         default: KERNEL<25><<<__VA_ARGS__>>>(a); break;         \
     }
 
+// Flexible-CG pieces shared with the continuous moment solve (grid-stride
+// over a.nrow unknowns; the operator-product partials are a.part[0..a.nblk))
+void launch_cgx_update(const CGArgs& a, cudaStream_t s) { cgx_update_kernel<<<a.nvblk, 256, 0, s>>>(a); }
+void launch_cgx_rz(const CGArgs& a, cudaStream_t s) { cgx_rz_kernel<<<a.nvblk, 256, 0, s>>>(a); }
+void launch_cgx_direction(const CGArgs& a, cudaStream_t s) { cgx_direction_kernel<<<a.nvblk, 256, 0, s>>>(a); }
+void launch_cg_init_scalars(const CGArgs& a, double tol, int max_iters, cudaStream_t s) {
+    cg_init_scalars_kernel<<<1, 256, 0, s>>>(a, tol * tol, max_iters);
+}
+
 void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s) {
     const int tpb = cg_threads_per_block(a.n);
     if (a.AoT_dense) {

@@ -260,6 +260,50 @@ int factor_face_blocks(Setup& s, std::string& err) {
     return 0;
 }
 
+// Global node of every element node for the continuous space V_p: the
+// element nodes of a face are joined with the matching nodes of the
+// neighbour's face (union-find), ids numbered by first appearance.
+void continuous_numbering(Setup& s) {
+    const int ne = s.ne, n = s.n, p = s.p;
+    std::vector<int32_t> parent((size_t)ne * n);
+    for (size_t k = 0; k < parent.size(); ++k) parent[k] = (int32_t)k;
+    auto find = [&](int32_t x) {
+        while (parent[x] != x) {
+            parent[x] = parent[parent[x]];
+            x = parent[x];
+        }
+        return x;
+    };
+    for (int e = 0; e < ne; ++e)
+        for (int f = 0; f < 4; ++f) {
+            const int e2 = s.nbr[e * 4 + f];
+            if (e2 < 0) continue;
+            const int f2 = s.nbr_face[e * 4 + f], flip = s.nbr_flip[e * 4 + f];
+            for (int a = 0; a <= p; ++a) {
+                const int32_t r1 = find(e * n + face_node(p, f, a));
+                const int32_t r2 = find(e2 * n + face_node(p, f2, flip ? p - a : a));
+                if (r1 != r2) parent[std::max(r1, r2)] = std::min(r1, r2);
+            }
+        }
+    s.gid.assign((size_t)ne * n, -1);
+    std::vector<int32_t> id_of((size_t)ne * n, -1);
+    int ng = 0;
+    for (size_t k = 0; k < (size_t)ne * n; ++k) {
+        const int32_t r = find((int32_t)k);
+        if (id_of[r] < 0) id_of[r] = ng++;
+        s.gid[k] = id_of[r];
+    }
+    s.nglob = ng;
+    s.grp.assign((size_t)ng + 1, 0);
+    for (size_t k = 0; k < s.gid.size(); ++k) s.grp[(size_t)s.gid[k] + 1] += 1;
+    for (int g = 0; g < ng; ++g) s.grp[(size_t)g + 1] += s.grp[g];
+    s.ginc.assign(s.gid.size(), 0);
+    std::vector<int32_t> pos(s.grp.begin(), s.grp.end() - 1);
+    for (size_t k = 0; k < s.gid.size(); ++k) s.ginc[pos[s.gid[k]]++] = (int32_t)k;
+    s.gown.assign((size_t)ng, 0);
+    for (int g = 0; g < ng; ++g) s.gown[g] = s.ginc[s.grp[g]];
+}
+
 }  // namespace
 
 Rule1D gauss_legendre01(int n) {
@@ -646,6 +690,7 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
     s.Adiag.assign((size_t)ne * n * n, 0.0);
     s.Aoff.assign((size_t)ne * 4 * n * n, 0.0);
     s.Pinv.assign((size_t)ne * n * n, 0.0);
+    if (in.moment_cg) s.Kcg.assign((size_t)ne * n * n, 0.0);
     int sing = 0;
 #pragma omp parallel for schedule(static) reduction(+ : sing)
     for (int e = 0; e < ne; ++e) {
@@ -667,6 +712,7 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
                 }
                 continue;
             }
+
             const int f2 = s.nbr_face[e * 4 + f], flip = s.nbr_flip[e * 4 + f];
             const double st2 = s.sigma_t[e2], D2 = 1.0 / (3.0 * st2);
             const double kappa = in.kappa_scale * 0.5 *
@@ -701,6 +747,29 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
     }
     if (sing) { err = "singular diagonal block of the moment operator"; return 4; }
     if (int rc = factor_face_blocks(s, err)) return rc;
+
+    // ---- continuous (CG) moment system (Sec. 5.1): element blocks without any
+    //      interior-face term, and the continuous node numbering ----
+    if (in.moment_cg) {
+#pragma omp parallel for schedule(static)
+        for (int e = 0; e < ne; ++e) {
+            const double sa = s.sigma_t[e] - s.sigma_s[e], D = 1.0 / (3.0 * s.sigma_t[e]);
+            double* Kc = &s.Kcg[(size_t)e * n * n];
+            for (size_t ij = 0; ij < (size_t)n * n; ++ij)
+                Kc[ij] = D * (s.Kxx[(size_t)e * n * n + ij] + s.Kyy[(size_t)e * n * n + ij]) + sa * s.M[(size_t)e * n * n + ij];
+            for (int f = 0; f < 4; ++f) {
+                if (s.nbr[e * 4 + f] >= 0) continue;
+                const int b = s.bface_id[e * 4 + f];
+                const double* V1 = &faceV[((size_t)e * 4 + f) * nfq * n];
+                for (int q = 0; q < nfq; ++q) {
+                    const double c = s.b_eb0[(size_t)b * nfq + q] * s.b_ds[(size_t)b * nfq + q];
+                    for (int i = 0; i < n; ++i)
+                        for (int j = 0; j < n; ++j) Kc[(size_t)i * n + j] += c * V1[q * n + i] * V1[q * n + j];
+                }
+            }
+        }
+        continuous_numbering(s);
+    }
 
     // ---- fixed right-hand side: Q_0, Q_1 and J_in terms of Eq. ipsmm ----
     // Q_0 = sum_d w_d q_d, Q_1 = sum_d w_d Omega_d q_d (nodal)

@@ -36,6 +36,7 @@ struct Input {
     int inflow_kind = 0;                 // 0 vacuum, 1 nodal [nd][nb][p+1]
     const double* inflow = nullptr;
     double kappa_scale = 1.0;
+    int moment_cg = 0;                   // also build the continuous (CG) moment system
 };
 
 struct Setup {
@@ -73,6 +74,15 @@ struct Setup {
     std::vector<double> nds;                      // [ne][4][nfq][2]
     std::vector<double> bfixed;                   // [ne][n]
     std::vector<double> hK, area;
+    // continuous (CG) moment system, Sec. 5.1 (built when Input::moment_cg):
+    // element blocks D (Kxx + Kyy) + sigma_a M + Marshak boundary terms, the
+    // global node of every element node (element nodes identified across
+    // faces), the element nodes of every global node (CSR, element order) and
+    // the first of them
+    std::vector<double> Kcg;                      // [ne][n][n]
+    std::vector<int32_t> gid;                     // [ne][n]
+    int nglob = 0;
+    std::vector<int32_t> grp, ginc, gown;         // [nglob+1], [ne*n], [nglob]
 };
 
 // Node of element-local index (face f, face position a, line position t):
