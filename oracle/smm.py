@@ -24,10 +24,11 @@ class SMMProblem:
     """A discretization plus its data: q (per steradian, isotropic [ne][n]
     or angular [nd][ne][n]) and inflow psibar ([nd][n_bface][p+1] or None)."""
 
-    def __init__(self, disc: Discretization, q, psibar=None, kappa_scale=1.0):
+    def __init__(self, disc: Discretization, q, psibar=None, kappa_scale=1.0, fixup=False):
         self.disc = disc
         self.q = np.asarray(q, float)
         self.psibar = psibar
+        self.fixup = fixup
         self.A = ipsmm.assemble_lhs(disc, kappa_scale)
         self.Q = closures.source_moments(disc, self.q)
         self.jin = closures.j_in(disc, psibar)
@@ -39,7 +40,7 @@ class SMMProblem:
 
     def G(self, varphi):
         """One application of the fixed-point map; returns (varphi_new, psi)."""
-        psi = self.disc.sweep(varphi, self.q, self.psibar)
+        psi = self.disc.sweep(varphi, self.q, self.psibar, self.fixup)
         b = self.rhs_from_psi(psi)
         x = ipsmm.solve(self.A, b)
         return x.reshape(self.disc.ne, self.disc.n), psi

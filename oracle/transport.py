@@ -31,6 +31,23 @@ from .fem import Element, face_corners, face_nodes, face_point, lagrange, tensor
 from .quadrature import gauss_lobatto, level_symmetric_2d
 
 
+def zero_and_scale(A, x):
+    """Zero and scale negative flux fixup of one element solution (the fixup
+    Sec. 6.3 uses inside the sweep, cited there, not printed): negative nodal
+    values are set to zero and the rest scaled so that the element's particle
+    balance -- the local system tested with v = 1, sum_i (A x)_i, i.e.
+    outflow + collisions -- keeps its value; if that value is not positive
+    the element flux is set to zero."""
+    if np.all(x >= 0.0):
+        return x
+    c = A.sum(axis=0)                 # balance functional 1^T A
+    pos = np.maximum(x, 0.0)
+    t, tp = float(c @ x), float(c @ pos)
+    if t <= 0.0 or tp <= 0.0:
+        return np.zeros_like(x)
+    return (t / tp) * pos
+
+
 class CycleError(RuntimeError):
     pass
 
@@ -150,10 +167,12 @@ class Discretization:
             return np.zeros(len(self.elems[e].fq_s))
         return self.L1 @ psibar[d][self.bindex[(e, f)]]
 
-    def sweep_ordinate(self, d: int, src, psibar=None):
+    def sweep_ordinate(self, d: int, src, psibar=None, fixup=False):
         """Solve L psi_d = src_d with inflow psibar; src: [ne][n] nodal
         values of the total source for this ordinate; psibar: None (vacuum)
-        or [nd][n_bface][p+1] face-node values."""
+        or [nd][n_bface][p+1] face-node values.  fixup: apply the zero and
+        scale negative flux fixup to every element solution before it is
+        passed downwind."""
         psi = np.zeros((self.ne, self.n))
         for e in self.upwind_order(d):
             A = self.local_matrix(e, d)
@@ -166,9 +185,11 @@ class Discretization:
                     up = self.upwind_values(e, f, d, psi, psibar)
                     b = b - fd["V"].T @ (neg * up)
             psi[e] = np.linalg.solve(A, b)
+            if fixup:
+                psi[e] = zero_and_scale(A, psi[e])
         return psi
 
-    def sweep(self, varphi, q, psibar=None):
+    def sweep(self, varphi, q, psibar=None, fixup=False):
         """psi = L^{-1}(sigma_s/(4 pi) varphi + q) for all ordinates.
 
         varphi: [ne][n] nodal scalar flux (or None for zero);
@@ -181,7 +202,7 @@ class Discretization:
             scat = (self.sigma_s / (4.0 * math.pi))[:, None] * np.asarray(varphi, float)
         for d in range(self.nd):
             qd = q if q.ndim == 2 else q[d]
-            out[d] = self.sweep_ordinate(d, scat + qd, psibar)
+            out[d] = self.sweep_ordinate(d, scat + qd, psibar, fixup)
         return out
 
     # -- global assembly of one ordinate's DG system (brute force check) ------
