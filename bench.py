@@ -213,9 +213,11 @@ def run_ours(args) -> None:
     t_in = time.time() - t_in
     stream = torch.cuda.Stream()
 
-    def create(precision, solver=None, precond=None, anderson=0):
+    def create(precision, solver=None, precond=None, anderson=0, moment=None):
         opt = P.smm_default_options()
         opt.anderson_depth = anderson
+        if moment is not None:
+            opt.moment_discretization = moment
         opt.sweep_precision = precision
         opt.tol_cg = 1e-12
         if solver is not None:
@@ -364,8 +366,8 @@ def run_ours(args) -> None:
         extra["fp64_lu_step"] = time_steps(hlu)
         hlu.destroy()
 
-        def solve(precision, solver=None, precond=None, anderson=0):
-            hh, _ = create(precision, solver, precond, anderson)
+        def solve(precision, solver=None, precond=None, anderson=0, moment=None):
+            hh, _ = create(precision, solver, precond, anderson, moment)
             x = torch.zeros_like(phi)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -380,6 +382,13 @@ def run_ours(args) -> None:
         tc, sc, rcc, xc = solve(P.SMM_SWEEP_FP64)
         ta, sa, rca, xa = solve(P.SMM_SWEEP_FP64, anderson=2)
         t3, s3, rc3, x3 = solve(P.SMM_SWEEP_FP32_REFINED)
+        tg, sg, rcg, xg = solve(P.SMM_SWEEP_FP64, moment=P.smm.SMM_MOMENT_CG)
+        extra["time_to_1e-8_cg_moments"] = dict(
+            seconds=tg, outer=sg["outer_iterations"], cg_total=sg["cg_total"], status=rcg,
+            ms_solve_per_outer=sg["ms_solve"] / max(1, sg["outer_iterations"]),
+            rel_diff_vs_ip=float((xg - xc).abs().max() / xc.abs().max()),
+            method="continuous finite element moment system (Sec. 5.1), FP64 cached sweep, V-cycle-preconditioned "
+                   "CG on the continuous nodes; differs from the IP solution by the discretization error")
         extra["time_to_1e-8"] = dict(
             plain_s=tp, plain_outer=sp["outer_iterations"], plain_cg_total=sp["cg_total"], plain_status=rcp,
             plain="FP64 sweep with on-the-fly LU, element-block-Jacobi PCG, zero guess",
@@ -396,6 +405,8 @@ def run_ours(args) -> None:
         extra["batched_sweep"] = run_batch(args.batch, stream)
     if not args.quick and args.learned > 0:
         extra["learned_guess"] = run_learned(args.learned, stream)
+    if not args.quick:
+        extra["thick_thin"] = run_thick_thin(stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -582,6 +593,44 @@ def run_learned(nx: int, stream, n_train: int = 128, n_test: int = 8, p: int = 2
                 max_rel_diff_vs_plain=max(r["rel_diff_guess_vs_plain"] for r in rows),
                 note="times to a 1e-8 relative successive difference, inference included; the plain method is the "
                      "FP64 on-the-fly LU sweep with block-Jacobi PCG and a zero guess")
+
+
+def run_thick_thin(stream, nx: int = 256, blocks: int = 8, p: int = 3, sn: int = 12) -> dict:
+    """Multi-material thick/thin workload: [0,8]^2, nx x nx straight quads, a
+    seeded blocks x blocks layout of thick (sigma_t = 200, c = 0.999) and thin
+    (sigma_t = 0.2, c = 0.5) cells, unit isotropic source in the lowest-index
+    thin block, vacuum, p = 3, S12.  Time to a 1e-8 relative successive
+    difference from zero, outer iterations and CG iterations per outer step,
+    for the default method and with Anderson acceleration of depth 2."""
+    import numpy as np
+    import torch
+
+    import paper_2304_07386_gb300 as P
+    import smm_workloads as W
+
+    mesh = W.structured_mesh(nx, m=1, domain=(0.0, 8.0, 0.0, 8.0))
+    st, ss, blk, thick = W.block_materials(nx, blocks, 0)
+    src_blk = int(np.flatnonzero(~thick)[0])
+    n = (p + 1) ** 2
+    q = np.repeat((blk == src_blk).astype(np.float64)[:, None], n, axis=1)
+    out = dict(grid=f"{nx}x{nx}", p=p, sn=sn, thick_blocks=int(thick.sum()), blocks=blocks * blocks)
+    for name, depth in (("default", 0), ("anderson2", 2)):
+        opt = P.smm_default_options()
+        opt.anderson_depth = depth
+        h = P.smm_create(mesh.nodes, mesh.elem_nodes, 1, p, sn, st, ss, q, options=opt, stream=stream)
+        info = h.info()
+        x = torch.zeros(info.n_elem * info.n_dof_elem, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, s = P.smm_iterate(h, x, 1e-8, 200, relative=True, raise_on_error=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        out[name] = dict(seconds=dt, status=rc, outer=s["outer_iterations"],
+                         cg_per_outer=s["cg_total"] / max(1, s["outer_iterations"]), cg_max=s["cg_max"],
+                         angular_unknowns=int(info.n_angular))
+        h.destroy()
+    return out
 
 
 def run_reference(args) -> None:

@@ -124,6 +124,16 @@ typedef struct {
                                    passed as DG nodal values, and the solve
                                    returns P varphi (equal values at shared
                                    nodes). */
+    int32_t negative_flux_fixup; /* nonzero: the zero and scale negative flux
+                                   fixup inside the sweep (paper Sec. "Crooked
+                                   Pipe"): after each element solve, negative
+                                   nodal values are set to zero and the rest
+                                   scaled so that the element's particle
+                                   balance (local system tested with v = 1)
+                                   keeps its value (zero if that value is not
+                                   positive).  FP64 sweeps only
+                                   (INVALID_ARG with SMM_SWEEP_FP32_REFINED).
+                                   Default 0: SMM closures need no positivity. */
 } smm_options;
 
 typedef struct {

@@ -66,6 +66,8 @@ struct smm_ctx {
     float2 *ox2 = nullptr, *oy2 = nullptr, *Fx2 = nullptr, *Fy2 = nullptr, *inflow2 = nullptr;
     float2* psi2 = nullptr;
     float2* wq2 = nullptr;         // [6][nd] pairs of w_d (1, Ox, Oy, OxOx, OxOy, OyOy) for the pair moments
+    // negative flux fixup: column sums of M, Gx, Gy [ne][n] and of Fx, Fy over the test index [ne][4][p1]
+    double *colM = nullptr, *colGx = nullptr, *colGy = nullptr, *colFx = nullptr, *colFy = nullptr;
     std::vector<int32_t> tasks_host, level_start;  // level-sorted task list (for batching)
     // Anderson acceleration: rings of G(x_k) and f_k = G(x_k) - x_k (depth + 1 slots)
     std::vector<double*> aaG, aaF;
@@ -188,6 +190,7 @@ void smm_default_options(smm_options* opt) {
     opt->guess_check = 0;
     opt->mg_smooth_steps = 2;
     opt->moment_discretization = SMM_MOMENT_IP;
+    opt->negative_flux_fixup = 0;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -222,7 +225,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         (o.precond != SMM_PRECOND_BLOCK_JACOBI && o.precond != SMM_PRECOND_MULTIGRID) ||
         (o.sweep_solver != SMM_SOLVER_LU && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) || o.anderson_depth < 0 ||
         o.anderson_depth > 5 || o.mg_smooth_steps < 1 || o.mg_smooth_steps > 4 ||
-        (o.moment_discretization != SMM_MOMENT_IP && o.moment_discretization != SMM_MOMENT_CG))
+        (o.moment_discretization != SMM_MOMENT_IP && o.moment_discretization != SMM_MOMENT_CG) ||
+        (o.negative_flux_fixup && o.sweep_precision != SMM_SWEEP_FP64))
         return fail(SMM_ERR_INVALID_ARG, "bad options");
 
     smm::Input in;
@@ -263,6 +267,29 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     ok &= upload(h, h->Kxx, s.Kxx) && upload(h, h->Ks, s.Ks) && upload(h, h->Kyy, s.Kyy);
     ok &= upload(h, h->Dfx, s.Dfx) && upload(h, h->Dfy, s.Dfy) && upload(h, h->nds, s.nds) && upload(h, h->bfixed, s.bfixed);
     if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
+    if (o.negative_flux_fixup) {
+        const size_t nn = (size_t)s.n * s.n;
+        std::vector<double> cm((size_t)s.ne * s.n, 0.0), cgx(cm.size(), 0.0), cgy(cm.size(), 0.0);
+        std::vector<double> cfx((size_t)s.ne * 4 * s.p1, 0.0), cfy(cfx.size(), 0.0);
+        for (int e = 0; e < s.ne; ++e) {
+            for (int i = 0; i < s.n; ++i)
+                for (int j = 0; j < s.n; ++j) {
+                    cm[(size_t)e * s.n + j] += s.M[e * nn + (size_t)i * s.n + j];
+                    cgx[(size_t)e * s.n + j] += s.Gx[e * nn + (size_t)i * s.n + j];
+                    cgy[(size_t)e * s.n + j] += s.Gy[e * nn + (size_t)i * s.n + j];
+                }
+            for (int f = 0; f < 4; ++f)
+                for (int a = 0; a < s.p1; ++a)
+                    for (int b = 0; b < s.p1; ++b) {
+                        const size_t fo = (((size_t)e * 4 + f) * s.p1 + a) * s.p1 + b;
+                        cfx[((size_t)e * 4 + f) * s.p1 + b] += s.Fx[fo];
+                        cfy[((size_t)e * 4 + f) * s.p1 + b] += s.Fy[fo];
+                    }
+        }
+        ok &= upload(h, h->colM, cm) && upload(h, h->colGx, cgx) && upload(h, h->colGy, cgy) &&
+              upload(h, h->colFx, cfx) && upload(h, h->colFy, cfy);
+        if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
+    }
     {
         std::vector<double> t = transpose_blocks(s.Adiag, s.n);
         ok &= upload(h, h->AdT, t);
@@ -539,6 +566,8 @@ smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) 
     if constexpr (std::is_same<T, double>::value) {
         a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy;
         a.phi = phi; a.src = h->src; a.src_angular = h->src_angular; a.inflow = h->has_inflow ? h->inflow : nullptr;
+        a.fixup = h->opt.negative_flux_fixup ? 1 : 0;
+        a.colM = h->colM; a.colGx = h->colGx; a.colGy = h->colGy; a.colFx = h->colFx; a.colFy = h->colFy;
         a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr;
         if (h->cached) {
             smm::launch_source(h->ne, h->n, h->M, h->sigma_s, phi, h->src_angular ? nullptr : h->src, h->msrc2,

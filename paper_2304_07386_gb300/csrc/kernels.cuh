@@ -49,6 +49,14 @@ struct SweepArgs {
     const float2* Fy2;
     const float2* inflow2;
     float2* psi2;              // FP64 cached mode: psi as pairs (read by downwind tasks and the moments)
+    // zero and scale negative flux fixup (source mode): column sums of M, Gx, Gy [ne][n] and of the
+    // face matrices Fx, Fy over their test index [ne][4][p1]
+    int fixup;
+    const double* colM;
+    const double* colGx;
+    const double* colGy;
+    const double* colFx;
+    const double* colFy;
     const double* msrc;        // cached mode, SOURCE: [ne][n] M (sigma_s/(4pi) phi + q_iso) of this sweep
     const double* mq;          // cached mode, SOURCE, angular q: [ne][nd][n] M q_d, else nullptr
     T* psi;                    // [ne][nd][n] output, read by downwind tasks

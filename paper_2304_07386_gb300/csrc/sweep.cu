@@ -289,11 +289,44 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
             }
         }
 
+        // ---- zero and scale negative flux fixup (source mode): negative nodal
+        //      values are zeroed and the rest scaled so that the element balance
+        //      c . x, c = 1^T A (column sums of the local operator), keeps its
+        //      value; warp-uniform branch, taken only when a value is negative ----
+        bool fixed = false;
+        if (MODE == SWEEP_SOURCE && a.fixup && __any_sync(FULL, lane < N && x < T(0))) {
+            double c = 0.0;
+            if (lane < N) {
+                const size_t eo = (size_t)e * N + lane;
+                c = a.sigma_t[e] * a.colM[eo] - a.ox[d] * a.colGx[eo] - a.oy[d] * a.colGy[eo];
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const bool on = (f == 0 && iy == 0) || (f == 1 && ix == P) || (f == 2 && iy == P) ||
+                                    (f == 3 && ix == 0);
+                    if (dir[f] > 0 && on) {
+                        const int fa = (f == 0 || f == 2) ? ix : iy;
+                        const size_t fo = ((size_t)e * 4 + f) * P1 + fa;
+                        c += a.ox[d] * a.colFx[fo] + a.oy[d] * a.colFy[fo];
+                    }
+                }
+            }
+            const double xv = lane < N ? (double)x : 0.0, xp = xv > 0.0 ? xv : 0.0;
+            double t = c * xv, tp = c * xp;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                t += __shfl_xor_sync(FULL, t, o);
+                tp += __shfl_xor_sync(FULL, tp, o);
+            }
+            const double alpha = (t > 0.0 && tp > 0.0) ? t / tp : 0.0;
+            x = (T)(alpha * xp);
+            fixed = true;
+        }
+
         // ---- publish ----
         if (lane < N) {
             const size_t o = ((size_t)e * nd + d) * N + lane;
             a.psi[o] = x;
-            if constexpr (DF) a.psi2[o] = df_norm(ys, yc);
+            if constexpr (DF) a.psi2[o] = fixed ? df_make((double)x) : df_norm(ys, yc);
             if (MODE == SWEEP_RESIDUAL) a.psi_acc[o] += (double)x;
         }
         __threadfence();  // one warp-wide fence instruction orders every lane's stores
