@@ -24,11 +24,14 @@ class SMMProblem:
     """A discretization plus its data: q (per steradian, isotropic [ne][n]
     or angular [nd][ne][n]) and inflow psibar ([nd][n_bface][p+1] or None)."""
 
-    def __init__(self, disc: Discretization, q, psibar=None, kappa_scale=1.0, fixup=False):
+    def __init__(self, disc: Discretization, q, psibar=None, kappa_scale=1.0, fixup=False, tiles=1):
         self.disc = disc
         self.q = np.asarray(q, float)
         self.psibar = psibar
         self.fixup = fixup
+        # parallel block Jacobi sweep: tile ids and the previous sweep's psi (zero at first)
+        self.block = disc.element_tiles(tiles) if tiles > 1 else None
+        self.psi_prev = np.zeros((disc.nd, disc.ne, disc.n))
         self.A = ipsmm.assemble_lhs(disc, kappa_scale)
         self.Q = closures.source_moments(disc, self.q)
         self.jin = closures.j_in(disc, psibar)
@@ -40,7 +43,9 @@ class SMMProblem:
 
     def G(self, varphi):
         """One application of the fixed-point map; returns (varphi_new, psi)."""
-        psi = self.disc.sweep(varphi, self.q, self.psibar, self.fixup)
+        psi = self.disc.sweep(varphi, self.q, self.psibar, self.fixup, self.block,
+                              self.psi_prev if self.block is not None else None)
+        self.psi_prev = psi
         b = self.rhs_from_psi(psi)
         x = ipsmm.solve(self.A, b)
         return x.reshape(self.disc.ne, self.disc.n), psi

@@ -108,22 +108,40 @@ class Discretization:
         self.L1, _ = lagrange(gp, self.elems[0].fq_s) if self.ne else (None, None)
 
     # -- upwind graph -------------------------------------------------------
-    def upwind_order(self, d: int):
+    def element_tiles(self, tiles: int):
+        """Tile of every element for the parallel block Jacobi sweep: the
+        mesh's bounding box cut into tiles x tiles equal rectangles, an
+        element belonging to the rectangle holding the mean of its four
+        corner control points (ids by * tiles + bx)."""
+        ctrl = np.array([el.ctrl for el in self.elems])          # [ne][(m+1)^2][2]
+        m = self.m
+        corners = ctrl[:, [0, m, m * (m + 1), m * (m + 1) + m], :].mean(axis=1)
+        allp = ctrl.reshape(-1, 2)
+        lo, hi = allp.min(axis=0), allp.max(axis=0)
+        t = np.minimum(((corners - lo) / (hi - lo) * tiles).astype(int), tiles - 1)
+        return t[:, 1] * tiles + t[:, 0]
+
+    def upwind_order(self, d: int, block=None):
         """Topological order of the elements for ordinate d (smallest index
-        first among ready elements); raises CycleError on a cycle."""
+        first among ready elements); with a tile array, upwind neighbours in
+        another tile are not dependencies (their values are lagged).  Raises
+        CycleError on a cycle."""
         if not hasattr(self, "_orders"):
             self._orders = {}
-        if d not in self._orders:
-            self._orders[d] = self._topological_order(d)
-        return self._orders[d]
+        key = (d, None if block is None else tuple(block))
+        if key not in self._orders:
+            self._orders[key] = self._topological_order(d, block)
+        return self._orders[key]
 
-    def _topological_order(self, d: int):
+    def _topological_order(self, d: int, block=None):
         om = self.omega[d]
         deps = [set() for _ in range(self.ne)]
         for e in range(self.ne):
             for f in range(4):
                 nb = self.nbr[e][f]
                 if nb is None:
+                    continue
+                if block is not None and block[nb[0]] != block[e]:
                     continue
                 a = self.faces[e][f]["nds"] @ om
                 if np.any(a < 0.0):
@@ -167,14 +185,16 @@ class Discretization:
             return np.zeros(len(self.elems[e].fq_s))
         return self.L1 @ psibar[d][self.bindex[(e, f)]]
 
-    def sweep_ordinate(self, d: int, src, psibar=None, fixup=False):
+    def sweep_ordinate(self, d: int, src, psibar=None, fixup=False, block=None, psi_lag=None):
         """Solve L psi_d = src_d with inflow psibar; src: [ne][n] nodal
         values of the total source for this ordinate; psibar: None (vacuum)
         or [nd][n_bface][p+1] face-node values.  fixup: apply the zero and
         scale negative flux fixup to every element solution before it is
-        passed downwind."""
+        passed downwind.  block/psi_lag: parallel block Jacobi sweep (Sec.
+        6.5) -- an upwind neighbour in another tile contributes its value
+        from psi_lag [ne][n] (the previous sweep) instead of this one."""
         psi = np.zeros((self.ne, self.n))
-        for e in self.upwind_order(d):
+        for e in self.upwind_order(d, block):
             A = self.local_matrix(e, d)
             b = self.M[e] @ src[e]
             for f in range(4):
@@ -182,14 +202,16 @@ class Discretization:
                 a = fd["nds"] @ self.omega[d]
                 neg = np.minimum(a, 0.0)
                 if np.any(neg < 0.0):
-                    up = self.upwind_values(e, f, d, psi, psibar)
+                    nb = self.nbr[e][f]
+                    lagged = block is not None and nb is not None and block[nb[0]] != block[e]
+                    up = self.upwind_values(e, f, d, psi_lag if lagged else psi, psibar)
                     b = b - fd["V"].T @ (neg * up)
             psi[e] = np.linalg.solve(A, b)
             if fixup:
                 psi[e] = zero_and_scale(A, psi[e])
         return psi
 
-    def sweep(self, varphi, q, psibar=None, fixup=False):
+    def sweep(self, varphi, q, psibar=None, fixup=False, block=None, psi_lag=None):
         """psi = L^{-1}(sigma_s/(4 pi) varphi + q) for all ordinates.
 
         varphi: [ne][n] nodal scalar flux (or None for zero);
@@ -202,7 +224,8 @@ class Discretization:
             scat = (self.sigma_s / (4.0 * math.pi))[:, None] * np.asarray(varphi, float)
         for d in range(self.nd):
             qd = q if q.ndim == 2 else q[d]
-            out[d] = self.sweep_ordinate(d, scat + qd, psibar, fixup)
+            out[d] = self.sweep_ordinate(d, scat + qd, psibar, fixup, block,
+                                         None if psi_lag is None else psi_lag[d])
         return out
 
     # -- global assembly of one ordinate's DG system (brute force check) ------
