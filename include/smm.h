@@ -134,6 +134,18 @@ typedef struct {
                                    positive).  FP64 sweeps only
                                    (INVALID_ARG with SMM_SWEEP_FP32_REFINED).
                                    Default 0: SMM closures need no positivity. */
+    int32_t sweep_tiles;        /* T > 1: parallel block Jacobi sweep (paper Sec.
+                                   "Weak Scaling"): the mesh's bounding box is
+                                   cut into T x T tiles, an element belongs to
+                                   the tile holding the mean of its four corner
+                                   control points, every tile sweeps its own
+                                   elements, and inflow across tile borders is
+                                   taken from the previous sweep (zero at
+                                   first).  Shortens the sweep's dependency
+                                   chains; the outer iteration needs more steps
+                                   and converges to the same fixed point.
+                                   1..64, default 1 (exact sweep); FP64 sweeps
+                                   only. */
 } smm_options;
 
 typedef struct {

@@ -66,6 +66,8 @@ struct smm_ctx {
     float2 *ox2 = nullptr, *oy2 = nullptr, *Fx2 = nullptr, *Fy2 = nullptr, *inflow2 = nullptr;
     float2* psi2 = nullptr;
     float2* wq2 = nullptr;         // [6][nd] pairs of w_d (1, Ox, Oy, OxOx, OxOy, OyOy) for the pair moments
+    double* psi_lag = nullptr;     // block Jacobi sweep: previous sweep's psi (on-the-fly LU mode)
+    float2* psi2_lag = nullptr;    // ... and its pairs (cached-inverse mode)
     // negative flux fixup: column sums of M, Gx, Gy [ne][n] and of Fx, Fy over the test index [ne][4][p1]
     double *colM = nullptr, *colGx = nullptr, *colGy = nullptr, *colFx = nullptr, *colFy = nullptr;
     std::vector<int32_t> tasks_host, level_start;  // level-sorted task list (for batching)
@@ -191,6 +193,7 @@ void smm_default_options(smm_options* opt) {
     opt->mg_smooth_steps = 2;
     opt->moment_discretization = SMM_MOMENT_IP;
     opt->negative_flux_fixup = 0;
+    opt->sweep_tiles = 1;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -226,7 +229,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         (o.sweep_solver != SMM_SOLVER_LU && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) || o.anderson_depth < 0 ||
         o.anderson_depth > 5 || o.mg_smooth_steps < 1 || o.mg_smooth_steps > 4 ||
         (o.moment_discretization != SMM_MOMENT_IP && o.moment_discretization != SMM_MOMENT_CG) ||
-        (o.negative_flux_fixup && o.sweep_precision != SMM_SWEEP_FP64))
+        (o.negative_flux_fixup && o.sweep_precision != SMM_SWEEP_FP64) || o.sweep_tiles < 1 || o.sweep_tiles > 64 ||
+        (o.sweep_tiles > 1 && o.sweep_precision != SMM_SWEEP_FP64))
         return fail(SMM_ERR_INVALID_ARG, "bad options");
 
     smm::Input in;
@@ -235,6 +239,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     in.source_kind = source_kind; in.q = q; in.inflow_kind = inflow_kind; in.inflow = inflow;
     in.kappa_scale = o.kappa_scale;
     in.moment_cg = o.moment_discretization == SMM_MOMENT_CG;
+    in.sweep_tiles = o.sweep_tiles;
     smm::Setup s;
     std::string err;
     int rc = smm::build_setup(in, s, err);
@@ -309,6 +314,10 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
     const size_t nang = (size_t)s.ne * s.nd * s.n, nphi = (size_t)s.ne * s.n;
     h->psi = h->alloc<double>(nang);
+    if (o.sweep_tiles > 1 && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) {
+        h->psi_lag = h->alloc<double>(nang);
+        if (!h->psi_lag) return bail(SMM_ERR_OOM, "device allocation failed");
+    }
     if (h->fp32) {
         h->dpsi = h->alloc<float>(nang);
         h->res = h->alloc<float>(nang);
@@ -494,6 +503,10 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             if (!okp || !h->psi2) return bail(SMM_ERR_OOM, "device allocation failed");
             if (cudaMemsetAsync(h->psi2, 0, nang * sizeof(float2), h->stream) != cudaSuccess)
                 return bail(SMM_ERR_CUDA, "cudaMemsetAsync failed");
+            if (o.sweep_tiles > 1) {
+                h->psi2_lag = h->alloc<float2>(nang);
+                if (!h->psi2_lag) return bail(SMM_ERR_OOM, "device allocation failed");
+            }
         }
         if (h->fp32) {
             h->ainv32 = h->alloc<float>(ninv);
@@ -569,6 +582,19 @@ smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) 
         a.fixup = h->opt.negative_flux_fixup ? 1 : 0;
         a.colM = h->colM; a.colGx = h->colGx; a.colGy = h->colGy; a.colFx = h->colFx; a.colFy = h->colFy;
         a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr;
+        if (h->opt.sweep_tiles > 1) {
+            // block Jacobi sweep: the previous sweep's psi feeds the faces between tiles
+            const size_t nang = (size_t)h->ne * h->nd * h->n;
+            if (h->cached) {
+                SMM_CUDA(cudaMemcpyAsync(h->psi2_lag, h->psi2, nang * sizeof(float2), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+            } else {
+                SMM_CUDA(cudaMemcpyAsync(h->psi_lag, h->psi, nang * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+            }
+            a.psi_lag = h->psi_lag;
+            a.psi2_lag = h->psi2_lag;
+        }
         if (h->cached) {
             smm::launch_source(h->ne, h->n, h->M, h->sigma_s, phi, h->src_angular ? nullptr : h->src, h->msrc2,
                                h->stream);

@@ -49,6 +49,9 @@ struct SweepArgs {
     const float2* Fy2;
     const float2* inflow2;
     float2* psi2;              // FP64 cached mode: psi as pairs (read by downwind tasks and the moments)
+    // block Jacobi sweep: the previous sweep's psi, read across tiles (fdir == -2)
+    const T* psi_lag;
+    const float2* psi2_lag;
     // zero and scale negative flux fixup (source mode): column sums of M, Gx, Gy [ne][n] and of the
     // face matrices Fx, Fy over their test index [ne][4][p1]
     int fixup;

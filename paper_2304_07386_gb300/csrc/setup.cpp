@@ -606,6 +606,41 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
         return 5;
     }
 
+    // ---- parallel block Jacobi sweep (Sec. 6.5): tiles of the bounding box by
+    //      the mean of each element's corner control points; inflow from another
+    //      tile is lagged (previous sweep) and is no dependency ----
+    s.tile.assign(ne, 0);
+    if (in.sweep_tiles > 1) {
+        const int T = in.sweep_tiles, m = in.m, nc = (m + 1) * (m + 1);
+        double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+        for (size_t k = 0; k < (size_t)ne * nc; ++k)
+            for (int c = 0; c < 2; ++c) {
+                const double v = in.nodes[2 * (size_t)in.elem_nodes[k] + c];
+                lo[c] = std::min(lo[c], v);
+                hi[c] = std::max(hi[c], v);
+            }
+        const int cidx[4] = {0, m, m * (m + 1), m * (m + 1) + m};
+        for (int e = 0; e < ne; ++e) {
+            int t[2];
+            for (int c = 0; c < 2; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < 4; ++k) acc += in.nodes[2 * (size_t)in.elem_nodes[(size_t)e * nc + cidx[k]] + c];
+                const double cen = acc / 4.0;
+                t[c] = std::min((int)((cen - lo[c]) / (hi[c] - lo[c]) * T), T - 1);
+            }
+            s.tile[e] = t[1] * T + t[0];
+        }
+        for (int e = 0; e < ne; ++e)
+            for (int f = 0; f < 4; ++f) {
+                const int e2 = s.nbr[e * 4 + f];
+                if (e2 < 0 || s.tile[e2] == s.tile[e]) continue;
+                for (int d = 0; d < nd; ++d) {
+                    int8_t& fd = s.fdir[((size_t)e * nd + d) * 4 + f];
+                    if (fd < 0) fd = -2;
+                }
+            }
+    }
+
     // ---- upwind levels per ordinate (Kahn), task list sorted by (level, e, d) ----
     s.level.assign((size_t)nd * ne, -1);
     int maxlev = 0;
@@ -617,7 +652,7 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
             for (int e = 0; e < ne; ++e) {
                 int c = 0;
                 for (int f = 0; f < 4; ++f)
-                    if (s.nbr[e * 4 + f] >= 0 && s.fdir[((size_t)e * nd + d) * 4 + f] < 0) ++c;
+                    if (s.nbr[e * 4 + f] >= 0 && s.fdir[((size_t)e * nd + d) * 4 + f] == -1) ++c;
                 indeg[e] = c;
                 if (c == 0) { lev[e] = 0; queue[tail++] = e; }
             }
@@ -626,6 +661,7 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
                 for (int f = 0; f < 4; ++f) {
                     int v = s.nbr[u * 4 + f];
                     if (v < 0 || s.fdir[((size_t)u * nd + d) * 4 + f] <= 0) continue;  // u -> v through u's outflow face
+                    if (s.tile[v] != s.tile[u]) continue;                                // lagged across tiles
                     lev[v] = std::max(lev[v], lev[u] + 1);
                     if (--indeg[v] == 0) queue[tail++] = v;
                 }

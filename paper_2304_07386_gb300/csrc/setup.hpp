@@ -37,6 +37,7 @@ struct Input {
     const double* inflow = nullptr;
     double kappa_scale = 1.0;
     int moment_cg = 0;                   // also build the continuous (CG) moment system
+    int sweep_tiles = 1;                 // parallel block Jacobi sweep over tiles x tiles tiles (1: exact)
 };
 
 struct Setup {
@@ -50,7 +51,9 @@ struct Setup {
     std::vector<double> sigma_t, sigma_s;
     std::vector<double> M, Gx, Gy;                // [ne][n][n], row = test function
     std::vector<double> Fx, Fy;                   // [ne][4][p1][p1]
-    std::vector<int8_t> fdir;                     // [ne][nd][4]: +1 out, -1 in, 0 none
+    std::vector<int8_t> fdir;                     // [ne][nd][4]: +1 out, -1 in, -2 in from another tile
+                                                  // (lagged: previous sweep's values), 0 none
+    std::vector<int32_t> tile;                    // [ne] tile of the block Jacobi sweep (all 0: exact sweep)
     std::vector<int32_t> level;                   // [nd][ne]
     std::vector<int32_t> tasks;                   // e*nd + d sorted by (level, e, d)
     std::vector<int32_t> level_start;             // [nlevels+1] offsets into tasks

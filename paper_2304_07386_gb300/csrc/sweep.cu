@@ -136,7 +136,8 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
             const int f = lane;
             const int df = f == 0 ? dir[0] : (f == 1 ? dir[1] : (f == 2 ? dir[2] : dir[3]));
             const int nb = a.nbr[e * 4 + f];
-            if (df < 0 && nb >= 0) ok = wait_epoch(a.done + (size_t)nb * nd + d, a.epoch, a.timeout_ns, a.err);
+            // (-2: inflow from another tile of a block Jacobi sweep, taken from the previous sweep)
+            if (df == -1 && nb >= 0) ok = wait_epoch(a.done + (size_t)nb * nd + d, a.epoch, a.timeout_ns, a.err);
         }
         ok = __all_sync(FULL, ok);
         if (!ok) {
@@ -203,7 +204,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                         const int f2 = a.nbr_face[e * 4 + f];
                         const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
                         const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
-                        u = __ldcg(a.psi2 + ((size_t)nb * nd + d) * N + node);
+                        u = __ldcg((df == -2 ? a.psi2_lag : a.psi2) + ((size_t)nb * nd + d) * N + node);
                     } else if (MODE == SWEEP_SOURCE && a.inflow2) {
                         const int bi = a.bface_id[e * 4 + f];
                         u = a.inflow2[((size_t)bi * nd + d) * P1 + lc];
@@ -237,7 +238,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                         const int f2 = a.nbr_face[e * 4 + f];
                         const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
                         const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
-                        upv = ldg_cg(a.psi + ((size_t)nb * nd + d) * N + node);
+                        upv = ldg_cg((df == -2 ? a.psi_lag : a.psi) + ((size_t)nb * nd + d) * N + node);
                     } else if (MODE == SWEEP_SOURCE && a.inflow) {
                         const int bi = a.bface_id[e * 4 + f];
                         upv = (T)a.inflow[((size_t)bi * nd + d) * P1 + lc];
