@@ -156,7 +156,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per launch measured by ncu for the current kernels
 # on this workload (the cg_iteration, sweep-kernel and launch-list summaries for this workload); a key
 # is dropped whenever the kernels it covers change.
-NCU_TRAFFIC: dict = {"cg_iteration": 637.0e6, "sweep_kernel": 3882.7e6, "moments": 138.8e6}
+NCU_TRAFFIC: dict = {"cg_iteration": None, "sweep_kernel": None, "moments": 138.8e6}
 
 # a timed step is outer iteration START_ITERATIONS + 1 from varphi^0 = 0
 START_ITERATIONS = 3
@@ -180,14 +180,16 @@ def mg_cg_bytes_per_iter(ne: int, n: int) -> float:
     """HBM bytes of one multigrid-preconditioned CG iteration on the element
     blocks.  The operator is stored as the n x n diagonal block plus four
     G x G face-coupling matrices per element (G = 2(p+1)): the FP64 product
-    reads it once (8 (n^2 + 4 G^2) B); the V-cycle's level 0 applies the FP32
-    copy four times (second pre-smoothing step, residual, two post-smoothing
-    steps) and the FP32 block-Jacobi inverse four times (16 (n^2 + 4 G^2)
-    + 16 n^2 B); about 30 FP64 vector passes of n words each.  The vertex and
+    reads it once (8 (n^2 + 4 G^2) B); the V-cycle's level 0 reads the FP32
+    block-Jacobi inverse in all four smoothing steps (16 n^2 B), the FP32 face
+    couplings in the three steps that start from a nonzero iterate and in the
+    residual (64 G^2 B), and the FP32 diagonal block in the residual only
+    (4 n^2 B; a smoothing step needs no diagonal block because Pinv is its
+    inverse); about 30 FP64 vector passes of n words each.  The vertex and
     aggregation levels are < 2 % of the bytes and left out."""
     g = 2 * (int(round(n ** 0.5)))
     op = n * n + 4 * g * g
-    return ne * (8 * op + 16 * op + 16 * n * n + 30 * n * 8)
+    return ne * (8 * op + 16 * n * n + 64 * g * g + 4 * n * n + 30 * n * 8)
 
 
 def run_ours(args) -> None:
@@ -307,9 +309,10 @@ def run_ours(args) -> None:
                     launches_per_step=launches_per_step, kernel=kernel, peak_note=f"{hbm_src} copy bandwidth")
 
     rooflines = {
-        "cg_iteration": entry(cg_bytes, ms_iter, "one flexible-CG iteration: CUDA graph of 10 kernels (operator "
-                              "product, update, V-cycle: 4 smoothing steps, residual, cluster coarse cycle, "
-                              "prolongation; dot products, direction)", "cg_iteration", cg_it),
+        "cg_iteration": entry(cg_bytes, ms_iter, "one flexible-CG iteration: CUDA graph of 10 kernels (staged "
+                              "operator product; V-cycle: first smoothing step with the CG update, smoothing step, "
+                              "residual, cluster coarse cycle, prolongation, smoothing step, last smoothing step "
+                              "with the dot products; one-block finish; direction)", "cg_iteration", cg_it),
         "sweep_kernel": entry(sweep_bytes, ms_sweep, "sweep_kernel<double, 4, SOURCE, cached inverse> "
                               "(plus the per-sweep source kernel)", "sweep_kernel", 1),
         "moments": entry(mom_bytes, ms_mom, "moments_df_kernel + beta_kernel", "moments", 1),

@@ -113,11 +113,13 @@ struct smm_ctx {
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     long long launches = 0;
 
+    // every array carries 16 bytes of slack after its end, so that a bulk
+    // prefetch of a span rounded up to 16 bytes stays inside the allocation
     template <class T>
     T* alloc(size_t count) {
         if (count == 0) count = 1;
         void* ptr = nullptr;
-        if (cudaMalloc(&ptr, count * sizeof(T)) != cudaSuccess) return nullptr;
+        if (cudaMalloc(&ptr, count * sizeof(T) + 16) != cudaSuccess) return nullptr;
         allocs.push_back(ptr);
         return (T*)ptr;
     }
@@ -150,6 +152,25 @@ bool upload_f32(smm_ctx* h, float*& dst, const std::vector<T>& src) {
 }
 
 // transpose each n x n block ([blk][i][j] -> [blk][j][i])
+// k-major ELL copy of a CSR pattern with values val (in CSR order): entry k
+// of row i at [k * nrow + i]; width = the longest row; padding entries repeat
+// the row's first column (column 0 for an empty row) with value 0
+void to_ell(const smm::CSR& A, const std::vector<double>& val, int& width, std::vector<int>& ci,
+            std::vector<float>& v) {
+    width = 0;
+    for (int i = 0; i < A.nrow; ++i) width = std::max(width, A.rp[i + 1] - A.rp[i]);
+    ci.assign((size_t)width * A.nrow, 0);
+    v.assign((size_t)width * A.nrow, 0.0f);
+    for (int i = 0; i < A.nrow; ++i) {
+        const int k0 = A.rp[i], len = A.rp[i + 1] - k0;
+        for (int k = 0; k < width; ++k) {
+            const size_t o = (size_t)k * A.nrow + i;
+            ci[o] = k < len ? A.ci[k0 + k] : (len > 0 ? A.ci[k0] : 0);
+            v[o] = k < len ? (float)val[k0 + k] : 0.0f;
+        }
+    }
+}
+
 // FP32 pairs (hi, lo) with hi + lo = v to 2^-48
 std::vector<float2> to_pairs(const std::vector<double>& v) {
     std::vector<float2> out(v.size());
@@ -339,9 +360,9 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     const int epb = smm::cg_threads_per_block(s.n) / s.n;
     h->cg_nblk = (s.ne + epb - 1) / epb;
     h->cg_nvblk = std::max(1, std::min(2 * h->sms, (int)((nphi + 255) / 256)));
-    // partial sums: [3][max(element blocks, continuous-node blocks)] then [3][vector blocks]
+    // partial sums: [4][max(element blocks, continuous-node blocks)] then [3][vector blocks]
     h->cg_pmax = std::max(h->cg_nblk, std::max(1, (s.nglob + 255) / 256));
-    h->part = h->alloc<double>(3 * (size_t)h->cg_pmax + 3 * (size_t)h->cg_nvblk);
+    h->part = h->alloc<double>(4 * (size_t)h->cg_pmax + 3 * (size_t)h->cg_nvblk);
     h->scal = h->alloc<double>(8);
     h->ctl = h->alloc<int>(8);
     h->dpart = h->alloc<double>(2 * 256);
@@ -399,10 +420,20 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             ok &= P.x0 && P.x0b && P.res0;
         }
         P.nvert = H.nvert;
-        int *vid = nullptr, *vrp = nullptr, *vinc = nullptr;
+        int *vid = nullptr, *vinc = nullptr;
         float* w4 = nullptr;
-        ok &= upload(h, vid, H.vid) && upload(h, vrp, H.vrp) && upload(h, vinc, H.vinc) && upload_f32(h, w4, H.w4);
-        P.vid = vid; P.vrp = vrp; P.vinc = vinc; P.w4 = w4;
+        {
+            // vertex incidences as k-major ELL with -1 padding
+            int vw = 0;
+            for (int v = 0; v < H.nvert; ++v) vw = std::max(vw, H.vrp[v + 1] - H.vrp[v]);
+            std::vector<int> ell((size_t)vw * H.nvert, -1);
+            for (int v = 0; v < H.nvert; ++v)
+                for (int k = H.vrp[v]; k < H.vrp[v + 1]; ++k) ell[(size_t)(k - H.vrp[v]) * H.nvert + v] = H.vinc[k];
+            ok &= upload(h, vinc, ell);
+            P.vw = vw;
+        }
+        ok &= upload(h, vid, H.vid) && upload_f32(h, w4, H.w4);
+        P.vid = vid; P.vinc = vinc; P.w4 = w4;
         P.nlev = (int)H.lv.size() - 1;
         P.coarse_ctas = smm::mg_coarse_cluster_size();
         for (int l = 1; l <= P.nlev; ++l) {
@@ -414,26 +445,58 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             D.t = h->alloc<float>(D.n);
             ok &= D.b && D.x && D.r && D.t;
             if (l < P.nlev) {
-                int *arp, *aci, *prp, *pci, *rrp, *rci;
-                float *av, *dv, *pv, *rv;
-                ok &= upload(h, arp, L.A.rp) && upload(h, aci, L.A.ci) && upload_f32(h, av, L.A.v) &&
-                      upload_f32(h, dv, L.dinv);
-                ok &= upload(h, prp, L.P.rp) && upload(h, pci, L.P.ci) && upload_f32(h, pv, L.P.v);
-                ok &= upload(h, rrp, L.R.rp) && upload(h, rci, L.R.ci) && upload_f32(h, rv, L.R.v);
                 std::vector<double> asv(L.A.v.size());
                 for (int i = 0; i < L.A.nrow; ++i)
                     for (int k = L.A.rp[i]; k < L.A.rp[i + 1]; ++k)
                         asv[k] = L.A.v[k] * L.omega * L.dinv[L.A.ci[k]];
-                float* asd = nullptr;
-                ok &= upload_f32(h, asd, asv);
-                D.Asv = asd;
-                D.Arp = arp; D.Aci = aci; D.Av = av; D.dinv = dv; D.Prp = prp; D.Pci = pci; D.Pv = pv;
-                D.Rrp = rrp; D.Rci = rci; D.Rv = rv;
+                std::vector<int> ci;
+                std::vector<float> v, vs;
+                int *aci, *pci, *rci;
+                float *av, *asd, *dv, *pv, *rv;
+                to_ell(L.A, asv, D.aw, ci, vs);
+                to_ell(L.A, L.A.v, D.aw, ci, v);
+                ok &= upload(h, aci, ci) && upload(h, av, v) && upload(h, asd, vs) && upload_f32(h, dv, L.dinv);
+                to_ell(L.P, L.P.v, D.pw, ci, v);
+                ok &= upload(h, pci, ci) && upload(h, pv, v);
+                to_ell(L.R, L.R.v, D.rw, ci, v);
+                ok &= upload(h, rci, ci) && upload(h, rv, v);
+                D.Aci = aci; D.Av = av; D.Asv = asd; D.dinv = dv; D.Pci = pci; D.Pv = pv; D.Rci = rci; D.Rv = rv;
             }
         }
         float* cinv = nullptr;
         ok &= upload_f32(h, cinv, H.coarse_inv);
         P.cinv = cinv;
+        // the coarse levels' read-only data in 32 KB chunks, prefetched into L2
+        // by the level-0 residual kernel just before the coarse cycle reads it
+        // (each span rounded up to 16 bytes stays inside its allocation's slack)
+        {
+            std::vector<smm::L2Chunk> pf;
+            auto span = [&pf](const void* p, size_t bytes) {
+                constexpr size_t kChunk = 32768;
+                const size_t rb = (bytes + 15) & ~(size_t)15;
+                for (size_t o = 0; p && o < rb; o += kChunk)
+                    pf.push_back(smm::L2Chunk{(const char*)p + o, (unsigned)std::min(kChunk, rb - o), 0u});
+            };
+            span(P.vinc, (size_t)P.vw * H.nvert * sizeof(int));
+            for (int l = 1; l < P.nlev; ++l) {
+                const smm::MGLevel& L = H.lv[l];
+                const smm::MGLevelDev& D = P.lv[l];
+                const size_t a = (size_t)D.aw * L.A.nrow, pe = (size_t)D.pw * L.P.nrow, re = (size_t)D.rw * L.R.nrow;
+                span(D.Aci, a * sizeof(int));
+                span(D.Av, a * sizeof(float));
+                span(D.Asv, a * sizeof(float));
+                span(D.dinv, L.dinv.size() * sizeof(float));
+                span(D.Pci, pe * sizeof(int));
+                span(D.Pv, pe * sizeof(float));
+                span(D.Rci, re * sizeof(int));
+                span(D.Rv, re * sizeof(float));
+            }
+            span(P.cinv, H.coarse_inv.size() * sizeof(float));
+            smm::L2Chunk* pfd = nullptr;
+            ok &= upload(h, pfd, pf);
+            P.coarse_pf = pfd;
+            P.coarse_npf = (int)pf.size();
+        }
         ok &= cudaStreamSynchronize(h->stream) == cudaSuccess;
         if (!ok) return bail(SMM_ERR_OOM, "multigrid upload failed");
         h->rold = h->alloc<double>(nphi);
@@ -745,7 +808,7 @@ smm_status setup_cg_moment_system(smm_handle h, const smm::Setup& s) {
 smm::CGArgs cg_args(smm_handle h, double* x) {
     smm::CGArgs a{};
     a.ne = h->ne; a.n = h->n; a.nrow = h->ne * h->n; a.nblk = h->cg_nblk;
-    a.nvblk = h->cg_nvblk; a.pvec = h->part + 3 * (size_t)h->cg_pmax;
+    a.nvblk = h->cg_nvblk; a.pvec = h->part + 4 * (size_t)h->cg_pmax;
     a.A.AdT = h->AdT; a.A.CT = h->CT; a.A.nbr = h->nbr; a.A.nface = h->nbr_face;
     for (int k = 0; k < 5; ++k) a.A.wd[k] = h->wd[k];
     a.A2.AdT = h->AdT2; a.A2.CT = h->CT2; a.A2.nbr = h->nbr; a.A2.nface = h->nbr_face;

@@ -36,80 +36,112 @@ struct FaceScratch {
     AT w[FaceDims<N>::EPB * FaceDims<N>::NG];
 };
 
-// (A x)_i for row i of element e (act: this thread owns a row).  Every thread
-// of the block must call it (two block barriers).  Steps: diagonal block row;
-// the neighbours' face data g = E_f2 x_e2 (trace values and normal
-// derivatives); w = C_{e,f} g per face; lift (E_f^T w)_i.
+// (A x)_i for row i of element e, in three phases separated by block
+// barriers: (1) the neighbours' face data g = E_f2 x_e2 (trace values and
+// normal derivatives) into shared scratch, (2) w = C_{e,f} g per face,
+// (3) the lift (E_f^T w)_i.  The diagonal block row is added before the lift.
+// The phases are separate functions so that a kernel can stage the matrix
+// data (the diagonal block and the face couplings) while phase 1 runs.
+
+// phase 1 for the thread of row i of element e: face data v = i, i + N, ...
 template <int N, typename T, typename AT, typename VT>
-__device__ __forceinline__ AT faceop_row(const FaceOp<T>& op, const VT* __restrict__ x, int e, int i, bool act,
-                                         FaceScratch<N, AT>& sc) {
+__device__ __forceinline__ void face_gather(const FaceOp<T>& op, const VT* __restrict__ x, int e, int i,
+                                            FaceScratch<N, AT>& sc) {
     using D = FaceDims<N>;
     constexpr int P1 = D::P1, G = D::G, NG = D::NG;
     const int le = threadIdx.x / N;
+#pragma unroll
+    for (int v0 = 0; v0 < NG; v0 += N) {
+        const int v = v0 + i;
+        if (v < NG) {
+            const int f = v / G, r = v - f * G;
+            const int e2 = op.nbr[e * 4 + f];
+            AT g = 0;
+            if (e2 >= 0) {
+                const int f2 = op.nface[e * 4 + f];
+                const VT* x2 = x + (size_t)e2 * N;
+                if (r < P1) {
+                    g = (AT)x2[line_node<P1>(f2, r, 0)];
+                } else {
+                    const int a = r - P1;
+#pragma unroll
+                    for (int t = 0; t < P1; ++t) g += (AT)op.wd[t] * (AT)x2[line_node<P1>(f2, a, t)];
+                }
+            }
+            sc.g[le * NG + v] = g;
+        }
+    }
+}
+
+// phase 2: w = C g with Ce the element's four G x G face blocks (column-major)
+template <int N, typename CTy, typename AT>
+__device__ __forceinline__ void face_couple(const CTy* __restrict__ Ce, const int32_t* __restrict__ nbr, int e, int i,
+                                            FaceScratch<N, AT>& sc) {
+    using D = FaceDims<N>;
+    constexpr int G = D::G, NG = D::NG;
+    const int le = threadIdx.x / N;
+#pragma unroll
+    for (int v0 = 0; v0 < NG; v0 += N) {
+        const int v = v0 + i;
+        if (v < NG) {
+            const int f = v / G, r = v - f * G;
+            AT w = 0;
+            if (nbr[e * 4 + f] >= 0) {
+                const CTy* C = Ce + (size_t)f * G * G + r;
+                const AT* g = sc.g + le * NG + f * G;
+#pragma unroll
+                for (int c = 0; c < G; ++c) w += (AT)C[c * G] * g[c];
+            }
+            sc.w[le * NG + v] = w;
+        }
+    }
+}
+
+// phase 3: y + (E_f^T w)_i
+template <int N, typename T, typename AT>
+__device__ __forceinline__ AT face_lift(const FaceOp<T>& op, int i, AT y, const FaceScratch<N, AT>& sc) {
+    using D = FaceDims<N>;
+    constexpr int P1 = D::P1, G = D::G, NG = D::NG;
+    constexpr int p = P1 - 1;
+    const int le = threadIdx.x / N;
+    const int ix = i % P1, iy = i / P1;
+    const AT* w = sc.w + le * NG;
+    // (face, face position, line position) of this node for each face
+    const int fa[4] = {ix, iy, ix, iy};
+    const int ft[4] = {iy, p - ix, p - iy, ix};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        AT c = 0;
+#pragma unroll
+        for (int t = 0; t < P1; ++t)
+            if (t == ft[f]) c = (AT)op.wd[t];
+        y += c * w[f * G + P1 + fa[f]];
+        if (ft[f] == 0) y += w[f * G + fa[f]];
+    }
+    return y;
+}
+
+// (A x)_i (act: this thread owns a row); every thread of the block must call
+// it (two block barriers).  With DIAG false the diagonal block is left out:
+// the row of the off-diagonal part alone.
+template <int N, typename T, typename AT, typename VT, bool DIAG = true>
+__device__ __forceinline__ AT faceop_row(const FaceOp<T>& op, const VT* __restrict__ x, int e, int i, bool act,
+                                         FaceScratch<N, AT>& sc) {
+    constexpr int G = FaceDims<N>::G;
     AT y = 0;
     if (act) {
-        const T* Ad = op.AdT + (size_t)e * N * N + i;
-        const VT* xe = x + (size_t)e * N;
+        if constexpr (DIAG) {
+            const T* Ad = op.AdT + (size_t)e * N * N + i;
+            const VT* xe = x + (size_t)e * N;
 #pragma unroll
-        for (int j = 0; j < N; ++j) y += (AT)Ad[j * N] * (AT)xe[j];
-#pragma unroll
-        for (int v0 = 0; v0 < NG; v0 += N) {
-            const int v = v0 + i;
-            if (v < NG) {
-                const int f = v / G, r = v - f * G;
-                const int e2 = op.nbr[e * 4 + f];
-                AT g = 0;
-                if (e2 >= 0) {
-                    const int f2 = op.nface[e * 4 + f];
-                    const VT* x2 = x + (size_t)e2 * N;
-                    if (r < P1) {
-                        g = (AT)x2[line_node<P1>(f2, r, 0)];
-                    } else {
-                        const int a = r - P1;
-#pragma unroll
-                        for (int t = 0; t < P1; ++t) g += (AT)op.wd[t] * (AT)x2[line_node<P1>(f2, a, t)];
-                    }
-                }
-                sc.g[le * NG + v] = g;
-            }
+            for (int j = 0; j < N; ++j) y += (AT)Ad[j * N] * (AT)xe[j];
         }
+        face_gather<N, T, AT, VT>(op, x, e, i, sc);
     }
     __syncthreads();
-    if (act) {
-#pragma unroll
-        for (int v0 = 0; v0 < NG; v0 += N) {
-            const int v = v0 + i;
-            if (v < NG) {
-                const int f = v / G, r = v - f * G;
-                AT w = 0;
-                if (op.nbr[e * 4 + f] >= 0) {
-                    const T* C = op.CT + ((size_t)(e * 4 + f) * G) * G + r;
-                    const AT* g = sc.g + le * NG + f * G;
-#pragma unroll
-                    for (int c = 0; c < G; ++c) w += (AT)C[c * G] * g[c];
-                }
-                sc.w[le * NG + v] = w;
-            }
-        }
-    }
+    if (act) face_couple<N, T, AT>(op.CT + (size_t)e * 4 * G * G, op.nbr, e, i, sc);
     __syncthreads();
-    if (act) {
-        constexpr int p = P1 - 1;
-        const int ix = i % P1, iy = i / P1;
-        const AT* w = sc.w + le * NG;
-        // (face, face position, line position) of this node for each face
-        const int fa[4] = {ix, iy, ix, iy};
-        const int ft[4] = {iy, p - ix, p - iy, ix};
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            AT c = 0;
-#pragma unroll
-            for (int t = 0; t < P1; ++t)
-                if (t == ft[f]) c = (AT)op.wd[t];
-            y += c * w[f * G + P1 + fa[f]];
-            if (ft[f] == 0) y += w[f * G + fa[f]];
-        }
-    }
+    if (act) y = face_lift<N, T, AT>(op, i, y, sc);
     return y;
 }
 
@@ -119,93 +151,123 @@ struct FaceScratchDF {
     float2 w[FaceDims<N>::EPB * FaceDims<N>::NG];
 };
 
-// faceop_row with the operator and x as FP32 pairs, pair arithmetic
-// throughout (see dfloat.cuh); the row value is returned in FP64
+// the three phases with the operator and x as FP32 pairs, pair arithmetic
+// throughout (see dfloat.cuh)
 template <int N>
-__device__ __forceinline__ double faceop_row_df(const FaceOpDF& op, const float2* __restrict__ x, int e, int i,
-                                                bool act, FaceScratchDF<N>& sc) {
+__device__ __forceinline__ void face_gather_df(const FaceOpDF& op, const float2* __restrict__ x, int e, int i,
+                                               FaceScratchDF<N>& sc) {
     using D = FaceDims<N>;
     constexpr int P1 = D::P1, G = D::G, NG = D::NG;
     const int le = threadIdx.x / N;
-    float ys = 0.0f, yc = 0.0f;
-    if (act) {
-        const float2* Ad = op.AdT + (size_t)e * N * N + i;
-        const float2* xe = x + (size_t)e * N;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const float2 a = Ad[j * N], v = xe[j];
-            df_acc(ys, yc, a.x, a.y, v.x, v.y);
-        }
+    for (int v0 = 0; v0 < NG; v0 += N) {
+        const int v = v0 + i;
+        if (v < NG) {
+            const int f = v / G, r = v - f * G;
+            const int e2 = op.nbr[e * 4 + f];
+            float2 g = make_float2(0.0f, 0.0f);
+            if (e2 >= 0) {
+                const int f2 = op.nface[e * 4 + f];
+                const float2* x2 = x + (size_t)e2 * N;
+                if (r < P1) {
+                    g = x2[line_node<P1>(f2, r, 0)];
+                } else {
+                    const int a = r - P1;
+                    float gs = 0.0f, gc = 0.0f;
 #pragma unroll
-        for (int v0 = 0; v0 < NG; v0 += N) {
-            const int v = v0 + i;
-            if (v < NG) {
-                const int f = v / G, r = v - f * G;
-                const int e2 = op.nbr[e * 4 + f];
-                float2 g = make_float2(0.0f, 0.0f);
-                if (e2 >= 0) {
-                    const int f2 = op.nface[e * 4 + f];
-                    const float2* x2 = x + (size_t)e2 * N;
-                    if (r < P1) {
-                        g = x2[line_node<P1>(f2, r, 0)];
-                    } else {
-                        const int a = r - P1;
-                        float gs = 0.0f, gc = 0.0f;
-#pragma unroll
-                        for (int t = 0; t < P1; ++t) {
-                            const float2 xv = x2[line_node<P1>(f2, a, t)];
-                            df_acc(gs, gc, op.wd[t].x, op.wd[t].y, xv.x, xv.y);
-                        }
-                        g = df_norm(gs, gc);
+                    for (int t = 0; t < P1; ++t) {
+                        const float2 xv = x2[line_node<P1>(f2, a, t)];
+                        df_acc(gs, gc, op.wd[t].x, op.wd[t].y, xv.x, xv.y);
                     }
+                    g = df_norm(gs, gc);
                 }
-                sc.g[le * NG + v] = g;
             }
+            sc.g[le * NG + v] = g;
         }
     }
-    __syncthreads();
-    if (act) {
+}
+
+template <int N>
+__device__ __forceinline__ void face_couple_df(const float2* __restrict__ Ce, const int32_t* __restrict__ nbr, int e,
+                                               int i, FaceScratchDF<N>& sc) {
+    using D = FaceDims<N>;
+    constexpr int G = D::G, NG = D::NG;
+    const int le = threadIdx.x / N;
 #pragma unroll
-        for (int v0 = 0; v0 < NG; v0 += N) {
-            const int v = v0 + i;
-            if (v < NG) {
-                const int f = v / G, r = v - f * G;
-                float ws = 0.0f, wc = 0.0f;
-                if (op.nbr[e * 4 + f] >= 0) {
-                    const float2* C = op.CT + ((size_t)(e * 4 + f) * G) * G + r;
-                    const float2* g = sc.g + le * NG + f * G;
+    for (int v0 = 0; v0 < NG; v0 += N) {
+        const int v = v0 + i;
+        if (v < NG) {
+            const int f = v / G, r = v - f * G;
+            float ws = 0.0f, wc = 0.0f;
+            if (nbr[e * 4 + f] >= 0) {
+                const float2* C = Ce + (size_t)f * G * G + r;
+                const float2* g = sc.g + le * NG + f * G;
 #pragma unroll
-                    for (int c = 0; c < G; ++c) {
-                        const float2 cv = C[c * G], gv = g[c];
-                        df_acc(ws, wc, cv.x, cv.y, gv.x, gv.y);
-                    }
+                for (int c = 0; c < G; ++c) {
+                    const float2 cv = C[c * G], gv = g[c];
+                    df_acc(ws, wc, cv.x, cv.y, gv.x, gv.y);
                 }
-                sc.w[le * NG + v] = df_norm(ws, wc);
             }
+            sc.w[le * NG + v] = df_norm(ws, wc);
         }
     }
-    __syncthreads();
-    if (act) {
-        constexpr int p = P1 - 1;
-        const int ix = i % P1, iy = i / P1;
-        const float2* w = sc.w + le * NG;
-        const int fa[4] = {ix, iy, ix, iy};
-        const int ft[4] = {iy, p - ix, p - iy, ix};
+}
+
+// diagonal block row (Ad: row i of the element's column-major block) into the pair sum (ys, yc)
+template <int N>
+__device__ __forceinline__ void diag_row_df(const float2* __restrict__ Ad, const float2* __restrict__ xe, float& ys,
+                                            float& yc) {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            float2 cf = make_float2(0.0f, 0.0f);
+    for (int j = 0; j < N; ++j) {
+        const float2 a = Ad[j * N], v = xe[j];
+        df_acc(ys, yc, a.x, a.y, v.x, v.y);
+    }
+}
+
+// phase 3 added to the pair sum (ys, yc); the row value in FP64
+template <int N>
+__device__ __forceinline__ double face_lift_df(const FaceOpDF& op, int i, float ys, float yc,
+                                               const FaceScratchDF<N>& sc) {
+    using D = FaceDims<N>;
+    constexpr int P1 = D::P1, G = D::G, NG = D::NG;
+    constexpr int p = P1 - 1;
+    const int le = threadIdx.x / N;
+    const int ix = i % P1, iy = i / P1;
+    const float2* w = sc.w + le * NG;
+    const int fa[4] = {ix, iy, ix, iy};
+    const int ft[4] = {iy, p - ix, p - iy, ix};
 #pragma unroll
-            for (int t = 0; t < P1; ++t)
-                if (t == ft[f]) cf = op.wd[t];
-            const float2 wv = w[f * G + P1 + fa[f]];
-            df_acc(ys, yc, cf.x, cf.y, wv.x, wv.y);
-            if (ft[f] == 0) {
-                const float2 wt = w[f * G + fa[f]];
-                df_add(ys, yc, wt.x, wt.y);
-            }
+    for (int f = 0; f < 4; ++f) {
+        float2 cf = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int t = 0; t < P1; ++t)
+            if (t == ft[f]) cf = op.wd[t];
+        const float2 wv = w[f * G + P1 + fa[f]];
+        df_acc(ys, yc, cf.x, cf.y, wv.x, wv.y);
+        if (ft[f] == 0) {
+            const float2 wt = w[f * G + fa[f]];
+            df_add(ys, yc, wt.x, wt.y);
         }
     }
     return df_to_double(ys, yc);
+}
+
+// faceop_row in pair arithmetic; the row value is returned in FP64
+template <int N>
+__device__ __forceinline__ double faceop_row_df(const FaceOpDF& op, const float2* __restrict__ x, int e, int i,
+                                                bool act, FaceScratchDF<N>& sc) {
+    constexpr int G = FaceDims<N>::G;
+    float ys = 0.0f, yc = 0.0f;
+    if (act) {
+        diag_row_df<N>(op.AdT + (size_t)e * N * N + i, x + (size_t)e * N, ys, yc);
+        face_gather_df<N>(op, x, e, i, sc);
+    }
+    __syncthreads();
+    if (act) face_couple_df<N>(op.CT + (size_t)e * 4 * G * G, op.nbr, e, i, sc);
+    __syncthreads();
+    double y = 0.0;
+    if (act) y = face_lift_df<N>(op, i, ys, yc, sc);
+    return y;
 }
 
 // (A v)_i with dense column-major neighbour blocks (runtime n)
@@ -227,5 +289,78 @@ __device__ __forceinline__ double dense_block_row(const double* __restrict__ AdT
 }
 
 __device__ __forceinline__ bool cg_finished(const int* ctl) { return ctl && *(const volatile int*)ctl; }
+
+// ---- deterministic reductions of the CG kernels ----
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum of v into out (thread 0 writes); deterministic order.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    v = warp_sum(v);
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) s += sh[i];
+    return s;  // valid in thread 0
+}
+
+// same sum over partials written by other blocks of the running kernel (read through L2)
+__device__ __forceinline__ double sum_partials_cg(const double* part, int nblk, double* sh) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += __ldcg(part + i);
+    double s = block_sum(v, sh);
+    if (threadIdx.x == 0) sh[32] = s;
+    __syncthreads();
+    s = sh[32];
+    __syncthreads();
+    return s;
+}
+
+// the three partial arrays part[0..nblk), part[nblk..2 nblk), part[2 nblk..3 nblk)
+// summed in one pass (independent loads in flight)
+__device__ __forceinline__ void sum3_partials_cg(const double* part, int nblk, double* sh, double& s0, double& s1,
+                                                 double& s2) {
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        const double a0 = __ldcg(part + i), a1 = __ldcg(part + nblk + i), a2 = __ldcg(part + 2 * nblk + i);
+        v0 += a0;
+        v1 += a1;
+        v2 += a2;
+    }
+    s0 = block_sum(v0, sh);
+    s1 = block_sum(v1, sh);
+    s2 = block_sum(v2, sh);
+    if (threadIdx.x == 0) {
+        sh[32] = s0;
+        sh[33] = s1;
+        sh[34] = s2;
+    }
+    __syncthreads();
+    s0 = sh[32];
+    s1 = sh[33];
+    s2 = sh[34];
+    __syncthreads();
+}
+
+// True in the last block of the grid to get here (after its partials are
+// written): that block then reduces all partials.  No block waits.
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+    __shared__ bool am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        am_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
 
 }  // namespace smm

@@ -175,16 +175,30 @@ struct CGArgs {
     double* scal;              // [8]: rz, pq, rr, bb, thresh2, -, -, -
     int* ctl;                  // [4]: done, iters, max_iters, nonfinite
 };
-// multigrid preconditioner (device side of an MGHierarchy); levels >= 1 in FP32
+// multigrid preconditioner (device side of an MGHierarchy); levels >= 1 in
+// FP32.  Their sparse matrices are stored as k-major ELL: entry k of row i at
+// [k * rows + i], every row padded to the longest one with value 0 (column of
+// the row's first entry), so that a warp's loads of one k over consecutive
+// rows are coalesced and a row's loads are independent of each other.
 struct MGLevelDev {
     int n = 0;                                   // unknowns on this level
-    const int* Arp = nullptr; const int* Aci = nullptr; const float* Av = nullptr;
+    int aw = 0;                                  // A: n rows of width aw
+    const int* Aci = nullptr; const float* Av = nullptr;
     const float* Asv = nullptr;                  // A diag(omega dinv): the values of A scaled by column
     const float* dinv = nullptr;
     float omega = 0.0f;
-    const int* Prp = nullptr; const int* Pci = nullptr; const float* Pv = nullptr;  // from level l+1
-    const int* Rrp = nullptr; const int* Rci = nullptr; const float* Rv = nullptr;  // to level l+1
+    int pw = 0;                                  // P (from level l+1): n rows of width pw
+    const int* Pci = nullptr; const float* Pv = nullptr;
+    int rw = 0;                                  // R (to level l+1): n_{l+1} rows of width rw
+    const int* Rci = nullptr; const float* Rv = nullptr;
     float* b = nullptr; float* x = nullptr; float* r = nullptr; float* t = nullptr;
+};
+// a 16-byte-aligned span (size a multiple of 16) of read-only device data that a
+// kernel prefetches into L2 ahead of the kernel that reads it
+struct L2Chunk {
+    const void* p;
+    unsigned bytes;
+    unsigned pad;
 };
 struct MGPlan {
     bool enabled = false;
@@ -195,11 +209,15 @@ struct MGPlan {
     float* x0 = nullptr; float* x0b = nullptr;   // [ne*n], level 0 works in FP32
     float* res0 = nullptr;                        // [ne][4] element-corner sums of the level-0 residual
     int nvert = 0;
-    const int* vid = nullptr; const float* w4 = nullptr; const int* vrp = nullptr; const int* vinc = nullptr;
+    const int* vid = nullptr; const float* w4 = nullptr;
+    int vw = 0;                                   // vertex -> incident (element*4 + corner) as k-major ELL
+    const int* vinc = nullptr;                    // [vw][nvert], -1 padding
     int nlev = 0;                                 // levels 1..nlev (nlev = coarsest, dense)
     int coarse_ctas = 8;                          // cluster size of the coarse-level launch
     MGLevelDev lv[12];
     const float* cinv = nullptr;                  // [nc][nc] row-major
+    const L2Chunk* coarse_pf = nullptr;           // the coarse levels' read-only data in 32 KB chunks
+    int coarse_npf = 0;
 };
 // cluster size for the coarse-level launch on the current device (8 or 16)
 int mg_coarse_cluster_size();
@@ -207,8 +225,12 @@ int mg_coarse_cluster_size();
 // sums cres [ne][4], aggregation levels, coarsest solve) as one cluster
 // launch; returns the vertex-level correction (device pointer, nvert floats)
 const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* ctl, cudaStream_t s);
-// z = V-cycle(r); returns the number of kernel launches; ctl (nullable): skip when set
+// z = V-cycle(r); returns the number of kernel launches; the kernels return at once when ctl[0]
+// (CG finished) is set
 int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s);
+// one flexible-CG iteration's V-cycle with the update and the dot products folded into the level-0
+// steps (IP system, element blocks); returns the number of launches
+int mg_cg_iteration(const MGPlan& m, const CGArgs& a, cudaStream_t s);
 
 void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s);
 void launch_cgx_update(const CGArgs& a, cudaStream_t s);

@@ -25,64 +25,185 @@ namespace smm {
 
 namespace {
 
+// ---- level-0 kernels: one block per EPB = 256 / N elements (thread = row)
+
+// asynchronous L2 prefetch of a 16-byte-aligned span (size a multiple of 16);
+// nothing waits for it
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// true when the CG has finished
+__device__ __forceinline__ bool mg_skip(const int* ctl) { return ((const volatile int*)ctl)[0] != 0; }
+
 // xout = xin + omega Pinv (b - A xin) in FP32; xin == nullptr means xin = 0;
-// b is the FP64 right-hand side, xout is FP32 (inner steps) or FP64 (last step)
+// b is the FP64 right-hand side, xout is FP32 (inner steps) or FP64 (last step).
+// Pinv is the inverse of the diagonal block A_d (formed in FP64), so
+// Pinv (b - A xin) = Pinv (b - A_off xin) - xin: the step reads the face
+// couplings and Pinv but not A_d, and computes xin + omega (z - xin) with
+// z = Pinv (b - A_off xin).
 template <typename OT, int N>
 __global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, FaceOp<float> A, const float* __restrict__ PinvT,
                                                         float omega, const double* __restrict__ b,
                                                         const float* __restrict__ xin, OT* __restrict__ xout,
                                                         const int* ctl) {
-    if (cg_finished(ctl)) return;
-    constexpr int n = N;
+    if (mg_skip(ctl)) return;
     __shared__ float res[256];
     __shared__ FaceScratch<N, float> sc;
-    const int epb = blockDim.x / n;
-    const int e = blockIdx.x * epb + threadIdx.x / n, i = threadIdx.x % n;
+    const int le = threadIdx.x / N, i = threadIdx.x % N;
+    const int e = blockIdx.x * FaceDims<N>::EPB + le;
     const bool act = e < ne;
     float r = 0.0f, x = 0.0f;
     if (xin) {
-        const float ax = faceop_row<N, float, float, float>(A, xin, e, i, act, sc);
+        const float ax = faceop_row<N, float, float, float, false>(A, xin, e, i, act, sc);
         if (act) {
-            x = xin[(size_t)e * n + i];
-            r = (float)b[(size_t)e * n + i] - ax;
+            x = xin[(size_t)e * N + i];
+            r = (float)b[(size_t)e * N + i] - ax;
         }
     } else if (act) {
-        r = (float)b[(size_t)e * n + i];
+        r = (float)b[(size_t)e * N + i];
     }
     res[threadIdx.x] = r;
     __syncthreads();
     if (act) {
-        const float* P = PinvT + (size_t)e * n * n + i;
-        const float* re = res + (threadIdx.x / n) * n;
+        const float* P = PinvT + (size_t)e * N * N + i;
+        const float* re = res + le * N;
         float z = 0.0f;
 #pragma unroll
-        for (int j = 0; j < n; ++j) z = fmaf(P[j * n], re[j], z);
-        xout[(size_t)e * n + i] = (OT)(x + omega * z);
+        for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
+        xout[(size_t)e * N + i] = (OT)(x + omega * (z - x));
     }
 }
 
 // Level-0 residual res = b - A x (FP32) restricted to the element corners:
 // cres[e][c] = sum_i w4[i][c] res[e][i] (the vertex level sums these over the
-// elements at each vertex)
+// elements at each vertex).  The coarse cycle runs next and chains dependent
+// loads through its levels' CSR data, which the operator product has pushed
+// out of L2: thread 0 of the first blocks prefetches those chunks (pf) into L2.
 template <int N>
 __global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> A, const double* __restrict__ b,
                                                           const float* __restrict__ x, const float* __restrict__ w4,
-                                                          float* __restrict__ cres, const int* ctl) {
-    if (cg_finished(ctl)) return;
+                                                          float* __restrict__ cres, const L2Chunk* __restrict__ pf,
+                                                          int npf, const int* ctl) {
+    if (mg_skip(ctl)) return;
+    if (threadIdx.x == 0)
+        for (int c = blockIdx.x; c < npf; c += gridDim.x) prefetch_l2(pf[c].p, pf[c].bytes);
     __shared__ FaceScratch<N, float> sc;
     __shared__ float rs[256];
-    const int epb = blockDim.x / N;
-    const int e = blockIdx.x * epb + threadIdx.x / N, i = threadIdx.x % N;
+    const int le = threadIdx.x / N, i = threadIdx.x % N;
+    const int e = blockIdx.x * FaceDims<N>::EPB + le;
     const bool act = e < ne;
     const float ax = faceop_row<N, float, float, float>(A, x, e, i, act, sc);
     rs[threadIdx.x] = act ? (float)b[(size_t)e * N + i] - ax : 0.0f;
     __syncthreads();
     if (act && i < 4) {
-        const float* re = rs + (threadIdx.x / N) * N;
+        const float* re = rs + le * N;
         float s = 0.0f;
 #pragma unroll
         for (int j = 0; j < N; ++j) s = fmaf(w4[j * 4 + i], re[j], s);
         cres[(size_t)e * 4 + i] = s;
+    }
+}
+
+// First pre-smoothing step (from zero) of a flexible-CG iteration with the
+// CG update folded in: x += alpha p, r_old = r, r -= alpha q (alpha = rz / p.q
+// from the operator product's last block), partial r.r -> part[nblk + block];
+// xout = omega Pinv r in FP32.  One block per EPB elements, as the product.
+template <int N>
+__global__ void __launch_bounds__(256) bj_first_update_kernel(CGArgs a, const float* __restrict__ PinvT, float omega,
+                                                              float* __restrict__ xout) {
+    if (mg_skip(a.ctl)) return;
+    __shared__ float res[256];
+    __shared__ double sh[40];
+    const int le = threadIdx.x / N, i = threadIdx.x % N;
+    const int e = blockIdx.x * FaceDims<N>::EPB + le;
+    const bool act = e < a.ne;
+    const double alpha = a.scal[5];
+    double rr = 0.0;
+    float r = 0.0f;
+    if (act) {
+        const size_t o = (size_t)e * N + i;
+        a.x[o] += alpha * a.p[o];
+        const double ro = a.r[o];
+        a.rold[o] = ro;
+        const double rn = ro - alpha * a.q[o];
+        a.r[o] = rn;
+        rr = rn * rn;
+        r = (float)rn;
+    }
+    res[threadIdx.x] = r;
+    __syncthreads();
+    if (act) {
+        const float* P = PinvT + (size_t)e * N * N + i;
+        const float* re = res + le * N;
+        float z = 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
+        xout[(size_t)e * N + i] = omega * z;
+    }
+    const double s = block_sum(rr, sh);
+    if (threadIdx.x == 0) a.part[a.nblk + blockIdx.x] = s;
+}
+
+// Last post-smoothing step of a flexible-CG iteration, z = x + omega (Pinv
+// (r - A_off x) - x) written in FP64, with the CG dot products folded in:
+// partials r.z -> part[2 nblk + block] and (r - r_old).z -> part[3 nblk +
+// block].  The last block reduces them with the first step's r.r partials:
+// beta = (r - r_old).z / rz_old, rz, rr, the iteration count and the
+// convergence test.
+template <int N>
+__global__ void __launch_bounds__(256) bj_last_dots_kernel(CGArgs a, FaceOp<float> A, const float* __restrict__ PinvT,
+                                                           float omega, const float* __restrict__ xin) {
+    if (mg_skip(a.ctl)) return;
+    __shared__ float res[256];
+    __shared__ FaceScratch<N, float> sc;
+    __shared__ double sh[40];
+    const int le = threadIdx.x / N, i = threadIdx.x % N;
+    const int e = blockIdx.x * FaceDims<N>::EPB + le;
+    const bool act = e < a.ne;
+    const float ax = faceop_row<N, float, float, float, false>(A, xin, e, i, act, sc);
+    float x = 0.0f, r = 0.0f;
+    double rd = 0.0;
+    if (act) {
+        x = xin[(size_t)e * N + i];
+        rd = a.r[(size_t)e * N + i];
+        r = (float)rd - ax;
+    }
+    res[threadIdx.x] = r;
+    __syncthreads();
+    double rz = 0.0, dz = 0.0;
+    if (act) {
+        const float* P = PinvT + (size_t)e * N * N + i;
+        const float* re = res + le * N;
+        float z = 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
+        const size_t o = (size_t)e * N + i;
+        const double zd = (double)(x + omega * (z - x));
+        a.z[o] = zd;
+        rz = rd * zd;
+        dz = (rd - a.rold[o]) * zd;
+    }
+    const double s1 = block_sum(rz, sh);
+    const double s2 = block_sum(dz, sh);
+    if (threadIdx.x == 0) {
+        a.part[2 * a.nblk + blockIdx.x] = s1;
+        a.part[3 * a.nblk + blockIdx.x] = s2;
+    }
+    if (last_block((unsigned*)(a.ctl + 6))) {
+        double rr, rz_new, dz_all;
+        sum3_partials_cg(a.part + a.nblk, a.nblk, sh, rr, rz_new, dz_all);
+        if (threadIdx.x == 0) {
+            a.scal[6] = dz_all / a.scal[0];
+            a.scal[0] = rz_new;
+            a.scal[2] = rr;
+            const int it = a.ctl[1] + 1;
+            a.ctl[1] = it;
+            const bool bad = !(isfinite(rz_new) && isfinite(rr) && isfinite(dz_all));
+            if (bad) a.ctl[3] = 1;
+            if (rr <= a.scal[4] || it >= a.ctl[2] || bad) a.ctl[0] = 1;
+            a.ctl[6] = 0;
+        }
     }
 }
 
@@ -110,47 +231,46 @@ constexpr int kCoarseThreads = 1024;
 struct CoarseArgs {
     int nvert, nlev;
     const float* cres;                          // [ne][4] corner sums of the level-0 residual
-    const int* vrp; const int* vinc;
+    int vw; const int* vinc;                    // vertex incidences, k-major ELL with -1 padding
     MGLevelDev lv[12];
     const float* cinv;
 };
 
-// rows i and j (j < 0: none) of a CSR matrix times x, with the loads of the two
-// rows interleaved so a thread holding two rows waits about as long as one
-__device__ __forceinline__ void csr_row2_f(const int* __restrict__ rp, const int* __restrict__ ci,
-                                           const float* __restrict__ v, const float* x, int i, int j, float& si,
-                                           float& sj) {
-    int ki = rp[i], kj = j >= 0 ? rp[j] : 0;
-    const int ei = rp[i + 1], ej = j >= 0 ? rp[j + 1] : 0;
-    float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-    while (ki < ei || kj < ej) {
-        int c[8], d[8];
-        float w[8], u[8], xv[8], yv[8];
+// row i of a k-major ELL matrix (width w <= W, R rows) times x: all column
+// and value loads are issued first, then all gathers of x, so the row costs
+// two dependent round trips; a warp's loads for one k cover consecutive rows
+template <int W>
+__device__ __forceinline__ float ell_row_w(int w, int R, const int* __restrict__ ci, const float* __restrict__ v,
+                                           const float* x, int i) {
+    int c[W];
+    float wv[W];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const bool oi = ki + q < ei, oj = kj + q < ej;
-            c[q] = oi ? ci[ki + q] : 0;
-            w[q] = oi ? v[ki + q] : 0.0f;
-            d[q] = oj ? ci[kj + q] : 0;
-            u[q] = oj ? v[kj + q] : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            xv[q] = ki + q < ei ? __ldcg(x + c[q]) : 0.0f;
-            yv[q] = kj + q < ej ? __ldcg(x + d[q]) : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            a0 = fmaf(w[q], xv[q], a0);
-            a1 = fmaf(w[q + 1], xv[q + 1], a1);
-            b0 = fmaf(u[q], yv[q], b0);
-            b1 = fmaf(u[q + 1], yv[q + 1], b1);
-        }
-        ki += 8;
-        kj += 8;
+    for (int k = 0; k < W; ++k) {
+        const bool on = k < w;
+        c[k] = on ? ci[(size_t)k * R + i] : 0;
+        wv[k] = on ? v[(size_t)k * R + i] : 0.0f;
     }
-    si = a0 + a1;
-    sj = b0 + b1;
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < W; k += 2) {
+        a0 = fmaf(wv[k], k < w ? __ldcg(x + c[k]) : 0.0f, a0);
+        a1 = fmaf(wv[k + 1], k + 1 < w ? __ldcg(x + c[k + 1]) : 0.0f, a1);
+    }
+    return a0 + a1;
+}
+
+// row i of a k-major ELL matrix of any width: one pass for w <= 32, passes of
+// 32 entries beyond.  Kept out of line so that its registers do not add to the
+// live set of the calling stage (a 1024-thread CTA has 64 per thread).
+__device__ __noinline__ float ell_row(int w, int R, const int* __restrict__ ci, const float* __restrict__ v,
+                                      const float* x, int i) {
+    if (w <= 8) return ell_row_w<8>(w, R, ci, v, x, i);
+    if (w <= 16) return ell_row_w<16>(w, R, ci, v, x, i);
+    if (w <= 24) return ell_row_w<24>(w, R, ci, v, x, i);
+    float s = 0.0f;
+    for (int k0 = 0; k0 < w; k0 += 32)
+        s += ell_row_w<32>(min(32, w - k0), R, ci + (size_t)k0 * R, v + (size_t)k0 * R, x, i);
+    return s;
 }
 
 // launched as one cluster of gridDim.x CTAs (8, or 16 where the GPU allows it)
@@ -164,7 +284,13 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
         float* b1 = a.lv[1].b;
         for (int v = tid; v < a.nvert; v += T) {
             float s = 0.0f;
-            for (int k = a.vrp[v]; k < a.vrp[v + 1]; ++k) s += a.cres[a.vinc[k]];
+            for (int k0 = 0; k0 < a.vw; k0 += 8) {
+                int c[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) c[k] = k0 + k < a.vw ? a.vinc[(size_t)(k0 + k) * a.nvert + v] : -1;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) s += c[k] >= 0 ? __ldcg(a.cres + c[k]) : 0.0f;
+            }
             b1[v] = s;
         }
     }
@@ -174,28 +300,15 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
     // out of one pass over b.
     for (int l = 1; l < a.nlev; ++l) {
         const MGLevelDev& L = a.lv[l];
-        for (int i = tid; i < L.n; i += 2 * T) {
-            const int j = i + T < L.n ? i + T : -1;
-            float si, sj;
-            csr_row2_f(L.Arp, L.Aci, L.Asv, L.b, i, j, si, sj);
+        for (int i = tid; i < L.n; i += T) {
             const float bi = __ldcg(L.b + i);
+            const float si = ell_row(L.aw, L.n, L.Aci, L.Asv, L.b, i);
             L.r[i] = bi - si;
             L.x[i] = L.omega * L.dinv[i] * bi;
-            if (j >= 0) {
-                const float bj = __ldcg(L.b + j);
-                L.r[j] = bj - sj;
-                L.x[j] = L.omega * L.dinv[j] * bj;
-            }
         }
         cl.sync();
         const MGLevelDev& Lc = a.lv[l + 1];
-        for (int i = tid; i < Lc.n; i += 2 * T) {
-            const int j = i + T < Lc.n ? i + T : -1;
-            float si, sj;
-            csr_row2_f(L.Rrp, L.Rci, L.Rv, L.r, i, j, si, sj);
-            Lc.b[i] = si;
-            if (j >= 0) Lc.b[j] = sj;
-        }
+        for (int i = tid; i < Lc.n; i += T) Lc.b[i] = ell_row(L.rw, Lc.n, L.Rci, L.Rv, L.r, i);
         cl.sync();
     }
     // coarsest: x = Cinv b, one warp per row
@@ -205,7 +318,17 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
         for (int row = w; row < C.n; row += nw) {
             const float* cr = a.cinv + (size_t)row * C.n;
             float s = 0.0f;
-            for (int j = lane; j < C.n; j += 32) s = fmaf(cr[j], __ldcg(C.b + j), s);
+            for (int j0 = 0; j0 < C.n; j0 += 256) {
+                float cv[8], bv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = j0 + q * 32 + lane;
+                    cv[q] = j < C.n ? cr[j] : 0.0f;
+                    bv[q] = j < C.n ? __ldcg(C.b + j) : 0.0f;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s = fmaf(cv[q], bv[q], s);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) C.x[row] = s;
@@ -216,20 +339,15 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
     const float* coarse_out = a.lv[a.nlev].x;
     for (int l = a.nlev - 1; l >= 1; --l) {
         const MGLevelDev& L = a.lv[l];
-        for (int i = tid; i < L.n; i += 2 * T) {
-            const int j = i + T < L.n ? i + T : -1;
-            float si, sj;
-            csr_row2_f(L.Prp, L.Pci, L.Pv, coarse_out, i, j, si, sj);
-            L.x[i] = __ldcg(L.x + i) + si;
-            if (j >= 0) L.x[j] = __ldcg(L.x + j) + sj;
+        for (int i = tid; i < L.n; i += T) {
+            const float xi = __ldcg(L.x + i);
+            L.x[i] = xi + ell_row(L.pw, L.n, L.Pci, L.Pv, coarse_out, i);
         }
         cl.sync();
-        for (int i = tid; i < L.n; i += 2 * T) {
-            const int j = i + T < L.n ? i + T : -1;
-            float si, sj;
-            csr_row2_f(L.Arp, L.Aci, L.Av, L.x, i, j, si, sj);
-            L.t[i] = __ldcg(L.x + i) + L.omega * L.dinv[i] * (__ldcg(L.b + i) - si);
-            if (j >= 0) L.t[j] = __ldcg(L.x + j) + L.omega * L.dinv[j] * (__ldcg(L.b + j) - sj);
+        for (int i = tid; i < L.n; i += T) {
+            const float xi = __ldcg(L.x + i), bi = __ldcg(L.b + i), di = L.dinv[i];
+            const float si = ell_row(L.aw, L.n, L.Aci, L.Av, L.x, i);
+            L.t[i] = xi + L.omega * di * (bi - si);
         }
         cl.sync();
         coarse_out = L.t;
@@ -270,7 +388,7 @@ int mg_coarse_cluster_size() {
 
 const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* ctl, cudaStream_t s) {
     CoarseArgs ca{};
-    ca.nvert = m.nvert; ca.nlev = m.nlev; ca.cres = cres; ca.vrp = m.vrp; ca.vinc = m.vinc;
+    ca.nvert = m.nvert; ca.nlev = m.nlev; ca.cres = cres; ca.vw = m.vw; ca.vinc = m.vinc;
     for (int l = 0; l <= m.nlev; ++l) ca.lv[l] = m.lv[l];
     ca.cinv = m.cinv;
     cudaLaunchConfig_t cfg{};
@@ -303,20 +421,19 @@ template <int N>
 int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s) {
     int launches = 0;
     const int tpb = cg_threads_per_block(N);
-    const int nblk0 = (m.ne + tpb / N - 1) / (tpb / N);
-    const size_t shm = 0;
+    const int nblk0 = (m.ne + FaceDims<N>::EPB - 1) / FaceDims<N>::EPB;
     const float w0 = (float)m.omega0;
     // level 0 pre-smoothing from zero (FP32)
     float* xa = m.x0;
     float* xb = m.x0b;
-    bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.A, m.PinvT, w0, r, nullptr, xa, ctl);
+    bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, r, nullptr, xa, ctl);
     ++launches;
     for (int k = 1; k < m.nu0; ++k) {
-        bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, xb, ctl);
+        bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, xb, ctl);
         std::swap(xa, xb);
         ++launches;
     }
-    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, r, xa, m.w4, m.res0, ctl);
+    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, r, xa, m.w4, m.res0, m.coarse_pf, m.coarse_npf, ctl);
     // vertex and aggregation levels and the coarsest solve (one cluster launch)
     const float* coarse_out = launch_coarse_cycle(m, m.res0, ctl, s);
     const int rows0 = m.ne * N;
@@ -324,9 +441,9 @@ int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cuda
     launches += 3;
     for (int k = 0; k < m.nu0; ++k) {
         if (k == m.nu0 - 1) {
-            bj_smooth_kernel<double, N><<<nblk0, tpb, shm, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, z, ctl);
+            bj_smooth_kernel<double, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, z, ctl);
         } else {
-            bj_smooth_kernel<float, N><<<nblk0, tpb, shm, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, xb, ctl);
+            bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, xb, ctl);
             std::swap(xa, xb);
         }
         ++launches;
@@ -338,5 +455,51 @@ template int mg_apply_n<4>(const MGPlan&, const double*, double*, const int*, cu
 template int mg_apply_n<9>(const MGPlan&, const double*, double*, const int*, cudaStream_t);
 template int mg_apply_n<16>(const MGPlan&, const double*, double*, const int*, cudaStream_t);
 template int mg_apply_n<25>(const MGPlan&, const double*, double*, const int*, cudaStream_t);
+
+// The V-cycle part of one flexible-CG iteration with the CG vector work
+// folded into its first and last level-0 steps (bj_first_update_kernel,
+// bj_last_dots_kernel); z = M r as mg_apply computes it, for the residual r
+// after the update.
+template <int N>
+int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
+    const int tpb = cg_threads_per_block(N);
+    const int nblk0 = a.nblk;
+    const float w0 = (float)m.omega0;
+    float* xa = m.x0;
+    float* xb = m.x0b;
+    bj_first_update_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.PinvT, w0, xa);
+    int launches = 1;
+    for (int k = 1; k < m.nu0; ++k) {
+        bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, a.r, xa, xb, a.ctl);
+        std::swap(xa, xb);
+        ++launches;
+    }
+    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, a.r, xa, m.w4, m.res0, m.coarse_pf, m.coarse_npf,
+                                                  a.ctl);
+    const float* coarse_out = launch_coarse_cycle(m, m.res0, a.ctl, s);
+    const int rows0 = m.ne * N;
+    prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, xa, a.ctl);
+    launches += 3;
+    for (int k = 0; k < m.nu0; ++k) {
+        if (k == m.nu0 - 1) {
+            bj_last_dots_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.A, m.PinvT, w0, xa);
+        } else {
+            bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, a.r, xa, xb, a.ctl);
+            std::swap(xa, xb);
+        }
+        ++launches;
+    }
+    return launches;
+}
+
+int mg_cg_iteration(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
+    switch (m.n) {
+        case 4: return mg_cg_iteration_n<4>(m, a, s);
+        case 9: return mg_cg_iteration_n<9>(m, a, s);
+        case 16: return mg_cg_iteration_n<16>(m, a, s);
+        case 25: return mg_cg_iteration_n<25>(m, a, s);
+        default: return 0;
+    }
+}
 
 }  // namespace smm

@@ -10,31 +10,12 @@ namespace smm {
 
 namespace {
 
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
-// Block sum of v into out (thread 0 writes); deterministic order.
-__device__ double block_sum(double v, double* sh) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    v = warp_sum(v);
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) s += sh[i];
-    return s;  // valid in thread 0
-}
 
 }  // namespace
 
@@ -268,56 +249,8 @@ __device__ double sum_partials(const double* part, int nblk, double* sh) {
     return s;
 }
 
-// same sum over partials written by other blocks of the running kernel (read through L2)
-__device__ double sum_partials_cg(const double* part, int nblk, double* sh) {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += __ldcg(part + i);
-    double s = block_sum(v, sh);
-    if (threadIdx.x == 0) sh[32] = s;
-    __syncthreads();
-    s = sh[32];
-    __syncthreads();
-    return s;
-}
 
-// the three partial arrays part[0..nblk), part[nblk..2 nblk), part[2 nblk..3 nblk)
-// summed in one pass (independent loads in flight)
-__device__ void sum3_partials_cg(const double* part, int nblk, double* sh, double& s0, double& s1, double& s2) {
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-        const double a0 = __ldcg(part + i), a1 = __ldcg(part + nblk + i), a2 = __ldcg(part + 2 * nblk + i);
-        v0 += a0;
-        v1 += a1;
-        v2 += a2;
-    }
-    s0 = block_sum(v0, sh);
-    s1 = block_sum(v1, sh);
-    s2 = block_sum(v2, sh);
-    if (threadIdx.x == 0) {
-        sh[32] = s0;
-        sh[33] = s1;
-        sh[34] = s2;
-    }
-    __syncthreads();
-    s0 = sh[32];
-    s1 = sh[33];
-    s2 = sh[34];
-    __syncthreads();
-}
 
-// True in the last block of the grid to get here (after its partials are
-// written): that block then reduces all partials.  No block waits.
-__device__ bool last_block(unsigned* ticket) {
-    __shared__ bool am_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        am_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (am_last) __threadfence();
-    return am_last;
-}
 
 // r = b - A x ; z = P r ; p = z ; partials: rz, rr, bb
 template <int N>
@@ -549,7 +482,8 @@ __global__ void cgx_init_p_kernel(CGArgs a) {
     if (threadIdx.x == 0) a.part[blockIdx.x] = s;
 }
 
-// q = A p (FP64, compile-time block size) ; partial p.q -> part[0]
+// q = A p (FP32-pair arithmetic, FP64 result) ; partial p.q -> part[block];
+// the last block reduces the partials: p.q -> scal[1], alpha = rz / p.q -> scal[5]
 template <int N>
 __global__ void __launch_bounds__(256) cgx_spmv_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
@@ -565,6 +499,14 @@ __global__ void __launch_bounds__(256) cgx_spmv_kernel(CGArgs a) {
     }
     double s = block_sum(pq, sh);
     if (threadIdx.x == 0) a.part[blockIdx.x] = s;
+    if (last_block((unsigned*)(a.ctl + 7))) {
+        const double pq_all = sum_partials_cg(a.part, a.nblk, sh);
+        if (threadIdx.x == 0) {
+            a.scal[1] = pq_all;
+            a.scal[5] = a.scal[0] / pq_all;
+            a.ctl[7] = 0;
+        }
+    }
 }
 
 // x += alpha p ; r_old = r ; r -= alpha q ; partial rr -> part[2 nblk]
@@ -703,7 +645,7 @@ void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s) {
 int cgx_start(const CGArgs& a, double tol, int max_iters, const MGPlan& mg, cudaStream_t s) {
     const int tpb = cg_threads_per_block(a.n);
     SMM_DISPATCH_N(a.n, cgx_init_r_kernel, a.nblk, tpb, 0, s)
-    const int l = mg_apply(mg, a.r, a.z, nullptr, s);
+    const int l = mg_apply(mg, a.r, a.z, a.ctl, s);
     cgx_init_p_kernel<<<a.nblk, tpb, 0, s>>>(a);
     cg_init_scalars_kernel<<<1, 256, 0, s>>>(a, tol * tol, max_iters);
     return 3 + l;
@@ -713,12 +655,12 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
     const int tpb = cg_threads_per_block(a.n);
     int launches = 0;
     for (int k = 0; k < count; ++k) {
+        // q = A p and alpha; V-cycle with the update (x, r) and the dots (beta,
+        // convergence) folded into its first and last level-0 steps; p = z + beta p
         SMM_DISPATCH_N(a.n, cgx_spmv_kernel, a.nblk, tpb, 0, s)
-        cgx_update_kernel<<<a.nvblk, 256, 0, s>>>(a);
-        launches += 2 + mg_apply(mg, a.r, a.z, a.ctl, s);
-        cgx_rz_kernel<<<a.nvblk, 256, 0, s>>>(a);
+        launches += 1 + mg_cg_iteration(mg, a, s);
         cgx_direction_kernel<<<a.nvblk, 256, 0, s>>>(a);
-        launches += 2;
+        launches += 1;
     }
     return launches;
 }

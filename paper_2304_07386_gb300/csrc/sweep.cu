@@ -69,8 +69,10 @@ template <typename T> __device__ __forceinline__ T ldg_cg(const T* p) { return _
 }  // namespace
 
 // One (element, ordinate) task of one problem, executed by a whole warp.
-// Returns false if a dependency wait gave up.
-template <typename T, int P, int MODE, bool INV>
+// Returns false if a dependency wait gave up.  EXT compiles in the optional
+// parts (negative flux fixup, lagged inflow of a block Jacobi sweep); without
+// it the kernel carries neither branch.
+template <typename T, int P, int MODE, bool INV, bool EXT>
 __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task) {
     constexpr int P1 = P + 1, N = P1 * P1;
     constexpr unsigned FULL = 0xffffffffu;
@@ -204,7 +206,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                         const int f2 = a.nbr_face[e * 4 + f];
                         const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
                         const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
-                        u = __ldcg((df == -2 ? a.psi2_lag : a.psi2) + ((size_t)nb * nd + d) * N + node);
+                        u = __ldcg((EXT && df == -2 ? a.psi2_lag : a.psi2) + ((size_t)nb * nd + d) * N + node);
                     } else if (MODE == SWEEP_SOURCE && a.inflow2) {
                         const int bi = a.bface_id[e * 4 + f];
                         u = a.inflow2[((size_t)bi * nd + d) * P1 + lc];
@@ -238,7 +240,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                         const int f2 = a.nbr_face[e * 4 + f];
                         const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
                         const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
-                        upv = ldg_cg((df == -2 ? a.psi_lag : a.psi) + ((size_t)nb * nd + d) * N + node);
+                        upv = ldg_cg((EXT && df == -2 ? a.psi_lag : a.psi) + ((size_t)nb * nd + d) * N + node);
                     } else if (MODE == SWEEP_SOURCE && a.inflow) {
                         const int bi = a.bface_id[e * 4 + f];
                         upv = (T)a.inflow[((size_t)bi * nd + d) * P1 + lc];
@@ -295,7 +297,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         //      c . x, c = 1^T A (column sums of the local operator), keeps its
         //      value; warp-uniform branch, taken only when a value is negative ----
         bool fixed = false;
-        if (MODE == SWEEP_SOURCE && a.fixup && __any_sync(FULL, lane < N && x < T(0))) {
+        if (EXT && MODE == SWEEP_SOURCE && a.fixup && __any_sync(FULL, lane < N && x < T(0))) {
             double c = 0.0;
             if (lane < N) {
                 const size_t eo = (size_t)e * N + lane;
@@ -341,12 +343,12 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
 // t mod W, so each warp meets its tasks in level order; with every warp
 // co-resident (cooperative launch) the task a warp waits for is owned by a
 // running warp that reaches it after finishing only earlier-level tasks.
-template <typename T, int P, int MODE, bool INV>
+template <typename T, int P, int MODE, bool INV, bool EXT>
 __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
     const int W = (gridDim.x * blockDim.x) >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     for (int t = gw; t < a.ntask; t += W)
-        if (!sweep_task<T, P, MODE, INV>(a, a.tasks[t])) break;
+        if (!sweep_task<T, P, MODE, INV, EXT>(a, a.tasks[t])) break;
 }
 
 // Many problems in one launch: the merged list holds (problem, task) pairs
@@ -358,15 +360,16 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(const SweepArgs<T>* __
                                                           const int2* __restrict__ tasks, int ntask) {
     const int W = (gridDim.x * blockDim.x) >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    constexpr bool EXT = sizeof(T) == 8 && MODE == SWEEP_SOURCE;  // problems may use fixup or tiles
     for (int t = gw; t < ntask; t += W) {
         const int2 it = tasks[t];
         const SweepArgs<T>& a = args[it.x];
         bool ok = true;
         switch (a.p) {
-            case 1: ok = sweep_task<T, 1, MODE, INV>(a, it.y); break;
-            case 2: ok = sweep_task<T, 2, MODE, INV>(a, it.y); break;
-            case 3: ok = sweep_task<T, 3, MODE, INV>(a, it.y); break;
-            default: ok = sweep_task<T, 4, MODE, INV>(a, it.y); break;
+            case 1: ok = sweep_task<T, 1, MODE, INV, EXT>(a, it.y); break;
+            case 2: ok = sweep_task<T, 2, MODE, INV, EXT>(a, it.y); break;
+            case 3: ok = sweep_task<T, 3, MODE, INV, EXT>(a, it.y); break;
+            default: ok = sweep_task<T, 4, MODE, INV, EXT>(a, it.y); break;
         }
         if (!ok) break;
     }
@@ -544,17 +547,25 @@ __global__ void source_kernel(int ne, int n, const double* __restrict__ M, const
     msrc[t] = df_make(s);
 }
 
-template <typename T, int P, int MODE, bool INV>
+template <typename T, int P, int MODE, bool INV, bool EXT = false>
 static void launch_one(const SweepArgs<T>& a, int grid, cudaStream_t s) {
     SweepArgs<T> arg = a;
     void* params[] = {&arg};
-    cudaLaunchCooperativeKernel((const void*)sweep_kernel<T, P, MODE, INV>, dim3(grid), dim3(256), params, 0, s);
+    cudaLaunchCooperativeKernel((const void*)sweep_kernel<T, P, MODE, INV, EXT>, dim3(grid), dim3(256), params, 0,
+                                s);
 }
 
 template <typename T, int P>
 static void launch_p(int mode, const SweepArgs<T>& a, int grid, cudaStream_t s) {
     const bool inv = a.ainv != nullptr || a.ainv_df != nullptr;
     if (mode == SWEEP_SOURCE) {
+        if constexpr (sizeof(T) == 8) {
+            if (a.fixup || a.psi_lag || a.psi2_lag) {
+                if (inv) launch_one<T, P, SWEEP_SOURCE, true, true>(a, grid, s);
+                else launch_one<T, P, SWEEP_SOURCE, false, true>(a, grid, s);
+                return;
+            }
+        }
         if (inv) launch_one<T, P, SWEEP_SOURCE, true>(a, grid, s);
         else launch_one<T, P, SWEEP_SOURCE, false>(a, grid, s);
     } else {
@@ -668,17 +679,24 @@ void launch_source(int ne, int n, const double* M, const double* sigma_s, const 
 }
 
 int sweep_blocks_per_sm(int p, int mode, bool fp32, bool cached) {
-    int nb = 0;
+    // FP64 source mode launches either form (with or without the optional
+    // parts), so the grid is sized for the one with the lower occupancy
+    int nb = 0, nb_ext = 1 << 30;
 #define SMM_OCC(T, PP)                                                                                           \
     do {                                                                                                         \
-        if (mode == SWEEP_SOURCE)                                                                                \
+        if (mode == SWEEP_SOURCE) {                                                                              \
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                                       \
-                &nb, cached ? (const void*)sweep_kernel<T, PP, SWEEP_SOURCE, true>                               \
-                            : (const void*)sweep_kernel<T, PP, SWEEP_SOURCE, false>, 256, 0);                    \
-        else                                                                                                     \
+                &nb, cached ? (const void*)sweep_kernel<T, PP, SWEEP_SOURCE, true, false>                        \
+                            : (const void*)sweep_kernel<T, PP, SWEEP_SOURCE, false, false>, 256, 0);             \
+            if (sizeof(T) == 8)                                                                                  \
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                                   \
+                    &nb_ext, cached ? (const void*)sweep_kernel<double, PP, SWEEP_SOURCE, true, true>            \
+                                    : (const void*)sweep_kernel<double, PP, SWEEP_SOURCE, false, true>, 256, 0); \
+        } else {                                                                                                 \
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                                       \
-                &nb, cached ? (const void*)sweep_kernel<T, PP, SWEEP_RESIDUAL, true>                             \
-                            : (const void*)sweep_kernel<T, PP, SWEEP_RESIDUAL, false>, 256, 0);                  \
+                &nb, cached ? (const void*)sweep_kernel<T, PP, SWEEP_RESIDUAL, true, false>                      \
+                            : (const void*)sweep_kernel<T, PP, SWEEP_RESIDUAL, false, false>, 256, 0);           \
+        }                                                                                                        \
     } while (0)
     switch (p) {
         case 1: if (fp32) SMM_OCC(float, 1); else SMM_OCC(double, 1); break;
@@ -688,6 +706,7 @@ int sweep_blocks_per_sm(int p, int mode, bool fp32, bool cached) {
         default: break;
     }
 #undef SMM_OCC
+    nb = std::min(nb, nb_ext);
     return nb > 0 ? nb : 1;
 }
 
