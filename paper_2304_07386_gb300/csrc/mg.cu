@@ -226,20 +226,26 @@ __global__ void prolong_q1_kernel(int ne, int n, const int* __restrict__ vid, co
 // cluster's hardware barrier (no flag waits).  Vectors written inside the
 // kernel are read through L2 (ld.global.cg).  The result is lv[1].t (or the
 // coarsest x when the vertex level is the coarsest).
-constexpr int kCoarseThreads = 1024;
+constexpr int kCoarseThreads = 512;   // 128 registers per thread: a row's loads stay in flight
 
 struct CoarseArgs {
     int nvert, nlev;
+    int cap;                                    // floats of dynamic shared memory (staged vectors)
     const float* cres;                          // [ne][4] corner sums of the level-0 residual
     int vw; const int* vinc;                    // vertex incidences, k-major ELL with -1 padding
     MGLevelDev lv[12];
     const float* cinv;
 };
 
-// row i of a k-major ELL matrix (width w <= W, R rows) times x: all column
-// and value loads are issued first, then all gathers of x, so the row costs
-// two dependent round trips; a warp's loads for one k cover consecutive rows
-template <int W>
+// vectors of up to this many floats are staged in each CTA's shared memory
+// for a stage's gathers (192 KB of the 227 KB a CTA may hold)
+constexpr int kCoarseSmemFloats = 49152;
+
+// row i of a k-major ELL matrix (width w <= W, R rows) times x: the column and
+// value loads are issued first (coalesced: a warp's loads for one k cover
+// consecutive rows), then the gathers of x, from shared memory (SH) or
+// through L2
+template <int W, bool SH>
 __device__ __forceinline__ float ell_row_w(int w, int R, const int* __restrict__ ci, const float* __restrict__ v,
                                            const float* x, int i) {
     int c[W];
@@ -253,32 +259,76 @@ __device__ __forceinline__ float ell_row_w(int w, int R, const int* __restrict__
     float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < W; k += 2) {
-        a0 = fmaf(wv[k], k < w ? __ldcg(x + c[k]) : 0.0f, a0);
-        a1 = fmaf(wv[k + 1], k + 1 < w ? __ldcg(x + c[k + 1]) : 0.0f, a1);
+        const float x0 = k < w ? (SH ? x[c[k]] : __ldcg(x + c[k])) : 0.0f;
+        const float x1 = k + 1 < w ? (SH ? x[c[k + 1]] : __ldcg(x + c[k + 1])) : 0.0f;
+        a0 = fmaf(wv[k], x0, a0);
+        a1 = fmaf(wv[k + 1], x1, a1);
     }
     return a0 + a1;
 }
 
-// row i of a k-major ELL matrix of any width: one pass for w <= 32, passes of
-// 32 entries beyond.  Kept out of line so that its registers do not add to the
-// live set of the calling stage (a 1024-thread CTA has 64 per thread).
-__device__ __noinline__ float ell_row(int w, int R, const int* __restrict__ ci, const float* __restrict__ v,
+// row i of a k-major ELL matrix of any width: one pass for w <= 24, passes of
+// 24 entries beyond
+template <bool SH>
+__device__ __forceinline__ float ell_row(int w, int R, const int* __restrict__ ci, const float* __restrict__ v,
                                       const float* x, int i) {
-    if (w <= 8) return ell_row_w<8>(w, R, ci, v, x, i);
-    if (w <= 16) return ell_row_w<16>(w, R, ci, v, x, i);
-    if (w <= 24) return ell_row_w<24>(w, R, ci, v, x, i);
+    if (w <= 8) return ell_row_w<8, SH>(w, R, ci, v, x, i);
+    if (w <= 16) return ell_row_w<16, SH>(w, R, ci, v, x, i);
     float s = 0.0f;
-    for (int k0 = 0; k0 < w; k0 += 32)
-        s += ell_row_w<32>(min(32, w - k0), R, ci + (size_t)k0 * R, v + (size_t)k0 * R, x, i);
+    for (int k0 = 0; k0 < w; k0 += 24)
+        s += ell_row_w<24, SH>(min(24, w - k0), R, ci + (size_t)k0 * R, v + (size_t)k0 * R, x, i);
     return s;
+}
+
+// Copy x[0..n) into this CTA's shared memory xs when it fits (every thread of
+// the CTA takes part); true if staged.  x (16-byte aligned, a device
+// allocation) was written by other CTAs before the last cluster barrier, so it
+// is read through L2, as 16-byte loads with four in flight per thread.
+__device__ __forceinline__ bool stage_x(const float* x, int n, float* xs, int cap) {
+    if (n > cap) return false;
+    const int n4 = n >> 2;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float4* xs4 = reinterpret_cast<float4*>(xs);
+    for (int k0 = threadIdx.x; k0 < n4; k0 += 4 * blockDim.x) {
+        float4 t[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q * blockDim.x;
+            if (k < n4) t[q] = __ldcg(x4 + k);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q * blockDim.x;
+            if (k < n4) xs4[k] = t[q];
+        }
+    }
+    for (int k = 4 * n4 + threadIdx.x; k < n; k += blockDim.x) xs[k] = __ldcg(x + k);
+    __syncthreads();
+    return true;
+}
+
+// row with x in global memory (vectors larger than the shared-memory budget);
+// out of line, so that it does not add to the registers of the staged path
+__device__ __noinline__ float ell_row_global(int w, int R, const int* ci, const float* v, const float* x, int i) {
+    return ell_row<false>(w, R, ci, v, x, i);
+}
+
+// (M x)_i with x staged in xs (sh) or read from global memory
+__device__ __forceinline__ float ell_apply(bool sh, int w, int R, const int* ci, const float* v, const float* x,
+                                           const float* xs, int i) {
+    return sh ? ell_row<true>(w, R, ci, v, xs, i) : ell_row_global(w, R, ci, v, x, i);
 }
 
 // launched as one cluster of gridDim.x CTAs (8, or 16 where the GPU allows it)
 __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs a, const int* ctl) {
     if (cg_finished(ctl)) return;  // uniform over the cluster: no barrier is left waiting
+    extern __shared__ __align__(16) float xs[];   // a.cap floats
     cg::cluster_group cl = cg::this_cluster();
     const int T = gridDim.x * kCoarseThreads;
-    const int tid = blockIdx.x * kCoarseThreads + threadIdx.x;
+    // warps numbered across the CTAs first (warp slot w of CTA c is warp w * gridDim.x + c), so
+    // that a stage with few rows still spreads over every SM of the cluster while each warp
+    // covers 32 consecutive rows (coalesced ELL loads)
+    const int tid = (((int)threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x) * 32 + ((int)threadIdx.x & 31);
     // vertex-level right-hand side: sum of the corner sums of the elements at each vertex
     {
         float* b1 = a.lv[1].b;
@@ -295,25 +345,32 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
         }
     }
     cl.sync();
+    // Each stage below reads one vector written in the stage before (by any
+    // CTA): it is first copied into every CTA's shared memory (when it fits)
+    // so that the row gathers are shared-memory loads.
     // down: x = omega dinv b ; r = b - A x ; b_{l+1} = R r.  The residual is
     // formed as b - As b with As = A diag(omega dinv) (stored), so x and r come
     // out of one pass over b.
     for (int l = 1; l < a.nlev; ++l) {
         const MGLevelDev& L = a.lv[l];
+        const bool sb = stage_x(L.b, L.n, xs, a.cap);
         for (int i = tid; i < L.n; i += T) {
-            const float bi = __ldcg(L.b + i);
-            const float si = ell_row(L.aw, L.n, L.Aci, L.Asv, L.b, i);
+            const float bi = sb ? xs[i] : __ldcg(L.b + i);
+            const float si = ell_apply(sb, L.aw, L.n, L.Aci, L.Asv, L.b, xs, i);
             L.r[i] = bi - si;
             L.x[i] = L.omega * L.dinv[i] * bi;
         }
         cl.sync();
         const MGLevelDev& Lc = a.lv[l + 1];
-        for (int i = tid; i < Lc.n; i += T) Lc.b[i] = ell_row(L.rw, Lc.n, L.Rci, L.Rv, L.r, i);
+        const bool sr = stage_x(L.r, L.n, xs, a.cap);
+        for (int i = tid; i < Lc.n; i += T) Lc.b[i] = ell_apply(sr, L.rw, Lc.n, L.Rci, L.Rv, L.r, xs, i);
         cl.sync();
     }
     // coarsest: x = Cinv b, one warp per row
     {
         const MGLevelDev& C = a.lv[a.nlev];
+        const bool sc = stage_x(C.b, C.n, xs, a.cap);
+        const float* bsrc = sc ? (const float*)xs : C.b;
         const int lane = threadIdx.x & 31, w = tid >> 5, nw = T >> 5;
         for (int row = w; row < C.n; row += nw) {
             const float* cr = a.cinv + (size_t)row * C.n;
@@ -324,7 +381,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
                 for (int q = 0; q < 8; ++q) {
                     const int j = j0 + q * 32 + lane;
                     cv[q] = j < C.n ? cr[j] : 0.0f;
-                    bv[q] = j < C.n ? __ldcg(C.b + j) : 0.0f;
+                    bv[q] = j < C.n ? (sc ? bsrc[j] : __ldcg(bsrc + j)) : 0.0f;
                 }
 #pragma unroll
                 for (int q = 0; q < 8; ++q) s = fmaf(cv[q], bv[q], s);
@@ -339,14 +396,16 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
     const float* coarse_out = a.lv[a.nlev].x;
     for (int l = a.nlev - 1; l >= 1; --l) {
         const MGLevelDev& L = a.lv[l];
+        const bool sp = stage_x(coarse_out, a.lv[l + 1].n, xs, a.cap);
         for (int i = tid; i < L.n; i += T) {
             const float xi = __ldcg(L.x + i);
-            L.x[i] = xi + ell_row(L.pw, L.n, L.Pci, L.Pv, coarse_out, i);
+            L.x[i] = xi + ell_apply(sp, L.pw, L.n, L.Pci, L.Pv, coarse_out, xs, i);
         }
         cl.sync();
+        const bool sx = stage_x(L.x, L.n, xs, a.cap);
         for (int i = tid; i < L.n; i += T) {
-            const float xi = __ldcg(L.x + i), bi = __ldcg(L.b + i), di = L.dinv[i];
-            const float si = ell_row(L.aw, L.n, L.Aci, L.Av, L.x, i);
+            const float xi = sx ? xs[i] : __ldcg(L.x + i), bi = __ldcg(L.b + i), di = L.dinv[i];
+            const float si = ell_apply(sx, L.aw, L.n, L.Aci, L.Av, L.x, xs, i);
             L.t[i] = xi + L.omega * di * (bi - si);
         }
         cl.sync();
@@ -365,12 +424,15 @@ int mg_coarse_cluster_size() {
     static int chosen = 0;
     if (chosen) return chosen;
     int ctas = 8;
+    cudaFuncSetAttribute(coarse_cycle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kCoarseSmemFloats * (int)sizeof(float));
     if (cudaFuncSetAttribute(coarse_cycle_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
         cudaSuccess) {
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr[1];
         cfg.gridDim = dim3(16, 1, 1);
         cfg.blockDim = dim3(kCoarseThreads, 1, 1);
+        cfg.dynamicSmemBytes = kCoarseSmemFloats * sizeof(float);
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = 16;
         attr[0].val.clusterDim.y = 1;
@@ -391,11 +453,15 @@ const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* 
     ca.nvert = m.nvert; ca.nlev = m.nlev; ca.cres = cres; ca.vw = m.vw; ca.vinc = m.vinc;
     for (int l = 0; l <= m.nlev; ++l) ca.lv[l] = m.lv[l];
     ca.cinv = m.cinv;
+    // shared memory for the largest vector a stage stages (the vertex level), up to kCoarseSmemFloats
+    int vmax = 0;
+    for (int l = 1; l <= m.nlev; ++l) vmax = std::max(vmax, m.lv[l].n);
+    ca.cap = std::min(vmax, kCoarseSmemFloats);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(m.coarse_ctas, 1, 1);
     cfg.blockDim = dim3(kCoarseThreads, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = (size_t)ca.cap * sizeof(float);
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = m.coarse_ctas;
