@@ -311,11 +311,22 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;  // valid in thread 0
 }
 
-// same sum over partials written by other blocks of the running kernel (read through L2)
+// sum over partials written by other blocks of the running kernel (read
+// through L2, four loads in flight per thread); deterministic order
 __device__ __forceinline__ double sum_partials_cg(const double* part, int nblk, double* sh) {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += __ldcg(part + i);
-    double s = block_sum(v, sh);
+    const int bd = blockDim.x;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int i = threadIdx.x;
+    for (; i + 3 * bd < nblk; i += 4 * bd) {
+        const double a0 = __ldcg(part + i), a1 = __ldcg(part + i + bd), a2 = __ldcg(part + i + 2 * bd),
+                     a3 = __ldcg(part + i + 3 * bd);
+        v0 += a0;
+        v1 += a1;
+        v2 += a2;
+        v3 += a3;
+    }
+    for (; i < nblk; i += bd) v0 += __ldcg(part + i);
+    double s = block_sum((v0 + v1) + (v2 + v3), sh);
     if (threadIdx.x == 0) sh[32] = s;
     __syncthreads();
     s = sh[32];
@@ -324,16 +335,31 @@ __device__ __forceinline__ double sum_partials_cg(const double* part, int nblk, 
 }
 
 // the three partial arrays part[0..nblk), part[nblk..2 nblk), part[2 nblk..3 nblk)
-// summed in one pass (independent loads in flight)
+// summed in one pass (six independent loads in flight per thread)
 __device__ __forceinline__ void sum3_partials_cg(const double* part, int nblk, double* sh, double& s0, double& s1,
                                                  double& s2) {
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    const int bd = blockDim.x;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0;
+    int i = threadIdx.x;
+    for (; i + bd < nblk; i += 2 * bd) {
         const double a0 = __ldcg(part + i), a1 = __ldcg(part + nblk + i), a2 = __ldcg(part + 2 * nblk + i);
+        const double b0 = __ldcg(part + i + bd), b1 = __ldcg(part + nblk + i + bd),
+                     b2 = __ldcg(part + 2 * nblk + i + bd);
         v0 += a0;
         v1 += a1;
         v2 += a2;
+        u0 += b0;
+        u1 += b1;
+        u2 += b2;
     }
+    for (; i < nblk; i += bd) {
+        v0 += __ldcg(part + i);
+        v1 += __ldcg(part + nblk + i);
+        v2 += __ldcg(part + 2 * nblk + i);
+    }
+    v0 += u0;
+    v1 += u1;
+    v2 += u2;
     s0 = block_sum(v0, sh);
     s1 = block_sum(v1, sh);
     s2 = block_sum(v2, sh);
