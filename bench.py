@@ -156,7 +156,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per launch measured by ncu for the current kernels
 # on this workload (the cg_iteration, sweep-kernel and launch-list summaries for this workload); a key
 # is dropped whenever the kernels it covers change.
-NCU_TRAFFIC: dict = {"cg_iteration": 512.9e6, "sweep_kernel": 3882.6e6, "moments": 138.5e6}
+NCU_TRAFFIC: dict = {"cg_iteration": None, "sweep_kernel": 3882.6e6, "moments": 138.5e6}
 
 # a timed step is outer iteration START_ITERATIONS + 1 from varphi^0 = 0
 START_ITERATIONS = 3
@@ -176,20 +176,24 @@ def moments_bytes_per_elem(n: int, nd: int) -> float:
     return 8 * nd * n + 48 * n
 
 
-def mg_cg_bytes_per_iter(ne: int, n: int) -> float:
+def mg_cg_bytes_per_iter(ne: int, n: int, nu0: int = 3) -> float:
     """HBM bytes of one multigrid-preconditioned CG iteration on the element
-    blocks.  The operator is stored as the n x n diagonal block plus four
-    G x G face-coupling matrices per element (G = 2(p+1)): the FP64 product
-    reads it once (8 (n^2 + 4 G^2) B); the V-cycle's level 0 reads the FP32
-    block-Jacobi inverse in all four smoothing steps (16 n^2 B), the FP32 face
-    couplings in the three steps that start from a nonzero iterate and in the
-    residual (64 G^2 B), and the FP32 diagonal block in the residual only
-    (4 n^2 B; a smoothing step needs no diagonal block because Pinv is its
-    inverse); about 30 FP64 vector passes of n words each.  The vertex and
-    aggregation levels are < 2 % of the bytes and left out."""
+    blocks, with nu0 level-0 smoothing steps before and after the coarse
+    correction (the library's default: 3).  The operator is stored as the n x n
+    diagonal block plus four G x G face-coupling matrices per element
+    (G = 2(p+1)): the FP64-accuracy product reads it once as FP32 pairs
+    (8 (n^2 + 4 G^2) B); level 0 reads the FP32 block-Jacobi inverse in every
+    smoothing step (2 nu0 * 4 n^2 B), the FP32 face couplings in the 2 nu0 - 1
+    steps that start from a nonzero iterate and in the residual (2 nu0 * 16 G^2
+    B), and the FP32 diagonal block in the residual only (4 n^2 B; a smoothing
+    step needs no diagonal block because Pinv is its inverse); the Chebyshev
+    recurrence reads the previous FP32 iterate in 2 nu0 - 3 steps; about 30 FP64
+    vector passes of n words.  The vertex and aggregation levels are < 2 % of
+    the bytes and left out."""
     g = 2 * (int(round(n ** 0.5)))
     op = n * n + 4 * g * g
-    return ne * (8 * op + 16 * n * n + 64 * g * g + 4 * n * n + 30 * n * 8)
+    prev = max(0, 2 * nu0 - 3)
+    return ne * (8 * op + 2 * nu0 * 4 * n * n + 2 * nu0 * 16 * g * g + 4 * n * n + prev * 4 * n + 30 * n * 8)
 
 
 def run_ours(args) -> None:
@@ -309,10 +313,10 @@ def run_ours(args) -> None:
                     launches_per_step=launches_per_step, kernel=kernel, peak_note=f"{hbm_src} copy bandwidth")
 
     rooflines = {
-        "cg_iteration": entry(cg_bytes, ms_iter, "one flexible-CG iteration: CUDA graph of 10 kernels (staged "
-                              "operator product; V-cycle: first smoothing step with the CG update, smoothing step, "
-                              "residual, cluster coarse cycle, prolongation, smoothing step, last smoothing step "
-                              "with the dot products; one-block finish; direction)", "cg_iteration", cg_it),
+        "cg_iteration": entry(cg_bytes, ms_iter, "one flexible-CG iteration: CUDA graph of 12 kernels (operator "
+                              "product; V-cycle: first smoothing step with the CG update, 2 smoothing steps, "
+                              "residual, cluster coarse cycle, prolongation, 2 smoothing steps, last smoothing step "
+                              "with the dot products; direction)", "cg_iteration", cg_it),
         "sweep_kernel": entry(sweep_bytes, ms_sweep, "sweep_kernel<double, 4, SOURCE, cached inverse> "
                               "(plus the per-sweep source kernel)", "sweep_kernel", 1),
         "moments": entry(mom_bytes, ms_mom, "moments_df_kernel + beta_kernel", "moments", 1),
@@ -443,7 +447,7 @@ def run_ours(args) -> None:
                        "l2": "flushed between timed steps (256 MiB write)", "sweep": "fp64, cached local inverses",
                        "step_state": f"outer iteration {START_ITERATIONS + 1} from varphi^0 = 0, restored before "
                                      "every step",
-                       "moment_solve": "multigrid-preconditioned flexible CG", "cg_tol": 1e-12},
+                       "moment_solve": "flexible CG, multigrid V-cycle with degree-3 Chebyshev level-0 smoothing", "cg_tol": 1e-12},
             "roofline": roof, "roofline_all": rooflines, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "phases_ms": dict(residual=ms_res, sweep=ms_sweep, moments=mean("ms_moments"), rhs=mean("ms_rhs"),

@@ -67,6 +67,7 @@ enum { SMM_SWEEP_FP64 = 0, SMM_SWEEP_FP32_REFINED = 1 };
 enum { SMM_PRECOND_BLOCK_JACOBI = 0, SMM_PRECOND_MULTIGRID = 1 };
 enum { SMM_SOLVER_LU = 0, SMM_SOLVER_CACHED_INVERSE = 1 };
 enum { SMM_MOMENT_IP = 0, SMM_MOMENT_CG = 1 };
+enum { SMM_SMOOTHER_JACOBI = 0, SMM_SMOOTHER_CHEBYSHEV = 1 };
 
 typedef struct {
     int32_t n_elem;             /* number of quadrilaterals */
@@ -109,9 +110,12 @@ typedef struct {
                                    max|G(x0)|, the first residual of the zero
                                    guess being max|G(0)| ~ max|G(x0)|), restart
                                    from zero (default 0) */
-    int32_t mg_smooth_steps;    /* multigrid preconditioner: damped block-Jacobi
-                                   steps on the DG level before and after the
-                                   coarse correction, 1..4 (default 2) */
+    int32_t mg_smooth_steps;    /* multigrid preconditioner: smoothing steps on
+                                   the DG level before and after the coarse
+                                   correction (the Chebyshev degree with
+                                   SMM_SMOOTHER_CHEBYSHEV), 1..4 (default 3);
+                                   also the point-Jacobi steps of the
+                                   continuous system's V-cycle */
     int32_t moment_discretization; /* SMM_MOMENT_IP (default): interior penalty
                                    moment system on the DG space (paper Eq.
                                    ipsmm).  SMM_MOMENT_CG: the continuous
@@ -146,6 +150,15 @@ typedef struct {
                                    and converges to the same fixed point.
                                    1..64, default 1 (exact sweep); FP64 sweeps
                                    only. */
+    int32_t mg_smoother;        /* level-0 smoother of the IP-SMM multigrid
+                                   preconditioner: SMM_SMOOTHER_CHEBYSHEV
+                                   (default: the Chebyshev polynomial of degree
+                                   mg_smooth_steps in Pinv A on
+                                   [lambda_max / 60, lambda_max]) or
+                                   SMM_SMOOTHER_JACOBI (damped element-block
+                                   Jacobi, omega = (4/3) / lambda_max); the
+                                   same cost per step.  lambda_max is a
+                                   power-iteration estimate times 1.05. */
 } smm_options;
 
 typedef struct {

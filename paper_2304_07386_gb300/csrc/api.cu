@@ -211,10 +211,11 @@ void smm_default_options(smm_options* opt) {
     opt->sweep_solver = SMM_SOLVER_CACHED_INVERSE;
     opt->anderson_depth = 0;
     opt->guess_check = 0;
-    opt->mg_smooth_steps = 2;
+    opt->mg_smooth_steps = 3;
     opt->moment_discretization = SMM_MOMENT_IP;
     opt->negative_flux_fixup = 0;
     opt->sweep_tiles = 1;
+    opt->mg_smoother = SMM_SMOOTHER_CHEBYSHEV;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -251,7 +252,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         o.anderson_depth > 5 || o.mg_smooth_steps < 1 || o.mg_smooth_steps > 4 ||
         (o.moment_discretization != SMM_MOMENT_IP && o.moment_discretization != SMM_MOMENT_CG) ||
         (o.negative_flux_fixup && o.sweep_precision != SMM_SWEEP_FP64) || o.sweep_tiles < 1 || o.sweep_tiles > 64 ||
-        (o.sweep_tiles > 1 && o.sweep_precision != SMM_SWEEP_FP64))
+        (o.sweep_tiles > 1 && o.sweep_precision != SMM_SWEEP_FP64) ||
+        (o.mg_smoother != SMM_SMOOTHER_JACOBI && o.mg_smoother != SMM_SMOOTHER_CHEBYSHEV))
         return fail(SMM_ERR_INVALID_ARG, "bad options");
 
     smm::Input in;
@@ -406,6 +408,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         smm::MGPlan& P = h->mg;
         P.enabled = true;
         P.ne = s.ne; P.n = s.n; P.nu0 = o.mg_smooth_steps; P.omega0 = H.omega0;
+        P.chebyshev = o.mg_smoother == SMM_SMOOTHER_CHEBYSHEV;
         if (!cgm) {
             float *ad32 = nullptr, *c32 = nullptr, *pi32 = nullptr;
             ok &= upload_f32(h, ad32, transpose_blocks(s.Adiag, s.n));

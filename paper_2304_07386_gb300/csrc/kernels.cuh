@@ -203,7 +203,8 @@ struct L2Chunk {
 struct MGPlan {
     bool enabled = false;
     int ne = 0, n = 0, nu0 = 2;
-    double omega0 = 0.0;
+    double omega0 = 0.0;                          // Jacobi damping (4/3) / lambda_max
+    bool chebyshev = false;                       // level-0 smoother: Chebyshev polynomial of degree nu0
     FaceOp<float> A;                              // FP32 copy of the operator
     const float* PinvT = nullptr;                 // FP32 block-Jacobi inverses
     float* x0 = nullptr; float* x0b = nullptr;   // [ne*n], level 0 works in FP32

@@ -36,17 +36,20 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // true when the CG has finished
 __device__ __forceinline__ bool mg_skip(const int* ctl) { return ((const volatile int*)ctl)[0] != 0; }
 
-// xout = xin + omega Pinv (b - A xin) in FP32; xin == nullptr means xin = 0;
-// b is the FP64 right-hand side, xout is FP32 (inner steps) or FP64 (last step).
+// One level-0 smoothing step in FP32:
+//   xout = xin + c2 Pinv (b - A xin) + c1 (xin - xprev)
+// (damped block Jacobi: c1 = 0, c2 = omega; a Chebyshev step: the three-term
+// recurrence's coefficients).  xin == nullptr means xin = 0, xprev == nullptr
+// means xprev = 0; xout may be xprev (each row reads only its own xprev).  b is
+// the FP64 right-hand side, xout is FP32 (inner steps) or FP64 (last step).
 // Pinv is the inverse of the diagonal block A_d (formed in FP64), so
 // Pinv (b - A xin) = Pinv (b - A_off xin) - xin: the step reads the face
-// couplings and Pinv but not A_d, and computes xin + omega (z - xin) with
-// z = Pinv (b - A_off xin).
+// couplings and Pinv but not A_d, and uses z - xin with z = Pinv (b - A_off xin).
 template <typename OT, int N>
 __global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, FaceOp<float> A, const float* __restrict__ PinvT,
-                                                        float omega, const double* __restrict__ b,
-                                                        const float* __restrict__ xin, OT* __restrict__ xout,
-                                                        const int* ctl) {
+                                                        float c1, float c2, const double* __restrict__ b,
+                                                        const float* __restrict__ xin, const float* xprev,
+                                                        OT* xout, const int* ctl) {
     if (mg_skip(ctl)) return;
     __shared__ float res[256];
     __shared__ FaceScratch<N, float> sc;
@@ -71,7 +74,9 @@ __global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, FaceOp<float> A,
         float z = 0.0f;
 #pragma unroll
         for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
-        xout[(size_t)e * N + i] = (OT)(x + omega * (z - x));
+        const size_t o = (size_t)e * N + i;
+        const float xp = xprev ? xprev[o] : 0.0f;
+        xout[o] = (OT)(x + c2 * (z - x) + c1 * (x - xp));
     }
 }
 
@@ -108,9 +113,9 @@ __global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> 
 // First pre-smoothing step (from zero) of a flexible-CG iteration with the
 // CG update folded in: x += alpha p, r_old = r, r -= alpha q (alpha = rz / p.q
 // from the operator product's last block), partial r.r -> part[nblk + block];
-// xout = omega Pinv r in FP32.  One block per EPB elements, as the product.
+// xout = c2 Pinv r in FP32.  One block per EPB elements, as the product.
 template <int N>
-__global__ void __launch_bounds__(256) bj_first_update_kernel(CGArgs a, const float* __restrict__ PinvT, float omega,
+__global__ void __launch_bounds__(256) bj_first_update_kernel(CGArgs a, const float* __restrict__ PinvT, float c2,
                                                               float* __restrict__ xout) {
     if (mg_skip(a.ctl)) return;
     __shared__ float res[256];
@@ -139,21 +144,23 @@ __global__ void __launch_bounds__(256) bj_first_update_kernel(CGArgs a, const fl
         float z = 0.0f;
 #pragma unroll
         for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
-        xout[(size_t)e * N + i] = omega * z;
+        xout[(size_t)e * N + i] = c2 * z;
     }
     const double s = block_sum(rr, sh);
     if (threadIdx.x == 0) a.part[a.nblk + blockIdx.x] = s;
 }
 
-// Last post-smoothing step of a flexible-CG iteration, z = x + omega (Pinv
-// (r - A_off x) - x) written in FP64, with the CG dot products folded in:
+// Last post-smoothing step of a flexible-CG iteration, z = x + c2 (Pinv
+// (r - A_off x) - x) + c1 (x - xprev) written in FP64 (xprev == nullptr:
+// zero), with the CG dot products folded in:
 // partials r.z -> part[2 nblk + block] and (r - r_old).z -> part[3 nblk +
 // block].  The last block reduces them with the first step's r.r partials:
 // beta = (r - r_old).z / rz_old, rz, rr, the iteration count and the
 // convergence test.
 template <int N>
 __global__ void __launch_bounds__(256) bj_last_dots_kernel(CGArgs a, FaceOp<float> A, const float* __restrict__ PinvT,
-                                                           float omega, const float* __restrict__ xin) {
+                                                           float c1, float c2, const float* __restrict__ xin,
+                                                           const float* __restrict__ xprev) {
     if (mg_skip(a.ctl)) return;
     __shared__ float res[256];
     __shared__ FaceScratch<N, float> sc;
@@ -179,7 +186,8 @@ __global__ void __launch_bounds__(256) bj_last_dots_kernel(CGArgs a, FaceOp<floa
 #pragma unroll
         for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
         const size_t o = (size_t)e * N + i;
-        const double zd = (double)(x + omega * (z - x));
+        const float xp = xprev ? xprev[o] : 0.0f;
+        const double zd = (double)(x + c2 * (z - x) + c1 * (x - xp));
         a.z[o] = zd;
         rz = rd * zd;
         dz = (rd - a.rold[o]) * zd;
@@ -483,34 +491,86 @@ int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaSt
     }
 }
 
+// Coefficients (c1[k], c2[k]) of the level-0 smoothing steps k = 0..nu0-1,
+// x_{k+1} = x_k + c2 Pinv (b - A x_k) + c1 (x_k - x_{k-1}).  Damped block
+// Jacobi: c1 = 0, c2 = omega0.  Chebyshev of degree nu0 for Pinv A on
+// [lmax / 60, lmax], lmax = (4/3) / omega0 (the power-iteration estimate times
+// 1.05), by the three-term recurrence of Chebyshev acceleration: with
+// theta, delta the interval's centre and half-width, sigma = theta / delta,
+// rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1}): c2 = 1 / theta, c1 = 0
+// for k = 0 and c2 = 2 rho_k / delta, c1 = rho_k rho_{k-1} after.
+static void smoother_coeffs(const MGPlan& m, float* c1, float* c2) {
+    if (!m.chebyshev) {
+        for (int k = 0; k < m.nu0; ++k) {
+            c1[k] = 0.0f;
+            c2[k] = (float)m.omega0;
+        }
+        return;
+    }
+    const double hi = (4.0 / 3.0) / m.omega0, lo = hi / 60.0;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    c1[0] = 0.0f;
+    c2[0] = (float)(1.0 / theta);
+    for (int k = 1; k < m.nu0; ++k) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        c1[k] = (float)(rn * rho);
+        c2[k] = (float)(2.0 * rn / delta);
+        rho = rn;
+    }
+}
+
+// The smoothing steps after the first keep the current and the previous
+// iterate in the two FP32 buffers; a step writes over the previous iterate
+// (or into the other buffer while the previous iterate is zero).
+struct SmoothState {
+    float* cur;
+    float* prev;   // nullptr: zero
+    float* other;  // the buffer that is not cur
+    float* next() const { return prev ? prev : other; }
+    void advance(float* out) {
+        other = cur == out ? other : cur;
+        prev = cur;
+        cur = out;
+    }
+};
+
 template <int N>
 int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s) {
     int launches = 0;
     const int tpb = cg_threads_per_block(N);
     const int nblk0 = (m.ne + FaceDims<N>::EPB - 1) / FaceDims<N>::EPB;
-    const float w0 = (float)m.omega0;
+    float c1[4], c2[4];
+    smoother_coeffs(m, c1, c2);
     // level 0 pre-smoothing from zero (FP32)
-    float* xa = m.x0;
-    float* xb = m.x0b;
-    bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, r, nullptr, xa, ctl);
+    SmoothState st{m.x0, nullptr, m.x0b};
+    bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[0], c2[0], r, nullptr, nullptr, st.cur,
+                                                     ctl);
     ++launches;
     for (int k = 1; k < m.nu0; ++k) {
-        bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, xb, ctl);
-        std::swap(xa, xb);
+        float* out = st.next();
+        bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev, out,
+                                                         ctl);
+        st.advance(out);
         ++launches;
     }
-    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, r, xa, m.w4, m.res0, m.coarse_pf, m.coarse_npf, ctl);
+    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, r, st.cur, m.w4, m.res0, m.coarse_pf, m.coarse_npf, ctl);
     // vertex and aggregation levels and the coarsest solve (one cluster launch)
     const float* coarse_out = launch_coarse_cycle(m, m.res0, ctl, s);
     const int rows0 = m.ne * N;
-    prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, xa, ctl);
+    prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, st.cur, ctl);
     launches += 3;
+    // post-smoothing: the recurrence restarts from the corrected iterate
+    st.prev = nullptr;
     for (int k = 0; k < m.nu0; ++k) {
         if (k == m.nu0 - 1) {
-            bj_smooth_kernel<double, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, z, ctl);
+            bj_smooth_kernel<double, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev, z,
+                                                              ctl);
         } else {
-            bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, r, xa, xb, ctl);
-            std::swap(xa, xb);
+            float* out = st.next();
+            bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev,
+                                                             out, ctl);
+            st.advance(out);
         }
         ++launches;
     }
@@ -530,28 +590,33 @@ template <int N>
 int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
     const int tpb = cg_threads_per_block(N);
     const int nblk0 = a.nblk;
-    const float w0 = (float)m.omega0;
-    float* xa = m.x0;
-    float* xb = m.x0b;
-    bj_first_update_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.PinvT, w0, xa);
+    float c1[4], c2[4];
+    smoother_coeffs(m, c1, c2);
+    SmoothState st{m.x0, nullptr, m.x0b};
+    bj_first_update_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.PinvT, c2[0], st.cur);
     int launches = 1;
     for (int k = 1; k < m.nu0; ++k) {
-        bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, a.r, xa, xb, a.ctl);
-        std::swap(xa, xb);
+        float* out = st.next();
+        bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], a.r, st.cur, st.prev, out,
+                                                         a.ctl);
+        st.advance(out);
         ++launches;
     }
-    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, a.r, xa, m.w4, m.res0, m.coarse_pf, m.coarse_npf,
-                                                  a.ctl);
+    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, a.r, st.cur, m.w4, m.res0, m.coarse_pf, m.coarse_npf,
+                                                a.ctl);
     const float* coarse_out = launch_coarse_cycle(m, m.res0, a.ctl, s);
     const int rows0 = m.ne * N;
-    prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, xa, a.ctl);
+    prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, st.cur, a.ctl);
     launches += 3;
+    st.prev = nullptr;
     for (int k = 0; k < m.nu0; ++k) {
         if (k == m.nu0 - 1) {
-            bj_last_dots_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.A, m.PinvT, w0, xa);
+            bj_last_dots_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.A, m.PinvT, c1[k], c2[k], st.cur, st.prev);
         } else {
-            bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, w0, a.r, xa, xb, a.ctl);
-            std::swap(xa, xb);
+            float* out = st.next();
+            bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], a.r, st.cur, st.prev,
+                                                             out, a.ctl);
+            st.advance(out);
         }
         ++launches;
     }

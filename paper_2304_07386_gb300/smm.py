@@ -25,6 +25,7 @@ SMM_SWEEP_FP64, SMM_SWEEP_FP32_REFINED = 0, 1
 SMM_PRECOND_BLOCK_JACOBI, SMM_PRECOND_MULTIGRID = 0, 1
 SMM_SOLVER_LU, SMM_SOLVER_CACHED_INVERSE = 0, 1
 SMM_MOMENT_IP, SMM_MOMENT_CG = 0, 1
+SMM_SMOOTHER_JACOBI, SMM_SMOOTHER_CHEBYSHEV = 0, 1
 
 
 class smm_mesh(C.Structure):
@@ -37,7 +38,7 @@ class smm_options(C.Structure):
                 ("kappa_scale", C.c_double), ("spin_timeout_s", C.c_double), ("precond", C.c_int32),
                 ("sweep_solver", C.c_int32), ("anderson_depth", C.c_int32), ("guess_check", C.c_int32),
                 ("mg_smooth_steps", C.c_int32), ("moment_discretization", C.c_int32),
-                ("negative_flux_fixup", C.c_int32), ("sweep_tiles", C.c_int32)]
+                ("negative_flux_fixup", C.c_int32), ("sweep_tiles", C.c_int32), ("mg_smoother", C.c_int32)]
 
 
 class smm_info(C.Structure):
