@@ -106,6 +106,7 @@ struct smm_ctx {
     double* xcg = nullptr;         // CG iterate owned by the handle (captured in the iteration graph)
     cudaStream_t cap = nullptr;    // private stream used once to capture the CG iteration graph
     cudaGraphExec_t cg_graph = nullptr;
+    cudaGraphExec_t cg_loop = nullptr;   // the whole CG loop (while node over one iteration); null: chunked launches
     int graph_kernels = 0;
     // pinned host scratch
     double* h_scal = nullptr;
@@ -125,6 +126,7 @@ struct smm_ctx {
     }
     ~smm_ctx() {
         if (cg_graph) cudaGraphExecDestroy(cg_graph);
+        if (cg_loop) cudaGraphExecDestroy(cg_loop);
         if (cap) cudaStreamDestroy(cap);
         for (void* ptr : allocs) cudaFree(ptr);
         if (h_scal) cudaFreeHost(h_scal);
@@ -526,6 +528,41 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         const cudaError_t ie = cudaGraphInstantiate(&h->cg_graph, g, 0);
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) return bail(SMM_ERR_CUDA, "CG graph instantiation failed");
+        // the whole CG loop as one graph: a while node whose body is one
+        // iteration followed by the loop-control kernel, so a solve needs no
+        // host round trip between iterations; where the runtime cannot build
+        // it, the solve launches the one-iteration graph in chunks
+        {
+            cudaGraph_t G = nullptr;
+            cudaGraphConditionalHandle hc = 0;
+            bool okg = cudaGraphCreate(&G, 0) == cudaSuccess &&
+                       cudaGraphConditionalHandleCreate(&hc, G, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = hc;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node = nullptr;
+            okg = okg && cudaGraphAddNode(&node, G, nullptr, nullptr, 0, &np) == cudaSuccess;
+            okg = okg && cudaStreamBeginCaptureToGraph(h->cap, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (okg) {
+                if (cgm)
+                    smm::cgc_iteration(ca, h->cgc, h->mg, h->cap);
+                else
+                    smm::cgx_iterations(ca, 1, h->mg, h->cap);
+                smm::launch_cg_loop_control(hc, h->ctl, h->cap);
+                cudaGraph_t body = nullptr;
+                okg = cudaStreamEndCapture(h->cap, &body) == cudaSuccess;
+            }
+            okg = okg && cudaGraphInstantiate(&h->cg_loop, G, 0) == cudaSuccess;
+            if (G) cudaGraphDestroy(G);
+            if (!okg) {
+                if (h->cg_loop) cudaGraphExecDestroy(h->cg_loop);
+                h->cg_loop = nullptr;
+                cudaGetLastError();
+            }
+        }
     }
     if (o.anderson_depth > 0) {
         for (int k = 0; k <= o.anderson_depth; ++k) {
@@ -857,8 +894,14 @@ smm_status run_cg(smm_handle h, double* x, int* iters) {
         h->launches += 2;
     }
     SMM_CUDA(cudaGetLastError());
+    if (mg && h->cg_loop) {
+        SMM_CUDA(cudaGraphLaunch(h->cg_loop, h->stream));
+        SMM_CUDA(cudaMemcpyAsync(h->h_int, h->ctl, 8 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        SMM_CUDA(cudaStreamSynchronize(h->stream));
+        h->launches += (long long)h->h_int[5] * (h->graph_kernels + 1);
+    }
     int chunk = mg ? 4 : 8;
-    while (true) {
+    while (!(mg && h->cg_loop)) {
         SMM_CUDA(cudaMemcpyAsync(h->h_int, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         SMM_CUDA(cudaStreamSynchronize(h->stream));
         if (h->h_int[0]) break;

@@ -234,6 +234,8 @@ int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaSt
 int mg_cg_iteration(const MGPlan& m, const CGArgs& a, cudaStream_t s);
 
 void cg_start(const CGArgs& a, double tol, int max_iters, cudaStream_t s);
+// the loop-control kernel that ends a trip of the device-side CG loop (ctl[5] counts the trips)
+void launch_cg_loop_control(cudaGraphConditionalHandle handle, int* ctl, cudaStream_t s);
 void launch_cgx_update(const CGArgs& a, cudaStream_t s);
 void launch_cgx_rz(const CGArgs& a, cudaStream_t s);
 void launch_cgx_direction(const CGArgs& a, cudaStream_t s);

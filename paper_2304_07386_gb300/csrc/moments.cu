@@ -665,6 +665,24 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
     return launches;
 }
 
+namespace {
+
+// End of one trip of the device-side CG loop (a graph while node): continue
+// while the CG has not finished; a hard bound of max_iters + 2 trips (counted
+// in ctl[5]) ends the loop even if no kernel has set the finished flag.
+__global__ void cg_loop_kernel(cudaGraphConditionalHandle handle, int* ctl) {
+    const int trips = ctl[5] + 1;
+    ctl[5] = trips;
+    const bool stop = *(volatile int*)ctl != 0 || trips >= ctl[2] + 2;
+    cudaGraphSetConditional(handle, stop ? 0u : 1u);
+}
+
+}  // namespace
+
+void launch_cg_loop_control(cudaGraphConditionalHandle handle, int* ctl, cudaStream_t s) {
+    cg_loop_kernel<<<1, 1, 0, s>>>(handle, ctl);
+}
+
 void cg_iterations(const CGArgs& a, int count, cudaStream_t s) {
     const int tpb = cg_threads_per_block(a.n);
     for (int k = 0; k < count; ++k) {
