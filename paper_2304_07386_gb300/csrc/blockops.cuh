@@ -17,6 +17,32 @@ struct FaceDims {
     static constexpr int EPB = 256 / N;                                   // elements per block
 };
 
+// L2 eviction priority of loads (per-load cache policies, nothing global):
+// the level-0 FP32 blocks, which every V-cycle step reads again, are loaded
+// with evict_last; the FP32-pair operator of the CG product, streamed once per
+// iteration, with evict_first, so that it does not push the former out of L2
+__device__ __forceinline__ unsigned long long l2_keep() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_stream() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float ld_hint(const float* a, unsigned long long pol) {
+    float v;
+    asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float2 ld_hint(const float2* a, unsigned long long pol) {
+    float2 v;
+    asm("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_hint(const double* a, unsigned long long) { return *a; }
+
 // element-local node at face position a, line position t (t = 0 on face f)
 template <int P1>
 __device__ __forceinline__ int line_node(int f, int a, int t) {
@@ -89,8 +115,9 @@ __device__ __forceinline__ void face_couple(const CTy* __restrict__ Ce, const in
             if (nbr[e * 4 + f] >= 0) {
                 const CTy* C = Ce + (size_t)f * G * G + r;
                 const AT* g = sc.g + le * NG + f * G;
+                const unsigned long long pol = l2_keep();
 #pragma unroll
-                for (int c = 0; c < G; ++c) w += (AT)C[c * G] * g[c];
+                for (int c = 0; c < G; ++c) w += (AT)ld_hint(C + c * G, pol) * g[c];
             }
             sc.w[le * NG + v] = w;
         }
@@ -133,8 +160,9 @@ __device__ __forceinline__ AT faceop_row(const FaceOp<T>& op, const VT* __restri
         if constexpr (DIAG) {
             const T* Ad = op.AdT + (size_t)e * N * N + i;
             const VT* xe = x + (size_t)e * N;
+            const unsigned long long pol = l2_keep();
 #pragma unroll
-            for (int j = 0; j < N; ++j) y += (AT)Ad[j * N] * (AT)xe[j];
+            for (int j = 0; j < N; ++j) y += (AT)ld_hint(Ad + j * N, pol) * (AT)xe[j];
         }
         face_gather<N, T, AT, VT>(op, x, e, i, sc);
     }
@@ -202,9 +230,10 @@ __device__ __forceinline__ void face_couple_df(const float2* __restrict__ Ce, co
             if (nbr[e * 4 + f] >= 0) {
                 const float2* C = Ce + (size_t)f * G * G + r;
                 const float2* g = sc.g + le * NG + f * G;
+                const unsigned long long pol = l2_stream();
 #pragma unroll
                 for (int c = 0; c < G; ++c) {
-                    const float2 cv = C[c * G], gv = g[c];
+                    const float2 cv = ld_hint(C + c * G, pol), gv = g[c];
                     df_acc(ws, wc, cv.x, cv.y, gv.x, gv.y);
                 }
             }
@@ -217,9 +246,10 @@ __device__ __forceinline__ void face_couple_df(const float2* __restrict__ Ce, co
 template <int N>
 __device__ __forceinline__ void diag_row_df(const float2* __restrict__ Ad, const float2* __restrict__ xe, float& ys,
                                             float& yc) {
+    const unsigned long long pol = l2_stream();
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        const float2 a = Ad[j * N], v = xe[j];
+        const float2 a = ld_hint(Ad + j * N, pol), v = xe[j];
         df_acc(ys, yc, a.x, a.y, v.x, v.y);
     }
 }

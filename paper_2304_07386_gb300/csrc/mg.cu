@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, FaceOp<float> A,
         const float* P = PinvT + (size_t)e * N * N + i;
         const float* re = res + le * N;
         float z = 0.0f;
+        const unsigned long long pol = l2_keep();
 #pragma unroll
-        for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
+        for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
         const size_t o = (size_t)e * N + i;
         const float xp = xprev ? xprev[o] : 0.0f;
         xout[o] = (OT)(x + c2 * (z - x) + c1 * (x - xp));
@@ -142,8 +143,9 @@ __global__ void __launch_bounds__(256) bj_first_update_kernel(CGArgs a, const fl
         const float* P = PinvT + (size_t)e * N * N + i;
         const float* re = res + le * N;
         float z = 0.0f;
+        const unsigned long long pol = l2_keep();
 #pragma unroll
-        for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
+        for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
         xout[(size_t)e * N + i] = c2 * z;
     }
     const double s = block_sum(rr, sh);
@@ -183,8 +185,9 @@ __global__ void __launch_bounds__(256) bj_last_dots_kernel(CGArgs a, FaceOp<floa
         const float* P = PinvT + (size_t)e * N * N + i;
         const float* re = res + le * N;
         float z = 0.0f;
+        const unsigned long long pol = l2_keep();
 #pragma unroll
-        for (int j = 0; j < N; ++j) z = fmaf(P[j * N], re[j], z);
+        for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
         const size_t o = (size_t)e * N + i;
         const float xp = xprev ? xprev[o] : 0.0f;
         const double zd = (double)(x + c2 * (z - x) + c1 * (x - xp));
