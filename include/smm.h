@@ -159,6 +159,14 @@ typedef struct {
                                    Jacobi, omega = (4/3) / lambda_max); the
                                    same cost per step.  lambda_max is a
                                    power-iteration estimate times 1.05. */
+    int32_t cg_device_loop;     /* multigrid CG: nonzero (default) runs the
+                                   whole CG loop as one graph launch (a
+                                   device-controlled while node over one
+                                   iteration); 0 launches the one-iteration
+                                   graph in chunks checked by the host (for
+                                   profilers that do not see kernels inside
+                                   conditional graph nodes).  The same
+                                   arithmetic either way. */
 } smm_options;
 
 typedef struct {
@@ -234,10 +242,12 @@ smm_status smm_set_moments(smm_handle h, const double* moments_dev, const double
 smm_status smm_get_psi(smm_handle h, double* psi_dev);
 
 /* Solve the IP-SMM moment system (Eq. ipsmm) with the handle's closures by
- * preconditioned CG: a symmetric multigrid V-cycle (damped element-block
- * Jacobi on Y_p, Galerkin coarse level of continuous bilinear functions on
- * the mesh vertices, smoothed aggregation below it, dense coarsest solve) or
- * element-block Jacobi alone (options.precond).  phi_dev: dev [n_elem][n], in: initial
+ * preconditioned flexible CG: a multigrid V-cycle (Chebyshev or damped
+ * element-block Jacobi smoothing on Y_p, options.mg_smoother; Galerkin coarse
+ * level of continuous bilinear functions on the mesh vertices, smoothed
+ * aggregation below it, dense coarsest solve), the iterations run as one
+ * device-side graph loop (options.cg_device_loop), or element-block Jacobi
+ * alone (options.precond).  phi_dev: dev [n_elem][n], in: initial
  * guess, out: solution.  cg_iters (host, may be NULL): iterations used.
  * Errors: NOT_CONVERGED (phi_dev holds the last iterate), NONFINITE, CUDA. */
 smm_status smm_moment_solve(smm_handle h, double* phi_dev, int32_t* cg_iters);

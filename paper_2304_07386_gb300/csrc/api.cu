@@ -218,6 +218,7 @@ void smm_default_options(smm_options* opt) {
     opt->negative_flux_fixup = 0;
     opt->sweep_tiles = 1;
     opt->mg_smoother = SMM_SMOOTHER_CHEBYSHEV;
+    opt->cg_device_loop = 1;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -530,9 +531,10 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         if (ie != cudaSuccess) return bail(SMM_ERR_CUDA, "CG graph instantiation failed");
         // the whole CG loop as one graph: a while node whose body is one
         // iteration followed by the loop-control kernel, so a solve needs no
-        // host round trip between iterations; where the runtime cannot build
-        // it, the solve launches the one-iteration graph in chunks
-        {
+        // host round trip between iterations; without it (option off, or a
+        // runtime that cannot build it) the solve launches the one-iteration
+        // graph in chunks
+        if (o.cg_device_loop) {
             cudaGraph_t G = nullptr;
             cudaGraphConditionalHandle hc = 0;
             bool okg = cudaGraphCreate(&G, 0) == cudaSuccess &&

@@ -38,7 +38,8 @@ class smm_options(C.Structure):
                 ("kappa_scale", C.c_double), ("spin_timeout_s", C.c_double), ("precond", C.c_int32),
                 ("sweep_solver", C.c_int32), ("anderson_depth", C.c_int32), ("guess_check", C.c_int32),
                 ("mg_smooth_steps", C.c_int32), ("moment_discretization", C.c_int32),
-                ("negative_flux_fixup", C.c_int32), ("sweep_tiles", C.c_int32), ("mg_smoother", C.c_int32)]
+                ("negative_flux_fixup", C.c_int32), ("sweep_tiles", C.c_int32), ("mg_smoother", C.c_int32),
+                ("cg_device_loop", C.c_int32)]
 
 
 class smm_info(C.Structure):
