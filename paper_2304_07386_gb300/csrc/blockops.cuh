@@ -55,6 +55,15 @@ __device__ __forceinline__ int line_node(int f, int a, int t) {
     }
 }
 
+// the line of nodes of element-local face f at face position a: node(t) =
+// base + t * stride for line positions t = 0..p (the same nodes as line_node)
+template <int P1>
+__device__ __forceinline__ void line_of(int f, int a, int& base, int& stride) {
+    constexpr int p = P1 - 1;
+    base = f == 0 ? a : (f == 1 ? a * P1 + p : (f == 2 ? p * P1 + a : a * P1));
+    stride = f == 0 ? P1 : (f == 1 ? -1 : (f == 2 ? -P1 : 1));
+}
+
 // shared scratch of one thread block: neighbour face data and coupled face data
 template <int N, typename AT>
 struct FaceScratch {
@@ -85,13 +94,14 @@ __device__ __forceinline__ void face_gather(const FaceOp<T>& op, const VT* __res
             AT g = 0;
             if (e2 >= 0) {
                 const int f2 = op.nface[e * 4 + f];
-                const VT* x2 = x + (size_t)e2 * N;
+                int base, stride;
+                line_of<P1>(f2, r < P1 ? r : r - P1, base, stride);
+                const VT* x2 = x + (size_t)e2 * N + base;
                 if (r < P1) {
-                    g = (AT)x2[line_node<P1>(f2, r, 0)];
+                    g = (AT)x2[0];
                 } else {
-                    const int a = r - P1;
 #pragma unroll
-                    for (int t = 0; t < P1; ++t) g += (AT)op.wd[t] * (AT)x2[line_node<P1>(f2, a, t)];
+                    for (int t = 0; t < P1; ++t) g += (AT)op.wd[t] * (AT)x2[t * stride];
                 }
             }
             sc.g[le * NG + v] = g;
@@ -196,15 +206,16 @@ __device__ __forceinline__ void face_gather_df(const FaceOpDF& op, const float2*
             float2 g = make_float2(0.0f, 0.0f);
             if (e2 >= 0) {
                 const int f2 = op.nface[e * 4 + f];
-                const float2* x2 = x + (size_t)e2 * N;
+                int base, stride;
+                line_of<P1>(f2, r < P1 ? r : r - P1, base, stride);
+                const float2* x2 = x + (size_t)e2 * N + base;
                 if (r < P1) {
-                    g = x2[line_node<P1>(f2, r, 0)];
+                    g = x2[0];
                 } else {
-                    const int a = r - P1;
                     float gs = 0.0f, gc = 0.0f;
 #pragma unroll
                     for (int t = 0; t < P1; ++t) {
-                        const float2 xv = x2[line_node<P1>(f2, a, t)];
+                        const float2 xv = x2[t * stride];
                         df_acc(gs, gc, op.wd[t].x, op.wd[t].y, xv.x, xv.y);
                     }
                     g = df_norm(gs, gc);
