@@ -6,7 +6,9 @@ Chebyshev polynomial smoother with 1..4 steps (which exercises the two-buffer
 rotation of the three-term recurrence) reach the same solution within the CG
 tolerance, and that solution satisfies the oracle's IP-SMM system (Eq. ipsmm)
 to the same tolerance.  On a 32x32 mesh the degree-3 Chebyshev smoother takes
-fewer CG iterations than two Jacobi steps.
+fewer CG iterations than two Jacobi steps.  The CG loop run as one device-side
+graph and as host-checked chunks of the one-iteration graph executes the same
+kernels: the same solution bit for bit and the same iteration count.
 """
 import numpy as np
 import pytest
@@ -26,7 +28,7 @@ def _lib():
     B.build()
 
 
-def solve(prob, smoother, steps, phi):
+def solve(prob, smoother, steps, phi, device_loop=1):
     """Sweep from phi, then the moment solve; returns (solution, CG iterations)."""
     import paper_2304_07386_gb300 as P
     om, _ = P.smm_quadrature(prob["sn"])
@@ -34,6 +36,7 @@ def solve(prob, smoother, steps, phi):
     opt = P.smm_default_options()
     opt.mg_smoother = smoother
     opt.mg_smooth_steps = steps
+    opt.cg_device_loop = device_loop
     opt.tol_cg = 1e-13
     mesh = prob["mesh"]
     h = P.smm_create(mesh.nodes, mesh.elem_nodes, mesh.m, prob["p"], prob["sn"], prob["sigma_t"], prob["sigma_s"],
@@ -79,3 +82,13 @@ def test_chebyshev_needs_fewer_iterations():
     _, its_j = solve(prob, P.smm.SMM_SMOOTHER_JACOBI, 2, phi)
     _, its_c = solve(prob, P.smm.SMM_SMOOTHER_CHEBYSHEV, 3, phi)
     assert its_c < its_j, (its_c, its_j)
+
+
+def test_device_loop_matches_host_loop():
+    import paper_2304_07386_gb300 as P
+    prob = problem(20, 13, m=2, p=4, sn=4, seed=9, kind="mms", c=0.9)
+    phi = np.ones((prob["mesh"].n_elem, 25))
+    x_dev, its_dev = solve(prob, P.smm.SMM_SMOOTHER_CHEBYSHEV, 3, phi, device_loop=1)
+    x_host, its_host = solve(prob, P.smm.SMM_SMOOTHER_CHEBYSHEV, 3, phi, device_loop=0)
+    assert its_dev == its_host, (its_dev, its_host)
+    assert np.array_equal(x_dev, x_host)
