@@ -64,11 +64,13 @@ __device__ __forceinline__ void line_of(int f, int a, int& base, int& stride) {
     stride = f == 0 ? P1 : (f == 1 ? -1 : (f == 2 ? -P1 : 1));
 }
 
-// shared scratch of one thread block: neighbour face data and coupled face data
-template <int N, typename AT>
+// shared scratch of one thread block: neighbour face data and coupled face
+// data of its S element slots (the EPB elements of a block, or more when a
+// thread handles rows of several elements)
+template <int N, typename AT, int S = FaceDims<N>::EPB>
 struct FaceScratch {
-    AT g[FaceDims<N>::EPB * FaceDims<N>::NG];
-    AT w[FaceDims<N>::EPB * FaceDims<N>::NG];
+    AT g[S * FaceDims<N>::NG];
+    AT w[S * FaceDims<N>::NG];
 };
 
 // (A x)_i for row i of element e, in three phases separated by block
@@ -78,13 +80,14 @@ struct FaceScratch {
 // The phases are separate functions so that a kernel can stage the matrix
 // data (the diagonal block and the face couplings) while phase 1 runs.
 
-// phase 1 for the thread of row i of element e: face data v = i, i + N, ...
-template <int N, typename T, typename AT, typename VT>
+// phase 1 for the thread of row i of element e (element slot le of the
+// block's scratch; le < 0: threadIdx.x / N): face data v = i, i + N, ...
+template <int N, typename T, typename AT, typename VT, int S>
 __device__ __forceinline__ void face_gather(const FaceOp<T>& op, const VT* __restrict__ x, int e, int i,
-                                            FaceScratch<N, AT>& sc) {
+                                            FaceScratch<N, AT, S>& sc, int le = -1) {
     using D = FaceDims<N>;
     constexpr int P1 = D::P1, G = D::G, NG = D::NG;
-    const int le = threadIdx.x / N;
+    if (le < 0) le = threadIdx.x / N;
 #pragma unroll
     for (int v0 = 0; v0 < NG; v0 += N) {
         const int v = v0 + i;
@@ -110,12 +113,12 @@ __device__ __forceinline__ void face_gather(const FaceOp<T>& op, const VT* __res
 }
 
 // phase 2: w = C g with Ce the element's four G x G face blocks (column-major)
-template <int N, typename CTy, typename AT>
+template <int N, typename CTy, typename AT, int S>
 __device__ __forceinline__ void face_couple(const CTy* __restrict__ Ce, const int32_t* __restrict__ nbr, int e, int i,
-                                            FaceScratch<N, AT>& sc) {
+                                            FaceScratch<N, AT, S>& sc, int le = -1) {
     using D = FaceDims<N>;
     constexpr int G = D::G, NG = D::NG;
-    const int le = threadIdx.x / N;
+    if (le < 0) le = threadIdx.x / N;
 #pragma unroll
     for (int v0 = 0; v0 < NG; v0 += N) {
         const int v = v0 + i;
@@ -135,12 +138,13 @@ __device__ __forceinline__ void face_couple(const CTy* __restrict__ Ce, const in
 }
 
 // phase 3: y + (E_f^T w)_i
-template <int N, typename T, typename AT>
-__device__ __forceinline__ AT face_lift(const FaceOp<T>& op, int i, AT y, const FaceScratch<N, AT>& sc) {
+template <int N, typename T, typename AT, int S>
+__device__ __forceinline__ AT face_lift(const FaceOp<T>& op, int i, AT y, const FaceScratch<N, AT, S>& sc,
+                                        int le = -1) {
     using D = FaceDims<N>;
     constexpr int P1 = D::P1, G = D::G, NG = D::NG;
     constexpr int p = P1 - 1;
-    const int le = threadIdx.x / N;
+    if (le < 0) le = threadIdx.x / N;
     const int ix = i % P1, iy = i / P1;
     const AT* w = sc.w + le * NG;
     // (face, face position, line position) of this node for each face
@@ -174,12 +178,12 @@ __device__ __forceinline__ AT faceop_row(const FaceOp<T>& op, const VT* __restri
 #pragma unroll
             for (int j = 0; j < N; ++j) y += (AT)ld_hint(Ad + j * N, pol) * (AT)xe[j];
         }
-        face_gather<N, T, AT, VT>(op, x, e, i, sc);
+        face_gather<N>(op, x, e, i, sc);
     }
     __syncthreads();
-    if (act) face_couple<N, T, AT>(op.CT + (size_t)e * 4 * G * G, op.nbr, e, i, sc);
+    if (act) face_couple<N>(op.CT + (size_t)e * 4 * G * G, op.nbr, e, i, sc);
     __syncthreads();
-    if (act) y = face_lift<N, T, AT>(op, i, y, sc);
+    if (act) y = face_lift<N>(op, i, y, sc);
     return y;
 }
 

@@ -33,6 +33,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// rows per thread of the level-0 smoothing steps (see bj_smooth_kernel)
+constexpr int kSmoothRows = 2;
+
 // true when the CG has finished
 __device__ __forceinline__ bool mg_skip(const int* ctl) { return ((const volatile int*)ctl)[0] != 0; }
 
@@ -45,39 +48,73 @@ __device__ __forceinline__ bool mg_skip(const int* ctl) { return ((const volatil
 // Pinv is the inverse of the diagonal block A_d (formed in FP64), so
 // Pinv (b - A xin) = Pinv (b - A_off xin) - xin: the step reads the face
 // couplings and Pinv but not A_d, and uses z - xin with z = Pinv (b - A_off xin).
-template <typename OT, int N>
+// Thread (slot le, row i) of a block handles row i of the R elements
+// e0 + k EPB, k < R (e0 = blockIdx.x EPB R + le): with R = 2 the 16,384 x 25
+// rows of the bench workload fit the GPU's resident threads at once instead
+// of 1.35 waves, and each thread has R independent rows in flight.
+template <typename OT, int N, int R>
 __global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, FaceOp<float> A, const float* __restrict__ PinvT,
                                                         float c1, float c2, const double* __restrict__ b,
                                                         const float* __restrict__ xin, const float* xprev,
                                                         OT* xout, const int* ctl) {
     if (mg_skip(ctl)) return;
-    __shared__ float res[256];
-    __shared__ FaceScratch<N, float> sc;
+    constexpr int EPB = FaceDims<N>::EPB, G = FaceDims<N>::G;
+    __shared__ float res[R][256];
+    __shared__ FaceScratch<N, float, EPB * R> sc;
     const int le = threadIdx.x / N, i = threadIdx.x % N;
-    const int e = blockIdx.x * FaceDims<N>::EPB + le;
-    const bool act = e < ne;
-    float r = 0.0f, x = 0.0f;
-    if (xin) {
-        const float ax = faceop_row<N, float, float, float, false>(A, xin, e, i, act, sc);
-        if (act) {
-            x = xin[(size_t)e * N + i];
-            r = (float)b[(size_t)e * N + i] - ax;
-        }
-    } else if (act) {
-        r = (float)b[(size_t)e * N + i];
-    }
-    res[threadIdx.x] = r;
-    __syncthreads();
-    if (act) {
-        const float* P = PinvT + (size_t)e * N * N + i;
-        const float* re = res + le * N;
-        float z = 0.0f;
-        const unsigned long long pol = l2_keep();
+    const int e0 = blockIdx.x * EPB * R + le;
+    float r[R], x[R];
 #pragma unroll
-        for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
-        const size_t o = (size_t)e * N + i;
-        const float xp = xprev ? xprev[o] : 0.0f;
-        xout[o] = (OT)(x + c2 * (z - x) + c1 * (x - xp));
+    for (int k = 0; k < R; ++k) {
+        r[k] = 0.0f;
+        x[k] = 0.0f;
+    }
+    if (xin) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int e = e0 + k * EPB;
+            if (e < ne) face_gather<N>(A, xin, e, i, sc, le + k * EPB);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int e = e0 + k * EPB;
+            if (e < ne) face_couple<N>(A.CT + (size_t)e * 4 * G * G, A.nbr, e, i, sc, le + k * EPB);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int e = e0 + k * EPB;
+            if (e < ne) {
+                const float ax = face_lift<N>(A, i, 0.0f, sc, le + k * EPB);
+                x[k] = xin[(size_t)e * N + i];
+                r[k] = (float)b[(size_t)e * N + i] - ax;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int e = e0 + k * EPB;
+            if (e < ne) r[k] = (float)b[(size_t)e * N + i];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) res[k][threadIdx.x] = r[k];
+    __syncthreads();
+    const unsigned long long pol = l2_keep();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        if (e < ne) {
+            const float* P = PinvT + (size_t)e * N * N + i;
+            const float* re = res[k] + le * N;
+            float z = 0.0f;
+#pragma unroll
+            for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
+            const size_t o = (size_t)e * N + i;
+            const float xp = xprev ? xprev[o] : 0.0f;
+            xout[o] = (OT)(x[k] + c2 * (z - x[k]) + c1 * (x[k] - xp));
+        }
     }
 }
 
@@ -543,16 +580,17 @@ int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cuda
     int launches = 0;
     const int tpb = cg_threads_per_block(N);
     const int nblk0 = (m.ne + FaceDims<N>::EPB - 1) / FaceDims<N>::EPB;
+    const int nblkR = (m.ne + FaceDims<N>::EPB * kSmoothRows - 1) / (FaceDims<N>::EPB * kSmoothRows);
     float c1[4], c2[4];
     smoother_coeffs(m, c1, c2);
     // level 0 pre-smoothing from zero (FP32)
     SmoothState st{m.x0, nullptr, m.x0b};
-    bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[0], c2[0], r, nullptr, nullptr, st.cur,
+    bj_smooth_kernel<float, N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[0], c2[0], r, nullptr, nullptr, st.cur,
                                                      ctl);
     ++launches;
     for (int k = 1; k < m.nu0; ++k) {
         float* out = st.next();
-        bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev, out,
+        bj_smooth_kernel<float, N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev, out,
                                                          ctl);
         st.advance(out);
         ++launches;
@@ -567,11 +605,11 @@ int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cuda
     st.prev = nullptr;
     for (int k = 0; k < m.nu0; ++k) {
         if (k == m.nu0 - 1) {
-            bj_smooth_kernel<double, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev, z,
+            bj_smooth_kernel<double, N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev, z,
                                                               ctl);
         } else {
             float* out = st.next();
-            bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev,
+            bj_smooth_kernel<float, N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], r, st.cur, st.prev,
                                                              out, ctl);
             st.advance(out);
         }
@@ -593,6 +631,7 @@ template <int N>
 int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
     const int tpb = cg_threads_per_block(N);
     const int nblk0 = a.nblk;
+    const int nblkR = (m.ne + FaceDims<N>::EPB * kSmoothRows - 1) / (FaceDims<N>::EPB * kSmoothRows);
     float c1[4], c2[4];
     smoother_coeffs(m, c1, c2);
     SmoothState st{m.x0, nullptr, m.x0b};
@@ -600,7 +639,7 @@ int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
     int launches = 1;
     for (int k = 1; k < m.nu0; ++k) {
         float* out = st.next();
-        bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], a.r, st.cur, st.prev, out,
+        bj_smooth_kernel<float, N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], a.r, st.cur, st.prev, out,
                                                          a.ctl);
         st.advance(out);
         ++launches;
@@ -617,7 +656,7 @@ int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
             bj_last_dots_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.A, m.PinvT, c1[k], c2[k], st.cur, st.prev);
         } else {
             float* out = st.next();
-            bj_smooth_kernel<float, N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], a.r, st.cur, st.prev,
+            bj_smooth_kernel<float, N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], a.r, st.cur, st.prev,
                                                              out, a.ctl);
             st.advance(out);
         }
