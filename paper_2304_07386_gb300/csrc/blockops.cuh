@@ -379,17 +379,19 @@ __device__ __forceinline__ double sum_partials_cg(const double* part, int nblk, 
     return s;
 }
 
-// the three partial arrays part[0..nblk), part[nblk..2 nblk), part[2 nblk..3 nblk)
-// summed in one pass (six independent loads in flight per thread)
-__device__ __forceinline__ void sum3_partials_cg(const double* part, int nblk, double* sh, double& s0, double& s1,
-                                                 double& s2) {
+// the three partial arrays part[0..count), part[stride..stride + count),
+// part[2 stride..2 stride + count) summed in one pass (six independent loads
+// in flight per thread); stride < 0: stride = count
+__device__ __forceinline__ void sum3_partials_cg(const double* part, int count, double* sh, double& s0, double& s1,
+                                                 double& s2, int stride = -1) {
+    const int nblk = count;
+    const int st = stride < 0 ? count : stride;
     const int bd = blockDim.x;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0;
     int i = threadIdx.x;
     for (; i + bd < nblk; i += 2 * bd) {
-        const double a0 = __ldcg(part + i), a1 = __ldcg(part + nblk + i), a2 = __ldcg(part + 2 * nblk + i);
-        const double b0 = __ldcg(part + i + bd), b1 = __ldcg(part + nblk + i + bd),
-                     b2 = __ldcg(part + 2 * nblk + i + bd);
+        const double a0 = __ldcg(part + i), a1 = __ldcg(part + st + i), a2 = __ldcg(part + 2 * st + i);
+        const double b0 = __ldcg(part + i + bd), b1 = __ldcg(part + st + i + bd), b2 = __ldcg(part + 2 * st + i + bd);
         v0 += a0;
         v1 += a1;
         v2 += a2;
@@ -399,8 +401,8 @@ __device__ __forceinline__ void sum3_partials_cg(const double* part, int nblk, d
     }
     for (; i < nblk; i += bd) {
         v0 += __ldcg(part + i);
-        v1 += __ldcg(part + nblk + i);
-        v2 += __ldcg(part + 2 * nblk + i);
+        v1 += __ldcg(part + st + i);
+        v2 += __ldcg(part + 2 * st + i);
     }
     v0 += u0;
     v1 += u1;

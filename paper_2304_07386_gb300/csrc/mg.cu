@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, FaceOp<float> A,
 // elements at each vertex).  The coarse cycle runs next and chains dependent
 // loads through its levels' CSR data, which the operator product has pushed
 // out of L2: thread 0 of the first blocks prefetches those chunks (pf) into L2.
-template <int N>
+// R rows per thread as in bj_smooth_kernel.
+template <int N, int R>
 __global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> A, const double* __restrict__ b,
                                                           const float* __restrict__ x, const float* __restrict__ w4,
                                                           float* __restrict__ cres, const L2Chunk* __restrict__ pf,
@@ -131,59 +132,99 @@ __global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> 
     if (mg_skip(ctl)) return;
     if (threadIdx.x == 0)
         for (int c = blockIdx.x; c < npf; c += gridDim.x) prefetch_l2(pf[c].p, pf[c].bytes);
-    __shared__ FaceScratch<N, float> sc;
-    __shared__ float rs[256];
+    constexpr int EPB = FaceDims<N>::EPB, G = FaceDims<N>::G;
+    __shared__ FaceScratch<N, float, EPB * R> sc;
+    __shared__ float rs[R][256];
     const int le = threadIdx.x / N, i = threadIdx.x % N;
-    const int e = blockIdx.x * FaceDims<N>::EPB + le;
-    const bool act = e < ne;
-    const float ax = faceop_row<N, float, float, float>(A, x, e, i, act, sc);
-    rs[threadIdx.x] = act ? (float)b[(size_t)e * N + i] - ax : 0.0f;
-    __syncthreads();
-    if (act && i < 4) {
-        const float* re = rs + le * N;
-        float s = 0.0f;
+    const int e0 = blockIdx.x * EPB * R + le;
+    float y[R];
+    const unsigned long long pol = l2_keep();
 #pragma unroll
-        for (int j = 0; j < N; ++j) s = fmaf(w4[j * 4 + i], re[j], s);
-        cres[(size_t)e * 4 + i] = s;
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        y[k] = 0.0f;
+        if (e < ne) {
+            const float* Ad = A.AdT + (size_t)e * N * N + i;
+            const float* xe = x + (size_t)e * N;
+#pragma unroll
+            for (int j = 0; j < N; ++j) y[k] += ld_hint(Ad + j * N, pol) * xe[j];
+            face_gather<N>(A, x, e, i, sc, le + k * EPB);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        if (e < ne) face_couple<N>(A.CT + (size_t)e * 4 * G * G, A.nbr, e, i, sc, le + k * EPB);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        float rv = 0.0f;
+        if (e < ne) rv = (float)b[(size_t)e * N + i] - face_lift<N>(A, i, y[k], sc, le + k * EPB);
+        rs[k][threadIdx.x] = rv;
+    }
+    __syncthreads();
+    if (i < 4) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int e = e0 + k * EPB;
+            if (e < ne) {
+                const float* re = rs[k] + le * N;
+                float s = 0.0f;
+#pragma unroll
+                for (int j = 0; j < N; ++j) s = fmaf(w4[j * 4 + i], re[j], s);
+                cres[(size_t)e * 4 + i] = s;
+            }
+        }
     }
 }
 
 // First pre-smoothing step (from zero) of a flexible-CG iteration with the
 // CG update folded in: x += alpha p, r_old = r, r -= alpha q (alpha = rz / p.q
 // from the operator product's last block), partial r.r -> part[nblk + block];
-// xout = c2 Pinv r in FP32.  One block per EPB elements, as the product.
-template <int N>
+// xout = c2 Pinv r in FP32.  R rows per thread as in bj_smooth_kernel.
+template <int N, int R>
 __global__ void __launch_bounds__(256) bj_first_update_kernel(CGArgs a, const float* __restrict__ PinvT, float c2,
                                                               float* __restrict__ xout) {
     if (mg_skip(a.ctl)) return;
-    __shared__ float res[256];
+    constexpr int EPB = FaceDims<N>::EPB;
+    __shared__ float res[R][256];
     __shared__ double sh[40];
     const int le = threadIdx.x / N, i = threadIdx.x % N;
-    const int e = blockIdx.x * FaceDims<N>::EPB + le;
-    const bool act = e < a.ne;
+    const int e0 = blockIdx.x * EPB * R + le;
     const double alpha = a.scal[5];
     double rr = 0.0;
-    float r = 0.0f;
-    if (act) {
-        const size_t o = (size_t)e * N + i;
-        a.x[o] += alpha * a.p[o];
-        const double ro = a.r[o];
-        a.rold[o] = ro;
-        const double rn = ro - alpha * a.q[o];
-        a.r[o] = rn;
-        rr = rn * rn;
-        r = (float)rn;
-    }
-    res[threadIdx.x] = r;
-    __syncthreads();
-    if (act) {
-        const float* P = PinvT + (size_t)e * N * N + i;
-        const float* re = res + le * N;
-        float z = 0.0f;
-        const unsigned long long pol = l2_keep();
 #pragma unroll
-        for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
-        xout[(size_t)e * N + i] = c2 * z;
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        float r = 0.0f;
+        if (e < a.ne) {
+            const size_t o = (size_t)e * N + i;
+            a.x[o] += alpha * a.p[o];
+            const double ro = a.r[o];
+            a.rold[o] = ro;
+            const double rn = ro - alpha * a.q[o];
+            a.r[o] = rn;
+            rr += rn * rn;
+            r = (float)rn;
+        }
+        res[k][threadIdx.x] = r;
+    }
+    __syncthreads();
+    const unsigned long long pol = l2_keep();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        if (e < a.ne) {
+            const float* P = PinvT + (size_t)e * N * N + i;
+            const float* re = res[k] + le * N;
+            float z = 0.0f;
+#pragma unroll
+            for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
+            xout[(size_t)e * N + i] = c2 * z;
+        }
     }
     const double s = block_sum(rr, sh);
     if (threadIdx.x == 0) a.part[a.nblk + blockIdx.x] = s;
@@ -191,46 +232,70 @@ __global__ void __launch_bounds__(256) bj_first_update_kernel(CGArgs a, const fl
 
 // Last post-smoothing step of a flexible-CG iteration, z = x + c2 (Pinv
 // (r - A_off x) - x) + c1 (x - xprev) written in FP64 (xprev == nullptr:
-// zero), with the CG dot products folded in:
-// partials r.z -> part[2 nblk + block] and (r - r_old).z -> part[3 nblk +
-// block].  The last block reduces them with the first step's r.r partials:
-// beta = (r - r_old).z / rz_old, rz, rr, the iteration count and the
-// convergence test.
-template <int N>
+// zero), with the CG dot products folded in: partials r.z -> part[2 nblk +
+// block] and (r - r_old).z -> part[3 nblk + block].  The last block reduces
+// them with the first step's r.r partials (gridDim.x of each): beta =
+// (r - r_old).z / rz_old, rz, rr, the iteration count and the convergence
+// test.  R rows per thread as in bj_smooth_kernel; the first step has the same
+// grid, so the partial counts agree.
+template <int N, int R>
 __global__ void __launch_bounds__(256) bj_last_dots_kernel(CGArgs a, FaceOp<float> A, const float* __restrict__ PinvT,
                                                            float c1, float c2, const float* __restrict__ xin,
                                                            const float* __restrict__ xprev) {
     if (mg_skip(a.ctl)) return;
-    __shared__ float res[256];
-    __shared__ FaceScratch<N, float> sc;
+    constexpr int EPB = FaceDims<N>::EPB, G = FaceDims<N>::G;
+    __shared__ float res[R][256];
+    __shared__ FaceScratch<N, float, EPB * R> sc;
     __shared__ double sh[40];
     const int le = threadIdx.x / N, i = threadIdx.x % N;
-    const int e = blockIdx.x * FaceDims<N>::EPB + le;
-    const bool act = e < a.ne;
-    const float ax = faceop_row<N, float, float, float, false>(A, xin, e, i, act, sc);
-    float x = 0.0f, r = 0.0f;
-    double rd = 0.0;
-    if (act) {
-        x = xin[(size_t)e * N + i];
-        rd = a.r[(size_t)e * N + i];
-        r = (float)rd - ax;
+    const int e0 = blockIdx.x * EPB * R + le;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        if (e < a.ne) face_gather<N>(A, xin, e, i, sc, le + k * EPB);
     }
-    res[threadIdx.x] = r;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        if (e < a.ne) face_couple<N>(A.CT + (size_t)e * 4 * G * G, A.nbr, e, i, sc, le + k * EPB);
+    }
+    __syncthreads();
+    float x[R];
+    double rd[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        float r = 0.0f;
+        x[k] = 0.0f;
+        rd[k] = 0.0;
+        if (e < a.ne) {
+            const float ax = face_lift<N>(A, i, 0.0f, sc, le + k * EPB);
+            x[k] = xin[(size_t)e * N + i];
+            rd[k] = a.r[(size_t)e * N + i];
+            r = (float)rd[k] - ax;
+        }
+        res[k][threadIdx.x] = r;
+    }
     __syncthreads();
     double rz = 0.0, dz = 0.0;
-    if (act) {
-        const float* P = PinvT + (size_t)e * N * N + i;
-        const float* re = res + le * N;
-        float z = 0.0f;
-        const unsigned long long pol = l2_keep();
+    const unsigned long long pol = l2_keep();
 #pragma unroll
-        for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
-        const size_t o = (size_t)e * N + i;
-        const float xp = xprev ? xprev[o] : 0.0f;
-        const double zd = (double)(x + c2 * (z - x) + c1 * (x - xp));
-        a.z[o] = zd;
-        rz = rd * zd;
-        dz = (rd - a.rold[o]) * zd;
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        if (e < a.ne) {
+            const float* P = PinvT + (size_t)e * N * N + i;
+            const float* re = res[k] + le * N;
+            float z = 0.0f;
+#pragma unroll
+            for (int j = 0; j < N; ++j) z = fmaf(ld_hint(P + j * N, pol), re[j], z);
+            const size_t o = (size_t)e * N + i;
+            const float xp = xprev ? xprev[o] : 0.0f;
+            const double zd = (double)(x[k] + c2 * (z - x[k]) + c1 * (x[k] - xp));
+            a.z[o] = zd;
+            rz += rd[k] * zd;
+            dz += (rd[k] - a.rold[o]) * zd;
+        }
     }
     const double s1 = block_sum(rz, sh);
     const double s2 = block_sum(dz, sh);
@@ -240,7 +305,7 @@ __global__ void __launch_bounds__(256) bj_last_dots_kernel(CGArgs a, FaceOp<floa
     }
     if (last_block((unsigned*)(a.ctl + 6))) {
         double rr, rz_new, dz_all;
-        sum3_partials_cg(a.part + a.nblk, a.nblk, sh, rr, rz_new, dz_all);
+        sum3_partials_cg(a.part + a.nblk, gridDim.x, sh, rr, rz_new, dz_all, a.nblk);
         if (threadIdx.x == 0) {
             a.scal[6] = dz_all / a.scal[0];
             a.scal[0] = rz_new;
@@ -579,7 +644,6 @@ template <int N>
 int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s) {
     int launches = 0;
     const int tpb = cg_threads_per_block(N);
-    const int nblk0 = (m.ne + FaceDims<N>::EPB - 1) / FaceDims<N>::EPB;
     const int nblkR = (m.ne + FaceDims<N>::EPB * kSmoothRows - 1) / (FaceDims<N>::EPB * kSmoothRows);
     float c1[4], c2[4];
     smoother_coeffs(m, c1, c2);
@@ -595,7 +659,8 @@ int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cuda
         st.advance(out);
         ++launches;
     }
-    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, r, st.cur, m.w4, m.res0, m.coarse_pf, m.coarse_npf, ctl);
+    bj_residual_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, r, st.cur, m.w4, m.res0, m.coarse_pf,
+                                                           m.coarse_npf, ctl);
     // vertex and aggregation levels and the coarsest solve (one cluster launch)
     const float* coarse_out = launch_coarse_cycle(m, m.res0, ctl, s);
     const int rows0 = m.ne * N;
@@ -630,12 +695,11 @@ template int mg_apply_n<25>(const MGPlan&, const double*, double*, const int*, c
 template <int N>
 int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
     const int tpb = cg_threads_per_block(N);
-    const int nblk0 = a.nblk;
     const int nblkR = (m.ne + FaceDims<N>::EPB * kSmoothRows - 1) / (FaceDims<N>::EPB * kSmoothRows);
     float c1[4], c2[4];
     smoother_coeffs(m, c1, c2);
     SmoothState st{m.x0, nullptr, m.x0b};
-    bj_first_update_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.PinvT, c2[0], st.cur);
+    bj_first_update_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(a, m.PinvT, c2[0], st.cur);
     int launches = 1;
     for (int k = 1; k < m.nu0; ++k) {
         float* out = st.next();
@@ -644,8 +708,8 @@ int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
         st.advance(out);
         ++launches;
     }
-    bj_residual_kernel<N><<<nblk0, tpb, 0, s>>>(m.ne, m.A, a.r, st.cur, m.w4, m.res0, m.coarse_pf, m.coarse_npf,
-                                                a.ctl);
+    bj_residual_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, a.r, st.cur, m.w4, m.res0, m.coarse_pf,
+                                                           m.coarse_npf, a.ctl);
     const float* coarse_out = launch_coarse_cycle(m, m.res0, a.ctl, s);
     const int rows0 = m.ne * N;
     prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, st.cur, a.ctl);
@@ -653,7 +717,7 @@ int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
     st.prev = nullptr;
     for (int k = 0; k < m.nu0; ++k) {
         if (k == m.nu0 - 1) {
-            bj_last_dots_kernel<N><<<nblk0, tpb, 0, s>>>(a, m.A, m.PinvT, c1[k], c2[k], st.cur, st.prev);
+            bj_last_dots_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(a, m.A, m.PinvT, c1[k], c2[k], st.cur, st.prev);
         } else {
             float* out = st.next();
             bj_smooth_kernel<float, N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.PinvT, c1[k], c2[k], a.r, st.cur, st.prev,
