@@ -187,20 +187,20 @@ __device__ __forceinline__ AT faceop_row(const FaceOp<T>& op, const VT* __restri
     return y;
 }
 
-template <int N>
+template <int N, int S = FaceDims<N>::EPB>
 struct FaceScratchDF {
-    float2 g[FaceDims<N>::EPB * FaceDims<N>::NG];
-    float2 w[FaceDims<N>::EPB * FaceDims<N>::NG];
+    float2 g[S * FaceDims<N>::NG];
+    float2 w[S * FaceDims<N>::NG];
 };
 
 // the three phases with the operator and x as FP32 pairs, pair arithmetic
 // throughout (see dfloat.cuh)
-template <int N>
+template <int N, int S>
 __device__ __forceinline__ void face_gather_df(const FaceOpDF& op, const float2* __restrict__ x, int e, int i,
-                                               FaceScratchDF<N>& sc) {
+                                               FaceScratchDF<N, S>& sc, int le = -1) {
     using D = FaceDims<N>;
     constexpr int P1 = D::P1, G = D::G, NG = D::NG;
-    const int le = threadIdx.x / N;
+    if (le < 0) le = threadIdx.x / N;
 #pragma unroll
     for (int v0 = 0; v0 < NG; v0 += N) {
         const int v = v0 + i;
@@ -230,12 +230,12 @@ __device__ __forceinline__ void face_gather_df(const FaceOpDF& op, const float2*
     }
 }
 
-template <int N>
+template <int N, int S>
 __device__ __forceinline__ void face_couple_df(const float2* __restrict__ Ce, const int32_t* __restrict__ nbr, int e,
-                                               int i, FaceScratchDF<N>& sc) {
+                                               int i, FaceScratchDF<N, S>& sc, int le = -1) {
     using D = FaceDims<N>;
     constexpr int G = D::G, NG = D::NG;
-    const int le = threadIdx.x / N;
+    if (le < 0) le = threadIdx.x / N;
 #pragma unroll
     for (int v0 = 0; v0 < NG; v0 += N) {
         const int v = v0 + i;
@@ -270,13 +270,13 @@ __device__ __forceinline__ void diag_row_df(const float2* __restrict__ Ad, const
 }
 
 // phase 3 added to the pair sum (ys, yc); the row value in FP64
-template <int N>
+template <int N, int S>
 __device__ __forceinline__ double face_lift_df(const FaceOpDF& op, int i, float ys, float yc,
-                                               const FaceScratchDF<N>& sc) {
+                                               const FaceScratchDF<N, S>& sc, int le = -1) {
     using D = FaceDims<N>;
     constexpr int P1 = D::P1, G = D::G, NG = D::NG;
     constexpr int p = P1 - 1;
-    const int le = threadIdx.x / N;
+    if (le < 0) le = threadIdx.x / N;
     const int ix = i % P1, iy = i / P1;
     const float2* w = sc.w + le * NG;
     const int fa[4] = {ix, iy, ix, iy};
@@ -295,24 +295,6 @@ __device__ __forceinline__ double face_lift_df(const FaceOpDF& op, int i, float 
         }
     }
     return df_to_double(ys, yc);
-}
-
-// faceop_row in pair arithmetic; the row value is returned in FP64
-template <int N>
-__device__ __forceinline__ double faceop_row_df(const FaceOpDF& op, const float2* __restrict__ x, int e, int i,
-                                                bool act, FaceScratchDF<N>& sc) {
-    constexpr int G = FaceDims<N>::G;
-    float ys = 0.0f, yc = 0.0f;
-    if (act) {
-        diag_row_df<N>(op.AdT + (size_t)e * N * N + i, x + (size_t)e * N, ys, yc);
-        face_gather_df<N>(op, x, e, i, sc);
-    }
-    __syncthreads();
-    if (act) face_couple_df<N>(op.CT + (size_t)e * 4 * G * G, op.nbr, e, i, sc);
-    __syncthreads();
-    double y = 0.0;
-    if (act) y = face_lift_df<N>(op, i, ys, yc, sc);
-    return y;
 }
 
 // (A v)_i with dense column-major neighbour blocks (runtime n)

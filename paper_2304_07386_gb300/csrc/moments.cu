@@ -483,24 +483,50 @@ __global__ void cgx_init_p_kernel(CGArgs a) {
 }
 
 // q = A p (FP32-pair arithmetic, FP64 result) ; partial p.q -> part[block];
-// the last block reduces the partials: p.q -> scal[1], alpha = rz / p.q -> scal[5]
-template <int N>
+// the last block reduces the gridDim.x partials: p.q -> scal[1], alpha =
+// rz / p.q -> scal[5].  Thread (slot le, row i) handles row i of the R
+// elements e0 + k EPB, k < R (e0 = blockIdx.x EPB R + le), as the level-0
+// multigrid kernels do.
+template <int N, int R>
 __global__ void __launch_bounds__(256) cgx_spmv_kernel(CGArgs a) {
     if (*(volatile int*)a.ctl) return;
+    constexpr int EPB = FaceDims<N>::EPB, G = FaceDims<N>::G;
     __shared__ double sh[40];
-    __shared__ FaceScratchDF<N> sc;
-    const int epb = blockDim.x / N;
-    const int e = blockIdx.x * epb + threadIdx.x / N, i = threadIdx.x % N;
-    const double qv = faceop_row_df<N>(a.A2, a.p2, e, i, e < a.ne, sc);
+    __shared__ FaceScratchDF<N, EPB * R> sc;
+    const int le = threadIdx.x / N, i = threadIdx.x % N;
+    const int e0 = blockIdx.x * EPB * R + le;
+    float ys[R], yc[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        ys[k] = 0.0f;
+        yc[k] = 0.0f;
+        if (e < a.ne) {
+            diag_row_df<N>(a.A2.AdT + (size_t)e * N * N + i, a.p2 + (size_t)e * N, ys[k], yc[k]);
+            face_gather_df<N>(a.A2, a.p2, e, i, sc, le + k * EPB);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        if (e < a.ne) face_couple_df<N>(a.A2.CT + (size_t)e * 4 * G * G, a.A2.nbr, e, i, sc, le + k * EPB);
+    }
+    __syncthreads();
     double pq = 0.0;
-    if (e < a.ne) {
-        a.q[(size_t)e * N + i] = qv;
-        pq = qv * a.p[(size_t)e * N + i];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int e = e0 + k * EPB;
+        if (e < a.ne) {
+            const double qv = face_lift_df<N>(a.A2, i, ys[k], yc[k], sc, le + k * EPB);
+            a.q[(size_t)e * N + i] = qv;
+            pq += qv * a.p[(size_t)e * N + i];
+        }
     }
     double s = block_sum(pq, sh);
     if (threadIdx.x == 0) a.part[blockIdx.x] = s;
     if (last_block((unsigned*)(a.ctl + 7))) {
-        const double pq_all = sum_partials_cg(a.part, a.nblk, sh);
+        const double pq_all = sum_partials_cg(a.part, gridDim.x, sh);
         if (threadIdx.x == 0) {
             a.scal[1] = pq_all;
             a.scal[5] = a.scal[0] / pq_all;
@@ -657,7 +683,14 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
     for (int k = 0; k < count; ++k) {
         // q = A p and alpha; V-cycle with the update (x, r) and the dots (beta,
         // convergence) folded into its first and last level-0 steps; p = z + beta p
-        SMM_DISPATCH_N(a.n, cgx_spmv_kernel, a.nblk, tpb, 0, s)
+        constexpr int R = 2;   // rows per thread
+        const int epb = tpb / a.n, nblkR = (a.ne + epb * R - 1) / (epb * R);
+        switch (a.n) {
+            case 4: cgx_spmv_kernel<4, R><<<nblkR, tpb, 0, s>>>(a); break;
+            case 9: cgx_spmv_kernel<9, R><<<nblkR, tpb, 0, s>>>(a); break;
+            case 16: cgx_spmv_kernel<16, R><<<nblkR, tpb, 0, s>>>(a); break;
+            default: cgx_spmv_kernel<25, R><<<nblkR, tpb, 0, s>>>(a); break;
+        }
         launches += 1 + mg_cg_iteration(mg, a, s);
         cgx_direction_kernel<<<a.nvblk, 256, 0, s>>>(a);
         launches += 1;
