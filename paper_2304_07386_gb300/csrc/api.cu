@@ -295,7 +295,9 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     ok &= upload(h, h->Fx, s.Fx) && upload(h, h->Fy, s.Fy);
     ok &= upload(h, h->src, s.src) && upload(h, h->inflow, s.inflow);
     ok &= upload(h, h->L1, s.L1) && upload(h, h->b_nhat, s.b_nhat) && upload(h, h->b_ds, s.b_ds) && upload(h, h->b_eb0, s.b_eb0);
-    ok &= upload(h, h->Kxx, s.Kxx) && upload(h, h->Ks, s.Ks) && upload(h, h->Kyy, s.Kyy);
+    // column-major (transposed) blocks, so that the n threads of an element read contiguous entries
+    ok &= upload(h, h->Kxx, transpose_blocks(s.Kxx, s.n)) && upload(h, h->Ks, transpose_blocks(s.Ks, s.n)) &&
+          upload(h, h->Kyy, transpose_blocks(s.Kyy, s.n));
     ok &= upload(h, h->Dfx, s.Dfx) && upload(h, h->Dfy, s.Dfy) && upload(h, h->nds, s.nds) && upload(h, h->bfixed, s.bfixed);
     if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
     if (o.negative_flux_fixup) {

@@ -136,9 +136,10 @@ __global__ void rhs_assemble_kernel(int ne, int n, int p, int nfq, const double*
     const double* txx = mom + 3 * st + (size_t)e * n;
     const double* txy = mom + 4 * st + (size_t)e * n;
     const double* tyy = mom + 5 * st + (size_t)e * n;
-    const size_t mo = ((size_t)e * n + i) * n;
+    const size_t mo = (size_t)e * n * n + i;  // blocks stored column-major: entry (i, j) at [e][j][i]
     double acc = bfixed[t];
-    for (int j = 0; j < n; ++j) acc += Kxx[mo + j] * txx[j] + Ks[mo + j] * txy[j] + Kyy[mo + j] * tyy[j];
+    for (int j = 0; j < n; ++j)
+        acc += Kxx[mo + (size_t)j * n] * txx[j] + Ks[mo + (size_t)j * n] * txy[j] + Kyy[mo + (size_t)j * n] * tyy[j];
     const int p1 = p + 1, ix = i % p1, iy = i / p1;
     const double hs = 0.5 / sigma_t[e];
     for (int f = 0; f < 4; ++f) {
