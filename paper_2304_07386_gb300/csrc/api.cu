@@ -85,6 +85,7 @@ struct smm_ctx {
     // closures / rhs data
     double *L1 = nullptr, *b_nhat = nullptr, *b_ds = nullptr, *b_eb0 = nullptr;
     double *Kxx = nullptr, *Ks = nullptr, *Kyy = nullptr, *Dfx = nullptr, *Dfy = nullptr, *nds = nullptr;
+    double *DfxT = nullptr, *DfyT = nullptr;   // the face gradient operators with the face point index fastest
     double *bfixed = nullptr, *trace = nullptr, *rhs = nullptr;
     // moment operator and CG
     double *AdT = nullptr, *CT = nullptr, *PinvT = nullptr;   // diagonal blocks, face couplings, inverses
@@ -299,6 +300,19 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     ok &= upload(h, h->Kxx, transpose_blocks(s.Kxx, s.n)) && upload(h, h->Ks, transpose_blocks(s.Ks, s.n)) &&
           upload(h, h->Kyy, transpose_blocks(s.Kyy, s.n));
     ok &= upload(h, h->Dfx, s.Dfx) && upload(h, h->Dfy, s.Dfy) && upload(h, h->nds, s.nds) && upload(h, h->bfixed, s.bfixed);
+    {
+        // [element][face][node][point] copies for the trace kernel, whose threads are face points
+        const int nq = s.nfq, nn = s.n;
+        const size_t nb = (size_t)s.ne * 4;
+        std::vector<double> tx(s.Dfx.size()), ty(s.Dfy.size());
+        for (size_t b = 0; b < nb; ++b)
+            for (int q = 0; q < nq; ++q)
+                for (int j = 0; j < nn; ++j) {
+                    tx[(b * nn + j) * nq + q] = s.Dfx[(b * nq + q) * nn + j];
+                    ty[(b * nn + j) * nq + q] = s.Dfy[(b * nq + q) * nn + j];
+                }
+        ok &= upload(h, h->DfxT, tx) && upload(h, h->DfyT, ty);
+    }
     if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
     if (o.negative_flux_fixup) {
         const size_t nn = (size_t)s.n * s.n;
@@ -761,7 +775,8 @@ smm_status enqueue_moments(smm_handle h) {
 }
 
 smm_status enqueue_rhs(smm_handle h) {
-    smm::launch_rhs(h->ne, h->n, h->p, h->nfq, h->mom, h->beta, h->bfixed, h->Kxx, h->Ks, h->Kyy, h->Dfx, h->Dfy, h->nds,
+    smm::launch_rhs(h->ne, h->n, h->p, h->nfq, h->mom, h->beta, h->bfixed, h->Kxx, h->Ks, h->Kyy, h->Dfx, h->Dfy,
+                    h->DfxT, h->DfyT, h->nds,
                     h->L1, h->sigma_t, h->nbr, h->nbr_face, h->nbr_flip, h->bface_id, h->b_ds, h->trace, h->rhs,
                     h->stream);
     h->launches += 2;

@@ -125,7 +125,8 @@ void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_ele
                  const double* eb0, const double* psi, const double* mom, double* beta, cudaStream_t s);
 void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
                 const double* Kxx, const double* Ks, const double* Kyy, const double* Dfx, const double* Dfy,
-                const double* nds, const double* L1, const double* sigma_t, const int32_t* nbr,
+                const double* DfxT, const double* DfyT, const double* nds, const double* L1, const double* sigma_t,
+                const int32_t* nbr,
                 const int32_t* nbr_face, const int32_t* nbr_flip, const int32_t* bface_id, const double* b_ds,
                 double* trace, double* rhs, cudaStream_t s);
 

@@ -84,7 +84,7 @@ __global__ void beta_kernel(int nb, int nd, int n, int p, int nfq, const int32_t
 // Face traces of the correction tensor per (element, face, Gauss point):
 // g = (div T . n ds)/sigma_t, and T n ds (2 components).
 __global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, const double* __restrict__ mom,
-                                 const double* __restrict__ Dfx, const double* __restrict__ Dfy,
+                                 const double* __restrict__ DfxT, const double* __restrict__ DfyT,
                                  const double* __restrict__ nds, const double* __restrict__ L1,
                                  const double* __restrict__ sigma_t, double* __restrict__ tr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,12 +94,16 @@ __global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, const double* __
     const double* txx = mom + 3 * st + (size_t)e * n;
     const double* txy = mom + 4 * st + (size_t)e * n;
     const double* tyy = mom + 5 * st + (size_t)e * n;
-    const double* dx = Dfx + (size_t)t * n;
-    const double* dy = Dfy + (size_t)t * n;
+    // the face gradient operators as [element][face][node][point]: the threads of one face read
+    // consecutive words
+    const size_t fb = ((size_t)e * 4 + f) * n * nfq + q;
+    const double* dx = DfxT + fb;
+    const double* dy = DfyT + fb;
     double divx = 0.0, divy = 0.0;
     for (int j = 0; j < n; ++j) {
-        divx += dx[j] * txx[j] + dy[j] * txy[j];
-        divy += dx[j] * txy[j] + dy[j] * tyy[j];
+        const double ax = dx[(size_t)j * nfq], ay = dy[(size_t)j * nfq];
+        divx += ax * txx[j] + ay * txy[j];
+        divy += ax * txy[j] + ay * tyy[j];
     }
     const int p1 = p + 1;
     double vxx = 0, vxy = 0, vyy = 0;
@@ -218,11 +222,11 @@ void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_ele
 
 void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
                 const double* Kxx, const double* Ks, const double* Kyy, const double* Dfx, const double* Dfy,
-                const double* nds, const double* L1, const double* sigma_t, const int32_t* nbr, const int32_t* nbr_face,
+                const double* DfxT, const double* DfyT, const double* nds, const double* L1, const double* sigma_t, const int32_t* nbr, const int32_t* nbr_face,
                 const int32_t* nbr_flip, const int32_t* bface_id, const double* b_ds, double* trace, double* rhs,
                 cudaStream_t s) {
     const int t1 = ne * 4 * nfq;
-    rhs_trace_kernel<<<(t1 + 255) / 256, 256, 0, s>>>(ne, n, p, nfq, mom, Dfx, Dfy, nds, L1, sigma_t, trace);
+    rhs_trace_kernel<<<(t1 + 255) / 256, 256, 0, s>>>(ne, n, p, nfq, mom, DfxT, DfyT, nds, L1, sigma_t, trace);
     const int t2 = ne * n;
     rhs_assemble_kernel<<<(t2 + 255) / 256, 256, 0, s>>>(ne, n, p, nfq, mom, beta, bfixed, Kxx, Ks, Kyy, Dfx, Dfy, L1,
                                                          sigma_t, nbr, nbr_face, nbr_flip, bface_id, b_ds, trace, rhs);
