@@ -60,25 +60,32 @@ __global__ void beta_kernel(int nb, int nd, int n, int p, int nfq, const int32_t
                             const double* __restrict__ ox, const double* __restrict__ oy, const double* __restrict__ L1,
                             const double* __restrict__ nhat, const double* __restrict__ eb0,
                             const double* __restrict__ psi, const double* __restrict__ mom, double* __restrict__ beta) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per (boundary face, Gauss point); the lanes take the ordinates
+    // and the sum over them is a fixed-order warp reduction
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (t >= nb * nfq) return;
     const int b = t / nfq, q = t - b * nfq;
     const int e = bface_elem[b], f = bface_face[b];
     const int p1 = p + 1;
-    int node[8];
-    for (int a = 0; a < p1; ++a)
-        node[a] = f == 0 ? a : (f == 1 ? a * p1 + p : (f == 2 ? p * p1 + a : a * p1));
+    // face node a of face f is base + a * stride
+    const int base = f == 1 ? p : (f == 2 ? p * p1 : 0);
+    const int stride = (f == 0 || f == 2) ? 1 : p1;
+    const double* Lq = L1 + q * p1;
     const double nx = nhat[2 * t], ny = nhat[2 * t + 1];
     double B = 0.0;
-    for (int d = 0; d < nd; ++d) {
-        const double* ps = psi + ((size_t)e * nd + d) * n;
+    for (int d = lane; d < nd; d += 32) {
+        const double* ps = psi + ((size_t)e * nd + d) * n + base;
         double v = 0.0;
-        for (int a = 0; a < p1; ++a) v += L1[q * p1 + a] * __ldcg(ps + node[a]);
+        for (int a = 0; a < p1; ++a) v += Lq[a] * __ldcg(ps + a * stride);
         B += w[d] * fabs(ox[d] * nx + oy[d] * ny) * v;
     }
-    double phi = 0.0;
-    for (int a = 0; a < p1; ++a) phi += L1[q * p1 + a] * mom[(size_t)e * n + node[a]];
-    beta[t] = B - eb0[t] * phi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) B += __shfl_xor_sync(0xffffffffu, B, o);
+    if (lane == 0) {
+        double phi = 0.0;
+        for (int a = 0; a < p1; ++a) phi += Lq[a] * mom[(size_t)e * n + base + a * stride];
+        beta[t] = B - eb0[t] * phi;
+    }
 }
 
 // Face traces of the correction tensor per (element, face, Gauss point):
@@ -216,8 +223,8 @@ void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_ele
                  const double* eb0, const double* psi, const double* mom, double* beta, cudaStream_t s) {
     const int tot = nb * nfq;
     if (tot == 0) return;
-    beta_kernel<<<(tot + 127) / 128, 128, 0, s>>>(nb, nd, n, p, nfq, bface_elem, bface_face, w, ox, oy, L1, nhat, eb0,
-                                                  psi, mom, beta);
+    beta_kernel<<<(tot + 7) / 8, 256, 0, s>>>(nb, nd, n, p, nfq, bface_elem, bface_face, w, ox, oy, L1, nhat, eb0, psi,
+                                              mom, beta);
 }
 
 void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
