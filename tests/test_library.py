@@ -48,3 +48,45 @@ def test_invalid_arguments_rejected(lib):
     from paper_2304_07386_gb300 import SMMError, smm_quadrature
     with pytest.raises(SMMError):
         smm_quadrature(5)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The Python mirror of every struct in include/smm.h has the header's size
+    and field offsets (a C program compiled against the header prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2304_07386_gb300 import smm as S
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [S.smm_mesh, S.smm_options, S.smm_info, S.smm_stats]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "smm.h"', "int main(void) {"]
+    for st in structs:
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (st.__name__, st.__name__))
+        for name, _ in st._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (st.__name__, name, st.__name__, name))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        assert got[(st.__name__, "sizeof")] == ctypes.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert got[(st.__name__, name)] == getattr(st, name).offset, (st.__name__, name)
+
+
+def test_default_options(lib):
+    """The defaults the header documents: FP64 sweep with cached inverses,
+    multigrid CG with degree-3 Chebyshev smoothing run as one device-side loop."""
+    from paper_2304_07386_gb300 import smm as S
+    from paper_2304_07386_gb300 import smm_default_options
+    o = smm_default_options()
+    assert o.sweep_precision == S.SMM_SWEEP_FP64 and o.sweep_solver == S.SMM_SOLVER_CACHED_INVERSE
+    assert o.precond == S.SMM_PRECOND_MULTIGRID
+    assert o.mg_smoother == S.SMM_SMOOTHER_CHEBYSHEV and o.mg_smooth_steps == 3
+    assert o.cg_device_loop == 1 and o.sweep_tiles == 1 and o.negative_flux_fixup == 0
+    assert o.moment_discretization == S.SMM_MOMENT_IP
