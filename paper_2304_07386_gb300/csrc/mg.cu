@@ -1,17 +1,19 @@
 // Multigrid V-cycle preconditioner for the IP-SMM moment operator.
 //
-// Level 0: DG-p element blocks, nu0 steps of damped element-block Jacobi
-// before and after the coarse correction, in FP32 (the preconditioner only
-// has to approximate the inverse; FP64 arithmetic on these blocks is bound by
-// the GPU's FP64 rate, FP32 by HBM).  The CG around it is flexible, so the
-// rounding of the FP32 cycle does not break its recurrences.  Level 1: continuous bilinear
-// functions on the mesh vertices (restriction gathers the four corner
-// weights of every element node, prolongation interpolates them back).
-// Levels 2..: smoothed-aggregation CSR operators with one damped Jacobi
-// step before and after; the coarsest level is a dense inverse.  Levels >= 1
-// are stored and applied in FP32 and run as one cluster launch.  The cycle
-// is symmetric, so it is a valid CG preconditioner.  Every kernel returns at
-// once when the CG control word says the solve has finished.
+// Level 0: DG-p element blocks, nu0 smoothing steps before and after the
+// coarse correction -- the degree-nu0 Chebyshev polynomial in Pinv A (Pinv
+// the element-block inverses) or damped element-block Jacobi -- in FP32 (the
+// preconditioner only has to approximate the inverse; FP64 arithmetic on these
+// blocks is bound by the GPU's FP64 rate, FP32 by HBM).  The CG around it is
+// flexible, so the rounding of the FP32 cycle does not break its recurrences.
+// Level 1: continuous bilinear functions on the mesh vertices (restriction
+// gathers the four corner weights of every element node, prolongation
+// interpolates them back).  Levels 2..: smoothed-aggregation operators with
+// one damped Jacobi step before and after; the coarsest level is a dense
+// inverse.  Levels >= 1 are stored (k-major ELL) and applied in FP32 and run
+// as one cluster launch.  The same smoothing polynomial before and after keeps
+// the cycle symmetric.  Every kernel returns at once when the CG control word
+// says the solve has finished.
 #include <algorithm>
 
 #include <cooperative_groups.h>
