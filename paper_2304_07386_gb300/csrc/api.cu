@@ -429,11 +429,26 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         P.ne = s.ne; P.n = s.n; P.nu0 = o.mg_smooth_steps; P.omega0 = H.omega0;
         P.chebyshev = o.mg_smoother == SMM_SMOOTHER_CHEBYSHEV;
         if (!cgm) {
-            float *ad32 = nullptr, *c32 = nullptr, *pi32 = nullptr;
-            ok &= upload_f32(h, ad32, transpose_blocks(s.Adiag, s.n));
+            float *c32 = nullptr, *pi32 = nullptr, *wd32 = nullptr;
             ok &= upload_f32(h, c32, transpose_blocks(s.Cface, 2 * s.p1));
             ok &= upload_f32(h, pi32, transpose_blocks(s.Pinv, s.n));
-            P.A.AdT = ad32; P.A.CT = c32; P.PinvT = pi32;
+            // the level-0 residual is needed only as its element-corner sums w4^T (b - A x), so the
+            // diagonal blocks enter as W = w4^T A_d, [element][node][corner]
+            {
+                const int n = s.n;
+                std::vector<double> wt((size_t)s.ne * n * 4, 0.0);
+#pragma omp parallel for schedule(static)
+                for (int e = 0; e < s.ne; ++e)
+                    for (int j = 0; j < n; ++j)
+                        for (int c = 0; c < 4; ++c) {
+                            double acc = 0.0;
+                            for (int i = 0; i < n; ++i)
+                                acc += H.w4[(size_t)i * 4 + c] * s.Adiag[((size_t)e * n + i) * n + j];
+                            wt[((size_t)e * n + j) * 4 + c] = acc;
+                        }
+                ok &= upload_f32(h, wd32, wt);
+            }
+            P.A.AdT = nullptr; P.A.CT = c32; P.PinvT = pi32; P.WdT = wd32;
             P.A.nbr = h->nbr; P.A.nface = h->nbr_face;
             for (int k = 0; k < s.p1; ++k) P.A.wd[k] = (float)s.wd[k];
         }

@@ -208,6 +208,7 @@ struct MGPlan {
     bool chebyshev = false;                       // level-0 smoother: Chebyshev polynomial of degree nu0
     FaceOp<float> A;                              // FP32 copy of the operator
     const float* PinvT = nullptr;                 // FP32 block-Jacobi inverses
+    const float* WdT = nullptr;                   // [ne][n][4]: w4^T A_d, the diagonal blocks' part of the corner sums
     float* x0 = nullptr; float* x0b = nullptr;   // [ne*n], level 0 works in FP32
     float* res0 = nullptr;                        // [ne][4] element-corner sums of the level-0 residual
     int nvert = 0;

@@ -122,15 +122,18 @@ __global__ void __launch_bounds__(256) bj_smooth_kernel(int ne, FaceOp<float> A,
 
 // Level-0 residual res = b - A x (FP32) restricted to the element corners:
 // cres[e][c] = sum_i w4[i][c] res[e][i] (the vertex level sums these over the
-// elements at each vertex).  The coarse cycle runs next and chains dependent
-// loads through its levels' CSR data, which the operator product has pushed
-// out of L2: thread 0 of the first blocks prefetches those chunks (pf) into L2.
-// R rows per thread as in bj_smooth_kernel.
+// elements at each vertex).  Only these sums are needed, so the diagonal
+// blocks enter through W = w4^T A_d (WdT [e][j][c], 4 n words per element):
+// cres[e][c] = sum_i w4[i][c] (b - A_off x)_i - sum_j W[c][j] x_j.  The
+// coarse cycle runs next and chains dependent loads through its levels' data,
+// which the operator product has pushed out of L2: thread 0 of the first
+// blocks prefetches those chunks (pf) into L2.  R rows per thread as in
+// bj_smooth_kernel.
 template <int N, int R>
-__global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> A, const double* __restrict__ b,
-                                                          const float* __restrict__ x, const float* __restrict__ w4,
-                                                          float* __restrict__ cres, const L2Chunk* __restrict__ pf,
-                                                          int npf, const int* ctl) {
+__global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> A, const float* __restrict__ WdT,
+                                                          const double* __restrict__ b, const float* __restrict__ x,
+                                                          const float* __restrict__ w4, float* __restrict__ cres,
+                                                          const L2Chunk* __restrict__ pf, int npf, const int* ctl) {
     if (mg_skip(ctl)) return;
     if (threadIdx.x == 0)
         for (int c = blockIdx.x; c < npf; c += gridDim.x) prefetch_l2(pf[c].p, pf[c].bytes);
@@ -139,19 +142,10 @@ __global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> 
     __shared__ float rs[R][256];
     const int le = threadIdx.x / N, i = threadIdx.x % N;
     const int e0 = blockIdx.x * EPB * R + le;
-    float y[R];
-    const unsigned long long pol = l2_keep();
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int e = e0 + k * EPB;
-        y[k] = 0.0f;
-        if (e < ne) {
-            const float* Ad = A.AdT + (size_t)e * N * N + i;
-            const float* xe = x + (size_t)e * N;
-#pragma unroll
-            for (int j = 0; j < N; ++j) y[k] += ld_hint(Ad + j * N, pol) * xe[j];
-            face_gather<N>(A, x, e, i, sc, le + k * EPB);
-        }
+        if (e < ne) face_gather<N>(A, x, e, i, sc, le + k * EPB);
     }
     __syncthreads();
 #pragma unroll
@@ -164,7 +158,7 @@ __global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> 
     for (int k = 0; k < R; ++k) {
         const int e = e0 + k * EPB;
         float rv = 0.0f;
-        if (e < ne) rv = (float)b[(size_t)e * N + i] - face_lift<N>(A, i, y[k], sc, le + k * EPB);
+        if (e < ne) rv = (float)b[(size_t)e * N + i] - face_lift<N>(A, i, 0.0f, sc, le + k * EPB);
         rs[k][threadIdx.x] = rv;
     }
     __syncthreads();
@@ -174,9 +168,13 @@ __global__ void __launch_bounds__(256) bj_residual_kernel(int ne, FaceOp<float> 
             const int e = e0 + k * EPB;
             if (e < ne) {
                 const float* re = rs[k] + le * N;
+                const float* W = WdT + (size_t)e * N * 4 + i;
+                const float* xe = x + (size_t)e * N;
                 float s = 0.0f;
 #pragma unroll
                 for (int j = 0; j < N; ++j) s = fmaf(w4[j * 4 + i], re[j], s);
+#pragma unroll
+                for (int j = 0; j < N; ++j) s = fmaf(-W[j * 4], xe[j], s);
                 cres[(size_t)e * 4 + i] = s;
             }
         }
@@ -661,8 +659,8 @@ int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cuda
         st.advance(out);
         ++launches;
     }
-    bj_residual_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, r, st.cur, m.w4, m.res0, m.coarse_pf,
-                                                           m.coarse_npf, ctl);
+    bj_residual_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.WdT, r, st.cur, m.w4, m.res0,
+                                                           m.coarse_pf, m.coarse_npf, ctl);
     // vertex and aggregation levels and the coarsest solve (one cluster launch)
     const float* coarse_out = launch_coarse_cycle(m, m.res0, ctl, s);
     const int rows0 = m.ne * N;
@@ -710,8 +708,8 @@ int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
         st.advance(out);
         ++launches;
     }
-    bj_residual_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, a.r, st.cur, m.w4, m.res0, m.coarse_pf,
-                                                           m.coarse_npf, a.ctl);
+    bj_residual_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.WdT, a.r, st.cur, m.w4, m.res0,
+                                                           m.coarse_pf, m.coarse_npf, a.ctl);
     const float* coarse_out = launch_coarse_cycle(m, m.res0, a.ctl, s);
     const int rows0 = m.ne * N;
     prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, st.cur, a.ctl);
