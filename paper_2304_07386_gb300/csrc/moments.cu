@@ -665,7 +665,7 @@ __global__ void diff_final_kernel(int nblk, const double* part, double* out) {
 // over a.nrow unknowns; the operator-product partials are a.part[0..a.nblk))
 void launch_cgx_update(const CGArgs& a, cudaStream_t s) { cgx_update_kernel<<<a.nvblk, 256, 0, s>>>(a); }
 void launch_cgx_rz(const CGArgs& a, cudaStream_t s) { cgx_rz_kernel<<<a.nvblk, 256, 0, s>>>(a); }
-void launch_cgx_direction(const CGArgs& a, cudaStream_t s) { cgx_direction_kernel<<<a.nvblk, 256, 0, s>>>(a); }
+void launch_cgx_direction(const CGArgs& a, cudaStream_t s) { cgx_direction_kernel<<<(a.nrow + 255) / 256, 256, 0, s>>>(a); }
 void launch_cg_init_scalars(const CGArgs& a, double tol, int max_iters, cudaStream_t s) {
     cg_init_scalars_kernel<<<1, 256, 0, s>>>(a, tol * tol, max_iters);
 }
@@ -704,7 +704,8 @@ int cgx_iterations(const CGArgs& a, int count, const MGPlan& mg, cudaStream_t s)
             default: cgx_spmv_kernel<25, R><<<nblkR, tpb, 0, s>>>(a); break;
         }
         launches += 1 + mg_cg_iteration(mg, a, s);
-        cgx_direction_kernel<<<a.nvblk, 256, 0, s>>>(a);
+        // one thread per unknown: every load of the update is in flight at once
+        cgx_direction_kernel<<<(a.nrow + 255) / 256, 256, 0, s>>>(a);
         launches += 1;
     }
     return launches;
