@@ -84,8 +84,11 @@ struct smm_ctx {
     double *mom = nullptr, *beta = nullptr;
     // closures / rhs data
     double *L1 = nullptr, *b_nhat = nullptr, *b_ds = nullptr, *b_eb0 = nullptr;
-    double *Kxx = nullptr, *Ks = nullptr, *Kyy = nullptr, *Dfx = nullptr, *Dfy = nullptr, *nds = nullptr;
-    double *DfxT = nullptr, *DfyT = nullptr;   // the face gradient operators with the face point index fastest
+    double* nds = nullptr;
+    // right-hand-side operators as FP32 pairs: K blocks column-major, the face gradient operators
+    // point-major (Dfx, Dfy) and node-major (DfxT, DfyT)
+    float2 *Kxx = nullptr, *Ks = nullptr, *Kyy = nullptr, *Dfx = nullptr, *Dfy = nullptr;
+    float2 *DfxT = nullptr, *DfyT = nullptr;
     double *bfixed = nullptr, *trace = nullptr, *rhs = nullptr;
     // moment operator and CG
     double *AdT = nullptr, *CT = nullptr, *PinvT = nullptr;   // diagonal blocks, face couplings, inverses
@@ -297,9 +300,11 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     ok &= upload(h, h->src, s.src) && upload(h, h->inflow, s.inflow);
     ok &= upload(h, h->L1, s.L1) && upload(h, h->b_nhat, s.b_nhat) && upload(h, h->b_ds, s.b_ds) && upload(h, h->b_eb0, s.b_eb0);
     // column-major (transposed) blocks, so that the n threads of an element read contiguous entries
-    ok &= upload(h, h->Kxx, transpose_blocks(s.Kxx, s.n)) && upload(h, h->Ks, transpose_blocks(s.Ks, s.n)) &&
-          upload(h, h->Kyy, transpose_blocks(s.Kyy, s.n));
-    ok &= upload(h, h->Dfx, s.Dfx) && upload(h, h->Dfy, s.Dfy) && upload(h, h->nds, s.nds) && upload(h, h->bfixed, s.bfixed);
+    ok &= upload(h, h->Kxx, to_pairs(transpose_blocks(s.Kxx, s.n))) &&
+          upload(h, h->Ks, to_pairs(transpose_blocks(s.Ks, s.n))) &&
+          upload(h, h->Kyy, to_pairs(transpose_blocks(s.Kyy, s.n)));
+    ok &= upload(h, h->Dfx, to_pairs(s.Dfx)) && upload(h, h->Dfy, to_pairs(s.Dfy)) && upload(h, h->nds, s.nds) &&
+          upload(h, h->bfixed, s.bfixed);
     {
         // [element][face][node][point] copies for the trace kernel, whose threads are face points
         const int nq = s.nfq, nn = s.n;
@@ -311,7 +316,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
                     tx[(b * nn + j) * nq + q] = s.Dfx[(b * nq + q) * nn + j];
                     ty[(b * nn + j) * nq + q] = s.Dfy[(b * nq + q) * nn + j];
                 }
-        ok &= upload(h, h->DfxT, tx) && upload(h, h->DfyT, ty);
+        ok &= upload(h, h->DfxT, to_pairs(tx)) && upload(h, h->DfyT, to_pairs(ty));
     }
     if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
     if (o.negative_flux_fixup) {

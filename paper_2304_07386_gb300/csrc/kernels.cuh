@@ -124,11 +124,10 @@ void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_ele
                  const double* w, const double* ox, const double* oy, const double* L1, const double* nhat,
                  const double* eb0, const double* psi, const double* mom, double* beta, cudaStream_t s);
 void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
-                const double* Kxx, const double* Ks, const double* Kyy, const double* Dfx, const double* Dfy,
-                const double* DfxT, const double* DfyT, const double* nds, const double* L1, const double* sigma_t,
-                const int32_t* nbr,
-                const int32_t* nbr_face, const int32_t* nbr_flip, const int32_t* bface_id, const double* b_ds,
-                double* trace, double* rhs, cudaStream_t s);
+                const float2* Kxx, const float2* Ks, const float2* Kyy, const float2* Dfx, const float2* Dfy,
+                const float2* DfxT, const float2* DfyT, const double* nds, const double* L1, const double* sigma_t,
+                const int32_t* nbr, const int32_t* nbr_face, const int32_t* nbr_flip, const int32_t* bface_id,
+                const double* b_ds, double* trace, double* rhs, cudaStream_t s);
 
 // IP-SMM moment operator: diagonal blocks plus face-factored neighbour
 // blocks A_{e,e2} = E_f^T C_{e,f} E_f2, where E_f extracts the p+1 trace

@@ -88,38 +88,65 @@ __global__ void beta_kernel(int nb, int nd, int n, int p, int nfq, const int32_t
     }
 }
 
+// T (the three correction components, component stride cst) of cnt = elements
+// x n dofs into shared memory as pairs, component stride sst.  The rows of K
+// and of the face gradient operators sum to zero (the nodal basis is a
+// partition of unity), so each element's T enters shifted by its value at the
+// element's first node: the pair products then carry the variation of T across
+// the element instead of its size, which keeps their cancellation (and so the
+// pair rounding) small on fine meshes.
+__device__ __forceinline__ void stage_T(float2* sT, const double* __restrict__ t0, size_t cst, int cnt, int sst, int n) {
+    for (int k = threadIdx.x; k < 3 * cnt; k += blockDim.x) {
+        const int c = k / cnt, r = k - c * cnt;
+        const double* tc = t0 + c * cst;
+        sT[c * sst + r] = df_make(tc[r] - tc[r - r % n]);
+    }
+}
+
 // Face traces of the correction tensor per (element, face, Gauss point):
-// g = (div T . n ds)/sigma_t, and T n ds (2 components).
-__global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, const double* __restrict__ mom,
-                                 const double* __restrict__ DfxT, const double* __restrict__ DfyT,
+// g = (div T . n ds)/sigma_t, and T n ds (2 components).  A block takes epb
+// whole elements, one thread per face point; their T is staged in shared
+// memory as FP32 pairs and the gradient sums are pair dot products
+// (dfloat.cuh), since FP64 FMAs are the scarce unit here.
+__global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, int epb, const double* __restrict__ mom,
+                                 const float2* __restrict__ DfxT, const float2* __restrict__ DfyT,
                                  const double* __restrict__ nds, const double* __restrict__ L1,
                                  const double* __restrict__ sigma_t, double* __restrict__ tr) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ne * 4 * nfq) return;
-    const int q = t % nfq, f = (t / nfq) % 4, e = t / (4 * nfq);
+    extern __shared__ float2 sT[];  // [3][epb][n]: Txx, Txy, Tyy
+    const int e0 = blockIdx.x * epb, ecount = min(epb, ne - e0), cnt = ecount * n;
     const size_t st = (size_t)ne * n;
-    const double* txx = mom + 3 * st + (size_t)e * n;
-    const double* txy = mom + 4 * st + (size_t)e * n;
-    const double* tyy = mom + 5 * st + (size_t)e * n;
+    stage_T(sT, mom + 3 * st + (size_t)e0 * n, st, cnt, epb * n, n);
+    __syncthreads();
+    const int fq = 4 * nfq, le = threadIdx.x / fq;
+    if (le >= ecount) return;
+    const int r = threadIdx.x - le * fq, f = r / nfq, q = r - f * nfq, e = e0 + le;
+    const size_t t = (size_t)e * fq + r;
     // the face gradient operators as [element][face][node][point]: the threads of one face read
     // consecutive words
-    const size_t fb = ((size_t)e * 4 + f) * n * nfq + q;
-    const double* dx = DfxT + fb;
-    const double* dy = DfyT + fb;
-    double divx = 0.0, divy = 0.0;
+    const float2* dx = DfxT + ((size_t)e * 4 + f) * n * nfq + q;
+    const float2* dy = DfyT + ((size_t)e * 4 + f) * n * nfq + q;
+    const float2 *txx = sT + le * n, *txy = txx + epb * n, *tyy = txy + epb * n;
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
     for (int j = 0; j < n; ++j) {
-        const double ax = dx[(size_t)j * nfq], ay = dy[(size_t)j * nfq];
-        divx += ax * txx[j] + ay * txy[j];
-        divy += ax * txy[j] + ay * tyy[j];
+        const float2 ax = dx[(size_t)j * nfq], ay = dy[(size_t)j * nfq];
+        const float2 a = txx[j], b = txy[j], c = tyy[j];
+        df_acc(sx, cx, ax.x, ax.y, a.x, a.y);
+        df_acc(sx, cx, ay.x, ay.y, b.x, b.y);
+        df_acc(sy, cy, ax.x, ax.y, b.x, b.y);
+        df_acc(sy, cy, ay.x, ay.y, c.x, c.y);
     }
+    const double divx = df_to_double(sx, cx), divy = df_to_double(sy, cy);
+    const double* gxx = mom + 3 * st + (size_t)e * n;
+    const double* gxy = mom + 4 * st + (size_t)e * n;
+    const double* gyy = mom + 5 * st + (size_t)e * n;
     const int p1 = p + 1;
     double vxx = 0, vxy = 0, vyy = 0;
     for (int a = 0; a < p1; ++a) {
         const int nd_ = f == 0 ? a : (f == 1 ? a * p1 + p : (f == 2 ? p * p1 + a : a * p1));
         const double l = L1[q * p1 + a];
-        vxx += l * txx[nd_];
-        vxy += l * txy[nd_];
-        vyy += l * tyy[nd_];
+        vxx += l * gxx[nd_];
+        vxy += l * gxy[nd_];
+        vyy += l * gyy[nd_];
     }
     const double nx = nds[2 * t], ny = nds[2 * t + 1];
     tr[3 * t] = (divx * nx + divy * ny) / sigma_t[e];
@@ -131,50 +158,83 @@ __global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, const double* __
 // b = b_fixed - (1/sigma_t)(Kxx Txx + (Kxy+Kyx) Txy + Kyy Tyy)
 //   + sum_{interior f} sum_q [ l_a(s_q) (g_K - g_K')/2 + (grad phi_i/sigma_t) . (Tn_K + Tn_K')/2 ]
 //   - sum_{boundary f} sum_q ds_q l_a(s_q) beta_q
-__global__ void rhs_assemble_kernel(int ne, int n, int p, int nfq, const double* __restrict__ mom,
+// A block takes epb whole elements.  It first forms, once per face point, the
+// weights that every dof of the face shares: (Tn_K + Tn_K')/(2 sigma_t) as
+// pairs and the jump (g_K - g_K')/2, or -ds beta on a boundary face, in FP64.
+// The K and face-gradient products are then pair dot products (dfloat.cuh)
+// against T staged as pairs; the blocks of K are column-major (entry (i, j)
+// at [e][j][i]) so that the n threads of an element read contiguous words.
+__global__ void rhs_assemble_kernel(int ne, int n, int p, int nfq, int epb, const double* __restrict__ mom,
                                     const double* __restrict__ beta, const double* __restrict__ bfixed,
-                                    const double* __restrict__ Kxx, const double* __restrict__ Ks,
-                                    const double* __restrict__ Kyy, const double* __restrict__ Dfx,
-                                    const double* __restrict__ Dfy, const double* __restrict__ L1,
+                                    const float2* __restrict__ Kxx, const float2* __restrict__ Ks,
+                                    const float2* __restrict__ Kyy, const float2* __restrict__ Dfx,
+                                    const float2* __restrict__ Dfy, const double* __restrict__ L1,
                                     const double* __restrict__ sigma_t, const int32_t* __restrict__ nbr,
                                     const int32_t* __restrict__ nbr_face, const int32_t* __restrict__ nbr_flip,
                                     const int32_t* __restrict__ bface_id, const double* __restrict__ b_ds,
                                     const double* __restrict__ tr, double* __restrict__ rhs) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ne * n) return;
-    const int e = t / n, i = t - e * n;
+    extern __shared__ float2 sh2[];
+    const int nf = 4 * nfq;                     // face points of one element
+    float2* sT = sh2;                           // [3][epb][n]: Txx, Txy, Tyy
+    float2* sC = sh2 + 3 * epb * n;             // [epb][4 nfq][2]: (Tn_K + Tn_K')/(2 sigma_t)
+    double* sG = (double*)(sC + 2 * epb * nf);  // [epb][4 nfq]: jump or boundary weight
+    const int e0 = blockIdx.x * epb, ecount = min(epb, ne - e0), cnt = ecount * n;
     const size_t st = (size_t)ne * n;
-    const double* txx = mom + 3 * st + (size_t)e * n;
-    const double* txy = mom + 4 * st + (size_t)e * n;
-    const double* tyy = mom + 5 * st + (size_t)e * n;
-    const size_t mo = (size_t)e * n * n + i;  // blocks stored column-major: entry (i, j) at [e][j][i]
-    double acc = bfixed[t];
-    for (int j = 0; j < n; ++j)
-        acc += Kxx[mo + (size_t)j * n] * txx[j] + Ks[mo + (size_t)j * n] * txy[j] + Kyy[mo + (size_t)j * n] * tyy[j];
-    const int p1 = p + 1, ix = i % p1, iy = i / p1;
-    const double hs = 0.5 / sigma_t[e];
-    for (int f = 0; f < 4; ++f) {
-        const bool on = (f == 0 && iy == 0) || (f == 1 && ix == p) || (f == 2 && iy == p) || (f == 3 && ix == 0);
-        const int fa = (f == 0 || f == 2) ? ix : iy;
+    stage_T(sT, mom + 3 * st + (size_t)e0 * n, st, cnt, epb * n, n);
+    for (int k = threadIdx.x; k < ecount * nf; k += blockDim.x) {
+        const int le = k / nf, r = k - le * nf, f = r / nfq, q = r - f * nfq, e = e0 + le;
         const int e2 = nbr[e * 4 + f];
-        const size_t fo = ((size_t)e * 4 + f) * nfq;
         if (e2 >= 0) {
-            const int f2 = nbr_face[e * 4 + f], flip = nbr_flip[e * 4 + f];
-            const size_t fo2 = ((size_t)e2 * 4 + f2) * nfq;
-            for (int q = 0; q < nfq; ++q) {
-                const int q2 = flip ? nfq - 1 - q : q;
-                const double* a1 = tr + 3 * (fo + q);
-                const double* a2 = tr + 3 * (fo2 + q2);
-                const double tjx = a1[1] + a2[1], tjy = a1[2] + a2[2];
-                acc += hs * (Dfx[(fo + q) * n + i] * tjx + Dfy[(fo + q) * n + i] * tjy);
-                if (on) acc += L1[q * p1 + fa] * 0.5 * (a1[0] - a2[0]);
-            }
-        } else if (on) {
-            const int b = bface_id[e * 4 + f];
-            for (int q = 0; q < nfq; ++q) acc -= b_ds[(size_t)b * nfq + q] * L1[q * p1 + fa] * beta[(size_t)b * nfq + q];
+            const int f2 = nbr_face[e * 4 + f], q2 = nbr_flip[e * 4 + f] ? nfq - 1 - q : q;
+            const double* a1 = tr + 3 * ((size_t)e * nf + r);
+            const double* a2 = tr + 3 * (((size_t)e2 * 4 + f2) * nfq + q2);
+            const double hs = 0.5 / sigma_t[e];
+            sC[2 * k] = df_make(hs * (a1[1] + a2[1]));
+            sC[2 * k + 1] = df_make(hs * (a1[2] + a2[2]));
+            sG[k] = 0.5 * (a1[0] - a2[0]);
+        } else {
+            const size_t bq = (size_t)bface_id[e * 4 + f] * nfq + q;
+            sC[2 * k] = make_float2(0.f, 0.f);
+            sC[2 * k + 1] = make_float2(0.f, 0.f);
+            sG[k] = -(b_ds[bq] * beta[bq]);
         }
     }
-    rhs[t] = acc;
+    __syncthreads();
+    const int le = threadIdx.x / n;
+    if (le >= ecount) return;
+    const int i = threadIdx.x - le * n, e = e0 + le;
+    const size_t t = (size_t)e * n + i;
+    const size_t mo = (size_t)e * n * n + i;
+    const float2 *txx = sT + le * n, *txy = txx + epb * n, *tyy = txy + epb * n;
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    for (int j = 0; j < n; ++j) {
+        const float2 kx = Kxx[mo + (size_t)j * n], ks = Ks[mo + (size_t)j * n], ky = Kyy[mo + (size_t)j * n];
+        const float2 a = txx[j], b = txy[j], c = tyy[j];
+        df_acc(s0, c0, kx.x, kx.y, a.x, a.y);
+        df_acc(s1, c1, ks.x, ks.y, b.x, b.y);
+        df_acc(s2, c2, ky.x, ky.y, c.x, c.y);
+    }
+    const int p1 = p + 1, ix = i % p1, iy = i / p1;
+    double jump = 0.0;
+    for (int f = 0; f < 4; ++f) {
+        const int lf = le * nf + f * nfq;
+        if (nbr[e * 4 + f] >= 0) {
+            const float2* dx = Dfx + ((size_t)e * nf + f * nfq) * n + i;
+            const float2* dy = Dfy + ((size_t)e * nf + f * nfq) * n + i;
+            for (int q = 0; q < nfq; ++q) {
+                const float2 ax = dx[(size_t)q * n], ay = dy[(size_t)q * n];
+                const float2 wx = sC[2 * (lf + q)], wy = sC[2 * (lf + q) + 1];
+                df_acc(s0, c0, ax.x, ax.y, wx.x, wx.y);
+                df_acc(s1, c1, ay.x, ay.y, wy.x, wy.y);
+            }
+        }
+        const bool on = (f == 0 && iy == 0) || (f == 1 && ix == p) || (f == 2 && iy == p) || (f == 3 && ix == 0);
+        if (on) {
+            const int fa = (f == 0 || f == 2) ? ix : iy;
+            for (int q = 0; q < nfq; ++q) jump += L1[q * p1 + fa] * sG[lf + q];
+        }
+    }
+    rhs[t] = bfixed[t] + (df_to_double(s0, c0) + df_to_double(s1, c1) + df_to_double(s2, c2)) + jump;
 }
 
 // The same moments from psi stored as FP32 pairs, accumulated in pair
@@ -228,15 +288,22 @@ void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_ele
 }
 
 void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
-                const double* Kxx, const double* Ks, const double* Kyy, const double* Dfx, const double* Dfy,
-                const double* DfxT, const double* DfyT, const double* nds, const double* L1, const double* sigma_t, const int32_t* nbr, const int32_t* nbr_face,
-                const int32_t* nbr_flip, const int32_t* bface_id, const double* b_ds, double* trace, double* rhs,
-                cudaStream_t s) {
-    const int t1 = ne * 4 * nfq;
-    rhs_trace_kernel<<<(t1 + 255) / 256, 256, 0, s>>>(ne, n, p, nfq, mom, DfxT, DfyT, nds, L1, sigma_t, trace);
-    const int t2 = ne * n;
-    rhs_assemble_kernel<<<(t2 + 255) / 256, 256, 0, s>>>(ne, n, p, nfq, mom, beta, bfixed, Kxx, Ks, Kyy, Dfx, Dfy, L1,
-                                                         sigma_t, nbr, nbr_face, nbr_flip, bface_id, b_ds, trace, rhs);
+                const float2* Kxx, const float2* Ks, const float2* Kyy, const float2* Dfx, const float2* Dfy,
+                const float2* DfxT, const float2* DfyT, const double* nds, const double* L1, const double* sigma_t,
+                const int32_t* nbr, const int32_t* nbr_face, const int32_t* nbr_flip, const int32_t* bface_id,
+                const double* b_ds, double* trace, double* rhs, cudaStream_t s) {
+    // trace: whole elements of 4 nfq face points per block (nfq <= 11: at least 5 elements)
+    const int fq = 4 * nfq, ept = std::max(1, 256 / fq);
+    const size_t sh1 = (size_t)3 * ept * n * sizeof(float2);
+    rhs_trace_kernel<<<(ne + ept - 1) / ept, (ept * fq + 31) / 32 * 32, sh1, s>>>(ne, n, p, nfq, ept, mom, DfxT, DfyT,
+                                                                                nds, L1, sigma_t, trace);
+    // assembly: whole elements of n dofs per block; at most 32 elements keeps the face
+    // weights of p = 1 within 48 KB of shared memory
+    const int epa = std::max(1, std::min(256 / n, 32));
+    const size_t sh2 = (size_t)(3 * epa * n + 2 * epa * fq) * sizeof(float2) + (size_t)epa * fq * sizeof(double);
+    rhs_assemble_kernel<<<(ne + epa - 1) / epa, (epa * n + 31) / 32 * 32, sh2, s>>>(
+        ne, n, p, nfq, epa, mom, beta, bfixed, Kxx, Ks, Kyy, Dfx, Dfy, L1, sigma_t, nbr, nbr_face, nbr_flip, bface_id,
+        b_ds, trace, rhs);
 }
 
 // ---------------------------------------------------------------------------
