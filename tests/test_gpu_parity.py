@@ -267,3 +267,32 @@ def test_batched_iterate_matches_oracle():
         ref, k, _ = op.iterate(tol=1e-12)
         assert rel(ph.cpu().numpy(), ref.ravel()) < 1e-9
         assert abs(st["outer_iterations"] - k) <= 1
+
+
+def test_moment_solve_from_smooth_moments_on_a_fine_curved_mesh():
+    """The right-hand side's pair products where they cancel most: smooth T
+    (K and the face gradient operators annihilate constants, so K T is small
+    next to its terms) on a curved 32x32 p = 4 mesh, with a seeded beta on the
+    boundary.  The moment solve from these moments matches the oracle's solve
+    of the same IP-SMM system (Eq. ipsmm)."""
+    import paper_2304_07386_gb300 as P
+    from oracle import closures, ipsmm
+    prob = problem(32, 32, m=3, p=4, sn=4, seed=5, kind="iso", c=0.6)
+    h = make_gpu(prob, tol_cg=1e-13)
+    try:
+        disc = oracle_disc(prob)
+        q, inflow = sources(prob, disc.omega)
+        x, y = prob["pos"][:, :, 0], prob["pos"][:, :, 1]
+        T = np.stack([np.sin(2 * x + 1) * np.cos(1.5 * y - 1), 0.5 * np.cos(2 * x - y), 0.8 * np.sin(x + 2 * y) + 0.3])
+        jin = closures.j_in(disc, inflow)
+        beta = np.random.default_rng(11).uniform(-0.1, 0.1, jin.shape)
+        mom = np.concatenate([np.ones((1,) + x.shape), np.zeros((2,) + x.shape), T])
+        P.smm_set_moments(h, dev(mom), dev(beta))
+        phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+        its = P.smm_moment_solve(h, phi)
+        assert 0 < its < 200
+        b = ipsmm.assemble_rhs(disc, closures.source_moments(disc, q), T, jin, beta)
+        x_o = ipsmm.solve(ipsmm.assemble_lhs(disc), b)
+        assert rel(phi.cpu().numpy(), x_o) < 1e-9, rel(phi.cpu().numpy(), x_o)
+    finally:
+        h.destroy()
