@@ -108,10 +108,12 @@ __device__ __forceinline__ void stage_T(float2* sT, const double* __restrict__ t
 // whole elements, one thread per face point; their T is staged in shared
 // memory as FP32 pairs and the gradient sums are pair dot products
 // (dfloat.cuh), since FP64 FMAs are the scarce unit here.
-__global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, int epb, const double* __restrict__ mom,
+template <int N>  // dofs per element, or 0: taken from n_rt
+__global__ void rhs_trace_kernel(int ne, int n_rt, int p, int nfq, int epb, const double* __restrict__ mom,
                                  const float2* __restrict__ DfxT, const float2* __restrict__ DfyT,
                                  const double* __restrict__ nds, const double* __restrict__ L1,
                                  const double* __restrict__ sigma_t, double* __restrict__ tr) {
+    const int n = N > 0 ? N : n_rt;
     extern __shared__ float2 sT[];  // [3][epb][n]: Txx, Txy, Tyy
     const int e0 = blockIdx.x * epb, ecount = min(epb, ne - e0), cnt = ecount * n;
     const size_t st = (size_t)ne * n;
@@ -127,6 +129,7 @@ __global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, int epb, const d
     const float2* dy = DfyT + ((size_t)e * 4 + f) * n * nfq + q;
     const float2 *txx = sT + le * n, *txy = txx + epb * n, *tyy = txy + epb * n;
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+#pragma unroll
     for (int j = 0; j < n; ++j) {
         const float2 ax = dx[(size_t)j * nfq], ay = dy[(size_t)j * nfq];
         const float2 a = txx[j], b = txy[j], c = tyy[j];
@@ -164,7 +167,8 @@ __global__ void rhs_trace_kernel(int ne, int n, int p, int nfq, int epb, const d
 // The K and face-gradient products are then pair dot products (dfloat.cuh)
 // against T staged as pairs; the blocks of K are column-major (entry (i, j)
 // at [e][j][i]) so that the n threads of an element read contiguous words.
-__global__ void rhs_assemble_kernel(int ne, int n, int p, int nfq, int epb, const double* __restrict__ mom,
+template <int N>  // dofs per element, or 0: taken from n_rt
+__global__ void rhs_assemble_kernel(int ne, int n_rt, int p, int nfq, int epb, const double* __restrict__ mom,
                                     const double* __restrict__ beta, const double* __restrict__ bfixed,
                                     const float2* __restrict__ Kxx, const float2* __restrict__ Ks,
                                     const float2* __restrict__ Kyy, const float2* __restrict__ Dfx,
@@ -173,6 +177,7 @@ __global__ void rhs_assemble_kernel(int ne, int n, int p, int nfq, int epb, cons
                                     const int32_t* __restrict__ nbr_face, const int32_t* __restrict__ nbr_flip,
                                     const int32_t* __restrict__ bface_id, const double* __restrict__ b_ds,
                                     const double* __restrict__ tr, double* __restrict__ rhs) {
+    const int n = N > 0 ? N : n_rt;
     extern __shared__ float2 sh2[];
     const int nf = 4 * nfq;                     // face points of one element
     float2* sT = sh2;                           // [3][epb][n]: Txx, Txy, Tyy
@@ -207,6 +212,7 @@ __global__ void rhs_assemble_kernel(int ne, int n, int p, int nfq, int epb, cons
     const size_t mo = (size_t)e * n * n + i;
     const float2 *txx = sT + le * n, *txy = txx + epb * n, *tyy = txy + epb * n;
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+#pragma unroll
     for (int j = 0; j < n; ++j) {
         const float2 kx = Kxx[mo + (size_t)j * n], ks = Ks[mo + (size_t)j * n], ky = Kyy[mo + (size_t)j * n];
         const float2 a = txx[j], b = txy[j], c = tyy[j];
@@ -287,23 +293,42 @@ void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_ele
                                               mom, beta);
 }
 
+template <int N>
+void launch_rhs_n(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
+                  const float2* Kxx, const float2* Ks, const float2* Kyy, const float2* Dfx, const float2* Dfy,
+                  const float2* DfxT, const float2* DfyT, const double* nds, const double* L1, const double* sigma_t,
+                  const int32_t* nbr, const int32_t* nbr_face, const int32_t* nbr_flip, const int32_t* bface_id,
+                  const double* b_ds, double* trace, double* rhs, cudaStream_t s) {
+    // trace: whole elements of 4 nfq face points per block (nfq <= 11: at least 5 elements)
+    const int fq = 4 * nfq, ept = std::max(1, 256 / fq);
+    const size_t sh1 = (size_t)3 * ept * n * sizeof(float2);
+    rhs_trace_kernel<N><<<(ne + ept - 1) / ept, (ept * fq + 31) / 32 * 32, sh1, s>>>(ne, n, p, nfq, ept, mom, DfxT,
+                                                                                   DfyT, nds, L1, sigma_t, trace);
+    // assembly: whole elements of n dofs per block; at most 32 elements keeps the face
+    // weights of p = 1 within 48 KB of shared memory
+    const int epa = std::max(1, std::min(256 / n, 32));
+    const size_t sh2 = (size_t)(3 * epa * n + 2 * epa * fq) * sizeof(float2) + (size_t)epa * fq * sizeof(double);
+    rhs_assemble_kernel<N><<<(ne + epa - 1) / epa, (epa * n + 31) / 32 * 32, sh2, s>>>(
+        ne, n, p, nfq, epa, mom, beta, bfixed, Kxx, Ks, Kyy, Dfx, Dfy, L1, sigma_t, nbr, nbr_face, nbr_flip, bface_id,
+        b_ds, trace, rhs);
+}
+
 void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
                 const float2* Kxx, const float2* Ks, const float2* Kyy, const float2* Dfx, const float2* Dfy,
                 const float2* DfxT, const float2* DfyT, const double* nds, const double* L1, const double* sigma_t,
                 const int32_t* nbr, const int32_t* nbr_face, const int32_t* nbr_flip, const int32_t* bface_id,
                 const double* b_ds, double* trace, double* rhs, cudaStream_t s) {
-    // trace: whole elements of 4 nfq face points per block (nfq <= 11: at least 5 elements)
-    const int fq = 4 * nfq, ept = std::max(1, 256 / fq);
-    const size_t sh1 = (size_t)3 * ept * n * sizeof(float2);
-    rhs_trace_kernel<<<(ne + ept - 1) / ept, (ept * fq + 31) / 32 * 32, sh1, s>>>(ne, n, p, nfq, ept, mom, DfxT, DfyT,
-                                                                                nds, L1, sigma_t, trace);
-    // assembly: whole elements of n dofs per block; at most 32 elements keeps the face
-    // weights of p = 1 within 48 KB of shared memory
-    const int epa = std::max(1, std::min(256 / n, 32));
-    const size_t sh2 = (size_t)(3 * epa * n + 2 * epa * fq) * sizeof(float2) + (size_t)epa * fq * sizeof(double);
-    rhs_assemble_kernel<<<(ne + epa - 1) / epa, (epa * n + 31) / 32 * 32, sh2, s>>>(
-        ne, n, p, nfq, epa, mom, beta, bfixed, Kxx, Ks, Kyy, Dfx, Dfy, L1, sigma_t, nbr, nbr_face, nbr_flip, bface_id,
-        b_ds, trace, rhs);
+    // the element sizes of p = 1..4 get fully unrolled dot products
+    auto* f = &launch_rhs_n<0>;
+    switch (n) {
+        case 4: f = &launch_rhs_n<4>; break;
+        case 9: f = &launch_rhs_n<9>; break;
+        case 16: f = &launch_rhs_n<16>; break;
+        case 25: f = &launch_rhs_n<25>; break;
+        default: break;
+    }
+    f(ne, n, p, nfq, mom, beta, bfixed, Kxx, Ks, Kyy, Dfx, Dfy, DfxT, DfyT, nds, L1, sigma_t, nbr, nbr_face, nbr_flip,
+      bface_id, b_ds, trace, rhs, s);
 }
 
 // ---------------------------------------------------------------------------
