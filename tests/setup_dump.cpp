@@ -1,0 +1,54 @@
+// Test driver (CPU): runs the library's host setup on a mesh read from files
+// and writes the right-hand-side operators it builds, so that a test can
+// compare them with the oracle.  Usage: setup_dump DIR NE NNODES M P
+//   in:  DIR/nodes.f64 [nnodes][2], DIR/elem.i32 [ne][(m+1)^2], DIR/sigma_t.f64 [ne]
+//   out: DIR/dims.txt (n nfq), DIR/{Kxx,Ks,Kyy,Dfx,Dfy,nds}.f64
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <string>
+#include <vector>
+
+#include "setup.hpp"
+
+template <class T>
+static bool read_file(const std::string& path, std::vector<T>& v) {
+    std::ifstream in(path, std::ios::binary);
+    in.read(reinterpret_cast<char*>(v.data()), (std::streamsize)(v.size() * sizeof(T)));
+    return (bool)in;
+}
+
+static bool write_file(const std::string& path, const std::vector<double>& v) {
+    std::ofstream out(path, std::ios::binary);
+    out.write(reinterpret_cast<const char*>(v.data()), (std::streamsize)(v.size() * sizeof(double)));
+    return (bool)out;
+}
+
+int main(int argc, char** argv) {
+    if (argc != 6) return 2;
+    const std::string dir = argv[1];
+    const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
+    const int n = (p + 1) * (p + 1);
+    std::vector<double> nodes((size_t)nn * 2), st(ne), ss(ne), q((size_t)ne * n, 0.0);
+    std::vector<int32_t> elem((size_t)ne * (m + 1) * (m + 1));
+    if (!read_file(dir + "/nodes.f64", nodes) || !read_file(dir + "/elem.i32", elem) ||
+        !read_file(dir + "/sigma_t.f64", st))
+        return 3;
+    for (int e = 0; e < ne; ++e) ss[e] = 0.5 * st[e];
+    smm::Input in;
+    in.ne = ne; in.m = m; in.p = p; in.sn = 4; in.n_nodes = nn;
+    in.nodes = nodes.data(); in.elem_nodes = elem.data(); in.sigma_t = st.data(); in.sigma_s = ss.data();
+    in.q = q.data();
+    smm::Setup s;
+    std::string err;
+    if (smm::build_setup(in, s, err)) {
+        std::fprintf(stderr, "%s\n", err.c_str());
+        return 4;
+    }
+    std::ofstream dims(dir + "/dims.txt");
+    dims << s.n << " " << s.nfq << "\n";
+    const bool ok = write_file(dir + "/Kxx.f64", s.Kxx) && write_file(dir + "/Ks.f64", s.Ks) &&
+                    write_file(dir + "/Kyy.f64", s.Kyy) && write_file(dir + "/Dfx.f64", s.Dfx) &&
+                    write_file(dir + "/Dfy.f64", s.Dfy) && write_file(dir + "/nds.f64", s.nds);
+    return ok ? 0 : 5;
+}

@@ -1,0 +1,79 @@
+"""CPU checks of the host setup of the CUDA path (setup.cpp) against the oracle.
+
+The right-hand-side kernels stream three T-divergence blocks per element
+(K_xx, K_xy + K_yx, K_yy of the volume term -int grad u . (1/sigma_t) div_h T
+of Eq. ipsmm) and the physical basis gradients at the face quadrature points.
+A driver compiled against setup.cpp writes them for seeded curved meshes, and
+each must equal the oracle's own element quadrature (its stiffness integrals
+and face data).  The kernels also rely on both operators annihilating
+constants -- their rows sum to zero because the nodal basis is a partition of
+unity -- when they shift T by its value at an element's first node; that is
+checked here too.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import smm_workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2304_07386_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = tmp_path_factory.mktemp("setup") / "setup_dump"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", CSRC, os.path.join(ROOT, "tests", "setup_dump.cpp"),
+                    os.path.join(CSRC, "setup.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+CASES = [(4, 3, 3, 4, 2), (3, 3, 2, 2, 5), (2, 3, 1, 1, None), (2, 2, 6, 3, 7)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_rhs_operators_match_oracle_quadrature(driver, tmp_path, case):
+    from oracle.transport import Discretization
+    nx, ny, m, p, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne = mesh.n_elem
+    st = 1.0 + 0.25 * (np.arange(ne) % 4)
+    np.asarray(mesh.nodes, np.float64).tofile(tmp_path / "nodes.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    st.tofile(tmp_path / "sigma_t.f64")
+    subprocess.run([driver, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p)], check=True)
+    n, nfq = map(int, open(tmp_path / "dims.txt").read().split())
+    assert n == (p + 1) ** 2
+
+    def load(name, shape):
+        return np.fromfile(tmp_path / (name + ".f64")).reshape(shape)
+
+    Kxx, Ks, Kyy = (load(k, (ne, n, n)) for k in ("Kxx", "Ks", "Kyy"))
+    Dfx, Dfy = (load(k, (ne, 4, nfq, n)) for k in ("Dfx", "Dfy"))
+    nds = load("nds", (ne, 4, nfq, 2))
+
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, 0.5 * st)
+    assert nfq == len(disc.elems[0].fq_s)
+    for e in range(ne):
+        K = disc.elems[e].stiffness()  # [a][b][i][j] = int dphi_i/da dphi_j/db
+        scale = np.max(np.abs(K))
+        for got, want in ((Kxx[e], -K[0, 0] / st[e]), (Ks[e], -(K[0, 1] + K[1, 0]) / st[e]),
+                          (Kyy[e], -K[1, 1] / st[e])):
+            assert np.max(np.abs(got - want)) <= 1e-12 * scale, e
+            assert np.max(np.abs(got - got.T)) <= 1e-13 * scale, e
+            # rows annihilate constants
+            assert np.max(np.abs(got.sum(axis=1))) <= 1e-13 * scale, e
+        for f in range(4):
+            fd = disc.faces[e][f]
+            gscale = np.max(np.abs(fd["G"]))
+            assert np.max(np.abs(Dfx[e, f] - fd["G"][:, :, 0])) <= 1e-12 * gscale, (e, f)
+            assert np.max(np.abs(Dfy[e, f] - fd["G"][:, :, 1])) <= 1e-12 * gscale, (e, f)
+            assert np.max(np.abs(Dfx[e, f].sum(axis=1))) <= 1e-13 * gscale, (e, f)
+            assert np.max(np.abs(Dfy[e, f].sum(axis=1))) <= 1e-13 * gscale, (e, f)
+            assert np.max(np.abs(nds[e, f] - fd["nds"])) <= 1e-13 * np.max(np.abs(fd["nds"])), (e, f)
