@@ -1,8 +1,10 @@
 // Test driver (CPU): runs the library's host setup on a mesh read from files
-// and writes the right-hand-side operators it builds, so that a test can
-// compare them with the oracle.  Usage: setup_dump DIR NE NNODES M P
-//   in:  DIR/nodes.f64 [nnodes][2], DIR/elem.i32 [ne][(m+1)^2], DIR/sigma_t.f64 [ne]
-//   out: DIR/dims.txt (n nfq), DIR/{Kxx,Ks,Kyy,Dfx,Dfy,nds}.f64
+// and writes the element operators it builds, so that a test can compare them
+// with the oracle.  Usage: setup_dump DIR NE NNODES M P
+//   in:  DIR/nodes.f64 [nnodes][2], DIR/elem.i32 [ne][(m+1)^2], DIR/sigma_t.f64 [ne],
+//        DIR/q.f64 [ne][n] isotropic source per steradian (sigma_s = sigma_t / 2)
+//   out: DIR/dims.txt (n nfq), DIR/{Kxx,Ks,Kyy,Dfx,Dfy,nds,M,Gx,Gy,Adiag,Aoff,Pinv,bfixed}.f64,
+//        DIR/nbr.i32 [ne][4]
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -32,7 +34,7 @@ int main(int argc, char** argv) {
     std::vector<double> nodes((size_t)nn * 2), st(ne), ss(ne), q((size_t)ne * n, 0.0);
     std::vector<int32_t> elem((size_t)ne * (m + 1) * (m + 1));
     if (!read_file(dir + "/nodes.f64", nodes) || !read_file(dir + "/elem.i32", elem) ||
-        !read_file(dir + "/sigma_t.f64", st))
+        !read_file(dir + "/sigma_t.f64", st) || !read_file(dir + "/q.f64", q))
         return 3;
     for (int e = 0; e < ne; ++e) ss[e] = 0.5 * st[e];
     smm::Input in;
@@ -49,6 +51,12 @@ int main(int argc, char** argv) {
     dims << s.n << " " << s.nfq << "\n";
     const bool ok = write_file(dir + "/Kxx.f64", s.Kxx) && write_file(dir + "/Ks.f64", s.Ks) &&
                     write_file(dir + "/Kyy.f64", s.Kyy) && write_file(dir + "/Dfx.f64", s.Dfx) &&
-                    write_file(dir + "/Dfy.f64", s.Dfy) && write_file(dir + "/nds.f64", s.nds);
-    return ok ? 0 : 5;
+                    write_file(dir + "/Dfy.f64", s.Dfy) && write_file(dir + "/nds.f64", s.nds) &&
+                    write_file(dir + "/M.f64", s.M) && write_file(dir + "/Gx.f64", s.Gx) &&
+                    write_file(dir + "/Gy.f64", s.Gy) && write_file(dir + "/Adiag.f64", s.Adiag) &&
+                    write_file(dir + "/Aoff.f64", s.Aoff) && write_file(dir + "/Pinv.f64", s.Pinv) &&
+                    write_file(dir + "/bfixed.f64", s.bfixed);
+    std::ofstream nb(dir + "/nbr.i32", std::ios::binary);
+    nb.write(reinterpret_cast<const char*>(s.nbr.data()), (std::streamsize)(s.nbr.size() * sizeof(int32_t)));
+    return ok && nb ? 0 : 5;
 }
