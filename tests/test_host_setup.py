@@ -1,17 +1,20 @@
 """CPU checks of the host setup of the CUDA path (setup.cpp) against the oracle.
 
-The sweep's element matrices (mass and streaming, Sec. "Transport Discretization"), the IP-SMM
-operator's diagonal and neighbour blocks and their inverses (LHS of Eq. ipsmm)
-and the source part of its right-hand side are compared with the oracle's
-element quadratures and assembled system.  The right-hand-side kernels stream three T-divergence blocks per element
-(K_xx, K_xy + K_yx, K_yy of the volume term -int grad u . (1/sigma_t) div_h T
-of Eq. ipsmm) and the physical basis gradients at the face quadrature points.
-A driver compiled against setup.cpp writes them for seeded curved meshes, and
-each must equal the oracle's own element quadrature (its stiffness integrals
-and face data).  The kernels also rely on both operators annihilating
-constants -- their rows sum to zero because the nodal basis is a partition of
-unity -- when they shift T by its value at an element's first node; that is
-checked here too.
+A driver compiled against setup.cpp writes the element operators it builds
+for seeded curved meshes, and each must equal the oracle's own quadrature or
+assembled system:
+
+- the sweep's mass and streaming matrices (Sec. "Transport Discretization");
+- the IP-SMM operator's diagonal and neighbour blocks and their inverses (LHS
+  of Eq. ipsmm), and the source part of its right-hand side;
+- the operators the right-hand-side kernels stream: three T-divergence blocks
+  per element (K_xx, K_xy + K_yx, K_yy of the volume term
+  -int grad u . (1/sigma_t) div_h T of Eq. ipsmm) and the physical basis
+  gradients at the face quadrature points.
+
+The right-hand-side kernels also rely on the last two annihilating constants
+(their rows sum to zero because the nodal basis is a partition of unity) when
+they shift T by its value at an element's first node; that is checked too.
 """
 import os
 import shutil
