@@ -3,8 +3,9 @@
 // with the oracle.  Usage: setup_dump DIR NE NNODES M P
 //   in:  DIR/nodes.f64 [nnodes][2], DIR/elem.i32 [ne][(m+1)^2], DIR/sigma_t.f64 [ne],
 //        DIR/q.f64 [ne][n] isotropic source per steradian (sigma_s = sigma_t / 2)
-//   out: DIR/dims.txt (n nfq), DIR/{Kxx,Ks,Kyy,Dfx,Dfy,nds,M,Gx,Gy,Adiag,Aoff,Pinv,bfixed}.f64,
-//        DIR/nbr.i32 [ne][4]
+//   out: DIR/dims.txt (n nfq nd nlevels), DIR/{Kxx,Ks,Kyy,Dfx,Dfy,nds,M,Gx,Gy,Adiag,Aoff,Pinv,bfixed,
+//        ox,oy,w}.f64, DIR/{nbr,level,tasks,level_start}.i32, DIR/fdir.i8 [ne][nd][4]
+//   A setup error is printed on stderr and gives exit status 4.
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -20,9 +21,10 @@ static bool read_file(const std::string& path, std::vector<T>& v) {
     return (bool)in;
 }
 
-static bool write_file(const std::string& path, const std::vector<double>& v) {
+template <class T>
+static bool write_file(const std::string& path, const std::vector<T>& v) {
     std::ofstream out(path, std::ios::binary);
-    out.write(reinterpret_cast<const char*>(v.data()), (std::streamsize)(v.size() * sizeof(double)));
+    out.write(reinterpret_cast<const char*>(v.data()), (std::streamsize)(v.size() * sizeof(T)));
     return (bool)out;
 }
 
@@ -48,15 +50,17 @@ int main(int argc, char** argv) {
         return 4;
     }
     std::ofstream dims(dir + "/dims.txt");
-    dims << s.n << " " << s.nfq << "\n";
+    dims << s.n << " " << s.nfq << " " << s.nd << " " << s.nlevels << "\n";
     const bool ok = write_file(dir + "/Kxx.f64", s.Kxx) && write_file(dir + "/Ks.f64", s.Ks) &&
                     write_file(dir + "/Kyy.f64", s.Kyy) && write_file(dir + "/Dfx.f64", s.Dfx) &&
                     write_file(dir + "/Dfy.f64", s.Dfy) && write_file(dir + "/nds.f64", s.nds) &&
                     write_file(dir + "/M.f64", s.M) && write_file(dir + "/Gx.f64", s.Gx) &&
                     write_file(dir + "/Gy.f64", s.Gy) && write_file(dir + "/Adiag.f64", s.Adiag) &&
                     write_file(dir + "/Aoff.f64", s.Aoff) && write_file(dir + "/Pinv.f64", s.Pinv) &&
-                    write_file(dir + "/bfixed.f64", s.bfixed);
-    std::ofstream nb(dir + "/nbr.i32", std::ios::binary);
-    nb.write(reinterpret_cast<const char*>(s.nbr.data()), (std::streamsize)(s.nbr.size() * sizeof(int32_t)));
-    return ok && nb ? 0 : 5;
+                    write_file(dir + "/bfixed.f64", s.bfixed) && write_file(dir + "/ox.f64", s.quad.ox) &&
+                    write_file(dir + "/oy.f64", s.quad.oy) && write_file(dir + "/w.f64", s.quad.w) &&
+                    write_file(dir + "/nbr.i32", s.nbr) && write_file(dir + "/level.i32", s.level) &&
+                    write_file(dir + "/tasks.i32", s.tasks) && write_file(dir + "/level_start.i32", s.level_start) &&
+                    write_file(dir + "/fdir.i8", s.fdir);
+    return ok ? 0 : 5;
 }

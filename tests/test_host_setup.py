@@ -4,6 +4,9 @@ A driver compiled against setup.cpp writes the element operators it builds
 for seeded curved meshes, and each must equal the oracle's own quadrature or
 assembled system:
 
+- the sweep's ordering: ordinates, the inflow/outflow direction of every face
+  (the sign of Omega . n at the face quadrature points), the upwind level of
+  every (element, ordinate) and the task list the sweep kernel walks;
 - the sweep's mass and streaming matrices (Sec. "Transport Discretization");
 - the IP-SMM operator's diagonal and neighbour blocks and their inverses (LHS
   of Eq. ipsmm), and the source part of its right-hand side;
@@ -43,10 +46,7 @@ def driver(tmp_path_factory):
 CASES = [(4, 3, 3, 4, 2), (3, 3, 2, 2, 5), (2, 3, 1, 1, None), (2, 2, 6, 3, 7)]
 
 
-def run_setup(driver, tmp_path, case):
-    """Run the host setup on a seeded curved mesh; returns (mesh, sigma_t, q, loader, n, nfq)."""
-    nx, ny, m, p, seed = case
-    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+def write_inputs(tmp_path, mesh, p):
     ne, n = mesh.n_elem, (p + 1) ** 2
     st = 1.0 + 0.25 * (np.arange(ne) % 4)
     q = np.random.default_rng(3).uniform(0.5, 1.5, (ne, n))
@@ -54,23 +54,31 @@ def run_setup(driver, tmp_path, case):
     np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
     st.tofile(tmp_path / "sigma_t.f64")
     q.tofile(tmp_path / "q.f64")
-    subprocess.run([driver, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p)], check=True)
-    n_out, nfq = map(int, open(tmp_path / "dims.txt").read().split())
-    assert n_out == n
+    return st, q
+
+
+def run_setup(driver, tmp_path, case):
+    """Run the host setup on a seeded curved mesh; returns (mesh, sigma_t, q, loader, dims)."""
+    nx, ny, m, p, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    st, q = write_inputs(tmp_path, mesh, p)
+    subprocess.run([driver, str(tmp_path), str(mesh.n_elem), str(len(mesh.nodes)), str(m), str(p)], check=True)
+    n, nfq, nd, nlevels = map(int, open(tmp_path / "dims.txt").read().split())
+    assert n == (p + 1) ** 2
 
     def load(name, shape, dtype=np.float64):
-        ext = ".i32" if dtype == np.int32 else ".f64"
+        ext = {np.float64: ".f64", np.int32: ".i32", np.int8: ".i8"}[dtype]
         return np.fromfile(tmp_path / (name + ext), dtype=dtype).reshape(shape)
 
-    return mesh, st, q, load, n, nfq
+    return mesh, st, q, load, dict(n=n, nfq=nfq, nd=nd, nlevels=nlevels)
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
 def test_rhs_operators_match_oracle_quadrature(driver, tmp_path, case):
     from oracle.transport import Discretization
     m, p = case[2], case[3]
-    mesh, st, _, load, n, nfq = run_setup(driver, tmp_path, case)
-    ne = mesh.n_elem
+    mesh, st, _, load, dims = run_setup(driver, tmp_path, case)
+    ne, n, nfq = mesh.n_elem, dims["n"], dims["nfq"]
     Kxx, Ks, Kyy = (load(k, (ne, n, n)) for k in ("Kxx", "Ks", "Kyy"))
     Dfx, Dfy = (load(k, (ne, 4, nfq, n)) for k in ("Dfx", "Dfy"))
     nds = load("nds", (ne, 4, nfq, 2))
@@ -101,8 +109,8 @@ def test_sweep_and_moment_operators_match_oracle(driver, tmp_path, case):
     from oracle import closures, ipsmm
     from oracle.transport import Discretization
     m, p = case[2], case[3]
-    mesh, st, q, load, n, nfq = run_setup(driver, tmp_path, case)
-    ne = mesh.n_elem
+    mesh, st, q, load, dims = run_setup(driver, tmp_path, case)
+    ne, n = mesh.n_elem, dims["n"]
     M, Gx, Gy, Ad, Pinv = (load(k, (ne, n, n)) for k in ("M", "Gx", "Gy", "Adiag", "Pinv"))
     Aoff = load("Aoff", (ne, 4, n, n))
     nbr = load("nbr", (ne, 4), np.int32)
@@ -133,3 +141,70 @@ def test_sweep_and_moment_operators_match_oracle(driver, tmp_path, case):
     jin = closures.j_in(disc, None)
     b = ipsmm.assemble_rhs(disc, Q, np.zeros((3, ne, n)), jin, np.zeros_like(jin))
     assert np.max(np.abs(bfixed.ravel() - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("case", CASES + [(6, 5, 2, 1, 9)], ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_sweep_ordering_matches_oracle_upwind_graph(driver, tmp_path, case):
+    """Face directions from the sign of Omega_d . n at every face point; level
+    of (e, d) = 0 without upwind neighbours, else 1 + the largest level of its
+    upwind neighbours (longest path, unique); tasks = all (e, d) sorted by
+    (level, e, d), level_start the first task of each level."""
+    from oracle.transport import Discretization
+    m, p = case[2], case[3]
+    mesh, st, _, load, dims = run_setup(driver, tmp_path, case)
+    ne, nd, nfq, nlev = mesh.n_elem, dims["nd"], dims["nfq"], dims["nlevels"]
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, 0.5 * st)
+    assert nd == disc.nd
+    om = np.stack([load("ox", (nd,)), load("oy", (nd,))], axis=1)
+    assert np.array_equal(om, disc.omega)
+    fdir = load("fdir", (ne, nd, 4), np.int8)
+    level = load("level", (nd, ne), np.int32)
+    tasks = load("tasks", (ne * nd,), np.int32)
+    start = load("level_start", (nlev + 1,), np.int32)
+    for d in range(nd):
+        deps = [[] for _ in range(ne)]
+        for e in range(ne):
+            for f in range(4):
+                a = disc.faces[e][f]["nds"] @ disc.omega[d]
+                want = 1 if np.any(a > 0) else (-1 if np.any(a < 0) else 0)
+                assert fdir[e, d, f] == want, (e, d, f)
+                if disc.nbr[e][f] is not None and np.any(a < 0):
+                    deps[e].append(disc.nbr[e][f][0])
+        for e in disc.upwind_order(d):  # upwind neighbours first
+            want = 1 + max(level[d, u] for u in deps[e]) if deps[e] else 0
+            assert level[d, e] == want, (e, d)
+    assert nlev == level.max() + 1
+    assert np.array_equal(np.sort(tasks), np.arange(ne * nd))
+    e_of, d_of = tasks // nd, tasks % nd
+    key = np.stack([level[d_of, e_of], e_of, d_of], axis=1)
+    assert all(tuple(key[i]) < tuple(key[i + 1]) for i in range(len(key) - 1))
+    assert start[0] == 0 and start[-1] == ne * nd
+    for lv in range(nlev):
+        assert np.all(key[start[lv]:start[lv + 1], 0] == lv)
+
+
+def test_sign_indefinite_face_is_rejected(driver, tmp_path):
+    """Two elements sharing a bowed quadratic face: its normal turns through
+    the direction of some S4 ordinate, which then flows in at some face points
+    and out at others, which is not lagged but rejected: setup fails
+    with that error."""
+    nodes = np.array([[0, 0], [0.5, 0], [1, 0], [0, 0.5], [0.5, 0.5], [1, 0.5], [0, 1], [0.5, 1], [1, 1],
+                      [1.5, 0], [2, 0], [1.5, 0.5], [2, 0.5], [1.5, 1], [2, 1]], float)
+    nodes[5] = [1.25, 0.5]  # middle node of the shared face, pushed to the right
+    elem = np.array([[0, 1, 2, 3, 4, 5, 6, 7, 8], [2, 9, 10, 5, 11, 12, 8, 13, 14]], np.int32)
+
+    class Mesh:
+        n_elem = 2
+
+    mesh = Mesh()
+    mesh.nodes, mesh.elem_nodes = nodes, elem
+    write_inputs(tmp_path, mesh, 1)
+    r = subprocess.run([driver, str(tmp_path), "2", str(len(nodes)), "2", "1"], capture_output=True, text=True)
+    assert r.returncode == 4
+    assert "inflow at some quadrature points and outflow at others" in r.stderr
+    # the oracle rejects it too: across a mixed face each element is upwind of the other
+    from oracle.transport import CycleError, Discretization
+    disc = Discretization(nodes, elem, 2, 1, 4, np.ones(2), 0.5 * np.ones(2))
+    with pytest.raises(CycleError):
+        for d in range(disc.nd):
+            disc.upwind_order(d)
