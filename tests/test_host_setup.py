@@ -18,6 +18,12 @@ assembled system:
 The right-hand-side kernels also rely on the last two annihilating constants
 (their rows sum to zero because the nodal basis is a partition of unity) when
 they shift T by its value at an element's first node; that is checked too.
+
+A second driver builds the multigrid hierarchy of the moment solve's
+preconditioner (amg.cpp; the project's replacement for the AMG-based subspace
+correction of Sec. "Results"), which is checked against its definitions:
+Galerkin products, the vertex-bilinear level, smoothed aggregation, the
+damping estimates and the coarsest inverse.
 """
 import os
 import shutil
@@ -208,3 +214,132 @@ def test_sign_indefinite_face_is_rejected(driver, tmp_path):
     with pytest.raises(CycleError):
         for d in range(disc.nd):
             disc.upwind_order(d)
+
+
+# ---------------------------------------------------------------------------
+# multigrid hierarchy of the moment-system preconditioner (amg.cpp)
+
+@pytest.fixture(scope="module")
+def mg_driver(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = tmp_path_factory.mktemp("mg") / "mg_dump"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", CSRC, os.path.join(ROOT, "tests", "mg_dump.cpp"),
+                    os.path.join(CSRC, "setup.cpp"), os.path.join(CSRC, "amg.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+def _csr(tmp_path, stem, nrow, ncol):
+    import scipy.sparse as sp
+    rp = np.fromfile(tmp_path / (stem + "_rp.i32"), dtype=np.int32)
+    ci = np.fromfile(tmp_path / (stem + "_ci.i32"), dtype=np.int32)
+    v = np.fromfile(tmp_path / (stem + "_v.f64"))
+    return sp.csr_matrix((v, ci, rp), shape=(nrow, ncol)).toarray()
+
+
+# Gauss-Lobatto points of [0, 1], closed forms
+GLL01 = {1: [0.0, 1.0], 2: [0.0, 0.5, 1.0],
+         3: [0.0, (1 - 5 ** -0.5) / 2, (1 + 5 ** -0.5) / 2, 1.0],
+         4: [0.0, (1 - (3 / 7) ** 0.5) / 2, 0.5, (1 + (3 / 7) ** 0.5) / 2, 1.0]}
+
+
+# (nx, ny, m, p, seed, coarse_max): the last two build two aggregation levels
+MG_CASES = [(8, 8, 2, 2, 4, 20), (10, 9, 3, 3, 6, 40), (5, 4, 3, 4, 2, 8), (16, 16, 1, 1, 5, 8), (14, 12, 2, 1, 3, 6)]
+
+
+@pytest.mark.parametrize("case", MG_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_multigrid_hierarchy(mg_driver, tmp_path, case):
+    """Level 1 is the Galerkin product P1^T A P1 of the DG operator with the
+    continuous bilinear functions on the mesh vertices (a DG node takes the
+    bilinear interpolant of its element's corner values); each further level
+    is R A P with R = P^T and P = (I - w D^-1 A) T, T a piecewise-constant
+    aggregation (one 1 per row); the damping factors come from Rayleigh
+    estimates that never exceed the largest eigenvalue of the Jacobi (or
+    element-block Jacobi) preconditioned operator; the coarsest level is
+    inverted."""
+    import scipy.linalg as sla
+    nx, ny, m, p, seed, coarse_max = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n, p1 = mesh.n_elem, (p + 1) ** 2, p + 1
+    write_inputs(tmp_path, mesh, p)
+    subprocess.run([mg_driver, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), str(coarse_max)],
+                   check=True)
+    lines = open(tmp_path / "mg.txt").read().split("\n")
+    nvert, ncoarse, nlev, omega0 = lines[0].split()
+    nvert, ncoarse, nlev, omega0 = int(nvert), int(ncoarse), int(nlev), float(omega0)
+    levels = [dict(zip(("nrow", "omega", "hasP"), (int(a), float(b), int(c))))
+              for a, b, c in (l.split() for l in lines[1:1 + nlev])]
+    f64 = lambda name: np.fromfile(tmp_path / (name + ".f64"))
+    i32 = lambda name: np.fromfile(tmp_path / (name + ".i32"), dtype=np.int32)
+    Ad, Aoff, Pinv = f64("Adiag").reshape(ne, n, n), f64("Aoff").reshape(ne, 4, n, n), f64("Pinv").reshape(ne, n, n)
+    nbr = i32("nbr").reshape(ne, 4)
+    N = ne * n
+    A0 = np.zeros((N, N))
+    for e in range(ne):
+        A0[e * n:(e + 1) * n, e * n:(e + 1) * n] = Ad[e]
+        for f in range(4):
+            if nbr[e, f] >= 0:
+                A0[e * n:(e + 1) * n, nbr[e, f] * n:(nbr[e, f] + 1) * n] += Aoff[e, f]
+    # vertices: the distinct corner control points, numbered in increasing id order
+    cidx = [0, m, m * (m + 1), m * (m + 1) + m]
+    corner_ids = np.asarray(mesh.elem_nodes)[:, cidx]
+    uniq = np.unique(corner_ids)
+    vid = i32("vid").reshape(ne, 4)
+    assert nvert == len(uniq) == (nx + 1) * (ny + 1)
+    assert np.array_equal(vid, np.searchsorted(uniq, corner_ids))
+    vrp, vinc = i32("vrp"), i32("vinc")
+    for v in range(nvert):
+        assert list(vinc[vrp[v]:vrp[v + 1]]) == list(np.flatnonzero(vid.ravel() == v))
+    # bilinear weights of the DG nodes (x fastest)
+    g = np.asarray(GLL01[p])
+    w4 = f64("w4").reshape(n, 4)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    X, Y = X.ravel(), Y.ravel()
+    want = np.stack([(1 - X) * (1 - Y), X * (1 - Y), (1 - X) * Y, X * Y], axis=1)
+    assert np.max(np.abs(w4 - want)) < 1e-15
+    P1 = np.zeros((N, nvert))
+    for e in range(ne):
+        for c in range(4):
+            P1[e * n:(e + 1) * n, vid[e, c]] += w4[:, c]
+    # level-0 block-Jacobi damping from a Rayleigh estimate of lambda_max(Pinv A)
+    Bd = sla.block_diag(*Ad)
+    assert np.max(np.abs(sla.block_diag(*Pinv) @ Bd - np.eye(N))) < 1e-9
+    lam0 = sla.eigh(A0, Bd, eigvals_only=True)[-1]
+    est0 = (4.0 / 3.0) / (1.05 * omega0)
+    assert 0.7 * lam0 <= est0 <= lam0 * (1 + 1e-9), (est0, lam0)
+    A_prev = P1.T @ A0 @ P1
+    for l, L in enumerate(levels, start=1):
+        A = _csr(tmp_path, "L%d_A" % l, L["nrow"], L["nrow"])
+        scale = np.max(np.abs(A))
+        assert np.max(np.abs(A - A_prev)) <= 1e-12 * scale, l
+        assert np.max(np.abs(A - A.T)) <= 1e-12 * scale, l
+        assert np.linalg.eigvalsh(A)[0] > 0, l
+        dinv = f64("L%d_dinv" % l)
+        assert np.array_equal(dinv, 1.0 / np.diag(A)), l
+        lam = np.linalg.eigvalsh(np.sqrt(dinv)[:, None] * A * np.sqrt(dinv)[None, :])[-1]
+        est = (4.0 / 3.0) / (1.05 * L["omega"])
+        assert 0.7 * lam <= est <= lam * (1 + 1e-9), (l, est, lam)
+        if not L["hasP"]:
+            assert l == nlev
+            break
+        nc = levels[l]["nrow"]
+        P = _csr(tmp_path, "L%d_P" % l, L["nrow"], nc)
+        R = _csr(tmp_path, "L%d_R" % l, nc, L["nrow"])
+        assert np.array_equal(R, P.T), l
+        # P = (I - w D^-1 A) T: w from P 1 = 1 - w D^-1 A 1, then T must be an aggregation
+        u = dinv * A.sum(axis=1)
+        k = np.argmax(np.abs(u))
+        w = (1.0 - P.sum(axis=1)[k]) / u[k]
+        S = np.eye(L["nrow"]) - w * dinv[:, None] * A
+        T = np.linalg.solve(S, P)
+        assert np.max(np.abs(T - np.round(T))) < 1e-8, l
+        T = np.round(T)
+        assert set(np.unique(T)) <= {0.0, 1.0} and np.all(T.sum(axis=1) == 1) and np.all(T.sum(axis=0) >= 1), l
+        # the prolongator's damping is a Rayleigh estimate of lambda_max(D^-1 A) too
+        assert 0.7 * lam <= (4.0 / 3.0) / w <= lam * (1 + 1e-9), (l, w, lam)
+        A_prev = R @ A @ P
+    assert ncoarse == levels[-1]["nrow"]
+    assert ncoarse <= coarse_max or nlev >= 2
+    Cinv = f64("coarse_inv").reshape(ncoarse, ncoarse)
+    assert np.max(np.abs(Cinv @ A_prev - np.eye(ncoarse))) < 1e-9
