@@ -72,3 +72,28 @@ def test_element_matrix_identities_curved():
         K = el.stiffness()
         xs = el.V  # unused; check symmetry of stiffness blocks
         assert np.allclose(K[0, 1], K[1, 0].T, atol=1e-14)
+
+
+@pytest.mark.parametrize("m,p,seed", [(2, 2, 4), (3, 3, 9), (2, 4, 1)])
+def test_physical_gradients_on_curved_elements(m, p, seed):
+    """Isoparametric reproduction: with p >= m a physical linear function
+    a . x + c lies in Q_p of every curved element (x(xi) has degree m), so its
+    nodal interpolant's gradient is exactly a at every volume and face point;
+    and the divergence theorem int_K dphi_i/dx_c = oint phi_i n_c ds holds
+    for every basis function (both exact under the element's quadrature)."""
+    from oracle.quadrature import gauss_lobatto
+    mesh = W.structured_mesh(3, 2, m=m, perturb_seed=seed)
+    disc = disc_for(mesh, p, 4, 1.0, 0.5)
+    g, _ = gauss_lobatto(p + 1)
+    XI, ETA = np.meshgrid(g, g, indexing="xy")
+    a = np.array([1.7, -0.6])
+    for e, el in enumerate(disc.elems):
+        xn, _ = el.map(XI.ravel(), ETA.ravel())  # physical DG node positions, x fastest
+        u = xn @ a + 0.3
+        assert np.max(np.abs(el.G.transpose(0, 2, 1) @ u - a)) < 1e-12
+        for f in range(4):
+            Gf = disc.faces[e][f]["G"]
+            assert np.max(np.abs(Gf.transpose(0, 2, 1) @ u - a)) < 1e-12
+        vol = np.einsum("q,qic->ic", el.w * el.J, el.G)
+        surf = sum(disc.faces[e][f]["V"].T @ disc.faces[e][f]["nds"] for f in range(4))
+        assert np.max(np.abs(vol - surf)) < 1e-13

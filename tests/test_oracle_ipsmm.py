@@ -87,3 +87,29 @@ def test_moment_system_mms_order(p, expect):
         x = ipsmm.solve(prob.A, prob.rhs_from_psi(psi)).reshape(disc.ne, disc.n)
         errs.append(disc.l2_error(x, W.mms_phi))
     assert math.log2(errs[-2] / errs[-1]) > expect
+
+
+def test_rhs_tensor_terms_are_the_diffusion_form_for_isotropic_T():
+    """For T = tau phi I, with phi any broken (discontinuous) function that
+    vanishes on the boundary faces, the three T-terms of Eq. ipsmm's
+    right-hand side (volume divergence, face average of div T . n against
+    [u], face average of grad u against [T n]) discretize div((1/sigma_t)
+    div T) = 3 tau div(D grad phi) exactly as the left-hand side's diffusion
+    terms do: they equal -3 tau times its penalty-free form (sigma_a = 0 here,
+    element-wise sigma_t)."""
+    from oracle.fem import face_nodes
+    mesh = W.structured_mesh(4, 3, m=2, perturb_seed=6)
+    ne = mesh.n_elem
+    st = 1.0 + 0.5 * (np.arange(ne) % 3)
+    disc = disc_for(mesh, 2, 4, st, st)
+    rng = np.random.default_rng(5)
+    phi = rng.uniform(-1.0, 1.0, (ne, disc.n))
+    for (e, f) in disc.bfaces:
+        phi[e, face_nodes(disc.p, f)] = 0.0
+    tau = 0.7
+    A0 = ipsmm.assemble_lhs(disc, kappa_scale=0.0)
+    nb, nfq = len(disc.bfaces), len(disc.elems[0].fq_s)
+    z = np.zeros((nb, nfq))
+    b = ipsmm.assemble_rhs(disc, np.zeros((3, ne, disc.n)), np.stack([tau * phi, 0.0 * phi, tau * phi]), z, z)
+    want = -3.0 * tau * (A0 @ phi.ravel())
+    assert np.max(np.abs(b - want)) <= 1e-12 * np.max(np.abs(want))
