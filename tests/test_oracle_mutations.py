@@ -91,25 +91,36 @@ def run_pins(copy_root, tests):
     return r.returncode, r.stdout + r.stderr
 
 
-def planted_copy(tmp_path, fname=None, old=None, new=None):
-    dst = tmp_path / "oracle"
+def planted_copy(root, fname=None, old=None, new=None):
+    dst = root / "oracle"
     shutil.copytree(os.path.join(ROOT, "oracle"), dst, ignore=shutil.ignore_patterns("__pycache__"))
     if fname is not None:
         path = dst / fname
         src = path.read_text()
         assert src.count(old) == 1, (fname, old)
         path.write_text(src.replace(old, new))
-    return tmp_path
+    return root
 
 
-def test_unmodified_copy_passes(tmp_path):
-    rc, out = run_pins(planted_copy(tmp_path), T_QUAD + T_CLOS + T_SWEEP)
+@pytest.fixture(scope="module")
+def results(tmp_path_factory):
+    """Every case's (exit status, output), the subprocesses run concurrently;
+    key None is the unmodified copy."""
+    from concurrent.futures import ThreadPoolExecutor
+    cases = [(None, None, None, None, T_QUAD + T_CLOS + T_SWEEP)] + MUTATIONS
+    roots = [planted_copy(tmp_path_factory.mktemp("copy"), *c[1:4]) for c in cases]
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as pool:
+        outs = list(pool.map(run_pins, roots, [c[4] for c in cases]))
+    return {c[0]: o for c, o in zip(cases, outs)}
+
+
+def test_unmodified_copy_passes(results):
+    rc, out = results[None]
     assert rc == 0, out[-2000:]
 
 
-@pytest.mark.parametrize("mutation", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_is_caught(tmp_path, mutation):
-    name, fname, old, new, tests = mutation
-    rc, out = run_pins(planted_copy(tmp_path, fname, old, new), tests)
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(results, name):
+    rc, out = results[name]
     # 1: some pin failed (not 0: all passed; not 2..5: the copy did not even load or collect)
     assert rc == 1, (name, rc, out[-2000:])
