@@ -70,6 +70,13 @@ MUTATIONS = [
     ("fixed_point_moment_slice", SMM, "T = closures.nodal_moments(self.disc, psi)[3:6]",
      "T = closures.nodal_moments(self.disc, psi)[2:5]",
      ["tests/test_oracle_smm.py::test_smm_approaches_sn_at_order_p_plus_1"]),
+    ("ip_marshak_term_halved", IP, 'add(fd["V"].T @ ((E * ds)[:, None] * fd["V"]), e * n, e * n)',
+     'add(fd["V"].T @ ((0.5 * ds)[:, None] * fd["V"]), e * n, e * n)', T_IP),
+    ("boundary_sum_without_abs", CL, "a = np.abs(nhat @ disc.omega.T)", "a = nhat @ disc.omega.T", T_CLOS),
+    ("gauss_legendre_weights", Q, "leggauss(n)\n    return 0.5 * (x + 1.0), 0.5 * w",
+     "leggauss(n)\n    return 0.5 * (x + 1.0), w", T_QUAD),
+    ("source_current_components_swapped", CL, 'np.einsum("d,den->en", disc.wq * disc.omega[:, 0], q)',
+     'np.einsum("d,den->en", disc.wq * disc.omega[:, 1], q)', T_IP + ["tests/test_oracle_smm.py"]),
     ("cnn_upsampling_adjoint", CNN, ".sum(axis=(3, 5))", ".mean(axis=(3, 5))", ["tests/test_oracle_cnn.py"]),
     ("cnn_relu_mask", CNN, 'g5 = g5 * (c["a5"] > 0)', 'g5 = g5 * (c["a4"].mean() > 0)',
      ["tests/test_oracle_cnn.py"]),
