@@ -1,0 +1,103 @@
+"""The IP-SMM right-hand-side kernels of moments.cu, run on the CPU, against
+the oracle's right-hand side (Eq. ipsmm).
+
+The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
+helper and the FP32-pair arithmetic of dfloat.cuh) is taken from the CUDA
+files as text and compiled for the host with host_kernel_shim.h, which runs
+every CUDA thread of a block as a std::thread with a barrier for
+__syncthreads; rhs_emu.cpp feeds it the operators of the library's host
+setup in the library's device layouts and launch shapes.  This checks the
+kernels' indexing, shared-memory phases and pair arithmetic without a GPU;
+the GPU parity tests check the same kernels on the device.  T carries jumps
+across faces (smooth plus seeded noise) so that every face term counts.
+"""
+import os
+import re
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import smm_workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2304_07386_gb300", "csrc")
+
+
+def extract(src, signature):
+    """The definition starting at `signature` (with a template line just above
+    it), through its closing brace."""
+    i = src.index(signature)
+    line_start = src.rfind("\n", 0, i - 1) + 1
+    if src.startswith("template", line_start):
+        i = line_start
+    depth, k = 0, src.index("{", i)
+    while True:
+        depth += {"{": 1, "}": -1}.get(src[k], 0)
+        if depth == 0:
+            return src[i:k + 1]
+        k += 1
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("rhs_emu")
+    moments = open(os.path.join(CSRC, "moments.cu")).read()
+    dfloat = open(os.path.join(CSRC, "dfloat.cuh")).read()
+    body = dfloat[dfloat.index("namespace smm {") + len("namespace smm {"):dfloat.rindex("}")]
+    parts = [body,
+             extract(moments, "__device__ __forceinline__ void stage_T("),
+             extract(moments, "__global__ void rhs_trace_kernel("),
+             extract(moments, "__global__ void rhs_assemble_kernel(")]
+    inc = "\n".join(parts)
+    n_shared = len(re.findall(r"extern __shared__ float2 (\w+)\[\];", inc))
+    assert n_shared == 2
+    inc = re.sub(r"extern __shared__ float2 (\w+)\[\];", r"float2* \1 = (float2*)emu_dynamic_smem;", inc)
+    (d / "rhs_kernels.inc").write_text(inc)
+    exe = d / "rhs_emu"
+    subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
+                    os.path.join(ROOT, "tests"), "-I", CSRC, os.path.join(ROOT, "tests", "rhs_emu.cpp"),
+                    os.path.join(CSRC, "setup.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+# (nx, ny, m, p, seed): every element size the kernels are compiled for, curved maps, a one-element mesh
+CASES = [(3, 2, 1, 1, None), (3, 3, 2, 2, 4), (2, 3, 3, 3, 7), (3, 2, 3, 4, 2), (1, 1, 1, 2, None), (2, 2, 6, 4, 5)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_rhs_kernels_match_oracle(emu, tmp_path, case):
+    from oracle import closures, ipsmm
+    from oracle.transport import Discretization
+    nx, ny, m, p, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n = mesh.n_elem, (p + 1) ** 2
+    st = 1.0 + 0.25 * (np.arange(ne) % 4)
+    rng = np.random.default_rng(17)
+    q = rng.uniform(0.5, 1.5, (ne, n))
+    pos = W.dg_node_positions(mesh, p)
+    x, y = pos[:, :, 0], pos[:, :, 1]
+    T = np.stack([np.sin(2 * x + 1) * np.cos(1.5 * y), 0.5 * np.cos(2 * x - y), 0.8 * np.sin(x + 2 * y) + 0.3])
+    T = T + 0.1 * rng.standard_normal(T.shape)
+    mom = np.concatenate([rng.uniform(0.5, 1.5, (3, ne, n)), T])
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, 0.5 * st)
+    nfq = len(disc.elems[0].fq_s)
+    beta = rng.uniform(-0.2, 0.2, (len(disc.bfaces), nfq))
+    np.asarray(mesh.nodes, np.float64).tofile(tmp_path / "nodes.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    st.tofile(tmp_path / "sigma_t.f64")
+    q.tofile(tmp_path / "q.f64")
+    mom.tofile(tmp_path / "mom.f64")
+    beta.tofile(tmp_path / "beta.f64")
+    subprocess.run([emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p)], check=True, timeout=300)
+    n_out, nfq_out, nb_out = map(int, open(tmp_path / "dims.txt").read().split())
+    assert (n_out, nfq_out, nb_out) == (n, nfq, len(disc.bfaces))
+    rhs = np.fromfile(tmp_path / "rhs.f64")
+    Q = closures.source_moments(disc, np.broadcast_to(q, (disc.nd,) + q.shape))
+    jin = closures.j_in(disc, None)
+    b = ipsmm.assemble_rhs(disc, Q, T, jin, beta)
+    assert np.max(np.abs(rhs - b)) <= 1e-12 * np.max(np.abs(b)), np.max(np.abs(rhs - b)) / np.max(np.abs(b))
