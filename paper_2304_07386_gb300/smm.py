@@ -139,6 +139,18 @@ def _devptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _devbuf(t, count, what):
+    """_devptr of a buffer that must hold exactly count elements: the C calls
+    take plain pointers, so a short buffer would be read or written past its
+    end on the device."""
+    if t is None:
+        return None
+    ptr = _devptr(t)
+    if t.numel() != count:
+        raise ValueError(f"{what}: expected {count} elements, got {t.numel()}")
+    return ptr
+
+
 def smm_default_options() -> smm_options:
     o = smm_options()
     load_library().smm_default_options(C.byref(o))
@@ -162,6 +174,7 @@ class Handle:
     def __init__(self, ptr, stream_keepalive=None):
         self.ptr = ptr
         self._keep = stream_keepalive
+        self._info = None
 
     def __del__(self):
         try:
@@ -178,6 +191,16 @@ class Handle:
         i = smm_info()
         _check(load_library().smm_get_info(self.ptr, C.byref(i)))
         return i
+
+    def sizes(self) -> smm_info:
+        """info(), fetched once (the sizes of a handle never change)."""
+        if self._info is None:
+            self._info = self.info()
+        return self._info
+
+    def n_phi(self) -> int:
+        i = self.sizes()
+        return i.n_elem * i.n_dof_elem
 
 
 def smm_create(nodes, elem_nodes, geom_order, p, sn_order, sigma_t, sigma_s, q, source_kind=None,
@@ -212,31 +235,38 @@ def smm_create(nodes, elem_nodes, geom_order, p, sn_order, sigma_t, sigma_s, q, 
 
 
 def smm_sweep(h: Handle, phi=None):
-    _check(load_library().smm_sweep(h.ptr, _devptr(phi)))
+    _check(load_library().smm_sweep(h.ptr, _devbuf(phi, h.n_phi(), "phi")))
+
+
+def _moment_bufs(h: Handle, moments, beta):
+    i = h.sizes()
+    return (_devbuf(moments, 6 * i.n_elem * i.n_dof_elem, "moments"),
+            _devbuf(beta, i.n_bface * i.n_fq, "beta"))
 
 
 def smm_moments(h: Handle, moments=None, beta=None):
-    _check(load_library().smm_moments(h.ptr, _devptr(moments), _devptr(beta)))
+    _check(load_library().smm_moments(h.ptr, *_moment_bufs(h, moments, beta)))
 
 
 def smm_set_moments(h: Handle, moments, beta=None):
-    _check(load_library().smm_set_moments(h.ptr, _devptr(moments), _devptr(beta)))
+    _check(load_library().smm_set_moments(h.ptr, *_moment_bufs(h, moments, beta)))
 
 
 def smm_get_psi(h: Handle, psi):
-    _check(load_library().smm_get_psi(h.ptr, _devptr(psi)))
+    _check(load_library().smm_get_psi(h.ptr, _devbuf(psi, h.sizes().n_angular, "psi")))
 
 
 def smm_moment_solve(h: Handle, phi) -> int:
     it = C.c_int32(0)
-    _check(load_library().smm_moment_solve(h.ptr, _devptr(phi), C.byref(it)))
+    _check(load_library().smm_moment_solve(h.ptr, _devbuf(phi, h.n_phi(), "phi"), C.byref(it)))
     return it.value
 
 
 def smm_iterate(h: Handle, phi, tol: float, max_outer: int = 200, relative: bool = False, raise_on_error=True):
     """Returns (status, stats dict)."""
     st = smm_stats()
-    rc = load_library().smm_iterate(h.ptr, tol, int(relative), max_outer, _devptr(phi), C.byref(st))
+    rc = load_library().smm_iterate(h.ptr, tol, int(relative), max_outer, _devbuf(phi, h.n_phi(), "phi"),
+                                    C.byref(st))
     if raise_on_error:
         _check(rc)
     return rc, st.as_dict()
@@ -256,11 +286,15 @@ def smm_block_pcg_noalloc(diag_blocks, off_blocks, nbr, pinv_blocks, b, x, tol=1
     n_elem, n = int(diag_blocks.shape[0]), int(diag_blocks.shape[1])
     if not (nbr.is_cuda and nbr.is_contiguous() and nbr.dtype == torch.int32):
         raise ValueError("nbr must be a contiguous CUDA int32 tensor")
+    if nbr.numel() != 4 * n_elem:
+        raise ValueError(f"nbr: expected {4 * n_elem} elements, got {nbr.numel()}")
+    ptrs = (_devbuf(diag_blocks, n_elem * n * n, "diag_blocks"), _devbuf(off_blocks, 4 * n_elem * n * n, "off_blocks"),
+            C.c_void_p(nbr.data_ptr()), _devbuf(pinv_blocks, n_elem * n * n, "pinv_blocks"),
+            _devbuf(b, n_elem * n, "b"), _devbuf(x, n_elem * n, "x"))
     s = stream if stream is not None else torch.cuda.current_stream()
     it = C.c_int32(0)
-    _check(load_library().smm_block_pcg_noalloc(n_elem, n, _devptr(diag_blocks), _devptr(off_blocks),
-                                                C.c_void_p(nbr.data_ptr()), _devptr(pinv_blocks), _devptr(b),
-                                                _devptr(x), tol, max_iters, C.c_void_p(s.cuda_stream), C.byref(it)))
+    _check(load_library().smm_block_pcg_noalloc(n_elem, n, *ptrs, tol, max_iters, C.c_void_p(s.cuda_stream),
+                                                C.byref(it)))
     return it.value
 
 
@@ -289,10 +323,12 @@ class Batch:
         return dict(grid=g.value, block=b.value, tuned_ms=ms.value, n_tasks=n.value)
 
 
-def _ptr_array(tensors):
+def _ptr_array(handles, tensors):
+    if len(tensors) != len(handles):
+        raise ValueError(f"expected {len(handles)} buffers, got {len(tensors)}")
     arr = (C.c_void_p * len(tensors))()
-    for i, t in enumerate(tensors):
-        arr[i] = None if t is None else _devptr(t).value
+    for i, (h, t) in enumerate(zip(handles, tensors)):
+        arr[i] = None if t is None else _devbuf(t, h.n_phi(), "phi[%d]" % i).value
     return arr
 
 
@@ -304,21 +340,23 @@ def smm_batch_create(handles) -> Batch:
 
 
 def smm_batch_sweep(b: Batch, phis=None):
-    arr = _ptr_array(phis if phis is not None else [None] * len(b.handles))
+    arr = _ptr_array(b.handles, phis if phis is not None else [None] * len(b.handles))
     _check(load_library().smm_batch_sweep(b.ptr, arr))
 
 
 def smm_batch_iterate(b: Batch, phis, tol: float, max_outer: int = 200, relative: bool = False):
-    arr = _ptr_array(phis)
+    arr = _ptr_array(b.handles, phis)
     st = (smm_stats * len(phis))()
     rc = load_library().smm_batch_iterate(b.ptr, tol, int(relative), max_outer, arr, st)
     _check(rc)
     return [s.as_dict() for s in st]
 
 
-def _fdev(t):
+def _fdev(t, count=None, what="buffer"):
     if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"):
         raise ValueError("network buffers must be contiguous CUDA float32 tensors")
+    if count is not None and t.numel() != count:
+        raise ValueError(f"{what}: expected {count} elements, got {t.numel()}")
     return C.c_void_p(t.data_ptr())
 
 
@@ -350,18 +388,27 @@ class Guess:
             load_library().smm_guess_destroy(self.ptr)
             self.ptr = None
 
+    def _io(self, x, y, what):
+        """(batch, input pointer, output/target pointer): inputs [batch][3][H][W],
+        outputs and targets [batch][n_out][H][W], batch <= max_batch."""
+        h, w, n_out = self.shape
+        batch = int(x.shape[0])
+        if not 0 < batch <= self.max_batch:
+            raise ValueError(f"batch {batch} outside 1..{self.max_batch}")
+        return batch, _fdev(x, batch * 3 * h * w, "inputs"), _fdev(y, batch * n_out * h * w, what)
+
     def forward(self, x, out):
-        _check(load_library().smm_guess_forward(self.ptr, x.shape[0], _fdev(x), _fdev(out)))
+        _check(load_library().smm_guess_forward(self.ptr, *self._io(x, out, "outputs")))
 
     def train_step(self, x, target, lr):
         loss = C.c_float(0.0)
-        _check(load_library().smm_guess_train_step(self.ptr, x.shape[0], _fdev(x), _fdev(target), lr, C.byref(loss)))
+        _check(load_library().smm_guess_train_step(self.ptr, *self._io(x, target, "targets"), lr, C.byref(loss)))
         return loss.value
 
     def gradients(self, x, target):
         g = np.zeros(self.n_params, dtype=np.float32)
         loss = C.c_float(0.0)
-        _check(load_library().smm_guess_gradients(self.ptr, x.shape[0], _fdev(x), _fdev(target),
+        _check(load_library().smm_guess_gradients(self.ptr, *self._io(x, target, "targets"),
                                                   g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
         return loss.value, g
 
@@ -372,4 +419,6 @@ class Guess:
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.n_params:
+            raise ValueError(f"params: expected {self.n_params} values, got {p.size}")
         _check(load_library().smm_guess_set_params(self.ptr, p.ctypes.data_as(C.POINTER(C.c_float))))

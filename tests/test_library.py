@@ -90,3 +90,49 @@ def test_default_options(lib):
     assert o.mg_smoother == S.SMM_SMOOTHER_CHEBYSHEV and o.mg_smooth_steps == 3
     assert o.cg_device_loop == 1 and o.sweep_tiles == 1 and o.negative_flux_fixup == 0
     assert o.moment_discretization == S.SMM_MOMENT_IP
+
+
+class _FakeDeviceBuffer:
+    """Just enough of a CUDA float64 tensor for the binding's pointer checks
+    (no device is touched: only the checks before a C call run)."""
+
+    def __init__(self, numel, dtype="torch.float64"):
+        self._numel, self.dtype, self.is_cuda = numel, dtype, True
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._numel
+
+    def data_ptr(self):
+        return 4096
+
+
+class _FakeHandle:
+    def __init__(self, n_phi):
+        self._n = n_phi
+
+    def n_phi(self):
+        return self._n
+
+
+def test_binding_rejects_buffers_of_the_wrong_size():
+    """The C calls take bare device pointers, so the binding checks each
+    buffer's element count against the layout the header states before the
+    call: a short buffer would be read or written past its end."""
+    from paper_2304_07386_gb300 import smm as S
+    assert S._devbuf(None, 10, "phi") is None
+    assert S._devbuf(_FakeDeviceBuffer(10), 10, "phi").value == 4096
+    for bad in (9, 11):
+        with pytest.raises(ValueError, match="phi"):
+            S._devbuf(_FakeDeviceBuffer(bad), 10, "phi")
+    with pytest.raises(ValueError):
+        S._devbuf(_FakeDeviceBuffer(10, "torch.float32"), 10, "phi")
+    hs = [_FakeHandle(8), _FakeHandle(12)]
+    arr = S._ptr_array(hs, [_FakeDeviceBuffer(8), None])
+    assert arr[0] == 4096 and arr[1] is None
+    with pytest.raises(ValueError, match=r"phi\[1\]"):
+        S._ptr_array(hs, [_FakeDeviceBuffer(8), _FakeDeviceBuffer(8)])
+    with pytest.raises(ValueError, match="expected 2 buffers"):
+        S._ptr_array(hs, [_FakeDeviceBuffer(8)])
