@@ -209,8 +209,10 @@ smm_status smm_quadrature(int32_t sn_order, double* omega_out, double* w_out, in
  *     SMM_INFLOW_NODAL: inflow host [n_ord][n_bface][p+1], psibar at the face
  *     nodal points in increasing s (used only where the ordinate enters).
  *   opt: NULL for defaults.
- * Errors: INVALID_ARG, MESH (J <= 0 at a quadrature point, a face shared by
- * more than two elements), CYCLE (see above), OOM, CUDA. */
+ * Errors: INVALID_ARG (also when n_elem times the ordinates, the control
+ * points or the dofs per element exceeds 2^31 - 1: those ids are 32-bit),
+ * MESH (J <= 0 at a quadrature point, a face shared by more than two
+ * elements), CYCLE (see above), OOM, CUDA. */
 smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order,
                       const double* sigma_t, const double* sigma_s,
                       int32_t source_kind, const double* q,
@@ -274,7 +276,8 @@ typedef struct smm_batch_ctx* smm_batch;
 /* handles: n problems created with the same sweep_precision, sweep_solver,
  * device and stream; they must outlive the batch.  Creation runs a few
  * sweeps with varphi = 0 to tune the launch (the handles' sweep state
- * changes as by smm_sweep).  Errors: INVALID_ARG, OOM, CUDA, DEVICE_TIMEOUT. */
+ * changes as by smm_sweep).  Errors: INVALID_ARG (also for more than
+ * 2^31 - 1 element-ordinate tasks in all), OOM, CUDA, DEVICE_TIMEOUT. */
 smm_status smm_batch_create(int32_t n, const smm_handle* handles, smm_batch* out);
 
 /* Chosen launch shape and the tuned time of one batched sweep (ms). */

@@ -1252,6 +1252,9 @@ smm_status smm_batch_create(int32_t n, const smm_handle* handles, smm_batch* out
         if (handles[i]->stream != h0->stream || handles[i]->device != h0->device)
             return fail(SMM_ERR_INVALID_ARG, "batched problems must share the device and the stream");
     }
+    long long total = 0;  // merged (problem, task) list is indexed with 32-bit integers
+    for (int i = 0; i < n; ++i) total += handles[i]->ntask;
+    if (total > (long long)INT32_MAX) return fail(SMM_ERR_INVALID_ARG, "batch too large: more than 2^31 - 1 tasks");
     auto* b = new smm_batch_ctx();
     auto bail = [&](smm_status st, const std::string& msg) { delete b; return fail(st, msg); };
     b->hs.assign(handles, handles + n);

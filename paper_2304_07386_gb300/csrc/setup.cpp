@@ -18,6 +18,7 @@
 #include "setup.hpp"
 
 #include <algorithm>
+#include <cstdint>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -427,6 +428,12 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
     s.nq = in.p + in.m + 1; s.nqv = s.nq * s.nq; s.nfq = s.nq; s.nd = s.quad.nd;
     const int ne = s.ne, n = s.n, p1 = s.p1, nd = s.nd, nfq = s.nfq, m1 = in.m + 1;
     const int nc = m1 * m1;
+    // (element, ordinate) task ids e * nd + d, control point slots e * nc + k and
+    // unknown ids e * n + i are 32-bit integers on the host and the device
+    if ((long long)ne * std::max(std::max(nd, nc), n) > (long long)INT32_MAX) {
+        err = "mesh too large: n_elem times the ordinates, control points or dofs per element exceeds 2^31 - 1";
+        return 1;
+    }
     for (int e = 0; e < ne; ++e) {
         if (!(in.sigma_t[e] > 0.0) || in.sigma_s[e] < 0.0 || in.sigma_s[e] > in.sigma_t[e]) {
             err = "need sigma_t > 0 and 0 <= sigma_s <= sigma_t";

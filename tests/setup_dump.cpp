@@ -6,6 +6,7 @@
 //   out: DIR/dims.txt (n nfq nd nlevels), DIR/{Kxx,Ks,Kyy,Dfx,Dfy,nds,M,Gx,Gy,Adiag,Aoff,Pinv,bfixed,
 //        ox,oy,w}.f64, DIR/{nbr,level,tasks,level_start}.i32, DIR/fdir.i8 [ne][nd][4]
 //   A setup error is printed on stderr and gives exit status 4.
+//   setup_dump --size-check NE M P SN: see size_check below.
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -28,7 +29,28 @@ static bool write_file(const std::string& path, const std::vector<T>& v) {
     return (bool)out;
 }
 
+// setup_dump --size-check NE M P SN: build_setup on NE elements whose arrays
+// are never read (one-element stand-ins); exit status 4 with the message on
+// stderr when the setup rejects the size before it touches them.
+static int size_check(int ne, int m, int p, int sn) {
+    std::vector<double> one(1, 1.0);
+    std::vector<int32_t> zero(1, 0);
+    smm::Input in;
+    in.ne = ne; in.m = m; in.p = p; in.sn = sn; in.n_nodes = 1;
+    in.nodes = one.data(); in.elem_nodes = zero.data(); in.sigma_t = one.data(); in.sigma_s = one.data();
+    in.q = one.data();
+    smm::Setup s;
+    std::string err;
+    if (smm::build_setup(in, s, err)) {
+        std::fprintf(stderr, "%s\n", err.c_str());
+        return 4;
+    }
+    return 0;
+}
+
 int main(int argc, char** argv) {
+    if (argc == 6 && std::string(argv[1]) == "--size-check")
+        return size_check(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]));
     if (argc != 6) return 2;
     const std::string dir = argv[1];
     const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);

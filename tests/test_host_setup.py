@@ -216,6 +216,21 @@ def test_sign_indefinite_face_is_rejected(driver, tmp_path):
             disc.upwind_order(d)
 
 
+@pytest.mark.parametrize("ne,m,p,sn", [
+    (2**31 // 40 + 1, 1, 1, 8),   # (element, ordinate) task ids: 40 ordinates
+    (2**31 // 49 + 1, 6, 1, 2),   # control point slots: 49 per element at geometry order 6
+    (2**31 // 25 + 1, 1, 4, 2),   # unknown ids: 25 dofs per element at p = 4
+])
+def test_sizes_beyond_32_bit_indexes_are_rejected(driver, ne, m, p, sn):
+    """Task ids, control point slots and unknown ids are 32-bit integers on the
+    host and in the kernels: a mesh whose element count times any of them
+    passes 2^31 - 1 is rejected before its arrays are read."""
+    r = subprocess.run([driver, "--size-check", str(ne), str(m), str(p), str(sn)], capture_output=True, text=True,
+                       timeout=60)
+    assert r.returncode == 4, (r.returncode, r.stderr)
+    assert "mesh too large" in r.stderr
+
+
 # ---------------------------------------------------------------------------
 # multigrid hierarchy of the moment-system preconditioner (amg.cpp)
 
