@@ -333,6 +333,9 @@ def run_ours(args) -> None:
                               "(plus the per-sweep source kernel)", "sweep_kernel", 1),
         "moments": entry(mom_bytes, ms_mom, "moments_df_kernel + beta_kernel", "moments", 1),
     }
+    rooflines["cg_iteration"]["traffic_note"] = (
+        "ncu DRAM bytes of the 11 kernels, captured before the direction update's launch grid changed from a "
+        "grid-stride loop to one thread per unknown (same kernel code, each unknown read and written once either way)")
     # dominant: the largest device time per step
     dom = max(rooflines, key=lambda k: rooflines[k]["ms"] * rooflines[k]["launches_per_step"])
     roof = dict(rooflines[dom])
