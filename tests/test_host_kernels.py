@@ -1,5 +1,7 @@
 """The IP-SMM right-hand-side kernels of moments.cu, run on the CPU, against
-the oracle's right-hand side (Eq. ipsmm).
+the oracle's right-hand side (Eq. ipsmm); and the angular-moment and boundary
+correction kernels of the same file against the oracle's closures (Eqs.
+correction_tensor_disc, bdr_correction_factor_disc).
 
 The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
 helper and the FP32-pair arithmetic of dfloat.cuh) is taken from the CUDA
@@ -103,3 +105,78 @@ def test_rhs_kernels_match_oracle(emu, tmp_path, case):
     jin = closures.j_in(disc, None)
     b = ipsmm.assemble_rhs(disc, Q, T, jin, beta)
     assert np.max(np.abs(rhs - b)) <= 1e-12 * np.max(np.abs(b)), np.max(np.abs(rhs - b)) / np.max(np.abs(b))
+
+
+# ---------------------------------------------------------------------------
+# angular moments and the boundary correction (moments_kernel,
+# moments_df_kernel, beta_kernel) against the oracle's closures
+
+@pytest.fixture(scope="module")
+def moments_emu(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("moments_emu")
+    moments = open(os.path.join(CSRC, "moments.cu")).read()
+    dfloat = open(os.path.join(CSRC, "dfloat.cuh")).read()
+    body = dfloat[dfloat.index("namespace smm {") + len("namespace smm {"):dfloat.rindex("}")]
+    parts = [body,
+             extract(moments, "__global__ void __launch_bounds__(256) moments_kernel("),
+             extract(moments, "__global__ void __launch_bounds__(256) moments_df_kernel("),
+             extract(moments, "__global__ void beta_kernel(")]
+    (d / "moments_kernels.inc").write_text("\n".join(parts))
+    exe = d / "moments_emu"
+    subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
+                    os.path.join(ROOT, "tests"), "-I", CSRC, os.path.join(ROOT, "tests", "moments_emu.cpp"),
+                    os.path.join(CSRC, "setup.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+# (nx, ny, m, p, S_N, seed): every element size, S2 to S12 (fewer and more
+# ordinates than a warp's lanes), curved maps, a one-element mesh
+MOMENT_CASES = [(3, 2, 1, 1, 4, None), (2, 3, 2, 2, 8, 4), (3, 3, 3, 3, 12, 7), (2, 2, 3, 4, 8, 2),
+                (1, 1, 1, 2, 2, None)]
+
+
+@pytest.mark.parametrize("case", MOMENT_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d_S%d" % c[:5])
+def test_moment_kernels_match_oracle(moments_emu, tmp_path, case):
+    from oracle import closures
+    from oracle.transport import Discretization
+    nx, ny, m, p, sn, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n = mesh.n_elem, (p + 1) ** 2
+    st = np.ones(ne)
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, sn, st, 0.5 * st)
+    rng = np.random.default_rng(23)
+    pos = W.dg_node_positions(mesh, p)
+    # an anisotropic, spatially varying psi [nd][ne][n] with seeded noise, so that
+    # every moment and every boundary sum is nonzero
+    om = disc.omega
+    psi = (1.0 + 0.5 * om[:, 0, None, None] * np.sin(2 * pos[None, :, :, 0])
+           + 0.3 * om[:, 1, None, None] ** 2 * np.cos(pos[None, :, :, 1])
+           + 0.2 * rng.uniform(0.0, 1.0, (disc.nd, ne, n)))
+    np.asarray(mesh.nodes, np.float64).tofile(tmp_path / "nodes.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    st.tofile(tmp_path / "sigma_t.f64")
+    np.ones((ne, n)).tofile(tmp_path / "q.f64")
+    np.ascontiguousarray(psi.transpose(1, 0, 2)).tofile(tmp_path / "psi.f64")
+    subprocess.run([moments_emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), str(sn)],
+                   check=True, timeout=300)
+    n_o, nd_o, nfq_o, nb_o = map(int, open(tmp_path / "dims.txt").read().split())
+    mom_ref = closures.nodal_moments(disc, psi)
+    beta_ref = closures.beta(disc, psi)
+    assert (n_o, nd_o, nb_o) == (n, disc.nd, len(disc.bfaces)) and beta_ref.shape == (nb_o, nfq_o)
+    scale = np.max(np.abs(mom_ref))
+    # FP64 sums: rounding only.  Pair sums: each of the nd pair multiply-adds
+    # leaves the float correction term an error of about 2^-48 of the sum.
+    for name, tol in (("mom", 1e-13), ("mom_df", 4 * disc.nd * 2.0 ** -48)):
+        got = np.fromfile(tmp_path / f"{name}.f64").reshape(6, ne, n)
+        assert np.max(np.abs(got - mom_ref)) <= tol * scale, (name, np.max(np.abs(got - mom_ref)) / scale)
+    # beta is a difference of terms of the size of phi (zero for S2, whose
+    # ordinates all have the same |Omega.n| on the straight boundary)
+    beta = np.fromfile(tmp_path / "beta.f64").reshape(nb_o, nfq_o)
+    assert np.max(np.abs(beta - beta_ref)) <= 1e-13 * scale
+    if sn == 2:
+        assert np.max(np.abs(beta_ref)) <= 1e-13 * scale
+    else:
+        assert np.max(np.abs(beta_ref)) > 1e-3 * scale
