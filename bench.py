@@ -96,6 +96,54 @@ def run_oracle_child(seconds: float, nx: int) -> dict:
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (x86: "model name"; Arm: implementer and part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    fields = {}
+    for line in info:
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return f"Arm implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return "unknown"
+
+
+def run_oracle_all_cores(seconds: float, nx: int, cores: int | None = None) -> dict:
+    """The same oracle sample on every host core at once: one single-threaded
+    child per core, each timing its own copy; the rates add up (independent
+    problems, as replicas)."""
+    if cores is None:
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_rate(%f, %d)))" % (ROOT, seconds, nx))
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                              text=True, env=env) for _ in range(cores)]
+    rates, err = [], None
+    for pr in procs:
+        try:
+            out, e = pr.communicate(timeout=900)
+        except subprocess.TimeoutExpired:
+            pr.kill()
+            out, e = pr.communicate()
+        if pr.returncode:
+            err = (e or "")[-500:] or f"exit status {pr.returncode}"
+        else:
+            rates.append(json.loads(out.strip().splitlines()[-1])["value"])
+    if err is not None:
+        return dict(error=err)
+    return dict(value=sum(rates), unit="unknowns/s", cores=cores, kind="oracle", cpu=cpu_model(),
+                sample=f"{cores} concurrent single-threaded copies of the cpu_baseline sample ({nx}x{nx} mesh, "
+                       f"~{seconds:g} s each), rates summed")
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -449,9 +497,11 @@ def run_ours(args) -> None:
     if not args.quick:
         extra["thick_thin"] = run_thick_thin(stream)
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = run_oracle_child(args.cpu_seconds, CPU_SAMPLE_NX)
+        cpu["cpu"] = cpu_model()
+        cpu_all = run_oracle_all_cores(args.cpu_seconds, CPU_SAMPLE_NX)
 
     if rank == 0:
         line = {
@@ -465,7 +515,8 @@ def run_ours(args) -> None:
                                      "every step",
                        "moment_solve": "flexible CG, multigrid V-cycle with degree-3 Chebyshev level-0 smoothing", "cg_tol": 1e-12,
                        "cg_loop": "host-checked chunks" if args.host_cg_loop else "one device-side graph loop"},
-            "roofline": roof, "roofline_all": rooflines, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "roofline_all": rooflines, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+            "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
             "phases_ms": dict(residual=ms_res, sweep=ms_sweep, moments=mean("ms_moments"), rhs=mean("ms_rhs"),
                               solve=ms_solve, cg_iters=cg_it),
@@ -714,7 +765,7 @@ def run_reference(args) -> None:
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WL_NAME, "sample_mesh": f"{nx}x{nx}", "angular_unknowns": unknowns},
         "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu": cpu_model()},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -1,7 +1,7 @@
 """CPU checks of bench.py's host logic: the max-over-ranks reduction of the
 step time across replica ranks (world size 2 over gloo), and the oracle arm
 (`--impl reference`), which prints one JSON line on rank 0 and nothing on the
-other ranks."""
+other ranks, and the all-cores oracle leg."""
 import json
 import os
 import socket
@@ -78,3 +78,17 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     # the unknowns per step and the step time give the value
     assert d["value"] == pytest.approx(d["config"]["angular_unknowns"] / (d["ms_per_step"] * 1e-3), rel=1e-12)
+
+
+def test_oracle_on_every_core_sums_independent_copies():
+    """The all-cores oracle leg runs one single-threaded copy of the sample per
+    core and adds their rates; each copy's rate is that of the one-core leg's
+    kind (a tiny 2x2 sample here)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    one = bench.oracle_rate(0.05, 2)
+    both = bench.run_oracle_all_cores(0.05, 2, cores=2)
+    assert "error" not in both, both
+    assert both["cores"] == 2 and both["kind"] == "oracle" and both["unit"] == one["unit"]
+    assert both["value"] > 0 and isinstance(both["cpu"], str)
