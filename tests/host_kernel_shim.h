@@ -3,14 +3,17 @@
 // another), a std::barrier for __syncthreads, the block's dynamic shared memory
 // as an exact-size heap buffer, the round-to-nearest intrinsics as IEEE
 // single-precision operations (compile with -ffp-contract=off so that no
-// multiply-add is fused that the kernel did not fuse), and __shfl_xor_sync as
-// an exchange through per-thread slots with a barrier per warp (every lane of
-// a warp that reaches a shuffle must take part, as the full mask requires).
+// multiply-add is fused that the kernel did not fuse), the warp shuffles and
+// votes as an exchange through per-thread slots with a barrier per warp (every
+// lane of a warp that reaches one must take part, as the full mask requires),
+// and the device atomics and fences as C++ atomics on the same memory.
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <barrier>
 #include <cmath>
+#include <cstring>
 #include <functional>
 #include <memory>
 #include <thread>
@@ -20,6 +23,13 @@ struct float2 {
     float x, y;
 };
 inline float2 make_float2(float a, float b) { return float2{a, b}; }
+struct int2 {
+    int x, y;
+};
+inline int2 make_int2(int a, int b) { return int2{a, b}; }
+struct char4 {
+    signed char x, y, z, w;
+};
 
 struct emu_dim3 {
     int x = 0, y = 0, z = 0;
@@ -47,16 +57,55 @@ inline float __double2float_rn(double v) { return (float)v; }
 template <class T>
 inline T __ldcg(const T* p) { return *p; }
 
-inline std::vector<double>* emu_warp_slots = nullptr;
+inline std::vector<unsigned long long>* emu_warp_slots = nullptr;
 inline std::vector<std::unique_ptr<std::barrier<>>>* emu_warp_barriers = nullptr;
 
-inline double __shfl_xor_sync(unsigned, double v, int lane_mask) {
+inline void __syncwarp(unsigned = 0xffffffffu) { (*emu_warp_barriers)[threadIdx.x >> 5]->arrive_and_wait(); }
+
+// every lane publishes v, then reads lane src of its warp
+template <class T>
+inline T emu_warp_exchange(T v, int src) {
+    static_assert(sizeof(T) <= sizeof(unsigned long long), "shuffled values are at most 8 bytes");
     const int t = threadIdx.x, w = t >> 5;
-    (*emu_warp_slots)[t] = v;
-    (*emu_warp_barriers)[w]->arrive_and_wait();
-    const double r = (*emu_warp_slots)[t ^ lane_mask];
-    (*emu_warp_barriers)[w]->arrive_and_wait();
+    unsigned long long bits = 0;
+    std::memcpy(&bits, &v, sizeof(T));
+    (*emu_warp_slots)[t] = bits;
+    __syncwarp();
+    const unsigned long long got = (*emu_warp_slots)[(w << 5) + src];
+    __syncwarp();
+    T r;
+    std::memcpy(&r, &got, sizeof(T));
     return r;
+}
+
+template <class T>
+inline T __shfl_sync(unsigned, T v, int src_lane) { return emu_warp_exchange(v, src_lane & 31); }
+template <class T>
+inline T __shfl_xor_sync(unsigned, T v, int lane_mask) { return emu_warp_exchange(v, (threadIdx.x & 31) ^ lane_mask); }
+template <class T>
+inline T __shfl_down_sync(unsigned, T v, unsigned delta) {
+    const int lane = threadIdx.x & 31, src = lane + (int)delta;
+    return emu_warp_exchange(v, src < 32 ? src : lane);
+}
+
+// number of lanes of the warp whose predicate holds
+inline int emu_warp_count(int pred) {
+    const int t = threadIdx.x, w = t >> 5;
+    (*emu_warp_slots)[t] = pred ? 1 : 0;
+    __syncwarp();
+    int c = 0;
+    for (int l = 0; l < 32; ++l) c += (int)(*emu_warp_slots)[(w << 5) + l];
+    __syncwarp();
+    return c;
+}
+inline int __all_sync(unsigned, int pred) { return emu_warp_count(pred) == 32; }
+inline int __any_sync(unsigned, int pred) { return emu_warp_count(pred) > 0; }
+
+inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
+inline void __nanosleep(unsigned) { std::this_thread::yield(); }
+inline int atomicCAS(int* p, int compare, int val) {
+    std::atomic_ref<int>(*p).compare_exchange_strong(compare, val);
+    return compare;
 }
 
 // Run body() as every thread of grid x threads, with smem bytes of dynamic
@@ -70,7 +119,7 @@ inline void emu_launch(int grid, int threads, size_t smem, const std::function<v
         emu_dynamic_smem = sm.data();
         std::barrier<> bar(threads);
         emu_block_barrier = &bar;
-        std::vector<double> slots(threads);
+        std::vector<unsigned long long> slots(threads);
         std::vector<std::unique_ptr<std::barrier<>>> warp_bars;
         for (int w = 0; w * 32 < threads; ++w)
             warp_bars.push_back(std::make_unique<std::barrier<>>(std::min(32, threads - 32 * w)));

@@ -1,0 +1,179 @@
+// Test driver (CPU): the wavefront sweep kernel of sweep.cu run on the host
+// through host_kernel_shim.h, in both FP64 local-solve forms the library
+// launches in source mode: the in-register LU (sweep_kernel<double, P,
+// SWEEP_SOURCE, false>) and the cached local inverses held as FP32 pairs
+// (invert_kernel, source_kernel and mass_apply_kernel first, then
+// sweep_kernel<double, P, SWEEP_SOURCE, true>).  The inputs are the library's
+// host setup (task list, face directions, element and face matrices) in the
+// device layouts, filled as the library fills its sweep arguments.  One block
+// of 256 threads (8 warps) takes the level-sorted task list round-robin, so
+// the epoch-flag waits between warps are exercised with real threads.  The
+// kernel source arrives as sweep_kernels.inc, extracted from the CUDA files by
+// the test; the inline-assembly loads, stores and timer it wraps are given
+// here as C++ atomics and a steady clock.
+// Usage: sweep_emu DIR NE NNODES M P SN ANGULAR INFLOW
+//   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, phi.f64 [ne][n],
+//        q.f64 ([ne][n], or [nd][ne][n] if ANGULAR), inflow.f64 [nd][n_bface][p+1] if INFLOW
+//   out: DIR/dims.txt (n nd n_bface nlevels), DIR/psi_lu.f64, DIR/psi_inv.f64 and
+//        DIR/psi2_inv.f64 (the pair copy as hi + lo) [ne][nd][n], DIR/err.txt (device error words)
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <string>
+#include <vector>
+
+#include "host_kernel_shim.h"
+#include "setup.hpp"
+
+namespace smm {
+
+inline unsigned ld_acquire(const unsigned* p) {
+    return std::atomic_ref<unsigned>(*const_cast<unsigned*>(p)).load(std::memory_order_acquire);
+}
+inline void st_release(unsigned* p, unsigned v) { std::atomic_ref<unsigned>(*p).store(v, std::memory_order_release); }
+inline long long global_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+inline int ld_volatile(const int* p) {
+    return std::atomic_ref<int>(*const_cast<int*>(p)).load(std::memory_order_relaxed);
+}
+
+#include "sweep_kernels.inc"
+
+}  // namespace smm
+
+template <class T>
+static bool read_file(const std::string& path, std::vector<T>& v) {
+    std::ifstream in(path, std::ios::binary);
+    in.read(reinterpret_cast<char*>(v.data()), (std::streamsize)(v.size() * sizeof(T)));
+    return (bool)in;
+}
+
+template <class T>
+static bool write_file(const std::string& path, const std::vector<T>& v) {
+    std::ofstream out(path, std::ios::binary);
+    out.write(reinterpret_cast<const char*>(v.data()), (std::streamsize)(v.size() * sizeof(T)));
+    return (bool)out;
+}
+
+static std::vector<float2> to_pairs(const std::vector<double>& v) {
+    std::vector<float2> out(v.size());
+    for (size_t i = 0; i < v.size(); ++i) out[i] = smm::df_make(v[i]);
+    return out;
+}
+
+struct Run {
+    std::vector<double> psi;
+    std::vector<float2> psi2;
+    int err = 0;
+};
+
+// the arguments the library's sweep preparation fills for an FP64 source sweep
+static smm::SweepArgs<double> base_args(const smm::Setup& s, const std::vector<double>& phi, bool inflow,
+                                        std::vector<unsigned>& done, int& err) {
+    smm::SweepArgs<double> a{};
+    a.ne = s.ne; a.nd = s.nd; a.ntask = (int)s.tasks.size(); a.p = s.p; a.tasks = s.tasks.data();
+    a.ox = s.quad.ox.data(); a.oy = s.quad.oy.data(); a.sigma_t = s.sigma_t.data(); a.sigma_s = s.sigma_s.data();
+    a.M = s.M.data(); a.Gx = s.Gx.data(); a.Gy = s.Gy.data(); a.Fx = s.Fx.data(); a.Fy = s.Fy.data();
+    a.fdir = s.fdir.data(); a.nbr = s.nbr.data(); a.nbr_face = s.nbr_face.data(); a.nbr_flip = s.nbr_flip.data();
+    a.bface_id = s.bface_id.data();
+    a.phi = phi.data(); a.src = s.src.data(); a.src_angular = s.src.size() > (size_t)s.ne * s.n ? 1 : 0;
+    a.inflow = inflow ? s.inflow.data() : nullptr;
+    done.assign((size_t)s.ne * s.nd, 0u);
+    a.done = done.data(); a.epoch = 1; a.err = &err;
+    a.timeout_ns = 60LL * 1000 * 1000 * 1000;
+    return a;
+}
+
+template <int P>
+static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow, Run& lu, Run& inv) {
+    const int ne = s.ne, nd = s.nd, n = s.n;
+    const size_t nang = (size_t)ne * nd * n;
+    {  // in-register LU
+        std::vector<unsigned> done;
+        smm::SweepArgs<double> a = base_args(s, phi, inflow, done, lu.err);
+        lu.psi.assign(nang, 0.0);
+        a.psi = lu.psi.data();
+        emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, false>(a); });
+    }
+    {  // cached inverses as FP32 pairs
+        std::vector<unsigned> done;
+        smm::SweepArgs<double> a = base_args(s, phi, inflow, done, inv.err);
+        const int ntask = a.ntask;
+        std::vector<float2> ainv((size_t)ntask * n * n), msrc((size_t)ne * n), mq;
+        emu_launch((ntask + 7) / 8, 256, 0, [&] { smm::invert_kernel<double, P>(a, nullptr, ainv.data()); });
+        emu_launch((ne * n + 255) / 256, 256, 0, [&] {
+            smm::source_kernel(ne, n, s.M.data(), s.sigma_s.data(), phi.data(), a.src_angular ? nullptr : s.src.data(),
+                               msrc.data());
+        });
+        if (a.src_angular) {
+            mq.resize(nang);
+            emu_launch((int)((nang + 255) / 256), 256, 0,
+                       [&] { smm::mass_apply_kernel(ne, nd, n, s.M.data(), s.src.data(), mq.data()); });
+        }
+        const auto ox2 = to_pairs(s.quad.ox), oy2 = to_pairs(s.quad.oy), Fx2 = to_pairs(s.Fx), Fy2 = to_pairs(s.Fy);
+        const auto inflow2 = to_pairs(s.inflow);
+        inv.psi.assign(nang, 0.0);
+        inv.psi2.assign(nang, make_float2(0.0f, 0.0f));
+        a.ainv_df = ainv.data(); a.msrc2 = msrc.data(); a.mq2 = a.src_angular ? mq.data() : nullptr;
+        a.ox2 = ox2.data(); a.oy2 = oy2.data(); a.Fx2 = Fx2.data(); a.Fy2 = Fy2.data();
+        a.inflow2 = inflow ? inflow2.data() : nullptr;
+        a.psi = inv.psi.data(); a.psi2 = inv.psi2.data();
+        emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, false>(a); });
+    }
+}
+
+int main(int argc, char** argv) {
+    if (argc != 9) return 2;
+    const std::string dir = argv[1];
+    const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
+    const int sn = std::atoi(argv[6]), angular = std::atoi(argv[7]), inflow = std::atoi(argv[8]);
+    const int n = (p + 1) * (p + 1);
+    std::string err;
+    std::vector<double> nodes((size_t)nn * 2), st(ne), ss(ne), phi((size_t)ne * n);
+    std::vector<int32_t> elem((size_t)ne * (m + 1) * (m + 1));
+    if (!read_file(dir + "/nodes.f64", nodes) || !read_file(dir + "/elem.i32", elem) ||
+        !read_file(dir + "/sigma_t.f64", st) || !read_file(dir + "/sigma_s.f64", ss) ||
+        !read_file(dir + "/phi.f64", phi))
+        return 3;
+    // the ordinate count and the boundary face count size the angular inputs
+    const int nd = sn * (sn + 2) / 2;
+    int nb = 0;
+    {
+        std::ifstream f(dir + "/nbface.txt");
+        f >> nb;
+    }
+    std::vector<double> q((size_t)(angular ? nd : 1) * ne * n), infl(inflow ? (size_t)nd * nb * (p + 1) : 0);
+    if (!read_file(dir + "/q.f64", q)) return 3;
+    if (inflow && !read_file(dir + "/inflow.f64", infl)) return 3;
+    smm::Input in;
+    in.ne = ne; in.m = m; in.p = p; in.sn = sn; in.n_nodes = nn;
+    in.nodes = nodes.data(); in.elem_nodes = elem.data(); in.sigma_t = st.data(); in.sigma_s = ss.data();
+    in.source_kind = angular ? 1 : 0; in.q = q.data();
+    in.inflow_kind = inflow ? 1 : 0; in.inflow = inflow ? infl.data() : nullptr;
+    smm::Setup s;
+    if (smm::build_setup(in, s, err)) {
+        std::fprintf(stderr, "%s\n", err.c_str());
+        return 4;
+    }
+    if (s.nd != nd || s.nb != nb) return 6;
+    Run lu, inv;
+    switch (p) {
+        case 1: run<1>(s, phi, inflow, lu, inv); break;
+        case 2: run<2>(s, phi, inflow, lu, inv); break;
+        case 3: run<3>(s, phi, inflow, lu, inv); break;
+        default: run<4>(s, phi, inflow, lu, inv); break;
+    }
+    std::vector<double> psi2(inv.psi2.size());
+    for (size_t i = 0; i < psi2.size(); ++i) psi2[i] = (double)inv.psi2[i].x + (double)inv.psi2[i].y;
+    std::ofstream dims(dir + "/dims.txt");
+    dims << s.n << " " << s.nd << " " << s.nb << " " << s.nlevels << "\n";
+    std::ofstream errs(dir + "/err.txt");
+    errs << lu.err << " " << inv.err << "\n";
+    const bool ok = write_file(dir + "/psi_lu.f64", lu.psi) && write_file(dir + "/psi_inv.f64", inv.psi) &&
+                    write_file(dir + "/psi2_inv.f64", psi2);
+    return ok && dims && errs ? 0 : 5;
+}

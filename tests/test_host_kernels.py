@@ -1,7 +1,9 @@
 """The IP-SMM right-hand-side kernels of moments.cu, run on the CPU, against
-the oracle's right-hand side (Eq. ipsmm); and the angular-moment and boundary
+the oracle's right-hand side (Eq. ipsmm); the angular-moment and boundary
 correction kernels of the same file against the oracle's closures (Eqs.
-correction_tensor_disc, bdr_correction_factor_disc).
+correction_tensor_disc, bdr_correction_factor_disc); and the wavefront sweep
+kernel of sweep.cu, in both FP64 local-solve forms, against the oracle's
+upwind DG sweep (Sec. 4).
 
 The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
 helper and the FP32-pair arithmetic of dfloat.cuh) is taken from the CUDA
@@ -180,3 +182,81 @@ def test_moment_kernels_match_oracle(moments_emu, tmp_path, case):
         assert np.max(np.abs(beta_ref)) <= 1e-13 * scale
     else:
         assert np.max(np.abs(beta_ref)) > 1e-3 * scale
+
+
+# ---------------------------------------------------------------------------
+# the wavefront sweep kernel (sweep_kernel with the in-register LU and with
+# cached pair inverses, after invert_kernel / source_kernel / mass_apply_kernel)
+# against the oracle's sweep
+
+@pytest.fixture(scope="module")
+def sweep_emu(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("sweep_emu")
+    sweep = open(os.path.join(CSRC, "sweep.cu")).read()
+    kcuh = open(os.path.join(CSRC, "kernels.cuh")).read()
+    dfloat = open(os.path.join(CSRC, "dfloat.cuh")).read()
+    body = dfloat[dfloat.index("namespace smm {") + len("namespace smm {"):dfloat.rindex("}")]
+    enums = re.findall(r"enum : int \{[^}]*\};", kcuh)
+    assert len(enums) == 2
+    parts = enums + [extract(kcuh, "struct SweepArgs {") + ";", body,
+                     extract(sweep, "__device__ bool wait_epoch("),
+                     extract(sweep, "__device__ __forceinline__ int face_node("),
+                     extract(sweep, "template <typename T> __device__ __forceinline__ T ldg_cg("),
+                     extract(sweep, "__device__ __forceinline__ bool sweep_task("),
+                     extract(sweep, "__global__ void __launch_bounds__(256) sweep_kernel("),
+                     extract(sweep, "__global__ void __launch_bounds__(256) invert_kernel("),
+                     extract(sweep, "__global__ void mass_apply_kernel("),
+                     extract(sweep, "__global__ void source_kernel(")]
+    (d / "sweep_kernels.inc").write_text("\n".join(parts))
+    exe = d / "sweep_emu"
+    subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
+                    os.path.join(ROOT, "tests"), "-I", CSRC, os.path.join(ROOT, "tests", "sweep_emu.cpp"),
+                    os.path.join(CSRC, "setup.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+# (nx, ny, m, p, S_N, seed, kind): every p, straight and curved maps, isotropic
+# source with vacuum boundaries or the manufactured angular source with its
+# inflow, a one-element mesh and a ragged strip
+SWEEP_CASES = [(3, 2, 1, 1, 4, None, "iso"), (2, 3, 2, 2, 4, 4, "mms"), (3, 3, 3, 3, 4, 7, "mms"),
+               (2, 2, 3, 4, 4, 2, "mms"), (1, 1, 1, 2, 8, None, "iso"), (5, 1, 2, 1, 8, 3, "mms")]
+
+
+@pytest.mark.parametrize("case", SWEEP_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d_S%d_%s" % (c[:5] + c[6:]))
+def test_sweep_kernel_matches_oracle(sweep_emu, tmp_path, case):
+    from oracle.transport import Discretization
+    nx, ny, m, p, sn, seed, kind = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n = mesh.n_elem, (p + 1) ** 2
+    st = 1.0 + 0.5 * (np.arange(ne) % 3)
+    ss = 0.6 * st
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, sn, st, ss)
+    rng = np.random.default_rng(31)
+    phi = rng.uniform(0.5, 2.0, (ne, n))
+    pos = W.dg_node_positions(mesh, p)
+    if kind == "mms":
+        fpos = W.face_node_positions(mesh, p, W.boundary_faces(mesh))
+        q = np.stack([W.mms_source(pos[:, :, 0], pos[:, :, 1], o[0], o[1], st[:, None], ss[:, None])
+                      for o in disc.omega])
+        inflow = np.stack([W.mms_psi(fpos[:, :, 0], fpos[:, :, 1], o[0], o[1]) for o in disc.omega])
+    else:
+        q, inflow = rng.uniform(0.0, 1.0, (ne, n)), None
+    for name, arr in (("nodes", mesh.nodes), ("sigma_t", st), ("sigma_s", ss), ("phi", phi), ("q", q)):
+        np.ascontiguousarray(arr, np.float64).tofile(tmp_path / f"{name}.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    if inflow is not None:
+        np.ascontiguousarray(inflow, np.float64).tofile(tmp_path / "inflow.f64")
+    (tmp_path / "nbface.txt").write_text(str(len(disc.bfaces)))
+    subprocess.run([sweep_emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), str(sn),
+                    str(int(kind == "mms")), str(int(inflow is not None))], check=True, timeout=600)
+    n_o, nd_o, nb_o, nlev = map(int, open(tmp_path / "dims.txt").read().split())
+    assert (n_o, nd_o, nb_o) == (n, disc.nd, len(disc.bfaces))
+    assert open(tmp_path / "err.txt").read().split() == ["0", "0"]
+    ref = disc.sweep(phi, q, inflow).transpose(1, 0, 2)   # [ne][nd][n], the device layout
+    scale = np.max(np.abs(ref))
+    for name in ("psi_lu", "psi_inv", "psi2_inv"):
+        got = np.fromfile(tmp_path / f"{name}.f64").reshape(ne, disc.nd, n)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (name, np.max(np.abs(got - ref)) / scale)
