@@ -11,10 +11,17 @@
 // kernel source arrives as sweep_kernels.inc, extracted from the CUDA files by
 // the test; the inline-assembly loads, stores and timer it wraps are given
 // here as C++ atomics and a steady clock.
-// Usage: sweep_emu DIR NE NNODES M P SN ANGULAR INFLOW
+// MODE fixup runs the kernels with the optional parts compiled in (EXT) and
+// the zero-and-scale fixup on; MODE refine runs, instead of the FP64 sweep,
+// K sweeps of the FP32-refined form: residual_kernel (FP64 transport residual
+// of the accumulated flux) and sweep_kernel<float, P, SWEEP_RESIDUAL> solving
+// for the correction in FP32 and adding it to the FP64 flux (the LU form, and
+// the cached FP32 inverses from invert_kernel<float, P>).
+// Usage: sweep_emu DIR NE NNODES M P SN ANGULAR INFLOW MODE K
 //   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, phi.f64 [ne][n],
-//        q.f64 ([ne][n], or [nd][ne][n] if ANGULAR), inflow.f64 [nd][n_bface][p+1] if INFLOW
-//   out: DIR/dims.txt (n nd n_bface nlevels), DIR/psi_lu.f64, DIR/psi_inv.f64 and
+//        q.f64 ([ne][n], or [nd][ne][n] if ANGULAR), inflow.f64 [nd][n_bface][p+1] if INFLOW,
+//        nbface.txt (the boundary face count); MODE plain | fixup | refine, K sweeps (refine)
+//   out: DIR/dims.txt (n nd n_bface nlevels), DIR/psi_lu.f64, DIR/psi_inv.f64 and (FP64 modes)
 //        DIR/psi2_inv.f64 (the pair copy as hi + lo) [ne][nd][n], DIR/err.txt (device error words)
 #include <atomic>
 #include <chrono>
@@ -88,16 +95,96 @@ static smm::SweepArgs<double> base_args(const smm::Setup& s, const std::vector<d
     return a;
 }
 
+// column sums of M, Gx, Gy and of the face matrices over their test index, as
+// the library forms them for the fixup
+struct ColSums {
+    std::vector<double> m, gx, gy, fx, fy;
+    explicit ColSums(const smm::Setup& s) {
+        const int n = s.n, p1 = s.p1;
+        const size_t nn = (size_t)n * n;
+        m.assign((size_t)s.ne * n, 0.0); gx = m; gy = m;
+        fx.assign((size_t)s.ne * 4 * p1, 0.0); fy = fx;
+        for (int e = 0; e < s.ne; ++e) {
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    m[(size_t)e * n + j] += s.M[e * nn + (size_t)i * n + j];
+                    gx[(size_t)e * n + j] += s.Gx[e * nn + (size_t)i * n + j];
+                    gy[(size_t)e * n + j] += s.Gy[e * nn + (size_t)i * n + j];
+                }
+            for (int f = 0; f < 4; ++f)
+                for (int a = 0; a < p1; ++a)
+                    for (int b = 0; b < p1; ++b) {
+                        const size_t fo = (((size_t)e * 4 + f) * p1 + a) * p1 + b;
+                        fx[((size_t)e * 4 + f) * p1 + b] += s.Fx[fo];
+                        fy[((size_t)e * 4 + f) * p1 + b] += s.Fy[fo];
+                    }
+        }
+    }
+    void fill(smm::SweepArgs<double>& a) const {
+        a.fixup = 1;
+        a.colM = m.data(); a.colGx = gx.data(); a.colGy = gy.data(); a.colFx = fx.data(); a.colFy = fy.data();
+    }
+};
+
+// K sweeps of the FP32-refined form from psi = 0, both local-solve forms
 template <int P>
-static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow, Run& lu, Run& inv) {
+static void run_refined(const smm::Setup& s, const std::vector<double>& phi, bool inflow, int K, Run& lu, Run& inv) {
+    const int ne = s.ne, nd = s.nd, n = s.n, ntask = (int)s.tasks.size();
+    const size_t nang = (size_t)ne * nd * n;
+    const std::vector<float> M(s.M.begin(), s.M.end()), Gx(s.Gx.begin(), s.Gx.end()), Gy(s.Gy.begin(), s.Gy.end());
+    const std::vector<float> Fx(s.Fx.begin(), s.Fx.end()), Fy(s.Fy.begin(), s.Fy.end());
+    for (int form = 0; form < 2; ++form) {
+        Run& out = form == 0 ? lu : inv;
+        out.psi.assign(nang, 0.0);
+        std::vector<float> res(nang), dpsi(nang), ainv;
+        std::vector<unsigned> done((size_t)ne * nd, 0u);
+        smm::SweepArgs<float> a{};
+        a.ne = ne; a.nd = nd; a.ntask = ntask; a.p = s.p; a.tasks = s.tasks.data();
+        a.ox = s.quad.ox.data(); a.oy = s.quad.oy.data(); a.sigma_t = s.sigma_t.data(); a.sigma_s = s.sigma_s.data();
+        a.M = M.data(); a.Gx = Gx.data(); a.Gy = Gy.data(); a.Fx = Fx.data(); a.Fy = Fy.data();
+        a.fdir = s.fdir.data(); a.nbr = s.nbr.data(); a.nbr_face = s.nbr_face.data(); a.nbr_flip = s.nbr_flip.data();
+        a.bface_id = s.bface_id.data();
+        a.rhs = res.data(); a.psi = dpsi.data(); a.psi_acc = out.psi.data();
+        a.done = done.data(); a.err = &out.err;
+        a.timeout_ns = 60LL * 1000 * 1000 * 1000;
+        if (form == 1) {
+            ainv.resize((size_t)ntask * n * n);
+            emu_launch((ntask + 7) / 8, 256, 0, [&] { smm::invert_kernel<float, P>(a, ainv.data(), nullptr); });
+            a.ainv = ainv.data();
+        }
+        smm::ResidualArgs r{};
+        r.ne = ne; r.nd = nd; r.ntask = ntask; r.ox = a.ox; r.oy = a.oy; r.sigma_t = a.sigma_t; r.sigma_s = a.sigma_s;
+        r.M = s.M.data(); r.Gx = s.Gx.data(); r.Gy = s.Gy.data(); r.Fx = s.Fx.data(); r.Fy = s.Fy.data();
+        r.fdir = a.fdir; r.nbr = a.nbr; r.nbr_face = a.nbr_face; r.nbr_flip = a.nbr_flip; r.bface_id = a.bface_id;
+        r.phi = phi.data(); r.src = s.src.data(); r.src_angular = s.src.size() > (size_t)ne * n ? 1 : 0;
+        r.inflow = inflow ? s.inflow.data() : nullptr; r.psi = out.psi.data(); r.rhs = res.data();
+        for (int k = 0; k < K; ++k) {
+            emu_launch((ntask + 7) / 8, 256, 0, [&] { smm::residual_kernel<P>(r); });
+            a.epoch = (unsigned)(k + 1);
+            if (form == 0)
+                emu_launch(1, 256, 0, [&] { smm::sweep_kernel<float, P, smm::SWEEP_RESIDUAL, false, false>(a); });
+            else
+                emu_launch(1, 256, 0, [&] { smm::sweep_kernel<float, P, smm::SWEEP_RESIDUAL, true, false>(a); });
+        }
+    }
+}
+
+template <int P>
+static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow, bool fixup, Run& lu, Run& inv) {
     const int ne = s.ne, nd = s.nd, n = s.n;
     const size_t nang = (size_t)ne * nd * n;
+    const ColSums cols(s);
     {  // in-register LU
         std::vector<unsigned> done;
         smm::SweepArgs<double> a = base_args(s, phi, inflow, done, lu.err);
         lu.psi.assign(nang, 0.0);
         a.psi = lu.psi.data();
-        emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, false>(a); });
+        if (fixup) {
+            cols.fill(a);
+            emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, true>(a); });
+        } else {
+            emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, false>(a); });
+        }
     }
     {  // cached inverses as FP32 pairs
         std::vector<unsigned> done;
@@ -122,12 +209,20 @@ static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow
         a.ox2 = ox2.data(); a.oy2 = oy2.data(); a.Fx2 = Fx2.data(); a.Fy2 = Fy2.data();
         a.inflow2 = inflow ? inflow2.data() : nullptr;
         a.psi = inv.psi.data(); a.psi2 = inv.psi2.data();
-        emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, false>(a); });
+        if (fixup) {
+            cols.fill(a);
+            emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, true>(a); });
+        } else {
+            emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, false>(a); });
+        }
     }
 }
 
 int main(int argc, char** argv) {
-    if (argc != 9) return 2;
+    if (argc != 11) return 2;
+    const std::string mode = argv[9];
+    const int K = std::atoi(argv[10]);
+    if (mode != "plain" && mode != "fixup" && mode != "refine") return 2;
     const std::string dir = argv[1];
     const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
     const int sn = std::atoi(argv[6]), angular = std::atoi(argv[7]), inflow = std::atoi(argv[8]);
@@ -161,11 +256,21 @@ int main(int argc, char** argv) {
     }
     if (s.nd != nd || s.nb != nb) return 6;
     Run lu, inv;
-    switch (p) {
-        case 1: run<1>(s, phi, inflow, lu, inv); break;
-        case 2: run<2>(s, phi, inflow, lu, inv); break;
-        case 3: run<3>(s, phi, inflow, lu, inv); break;
-        default: run<4>(s, phi, inflow, lu, inv); break;
+    const bool fix = mode == "fixup";
+    if (mode == "refine") {
+        switch (p) {
+            case 1: run_refined<1>(s, phi, inflow, K, lu, inv); break;
+            case 2: run_refined<2>(s, phi, inflow, K, lu, inv); break;
+            case 3: run_refined<3>(s, phi, inflow, K, lu, inv); break;
+            default: run_refined<4>(s, phi, inflow, K, lu, inv); break;
+        }
+    } else {
+        switch (p) {
+            case 1: run<1>(s, phi, inflow, fix, lu, inv); break;
+            case 2: run<2>(s, phi, inflow, fix, lu, inv); break;
+            case 3: run<3>(s, phi, inflow, fix, lu, inv); break;
+            default: run<4>(s, phi, inflow, fix, lu, inv); break;
+        }
     }
     std::vector<double> psi2(inv.psi2.size());
     for (size_t i = 0; i < psi2.size(); ++i) psi2[i] = (double)inv.psi2[i].x + (double)inv.psi2[i].y;

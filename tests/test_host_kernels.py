@@ -2,8 +2,9 @@
 the oracle's right-hand side (Eq. ipsmm); the angular-moment and boundary
 correction kernels of the same file against the oracle's closures (Eqs.
 correction_tensor_disc, bdr_correction_factor_disc); and the wavefront sweep
-kernel of sweep.cu, in both FP64 local-solve forms, against the oracle's
-upwind DG sweep (Sec. 4).
+kernel of sweep.cu, in both FP64 local-solve forms, with the negative flux
+fixup, and in the FP32-refined form (FP64 residual, FP32 correction), against
+the oracle's upwind DG sweep (Sec. 4).
 
 The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
 helper and the FP32-pair arithmetic of dfloat.cuh) is taken from the CUDA
@@ -201,13 +202,14 @@ def sweep_emu(tmp_path_factory):
     body = dfloat[dfloat.index("namespace smm {") + len("namespace smm {"):dfloat.rindex("}")]
     enums = re.findall(r"enum : int \{[^}]*\};", kcuh)
     assert len(enums) == 2
-    parts = enums + [extract(kcuh, "struct SweepArgs {") + ";", body,
+    parts = enums + [extract(kcuh, "struct SweepArgs {") + ";", extract(kcuh, "struct ResidualArgs {") + ";", body,
                      extract(sweep, "__device__ bool wait_epoch("),
                      extract(sweep, "__device__ __forceinline__ int face_node("),
                      extract(sweep, "template <typename T> __device__ __forceinline__ T ldg_cg("),
                      extract(sweep, "__device__ __forceinline__ bool sweep_task("),
                      extract(sweep, "__global__ void __launch_bounds__(256) sweep_kernel("),
                      extract(sweep, "__global__ void __launch_bounds__(256) invert_kernel("),
+                     extract(sweep, "__global__ void __launch_bounds__(256) residual_kernel("),
                      extract(sweep, "__global__ void mass_apply_kernel("),
                      extract(sweep, "__global__ void source_kernel(")]
     (d / "sweep_kernels.inc").write_text("\n".join(parts))
@@ -225,14 +227,16 @@ SWEEP_CASES = [(3, 2, 1, 1, 4, None, "iso"), (2, 3, 2, 2, 4, 4, "mms"), (3, 3, 3
                (2, 2, 3, 4, 4, 2, "mms"), (1, 1, 1, 2, 8, None, "iso"), (5, 1, 2, 1, 8, 3, "mms")]
 
 
-@pytest.mark.parametrize("case", SWEEP_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d_S%d_%s" % (c[:5] + c[6:]))
-def test_sweep_kernel_matches_oracle(sweep_emu, tmp_path, case):
+def _sweep_problem(case, sig=None, strip_light=False):
+    """Mesh, cross sections, the oracle's discretization, varphi, q and inflow
+    of one sweep case (isotropic q with vacuum boundaries, or the manufactured
+    angular source with its inflow, or a strip lit from the left face)."""
     from oracle.transport import Discretization
     nx, ny, m, p, sn, seed, kind = case
     mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
     ne, n = mesh.n_elem, (p + 1) ** 2
-    st = 1.0 + 0.5 * (np.arange(ne) % 3)
-    ss = 0.6 * st
+    st = np.full(ne, sig) if sig is not None else 1.0 + 0.5 * (np.arange(ne) % 3)
+    ss = (0.0 if strip_light else 0.6) * st
     disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, sn, st, ss)
     rng = np.random.default_rng(31)
     phi = rng.uniform(0.5, 2.0, (ne, n))
@@ -242,21 +246,71 @@ def test_sweep_kernel_matches_oracle(sweep_emu, tmp_path, case):
         q = np.stack([W.mms_source(pos[:, :, 0], pos[:, :, 1], o[0], o[1], st[:, None], ss[:, None])
                       for o in disc.omega])
         inflow = np.stack([W.mms_psi(fpos[:, :, 0], fpos[:, :, 1], o[0], o[1]) for o in disc.omega])
+    elif kind == "strip":
+        q = np.zeros((ne, n))
+        inflow = np.zeros((disc.nd, len(disc.bfaces), p + 1))
+        for b, (e, f) in enumerate(W.boundary_faces(mesh)):
+            if f == 3:
+                inflow[:, b, :] = 1.0
     else:
         q, inflow = rng.uniform(0.0, 1.0, (ne, n)), None
+    return mesh, st, ss, disc, phi, q, inflow
+
+
+def _run_sweep_emu(exe, tmp_path, case, mode="plain", K=0, **kw):
+    nx, ny, m, p, sn, seed, kind = case
+    mesh, st, ss, disc, phi, q, inflow = _sweep_problem(case, **kw)
+    ne, n = mesh.n_elem, (p + 1) ** 2
     for name, arr in (("nodes", mesh.nodes), ("sigma_t", st), ("sigma_s", ss), ("phi", phi), ("q", q)):
         np.ascontiguousarray(arr, np.float64).tofile(tmp_path / f"{name}.f64")
     np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
     if inflow is not None:
         np.ascontiguousarray(inflow, np.float64).tofile(tmp_path / "inflow.f64")
     (tmp_path / "nbface.txt").write_text(str(len(disc.bfaces)))
-    subprocess.run([sweep_emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), str(sn),
-                    str(int(kind == "mms")), str(int(inflow is not None))], check=True, timeout=600)
+    subprocess.run([exe, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), str(sn),
+                    str(int(q.ndim == 3)), str(int(inflow is not None)), mode, str(K)], check=True, timeout=600)
     n_o, nd_o, nb_o, nlev = map(int, open(tmp_path / "dims.txt").read().split())
     assert (n_o, nd_o, nb_o) == (n, disc.nd, len(disc.bfaces))
     assert open(tmp_path / "err.txt").read().split() == ["0", "0"]
+    names = ("psi_lu", "psi_inv") + (("psi2_inv",) if mode != "refine" else ())
+    got = {k: np.fromfile(tmp_path / f"{k}.f64").reshape(ne, disc.nd, n) for k in names}
+    return disc, phi, q, inflow, got
+
+
+@pytest.mark.parametrize("case", SWEEP_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d_S%d_%s" % (c[:5] + c[6:]))
+def test_sweep_kernel_matches_oracle(sweep_emu, tmp_path, case):
+    disc, phi, q, inflow, got = _run_sweep_emu(sweep_emu, tmp_path, case)
     ref = disc.sweep(phi, q, inflow).transpose(1, 0, 2)   # [ne][nd][n], the device layout
     scale = np.max(np.abs(ref))
-    for name in ("psi_lu", "psi_inv", "psi2_inv"):
-        got = np.fromfile(tmp_path / f"{name}.f64").reshape(ne, disc.nd, n)
-        assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (name, np.max(np.abs(got - ref)) / scale)
+    for name, psi in got.items():
+        assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
+
+
+def test_sweep_kernel_fixup_matches_oracle(sweep_emu, tmp_path):
+    """The kernels with their optional parts compiled in and the zero-and-scale
+    fixup on, on a thick absorbing strip lit from the left whose DG solution
+    dips below zero (Sec. 6.3), against the oracle's sweep with its fixup."""
+    case = (6, 1, 1, 2, 4, None, "strip")
+    disc, phi, q, inflow, got = _run_sweep_emu(sweep_emu, tmp_path, case, "fixup", sig=30.0, strip_light=True)
+    plain = disc.sweep(phi, q, inflow)
+    assert plain.min() < 0.0            # the case needs the fixup
+    ref = disc.sweep(phi, q, inflow, fixup=True).transpose(1, 0, 2)
+    assert ref.min() >= 0.0
+    scale = np.max(np.abs(ref))
+    for name, psi in got.items():
+        assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
+
+
+@pytest.mark.parametrize("case", [SWEEP_CASES[1], SWEEP_CASES[3]], ids=["p2_curved", "p4_curved"])
+def test_fp32_refined_sweeps_converge_to_the_fp64_sweep(sweep_emu, tmp_path, case):
+    """The FP32-refined form: one sweep is FP32-accurate, and repeated residual
+    sweeps (FP64 residual, FP32 correction) reach the FP64 sweep."""
+    errs = {}
+    for K in (1, 4):
+        disc, phi, q, inflow, got = _run_sweep_emu(sweep_emu, tmp_path, case, "refine", K)
+        ref = disc.sweep(phi, q, inflow).transpose(1, 0, 2)
+        scale = np.max(np.abs(ref))
+        errs[K] = {k: np.max(np.abs(v - ref)) / scale for k, v in got.items()}
+    for name in ("psi_lu", "psi_inv"):
+        assert 1e-10 < errs[1][name] < 1e-5, (name, errs)
+        assert errs[4][name] < 1e-12, (name, errs)
