@@ -319,9 +319,20 @@ __device__ __forceinline__ bool cg_finished(const int* ctl) { return ctl && *(co
 
 // ---- deterministic reductions of the CG kernels ----
 
+// Sum over the lanes of the calling warp, valid in lane 0.  Blocks of
+// (256 / n) n threads (n = 9, 25) end in a partial warp: its missing lanes
+// take no part (the mask names the lanes that exist) and count as zero (a
+// value shuffled from a missing lane is undefined, so it is not added).  For
+// a full warp this is the plain butterfly.
 __device__ __forceinline__ double warp_sum(double v) {
+    const int lane = threadIdx.x & 31;
+    const int nl = min(32, (int)blockDim.x - (int)(threadIdx.x & ~31u));
+    const unsigned mask = nl == 32 ? 0xffffffffu : (1u << nl) - 1u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_xor_sync(mask, v, o);
+        if ((lane ^ o) < nl) v += u;
+    }
     return v;
 }
 

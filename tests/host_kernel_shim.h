@@ -44,6 +44,9 @@ inline std::barrier<>* emu_block_barrier = nullptr;
 #define __forceinline__ inline
 #define __restrict__
 #define __launch_bounds__(...)
+// a block's static shared variables: one instance, which the block's threads
+// share (blocks run one after another)
+#define __shared__ static
 #define __syncthreads() emu_block_barrier->arrive_and_wait()
 using std::max;
 using std::min;
@@ -103,6 +106,7 @@ inline int __any_sync(unsigned, int pred) { return emu_warp_count(pred) > 0; }
 
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 inline void __nanosleep(unsigned) { std::this_thread::yield(); }
+inline unsigned atomicAdd(unsigned* p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_add(v); }
 inline int atomicCAS(int* p, int compare, int val) {
     std::atomic_ref<int>(*p).compare_exchange_strong(compare, val);
     return compare;
@@ -119,7 +123,10 @@ inline void emu_launch(int grid, int threads, size_t smem, const std::function<v
         emu_dynamic_smem = sm.data();
         std::barrier<> bar(threads);
         emu_block_barrier = &bar;
-        std::vector<unsigned long long> slots(threads);
+        // a slot for every lane of every warp, the missing lanes of a partial
+        // last warp included: a value read from one of those is undefined on
+        // the device, and here it is a NaN as a double and as a float
+        std::vector<unsigned long long> slots((threads + 31) / 32 * 32, 0x7ff800007fc00000ull);
         std::vector<std::unique_ptr<std::barrier<>>> warp_bars;
         for (int w = 0; w * 32 < threads; ++w)
             warp_bars.push_back(std::make_unique<std::barrier<>>(std::min(32, threads - 32 * w)));

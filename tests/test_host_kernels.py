@@ -4,7 +4,8 @@ correction kernels of the same file against the oracle's closures (Eqs.
 correction_tensor_disc, bdr_correction_factor_disc); and the wavefront sweep
 kernel of sweep.cu, in both FP64 local-solve forms, with the negative flux
 fixup, and in the FP32-refined form (FP64 residual, FP32 correction), against
-the oracle's upwind DG sweep (Sec. 4).
+the oracle's upwind DG sweep (Sec. 4); and the flexible-CG operator product of
+the moment solve against the oracle's IP-SMM matrix (Eq. ipsmm).
 
 The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
 helper and the FP32-pair arithmetic of dfloat.cuh) is taken from the CUDA
@@ -314,3 +315,77 @@ def test_fp32_refined_sweeps_converge_to_the_fp64_sweep(sweep_emu, tmp_path, cas
     for name in ("psi_lu", "psi_inv"):
         assert 1e-10 < errs[1][name] < 1e-5, (name, errs)
         assert errs[4][name] < 1e-12, (name, errs)
+
+
+# ---------------------------------------------------------------------------
+# the flexible-CG operator product (cgx_spmv_kernel: q = A p on the
+# face-factored IP-SMM operator in FP32-pair arithmetic, p.q by the last-block
+# reduction) against the oracle's assembled IP-SMM matrix
+
+@pytest.fixture(scope="module")
+def cg_emu(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("cg_emu")
+    moments = open(os.path.join(CSRC, "moments.cu")).read()
+    kcuh = open(os.path.join(CSRC, "kernels.cuh")).read()
+    dfloat = open(os.path.join(CSRC, "dfloat.cuh")).read()
+    blockops = open(os.path.join(CSRC, "blockops.cuh")).read()
+    body = dfloat[dfloat.index("namespace smm {") + len("namespace smm {"):dfloat.rindex("}")]
+    ops = blockops[blockops.index("namespace smm {") + len("namespace smm {"):blockops.rindex("}")]
+    # the cache-policy loads (inline assembly) become plain loads
+    host = {"__device__ __forceinline__ unsigned long long l2_keep(": "inline unsigned long long l2_keep() { return 0; }",
+            "__device__ __forceinline__ unsigned long long l2_stream(":
+                "inline unsigned long long l2_stream() { return 0; }",
+            "__device__ __forceinline__ float ld_hint(const float* a":
+                "inline float ld_hint(const float* a, unsigned long long) { return *a; }",
+            "__device__ __forceinline__ float2 ld_hint(const float2* a":
+                "inline float2 ld_hint(const float2* a, unsigned long long) { return *a; }"}
+    for sig, repl in host.items():
+        ops = ops.replace(extract(ops, sig), repl)
+    assert "asm" not in ops
+    parts = [extract(kcuh, "struct FaceOp {") + ";", extract(kcuh, "struct FaceOpDF {") + ";",
+             extract(kcuh, "struct CGArgs {") + ";", body, ops,
+             extract(moments, "__global__ void __launch_bounds__(256) cgx_spmv_kernel(")]
+    (d / "cg_kernels.inc").write_text("\n".join(parts))
+    exe = d / "cg_emu"
+    subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
+                    os.path.join(ROOT, "tests"), "-I", CSRC, os.path.join(ROOT, "tests", "cg_emu.cpp"),
+                    os.path.join(CSRC, "setup.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+# (nx, ny, m, p, seed): every element size, curved maps, a one-element mesh, and
+# meshes with more elements than one block's slots (several blocks and the
+# last-block reduction), ragged against the two-elements-per-thread tiling
+# (a block holds 2 x 64 / 28 / 16 / 10 elements for p = 1 / 2 / 3 / 4)
+CG_CASES = [(3, 2, 1, 1, None), (4, 3, 2, 2, 4), (3, 3, 3, 3, 7), (3, 2, 3, 4, 2), (1, 1, 1, 2, None),
+            (12, 11, 1, 1, 5), (8, 8, 2, 2, 3), (7, 5, 3, 3, 6), (5, 5, 3, 4, 2)]
+
+
+@pytest.mark.parametrize("case", CG_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_cg_operator_product_matches_oracle(cg_emu, tmp_path, case):
+    from oracle import ipsmm
+    from oracle.transport import Discretization
+    nx, ny, m, p, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n = mesh.n_elem, (p + 1) ** 2
+    st = 1.0 + 0.5 * (np.arange(ne) % 3)
+    ss = 0.7 * st
+    rng = np.random.default_rng(41)
+    pv = rng.standard_normal((ne, n))
+    for name, arr in (("nodes", mesh.nodes), ("sigma_t", st), ("sigma_s", ss), ("q", np.ones((ne, n))), ("p", pv)):
+        np.ascontiguousarray(arr, np.float64).tofile(tmp_path / f"{name}.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    subprocess.run([cg_emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p)], check=True, timeout=600)
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, ss)
+    A = ipsmm.assemble_lhs(disc).tocsr()
+    ref = A @ pv.ravel()
+    scale = np.max(abs(A) @ np.abs(pv.ravel()))
+    q = np.fromfile(tmp_path / "q_out.f64")
+    assert np.max(np.abs(q - ref)) <= 1e-12 * scale, np.max(np.abs(q - ref)) / scale
+    scal = np.fromfile(tmp_path / "scal.f64")
+    pq = float(pv.ravel() @ q)
+    assert abs(scal[1] - pq) <= 1e-12 * float(np.abs(pv.ravel()) @ np.abs(q))
+    assert scal[5] == pytest.approx(1.0 / scal[1], rel=1e-15)
