@@ -17,7 +17,8 @@
 // of the accumulated flux) and sweep_kernel<float, P, SWEEP_RESIDUAL> solving
 // for the correction in FP32 and adding it to the FP64 flux (the LU form, and
 // the cached FP32 inverses from invert_kernel<float, P>).
-// Usage: sweep_emu DIR NE NNODES M P SN ANGULAR INFLOW MODE K
+// Usage: sweep_emu DIR NE NNODES M P SN ANGULAR INFLOW MODE K   (one problem)
+//        sweep_emu --batch DIR COUNT                          (see run_batch)
 //   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, phi.f64 [ne][n],
 //        q.f64 ([ne][n], or [nd][ne][n] if ANGULAR), inflow.f64 [nd][n_bface][p+1] if INFLOW,
 //        nbface.txt (the boundary face count); MODE plain | fixup | refine, K sweeps (refine)
@@ -93,6 +94,38 @@ static smm::SweepArgs<double> base_args(const smm::Setup& s, const std::vector<d
     a.done = done.data(); a.epoch = 1; a.err = &err;
     a.timeout_ns = 60LL * 1000 * 1000 * 1000;
     return a;
+}
+
+// what the library's create and sweep preparation add for the cached pair
+// inverses: the inverses (invert_kernel), M s (source_kernel), M q_d for an
+// angular source (mass_apply_kernel) and the pair copies of the cosines, face
+// matrices and inflow
+struct Cached {
+    std::vector<float2> ainv, msrc, mq, ox2, oy2, Fx2, Fy2, inflow2;
+};
+
+template <int P>
+static void prepare_cached(const smm::Setup& s, const std::vector<double>& phi, bool inflow,
+                           smm::SweepArgs<double>& a, Cached& c) {
+    const int ne = s.ne, nd = s.nd, n = s.n, ntask = a.ntask;
+    const size_t nang = (size_t)ne * nd * n;
+    c.ainv.resize((size_t)ntask * n * n);
+    c.msrc.resize((size_t)ne * n);
+    emu_launch((ntask + 7) / 8, 256, 0, [&] { smm::invert_kernel<double, P>(a, nullptr, c.ainv.data()); });
+    emu_launch((ne * n + 255) / 256, 256, 0, [&] {
+        smm::source_kernel(ne, n, s.M.data(), s.sigma_s.data(), phi.data(), a.src_angular ? nullptr : s.src.data(),
+                           c.msrc.data());
+    });
+    if (a.src_angular) {
+        c.mq.resize(nang);
+        emu_launch((int)((nang + 255) / 256), 256, 0,
+                   [&] { smm::mass_apply_kernel(ne, nd, n, s.M.data(), s.src.data(), c.mq.data()); });
+    }
+    c.ox2 = to_pairs(s.quad.ox); c.oy2 = to_pairs(s.quad.oy); c.Fx2 = to_pairs(s.Fx); c.Fy2 = to_pairs(s.Fy);
+    c.inflow2 = to_pairs(s.inflow);
+    a.ainv_df = c.ainv.data(); a.msrc2 = c.msrc.data(); a.mq2 = a.src_angular ? c.mq.data() : nullptr;
+    a.ox2 = c.ox2.data(); a.oy2 = c.oy2.data(); a.Fx2 = c.Fx2.data(); a.Fy2 = c.Fy2.data();
+    a.inflow2 = inflow ? c.inflow2.data() : nullptr;
 }
 
 // column sums of M, Gx, Gy and of the face matrices over their test index, as
@@ -189,25 +222,10 @@ static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow
     {  // cached inverses as FP32 pairs
         std::vector<unsigned> done;
         smm::SweepArgs<double> a = base_args(s, phi, inflow, done, inv.err);
-        const int ntask = a.ntask;
-        std::vector<float2> ainv((size_t)ntask * n * n), msrc((size_t)ne * n), mq;
-        emu_launch((ntask + 7) / 8, 256, 0, [&] { smm::invert_kernel<double, P>(a, nullptr, ainv.data()); });
-        emu_launch((ne * n + 255) / 256, 256, 0, [&] {
-            smm::source_kernel(ne, n, s.M.data(), s.sigma_s.data(), phi.data(), a.src_angular ? nullptr : s.src.data(),
-                               msrc.data());
-        });
-        if (a.src_angular) {
-            mq.resize(nang);
-            emu_launch((int)((nang + 255) / 256), 256, 0,
-                       [&] { smm::mass_apply_kernel(ne, nd, n, s.M.data(), s.src.data(), mq.data()); });
-        }
-        const auto ox2 = to_pairs(s.quad.ox), oy2 = to_pairs(s.quad.oy), Fx2 = to_pairs(s.Fx), Fy2 = to_pairs(s.Fy);
-        const auto inflow2 = to_pairs(s.inflow);
+        Cached store;
+        prepare_cached<P>(s, phi, inflow, a, store);
         inv.psi.assign(nang, 0.0);
         inv.psi2.assign(nang, make_float2(0.0f, 0.0f));
-        a.ainv_df = ainv.data(); a.msrc2 = msrc.data(); a.mq2 = a.src_angular ? mq.data() : nullptr;
-        a.ox2 = ox2.data(); a.oy2 = oy2.data(); a.Fx2 = Fx2.data(); a.Fy2 = Fy2.data();
-        a.inflow2 = inflow ? inflow2.data() : nullptr;
         a.psi = inv.psi.data(); a.psi2 = inv.psi2.data();
         if (fixup) {
             cols.fill(a);
@@ -218,21 +236,23 @@ static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow
     }
 }
 
-int main(int argc, char** argv) {
-    if (argc != 11) return 2;
-    const std::string mode = argv[9];
-    const int K = std::atoi(argv[10]);
-    if (mode != "plain" && mode != "fixup" && mode != "refine") return 2;
-    const std::string dir = argv[1];
-    const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
-    const int sn = std::atoi(argv[6]), angular = std::atoi(argv[7]), inflow = std::atoi(argv[8]);
+// one problem's inputs (see the usage above) and the library's host setup of them
+struct Problem {
+    smm::Setup s;
+    std::vector<double> phi;
+    bool inflow = false;
+};
+
+static int load_problem(const std::string& dir, int ne, int nn, int m, int p, int sn, int angular, int inflow,
+                        Problem& pr) {
     const int n = (p + 1) * (p + 1);
-    std::string err;
-    std::vector<double> nodes((size_t)nn * 2), st(ne), ss(ne), phi((size_t)ne * n);
+    std::vector<double> nodes((size_t)nn * 2), st(ne), ss(ne);
     std::vector<int32_t> elem((size_t)ne * (m + 1) * (m + 1));
+    pr.phi.assign((size_t)ne * n, 0.0);
+    pr.inflow = inflow != 0;
     if (!read_file(dir + "/nodes.f64", nodes) || !read_file(dir + "/elem.i32", elem) ||
         !read_file(dir + "/sigma_t.f64", st) || !read_file(dir + "/sigma_s.f64", ss) ||
-        !read_file(dir + "/phi.f64", phi))
+        !read_file(dir + "/phi.f64", pr.phi))
         return 3;
     // the ordinate count and the boundary face count size the angular inputs
     const int nd = sn * (sn + 2) / 2;
@@ -249,36 +269,115 @@ int main(int argc, char** argv) {
     in.nodes = nodes.data(); in.elem_nodes = elem.data(); in.sigma_t = st.data(); in.sigma_s = ss.data();
     in.source_kind = angular ? 1 : 0; in.q = q.data();
     in.inflow_kind = inflow ? 1 : 0; in.inflow = inflow ? infl.data() : nullptr;
-    smm::Setup s;
-    if (smm::build_setup(in, s, err)) {
+    std::string err;
+    if (smm::build_setup(in, pr.s, err)) {
         std::fprintf(stderr, "%s\n", err.c_str());
         return 4;
     }
-    if (s.nd != nd || s.nb != nb) return 6;
-    Run lu, inv;
-    const bool fix = mode == "fixup";
-    if (mode == "refine") {
-        switch (p) {
-            case 1: run_refined<1>(s, phi, inflow, K, lu, inv); break;
-            case 2: run_refined<2>(s, phi, inflow, K, lu, inv); break;
-            case 3: run_refined<3>(s, phi, inflow, K, lu, inv); break;
-            default: run_refined<4>(s, phi, inflow, K, lu, inv); break;
-        }
-    } else {
-        switch (p) {
-            case 1: run<1>(s, phi, inflow, fix, lu, inv); break;
-            case 2: run<2>(s, phi, inflow, fix, lu, inv); break;
-            case 3: run<3>(s, phi, inflow, fix, lu, inv); break;
-            default: run<4>(s, phi, inflow, fix, lu, inv); break;
-        }
-    }
+    return pr.s.nd == nd && pr.s.nb == nb ? 0 : 6;
+}
+
+static bool write_outputs(const std::string& dir, const smm::Setup& s, const Run& lu, const Run& inv) {
     std::vector<double> psi2(inv.psi2.size());
     for (size_t i = 0; i < psi2.size(); ++i) psi2[i] = (double)inv.psi2[i].x + (double)inv.psi2[i].y;
     std::ofstream dims(dir + "/dims.txt");
     dims << s.n << " " << s.nd << " " << s.nb << " " << s.nlevels << "\n";
     std::ofstream errs(dir + "/err.txt");
     errs << lu.err << " " << inv.err << "\n";
-    const bool ok = write_file(dir + "/psi_lu.f64", lu.psi) && write_file(dir + "/psi_inv.f64", inv.psi) &&
-                    write_file(dir + "/psi2_inv.f64", psi2);
-    return ok && dims && errs ? 0 : 5;
+    return write_file(dir + "/psi_lu.f64", lu.psi) && write_file(dir + "/psi_inv.f64", inv.psi) &&
+           write_file(dir + "/psi2_inv.f64", psi2) && (bool)dims && (bool)errs;
+}
+
+// sweep_emu --batch DIR COUNT: problems DIR/0 .. DIR/COUNT-1 (each with its
+// inputs and args.txt = "NE NNODES M P SN ANGULAR INFLOW") swept together by
+// batch_sweep_kernel over their merged task list (level by level, problem by
+// problem, as the library merges it), with the LU and with cached inverses
+static int run_batch(const std::string& dir, int count) {
+    std::vector<Problem> prs(count);
+    for (int k = 0; k < count; ++k) {
+        const std::string d = dir + "/" + std::to_string(k);
+        std::ifstream f(d + "/args.txt");
+        int ne, nn, m, p, sn, ang, infl;
+        if (!(f >> ne >> nn >> m >> p >> sn >> ang >> infl)) return 3;
+        const int rc = load_problem(d, ne, nn, m, p, sn, ang, infl, prs[k]);
+        if (rc) return rc;
+    }
+    std::vector<int2> merged;
+    int maxlev = 0;
+    for (const Problem& pr : prs) maxlev = std::max(maxlev, pr.s.nlevels);
+    for (int l = 0; l < maxlev; ++l)
+        for (int k = 0; k < count; ++k) {
+            const smm::Setup& s = prs[k].s;
+            if (l >= s.nlevels) continue;
+            for (int t = s.level_start[l]; t < s.level_start[l + 1]; ++t) merged.push_back(make_int2(k, s.tasks[t]));
+        }
+    std::vector<Run> lu(count), inv(count);
+    for (int form = 0; form < 2; ++form) {
+        std::vector<smm::SweepArgs<double>> args(count);
+        std::vector<std::vector<unsigned>> done(count);
+        std::vector<Cached> store(count);
+        for (int k = 0; k < count; ++k) {
+            const smm::Setup& s = prs[k].s;
+            Run& out = form == 0 ? lu[k] : inv[k];
+            args[k] = base_args(s, prs[k].phi, prs[k].inflow, done[k], out.err);
+            const size_t nang = (size_t)s.ne * s.nd * s.n;
+            out.psi.assign(nang, 0.0);
+            args[k].psi = out.psi.data();
+            if (form == 1) {
+                switch (s.p) {
+                    case 1: prepare_cached<1>(s, prs[k].phi, prs[k].inflow, args[k], store[k]); break;
+                    case 2: prepare_cached<2>(s, prs[k].phi, prs[k].inflow, args[k], store[k]); break;
+                    case 3: prepare_cached<3>(s, prs[k].phi, prs[k].inflow, args[k], store[k]); break;
+                    default: prepare_cached<4>(s, prs[k].phi, prs[k].inflow, args[k], store[k]); break;
+                }
+                out.psi2.assign(nang, make_float2(0.0f, 0.0f));
+                args[k].psi2 = out.psi2.data();
+            }
+        }
+        const int ntask = (int)merged.size();
+        if (form == 0)
+            emu_launch(1, 256, 0, [&] {
+                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, false>(args.data(), merged.data(), ntask);
+            });
+        else
+            emu_launch(1, 256, 0, [&] {
+                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, true>(args.data(), merged.data(), ntask);
+            });
+    }
+    for (int k = 0; k < count; ++k)
+        if (!write_outputs(dir + "/" + std::to_string(k), prs[k].s, lu[k], inv[k])) return 5;
+    return 0;
+}
+
+int main(int argc, char** argv) {
+    if (argc == 4 && std::string(argv[1]) == "--batch") return run_batch(argv[2], std::atoi(argv[3]));
+    if (argc != 11) return 2;
+    const std::string mode = argv[9];
+    const int K = std::atoi(argv[10]);
+    if (mode != "plain" && mode != "fixup" && mode != "refine") return 2;
+    const std::string dir = argv[1];
+    const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
+    const int sn = std::atoi(argv[6]), angular = std::atoi(argv[7]), inflow = std::atoi(argv[8]);
+    Problem pr;
+    const int rc = load_problem(dir, ne, nn, m, p, sn, angular, inflow, pr);
+    if (rc) return rc;
+    const smm::Setup& s = pr.s;
+    Run lu, inv;
+    const bool fix = mode == "fixup";
+    if (mode == "refine") {
+        switch (p) {
+            case 1: run_refined<1>(s, pr.phi, pr.inflow, K, lu, inv); break;
+            case 2: run_refined<2>(s, pr.phi, pr.inflow, K, lu, inv); break;
+            case 3: run_refined<3>(s, pr.phi, pr.inflow, K, lu, inv); break;
+            default: run_refined<4>(s, pr.phi, pr.inflow, K, lu, inv); break;
+        }
+    } else {
+        switch (p) {
+            case 1: run<1>(s, pr.phi, pr.inflow, fix, lu, inv); break;
+            case 2: run<2>(s, pr.phi, pr.inflow, fix, lu, inv); break;
+            case 3: run<3>(s, pr.phi, pr.inflow, fix, lu, inv); break;
+            default: run<4>(s, pr.phi, pr.inflow, fix, lu, inv); break;
+        }
+    }
+    return write_outputs(dir, s, lu, inv) ? 0 : 5;
 }

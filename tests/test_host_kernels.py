@@ -3,8 +3,9 @@ the oracle's right-hand side (Eq. ipsmm); the angular-moment and boundary
 correction kernels of the same file against the oracle's closures (Eqs.
 correction_tensor_disc, bdr_correction_factor_disc); and the wavefront sweep
 kernel of sweep.cu, in both FP64 local-solve forms, with the negative flux
-fixup, and in the FP32-refined form (FP64 residual, FP32 correction), against
-the oracle's upwind DG sweep (Sec. 4); and the flexible-CG operator product of
+fixup, in the FP32-refined form (FP64 residual, FP32 correction), and as the
+batched kernel over several problems, against the oracle's upwind DG sweep
+(Sec. 4); and the flexible-CG operator product of
 the moment solve against the oracle's IP-SMM matrix (Eq. ipsmm).
 
 The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
@@ -209,6 +210,7 @@ def sweep_emu(tmp_path_factory):
                      extract(sweep, "template <typename T> __device__ __forceinline__ T ldg_cg("),
                      extract(sweep, "__device__ __forceinline__ bool sweep_task("),
                      extract(sweep, "__global__ void __launch_bounds__(256) sweep_kernel("),
+                     extract(sweep, "__global__ void __launch_bounds__(256) batch_sweep_kernel("),
                      extract(sweep, "__global__ void __launch_bounds__(256) invert_kernel("),
                      extract(sweep, "__global__ void __launch_bounds__(256) residual_kernel("),
                      extract(sweep, "__global__ void mass_apply_kernel("),
@@ -285,6 +287,38 @@ def test_sweep_kernel_matches_oracle(sweep_emu, tmp_path, case):
     scale = np.max(np.abs(ref))
     for name, psi in got.items():
         assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
+
+
+def test_batched_sweep_kernel_matches_oracle(sweep_emu, tmp_path):
+    """Problems of different p, S_N, size, geometry and source kind swept by
+    one batch_sweep_kernel launch over their merged level-by-level task list
+    (each task dispatching on its problem's p), with the LU and with cached
+    inverses, each against the oracle's sweep of that problem."""
+    cases = [(3, 2, 1, 1, 4, None, "iso"), (2, 3, 2, 2, 8, 4, "mms"), (2, 2, 3, 4, 4, 2, "mms"),
+             (1, 1, 1, 3, 2, None, "iso")]
+    refs = []
+    for k, case in enumerate(cases):
+        nx, ny, m, p, sn, seed, kind = case
+        mesh, st, ss, disc, phi, q, inflow = _sweep_problem(case)
+        d = tmp_path / str(k)
+        d.mkdir()
+        for name, arr in (("nodes", mesh.nodes), ("sigma_t", st), ("sigma_s", ss), ("phi", phi), ("q", q)):
+            np.ascontiguousarray(arr, np.float64).tofile(d / f"{name}.f64")
+        np.asarray(mesh.elem_nodes, np.int32).tofile(d / "elem.i32")
+        if inflow is not None:
+            np.ascontiguousarray(inflow, np.float64).tofile(d / "inflow.f64")
+        (d / "nbface.txt").write_text(str(len(disc.bfaces)))
+        (d / "args.txt").write_text("%d %d %d %d %d %d %d" % (mesh.n_elem, len(mesh.nodes), m, p, sn, int(q.ndim == 3),
+                                                           int(inflow is not None)))
+        refs.append(disc.sweep(phi, q, inflow).transpose(1, 0, 2))
+    subprocess.run([sweep_emu, "--batch", str(tmp_path), str(len(cases))], check=True, timeout=600)
+    for k, ref in enumerate(refs):
+        d = tmp_path / str(k)
+        assert open(d / "err.txt").read().split() == ["0", "0"]
+        scale = np.max(np.abs(ref))
+        for name in ("psi_lu", "psi_inv", "psi2_inv"):
+            got = np.fromfile(d / f"{name}.f64").reshape(ref.shape)
+            assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (k, name, np.max(np.abs(got - ref)) / scale)
 
 
 def test_sweep_kernel_fixup_matches_oracle(sweep_emu, tmp_path):
