@@ -1,0 +1,97 @@
+// Test driver (CPU): one level-0 smoothing step of the moment-solve multigrid
+// preconditioner (bj_smooth_kernel of mg.cu, FP32,
+//   xout = xin + c2 Pinv (b - A xin) + c1 (xin - xprev)
+// with A applied as its face couplings and Pinv = A_d^{-1}, two elements' rows
+// per thread) run on the host through host_kernel_shim.h, on the FP32 copies of
+// the face couplings and block inverses that the library's host setup builds,
+// stored and launched as the library stores and launches them.  The kernel
+// source and the helpers of blockops.cuh arrive as smooth_kernels.inc,
+// extracted by the test.
+// Usage: smooth_emu DIR NE NNODES M P C1 C2 FIRST
+//   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, q.f64 [ne][n], DIR/b.f64 [ne][n] (FP64),
+//        DIR/xin.f32 and DIR/xprev.f32 [ne][n] (FP32; not read when FIRST = 1: xin = xprev = 0)
+//   out: DIR/xout.f32 [ne][n]
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <string>
+#include <vector>
+
+#include "host_kernel_shim.h"
+#include "setup.hpp"
+
+namespace smm {
+#include "smooth_kernels.inc"
+}
+
+template <class T>
+static bool read_file(const std::string& path, std::vector<T>& v) {
+    std::ifstream in(path, std::ios::binary);
+    in.read(reinterpret_cast<char*>(v.data()), (std::streamsize)(v.size() * sizeof(T)));
+    return (bool)in;
+}
+
+static std::vector<float> f32_transposed(const std::vector<double>& a, int n) {
+    std::vector<float> t(a.size());
+    const size_t nb = a.size() / ((size_t)n * n);
+    for (size_t b = 0; b < nb; ++b)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) t[b * n * n + (size_t)j * n + i] = (float)a[b * n * n + (size_t)i * n + j];
+    return t;
+}
+
+template <int N>
+static void run(const smm::Setup& s, float c1, float c2, const std::vector<double>& b, const float* xin,
+                const float* xprev, std::vector<float>& xout) {
+    constexpr int R = 2;  // rows per thread, as the library launches the step
+    const auto CT = f32_transposed(s.Cface, 2 * s.p1), PinvT = f32_transposed(s.Pinv, s.n);
+    smm::FaceOp<float> A;
+    A.CT = CT.data(); A.nbr = s.nbr.data(); A.nface = s.nbr_face.data();
+    for (int k = 0; k < s.p1; ++k) A.wd[k] = (float)s.wd[k];
+    const int tpb = std::max(1, 256 / N) * N, epb = smm::FaceDims<N>::EPB;
+    const int nblk = (s.ne + epb * R - 1) / (epb * R);
+    std::vector<int> ctl(8, 0);
+    xout.assign((size_t)s.ne * N, 0.0f);
+    emu_launch(nblk, tpb, 0, [&] {
+        smm::bj_smooth_kernel<float, N, R>(s.ne, A, PinvT.data(), c1, c2, b.data(), xin, xprev, xout.data(),
+                                           ctl.data());
+    });
+}
+
+int main(int argc, char** argv) {
+    if (argc != 9) return 2;
+    const std::string dir = argv[1];
+    const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
+    const float c1 = (float)std::atof(argv[6]), c2 = (float)std::atof(argv[7]);
+    const bool first = std::atoi(argv[8]) != 0;
+    const int n = (p + 1) * (p + 1);
+    std::vector<double> nodes((size_t)nn * 2), st(ne), ss(ne), qs((size_t)ne * n), b((size_t)ne * n);
+    std::vector<int32_t> elem((size_t)ne * (m + 1) * (m + 1));
+    std::vector<float> xin((size_t)ne * n, 0.0f), xprev((size_t)ne * n, 0.0f), xout;
+    if (!read_file(dir + "/nodes.f64", nodes) || !read_file(dir + "/elem.i32", elem) ||
+        !read_file(dir + "/sigma_t.f64", st) || !read_file(dir + "/sigma_s.f64", ss) ||
+        !read_file(dir + "/q.f64", qs) || !read_file(dir + "/b.f64", b))
+        return 3;
+    if (!first && (!read_file(dir + "/xin.f32", xin) || !read_file(dir + "/xprev.f32", xprev))) return 3;
+    smm::Input in;
+    in.ne = ne; in.m = m; in.p = p; in.sn = 4; in.n_nodes = nn;
+    in.nodes = nodes.data(); in.elem_nodes = elem.data(); in.sigma_t = st.data(); in.sigma_s = ss.data();
+    in.q = qs.data();
+    smm::Setup s;
+    std::string err;
+    if (smm::build_setup(in, s, err)) {
+        std::fprintf(stderr, "%s\n", err.c_str());
+        return 4;
+    }
+    const float* xi = first ? nullptr : xin.data();
+    const float* xp = first ? nullptr : xprev.data();
+    switch (n) {
+        case 4: run<4>(s, c1, c2, b, xi, xp, xout); break;
+        case 9: run<9>(s, c1, c2, b, xi, xp, xout); break;
+        case 16: run<16>(s, c1, c2, b, xi, xp, xout); break;
+        default: run<25>(s, c1, c2, b, xi, xp, xout); break;
+    }
+    std::ofstream out(dir + "/xout.f32", std::ios::binary);
+    out.write(reinterpret_cast<const char*>(xout.data()), (std::streamsize)(xout.size() * sizeof(float)));
+    return out ? 0 : 5;
+}

@@ -356,13 +356,10 @@ def test_fp32_refined_sweeps_converge_to_the_fp64_sweep(sweep_emu, tmp_path, cas
 # face-factored IP-SMM operator in FP32-pair arithmetic, p.q by the last-block
 # reduction) against the oracle's assembled IP-SMM matrix
 
-@pytest.fixture(scope="module")
-def cg_emu(tmp_path_factory):
-    cxx = shutil.which("g++") or shutil.which("c++")
-    if cxx is None:
-        pytest.skip("no C++ compiler")
-    d = tmp_path_factory.mktemp("cg_emu")
-    moments = open(os.path.join(CSRC, "moments.cu")).read()
+def _operator_helpers():
+    """The operator structs of kernels.cuh, the pair arithmetic and the row and
+    reduction helpers of blockops.cuh, its cache-policy loads (inline
+    assembly) made plain loads."""
     kcuh = open(os.path.join(CSRC, "kernels.cuh")).read()
     dfloat = open(os.path.join(CSRC, "dfloat.cuh")).read()
     blockops = open(os.path.join(CSRC, "blockops.cuh")).read()
@@ -379,9 +376,18 @@ def cg_emu(tmp_path_factory):
     for sig, repl in host.items():
         ops = ops.replace(extract(ops, sig), repl)
     assert "asm" not in ops
-    parts = [extract(kcuh, "struct FaceOp {") + ";", extract(kcuh, "struct FaceOpDF {") + ";",
-             extract(kcuh, "struct CGArgs {") + ";", body, ops,
-             extract(moments, "__global__ void __launch_bounds__(256) cgx_spmv_kernel(")]
+    return [extract(kcuh, "struct FaceOp {") + ";", extract(kcuh, "struct FaceOpDF {") + ";",
+            extract(kcuh, "struct CGArgs {") + ";", body, ops]
+
+
+@pytest.fixture(scope="module")
+def cg_emu(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("cg_emu")
+    moments = open(os.path.join(CSRC, "moments.cu")).read()
+    parts = _operator_helpers() + [extract(moments, "__global__ void __launch_bounds__(256) cgx_spmv_kernel(")]
     (d / "cg_kernels.inc").write_text("\n".join(parts))
     exe = d / "cg_emu"
     subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
@@ -423,3 +429,63 @@ def test_cg_operator_product_matches_oracle(cg_emu, tmp_path, case):
     pq = float(pv.ravel() @ q)
     assert abs(scal[1] - pq) <= 1e-12 * float(np.abs(pv.ravel()) @ np.abs(q))
     assert scal[5] == pytest.approx(1.0 / scal[1], rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# one level-0 smoothing step of the multigrid preconditioner (bj_smooth_kernel,
+# FP32) against the same step formed from the oracle's IP-SMM matrix
+
+@pytest.fixture(scope="module")
+def smooth_emu(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("smooth_emu")
+    mg = open(os.path.join(CSRC, "mg.cu")).read()
+    parts = _operator_helpers() + [extract(mg, "__device__ __forceinline__ bool mg_skip("),
+                                   extract(mg, "__global__ void __launch_bounds__(256) bj_smooth_kernel(")]
+    (d / "smooth_kernels.inc").write_text("\n".join(parts))
+    exe = d / "smooth_emu"
+    subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
+                    os.path.join(ROOT, "tests"), "-I", CSRC, os.path.join(ROOT, "tests", "smooth_emu.cpp"),
+                    os.path.join(CSRC, "setup.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+@pytest.mark.parametrize("case", CG_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_level0_smoothing_step_matches_oracle(smooth_emu, tmp_path, case):
+    """xout = xin + c2 A_d^{-1} (b - A xin) + c1 (xin - xprev) (a Chebyshev
+    step; the first step of a V-cycle has xin = xprev = 0)."""
+    from oracle import ipsmm
+    from oracle.transport import Discretization
+    nx, ny, m, p, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n = mesh.n_elem, (p + 1) ** 2
+    st = 1.0 + 0.5 * (np.arange(ne) % 3)
+    ss = 0.7 * st
+    rng = np.random.default_rng(43)
+    b = rng.standard_normal(ne * n)
+    xin = rng.standard_normal(ne * n).astype(np.float32)
+    xprev = rng.standard_normal(ne * n).astype(np.float32)
+    for name, arr in (("nodes", mesh.nodes), ("sigma_t", st), ("sigma_s", ss), ("q", np.ones((ne, n))), ("b", b)):
+        np.ascontiguousarray(arr, np.float64).tofile(tmp_path / f"{name}.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    xin.tofile(tmp_path / "xin.f32")
+    xprev.tofile(tmp_path / "xprev.f32")
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, ss)
+    A = ipsmm.assemble_lhs(disc).toarray()
+    Pinv = np.zeros_like(A)
+    for e in range(ne):
+        sl = slice(e * n, (e + 1) * n)
+        Pinv[sl, sl] = np.linalg.inv(A[sl, sl])
+    c1, c2 = 0.375, 0.8125            # exactly representable in FP32
+    for first in (1, 0):
+        subprocess.run([smooth_emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), str(c1), str(c2),
+                        str(first)], check=True, timeout=600)
+        got = np.fromfile(tmp_path / "xout.f32", dtype=np.float32).astype(np.float64)
+        x0 = np.zeros(ne * n) if first else xin.astype(np.float64)
+        xp = np.zeros(ne * n) if first else xprev.astype(np.float64)
+        ref = x0 + c2 * (Pinv @ (b - A @ x0)) + c1 * (x0 - xp)
+        scale = np.max(np.abs(x0)) + c2 * np.max(np.abs(Pinv) @ (np.abs(b) + np.abs(A) @ np.abs(x0))) + \
+            c1 * np.max(np.abs(x0) + np.abs(xp))
+        assert np.max(np.abs(got - ref)) <= 1e-5 * scale, (first, np.max(np.abs(got - ref)) / scale)
