@@ -5,8 +5,8 @@ correction_tensor_disc, bdr_correction_factor_disc); and the wavefront sweep
 kernel of sweep.cu, in both FP64 local-solve forms, with the negative flux
 fixup, in the FP32-refined form (FP64 residual, FP32 correction), and as the
 batched kernel over several problems, against the oracle's upwind DG sweep
-(Sec. 4); and the flexible-CG operator product of
-the moment solve against the oracle's IP-SMM matrix (Eq. ipsmm).
+(Sec. 4); and the flexible-CG operator product and the level-0 smoothing step
+of the moment solve against the oracle's IP-SMM matrix (Eq. ipsmm).
 
 The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
 helper and the FP32-pair arithmetic of dfloat.cuh) is taken from the CUDA
