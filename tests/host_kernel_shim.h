@@ -48,6 +48,7 @@ inline std::barrier<>* emu_block_barrier = nullptr;
 // share (blocks run one after another)
 #define __shared__ static
 #define __syncthreads() emu_block_barrier->arrive_and_wait()
+using std::isfinite;
 using std::max;
 using std::min;
 

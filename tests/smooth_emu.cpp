@@ -7,10 +7,17 @@
 // stored and launched as the library stores and launches them.  The kernel
 // source and the helpers of blockops.cuh arrive as smooth_kernels.inc,
 // extracted by the test.
-// Usage: smooth_emu DIR NE NNODES M P C1 C2 FIRST
-//   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, q.f64 [ne][n], DIR/b.f64 [ne][n] (FP64),
-//        DIR/xin.f32 and DIR/xprev.f32 [ne][n] (FP32; not read when FIRST = 1: xin = xprev = 0)
-//   out: DIR/xout.f32 [ne][n]
+// MODE 2 runs instead the last smoothing step of a V-cycle inside the flexible
+// CG (bj_last_dots_kernel): the step in FP64 output z with b = r, the dots r.z
+// and (r - r_old).z per block, and in the last block beta = (r - r_old).z /
+// rz_old, the new rz, rr from the first step's partials, the iteration count
+// and the convergence test.
+// Usage: smooth_emu DIR NE NNODES M P C1 C2 MODE   (MODE 1: first step, 0: inner step, 2: last step)
+//   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, q.f64 [ne][n], DIR/b.f64 [ne][n] (FP64; r in
+//        MODE 2), DIR/xin.f32 and DIR/xprev.f32 [ne][n] (FP32; not read in MODE 1: xin = xprev = 0);
+//        MODE 2 also DIR/rold.f64 [ne][n], DIR/cg.f64 (rz_old, rr threshold, then the first step's rr
+//        partials, one per block)
+//   out: DIR/xout.f32 [ne][n] (MODE 0, 1); MODE 2: DIR/z.f64 [ne][n], DIR/scal.f64 [8], DIR/ctl.i32 [8]
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -58,12 +65,49 @@ static void run(const smm::Setup& s, float c1, float c2, const std::vector<doubl
     });
 }
 
+template <int N>
+static bool run_last(const std::string& dir, const smm::Setup& s, float c1, float c2, std::vector<double>& r,
+                     const std::vector<float>& xin, const std::vector<float>& xprev) {
+    constexpr int R = 2;
+    const int ne = s.ne;
+    const auto CT = f32_transposed(s.Cface, 2 * s.p1), PinvT = f32_transposed(s.Pinv, s.n);
+    smm::FaceOp<float> A;
+    A.CT = CT.data(); A.nbr = s.nbr.data(); A.nface = s.nbr_face.data();
+    for (int k = 0; k < s.p1; ++k) A.wd[k] = (float)s.wd[k];
+    const int tpb = std::max(1, 256 / N) * N, epb = smm::FaceDims<N>::EPB;
+    const int grid = (ne + epb * R - 1) / (epb * R);
+    const int nblk = grid + 3;  // the row kernels' block count sets the partials' stride; any count >= grid
+    std::vector<double> rold((size_t)ne * N), cg(2 + grid), z((size_t)ne * N, 0.0), part(4 * (size_t)nblk, 0.0);
+    if (!read_file(dir + "/rold.f64", rold) || !read_file(dir + "/cg.f64", cg)) return false;
+    for (int b = 0; b < grid; ++b) part[nblk + b] = cg[2 + b];
+    std::vector<double> scal(8, 0.0);
+    std::vector<int> ctl(8, 0);
+    scal[0] = cg[0];
+    scal[4] = cg[1];
+    ctl[1] = 5;   // iterations so far
+    ctl[2] = 100; // iteration limit
+    smm::CGArgs a{};
+    a.ne = ne; a.n = N; a.nrow = ne * N; a.nblk = nblk;
+    a.r = r.data(); a.rold = rold.data(); a.z = z.data(); a.part = part.data(); a.scal = scal.data();
+    a.ctl = ctl.data();
+    emu_launch(grid, tpb, 0, [&] {
+        smm::bj_last_dots_kernel<N, R>(a, A, PinvT.data(), c1, c2, xin.data(), xprev.data());
+    });
+    std::ofstream oz(dir + "/z.f64", std::ios::binary), os(dir + "/scal.f64", std::ios::binary),
+        oc(dir + "/ctl.i32", std::ios::binary);
+    oz.write(reinterpret_cast<const char*>(z.data()), (std::streamsize)(z.size() * sizeof(double)));
+    os.write(reinterpret_cast<const char*>(scal.data()), (std::streamsize)(scal.size() * sizeof(double)));
+    oc.write(reinterpret_cast<const char*>(ctl.data()), (std::streamsize)(ctl.size() * sizeof(int)));
+    return (bool)oz && (bool)os && (bool)oc;
+}
+
 int main(int argc, char** argv) {
     if (argc != 9) return 2;
     const std::string dir = argv[1];
     const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
     const float c1 = (float)std::atof(argv[6]), c2 = (float)std::atof(argv[7]);
-    const bool first = std::atoi(argv[8]) != 0;
+    const int mode = std::atoi(argv[8]);
+    const bool first = mode == 1;
     const int n = (p + 1) * (p + 1);
     std::vector<double> nodes((size_t)nn * 2), st(ne), ss(ne), qs((size_t)ne * n), b((size_t)ne * n);
     std::vector<int32_t> elem((size_t)ne * (m + 1) * (m + 1));
@@ -82,6 +126,16 @@ int main(int argc, char** argv) {
     if (smm::build_setup(in, s, err)) {
         std::fprintf(stderr, "%s\n", err.c_str());
         return 4;
+    }
+    if (mode == 2) {
+        bool ok = false;
+        switch (n) {
+            case 4: ok = run_last<4>(dir, s, c1, c2, b, xin, xprev); break;
+            case 9: ok = run_last<9>(dir, s, c1, c2, b, xin, xprev); break;
+            case 16: ok = run_last<16>(dir, s, c1, c2, b, xin, xprev); break;
+            default: ok = run_last<25>(dir, s, c1, c2, b, xin, xprev); break;
+        }
+        return ok ? 0 : 5;
     }
     const float* xi = first ? nullptr : xin.data();
     const float* xp = first ? nullptr : xprev.data();

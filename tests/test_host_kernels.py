@@ -443,7 +443,8 @@ def smooth_emu(tmp_path_factory):
     d = tmp_path_factory.mktemp("smooth_emu")
     mg = open(os.path.join(CSRC, "mg.cu")).read()
     parts = _operator_helpers() + [extract(mg, "__device__ __forceinline__ bool mg_skip("),
-                                   extract(mg, "__global__ void __launch_bounds__(256) bj_smooth_kernel(")]
+                                   extract(mg, "__global__ void __launch_bounds__(256) bj_smooth_kernel("),
+                                   extract(mg, "__global__ void __launch_bounds__(256) bj_last_dots_kernel(")]
     (d / "smooth_kernels.inc").write_text("\n".join(parts))
     exe = d / "smooth_emu"
     subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
@@ -489,3 +490,56 @@ def test_level0_smoothing_step_matches_oracle(smooth_emu, tmp_path, case):
         scale = np.max(np.abs(x0)) + c2 * np.max(np.abs(Pinv) @ (np.abs(b) + np.abs(A) @ np.abs(x0))) + \
             c1 * np.max(np.abs(x0) + np.abs(xp))
         assert np.max(np.abs(got - ref)) <= 1e-5 * scale, (first, np.max(np.abs(got - ref)) / scale)
+
+
+@pytest.mark.parametrize("case", CG_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_last_smoothing_step_and_cg_dots_match_oracle(smooth_emu, tmp_path, case):
+    """The last level-0 step inside the flexible CG: z (FP64 output of the
+    FP32 step with b = r), and from the last block beta = (r - r_old).z /
+    rz_old, rz = r.z, rr = the sum of the first step's partials, the iteration
+    count and the convergence flag (blocks with a partial last warp for p = 2, 4)."""
+    from oracle import ipsmm
+    from oracle.transport import Discretization
+    nx, ny, m, p, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n = mesh.n_elem, (p + 1) ** 2
+    st = 1.0 + 0.5 * (np.arange(ne) % 3)
+    ss = 0.7 * st
+    rng = np.random.default_rng(47)
+    r = rng.standard_normal(ne * n)
+    rold = rng.standard_normal(ne * n)
+    xin = rng.standard_normal(ne * n).astype(np.float32)
+    xprev = rng.standard_normal(ne * n).astype(np.float32)
+    epb = 256 // n
+    grid = (ne + 2 * epb - 1) // (2 * epb)
+    rr_parts = rng.uniform(0.5, 1.5, grid)
+    rz_old, thresh = 2.5, float(rr_parts.sum()) * 1.001        # rr just below the threshold: converged
+    for name, arr in (("nodes", mesh.nodes), ("sigma_t", st), ("sigma_s", ss), ("q", np.ones((ne, n))), ("b", r),
+                      ("rold", rold), ("cg", np.concatenate([[rz_old, thresh], rr_parts]))):
+        np.ascontiguousarray(arr, np.float64).tofile(tmp_path / f"{name}.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    xin.tofile(tmp_path / "xin.f32")
+    xprev.tofile(tmp_path / "xprev.f32")
+    c1, c2 = 0.375, 0.8125
+    subprocess.run([smooth_emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), str(c1), str(c2), "2"],
+                   check=True, timeout=600)
+    z = np.fromfile(tmp_path / "z.f64")
+    scal = np.fromfile(tmp_path / "scal.f64")
+    ctl = np.fromfile(tmp_path / "ctl.i32", dtype=np.int32)
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, ss)
+    A = ipsmm.assemble_lhs(disc).toarray()
+    Pinv = np.zeros_like(A)
+    for e in range(ne):
+        sl = slice(e * n, (e + 1) * n)
+        Pinv[sl, sl] = np.linalg.inv(A[sl, sl])
+    x0, xp = xin.astype(np.float64), xprev.astype(np.float64)
+    ref = x0 + c2 * (Pinv @ (r - A @ x0)) + c1 * (x0 - xp)
+    scale = np.max(np.abs(x0)) + c2 * np.max(np.abs(Pinv) @ (np.abs(r) + np.abs(A) @ np.abs(x0))) + \
+        c1 * np.max(np.abs(x0) + np.abs(xp))
+    assert np.max(np.abs(z - ref)) <= 1e-5 * scale
+    # the dots of the kernel's own z, in FP64: every row counted once
+    assert scal[0] == pytest.approx(float(r @ z), rel=1e-12, abs=1e-12 * float(np.abs(r) @ np.abs(z)))
+    dz = float((r - rold) @ z)
+    assert scal[6] * rz_old == pytest.approx(dz, rel=1e-12, abs=1e-12 * float(np.abs(r - rold) @ np.abs(z)))
+    assert scal[2] == pytest.approx(float(rr_parts.sum()), rel=1e-14)
+    assert ctl[1] == 6 and ctl[0] == 1 and ctl[3] == 0 and ctl[6] == 0
