@@ -12,6 +12,11 @@
 // and (r - r_old).z per block, and in the last block beta = (r - r_old).z /
 // rz_old, the new rz, rr from the first step's partials, the iteration count
 // and the convergence test.
+// MODE 3 runs the first step of a V-cycle inside the flexible CG
+// (bj_first_update_kernel): the CG update x += alpha p, r_old = r, r -= alpha q
+// folded in, xout = c2 Pinv r, and the per-block partials of r.r.
+//   MODE 3 in: DIR/b.f64 holds r, DIR/x.f64, p.f64, q.f64 [ne][n], DIR/cg.f64 (alpha);
+//   out: DIR/x_out.f64, r_out.f64, rold_out.f64 [ne][n], DIR/xout.f32, DIR/rr.f64 (the partials)
 // Usage: smooth_emu DIR NE NNODES M P C1 C2 MODE   (MODE 1: first step, 0: inner step, 2: last step)
 //   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, q.f64 [ne][n], DIR/b.f64 [ne][n] (FP64; r in
 //        MODE 2), DIR/xin.f32 and DIR/xprev.f32 [ne][n] (FP32; not read in MODE 1: xin = xprev = 0);
@@ -101,6 +106,39 @@ static bool run_last(const std::string& dir, const smm::Setup& s, float c1, floa
     return (bool)oz && (bool)os && (bool)oc;
 }
 
+template <class T>
+static bool write_vec(const std::string& path, const std::vector<T>& v) {
+    std::ofstream out(path, std::ios::binary);
+    out.write(reinterpret_cast<const char*>(v.data()), (std::streamsize)(v.size() * sizeof(T)));
+    return (bool)out;
+}
+
+template <int N>
+static bool run_first_update(const std::string& dir, const smm::Setup& s, float c2, std::vector<double>& r) {
+    constexpr int R = 2;
+    const int ne = s.ne;
+    const auto PinvT = f32_transposed(s.Pinv, s.n);
+    const int tpb = std::max(1, 256 / N) * N, epb = smm::FaceDims<N>::EPB;
+    const int grid = (ne + epb * R - 1) / (epb * R);
+    const int nblk = grid + 3;
+    std::vector<double> x((size_t)ne * N), pv((size_t)ne * N), q((size_t)ne * N), alpha(1);
+    std::vector<double> rold((size_t)ne * N, 0.0), part(4 * (size_t)nblk, 0.0), scal(8, 0.0);
+    std::vector<float> xout((size_t)ne * N, 0.0f);
+    std::vector<int> ctl(8, 0);
+    if (!read_file(dir + "/x.f64", x) || !read_file(dir + "/p.f64", pv) || !read_file(dir + "/q.f64", q) ||
+        !read_file(dir + "/cg.f64", alpha))
+        return false;
+    scal[5] = alpha[0];
+    smm::CGArgs a{};
+    a.ne = ne; a.n = N; a.nrow = ne * N; a.nblk = nblk;
+    a.x = x.data(); a.p = pv.data(); a.q = q.data(); a.r = r.data(); a.rold = rold.data(); a.part = part.data();
+    a.scal = scal.data(); a.ctl = ctl.data();
+    emu_launch(grid, tpb, 0, [&] { smm::bj_first_update_kernel<N, R>(a, PinvT.data(), c2, xout.data()); });
+    const std::vector<double> rr(part.begin() + nblk, part.begin() + nblk + grid);
+    return write_vec(dir + "/x_out.f64", x) && write_vec(dir + "/r_out.f64", r) &&
+           write_vec(dir + "/rold_out.f64", rold) && write_vec(dir + "/xout.f32", xout) && write_vec(dir + "/rr.f64", rr);
+}
+
 int main(int argc, char** argv) {
     if (argc != 9) return 2;
     const std::string dir = argv[1];
@@ -116,7 +154,8 @@ int main(int argc, char** argv) {
         !read_file(dir + "/sigma_t.f64", st) || !read_file(dir + "/sigma_s.f64", ss) ||
         !read_file(dir + "/q.f64", qs) || !read_file(dir + "/b.f64", b))
         return 3;
-    if (!first && (!read_file(dir + "/xin.f32", xin) || !read_file(dir + "/xprev.f32", xprev))) return 3;
+    if ((mode == 0 || mode == 2) && (!read_file(dir + "/xin.f32", xin) || !read_file(dir + "/xprev.f32", xprev)))
+        return 3;
     smm::Input in;
     in.ne = ne; in.m = m; in.p = p; in.sn = 4; in.n_nodes = nn;
     in.nodes = nodes.data(); in.elem_nodes = elem.data(); in.sigma_t = st.data(); in.sigma_s = ss.data();
@@ -126,6 +165,16 @@ int main(int argc, char** argv) {
     if (smm::build_setup(in, s, err)) {
         std::fprintf(stderr, "%s\n", err.c_str());
         return 4;
+    }
+    if (mode == 3) {
+        bool ok = false;
+        switch (n) {
+            case 4: ok = run_first_update<4>(dir, s, c2, b); break;
+            case 9: ok = run_first_update<9>(dir, s, c2, b); break;
+            case 16: ok = run_first_update<16>(dir, s, c2, b); break;
+            default: ok = run_first_update<25>(dir, s, c2, b); break;
+        }
+        return ok ? 0 : 5;
     }
     if (mode == 2) {
         bool ok = false;

@@ -6,7 +6,9 @@ kernel of sweep.cu, in both FP64 local-solve forms, with the negative flux
 fixup, in the FP32-refined form (FP64 residual, FP32 correction), and as the
 batched kernel over several problems, against the oracle's upwind DG sweep
 (Sec. 4); and the flexible-CG operator product and the level-0 smoothing step
-of the moment solve against the oracle's IP-SMM matrix (Eq. ipsmm).
+of the moment solve (first, inner and last steps, with the CG update and dot
+products folded into the first and last) against the oracle's IP-SMM matrix
+(Eq. ipsmm).
 
 The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
 helper and the FP32-pair arithmetic of dfloat.cuh) is taken from the CUDA
@@ -444,7 +446,8 @@ def smooth_emu(tmp_path_factory):
     mg = open(os.path.join(CSRC, "mg.cu")).read()
     parts = _operator_helpers() + [extract(mg, "__device__ __forceinline__ bool mg_skip("),
                                    extract(mg, "__global__ void __launch_bounds__(256) bj_smooth_kernel("),
-                                   extract(mg, "__global__ void __launch_bounds__(256) bj_last_dots_kernel(")]
+                                   extract(mg, "__global__ void __launch_bounds__(256) bj_last_dots_kernel("),
+                                   extract(mg, "__global__ void __launch_bounds__(256) bj_first_update_kernel(")]
     (d / "smooth_kernels.inc").write_text("\n".join(parts))
     exe = d / "smooth_emu"
     subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
@@ -543,3 +546,39 @@ def test_last_smoothing_step_and_cg_dots_match_oracle(smooth_emu, tmp_path, case
     assert scal[6] * rz_old == pytest.approx(dz, rel=1e-12, abs=1e-12 * float(np.abs(r - rold) @ np.abs(z)))
     assert scal[2] == pytest.approx(float(rr_parts.sum()), rel=1e-14)
     assert ctl[1] == 6 and ctl[0] == 1 and ctl[3] == 0 and ctl[6] == 0
+
+
+@pytest.mark.parametrize("case", CG_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_first_smoothing_step_with_cg_update_matches_oracle(smooth_emu, tmp_path, case):
+    """The first level-0 step inside the flexible CG: x += alpha p, r_old = r,
+    r -= alpha q (FP64), xout = c2 A_d^{-1} r (FP32), and per-block partials of
+    r.r that add up to the new r.r (blocks with a partial last warp for p = 2, 4)."""
+    from oracle import ipsmm
+    from oracle.transport import Discretization
+    nx, ny, m, p, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n = mesh.n_elem, (p + 1) ** 2
+    st = 1.0 + 0.5 * (np.arange(ne) % 3)
+    ss = 0.7 * st
+    rng = np.random.default_rng(53)
+    r, x, pv, q = (rng.standard_normal(ne * n) for _ in range(4))
+    alpha = 0.7071
+    for name, arr in (("nodes", mesh.nodes), ("sigma_t", st), ("sigma_s", ss), ("q", q), ("b", r), ("x", x),
+                      ("p", pv), ("cg", np.array([alpha]))):
+        np.ascontiguousarray(arr, np.float64).tofile(tmp_path / f"{name}.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    c2 = 0.8125
+    subprocess.run([smooth_emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), "0", str(c2), "3"],
+                   check=True, timeout=600)
+    rn = r - alpha * q
+    assert np.array_equal(np.fromfile(tmp_path / "x_out.f64"), x + alpha * pv)
+    assert np.array_equal(np.fromfile(tmp_path / "r_out.f64"), rn)
+    assert np.array_equal(np.fromfile(tmp_path / "rold_out.f64"), r)
+    assert np.fromfile(tmp_path / "rr.f64").sum() == pytest.approx(float(rn @ rn), rel=1e-13)
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, ss)
+    A = ipsmm.assemble_lhs(disc).toarray()
+    ref = np.concatenate([c2 * np.linalg.solve(A[e * n:(e + 1) * n, e * n:(e + 1) * n], rn[e * n:(e + 1) * n])
+                          for e in range(ne)])
+    got = np.fromfile(tmp_path / "xout.f32", dtype=np.float32).astype(np.float64)
+    # FP32 block inverses and residual: rounding of a few parts in 1e7, amplified by the blocks' conditioning
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
