@@ -17,6 +17,10 @@
 // folded in, xout = c2 Pinv r, and the per-block partials of r.r.
 //   MODE 3 in: DIR/b.f64 holds r, DIR/x.f64, p.f64, q.f64 [ne][n], DIR/cg.f64 (alpha);
 //   out: DIR/x_out.f64, r_out.f64, rold_out.f64 [ne][n], DIR/xout.f32, DIR/rr.f64 (the partials)
+// MODE 4 runs the level-0 residual restricted to the element corners
+// (bj_residual_kernel): cres[e][c] = sum_i w4[i][c] (b - A x)[e][i] with the
+// diagonal blocks entering as W = w4^T A_d, formed here as the library forms it.
+//   MODE 4 in: DIR/b.f64 [ne][n], DIR/xin.f32 [ne][n], DIR/w4.f64 [n][4]; out: DIR/cres.f32 [ne][4]
 // Usage: smooth_emu DIR NE NNODES M P C1 C2 MODE   (MODE 1: first step, 0: inner step, 2: last step)
 //   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, q.f64 [ne][n], DIR/b.f64 [ne][n] (FP64; r in
 //        MODE 2), DIR/xin.f32 and DIR/xprev.f32 [ne][n] (FP32; not read in MODE 1: xin = xprev = 0);
@@ -139,6 +143,39 @@ static bool run_first_update(const std::string& dir, const smm::Setup& s, float 
            write_vec(dir + "/rold_out.f64", rold) && write_vec(dir + "/xout.f32", xout) && write_vec(dir + "/rr.f64", rr);
 }
 
+template <int N>
+static bool run_residual(const std::string& dir, const smm::Setup& s, const std::vector<double>& b,
+                         const std::vector<float>& x) {
+    constexpr int R = 2;
+    const int ne = s.ne;
+    std::vector<double> w4d((size_t)N * 4);
+    if (!read_file(dir + "/w4.f64", w4d)) return false;
+    const std::vector<float> w4(w4d.begin(), w4d.end());
+    std::vector<float> WdT((size_t)ne * N * 4);
+    for (int e = 0; e < ne; ++e)
+        for (int j = 0; j < N; ++j)
+            for (int c = 0; c < 4; ++c) {
+                double acc = 0.0;
+                for (int i = 0; i < N; ++i) acc += w4d[(size_t)i * 4 + c] * s.Adiag[((size_t)e * N + i) * N + j];
+                WdT[((size_t)e * N + j) * 4 + c] = (float)acc;
+            }
+    const auto CT = f32_transposed(s.Cface, 2 * s.p1);
+    smm::FaceOp<float> A;
+    A.CT = CT.data(); A.nbr = s.nbr.data(); A.nface = s.nbr_face.data();
+    for (int k = 0; k < s.p1; ++k) A.wd[k] = (float)s.wd[k];
+    const int tpb = std::max(1, 256 / N) * N, epb = smm::FaceDims<N>::EPB;
+    const int grid = (ne + epb * R - 1) / (epb * R);
+    std::vector<float> cres((size_t)ne * 4, 0.0f);
+    std::vector<int> ctl(8, 0);
+    emu_launch(grid, tpb, 0, [&] {
+        smm::bj_residual_kernel<N, R>(ne, A, WdT.data(), b.data(), x.data(), w4.data(), cres.data(), nullptr, 0,
+                                      ctl.data());
+    });
+    std::ofstream out(dir + "/cres.f32", std::ios::binary);
+    out.write(reinterpret_cast<const char*>(cres.data()), (std::streamsize)(cres.size() * sizeof(float)));
+    return (bool)out;
+}
+
 int main(int argc, char** argv) {
     if (argc != 9) return 2;
     const std::string dir = argv[1];
@@ -156,6 +193,7 @@ int main(int argc, char** argv) {
         return 3;
     if ((mode == 0 || mode == 2) && (!read_file(dir + "/xin.f32", xin) || !read_file(dir + "/xprev.f32", xprev)))
         return 3;
+    if (mode == 4 && !read_file(dir + "/xin.f32", xin)) return 3;
     smm::Input in;
     in.ne = ne; in.m = m; in.p = p; in.sn = 4; in.n_nodes = nn;
     in.nodes = nodes.data(); in.elem_nodes = elem.data(); in.sigma_t = st.data(); in.sigma_s = ss.data();
@@ -165,6 +203,16 @@ int main(int argc, char** argv) {
     if (smm::build_setup(in, s, err)) {
         std::fprintf(stderr, "%s\n", err.c_str());
         return 4;
+    }
+    if (mode == 4) {
+        bool ok = false;
+        switch (n) {
+            case 4: ok = run_residual<4>(dir, s, b, xin); break;
+            case 9: ok = run_residual<9>(dir, s, b, xin); break;
+            case 16: ok = run_residual<16>(dir, s, b, xin); break;
+            default: ok = run_residual<25>(dir, s, b, xin); break;
+        }
+        return ok ? 0 : 5;
     }
     if (mode == 3) {
         bool ok = false;

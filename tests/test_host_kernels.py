@@ -7,8 +7,8 @@ fixup, in the FP32-refined form (FP64 residual, FP32 correction), and as the
 batched kernel over several problems, against the oracle's upwind DG sweep
 (Sec. 4); and the flexible-CG operator product and the level-0 smoothing step
 of the moment solve (first, inner and last steps, with the CG update and dot
-products folded into the first and last) against the oracle's IP-SMM matrix
-(Eq. ipsmm).
+products folded into the first and last, and the residual restricted to the
+element corners) against the oracle's IP-SMM matrix (Eq. ipsmm).
 
 The kernel source (rhs_trace_kernel, rhs_assemble_kernel, the T staging
 helper and the FP32-pair arithmetic of dfloat.cuh) is taken from the CUDA
@@ -444,7 +444,12 @@ def smooth_emu(tmp_path_factory):
         pytest.skip("no C++ compiler")
     d = tmp_path_factory.mktemp("smooth_emu")
     mg = open(os.path.join(CSRC, "mg.cu")).read()
-    parts = _operator_helpers() + [extract(mg, "__device__ __forceinline__ bool mg_skip("),
+    kcuh = open(os.path.join(CSRC, "kernels.cuh")).read()
+    # the L2 prefetch (inline assembly) of the residual kernel is a no-op here
+    parts = _operator_helpers() + [extract(kcuh, "struct L2Chunk {") + ";",
+                                   "inline void prefetch_l2(const void*, unsigned) {}",
+                                   extract(mg, "__device__ __forceinline__ bool mg_skip("),
+                                   extract(mg, "__global__ void __launch_bounds__(256) bj_residual_kernel("),
                                    extract(mg, "__global__ void __launch_bounds__(256) bj_smooth_kernel("),
                                    extract(mg, "__global__ void __launch_bounds__(256) bj_last_dots_kernel("),
                                    extract(mg, "__global__ void __launch_bounds__(256) bj_first_update_kernel(")]
@@ -582,3 +587,35 @@ def test_first_smoothing_step_with_cg_update_matches_oracle(smooth_emu, tmp_path
     got = np.fromfile(tmp_path / "xout.f32", dtype=np.float32).astype(np.float64)
     # FP32 block inverses and residual: rounding of a few parts in 1e7, amplified by the blocks' conditioning
     assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("case", CG_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
+def test_level0_residual_corner_sums_match_oracle(smooth_emu, tmp_path, case):
+    """The level-0 residual restricted to the element corners, w4^T (b - A x)
+    per element, with the diagonal blocks entering as W = w4^T A_d (any
+    weights w4 [n][4]; the library's are the bilinear ones)."""
+    from oracle import ipsmm
+    from oracle.transport import Discretization
+    nx, ny, m, p, seed = case
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    ne, n = mesh.n_elem, (p + 1) ** 2
+    st = 1.0 + 0.5 * (np.arange(ne) % 3)
+    ss = 0.7 * st
+    rng = np.random.default_rng(59)
+    b = rng.standard_normal(ne * n)
+    x = rng.standard_normal(ne * n).astype(np.float32)
+    w4 = rng.uniform(0.0, 1.0, (n, 4))
+    for name, arr in (("nodes", mesh.nodes), ("sigma_t", st), ("sigma_s", ss), ("q", np.ones((ne, n))), ("b", b),
+                      ("w4", w4)):
+        np.ascontiguousarray(arr, np.float64).tofile(tmp_path / f"{name}.f64")
+    np.asarray(mesh.elem_nodes, np.int32).tofile(tmp_path / "elem.i32")
+    x.tofile(tmp_path / "xin.f32")
+    subprocess.run([smooth_emu, str(tmp_path), str(ne), str(len(mesh.nodes)), str(m), str(p), "0", "0", "4"],
+                   check=True, timeout=600)
+    got = np.fromfile(tmp_path / "cres.f32", dtype=np.float32).astype(np.float64).reshape(ne, 4)
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, ss)
+    A = ipsmm.assemble_lhs(disc).toarray()
+    res = (b - A @ x.astype(np.float64)).reshape(ne, n)
+    ref = res @ w4
+    scale = np.max((np.abs(b) + np.abs(A) @ np.abs(x.astype(np.float64))).reshape(ne, n) @ w4)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * scale, np.max(np.abs(got - ref)) / scale
