@@ -104,12 +104,17 @@ typedef struct {
                                    acceleration of that depth (paper Sec. "The
                                    Moment Method Algorithm"; depth 2 in its
                                    crooked-pipe runs), with moment-sized history */
-    int32_t guess_check;        /* smm_iterate: if nonzero and the first step from
-                                   the given guess x0 changes it by more than
-                                   the zero guess would (max|G(x0)-x0| >
-                                   max|G(x0)|, the first residual of the zero
-                                   guess being max|G(0)| ~ max|G(x0)|), restart
-                                   from zero (default 0) */
+    int32_t guess_check;        /* smm_iterate: if nonzero and the first outer step
+                                   from the given guess x0 moves it farther than
+                                   its image is from zero, i.e.
+                                   max|G(x0) - x0| > max|G(x0) - 0|, the guess is
+                                   rejected and the iteration restarts from zero
+                                   with an empty Anderson history.  This compares
+                                   the guess with the zero vector as starting
+                                   points for the same image G(x0); it stands in
+                                   for the first residual of the zero guess,
+                                   max|G(0)|, which would cost one more outer
+                                   step (default 0) */
     int32_t mg_smooth_steps;    /* multigrid preconditioner: smoothing steps on
                                    the DG level before and after the coarse
                                    correction (the Chebyshev degree with
@@ -167,6 +172,15 @@ typedef struct {
                                    profilers that do not see kernels inside
                                    conditional graph nodes).  The same
                                    arithmetic either way. */
+    int32_t resume_history;     /* smm_iterate / smm_batch_iterate: 0 (default)
+                                   starts every call with an empty Anderson
+                                   history; nonzero continues the history that
+                                   the previous call on the handle left (or that
+                                   smm_set_state restored), so that an iteration
+                                   split over several calls, or restarted from a
+                                   checkpoint, takes the same steps as one
+                                   uninterrupted call.  The caller passes the
+                                   iterate the previous call returned. */
 } smm_options;
 
 typedef struct {
@@ -196,10 +210,15 @@ void smm_default_options(smm_options* opt);
  * Errors: SMM_ERR_INVALID_ARG for unsupported orders. */
 smm_status smm_quadrature(int32_t sn_order, double* omega_out, double* w_out, int32_t* n_ord_out);
 
-/* Build a solver: geometry factors, element and face matrices, upwind
- * level lists per ordinate, the IP-SMM operator blocks and its block-Jacobi
- * preconditioner; uploads everything to the device of cuda_stream (NULL =
- * legacy default stream of the current device).
+/* Build a solver for the transport problem of Eqs. transport and inflow
+ * (Sec. "Moment Methods for Radiation Transport") on a mesh of curved
+ * quadrilaterals with the DG discretization of Sec. "Transport
+ * Discretization" (nodal Q_p on Gauss-Lobatto points, upwind fluxes) and the
+ * IP-SMM moment system of Eq. ipsmm (penalty kappa of Sec. "Results"):
+ * geometry factors, element and face matrices, upwind level lists per
+ * ordinate, the IP-SMM operator blocks and its preconditioner; uploads
+ * everything to the device of cuda_stream (NULL = legacy default stream of
+ * the current device).  The handle owns all device memory it allocates.
  *   p: DG order 1..4.  sn_order: see smm_quadrature.
  *   sigma_t, sigma_s: host [n_elem], piecewise constant, sigma_t > 0,
  *     0 <= sigma_s <= sigma_t.
@@ -222,13 +241,17 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order,
 smm_status smm_get_info(smm_handle h, smm_info* info);
 
 /* One transport sweep psi = L^{-1}(sigma_s/(4 pi) varphi + q) over all
- * ordinates, followed by the angular moments and the boundary correction
- * (Eqs. correction_tensor_disc, bdr_correction_factor_disc), kept in the
- * handle.  phi_dev: dev [n_elem][n] FP64, or NULL for varphi = 0.
+ * ordinates (Sec. "Transport Discretization"), followed by the angular
+ * moments and the boundary correction (Eqs. correction_tensor_disc,
+ * bdr_correction_factor_disc), kept in the handle.
+ *   phi_dev: dev [n_elem][n] FP64, or NULL for varphi = 0.
+ *   phiT_out: NULL, or host or device [n_elem][n] FP64 that receives the
+ *     transport scalar flux phi_T = sum_d w_d psi_d of this sweep.
  * In SMM_SWEEP_FP32_REFINED mode the sweep corrects the handle's current
  * angular flux (zero after create) and repeated calls converge to the FP64
- * result.  Errors: DEVICE_TIMEOUT, CUDA. */
-smm_status smm_sweep(smm_handle h, const double* phi_dev);
+ * result.  Errors: DEVICE_TIMEOUT (the handle stays usable; the next sweep
+ * starts afresh), CUDA. */
+smm_status smm_sweep(smm_handle h, const double* phi_dev, double* phiT_out);
 
 /* Copy the moments of the last sweep.  moments_dev: dev [6][n_elem][n]
  * (phi, Jx, Jy, Txx, Txy, Tyy), or NULL; beta_dev: dev [n_bface][n_fq]
@@ -254,14 +277,47 @@ smm_status smm_get_psi(smm_handle h, double* psi_dev);
  * Errors: NOT_CONVERGED (phi_dev holds the last iterate), NONFINITE, CUDA. */
 smm_status smm_moment_solve(smm_handle h, double* phi_dev, int32_t* cg_iters);
 
-/* The SMM fixed-point iteration from the guess in phi_dev (dev [n_elem][n]):
- * sweep, moments, right-hand side, moment solve, until
+/* The SMM fixed-point iteration of Eqs. moment:smm_fp and fixed-point
+ * (Sec. "The Moment Method Algorithm"), varphi^{k+1} = G(varphi^k): sweep,
+ * moments, right-hand side, moment solve, until
  * max|varphi^{k+1}-varphi^k| < tol (relative == 0) or
  * max|varphi^{k+1}-varphi^k| / max|varphi^{k+1}| < tol (relative != 0), or
- * max_outer steps.  phi_dev receives the last iterate.  stats may be NULL.
- * Errors: NOT_CONVERGED, NONFINITE, DEVICE_TIMEOUT, CUDA. */
-smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_outer,
-                       double* phi_dev, smm_stats* stats);
+ * max_outer steps; with options.anderson_depth > 0 the steps are Anderson
+ * accelerated.
+ *   phi: host or device [n_elem][n] FP64 (the library tells them apart from
+ *     the pointer): the guess on entry, the last iterate on return (also
+ *     after NOT_CONVERGED and NONFINITE).  A host array is copied to the
+ *     device once before the first step and back once after the last.
+ *   stats: host, may be NULL.
+ * Errors: INVALID_ARG, NOT_CONVERGED, NONFINITE, DEVICE_TIMEOUT, CUDA. */
+smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_outer, double* phi,
+                       smm_stats* stats);
+
+/* Change the bound on every device-side wait of the handle's later sweeps
+ * (options.spin_timeout_s; Sec. "Transport Discretization" orders the sweep
+ * by upwind dependencies, whose waits these are).  seconds > 0, else
+ * INVALID_ARG.  After a wait expires (DEVICE_TIMEOUT) the handle stays
+ * usable: the next sweep uses a new flag epoch, so flags left by the aborted
+ * sweep are never taken for finished work. */
+smm_status smm_set_spin_timeout(smm_handle h, double seconds);
+
+/* ---- Checkpoint ----
+ * The state a later call depends on besides its arguments: the angular flux
+ * of the last sweep (which the next FP32-refined sweep corrects and a block
+ * Jacobi sweep lags), the moments and boundary correction (the next moment
+ * solve's closures), the previous iterate and the Anderson history with its
+ * length.  Restoring it into a handle created with the same mesh, data and
+ * options makes the following calls return bit for bit what they would have
+ * returned on the saved handle.  The buffer is opaque (a 256-byte header,
+ * then the arrays), host or device memory alike, owned by the caller.
+ *   smm_state_size: *bytes = the size of the state.
+ *   smm_get_state: write it to buf (at least that many bytes).
+ *   smm_set_state: restore it from buf.
+ * Errors: INVALID_ARG (small buffer; a state of another shape or mode),
+ * CUDA. */
+smm_status smm_state_size(smm_handle h, int64_t* bytes);
+smm_status smm_get_state(smm_handle h, void* buf, int64_t bytes);
+smm_status smm_set_state(smm_handle h, const void* buf, int64_t bytes);
 
 smm_status smm_destroy(smm_handle h);
 
@@ -344,8 +400,10 @@ smm_status smm_guess_destroy(smm_guess g);
  *   Stops when ||r||_2 <= tol ||b||_2 or after max_iters iterations.
  *   cuda_stream: stream of the current device (NULL = legacy default);
  *   iters_out (host, may be NULL): iterations used.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
+ * Every call looks up the array's device address in the current device's
+ * context (so a device reset or another context needs nothing from the
+ * caller); the first call on a device may load the library's device code,
+ * so make it before any stream capture.  All
  * calls share the array and it keeps the last call's contents; calls that
  * overlap on the GPU (other streams, other threads) race and must be
  * serialized by the caller.

@@ -100,27 +100,35 @@ def forward(params, x, n_out, bf=False):
     return y, dict(x0=x0, a1=a1, a2=a2, a3=a3, u3=u3, a4=a4, cat=cat, a5=a5, L=Lq)
 
 
-def loss_and_grad(params, x, target, n_out, bf=False):
+def loss_and_grad(params, x, target, n_out, bf=False, intermediates=False):
+    """Loss and the flat parameter gradient; with intermediates=True also the
+    forward cache and the gradients w.r.t. each layer's output before its
+    ReLU mask is applied (keys gy, gu5, gucat, gu3, gu2, gu1: the gradient
+    that reaches a5, [a4, a1], u3, a2, a1 from the layer above)."""
     y, c = forward(params, x, n_out, bf)
     r = y - target
     loss = float(np.mean(r * r))
     gy = 2.0 * r / r.size
     L = c["L"]
     grads = []
-    g5, gw5, gb5 = conv_grads(c["a5"], L[5][0], 1, gy)
-    g5 = g5 * (c["a5"] > 0)
+    gu5, gw5, gb5 = conv_grads(c["a5"], L[5][0], 1, gy)
+    g5 = gu5 * (c["a5"] > 0)
     gcat, gw4, gb4 = conv_grads(c["cat"], L[4][0], 1, g5)
     g4 = gcat[:, :C1] * (c["a4"] > 0)
     g1_skip = gcat[:, C1:] * (c["a1"] > 0)
     gu3, gw3, gb3 = conv_grads(c["u3"], L[3][0], 1, g4)
-    g3 = gu3.reshape(gu3.shape[0], gu3.shape[1], gu3.shape[2] // 2, 2, gu3.shape[3] // 2, 2).sum(axis=(3, 5))
-    g3 = g3 * (c["a3"] > 0)
-    g2, gw2, gb2 = conv_grads(c["a2"], L[2][0], 1, g3)
-    g2 = g2 * (c["a2"] > 0)
-    g1, gw1, gb1 = conv_grads(c["a1"], L[1][0], 2, g2)
-    g1 = g1 * (c["a1"] > 0) + g1_skip
+    gsum3 = gu3.reshape(gu3.shape[0], gu3.shape[1], gu3.shape[2] // 2, 2, gu3.shape[3] // 2, 2).sum(axis=(3, 5))
+    g3 = gsum3 * (c["a3"] > 0)
+    gu2, gw2, gb2 = conv_grads(c["a2"], L[2][0], 1, g3)
+    g2 = gu2 * (c["a2"] > 0)
+    gu1, gw1, gb1 = conv_grads(c["a1"], L[1][0], 2, g2)
+    g1 = gu1 * (c["a1"] > 0) + g1_skip
     _, gw0, gb0 = conv_grads(c["x0"], L[0][0], 1, g1)
     for gw, gb in ((gw0, gb0), (gw1, gb1), (gw2, gb2), (gw3, gb3), (gw4, gb4), (gw5, gb5)):
         grads.append(gw.ravel())
         grads.append(gb)
+    if intermediates:
+        inter = dict(gy=gy, gu5=gu5, g5=g5, gucat=gcat, g4=g4, g1_skip=g1_skip, gu3=gu3, gsum3=gsum3, g3=g3, gu2=gu2,
+                     g2=g2, gu1=gu1, g1=g1, y=y)
+        return loss, np.concatenate(grads), c, inter
     return loss, np.concatenate(grads)

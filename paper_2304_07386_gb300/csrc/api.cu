@@ -74,6 +74,8 @@ struct smm_ctx {
     // Anderson acceleration: rings of G(x_k) and f_k = G(x_k) - x_k (depth + 1 slots)
     std::vector<double*> aaG, aaF;
     double *aa_part = nullptr, *aa_out = nullptr;
+    int aa_k = 0;                  // outer steps in the current Anderson history (0: empty)
+    double* phi_io = nullptr;      // device copy of a host iterate passed to smm_iterate
     // state
     double* psi = nullptr;         // [ne][nd][n] FP64
     float* dpsi = nullptr;         // [ne][nd][n] FP32 correction (refined mode)
@@ -223,6 +225,7 @@ void smm_default_options(smm_options* opt) {
     opt->sweep_tiles = 1;
     opt->mg_smoother = SMM_SMOOTHER_CHEBYSHEV;
     opt->cg_device_loop = 1;
+    opt->resume_history = 0;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -383,6 +386,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->qv = h->alloc<double>(nphi);
     h->p2 = h->alloc<float2>(nphi);
     h->phi_prev = h->alloc<double>(nphi);
+    h->phi_io = h->alloc<double>(nphi);
     const int epb = smm::cg_threads_per_block(s.n) / s.n;
     h->cg_nblk = (s.ne + epb - 1) / epb;
     h->cg_nvblk = std::max(1, std::min(2 * h->sms, (int)((nphi + 255) / 256)));
@@ -395,7 +399,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->dout = h->alloc<double>(2);
     h->nonfinite = h->alloc<int>(1);
     if (!h->psi || !h->done || !h->ticket || !h->err || !h->mom || !h->beta || !h->trace || !h->rhs || !h->r || !h->z ||
-        !h->pv || !h->qv || !h->p2 || !h->phi_prev || !h->part || !h->scal || !h->ctl || !h->dpart || !h->dout || !h->nonfinite)
+        !h->pv || !h->qv || !h->p2 || !h->phi_prev || !h->phi_io || !h->part || !h->scal || !h->ctl || !h->dpart || !h->dout || !h->nonfinite)
         return bail(SMM_ERR_OOM, "device allocation failed");
     if (cudaMemsetAsync(h->psi, 0, nang * sizeof(double), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->done, 0, (size_t)s.ne * s.nd * sizeof(unsigned), h->stream) != cudaSuccess ||
@@ -1042,13 +1046,21 @@ smm_status anderson_step(smm_handle h, int k, double* phi) {
 
 extern "C" {
 
-smm_status smm_sweep(smm_handle h, const double* phi_dev) {
+smm_status smm_sweep(smm_handle h, const double* phi_dev, double* phiT_out) {
     if (!h) return fail(SMM_ERR_INVALID_ARG, "NULL handle");
     smm_status st = enqueue_sweep(h, phi_dev);
     if (st != SMM_OK) return st;
     st = enqueue_moments(h);
     if (st != SMM_OK) return st;
-    return check_device_error(h);
+    st = check_device_error(h);
+    if (st != SMM_OK) return st;
+    if (phiT_out) {
+        // component 0 of the moments is phi_T = sum_d w_d psi_d (host or device destination)
+        SMM_CUDA(cudaMemcpyAsync(phiT_out, h->mom, (size_t)h->ne * h->n * sizeof(double), cudaMemcpyDefault,
+                                 h->stream));
+        SMM_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return SMM_OK;
 }
 
 smm_status smm_moments(smm_handle h, double* moments_dev, double* beta_dev) {
@@ -1096,14 +1108,28 @@ smm_status smm_moment_solve(smm_handle h, double* phi_dev, int32_t* cg_iters) {
     return st;
 }
 
-smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_outer, double* phi_dev,
-                       smm_stats* stats) {
-    if (!h || !phi_dev || !(tol > 0) || max_outer < 1) return fail(SMM_ERR_INVALID_ARG, "bad argument");
+}  // extern "C"
+
+namespace {
+
+// true when p is memory the host addresses directly (pageable or pinned host memory)
+bool is_host_pointer(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t max_outer, double* phi_dev,
+                          smm_stats* stats) {
     smm_stats local{};
     local.cg_min = 1 << 30;
     const long long launches0 = h->launches;
     const size_t nphi = (size_t)h->ne * h->n;
     smm_status result = SMM_ERR_NOT_CONVERGED;
+    if (!h->opt.resume_history) h->aa_k = 0;
     for (int k = 1; k <= max_outer; ++k) {
         SMM_CUDA(cudaMemcpyAsync(h->phi_prev, phi_dev, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         SMM_CUDA(cudaEventRecord(h->ev[0], h->stream));
@@ -1129,6 +1155,7 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
         SMM_CUDA(cudaStreamSynchronize(h->stream));
         if (h->h_int[5] == smm::DEV_TIMEOUT) {
             cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+            h->aa_k = 0;
             if (stats) *stats = local;
             return fail(SMM_ERR_DEVICE_TIMEOUT, "a sweep dependency wait exceeded spin_timeout_s");
         }
@@ -1148,13 +1175,17 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
         local.last_diff = diff;
         local.last_rel_diff = mx > 0 ? diff / mx : diff;
         if (h->h_int[4]) {
+            h->aa_k = 0;
             if (stats) *stats = local;
             return fail(SMM_ERR_NONFINITE, "non-finite scalar flux");
         }
         if (k == 1 && h->opt.guess_check && diff > mx) {
-            // the guess raised the first residual above the zero guess's: restart from zero
+            // max|G(x0) - x0| > max|G(x0) - 0|: the given guess is farther from its
+            // own image than the zero vector is, so restart from zero with an
+            // empty Anderson history (no step from x0 enters it)
             SMM_CUDA(cudaMemsetAsync(phi_dev, 0, nphi * sizeof(double), h->stream));
             local.guess_rejected = 1;
+            h->aa_k = 0;
             continue;
         }
         const double crit = relative ? local.last_rel_diff : diff;
@@ -1163,13 +1194,139 @@ smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_o
             break;
         }
         if (h->opt.anderson_depth > 0) {
-            smm_status as = anderson_step(h, k, phi_dev);
+            h->aa_k += 1;
+            smm_status as = anderson_step(h, h->aa_k, phi_dev);
             if (as != SMM_OK) return as;
         }
     }
     if (local.cg_min == (1 << 30)) local.cg_min = 0;
     if (stats) *stats = local;
     if (result != SMM_OK) return fail(result, "outer iteration limit reached");
+    return SMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+smm_status smm_iterate(smm_handle h, double tol, int32_t relative, int32_t max_outer, double* phi,
+                       smm_stats* stats) {
+    if (!h || !phi || !(tol > 0) || max_outer < 1) return fail(SMM_ERR_INVALID_ARG, "bad argument");
+    if (!is_host_pointer(phi)) return iterate_device(h, tol, relative, max_outer, phi, stats);
+    // host iterate: copy in, iterate on the handle's device copy, copy the last iterate back
+    const size_t bytes = (size_t)h->ne * h->n * sizeof(double);
+    SMM_CUDA(cudaMemcpyAsync(h->phi_io, phi, bytes, cudaMemcpyHostToDevice, h->stream));
+    smm_status st = iterate_device(h, tol, relative, max_outer, h->phi_io, stats);
+    if (st == SMM_ERR_CUDA) return st;
+    const std::string msg = g_err;
+    SMM_CUDA(cudaMemcpyAsync(phi, h->phi_io, bytes, cudaMemcpyDeviceToHost, h->stream));
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    if (st != SMM_OK) g_err = msg;
+    return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Checkpoint layout: a header of 16 int64 words, then the handle's state
+// arrays, each starting on a 256-byte boundary.
+constexpr int64_t kStateMagic = 0x534d4d5354415445LL;  // "SMMSTATE"
+constexpr int64_t kStateVersion = 1;
+
+struct StateSection {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<StateSection> state_sections(smm_handle h) {
+    const size_t nang = (size_t)h->ne * h->nd * h->n, nphi = (size_t)h->ne * h->n;
+    std::vector<StateSection> v;
+    v.push_back({h->psi, nang * sizeof(double)});
+    if (h->psi2) v.push_back({h->psi2, nang * sizeof(float2)});
+    v.push_back({h->mom, 6 * nphi * sizeof(double)});
+    v.push_back({h->beta, (size_t)h->nb * h->nfq * sizeof(double)});
+    v.push_back({h->phi_prev, nphi * sizeof(double)});
+    for (size_t k = 0; k < h->aaG.size(); ++k) {
+        v.push_back({h->aaG[k], nphi * sizeof(double)});
+        v.push_back({h->aaF[k], nphi * sizeof(double)});
+    }
+    return v;
+}
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+int64_t state_bytes(smm_handle h) {
+    size_t total = 256;  // header
+    for (const auto& sec : state_sections(h)) total += round256(sec.bytes);
+    return (int64_t)total;
+}
+
+void state_header(smm_handle h, int64_t* hdr) {
+    for (int i = 0; i < 32; ++i) hdr[i] = 0;
+    hdr[0] = kStateMagic;
+    hdr[1] = kStateVersion;
+    hdr[2] = h->ne; hdr[3] = h->n; hdr[4] = h->nd; hdr[5] = h->nb; hdr[6] = h->nfq;
+    hdr[7] = (h->psi2 ? 1 : 0) | (h->fp32 ? 2 : 0);
+    hdr[8] = h->opt.anderson_depth;
+    hdr[9] = h->aa_k;
+    hdr[10] = state_bytes(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+smm_status smm_set_spin_timeout(smm_handle h, double seconds) {
+    if (!h || !(seconds > 0)) return fail(SMM_ERR_INVALID_ARG, "bad argument");
+    h->opt.spin_timeout_s = seconds;
+    return SMM_OK;
+}
+
+smm_status smm_state_size(smm_handle h, int64_t* bytes) {
+    if (!h || !bytes) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
+    *bytes = state_bytes(h);
+    return SMM_OK;
+}
+
+smm_status smm_get_state(smm_handle h, void* buf, int64_t bytes) {
+    if (!h || !buf) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
+    if (bytes < state_bytes(h)) return fail(SMM_ERR_INVALID_ARG, "state buffer smaller than smm_state_size()");
+    int64_t* hdr = reinterpret_cast<int64_t*>(h->h_scal);  // 32 pinned words
+    state_header(h, hdr);
+    char* out = static_cast<char*>(buf);
+    SMM_CUDA(cudaMemcpyAsync(out, hdr, 256, cudaMemcpyDefault, h->stream));
+    size_t off = 256;
+    for (const auto& sec : state_sections(h)) {
+        if (sec.bytes) SMM_CUDA(cudaMemcpyAsync(out + off, sec.dev, sec.bytes, cudaMemcpyDefault, h->stream));
+        off += round256(sec.bytes);
+    }
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    return SMM_OK;
+}
+
+smm_status smm_set_state(smm_handle h, const void* buf, int64_t bytes) {
+    if (!h || !buf) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
+    if (bytes < 256) return fail(SMM_ERR_INVALID_ARG, "state buffer too small");
+    int64_t* hdr = reinterpret_cast<int64_t*>(h->h_scal);
+    const char* in = static_cast<const char*>(buf);
+    SMM_CUDA(cudaMemcpyAsync(hdr, in, 256, cudaMemcpyDefault, h->stream));
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    int64_t want[32];
+    state_header(h, want);
+    if (hdr[0] != kStateMagic || hdr[1] != kStateVersion) return fail(SMM_ERR_INVALID_ARG, "not an smm state");
+    for (int i = 2; i <= 8; ++i)
+        if (hdr[i] != want[i]) return fail(SMM_ERR_INVALID_ARG, "state was saved from a handle of another shape or mode");
+    if (hdr[10] != want[10] || bytes < want[10]) return fail(SMM_ERR_INVALID_ARG, "state size mismatch");
+    if (hdr[9] < 0) return fail(SMM_ERR_INVALID_ARG, "bad Anderson history length");
+    const int aa_k = (int)hdr[9];
+    size_t off = 256;
+    for (const auto& sec : state_sections(h)) {
+        if (sec.bytes) SMM_CUDA(cudaMemcpyAsync(sec.dev, in + off, sec.bytes, cudaMemcpyDefault, h->stream));
+        off += round256(sec.bytes);
+    }
+    SMM_CUDA(cudaStreamSynchronize(h->stream));
+    h->aa_k = aa_k;
     return SMM_OK;
 }
 
@@ -1339,6 +1496,8 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
     std::vector<char> done(n, 0);
     for (auto& s : st) s.cg_min = 1 << 30;
     std::vector<const double*> phis(phi_dev, phi_dev + n);
+    for (smm_handle h : b->hs)
+        if (!h->opt.resume_history) h->aa_k = 0;
     int remaining = n;
     for (int k = 1; k <= max_outer && remaining > 0; ++k) {
         for (int i = 0; i < n; ++i) {
@@ -1375,7 +1534,8 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
                 done[i] = 1;
                 --remaining;
             } else if (h->opt.anderson_depth > 0) {
-                s = anderson_step(h, k, phi_dev[i]);
+                h->aa_k += 1;
+                s = anderson_step(h, h->aa_k, phi_dev[i]);
                 if (s != SMM_OK) return s;
             }
         }

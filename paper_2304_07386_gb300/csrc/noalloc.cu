@@ -10,8 +10,6 @@
 // library holds until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/smm.h"
 #include "kernels.cuh"
 
@@ -23,10 +21,6 @@ constexpr long long kMaxBlocks = kMaxRows / 128 + 2;  // row blocks hold >= 128 
 constexpr long long kScratchBytes = 8LL * (4 * kMaxRows + 3 * kMaxBlocks + 8) + 4LL * 8;
 
 static __device__ __align__(256) unsigned char g_pcg_scratch[kScratchBytes];
-
-// device address of g_pcg_scratch per device, looked up once per device
-std::mutex g_mu;
-void* g_addr[64] = {nullptr};
 
 smm_status fail(smm_status s, const char* msg) {
     smm::set_last_error(msg);
@@ -47,19 +41,14 @@ extern "C" smm_status smm_block_pcg_noalloc(int32_t n_elem, int32_t n, const dou
         return fail(SMM_ERR_INVALID_ARG,
                     "smm_block_pcg_noalloc: n_elem * n exceeds the fixed scratch capacity of 524288 unknowns");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-        return fail(SMM_ERR_CUDA, "smm_block_pcg_noalloc: no current CUDA device");
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(SMM_ERR_CUDA, "smm_block_pcg_noalloc: no current CUDA device");
+    // The array's device address in the current device's context, looked up on
+    // every call: a cached address would go stale after cudaDeviceReset or in
+    // another context of the same device, and the lookup costs microseconds
+    // against a CG loop that synchronizes with the host.
     void* base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_pcg_scratch) != cudaSuccess || !p)
-                return fail(SMM_ERR_CUDA, "smm_block_pcg_noalloc: cudaGetSymbolAddress failed");
-            g_addr[dev] = p;
-        }
-        base = g_addr[dev];
-    }
+    if (cudaGetSymbolAddress(&base, g_pcg_scratch) != cudaSuccess || !base)
+        return fail(SMM_ERR_CUDA, "smm_block_pcg_noalloc: cudaGetSymbolAddress failed");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     double* d = (double*)base;
     smm::CGArgs a{};

@@ -39,7 +39,7 @@ class smm_options(C.Structure):
                 ("sweep_solver", C.c_int32), ("anderson_depth", C.c_int32), ("guess_check", C.c_int32),
                 ("mg_smooth_steps", C.c_int32), ("moment_discretization", C.c_int32),
                 ("negative_flux_fixup", C.c_int32), ("sweep_tiles", C.c_int32), ("mg_smoother", C.c_int32),
-                ("cg_device_loop", C.c_int32)]
+                ("cg_device_loop", C.c_int32), ("resume_history", C.c_int32)]
 
 
 class smm_info(C.Structure):
@@ -85,13 +85,17 @@ def load_library(path: str | None = None):
     lib.smm_create.argtypes = [C.POINTER(smm_mesh), C.c_int32, C.c_int32, dp, dp, C.c_int32, dp, C.c_int32, dp,
                                C.POINTER(smm_options), vp, C.POINTER(vp)]
     lib.smm_get_info.argtypes = [vp, C.POINTER(smm_info)]
-    lib.smm_sweep.argtypes = [vp, vp]
+    lib.smm_sweep.argtypes = [vp, vp, vp]
     lib.smm_moments.argtypes = [vp, vp, vp]
     lib.smm_set_moments.argtypes = [vp, vp, vp]
     lib.smm_get_psi.argtypes = [vp, vp]
     lib.smm_moment_solve.argtypes = [vp, vp, ip]
     lib.smm_iterate.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, vp, C.POINTER(smm_stats)]
     lib.smm_destroy.argtypes = [vp]
+    lib.smm_set_spin_timeout.argtypes = [vp, C.c_double]
+    lib.smm_state_size.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.smm_get_state.argtypes = [vp, vp, C.c_int64]
+    lib.smm_set_state.argtypes = [vp, vp, C.c_int64]
     lib.smm_batch_create.argtypes = [C.c_int32, C.POINTER(vp), C.POINTER(vp)]
     lib.smm_batch_schedule.argtypes = [vp, ip, ip, dp, C.POINTER(C.c_int64)]
     lib.smm_batch_sweep.argtypes = [vp, C.POINTER(vp)]
@@ -114,7 +118,8 @@ def load_library(path: str | None = None):
     lib.smm_block_pcg_noalloc.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, C.c_double, C.c_int32, vp, ip]
     lib.smm_block_pcg_noalloc.restype = C.c_int
     for name in ("smm_quadrature", "smm_create", "smm_get_info", "smm_sweep", "smm_moments", "smm_set_moments",
-                 "smm_get_psi", "smm_moment_solve", "smm_iterate", "smm_destroy"):
+                 "smm_get_psi", "smm_moment_solve", "smm_iterate", "smm_destroy", "smm_state_size", "smm_get_state",
+                 "smm_set_state", "smm_set_spin_timeout"):
         getattr(lib, name).restype = C.c_int
     if path is None:
         _lib = lib
@@ -137,6 +142,31 @@ def _devptr(t):
     if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
         raise ValueError("device buffers must be contiguous CUDA float64 tensors")
     return C.c_void_p(t.data_ptr())
+
+
+def _anybuf(t, count, what):
+    """Pointer to a float64 buffer of exactly count elements in host memory (a
+    C-contiguous NumPy array) or device memory (a CUDA tensor)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"] or not t.flags["WRITEABLE"]:
+            raise ValueError(f"{what}: host buffers must be writeable C-contiguous float64 arrays")
+        if t.size != count:
+            raise ValueError(f"{what}: expected {count} elements, got {t.size}")
+        return C.c_void_p(t.ctypes.data)
+    return _devbuf(t, count, what)
+
+
+def _rawbuf(buf):
+    """(pointer, size in bytes) of a contiguous NumPy array or CUDA tensor."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("state buffer must be contiguous")
+        return C.c_void_p(buf.ctypes.data), buf.nbytes
+    if not (buf.is_cuda and buf.is_contiguous()):
+        raise ValueError("state buffer must be a contiguous CUDA tensor or a NumPy array")
+    return C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size()
 
 
 def _devbuf(t, count, what):
@@ -234,8 +264,10 @@ def smm_create(nodes, elem_nodes, geom_order, p, sn_order, sigma_t, sigma_s, q, 
     return Handle(out, s)
 
 
-def smm_sweep(h: Handle, phi=None):
-    _check(load_library().smm_sweep(h.ptr, _devbuf(phi, h.n_phi(), "phi")))
+def smm_sweep(h: Handle, phi=None, phi_t=None):
+    """One sweep from varphi = phi (None: zero); phi_t (None, a CUDA float64
+    tensor or a float64 NumPy array of n_elem * n values) receives phi_T."""
+    _check(load_library().smm_sweep(h.ptr, _devbuf(phi, h.n_phi(), "phi"), _anybuf(phi_t, h.n_phi(), "phi_t")))
 
 
 def _moment_bufs(h: Handle, moments, beta):
@@ -263,9 +295,10 @@ def smm_moment_solve(h: Handle, phi) -> int:
 
 
 def smm_iterate(h: Handle, phi, tol: float, max_outer: int = 200, relative: bool = False, raise_on_error=True):
-    """Returns (status, stats dict)."""
+    """phi: CUDA float64 tensor or float64 NumPy array (guess in, last iterate
+    out).  Returns (status, stats dict)."""
     st = smm_stats()
-    rc = load_library().smm_iterate(h.ptr, tol, int(relative), max_outer, _devbuf(phi, h.n_phi(), "phi"),
+    rc = load_library().smm_iterate(h.ptr, tol, int(relative), max_outer, _anybuf(phi, h.n_phi(), "phi"),
                                     C.byref(st))
     if raise_on_error:
         _check(rc)
@@ -274,6 +307,33 @@ def smm_iterate(h: Handle, phi, tol: float, max_outer: int = 200, relative: bool
 
 def smm_destroy(h: Handle):
     h.destroy()
+
+
+def smm_set_spin_timeout(h: Handle, seconds: float):
+    _check(load_library().smm_set_spin_timeout(h.ptr, seconds))
+
+
+def smm_state_size(h: Handle) -> int:
+    n = C.c_int64(0)
+    _check(load_library().smm_state_size(h.ptr, C.byref(n)))
+    return n.value
+
+
+def smm_get_state(h: Handle, buf=None):
+    """Save the handle's state into buf (a uint8 NumPy array or CUDA tensor of
+    at least smm_state_size bytes); with buf None a new NumPy array is
+    returned."""
+    n = smm_state_size(h)
+    if buf is None:
+        buf = np.zeros(n, dtype=np.uint8)
+    ptr, size = _rawbuf(buf)
+    _check(load_library().smm_get_state(h.ptr, ptr, size))
+    return buf
+
+
+def smm_set_state(h: Handle, buf):
+    ptr, size = _rawbuf(buf)
+    _check(load_library().smm_set_state(h.ptr, ptr, size))
 
 
 def smm_block_pcg_noalloc(diag_blocks, off_blocks, nbr, pinv_blocks, b, x, tol=1e-12, max_iters=20000,

@@ -17,11 +17,18 @@
 // of the accumulated flux) and sweep_kernel<float, P, SWEEP_RESIDUAL> solving
 // for the correction in FP32 and adding it to the FP64 flux (the LU form, and
 // the cached FP32 inverses from invert_kernel<float, P>).
+// MODE timeout first runs each form with the first task of the list left out,
+// so the flag of that task is never published and the tasks downwind of it
+// wait until the bounded wait gives up (timeout 20 ms): the kernel must
+// return with the device error word set to DEV_TIMEOUT, every warp having
+// stopped.  It then sweeps again with the next flag epoch and the whole list,
+// as the library's next sweep does, and that sweep's flux is the output.  The
+// error words of both runs go to DIR/timeout_err.txt.
 // Usage: sweep_emu DIR NE NNODES M P SN ANGULAR INFLOW MODE K   (one problem)
 //        sweep_emu --batch DIR COUNT                          (see run_batch)
 //   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, phi.f64 [ne][n],
 //        q.f64 ([ne][n], or [nd][ne][n] if ANGULAR), inflow.f64 [nd][n_bface][p+1] if INFLOW,
-//        nbface.txt (the boundary face count); MODE plain | fixup | refine, K sweeps (refine)
+//        nbface.txt (the boundary face count); MODE plain | fixup | refine | timeout, K sweeps (refine)
 //   out: DIR/dims.txt (n nd n_bface nlevels), DIR/psi_lu.f64, DIR/psi_inv.f64 and (FP64 modes)
 //        DIR/psi2_inv.f64 (the pair copy as hi + lo) [ne][nd][n], DIR/err.txt (device error words)
 #include <atomic>
@@ -236,6 +243,46 @@ static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow
     }
 }
 
+// Each form twice on the same flags: once without the list's first task (its
+// flag is never published, so its downwind tasks' waits expire), then, with
+// the device error word cleared and the next epoch, over the whole list.
+// e1/e2: the error words after the first and the second run of each form.
+template <int P>
+static void run_timeout(const smm::Setup& s, const std::vector<double>& phi, bool inflow, Run& lu, Run& inv,
+                        int e1[2], int e2[2]) {
+    const int ne = s.ne, nd = s.nd, n = s.n;
+    const size_t nang = (size_t)ne * nd * n;
+    for (int form = 0; form < 2; ++form) {
+        Run& out = form == 0 ? lu : inv;
+        std::vector<unsigned> done;
+        smm::SweepArgs<double> a = base_args(s, phi, inflow, done, out.err);
+        Cached store;
+        if (form == 1) prepare_cached<P>(s, phi, inflow, a, store);
+        out.psi.assign(nang, 0.0);
+        out.psi2.assign(nang, make_float2(0.0f, 0.0f));
+        a.psi = out.psi.data();
+        if (form == 1) a.psi2 = out.psi2.data();
+        auto sweep = [&] {
+            if (form == 0)
+                emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, false>(a); });
+            else
+                emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, false>(a); });
+        };
+        a.tasks = s.tasks.data() + 1;
+        a.ntask = (int)s.tasks.size() - 1;
+        a.timeout_ns = 20LL * 1000 * 1000;
+        sweep();
+        e1[form] = out.err;
+        out.err = 0;
+        a.tasks = s.tasks.data();
+        a.ntask = (int)s.tasks.size();
+        a.epoch = 2;
+        a.timeout_ns = 60LL * 1000 * 1000 * 1000;
+        sweep();
+        e2[form] = out.err;
+    }
+}
+
 // one problem's inputs (see the usage above) and the library's host setup of them
 struct Problem {
     smm::Setup s;
@@ -354,7 +401,7 @@ int main(int argc, char** argv) {
     if (argc != 11) return 2;
     const std::string mode = argv[9];
     const int K = std::atoi(argv[10]);
-    if (mode != "plain" && mode != "fixup" && mode != "refine") return 2;
+    if (mode != "plain" && mode != "fixup" && mode != "refine" && mode != "timeout") return 2;
     const std::string dir = argv[1];
     const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
     const int sn = std::atoi(argv[6]), angular = std::atoi(argv[7]), inflow = std::atoi(argv[8]);
@@ -364,7 +411,17 @@ int main(int argc, char** argv) {
     const smm::Setup& s = pr.s;
     Run lu, inv;
     const bool fix = mode == "fixup";
-    if (mode == "refine") {
+    if (mode == "timeout") {
+        int e1[2] = {0, 0}, e2[2] = {0, 0};
+        switch (p) {
+            case 1: run_timeout<1>(s, pr.phi, pr.inflow, lu, inv, e1, e2); break;
+            case 2: run_timeout<2>(s, pr.phi, pr.inflow, lu, inv, e1, e2); break;
+            case 3: run_timeout<3>(s, pr.phi, pr.inflow, lu, inv, e1, e2); break;
+            default: run_timeout<4>(s, pr.phi, pr.inflow, lu, inv, e1, e2); break;
+        }
+        std::ofstream f(dir + "/timeout_err.txt");
+        f << e1[0] << " " << e2[0] << " " << e1[1] << " " << e2[1] << "\n";
+    } else if (mode == "refine") {
         switch (p) {
             case 1: run_refined<1>(s, pr.phi, pr.inflow, K, lu, inv); break;
             case 2: run_refined<2>(s, pr.phi, pr.inflow, K, lu, inv); break;

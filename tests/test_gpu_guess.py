@@ -19,27 +19,66 @@ def _lib():
     B.build()
 
 
-def test_network_forward_and_gradients_match_oracle():
+@pytest.mark.parametrize("seed", [0, 1, 3])
+def test_network_reproduces_the_oracle_bit_for_bit_on_exact_cases(seed):
+    """Forward output, loss and every parameter gradient, element by element
+    and layer by layer (tests/cnn_exact.py: cases on which every FP32 sum of
+    the library's arithmetic is exact in any order, certified from the
+    oracle's values), must equal the oracle's exactly."""
     import paper_2304_07386_gb300 as P
     from oracle import cnn
+    from tests import cnn_exact
+    params, x, t, n_out = cnn_exact.case(seed)
+    cnn_exact.certify(params, x, t, n_out)
+    B, _, H, Wd = x.shape
+    net = P.smm.Guess(H, Wd, n_out, B, seed=3)
+    assert net.n_params == params.size
+    net.set_params(params.astype(np.float32))
+    xd = torch.as_tensor(x.astype(np.float32), device="cuda")
+    td = torch.as_tensor(t.astype(np.float32), device="cuda")
+    y = torch.zeros((B, n_out, H, Wd), dtype=torch.float32, device="cuda")
+    net.forward(xd, y)
+    loss_o, g_o, _, it = cnn.loss_and_grad(params, x, t, n_out, bf=True, intermediates=True)
+    assert np.array_equal(y.cpu().numpy().astype(np.float64), it["y"])
+    loss, g = net.gradients(xd, td)
+    assert loss == loss_o
+    bad = [name for name, sl in cnn_exact.blocks(n_out) if not np.array_equal(g[sl].astype(np.float64), g_o[sl])]
+    assert not bad, bad
+
+
+def test_network_forward_and_gradients_match_oracle_elementwise():
+    """General inputs (weights ~ N(0, 0.2^2), normal inputs and targets): the
+    library's FP32 sums round differently from the oracle's FP64 ones, by about
+    2^-24 K of a sum of K terms, and where such a difference crosses a BF16
+    rounding boundary a stored activation moves by one BF16 unit (at most
+    2^-7 of its value), moving what follows it by about that fraction.  So
+    every output value is checked against 1e-2 of its channel's largest
+    magnitude, and every gradient entry against 1e-2 of its layer block's
+    (weights and bias of each layer separately); the loss to 1e-3."""
+    import paper_2304_07386_gb300 as P
+    from oracle import cnn
+    from tests import cnn_exact
     H, Wd, n_out, B = 8, 6, 4, 2
     net = P.smm.Guess(H, Wd, n_out, B, seed=3)
     assert net.n_params == cnn.num_params(n_out)
-    rng = np.random.default_rng(1)
-    params = (rng.standard_normal(net.n_params) * 0.2).astype(np.float32)
-    net.set_params(params)
-    x = rng.standard_normal((B, 3, H, Wd)).astype(np.float32)
-    t = rng.standard_normal((B, n_out, H, Wd)).astype(np.float32)
-    xd, td = torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda")
-    y = torch.zeros((B, n_out, H, Wd), dtype=torch.float32, device="cuda")
-    net.forward(xd, y)
-    y_ref, _ = cnn.forward(params.astype(np.float64), x.astype(np.float64), n_out, bf=True)
-    assert np.max(np.abs(y.cpu().numpy() - y_ref)) < 2e-2 * np.max(np.abs(y_ref))
-    loss, g = net.gradients(xd, td)
-    loss_ref, g_ref = cnn.loss_and_grad(params.astype(np.float64), x.astype(np.float64), t.astype(np.float64), n_out,
-                                        bf=True)
-    assert abs(loss - loss_ref) < 1e-2 * loss_ref
-    assert np.linalg.norm(g - g_ref) < 3e-2 * np.linalg.norm(g_ref)
+    for seed in (1, 2):
+        rng = np.random.default_rng(seed)
+        params = (rng.standard_normal(net.n_params) * 0.2).astype(np.float32)
+        net.set_params(params)
+        x = rng.standard_normal((B, 3, H, Wd)).astype(np.float32)
+        t = rng.standard_normal((B, n_out, H, Wd)).astype(np.float32)
+        xd, td = torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda")
+        y = torch.zeros((B, n_out, H, Wd), dtype=torch.float32, device="cuda")
+        net.forward(xd, y)
+        y_ref, _ = cnn.forward(params.astype(np.float64), x.astype(np.float64), n_out, bf=True)
+        scale = np.max(np.abs(y_ref), axis=(0, 2, 3), keepdims=True)
+        assert np.all(np.abs(y.cpu().numpy() - y_ref) <= 1e-2 * scale)
+        loss, g = net.gradients(xd, td)
+        loss_ref, g_ref = cnn.loss_and_grad(params.astype(np.float64), x.astype(np.float64), t.astype(np.float64),
+                                            n_out, bf=True)
+        assert abs(loss - loss_ref) < 1e-3 * loss_ref
+        for name, sl in cnn_exact.blocks(n_out):
+            assert np.all(np.abs(g[sl] - g_ref[sl]) <= 1e-2 * np.max(np.abs(g_ref[sl]))), name
 
 
 def _solve(P, nx, seed, phi0=None, check=False, p=2, sn=4, tol=1e-8):

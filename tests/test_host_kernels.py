@@ -291,6 +291,28 @@ def test_sweep_kernel_matches_oracle(sweep_emu, tmp_path, case):
         assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
 
 
+def test_sweep_kernel_wait_expires_and_the_next_sweep_is_exact(sweep_emu, tmp_path):
+    """The bounded dependency wait: with the first task of the list never run,
+    its flag is never published and the tasks downwind of it give up after the
+    timeout (20 ms here).  Each form of the kernel must then return with the
+    device error word at DEV_TIMEOUT (every warp stopping, or the launch would
+    not end), and the following sweep on the same flags -- error word cleared,
+    next epoch, whole list, as the library's next call runs it -- must equal
+    the oracle's sweep: flags left at the old epoch are harmless."""
+    import re as _re
+    kcuh = open(os.path.join(CSRC, "kernels.cuh")).read()
+    dev_timeout = int(_re.search(r"DEV_TIMEOUT = (\d+)", kcuh).group(1))
+    case = (3, 3, 2, 2, 4, 4, "mms")
+    disc, phi, q, inflow, got = _run_sweep_emu(sweep_emu, tmp_path, case, "timeout")
+    e1_lu, e2_lu, e1_inv, e2_inv = map(int, open(tmp_path / "timeout_err.txt").read().split())
+    assert (e1_lu, e1_inv) == (dev_timeout, dev_timeout)
+    assert (e2_lu, e2_inv) == (0, 0)
+    ref = disc.sweep(phi, q, inflow).transpose(1, 0, 2)
+    scale = np.max(np.abs(ref))
+    for name, psi in got.items():
+        assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
+
+
 def test_batched_sweep_kernel_matches_oracle(sweep_emu, tmp_path):
     """Problems of different p, S_N, size, geometry and source kind swept by
     one batch_sweep_kernel launch over their merged level-by-level task list
