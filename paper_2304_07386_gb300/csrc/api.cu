@@ -52,6 +52,7 @@ struct smm_ctx {
     int32_t *tasks = nullptr, *nbr = nullptr, *nbr_face = nullptr, *nbr_flip = nullptr, *bface_id = nullptr;
     int32_t *bface_elem = nullptr, *bface_face = nullptr;
     int8_t* fdir = nullptr;
+    int32_t* red = nullptr;        // [ne] the element's last task in list order (forms its moments)
     // sweep matrices
     double *M = nullptr, *Gx = nullptr, *Gy = nullptr, *Fx = nullptr, *Fy = nullptr;
     float *M32 = nullptr, *Gx32 = nullptr, *Gy32 = nullptr, *Fx32 = nullptr, *Fy32 = nullptr;
@@ -77,7 +78,7 @@ struct smm_ctx {
     int aa_k = 0;                  // outer steps in the current Anderson history (0: empty)
     double* phi_io = nullptr;      // device copy of a host iterate passed to smm_iterate
     // state
-    double* psi = nullptr;         // [ne][nd][n] FP64
+    double* psi = nullptr;         // [ne][nd][n] FP64 (not kept in FP64 cached mode: psi2 holds the flux)
     float* dpsi = nullptr;         // [ne][nd][n] FP32 correction (refined mode)
     float* res = nullptr;          // [ne][nd][n] FP32 residual (refined mode)
     unsigned* done = nullptr;
@@ -363,7 +364,17 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     }
     if (!ok) return bail(SMM_ERR_OOM, "device allocation or upload failed");
     const size_t nang = (size_t)s.ne * s.nd * s.n, nphi = (size_t)s.ne * s.n;
-    h->psi = h->alloc<double>(nang);
+    const bool pairs_only = o.sweep_solver == SMM_SOLVER_CACHED_INVERSE && o.sweep_precision == SMM_SWEEP_FP64;
+    if (!pairs_only) {
+        h->psi = h->alloc<double>(nang);
+        if (!h->psi) return bail(SMM_ERR_OOM, "device allocation failed");
+    }
+    {
+        // the element's last task in list order forms the element's moments after its other ordinates
+        std::vector<int32_t> red(s.ne, 0);
+        for (int32_t t : s.tasks) red[t / s.nd] = t;
+        if (!upload(h, h->red, red)) return bail(SMM_ERR_OOM, "device allocation failed");
+    }
     if (o.sweep_tiles > 1 && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) {
         h->psi_lag = h->alloc<double>(nang);
         if (!h->psi_lag) return bail(SMM_ERR_OOM, "device allocation failed");
@@ -398,10 +409,10 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->dpart = h->alloc<double>(2 * 256);
     h->dout = h->alloc<double>(2);
     h->nonfinite = h->alloc<int>(1);
-    if (!h->psi || !h->done || !h->ticket || !h->err || !h->mom || !h->beta || !h->trace || !h->rhs || !h->r || !h->z ||
+    if (!h->done || !h->ticket || !h->err || !h->mom || !h->beta || !h->trace || !h->rhs || !h->r || !h->z ||
         !h->pv || !h->qv || !h->p2 || !h->phi_prev || !h->phi_io || !h->part || !h->scal || !h->ctl || !h->dpart || !h->dout || !h->nonfinite)
         return bail(SMM_ERR_OOM, "device allocation failed");
-    if (cudaMemsetAsync(h->psi, 0, nang * sizeof(double), h->stream) != cudaSuccess ||
+    if ((h->psi && cudaMemsetAsync(h->psi, 0, nang * sizeof(double), h->stream) != cudaSuccess) ||
         cudaMemsetAsync(h->done, 0, (size_t)s.ne * s.nd * sizeof(unsigned), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->err, 0, 4 * sizeof(int), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->mom, 0, 6 * nphi * sizeof(double), h->stream) != cudaSuccess ||
@@ -721,6 +732,8 @@ smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) 
     a.fdir = h->fdir; a.nbr = h->nbr; a.nbr_face = h->nbr_face; a.nbr_flip = h->nbr_flip; a.bface_id = h->bface_id;
     a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket; a.err = h->err;
     a.timeout_ns = (long long)(h->opt.spin_timeout_s * 1e9);
+    a.red = h->red; a.w = h->w; a.wq2 = h->wq2; a.mpsi = h->psi; a.mom = h->mom;
+    a.beta = h->nb > 0 ? h->beta : nullptr; a.nfq = h->nfq; a.L1 = h->L1; a.nhat = h->b_nhat; a.eb0 = h->b_eb0;
     if constexpr (std::is_same<T, double>::value) {
         a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy;
         a.phi = phi; a.src = h->src; a.src_angular = h->src_angular; a.inflow = h->has_inflow ? h->inflow : nullptr;
@@ -782,18 +795,6 @@ smm_status enqueue_sweep(smm_handle h, const double* phi) {
         smm::launch_sweep<float>(h->p, smm::SWEEP_RESIDUAL, a, h->sweep_grid, h->stream);
     }
     h->launches += 1;
-    SMM_CUDA(cudaGetLastError());
-    return SMM_OK;
-}
-
-smm_status enqueue_moments(smm_handle h) {
-    if (h->psi2)
-        smm::launch_moments_df(h->ne, h->nd, h->n, h->wq2, h->psi2, h->mom, h->stream);
-    else
-        smm::launch_moments(h->ne, h->nd, h->n, h->w, h->ox, h->oy, h->psi, h->mom, h->stream);
-    smm::launch_beta(h->nb, h->nd, h->n, h->p, h->nfq, h->bface_elem, h->bface_face, h->w, h->ox, h->oy, h->L1,
-                     h->b_nhat, h->b_eb0, h->psi, h->mom, h->beta, h->stream);
-    h->launches += h->nb > 0 ? 2 : 1;
     SMM_CUDA(cudaGetLastError());
     return SMM_OK;
 }
@@ -1050,8 +1051,6 @@ smm_status smm_sweep(smm_handle h, const double* phi_dev, double* phiT_out) {
     if (!h) return fail(SMM_ERR_INVALID_ARG, "NULL handle");
     smm_status st = enqueue_sweep(h, phi_dev);
     if (st != SMM_OK) return st;
-    st = enqueue_moments(h);
-    if (st != SMM_OK) return st;
     st = check_device_error(h);
     if (st != SMM_OK) return st;
     if (phiT_out) {
@@ -1092,8 +1091,14 @@ smm_status smm_set_moments(smm_handle h, const double* moments_dev, const double
 
 smm_status smm_get_psi(smm_handle h, double* psi_dev) {
     if (!h || !psi_dev) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
-    SMM_CUDA(cudaMemcpyAsync(psi_dev, h->psi, (size_t)h->ne * h->nd * h->n * sizeof(double), cudaMemcpyDeviceToDevice,
-                             h->stream));
+    const size_t nang = (size_t)h->ne * h->nd * h->n;
+    if (h->psi) {
+        SMM_CUDA(cudaMemcpyAsync(psi_dev, h->psi, nang * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        smm::launch_pairs_to_f64(nang, h->psi2, psi_dev, h->stream);  // hi + lo, the FP64 value of each pair
+        h->launches += 1;
+        SMM_CUDA(cudaGetLastError());
+    }
     SMM_CUDA(cudaStreamSynchronize(h->stream));
     return SMM_OK;
 }
@@ -1136,9 +1141,7 @@ smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t ma
         smm_status st = enqueue_sweep(h, phi_dev);
         if (st != SMM_OK) return st;
         SMM_CUDA(cudaEventRecord(h->ev[1], h->stream));
-        st = enqueue_moments(h);
-        if (st != SMM_OK) return st;
-        SMM_CUDA(cudaEventRecord(h->ev[2], h->stream));
+        SMM_CUDA(cudaEventRecord(h->ev[2], h->stream));  // the moments are formed inside the sweep
         st = enqueue_rhs(h);
         if (st != SMM_OK) return st;
         SMM_CUDA(cudaEventRecord(h->ev[3], h->stream));
@@ -1242,7 +1245,7 @@ struct StateSection {
 std::vector<StateSection> state_sections(smm_handle h) {
     const size_t nang = (size_t)h->ne * h->nd * h->n, nphi = (size_t)h->ne * h->n;
     std::vector<StateSection> v;
-    v.push_back({h->psi, nang * sizeof(double)});
+    if (h->psi) v.push_back({h->psi, nang * sizeof(double)});
     if (h->psi2) v.push_back({h->psi2, nang * sizeof(float2)});
     v.push_back({h->mom, 6 * nphi * sizeof(double)});
     v.push_back({h->beta, (size_t)h->nb * h->nfq * sizeof(double)});
@@ -1379,10 +1382,6 @@ smm_status batch_enqueue(smm_batch b, const double* const* phis) {
 smm_status batch_sweep_all(smm_batch b, const double* const* phis) {
     smm_status st = b->fp32 ? batch_enqueue<float>(b, phis) : batch_enqueue<double>(b, phis);
     if (st != SMM_OK) return st;
-    for (smm_handle h : b->hs) {
-        st = enqueue_moments(h);
-        if (st != SMM_OK) return st;
-    }
     int e = 0;
     SMM_CUDA(cudaMemcpyAsync(&e, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     SMM_CUDA(cudaStreamSynchronize(b->stream));

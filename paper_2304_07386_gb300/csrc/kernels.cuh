@@ -62,8 +62,23 @@ struct SweepArgs {
     const double* colFy;
     const double* msrc;        // cached mode, SOURCE: [ne][n] M (sigma_s/(4pi) phi + q_iso) of this sweep
     const double* mq;          // cached mode, SOURCE, angular q: [ne][nd][n] M q_d, else nullptr
-    T* psi;                    // [ne][nd][n] output, read by downwind tasks
+    T* psi;                    // [ne][nd][n] output, read by downwind tasks (not written in FP64
+                               // cached mode, whose flux is psi2)
     double* psi_acc;           // RESIDUAL: psi_acc += psi
+    // Angular moments fused into the sweep (Eqs. correction_tensor_disc, bdr_correction_factor_disc):
+    // the task of each element that comes last in the task list (red[e]) waits for the element's other
+    // ordinates, then forms the element's moments and the boundary correction at the Gauss points of
+    // its boundary faces.  mom == nullptr: no moments.
+    const int32_t* red;        // [ne] task id e*nd + d of the element's last task in list order
+    const double* w;           // [nd] ordinate weights
+    const float2* wq2;         // FP64 cached mode: [6][nd] pairs of w_d (1, Ox, Oy, OxOx, OxOy, OyOy)
+    const double* mpsi;        // other modes: the FP64 flux the moments read, [ne][nd][n]
+    double* mom;               // [6][ne][n]: phi, Jx, Jy, Txx, Txy, Tyy
+    double* beta;              // [nb][nfq]
+    int nfq;
+    const double* L1;          // [nfq][p1] face nodal values -> Gauss points
+    const double* nhat;        // [nb][nfq][2] outward unit normals
+    const double* eb0;         // [nb][nfq]
     unsigned* done;            // [ne*nd] epoch flags
     unsigned epoch;
     unsigned* ticket;          // task counter, zero at launch
@@ -115,14 +130,9 @@ void launch_source(int ne, int n, const double* M, const double* sigma_s, const 
 void launch_residual(int p, const ResidualArgs& a, cudaStream_t s);
 int sweep_blocks_per_sm(int p, int mode, bool fp32, bool cached);
 
-// moments and closures
-// moments from psi as FP32 pairs; wq [6][nd] pairs of w_d (1, Ox, Oy, OxOx, OxOy, OyOy)
-void launch_moments_df(int ne, int nd, int n, const float2* wq, const float2* psi2, double* mom, cudaStream_t s);
-void launch_moments(int ne, int nd, int n, const double* w, const double* ox, const double* oy,
-                    const double* psi, double* mom, cudaStream_t s);
-void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_elem, const int32_t* bface_face,
-                 const double* w, const double* ox, const double* oy, const double* L1, const double* nhat,
-                 const double* eb0, const double* psi, const double* mom, double* beta, cudaStream_t s);
+// the FP64 value hi + lo of each of n FP32 pairs
+void launch_pairs_to_f64(size_t n, const float2* in, double* out, cudaStream_t s);
+
 void launch_rhs(int ne, int n, int p, int nfq, const double* mom, const double* beta, const double* bfixed,
                 const float2* Kxx, const float2* Ks, const float2* Kyy, const float2* Dfx, const float2* Dfy,
                 const float2* DfxT, const float2* DfyT, const double* nds, const double* L1, const double* sigma_t,

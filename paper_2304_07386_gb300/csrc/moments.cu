@@ -19,75 +19,6 @@ __device__ __forceinline__ double warp_max(double v) {
 
 }  // namespace
 
-// ---------------------------------------------------------------------------
-// Moments (Eqs. correction_tensor_disc, broken_Tdiv): per element node,
-// phi = sum w psi, J = sum w Omega psi, T = sum w Omega Omega psi - phi/3 I.
-// One warp per element, lane = node; FP64 accumulation in ordinate order.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) moments_kernel(int ne, int nd, int n, const double* __restrict__ w,
-                                                      const double* __restrict__ ox, const double* __restrict__ oy,
-                                                      const double* __restrict__ psi, double* __restrict__ mom) {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < ne; e += warps) {
-        if (lane >= n) continue;
-        double phi = 0, jx = 0, jy = 0, pxx = 0, pxy = 0, pyy = 0;
-        const double* ps = psi + (size_t)e * nd * n + lane;
-        for (int d = 0; d < nd; ++d) {
-            const double v = __ldcg(ps + (size_t)d * n);
-            const double wv = w[d] * v, x = ox[d], y = oy[d];
-            phi += wv;
-            jx += wv * x;
-            jy += wv * y;
-            pxx += wv * x * x;
-            pxy += wv * x * y;
-            pyy += wv * y * y;
-        }
-        const size_t o = (size_t)e * n + lane, st = (size_t)ne * n;
-        mom[o] = phi;
-        mom[st + o] = jx;
-        mom[2 * st + o] = jy;
-        mom[3 * st + o] = pxx - phi / 3.0;
-        mom[4 * st + o] = pxy;
-        mom[5 * st + o] = pyy - phi / 3.0;
-    }
-}
-
-// beta(x_q) = sum_d w_d |Omega_d . n| psi_d(x_q) - E_b0(x_q) phi(x_q) at the
-// Gauss points of every boundary face (Eq. bdr_correction_factor_disc).
-__global__ void beta_kernel(int nb, int nd, int n, int p, int nfq, const int32_t* __restrict__ bface_elem,
-                            const int32_t* __restrict__ bface_face, const double* __restrict__ w,
-                            const double* __restrict__ ox, const double* __restrict__ oy, const double* __restrict__ L1,
-                            const double* __restrict__ nhat, const double* __restrict__ eb0,
-                            const double* __restrict__ psi, const double* __restrict__ mom, double* __restrict__ beta) {
-    // one warp per (boundary face, Gauss point); the lanes take the ordinates
-    // and the sum over them is a fixed-order warp reduction
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (t >= nb * nfq) return;
-    const int b = t / nfq, q = t - b * nfq;
-    const int e = bface_elem[b], f = bface_face[b];
-    const int p1 = p + 1;
-    // face node a of face f is base + a * stride
-    const int base = f == 1 ? p : (f == 2 ? p * p1 : 0);
-    const int stride = (f == 0 || f == 2) ? 1 : p1;
-    const double* Lq = L1 + q * p1;
-    const double nx = nhat[2 * t], ny = nhat[2 * t + 1];
-    double B = 0.0;
-    for (int d = lane; d < nd; d += 32) {
-        const double* ps = psi + ((size_t)e * nd + d) * n + base;
-        double v = 0.0;
-        for (int a = 0; a < p1; ++a) v += Lq[a] * __ldcg(ps + a * stride);
-        B += w[d] * fabs(ox[d] * nx + oy[d] * ny) * v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) B += __shfl_xor_sync(0xffffffffu, B, o);
-    if (lane == 0) {
-        double phi = 0.0;
-        for (int a = 0; a < p1; ++a) phi += Lq[a] * mom[(size_t)e * n + base + a * stride];
-        beta[t] = B - eb0[t] * phi;
-    }
-}
-
 // T (the three correction components, component stride cst) of cnt = elements
 // x n dofs into shared memory as pairs, component stride sst.  The rows of K
 // and of the face gradient operators sum to zero (the nodal basis is a
@@ -241,56 +172,6 @@ __global__ void rhs_assemble_kernel(int ne, int n_rt, int p, int nfq, int epb, c
         }
     }
     rhs[t] = bfixed[t] + (df_to_double(s0, c0) + df_to_double(s1, c1) + df_to_double(s2, c2)) + jump;
-}
-
-// The same moments from psi stored as FP32 pairs, accumulated in pair
-// arithmetic (see dfloat.cuh) against the six per-ordinate weights
-// wq[k][d] = w_d (1, Ox, Oy, Ox Ox, Ox Oy, Oy Oy)_k, also pairs.
-__global__ void __launch_bounds__(256) moments_df_kernel(int ne, int nd, int n, const float2* __restrict__ wq,
-                                                         const float2* __restrict__ psi2, double* __restrict__ mom) {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < ne; e += warps) {
-        if (lane >= n) continue;
-        float s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
-        const float2* ps = psi2 + (size_t)e * nd * n + lane;
-        for (int d = 0; d < nd; ++d) {
-            const float2 v = __ldcg(ps + (size_t)d * n);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float2 wk = wq[k * nd + d];
-                df_acc(s[k], c[k], wk.x, wk.y, v.x, v.y);
-            }
-        }
-        const size_t o = (size_t)e * n + lane, st = (size_t)ne * n;
-        const double phi = df_to_double(s[0], c[0]);
-        mom[o] = phi;
-        mom[st + o] = df_to_double(s[1], c[1]);
-        mom[2 * st + o] = df_to_double(s[2], c[2]);
-        mom[3 * st + o] = df_to_double(s[3], c[3]) - phi / 3.0;
-        mom[4 * st + o] = df_to_double(s[4], c[4]);
-        mom[5 * st + o] = df_to_double(s[5], c[5]) - phi / 3.0;
-    }
-}
-
-void launch_moments_df(int ne, int nd, int n, const float2* wq, const float2* psi2, double* mom, cudaStream_t s) {
-    int grid = std::max(1, std::min((ne + 7) / 8, 65535));
-    moments_df_kernel<<<grid, 256, 0, s>>>(ne, nd, n, wq, psi2, mom);
-}
-
-void launch_moments(int ne, int nd, int n, const double* w, const double* ox, const double* oy, const double* psi,
-                    double* mom, cudaStream_t s) {
-    int grid = std::max(1, std::min((ne + 7) / 8, 65535));
-    moments_kernel<<<grid, 256, 0, s>>>(ne, nd, n, w, ox, oy, psi, mom);
-}
-
-void launch_beta(int nb, int nd, int n, int p, int nfq, const int32_t* bface_elem, const int32_t* bface_face,
-                 const double* w, const double* ox, const double* oy, const double* L1, const double* nhat,
-                 const double* eb0, const double* psi, const double* mom, double* beta, cudaStream_t s) {
-    const int tot = nb * nfq;
-    if (tot == 0) return;
-    beta_kernel<<<(tot + 7) / 8, 256, 0, s>>>(nb, nd, n, p, nfq, bface_elem, bface_face, w, ox, oy, L1, nhat, eb0, psi,
-                                              mom, beta);
 }
 
 template <int N>

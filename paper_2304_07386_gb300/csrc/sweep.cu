@@ -68,6 +68,118 @@ template <typename T> __device__ __forceinline__ T ldg_cg(const T* p) { return _
 
 }  // namespace
 
+// Moments of element e once all its ordinates are done (Eqs.
+// correction_tensor_disc, broken_Tdiv and bdr_correction_factor_disc), run by
+// the warp of the element's last task in the list after publishing it:
+//   phi = sum_d w_d psi_d, J = sum_d w_d Omega_d psi_d,
+//   T = sum_d w_d Omega_d Omega_d psi_d - phi/3 I        (lane = node),
+// accumulated over the ordinates in their order, as FP32 pairs against the
+// pair weights in FP64 cached mode and in FP64 otherwise; then, at the Gauss
+// points of each boundary face, beta = sum_d w_d |Omega_d . n| psi_d - E_b0 phi
+// (lanes over the ordinates, a fixed-order butterfly sum).  Every other task
+// of the element is earlier in the list, so the bounded waits here end as the
+// upwind waits do.  Returns false if a wait gave up.
+template <typename T, int P, bool DF>
+__device__ __noinline__ bool element_moments(const SweepArgs<T>& a, const int e) {
+    constexpr int P1 = P + 1, N = P1 * P1;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int row = lane < N ? lane : 0;
+    const int nd = a.nd;
+    bool ok = true;
+    for (int d = lane; d < nd && ok; d += 32)
+        ok = wait_epoch(a.done + (size_t)e * nd + d, a.epoch, a.timeout_ns, a.err);
+    ok = __all_sync(FULL, ok);
+    if (!ok) {
+        if (lane == 0) atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
+        return false;
+    }
+    const size_t st = (size_t)a.ne * N, o = (size_t)e * N + row;
+    double phi;
+    if constexpr (DF) {
+        float s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
+        const float2* ps = a.psi2 + (size_t)e * nd * N + row;
+        for (int d = 0; d < nd; ++d) {
+            const float2 v = __ldcg(ps + (size_t)d * N);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float2 wk = a.wq2[k * nd + d];
+                df_acc(s[k], c[k], wk.x, wk.y, v.x, v.y);
+            }
+        }
+        phi = df_to_double(s[0], c[0]);
+        if (lane < N) {
+            a.mom[o] = phi;
+            a.mom[st + o] = df_to_double(s[1], c[1]);
+            a.mom[2 * st + o] = df_to_double(s[2], c[2]);
+            a.mom[3 * st + o] = df_to_double(s[3], c[3]) - phi / 3.0;
+            a.mom[4 * st + o] = df_to_double(s[4], c[4]);
+            a.mom[5 * st + o] = df_to_double(s[5], c[5]) - phi / 3.0;
+        }
+    } else {
+        double jx = 0, jy = 0, pxx = 0, pxy = 0, pyy = 0;
+        phi = 0;
+        const double* ps = a.mpsi + (size_t)e * nd * N + row;
+        for (int d = 0; d < nd; ++d) {
+            const double v = __ldcg(ps + (size_t)d * N);
+            const double wv = a.w[d] * v, x = a.ox[d], y = a.oy[d];
+            phi += wv;
+            jx += wv * x;
+            jy += wv * y;
+            pxx += wv * x * x;
+            pxy += wv * x * y;
+            pyy += wv * y * y;
+        }
+        if (lane < N) {
+            a.mom[o] = phi;
+            a.mom[st + o] = jx;
+            a.mom[2 * st + o] = jy;
+            a.mom[3 * st + o] = pxx - phi / 3.0;
+            a.mom[4 * st + o] = pxy;
+            a.mom[5 * st + o] = pyy - phi / 3.0;
+        }
+    }
+    if (!a.beta) return true;
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+        const int b = a.bface_id[e * 4 + f];  // -1 for interior faces
+        if (b < 0) continue;
+        // face node q of face f is base + q * stride
+        const int base = f == 1 ? P : (f == 2 ? P * P1 : 0);
+        const int stride = (f == 0 || f == 2) ? 1 : P1;
+#pragma unroll 1
+        for (int q = 0; q < a.nfq; ++q) {
+            const int t = b * a.nfq + q;
+            const double* Lq = a.L1 + q * P1;
+            const double nx = a.nhat[2 * t], ny = a.nhat[2 * t + 1];
+            double B = 0.0;
+            for (int d = lane; d < nd; d += 32) {
+                double v = 0.0;
+#pragma unroll
+                for (int k = 0; k < P1; ++k) {
+                    const size_t pi = ((size_t)e * nd + d) * N + base + k * stride;
+                    double pv;
+                    if constexpr (DF) {
+                        const float2 pp = __ldcg(a.psi2 + pi);
+                        pv = (double)pp.x + (double)pp.y;
+                    } else {
+                        pv = __ldcg(a.mpsi + pi);
+                    }
+                    v += Lq[k] * pv;
+                }
+                B += a.w[d] * fabs(a.ox[d] * nx + a.oy[d] * ny) * v;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) B += __shfl_xor_sync(FULL, B, off);
+            double ph = 0.0;
+#pragma unroll
+            for (int k = 0; k < P1; ++k) ph += Lq[k] * __shfl_sync(FULL, phi, base + k * stride);
+            if (lane == 0) a.beta[t] = B - a.eb0[t] * ph;
+        }
+    }
+    return true;
+}
+
 // One (element, ordinate) task of one problem, executed by a whole warp.
 // Returns false if a dependency wait gave up.  EXT compiles in the optional
 // parts (negative flux fixup, lagged inflow of a block Jacobi sweep); without
@@ -85,6 +197,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         const T ox = (T)a.ox[d], oy = (T)a.oy[d];
         const char4 dirs = *reinterpret_cast<const char4*>(a.fdir + ((size_t)e * nd + d) * 4);
         const int dir[4] = {dirs.x, dirs.y, dirs.z, dirs.w};
+        const bool reducer = a.mom != nullptr && a.red[e] == task;
 
         // ---- cached mode: everything that does not depend on upwind data is
         //      loaded before the wait, so HBM latency overlaps the wavefront ----
@@ -328,13 +441,14 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         // ---- publish ----
         if (lane < N) {
             const size_t o = ((size_t)e * nd + d) * N + lane;
-            a.psi[o] = x;
             if constexpr (DF) a.psi2[o] = fixed ? df_make((double)x) : df_norm(ys, yc);
+            else a.psi[o] = x;
             if (MODE == SWEEP_RESIDUAL) a.psi_acc[o] += (double)x;
         }
         __threadfence();  // one warp-wide fence instruction orders every lane's stores
         __syncwarp();
         if (lane == 0) st_release(a.done + task, a.epoch);
+        if (reducer && !element_moments<T, P, DF>(a, e)) return false;
     }
     return true;
 }
@@ -666,6 +780,18 @@ void launch_invert_df(int p, const SweepArgs<double>& a, float2* out, cudaStream
 
 template void launch_invert<double>(int, const SweepArgs<double>&, double*, cudaStream_t);
 template void launch_invert<float>(int, const SweepArgs<float>&, float*, cudaStream_t);
+
+__global__ void pairs_to_f64_kernel(size_t n, const float2* __restrict__ in, double* __restrict__ out) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const float2 v = in[t];
+        out[t] = (double)v.x + (double)v.y;
+    }
+}
+
+void launch_pairs_to_f64(size_t n, const float2* in, double* out, cudaStream_t s) {
+    if (n) pairs_to_f64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out);
+}
 
 void launch_mass_apply(int ne, int nd, int n, const double* M, const double* in, float2* out, cudaStream_t s) {
     const long long tot = (long long)ne * nd * n;

@@ -42,6 +42,7 @@ inline std::barrier<>* emu_block_barrier = nullptr;
 #define __global__
 #define __device__
 #define __forceinline__ inline
+#define __noinline__
 #define __restrict__
 #define __launch_bounds__(...)
 // a block's static shared variables: one instance, which the block's threads

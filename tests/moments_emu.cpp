@@ -1,15 +1,15 @@
-// Test driver (CPU): the angular-moment kernels of moments.cu (moments_kernel
-// on FP64 psi, moments_df_kernel on its FP32-pair copy, beta_kernel at the
-// boundary Gauss points) run on the host through host_kernel_shim.h, on the
-// quadrature and boundary data the library's host setup builds, in the
-// library's layouts and the launch shapes of launch_moments, launch_moments_df
-// and launch_beta.  The kernel source arrives as moments_kernels.inc,
-// extracted from moments.cu by the test.
+// Test driver (CPU): the moment epilogue of the sweep kernel (element_moments
+// in sweep.cu: the angular moments from the FP64 flux, or from its FP32-pair
+// copy as in FP64 cached mode, and beta at the boundary Gauss points) run on
+// the host through host_kernel_shim.h, one warp per element with every flag
+// of the element already published, on the quadrature and boundary data the
+// library's host setup builds, in the library's layouts.  The function's
+// source arrives as moments_kernels.inc, extracted from sweep.cu by the test.
 // Usage: moments_emu DIR NE NNODES M P SN
 //   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, q.f64 (as setup_dump),
 //        DIR/psi.f64 [ne][nd][n] (the device layout)
 //   out: DIR/dims.txt (n nd nfq n_bface), DIR/mom.f64 and DIR/mom_df.f64 [6][ne][n],
-//        DIR/beta.f64 [n_bface][nfq] (from the FP64 moments)
+//        DIR/beta.f64 and DIR/beta_df.f64 [n_bface][nfq]
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -20,8 +20,44 @@
 #include "host_kernel_shim.h"
 #include "setup.hpp"
 
+#include <atomic>
+#include <chrono>
+
 namespace smm {
+
+inline unsigned ld_acquire(const unsigned* p) {
+    return std::atomic_ref<unsigned>(*const_cast<unsigned*>(p)).load(std::memory_order_acquire);
+}
+inline long long global_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+inline int ld_volatile(const int* p) {
+    return std::atomic_ref<int>(*const_cast<int*>(p)).load(std::memory_order_relaxed);
+}
+
 #include "moments_kernels.inc"
+
+}  // namespace smm
+
+// every element's epilogue, one warp per element (8 warps take the elements round-robin)
+template <int P, bool DF>
+static void run_epilogue(const smm::SweepArgs<double>& a) {
+    emu_launch(1, 256, 0, [&] {
+        const int W = (gridDim.x * blockDim.x) >> 5;
+        const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        for (int e = gw; e < a.ne; e += W) smm::element_moments<double, P, DF>(a, e);
+    });
+}
+
+template <bool DF>
+static void run_p(int p, const smm::SweepArgs<double>& a) {
+    switch (p) {
+        case 1: run_epilogue<1, DF>(a); break;
+        case 2: run_epilogue<2, DF>(a); break;
+        case 3: run_epilogue<3, DF>(a); break;
+        default: run_epilogue<4, DF>(a); break;
+    }
 }
 
 template <class T>
@@ -71,21 +107,24 @@ int main(int argc, char** argv) {
         const double v[6] = {w, w * x, w * y, w * x * x, w * x * y, w * y * y};
         for (int k = 0; k < 6; ++k) wq[(size_t)k * nd + d] = smm::df_make(v[k]);
     }
-    std::vector<double> mom((size_t)6 * ne * n, 0.0), mom_df((size_t)6 * ne * n, 0.0), beta((size_t)nb * nfq, 0.0);
-    const int grid = std::max(1, std::min((ne + 7) / 8, 65535));
-    emu_launch(grid, 256, 0, [&] {
-        smm::moments_kernel(ne, nd, n, s.quad.w.data(), s.quad.ox.data(), s.quad.oy.data(), psi.data(), mom.data());
-    });
-    emu_launch(grid, 256, 0, [&] { smm::moments_df_kernel(ne, nd, n, wq.data(), psi2.data(), mom_df.data()); });
-    if (nb * nfq > 0)
-        emu_launch((nb * nfq + 7) / 8, 256, 0, [&] {
-            smm::beta_kernel(nb, nd, n, p, nfq, s.bface_elem.data(), s.bface_face.data(), s.quad.w.data(),
-                             s.quad.ox.data(), s.quad.oy.data(), s.L1.data(), s.b_nhat.data(), s.b_eb0.data(),
-                             psi.data(), mom.data(), beta.data());
-        });
+    std::vector<double> mom((size_t)6 * ne * n, 0.0), mom_df((size_t)6 * ne * n, 0.0);
+    std::vector<double> beta((size_t)nb * nfq, 0.0), beta_df((size_t)nb * nfq, 0.0);
+    std::vector<unsigned> done((size_t)ne * nd, 1u);  // every ordinate of every element published
+    int dev_err = 0;
+    smm::SweepArgs<double> a{};
+    a.ne = ne; a.nd = nd; a.p = p; a.ox = s.quad.ox.data(); a.oy = s.quad.oy.data();
+    a.nbr = s.nbr.data(); a.bface_id = s.bface_id.data();
+    a.done = done.data(); a.epoch = 1; a.err = &dev_err; a.timeout_ns = 60LL * 1000 * 1000 * 1000;
+    a.w = s.quad.w.data(); a.wq2 = wq.data(); a.nfq = nfq; a.L1 = s.L1.data(); a.nhat = s.b_nhat.data();
+    a.eb0 = s.b_eb0.data();
+    a.mpsi = psi.data(); a.mom = mom.data(); a.beta = nb > 0 ? beta.data() : nullptr;
+    run_p<false>(p, a);
+    a.psi2 = psi2.data(); a.mom = mom_df.data(); a.beta = nb > 0 ? beta_df.data() : nullptr;
+    run_p<true>(p, a);
+    if (dev_err) return 6;
     std::ofstream dims(dir + "/dims.txt");
     dims << n << " " << nd << " " << nfq << " " << nb << "\n";
     const bool ok = write_file(dir + "/mom.f64", mom) && write_file(dir + "/mom_df.f64", mom_df) &&
-                    write_file(dir + "/beta.f64", beta);
+                    write_file(dir + "/beta.f64", beta) && write_file(dir + "/beta_df.f64", beta_df);
     return ok && dims ? 0 : 5;
 }

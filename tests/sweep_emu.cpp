@@ -30,7 +30,9 @@
 //        q.f64 ([ne][n], or [nd][ne][n] if ANGULAR), inflow.f64 [nd][n_bface][p+1] if INFLOW,
 //        nbface.txt (the boundary face count); MODE plain | fixup | refine | timeout, K sweeps (refine)
 //   out: DIR/dims.txt (n nd n_bface nlevels), DIR/psi_lu.f64, DIR/psi_inv.f64 and (FP64 modes)
-//        DIR/psi2_inv.f64 (the pair copy as hi + lo) [ne][nd][n], DIR/err.txt (device error words)
+//        DIR/psi2_inv.f64 (the pair copy as hi + lo) [ne][nd][n], the moments the sweep forms
+//        DIR/mom_lu.f64, DIR/mom_inv.f64 [6][ne][n] and beta DIR/beta_lu.f64, DIR/beta_inv.f64
+//        [n_bface][nfq], DIR/err.txt (device error words)
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -83,8 +85,38 @@ static std::vector<float2> to_pairs(const std::vector<double>& v) {
 struct Run {
     std::vector<double> psi;
     std::vector<float2> psi2;
+    std::vector<double> mom, beta;   // formed inside the sweep by each element's last task
+    std::vector<int32_t> red;
+    std::vector<float2> wq2;
     int err = 0;
 };
+
+// the fused moments' arguments, as the library's sweep preparation fills them:
+// each element's last task in list order, the weights (and their pair copies
+// w_d (1, Ox, Oy, OxOx, OxOy, OyOy)), the boundary data, and the outputs
+template <typename T>
+static void moment_args(const smm::Setup& s, smm::SweepArgs<T>& a, Run& out, const double* mpsi) {
+    const int ne = s.ne, nd = s.nd, n = s.n;
+    out.red.assign(ne, 0);
+    for (int32_t t : s.tasks) out.red[t / nd] = t;
+    out.wq2.resize((size_t)6 * nd);
+    for (int d = 0; d < nd; ++d) {
+        const double w = s.quad.w[d], x = s.quad.ox[d], y = s.quad.oy[d];
+        const double v[6] = {w, w * x, w * y, w * x * x, w * x * y, w * y * y};
+        for (int k = 0; k < 6; ++k) out.wq2[(size_t)k * nd + d] = smm::df_make(v[k]);
+    }
+    out.mom.assign((size_t)6 * ne * n, 0.0);
+    out.beta.assign((size_t)s.nb * s.nfq, 0.0);
+    a.red = out.red.data(); a.w = s.quad.w.data(); a.wq2 = out.wq2.data(); a.mpsi = mpsi;
+    a.mom = out.mom.data(); a.beta = s.nb > 0 ? out.beta.data() : nullptr; a.nfq = s.nfq; a.L1 = s.L1.data();
+    a.nhat = s.b_nhat.data(); a.eb0 = s.b_eb0.data();
+}
+
+// FP64 cached mode keeps the flux only as pairs: its FP64 value, as smm_get_psi forms it
+static void pairs_to_psi(Run& r) {
+    r.psi.resize(r.psi2.size());
+    for (size_t i = 0; i < r.psi2.size(); ++i) r.psi[i] = (double)r.psi2[i].x + (double)r.psi2[i].y;
+}
 
 // the arguments the library's sweep preparation fills for an FP64 source sweep
 static smm::SweepArgs<double> base_args(const smm::Setup& s, const std::vector<double>& phi, bool inflow,
@@ -185,6 +217,7 @@ static void run_refined(const smm::Setup& s, const std::vector<double>& phi, boo
         a.fdir = s.fdir.data(); a.nbr = s.nbr.data(); a.nbr_face = s.nbr_face.data(); a.nbr_flip = s.nbr_flip.data();
         a.bface_id = s.bface_id.data();
         a.rhs = res.data(); a.psi = dpsi.data(); a.psi_acc = out.psi.data();
+        moment_args(s, a, out, out.psi.data());
         a.done = done.data(); a.err = &out.err;
         a.timeout_ns = 60LL * 1000 * 1000 * 1000;
         if (form == 1) {
@@ -219,6 +252,7 @@ static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow
         smm::SweepArgs<double> a = base_args(s, phi, inflow, done, lu.err);
         lu.psi.assign(nang, 0.0);
         a.psi = lu.psi.data();
+        moment_args(s, a, lu, lu.psi.data());
         if (fixup) {
             cols.fill(a);
             emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, true>(a); });
@@ -231,15 +265,16 @@ static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow
         smm::SweepArgs<double> a = base_args(s, phi, inflow, done, inv.err);
         Cached store;
         prepare_cached<P>(s, phi, inflow, a, store);
-        inv.psi.assign(nang, 0.0);
         inv.psi2.assign(nang, make_float2(0.0f, 0.0f));
-        a.psi = inv.psi.data(); a.psi2 = inv.psi2.data();
+        a.psi = nullptr; a.psi2 = inv.psi2.data();
+        moment_args(s, a, inv, nullptr);
         if (fixup) {
             cols.fill(a);
             emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, true>(a); });
         } else {
             emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, false>(a); });
         }
+        pairs_to_psi(inv);
     }
 }
 
@@ -260,8 +295,9 @@ static void run_timeout(const smm::Setup& s, const std::vector<double>& phi, boo
         if (form == 1) prepare_cached<P>(s, phi, inflow, a, store);
         out.psi.assign(nang, 0.0);
         out.psi2.assign(nang, make_float2(0.0f, 0.0f));
-        a.psi = out.psi.data();
+        a.psi = form == 0 ? out.psi.data() : nullptr;
         if (form == 1) a.psi2 = out.psi2.data();
+        moment_args(s, a, out, form == 0 ? out.psi.data() : nullptr);
         auto sweep = [&] {
             if (form == 0)
                 emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, false>(a); });
@@ -280,6 +316,7 @@ static void run_timeout(const smm::Setup& s, const std::vector<double>& phi, boo
         a.timeout_ns = 60LL * 1000 * 1000 * 1000;
         sweep();
         e2[form] = out.err;
+        if (form == 1) pairs_to_psi(out);
     }
 }
 
@@ -332,7 +369,9 @@ static bool write_outputs(const std::string& dir, const smm::Setup& s, const Run
     std::ofstream errs(dir + "/err.txt");
     errs << lu.err << " " << inv.err << "\n";
     return write_file(dir + "/psi_lu.f64", lu.psi) && write_file(dir + "/psi_inv.f64", inv.psi) &&
-           write_file(dir + "/psi2_inv.f64", psi2) && (bool)dims && (bool)errs;
+           write_file(dir + "/psi2_inv.f64", psi2) && write_file(dir + "/mom_lu.f64", lu.mom) &&
+           write_file(dir + "/mom_inv.f64", inv.mom) && write_file(dir + "/beta_lu.f64", lu.beta) &&
+           write_file(dir + "/beta_inv.f64", inv.beta) && (bool)dims && (bool)errs;
 }
 
 // sweep_emu --batch DIR COUNT: problems DIR/0 .. DIR/COUNT-1 (each with its
@@ -369,7 +408,8 @@ static int run_batch(const std::string& dir, int count) {
             args[k] = base_args(s, prs[k].phi, prs[k].inflow, done[k], out.err);
             const size_t nang = (size_t)s.ne * s.nd * s.n;
             out.psi.assign(nang, 0.0);
-            args[k].psi = out.psi.data();
+            args[k].psi = form == 0 ? out.psi.data() : nullptr;
+            moment_args(s, args[k], out, form == 0 ? out.psi.data() : nullptr);
             if (form == 1) {
                 switch (s.p) {
                     case 1: prepare_cached<1>(s, prs[k].phi, prs[k].inflow, args[k], store[k]); break;
@@ -391,8 +431,10 @@ static int run_batch(const std::string& dir, int count) {
                 smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, true>(args.data(), merged.data(), ntask);
             });
     }
-    for (int k = 0; k < count; ++k)
+    for (int k = 0; k < count; ++k) {
+        pairs_to_psi(inv[k]);
         if (!write_outputs(dir + "/" + std::to_string(k), prs[k].s, lu[k], inv[k])) return 5;
+    }
     return 0;
 }
 

@@ -115,8 +115,9 @@ def test_rhs_kernels_match_oracle(emu, tmp_path, case):
 
 
 # ---------------------------------------------------------------------------
-# angular moments and the boundary correction (moments_kernel,
-# moments_df_kernel, beta_kernel) against the oracle's closures
+# angular moments and the boundary correction (the sweep kernel's epilogue,
+# element_moments, from the FP64 flux and from its pair copy) against the
+# oracle's closures
 
 @pytest.fixture(scope="module")
 def moments_emu(tmp_path_factory):
@@ -124,13 +125,14 @@ def moments_emu(tmp_path_factory):
     if cxx is None:
         pytest.skip("no C++ compiler")
     d = tmp_path_factory.mktemp("moments_emu")
-    moments = open(os.path.join(CSRC, "moments.cu")).read()
+    sweep = open(os.path.join(CSRC, "sweep.cu")).read()
+    kcuh = open(os.path.join(CSRC, "kernels.cuh")).read()
     dfloat = open(os.path.join(CSRC, "dfloat.cuh")).read()
     body = dfloat[dfloat.index("namespace smm {") + len("namespace smm {"):dfloat.rindex("}")]
-    parts = [body,
-             extract(moments, "__global__ void __launch_bounds__(256) moments_kernel("),
-             extract(moments, "__global__ void __launch_bounds__(256) moments_df_kernel("),
-             extract(moments, "__global__ void beta_kernel(")]
+    enums = re.findall(r"enum : int \{[^}]*\};", kcuh)
+    parts = enums + [extract(kcuh, "struct SweepArgs {") + ";", body,
+                     extract(sweep, "__device__ bool wait_epoch("),
+                     extract(sweep, "__device__ __noinline__ bool element_moments(")]
     (d / "moments_kernels.inc").write_text("\n".join(parts))
     exe = d / "moments_emu"
     subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
@@ -175,14 +177,16 @@ def test_moment_kernels_match_oracle(moments_emu, tmp_path, case):
     assert (n_o, nd_o, nb_o) == (n, disc.nd, len(disc.bfaces)) and beta_ref.shape == (nb_o, nfq_o)
     scale = np.max(np.abs(mom_ref))
     # FP64 sums: rounding only.  Pair sums: each of the nd pair multiply-adds
-    # leaves the float correction term an error of about 2^-48 of the sum.
+    # leaves the float correction term an error of about 2^-48 of the sum
+    # (and the pair copy of psi differs from it by 2^-48).
     for name, tol in (("mom", 1e-13), ("mom_df", 4 * disc.nd * 2.0 ** -48)):
         got = np.fromfile(tmp_path / f"{name}.f64").reshape(6, ne, n)
         assert np.max(np.abs(got - mom_ref)) <= tol * scale, (name, np.max(np.abs(got - mom_ref)) / scale)
     # beta is a difference of terms of the size of phi (zero for S2, whose
     # ordinates all have the same |Omega.n| on the straight boundary)
-    beta = np.fromfile(tmp_path / "beta.f64").reshape(nb_o, nfq_o)
-    assert np.max(np.abs(beta - beta_ref)) <= 1e-13 * scale
+    for name in ("beta", "beta_df"):
+        beta = np.fromfile(tmp_path / f"{name}.f64").reshape(nb_o, nfq_o)
+        assert np.max(np.abs(beta - beta_ref)) <= 1e-13 * scale, name
     if sn == 2:
         assert np.max(np.abs(beta_ref)) <= 1e-13 * scale
     else:
@@ -210,6 +214,7 @@ def sweep_emu(tmp_path_factory):
                      extract(sweep, "__device__ bool wait_epoch("),
                      extract(sweep, "__device__ __forceinline__ int face_node("),
                      extract(sweep, "template <typename T> __device__ __forceinline__ T ldg_cg("),
+                     extract(sweep, "__device__ __noinline__ bool element_moments("),
                      extract(sweep, "__device__ __forceinline__ bool sweep_task("),
                      extract(sweep, "__global__ void __launch_bounds__(256) sweep_kernel("),
                      extract(sweep, "__global__ void __launch_bounds__(256) batch_sweep_kernel("),
@@ -279,16 +284,35 @@ def _run_sweep_emu(exe, tmp_path, case, mode="plain", K=0, **kw):
     assert open(tmp_path / "err.txt").read().split() == ["0", "0"]
     names = ("psi_lu", "psi_inv") + (("psi2_inv",) if mode != "refine" else ())
     got = {k: np.fromfile(tmp_path / f"{k}.f64").reshape(ne, disc.nd, n) for k in names}
+    got_mom = {k: np.fromfile(tmp_path / f"mom_{k}.f64").reshape(6, ne, n) for k in ("lu", "inv")}
+    got_beta = {k: np.fromfile(tmp_path / f"beta_{k}.f64").reshape(len(disc.bfaces), -1) for k in ("lu", "inv")}
+    _run_sweep_emu.moments = (got_mom, got_beta)
     return disc, phi, q, inflow, got
+
+
+def _check_fused_moments(disc, psi_nd, tol=1e-12):
+    """The moments and beta the last emulated sweep formed in its epilogue
+    (each element's last task in list order, after the element's other
+    ordinates) against the oracle's closures of psi_nd ([nd][ne][n])."""
+    from oracle import closures
+    got_mom, got_beta = _run_sweep_emu.moments
+    mom_ref = closures.nodal_moments(disc, psi_nd)
+    beta_ref = closures.beta(disc, psi_nd)
+    scale = np.max(np.abs(mom_ref))
+    for k in ("lu", "inv"):
+        assert np.max(np.abs(got_mom[k] - mom_ref)) <= tol * scale, (k, np.max(np.abs(got_mom[k] - mom_ref)) / scale)
+        assert np.max(np.abs(got_beta[k] - beta_ref)) <= tol * scale, k
 
 
 @pytest.mark.parametrize("case", SWEEP_CASES, ids=lambda c: "nx%d_ny%d_m%d_p%d_S%d_%s" % (c[:5] + c[6:]))
 def test_sweep_kernel_matches_oracle(sweep_emu, tmp_path, case):
     disc, phi, q, inflow, got = _run_sweep_emu(sweep_emu, tmp_path, case)
-    ref = disc.sweep(phi, q, inflow).transpose(1, 0, 2)   # [ne][nd][n], the device layout
+    ref_nd = disc.sweep(phi, q, inflow)
+    ref = ref_nd.transpose(1, 0, 2)   # [ne][nd][n], the device layout
     scale = np.max(np.abs(ref))
     for name, psi in got.items():
         assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
+    _check_fused_moments(disc, ref_nd)
 
 
 def test_sweep_kernel_wait_expires_and_the_next_sweep_is_exact(sweep_emu, tmp_path):
@@ -343,6 +367,17 @@ def test_batched_sweep_kernel_matches_oracle(sweep_emu, tmp_path):
         for name in ("psi_lu", "psi_inv", "psi2_inv"):
             got = np.fromfile(d / f"{name}.f64").reshape(ref.shape)
             assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (k, name, np.max(np.abs(got - ref)) / scale)
+        # the moments each problem's own last tasks formed inside the batched launch
+        from oracle import closures
+        disc = _sweep_problem(cases[k])[3]
+        ref_nd = ref.transpose(1, 0, 2)
+        mom_ref, beta_ref = closures.nodal_moments(disc, ref_nd), closures.beta(disc, ref_nd)
+        mscale = np.max(np.abs(mom_ref))
+        for form in ("lu", "inv"):
+            mom = np.fromfile(d / f"mom_{form}.f64").reshape(mom_ref.shape)
+            beta = np.fromfile(d / f"beta_{form}.f64").reshape(beta_ref.shape)
+            assert np.max(np.abs(mom - mom_ref)) <= 1e-12 * mscale, (k, form)
+            assert np.max(np.abs(beta - beta_ref)) <= 1e-12 * mscale, (k, form)
 
 
 def test_sweep_kernel_fixup_matches_oracle(sweep_emu, tmp_path):
@@ -358,6 +393,7 @@ def test_sweep_kernel_fixup_matches_oracle(sweep_emu, tmp_path):
     scale = np.max(np.abs(ref))
     for name, psi in got.items():
         assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
+    _check_fused_moments(disc, ref.transpose(1, 0, 2))
 
 
 @pytest.mark.parametrize("case", [SWEEP_CASES[1], SWEEP_CASES[3]], ids=["p2_curved", "p4_curved"])
@@ -373,6 +409,8 @@ def test_fp32_refined_sweeps_converge_to_the_fp64_sweep(sweep_emu, tmp_path, cas
     for name in ("psi_lu", "psi_inv"):
         assert 1e-10 < errs[1][name] < 1e-5, (name, errs)
         assert errs[4][name] < 1e-12, (name, errs)
+    # the moments formed inside the last correction sweep, from the accumulated FP64 flux
+    _check_fused_moments(disc, ref.transpose(1, 0, 2), tol=1e-11)
 
 
 # ---------------------------------------------------------------------------
