@@ -52,7 +52,7 @@ struct smm_ctx {
     int32_t *tasks = nullptr, *nbr = nullptr, *nbr_face = nullptr, *nbr_flip = nullptr, *bface_id = nullptr;
     int32_t *bface_elem = nullptr, *bface_face = nullptr;
     int8_t* fdir = nullptr;
-    int32_t* red = nullptr;        // [ne] the element's last task in list order (forms its moments)
+    unsigned* gate = nullptr;      // the sweep's gate before its moment reductions (one word)
     // sweep matrices
     double *M = nullptr, *Gx = nullptr, *Gy = nullptr, *Fx = nullptr, *Fy = nullptr;
     float *M32 = nullptr, *Gx32 = nullptr, *Gy32 = nullptr, *Fx32 = nullptr, *Fy32 = nullptr;
@@ -369,12 +369,6 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         h->psi = h->alloc<double>(nang);
         if (!h->psi) return bail(SMM_ERR_OOM, "device allocation failed");
     }
-    {
-        // the element's last task in list order forms the element's moments after its other ordinates
-        std::vector<int32_t> red(s.ne, 0);
-        for (int32_t t : s.tasks) red[t / s.nd] = t;
-        if (!upload(h, h->red, red)) return bail(SMM_ERR_OOM, "device allocation failed");
-    }
     if (o.sweep_tiles > 1 && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) {
         h->psi_lag = h->alloc<double>(nang);
         if (!h->psi_lag) return bail(SMM_ERR_OOM, "device allocation failed");
@@ -384,6 +378,8 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         h->res = h->alloc<float>(nang);
         if (!h->dpsi || !h->res) return bail(SMM_ERR_OOM, "device allocation failed");
     }
+    h->gate = h->alloc<unsigned>(1);
+    if (!h->gate) return bail(SMM_ERR_OOM, "device allocation failed");
     h->done = h->alloc<unsigned>((size_t)s.ne * s.nd);
     h->ticket = h->alloc<unsigned>(4);
     h->err = h->alloc<int>(4);
@@ -732,7 +728,8 @@ smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) 
     a.fdir = h->fdir; a.nbr = h->nbr; a.nbr_face = h->nbr_face; a.nbr_flip = h->nbr_flip; a.bface_id = h->bface_id;
     a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket; a.err = h->err;
     a.timeout_ns = (long long)(h->opt.spin_timeout_s * 1e9);
-    a.red = h->red; a.w = h->w; a.wq2 = h->wq2; a.mpsi = h->psi; a.mom = h->mom;
+    SMM_CUDA(cudaMemsetAsync(h->gate, 0, sizeof(unsigned), h->stream));
+    a.gate = h->gate; a.w = h->w; a.wq2 = h->wq2; a.mpsi = h->psi; a.mom = h->mom;
     a.beta = h->nb > 0 ? h->beta : nullptr; a.nfq = h->nfq; a.L1 = h->L1; a.nhat = h->b_nhat; a.eb0 = h->b_eb0;
     if constexpr (std::is_same<T, double>::value) {
         a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy;
@@ -1343,19 +1340,23 @@ struct smm_batch_ctx {
     std::vector<smm_handle> hs;
     bool fp32 = false, cached = false;
     cudaStream_t stream = nullptr;
-    int ntask = 0, grid = 1, block = 256, sms = 1;
+    int ntask = 0, nelem = 0, grid = 1, block = 256, sms = 1;
     double tuned_ms = 0.0;
     int2* tasks = nullptr;
+    int2* elems = nullptr;          // (problem, element) in the order the elements finish
     void* args_dev = nullptr;
     void* args_host = nullptr;  // pinned
     size_t args_bytes = 0;
     int* err = nullptr;
+    unsigned* gate = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     ~smm_batch_ctx() {
         if (tasks) cudaFree(tasks);
+        if (elems) cudaFree(elems);
         if (args_dev) cudaFree(args_dev);
         if (args_host) cudaFreeHost(args_host);
         if (err) cudaFree(err);
+        if (gate) cudaFree(gate);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -1366,15 +1367,17 @@ namespace {
 template <typename T>
 smm_status batch_enqueue(smm_batch b, const double* const* phis) {
     auto* host = static_cast<smm::SweepArgs<T>*>(b->args_host);
+    SMM_CUDA(cudaMemsetAsync(b->gate, 0, sizeof(unsigned), b->stream));
     for (size_t i = 0; i < b->hs.size(); ++i) {
         smm_status st = prepare_sweep<T>(b->hs[i], phis ? phis[i] : nullptr, host[i]);
         if (st != SMM_OK) return st;
         host[i].err = b->err;
+        host[i].gate = b->gate;  // one gate for the whole launch
     }
     SMM_CUDA(cudaMemcpyAsync(b->args_dev, b->args_host, b->args_bytes, cudaMemcpyHostToDevice, b->stream));
     SMM_CUDA(smm::launch_batch_sweep<T>(b->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE, b->cached,
                                          static_cast<const smm::SweepArgs<T>*>(b->args_dev), b->tasks, b->ntask,
-                                         b->grid, b->block, b->stream));
+                                         b->elems, b->nelem, b->grid, b->block, b->stream));
     b->hs[0]->launches += 1;
     return SMM_OK;
 }
@@ -1429,12 +1432,20 @@ smm_status smm_batch_create(int32_t n, const smm_handle* handles, smm_batch* out
             for (int t = h->level_start[l]; t < h->level_start[l + 1]; ++t) merged.push_back(make_int2(i, h->tasks_host[t]));
         }
     b->ntask = (int)merged.size();
+    // every problem's elements, for the moment reductions after the batched sweep's tasks
+    std::vector<int2> elems;
+    for (int i = 0; i < n; ++i)
+        for (int e = 0; e < b->hs[i]->ne; ++e) elems.push_back(make_int2(i, e));
+    b->nelem = (int)elems.size();
     b->args_bytes = (size_t)n * (b->fp32 ? sizeof(smm::SweepArgs<float>) : sizeof(smm::SweepArgs<double>));
     if (cudaMalloc(&b->tasks, merged.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&b->elems, elems.size() * sizeof(int2)) != cudaSuccess ||
         cudaMalloc(&b->args_dev, b->args_bytes) != cudaSuccess || cudaMallocHost(&b->args_host, b->args_bytes) != cudaSuccess ||
-        cudaMalloc(&b->err, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&b->err, sizeof(int)) != cudaSuccess || cudaMalloc(&b->gate, sizeof(unsigned)) != cudaSuccess)
         return bail(SMM_ERR_OOM, "batch allocation failed");
     if (cudaMemcpyAsync(b->tasks, merged.data(), merged.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->elems, elems.data(), elems.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) !=
             cudaSuccess ||
         cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess)
         return bail(SMM_ERR_CUDA, "batch upload failed");

@@ -66,10 +66,10 @@ struct SweepArgs {
                                // cached mode, whose flux is psi2)
     double* psi_acc;           // RESIDUAL: psi_acc += psi
     // Angular moments fused into the sweep (Eqs. correction_tensor_disc, bdr_correction_factor_disc):
-    // the task of each element that comes last in the task list (red[e]) waits for the element's other
-    // ordinates, then forms the element's moments and the boundary correction at the Gauss points of
-    // its boundary faces.  mom == nullptr: no moments.
-    const int32_t* red;        // [ne] task id e*nd + d of the element's last task in list order
+    // once every warp of the launch has finished its tasks (the gate), warp k forms the moments of
+    // elements k, k + warps, ... and the boundary correction at the Gauss points of their boundary
+    // faces.  mom == nullptr: no moments.
+    unsigned* gate;            // warps arrived after their last task (zero at launch; one per launch)
     const double* w;           // [nd] ordinate weights
     const float2* wq2;         // FP64 cached mode: [6][nd] pairs of w_d (1, Ox, Oy, OxOx, OxOy, OyOy)
     const double* mpsi;        // other modes: the FP64 flux the moments read, [ne][nd][n]
@@ -112,10 +112,11 @@ struct ResidualArgs {
 
 template <typename T>
 void launch_sweep(int p, int mode, const SweepArgs<T>& a, int grid, cudaStream_t s);
-// many problems in one cooperative launch; tasks: (problem, task) pairs sorted by level
+// many problems in one cooperative launch; tasks: (problem, task) pairs sorted by level; elems:
+// (problem, element) of every element of every problem
 template <typename T>
-cudaError_t launch_batch_sweep(int mode, bool cached, const SweepArgs<T>* args, const int2* tasks, int ntask, int grid,
-                               int block, cudaStream_t s);
+cudaError_t launch_batch_sweep(int mode, bool cached, const SweepArgs<T>* args, const int2* tasks, int ntask,
+                               const int2* elems, int nelem, int grid, int block, cudaStream_t s);
 int batch_blocks_per_sm(int mode, bool fp32, bool cached, int block);
 // form every local inverse A_{K,d}^{-1} (column-major, type T) in ainv_out
 template <typename T>

@@ -68,43 +68,41 @@ template <typename T> __device__ __forceinline__ T ldg_cg(const T* p) { return _
 
 }  // namespace
 
-// Moments of element e once all its ordinates are done (Eqs.
-// correction_tensor_disc, broken_Tdiv and bdr_correction_factor_disc), run by
-// the warp of the element's last task in the list after publishing it:
+// Moments of element e (Eqs. correction_tensor_disc, broken_Tdiv and
+// bdr_correction_factor_disc), formed after the sweep's last task:
 //   phi = sum_d w_d psi_d, J = sum_d w_d Omega_d psi_d,
 //   T = sum_d w_d Omega_d Omega_d psi_d - phi/3 I        (lane = node),
-// accumulated over the ordinates in their order, as FP32 pairs against the
-// pair weights in FP64 cached mode and in FP64 otherwise; then, at the Gauss
-// points of each boundary face, beta = sum_d w_d |Omega_d . n| psi_d - E_b0 phi
-// (lanes over the ordinates, a fixed-order butterfly sum).  Every other task
-// of the element is earlier in the list, so the bounded waits here end as the
-// upwind waits do.  Returns false if a wait gave up.
+// accumulated over the ordinates in their order (so the result does not
+// depend on which warp forms it), as FP32 pairs against the pair weights in
+// FP64 cached mode and in FP64 otherwise; then, at the Gauss points of each
+// boundary face, beta = sum_d w_d |Omega_d . n| psi_d - E_b0 phi (lanes over
+// the ordinates, a fixed-order butterfly sum).  The flux loads are issued
+// eight ordinates at a time.
 template <typename T, int P, bool DF>
-__device__ __noinline__ bool element_moments(const SweepArgs<T>& a, const int e) {
+__device__ __noinline__ void element_moments(const SweepArgs<T>& a, const int e) {
     constexpr int P1 = P + 1, N = P1 * P1;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int row = lane < N ? lane : 0;
     const int nd = a.nd;
-    bool ok = true;
-    for (int d = lane; d < nd && ok; d += 32)
-        ok = wait_epoch(a.done + (size_t)e * nd + d, a.epoch, a.timeout_ns, a.err);
-    ok = __all_sync(FULL, ok);
-    if (!ok) {
-        if (lane == 0) atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
-        return false;
-    }
     const size_t st = (size_t)a.ne * N, o = (size_t)e * N + row;
+    constexpr int B = 8;  // ordinates whose loads are in flight together
     double phi;
     if constexpr (DF) {
         float s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
         const float2* ps = a.psi2 + (size_t)e * nd * N + row;
-        for (int d = 0; d < nd; ++d) {
-            const float2 v = __ldcg(ps + (size_t)d * N);
+        for (int d0 = 0; d0 < nd; d0 += B) {
+            float2 v[B];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float2 wk = a.wq2[k * nd + d];
-                df_acc(s[k], c[k], wk.x, wk.y, v.x, v.y);
+            for (int k = 0; k < B; ++k) v[k] = d0 + k < nd ? __ldcg(ps + (size_t)(d0 + k) * N) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                if (d0 + k >= nd) break;
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    const float2 wk = a.wq2[m * nd + d0 + k];
+                    df_acc(s[m], c[m], wk.x, wk.y, v[k].x, v[k].y);
+                }
             }
         }
         phi = df_to_double(s[0], c[0]);
@@ -120,15 +118,22 @@ __device__ __noinline__ bool element_moments(const SweepArgs<T>& a, const int e)
         double jx = 0, jy = 0, pxx = 0, pxy = 0, pyy = 0;
         phi = 0;
         const double* ps = a.mpsi + (size_t)e * nd * N + row;
-        for (int d = 0; d < nd; ++d) {
-            const double v = __ldcg(ps + (size_t)d * N);
-            const double wv = a.w[d] * v, x = a.ox[d], y = a.oy[d];
-            phi += wv;
-            jx += wv * x;
-            jy += wv * y;
-            pxx += wv * x * x;
-            pxy += wv * x * y;
-            pyy += wv * y * y;
+        for (int d0 = 0; d0 < nd; d0 += B) {
+            double v[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k) v[k] = d0 + k < nd ? __ldcg(ps + (size_t)(d0 + k) * N) : 0.0;
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                if (d0 + k >= nd) break;
+                const int d = d0 + k;
+                const double wv = a.w[d] * v[k], x = a.ox[d], y = a.oy[d];
+                phi += wv;
+                jx += wv * x;
+                jy += wv * y;
+                pxx += wv * x * x;
+                pxy += wv * x * y;
+                pyy += wv * y * y;
+            }
         }
         if (lane < N) {
             a.mom[o] = phi;
@@ -139,7 +144,7 @@ __device__ __noinline__ bool element_moments(const SweepArgs<T>& a, const int e)
             a.mom[5 * st + o] = pyy - phi / 3.0;
         }
     }
-    if (!a.beta) return true;
+    if (!a.beta) return;
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
         const int b = a.bface_id[e * 4 + f];  // -1 for interior faces
@@ -177,7 +182,35 @@ __device__ __noinline__ bool element_moments(const SweepArgs<T>& a, const int e)
             if (lane == 0) a.beta[t] = B - a.eb0[t] * ph;
         }
     }
-    return true;
+}
+
+// Grid-wide gate between the sweep's tasks and its moment reductions: every
+// warp arrives after its last task and waits (bounded) until all warps have.
+// Reductions started while the wavefront's last levels still run would take
+// issue slots from their latency-bound tasks.  Returns false if the wait gave
+// up or a task's wait did; every warp arrives either way.
+__device__ bool sweep_gate(unsigned* gate, unsigned warps, long long timeout_ns, int* err) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane == 0) {
+        __threadfence();
+        atomicAdd(gate, 1u);
+        if (ld_acquire(gate) != warps) {
+            const long long t0 = global_ns();
+            ok = false;
+            for (unsigned it = 1; it < (1u << 30); ++it) {
+                if (ld_acquire(gate) == warps) {
+                    ok = true;
+                    break;
+                }
+                if ((it & 31u) == 0 && global_ns() - t0 > timeout_ns) break;
+                __nanosleep(256);
+            }
+            if (!ok) atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+        }
+        ok = ok && ld_volatile(err) == DEV_OK;
+    }
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
 // One (element, ordinate) task of one problem, executed by a whole warp.
@@ -197,7 +230,6 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         const T ox = (T)a.ox[d], oy = (T)a.oy[d];
         const char4 dirs = *reinterpret_cast<const char4*>(a.fdir + ((size_t)e * nd + d) * 4);
         const int dir[4] = {dirs.x, dirs.y, dirs.z, dirs.w};
-        const bool reducer = a.mom != nullptr && a.red[e] == task;
 
         // ---- cached mode: everything that does not depend on upwind data is
         //      loaded before the wait, so HBM latency overlaps the wavefront ----
@@ -448,7 +480,6 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         __threadfence();  // one warp-wide fence instruction orders every lane's stores
         __syncwarp();
         if (lane == 0) st_release(a.done + task, a.epoch);
-        if (reducer && !element_moments<T, P, DF>(a, e)) return false;
     }
     return true;
 }
@@ -457,12 +488,21 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
 // t mod W, so each warp meets its tasks in level order; with every warp
 // co-resident (cooperative launch) the task a warp waits for is owned by a
 // running warp that reaches it after finishing only earlier-level tasks.
+// Cached-inverse sweeps: at least three blocks per SM (four for p <= 3, whose
+// tasks hold fewer inverse entries per lane).  They are bound by the latency
+// of each task's chain of dependent loads, so resident warps set their
+// throughput; the moment reduction after the tasks takes any register spills.
+// (The in-register LU keeps its registers: it is bound by its FP64 arithmetic.)
 template <typename T, int P, int MODE, bool INV, bool EXT>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(256, INV ? (P <= 3 ? 4 : 3) : 1) sweep_kernel(SweepArgs<T> a) {
+    constexpr bool DF = INV && sizeof(T) == 8;
     const int W = (gridDim.x * blockDim.x) >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (int t = gw; t < a.ntask; t += W)
-        if (!sweep_task<T, P, MODE, INV, EXT>(a, a.tasks[t])) break;
+    bool ok = true;
+    for (int t = gw; t < a.ntask && ok; t += W) ok = sweep_task<T, P, MODE, INV, EXT>(a, a.tasks[t]);
+    if (!a.mom) return;
+    if (!sweep_gate(a.gate, (unsigned)W, a.timeout_ns, a.err) || !ok) return;
+    for (int e = gw; e < a.ne; e += W) element_moments<T, P, DF>(a, e);
 }
 
 // Many problems in one launch: the merged list holds (problem, task) pairs
@@ -470,22 +510,36 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
 // problem's order p.  The same schedule argument holds: a task's upwind tasks
 // belong to its problem, sit at lower levels and so earlier in the list.
 template <typename T, int MODE, bool INV>
-__global__ void __launch_bounds__(256) batch_sweep_kernel(const SweepArgs<T>* __restrict__ args,
-                                                          const int2* __restrict__ tasks, int ntask) {
+__global__ void __launch_bounds__(256, INV ? 3 : 1) batch_sweep_kernel(const SweepArgs<T>* __restrict__ args,
+                                                          const int2* __restrict__ tasks, int ntask,
+                                                          const int2* __restrict__ elems, int nelem) {
     const int W = (gridDim.x * blockDim.x) >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     constexpr bool EXT = sizeof(T) == 8 && MODE == SWEEP_SOURCE;  // problems may use fixup or tiles
-    for (int t = gw; t < ntask; t += W) {
+    constexpr bool DF = INV && sizeof(T) == 8;
+    bool ok = true;
+    for (int t = gw; t < ntask && ok; t += W) {
         const int2 it = tasks[t];
         const SweepArgs<T>& a = args[it.x];
-        bool ok = true;
         switch (a.p) {
             case 1: ok = sweep_task<T, 1, MODE, INV, EXT>(a, it.y); break;
             case 2: ok = sweep_task<T, 2, MODE, INV, EXT>(a, it.y); break;
             case 3: ok = sweep_task<T, 3, MODE, INV, EXT>(a, it.y); break;
             default: ok = sweep_task<T, 4, MODE, INV, EXT>(a, it.y); break;
         }
-        if (!ok) break;
+    }
+    if (!args[0].mom) return;
+    if (!sweep_gate(args[0].gate, (unsigned)W, args[0].timeout_ns, args[0].err) || !ok) return;
+    // every problem's element moments
+    for (int k = gw; k < nelem; k += W) {
+        const int2 pe = elems[k];
+        const SweepArgs<T>& b = args[pe.x];
+        switch (b.p) {
+            case 1: element_moments<T, 1, DF>(b, pe.y); break;
+            case 2: element_moments<T, 2, DF>(b, pe.y); break;
+            case 3: element_moments<T, 3, DF>(b, pe.y); break;
+            default: element_moments<T, 4, DF>(b, pe.y); break;
+        }
     }
 }
 
@@ -711,27 +765,27 @@ static int residual_grid(long long ntask) {
 }
 
 template <typename T, int MODE, bool INV>
-static cudaError_t launch_batch_one(const SweepArgs<T>* args, const int2* tasks, int ntask, int grid, int block,
-                                   cudaStream_t s) {
-    void* params[] = {(void*)&args, (void*)&tasks, (void*)&ntask};
+static cudaError_t launch_batch_one(const SweepArgs<T>* args, const int2* tasks, int ntask, const int2* elems,
+                                   int nelem, int grid, int block, cudaStream_t s) {
+    void* params[] = {(void*)&args, (void*)&tasks, (void*)&ntask, (void*)&elems, (void*)&nelem};
     return cudaLaunchCooperativeKernel((const void*)batch_sweep_kernel<T, MODE, INV>, dim3(grid), dim3(block),
                                        params, 0, s);
 }
 
 template <typename T>
-cudaError_t launch_batch_sweep(int mode, bool cached, const SweepArgs<T>* args, const int2* tasks, int ntask, int grid,
-                               int block, cudaStream_t s) {
+cudaError_t launch_batch_sweep(int mode, bool cached, const SweepArgs<T>* args, const int2* tasks, int ntask,
+                               const int2* elems, int nelem, int grid, int block, cudaStream_t s) {
     if (mode == SWEEP_SOURCE)
-        return cached ? launch_batch_one<T, SWEEP_SOURCE, true>(args, tasks, ntask, grid, block, s)
-                      : launch_batch_one<T, SWEEP_SOURCE, false>(args, tasks, ntask, grid, block, s);
-    return cached ? launch_batch_one<T, SWEEP_RESIDUAL, true>(args, tasks, ntask, grid, block, s)
-                  : launch_batch_one<T, SWEEP_RESIDUAL, false>(args, tasks, ntask, grid, block, s);
+        return cached ? launch_batch_one<T, SWEEP_SOURCE, true>(args, tasks, ntask, elems, nelem, grid, block, s)
+                      : launch_batch_one<T, SWEEP_SOURCE, false>(args, tasks, ntask, elems, nelem, grid, block, s);
+    return cached ? launch_batch_one<T, SWEEP_RESIDUAL, true>(args, tasks, ntask, elems, nelem, grid, block, s)
+                  : launch_batch_one<T, SWEEP_RESIDUAL, false>(args, tasks, ntask, elems, nelem, grid, block, s);
 }
 
-template cudaError_t launch_batch_sweep<double>(int, bool, const SweepArgs<double>*, const int2*, int, int, int,
-                                                cudaStream_t);
-template cudaError_t launch_batch_sweep<float>(int, bool, const SweepArgs<float>*, const int2*, int, int, int,
-                                               cudaStream_t);
+template cudaError_t launch_batch_sweep<double>(int, bool, const SweepArgs<double>*, const int2*, int, const int2*,
+                                                int, int, int, cudaStream_t);
+template cudaError_t launch_batch_sweep<float>(int, bool, const SweepArgs<float>*, const int2*, int, const int2*, int,
+                                               int, int, cudaStream_t);
 
 int batch_blocks_per_sm(int mode, bool fp32, bool cached, int block) {
     int nb = 0;

@@ -1,8 +1,8 @@
 // Test driver (CPU): the moment epilogue of the sweep kernel (element_moments
 // in sweep.cu: the angular moments from the FP64 flux, or from its FP32-pair
 // copy as in FP64 cached mode, and beta at the boundary Gauss points) run on
-// the host through host_kernel_shim.h, one warp per element with every flag
-// of the element already published, on the quadrature and boundary data the
+// the host through host_kernel_shim.h, one warp per element (as after the
+// sweep's gate, every ordinate already swept), on the quadrature and boundary data the
 // library's host setup builds, in the library's layouts.  The function's
 // source arrives as moments_kernels.inc, extracted from sweep.cu by the test.
 // Usage: moments_emu DIR NE NNODES M P SN
@@ -109,19 +109,15 @@ int main(int argc, char** argv) {
     }
     std::vector<double> mom((size_t)6 * ne * n, 0.0), mom_df((size_t)6 * ne * n, 0.0);
     std::vector<double> beta((size_t)nb * nfq, 0.0), beta_df((size_t)nb * nfq, 0.0);
-    std::vector<unsigned> done((size_t)ne * nd, 1u);  // every ordinate of every element published
-    int dev_err = 0;
     smm::SweepArgs<double> a{};
     a.ne = ne; a.nd = nd; a.p = p; a.ox = s.quad.ox.data(); a.oy = s.quad.oy.data();
     a.nbr = s.nbr.data(); a.bface_id = s.bface_id.data();
-    a.done = done.data(); a.epoch = 1; a.err = &dev_err; a.timeout_ns = 60LL * 1000 * 1000 * 1000;
     a.w = s.quad.w.data(); a.wq2 = wq.data(); a.nfq = nfq; a.L1 = s.L1.data(); a.nhat = s.b_nhat.data();
     a.eb0 = s.b_eb0.data();
     a.mpsi = psi.data(); a.mom = mom.data(); a.beta = nb > 0 ? beta.data() : nullptr;
     run_p<false>(p, a);
     a.psi2 = psi2.data(); a.mom = mom_df.data(); a.beta = nb > 0 ? beta_df.data() : nullptr;
     run_p<true>(p, a);
-    if (dev_err) return 6;
     std::ofstream dims(dir + "/dims.txt");
     dims << n << " " << nd << " " << nfq << " " << nb << "\n";
     const bool ok = write_file(dir + "/mom.f64", mom) && write_file(dir + "/mom_df.f64", mom_df) &&

@@ -33,6 +33,7 @@
 //        DIR/psi2_inv.f64 (the pair copy as hi + lo) [ne][nd][n], the moments the sweep forms
 //        DIR/mom_lu.f64, DIR/mom_inv.f64 [6][ne][n] and beta DIR/beta_lu.f64, DIR/beta_inv.f64
 //        [n_bface][nfq], DIR/err.txt (device error words)
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -85,20 +86,19 @@ static std::vector<float2> to_pairs(const std::vector<double>& v) {
 struct Run {
     std::vector<double> psi;
     std::vector<float2> psi2;
-    std::vector<double> mom, beta;   // formed inside the sweep by each element's last task
-    std::vector<int32_t> red;
+    std::vector<double> mom, beta;   // formed inside the sweep after all its tasks
+    std::vector<unsigned> gate;
     std::vector<float2> wq2;
     int err = 0;
 };
 
 // the fused moments' arguments, as the library's sweep preparation fills them:
-// each element's last task in list order, the weights (and their pair copies
-// w_d (1, Ox, Oy, OxOx, OxOy, OyOy)), the boundary data, and the outputs
+// the gate (zero), the weights (and their pair copies w_d (1, Ox, Oy, OxOx,
+// OxOy, OyOy)), the boundary data, and the outputs
 template <typename T>
 static void moment_args(const smm::Setup& s, smm::SweepArgs<T>& a, Run& out, const double* mpsi) {
     const int ne = s.ne, nd = s.nd, n = s.n;
-    out.red.assign(ne, 0);
-    for (int32_t t : s.tasks) out.red[t / nd] = t;
+    out.gate.assign(1, 0u);
     out.wq2.resize((size_t)6 * nd);
     for (int d = 0; d < nd; ++d) {
         const double w = s.quad.w[d], x = s.quad.ox[d], y = s.quad.oy[d];
@@ -107,7 +107,7 @@ static void moment_args(const smm::Setup& s, smm::SweepArgs<T>& a, Run& out, con
     }
     out.mom.assign((size_t)6 * ne * n, 0.0);
     out.beta.assign((size_t)s.nb * s.nfq, 0.0);
-    a.red = out.red.data(); a.w = s.quad.w.data(); a.wq2 = out.wq2.data(); a.mpsi = mpsi;
+    a.gate = out.gate.data(); a.w = s.quad.w.data(); a.wq2 = out.wq2.data(); a.mpsi = mpsi;
     a.mom = out.mom.data(); a.beta = s.nb > 0 ? out.beta.data() : nullptr; a.nfq = s.nfq; a.L1 = s.L1.data();
     a.nhat = s.b_nhat.data(); a.eb0 = s.b_eb0.data();
 }
@@ -234,6 +234,7 @@ static void run_refined(const smm::Setup& s, const std::vector<double>& phi, boo
         for (int k = 0; k < K; ++k) {
             emu_launch((ntask + 7) / 8, 256, 0, [&] { smm::residual_kernel<P>(r); });
             a.epoch = (unsigned)(k + 1);
+            out.gate[0] = 0u;
             if (form == 0)
                 emu_launch(1, 256, 0, [&] { smm::sweep_kernel<float, P, smm::SWEEP_RESIDUAL, false, false>(a); });
             else
@@ -314,6 +315,7 @@ static void run_timeout(const smm::Setup& s, const std::vector<double>& phi, boo
         a.ntask = (int)s.tasks.size();
         a.epoch = 2;
         a.timeout_ns = 60LL * 1000 * 1000 * 1000;
+        out.gate[0] = 0u;
         sweep();
         e2[form] = out.err;
         if (form == 1) pairs_to_psi(out);
@@ -422,13 +424,22 @@ static int run_batch(const std::string& dir, int count) {
             }
         }
         const int ntask = (int)merged.size();
+        // every problem's elements; one gate for the launch
+        std::vector<int2> elems;
+        for (int k = 0; k < count; ++k)
+            for (int e = 0; e < prs[k].s.ne; ++e) elems.push_back(make_int2(k, e));
+        std::vector<unsigned> gate(1, 0u);
+        for (int k = 0; k < count; ++k) args[k].gate = gate.data();
+        const int nelem = (int)elems.size();
         if (form == 0)
             emu_launch(1, 256, 0, [&] {
-                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, false>(args.data(), merged.data(), ntask);
+                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, false>(args.data(), merged.data(), ntask,
+                                                                          elems.data(), nelem);
             });
         else
             emu_launch(1, 256, 0, [&] {
-                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, true>(args.data(), merged.data(), ntask);
+                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, true>(args.data(), merged.data(), ntask,
+                                                                         elems.data(), nelem);
             });
     }
     for (int k = 0; k < count; ++k) {

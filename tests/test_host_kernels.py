@@ -131,8 +131,7 @@ def moments_emu(tmp_path_factory):
     body = dfloat[dfloat.index("namespace smm {") + len("namespace smm {"):dfloat.rindex("}")]
     enums = re.findall(r"enum : int \{[^}]*\};", kcuh)
     parts = enums + [extract(kcuh, "struct SweepArgs {") + ";", body,
-                     extract(sweep, "__device__ bool wait_epoch("),
-                     extract(sweep, "__device__ __noinline__ bool element_moments(")]
+                     extract(sweep, "__device__ __noinline__ void element_moments(")]
     (d / "moments_kernels.inc").write_text("\n".join(parts))
     exe = d / "moments_emu"
     subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
@@ -214,10 +213,11 @@ def sweep_emu(tmp_path_factory):
                      extract(sweep, "__device__ bool wait_epoch("),
                      extract(sweep, "__device__ __forceinline__ int face_node("),
                      extract(sweep, "template <typename T> __device__ __forceinline__ T ldg_cg("),
-                     extract(sweep, "__device__ __noinline__ bool element_moments("),
+                     extract(sweep, "__device__ __noinline__ void element_moments("),
+                     extract(sweep, "__device__ bool sweep_gate("),
                      extract(sweep, "__device__ __forceinline__ bool sweep_task("),
-                     extract(sweep, "__global__ void __launch_bounds__(256) sweep_kernel("),
-                     extract(sweep, "__global__ void __launch_bounds__(256) batch_sweep_kernel("),
+                     extract(sweep, "__global__ void __launch_bounds__(256, INV ? (P <= 3 ? 4 : 3) : 1) sweep_kernel("),
+                     extract(sweep, "__global__ void __launch_bounds__(256, INV ? 3 : 1) batch_sweep_kernel("),
                      extract(sweep, "__global__ void __launch_bounds__(256) invert_kernel("),
                      extract(sweep, "__global__ void __launch_bounds__(256) residual_kernel("),
                      extract(sweep, "__global__ void mass_apply_kernel("),
