@@ -1,22 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the SMM hot path on one GB300 (replicas on N GPUs).
 
-Workload: manufactured-solution transport on a curved mesh -- [0,1]^2,
-128x128 quads of geometry order 3 moved by the seeded sinusoidal map
-(amplitude 0.05), DG p=4 (25 dofs/element), level-symmetric S8 (40
-ordinates), sigma_t = 1, scattering ratio 0.9, MMS angular source and MMS
-inflow.  16,384,000 angular unknowns per sweep.
+Workload (headline): multi-material thick/thin transport -- [0,8]^2, 256x256
+straight quads, a seeded 8x8 layout of 1x1 blocks, each thick (sigma_t = 200,
+scattering ratio 0.999) or thin (sigma_t = 0.2, ratio 0.5), a unit isotropic
+source in the lowest-index thin block, vacuum boundaries; DG p=3 (16
+dofs/element), level-symmetric S12 (84 ordinates): 88,080,384 angular
+unknowns per sweep.
 
 A step is one SMM outer iteration through the C ABI (smm_iterate with
-max_outer = 1): FP64 sweep with cached local inverses, FP64 moments and
-boundary correction, IP-SMM right-hand side, multigrid-preconditioned CG to
-1e-12, successive-difference check.  value = angular unknowns swept per second of
-whole steps (all ranks).  Inputs stay resident; L2 is flushed (256 MiB
-write) between timed steps.  Also reported: the FP32-refined and on-the-fly
-LU variants of the step, the time to a 1e-8 relative successive difference
-for the plain method (FP64 on-the-fly LU sweep, block-Jacobi PCG) and the
-chosen one, the oracle on the host cores (cpu_baseline), and an end-to-end
-number with host buffers.
+max_outer = 1): the sweep with cached local inverses applied in FP32-pair
+arithmetic and the moments formed in its epilogue, the IP-SMM right-hand
+side, multigrid-preconditioned flexible CG to 1e-12, the successive-difference
+check.  value = angular unknowns swept per second of whole steps (all ranks).
+Inputs stay resident; L2 is flushed (256 MiB write) between timed steps.
+Also reported: the sweep alone (sweep_unknowns_per_s), rooflines of its
+kernels, the time to a 1e-8 relative successive difference, the curved
+manufactured-solution workload, the FP32-refined sweep, batched uneven
+problems, the learned-guess comparison, the oracle on the host cores
+(cpu_baseline), and an end-to-end number through smm_iterate on a host array.
 """
 from __future__ import annotations
 
@@ -31,10 +33,30 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WL = dict(nx=128, m=3, p=4, sn=8, sigma_t=1.0, c=0.9, seed=0)
-WL_NAME = "mms-curved-128x128-m3-p4-S8-c0.9"
+# headline workload: thick/thin contrast (the element size of the 256x256 mesh on [0,8]^2 is 1/32; a
+# block is 32x32 elements)
+WL = dict(nx=256, blocks=8, p=3, sn=12, seed=0, length=8.0)
+WL_NAME = "thick-thin-256x256-p3-S12"
 METRIC = "sweep unknowns/s (elem*dof*angle)"
-CPU_SAMPLE_NX = 16
+# the oracle's sample: 16x16 elements of the same size and materials, 2x2 blocks of 8x8 elements
+CPU_SAMPLE = dict(nx=16, blocks=2, length=0.5)
+# the curved manufactured-solution workload of the extras
+WL2 = dict(nx=128, m=3, p=4, sn=8, sigma_t=1.0, c=0.9, seed=0)
+WL2_NAME = "mms-curved-128x128-m3-p4-S8-c0.9"
+
+
+def thick_thin_inputs(nx, blocks, p, seed, length):
+    """Mesh, sigma_t, sigma_s and the isotropic source [n_elem][n] of the
+    thick/thin workload (vacuum boundaries)."""
+    import numpy as np
+
+    import smm_workloads as W
+
+    mesh = W.structured_mesh(nx, m=1, domain=(0.0, length, 0.0, length))
+    st, ss, blk, thick = W.block_materials(nx, blocks, seed)
+    src_blk = int(np.flatnonzero(~thick)[0])
+    q = np.repeat((blk == src_blk).astype(np.float64)[:, None], (p + 1) ** 2, axis=1)
+    return mesh, st, ss, q, thick
 
 
 def workload_inputs(nx, m, p, sn_omega, sigma_t, c, seed):
@@ -59,17 +81,16 @@ def workload_inputs(nx, m, p, sn_omega, sigma_t, c, seed):
 
 def oracle_rate(seconds: float, nx: int) -> dict:
     """Time oracle outer steps G(varphi) (sweep + closures + RHS + direct IP
-    solve) on an nx*nx mesh of the bench workload's kind for ~`seconds`."""
+    solve) on the thick/thin sample for ~`seconds`."""
     import numpy as np
 
     from oracle.smm import SMMProblem
     from oracle.transport import Discretization
 
-    from oracle.quadrature import level_symmetric_2d
-    om, _ = level_symmetric_2d(WL["sn"])
-    mesh, st, ss, q, inflow = workload_inputs(nx, WL["m"], WL["p"], om, WL["sigma_t"], WL["c"], WL["seed"])
-    disc = Discretization(mesh.nodes, mesh.elem_nodes, WL["m"], WL["p"], WL["sn"], st, ss)
-    prob = SMMProblem(disc, q, inflow)
+    c = CPU_SAMPLE
+    mesh, st, ss, q, _ = thick_thin_inputs(c["nx"], c["blocks"], WL["p"], WL["seed"], c["length"])
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, 1, WL["p"], WL["sn"], st, ss)
+    prob = SMMProblem(disc, q)
     phi = np.zeros((disc.ne, disc.n))
     times = []
     t_end = time.perf_counter() + seconds
@@ -80,9 +101,15 @@ def oracle_rate(seconds: float, nx: int) -> dict:
     unknowns = disc.ne * disc.n * disc.nd
     med = statistics.median(times)
     return dict(value=unknowns / med, unit="unknowns/s", cores=1, kind="oracle", steps=len(times),
-                seconds_per_step=med,
-                sample=f"oracle outer steps (sweep+closures+RHS+direct IP solve) on a {nx}x{nx} mesh of the same "
-                       f"kind (m={WL['m']}, p={WL['p']}, S{WL['sn']}, c={WL['c']}), median of {len(times)}")
+                seconds_per_step=med, sample=cpu_sample_text(len(times)))
+
+
+def cpu_sample_text(steps=None) -> str:
+    c = CPU_SAMPLE
+    return (f"oracle outer steps (sweep + closures + RHS + direct IP solve) on a {c['nx']}x{c['nx']} piece of the "
+            f"thick/thin workload (same element size and materials, {c['blocks']}x{c['blocks']} blocks, p={WL['p']}, "
+            f"S{WL['sn']})" + (f", median of {steps}" if steps else "") +
+            f"; the full workload has {(WL['nx'] // c['nx']) ** 2}x the elements")
 
 
 def run_oracle_child(seconds: float, nx: int) -> dict:
@@ -201,27 +228,43 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
-# DRAM bytes (read + write) per launch measured by ncu for the current kernels
-# on this workload (the cg_iteration, sweep-kernel and launch-list summaries for this workload); a key
-# is dropped whenever the kernels it covers change.
-NCU_TRAFFIC: dict = {"cg_iteration": 644.0e6, "sweep_kernel": 3882.6e6, "moments": 138.6e6}
+# DRAM bytes (read + write) per launch measured by ncu for the current kernels on the headline
+# workload (profiles/); a key is dropped whenever the kernels it covers change.
+NCU_TRAFFIC: dict = {}
 
 # a timed step is outer iteration START_ITERATIONS + 1 from varphi^0 = 0
 START_ITERATIONS = 3
 
 
-def cached_sweep_bytes_per_task(p: int, word: int, angular: bool) -> float:
-    """HBM bytes of one cached-inverse task: the n x n inverse, the n outputs
-    (FP64 and, in the FP64 path, the FP32-pair copy), the angular source term
-    M q_d (an FP32 pair per node) and two inflow traces."""
+def sweep_bytes(ne: int, nd: int, p: int, angular: bool) -> float:
+    """Algorithmic HBM bytes of one sweep launch of this design (FP64 cached
+    mode): per (element, ordinate) task the n x n inverse as FP32 pairs
+    (8 n^2), the n solution pairs written (8 n), two inflow traces of p+1
+    pairs read (16 (p+1)) and, for an angular source, M q_d as pairs (8 n);
+    per element M s as pairs (8 n), the flux re-read by the moment reduction
+    (8 n nd) and six FP64 moments written (48 n)."""
     n = (p + 1) ** 2
-    return word * (n * n + 2 * n + 2 * (p + 1)) + (8 * n if angular else 0)
+    task = 8 * n * n + 8 * n + 16 * (p + 1) + (8 * n if angular else 0)
+    return ne * nd * task + ne * (8 * n + 8 * n * nd + 48 * n)
 
 
-def moments_bytes_per_elem(n: int, nd: int) -> float:
-    """HBM bytes of the moment reduction per element: psi as FP32 pairs read
-    once (8 nd n) and six FP64 moments written (48 n)."""
-    return 8 * nd * n + 48 * n
+def sweep_trace_bytes(ne: int, nd: int, p: int, m: int) -> float:
+    """The sweep's algorithmic bytes as SURVEY 8(d) counts them for a method
+    that assembles every local system from geometry (no stored operators):
+    per task four face traces of p+1 FP64 values (two inflow read, two
+    outflow written); per element varphi (8 n), the control points
+    (16 (m+1)^2) and the six moments (48 n)."""
+    n = (p + 1) ** 2
+    return ne * nd * 32 * (p + 1) + ne * (8 * n + 16 * (m + 1) ** 2 + 48 * n)
+
+
+def sweep_fp32_ops(ne: int, nd: int, p: int) -> float:
+    """FP32 instructions of the sweep's pair arithmetic per launch: a pair
+    multiply-add (Dekker product, TwoSum, error accumulation) is 12 FP32
+    instructions; a task forms n^2 of them for A^-1 b and about 2 n (p+1) for
+    its two inflow faces; the moment reduction forms 6 n nd per element."""
+    n = (p + 1) ** 2
+    return 12.0 * (ne * nd * (n * n + 2 * n * (p + 1)) + ne * 6 * n * nd)
 
 
 def mg_cg_bytes_per_iter(ne: int, n: int, nu0: int = 3) -> float:
@@ -257,6 +300,20 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
+def load_peaks() -> tuple:
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    return hbm, src
+
+
+# FP32 instruction issue of the whole GPU at the maximum SM clock: 152 SMs x 128 FP32 lanes x 2.07 GHz
+FP32_ISSUE_PEAK = 152 * 128 * 2.07e9
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -274,32 +331,28 @@ def run_ours(args) -> None:
 
     from paper_2304_07386_gb300 import build as B
     B.build()
-    om, _ = P.smm_quadrature(WL["sn"])
     t_in = time.time()
-    mesh, st, ss, q, inflow = workload_inputs(WL["nx"], WL["m"], WL["p"], om, WL["sigma_t"], WL["c"], WL["seed"])
+    nx = args.nx
+    mesh, st, ss, q, thick = thick_thin_inputs(nx, WL["blocks"], WL["p"], WL["seed"], WL["length"] * nx / WL["nx"])
     t_in = time.time() - t_in
     stream = torch.cuda.Stream()
 
-    def create(precision, solver=None, precond=None, anderson=0, moment=None, tiles=1):
+    def create(precision=P.SMM_SWEEP_FP64, anderson=0, moment=None, solver=None):
         opt = P.smm_default_options()
         opt.anderson_depth = anderson
-        opt.sweep_tiles = tiles
-        if moment is not None:
-            opt.moment_discretization = moment
         opt.sweep_precision = precision
         opt.tol_cg = 1e-12
+        if moment is not None:
+            opt.moment_discretization = moment
         if solver is not None:
             opt.sweep_solver = solver
-        if precond is not None:
-            opt.precond = precond
         if args.host_cg_loop:
             opt.cg_device_loop = 0
         t0 = time.time()
-        h = P.smm_create(mesh.nodes, mesh.elem_nodes, WL["m"], WL["p"], WL["sn"], st, ss, q, inflow=inflow,
-                         options=opt, stream=stream)
+        h = P.smm_create(mesh.nodes, mesh.elem_nodes, 1, WL["p"], WL["sn"], st, ss, q, options=opt, stream=stream)
         return h, time.time() - t0
 
-    h, t_setup = create(P.SMM_SWEEP_FP64)
+    h, t_setup = create()
     info = h.info()
     ne, n, nd = info.n_elem, info.n_dof_elem, info.n_ord
     unknowns = info.n_angular
@@ -312,10 +365,10 @@ def run_ours(args) -> None:
             dist.barrier()
 
     def step(handle, x):
-        rc, s = P.smm_iterate(handle, x, 1e-300, 1, relative=True, raise_on_error=False)
+        rc, s_ = P.smm_iterate(handle, x, 1e-300, 1, relative=True, raise_on_error=False)
         if rc not in (0, 7):
             raise P.SMMError(rc, P.load_library().smm_last_error().decode())
-        return s
+        return s_
 
     # Every warm-up and timed step is the same outer iteration: the fourth one
     # from varphi^0 = 0 (varphi^3 is restored before each step, outside the
@@ -344,191 +397,198 @@ def run_ours(args) -> None:
     value = world * unknowns / (ms * 1e-3)
 
     def mean(key):
-        return sum(s[key] for s in stats) / len(stats)
+        return sum(s_[key] for s_ in stats) / len(stats)
 
-    ms_sweep, ms_res, ms_solve = mean("ms_sweep"), mean("ms_residual"), mean("ms_solve")
+    ms_sweep, ms_src, ms_solve, ms_rhs = mean("ms_sweep"), mean("ms_residual"), mean("ms_solve"), mean("ms_rhs")
     cg_it = mean("cg_total")
-    launches = int(sum(s["n_launches"] for s in stats))
-
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    tasks = ne * nd
-    # the sweep phase also runs the source kernel: M (n^2), varphi and q (2n) read, M s written as pairs (n)
-    sweep_bytes = tasks * cached_sweep_bytes_per_task(WL["p"], 8, True) + ne * 8 * (n * n + 3 * n)
+    launches = int(sum(s_["n_launches"] for s_ in stats))
+    hbm, hbm_src = load_peaks()
     cg_bytes = mg_cg_bytes_per_iter(ne, n)
-    mom_bytes = ne * moments_bytes_per_elem(n, nd)
-    ms_mom = mean("ms_moments")
     ms_iter = ms_solve / cg_it if cg_it > 0 else 0.0
 
-    def entry(bytes_per_launch, ms_per_launch, kernel, traffic_key, launches_per_step):
-        gbs = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9 if ms_per_launch > 0 else 0.0
-        return dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=gbs / hbm,
-                    traffic=NCU_TRAFFIC.get(traffic_key), algorithmic_bytes=bytes_per_launch, ms=ms_per_launch,
-                    launches_per_step=launches_per_step, kernel=kernel, peak_note=f"{hbm_src} copy bandwidth")
+    def entry(amount, ms_per_launch, kernel, traffic_key, launches_per_step, bound="hbm", peak=hbm, unit="GB/s",
+              scale=1e9, peak_note=None):
+        ach = amount / (ms_per_launch * 1e-3) / scale if ms_per_launch > 0 else 0.0
+        return dict(bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak,
+                    traffic=NCU_TRAFFIC.get(traffic_key), algorithmic=amount, ms=ms_per_launch,
+                    launches_per_step=launches_per_step, kernel=kernel,
+                    peak_note=peak_note or f"{hbm_src} copy bandwidth")
 
+    sweep_kernel = (f"sweep_kernel<double, {WL['p']}, SOURCE, cached inverse>: the wavefront tasks, then the "
+                    "element moments after the grid-wide gate")
     rooflines = {
-        "cg_iteration": entry(cg_bytes, ms_iter, "one flexible-CG iteration: 11 kernels (operator product; "
-                              "V-cycle: first smoothing step with the CG update, 2 smoothing steps, residual, "
-                              "cluster coarse cycle, prolongation, 2 smoothing steps, last smoothing step with the "
-                              "dot products; direction), run inside one device-side graph loop",
-                              "cg_iteration", cg_it),
-        "sweep_kernel": entry(sweep_bytes, ms_sweep, "sweep_kernel<double, 4, SOURCE, cached inverse> "
-                              "(plus the per-sweep source kernel)", "sweep_kernel", 1),
-        "moments": entry(mom_bytes, ms_mom, "moments_df_kernel + beta_kernel", "moments", 1),
+        "cg_iteration": entry(cg_bytes, ms_iter, "one flexible-CG iteration: the operator product and the "
+                              "multigrid V-cycle (level-0 Chebyshev smoothing, cluster coarse cycle), run inside "
+                              "one device-side graph loop", "cg_iteration", cg_it),
+        "sweep_kernel": entry(sweep_bytes(ne, nd, WL["p"], False), ms_sweep, sweep_kernel, "sweep_kernel", 1),
+        "sweep_kernel_trace_bytes": entry(sweep_trace_bytes(ne, nd, WL["p"], 1), ms_sweep, sweep_kernel,
+                                          None, 1),
+        "sweep_kernel_fp32_issue": entry(sweep_fp32_ops(ne, nd, WL["p"]), ms_sweep, sweep_kernel, None, 1,
+                                         bound="alu", peak=FP32_ISSUE_PEAK / 1e12, unit="T FP32 instr/s",
+                                         scale=1e12, peak_note="152 SMs x 128 FP32 lanes x 2.07 GHz (one "
+                                                               "instruction per lane per clock)"),
     }
-    rooflines["cg_iteration"]["traffic_note"] = (
-        "ncu DRAM bytes of the 11 kernels, captured before the direction update's launch grid changed from a "
-        "grid-stride loop to one thread per unknown (same kernel code, each unknown read and written once either way)")
-    # dominant: the largest device time per step
-    dom = max(rooflines, key=lambda k: rooflines[k]["ms"] * rooflines[k]["launches_per_step"])
+    rooflines["sweep_kernel_trace_bytes"]["note"] = (
+        "SURVEY 8(d)'s bytes for a sweep that re-assembles each local system from geometry: this design reads "
+        "a cached inverse per task instead (far more bytes, no per-sweep factorization)")
+    # dominant: the largest device time per step among the kernels' own entries
+    dom = max(("cg_iteration", "sweep_kernel"),
+              key=lambda k: rooflines[k]["ms"] * rooflines[k]["launches_per_step"])
     roof = dict(rooflines[dom])
+    roof["traffic"] = NCU_TRAFFIC.get(dom)
 
-    # end to end through the C ABI with host buffers: H2D of varphi^k, one outer
-    # step, D2H of varphi^{k+1}, all inside the timed region
-    host = torch.zeros(ne * n, dtype=torch.float64).pin_memory()
+    # end to end through the C ABI with a host array: smm_iterate copies varphi^k in,
+    # runs one outer step and copies varphi^{k+1} back, all inside the timed call
+    host = np.zeros(ne * n)
+    start_host = phi_start.cpu().numpy()
     e2e_ms = []
     with torch.cuda.stream(stream):
         for k in range(max(2, args.steps)):
             flush.fill_(1.0)
-            host.copy_(phi_start)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            phi.copy_(host, non_blocking=True)
-            step(h, phi)
-            host.copy_(phi, non_blocking=True)
-            b.record(stream)
-            b.synchronize()
-            e2e_ms.append(a.elapsed_time(b))
-    e2e = dict(value=world * unknowns / (max_over_ranks(statistics.mean(e2e_ms), dist, "cuda") * 1e-3),
-               unit="unknowns/s",
-               h2d_bytes_per_step=8 * ne * n, d2h_bytes_per_step=8 * ne * n)
+            host[:] = start_host
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, _ = P.smm_iterate(h, host, 1e-300, 1, relative=True, raise_on_error=False)
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e = dict(value=world * unknowns / (max_over_ranks(statistics.median(e2e_ms), dist, "cuda") * 1e-3),
+               unit="unknowns/s", h2d_bytes_per_step=8 * ne * n, d2h_bytes_per_step=8 * ne * n,
+               note="smm_iterate on a host array (wall clock, median of the steps)")
 
     extra = {}
     if not args.quick:
-        def time_steps(handle, nsteps=4):
-            x = torch.zeros_like(phi)
-            out = []
-            with torch.cuda.stream(stream):
-                for _ in range(2):
-                    step(handle, x)
-                torch.cuda.synchronize()
-                for _ in range(nsteps):
-                    flush.fill_(2.0)
-                    a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    s_ = step(handle, x)
-                    b2.record(stream)
-                    b2.synchronize()
-                    out.append((a.elapsed_time(b2), s_))
-            msx = statistics.mean(t for t, _ in out)
-            return dict(value=unknowns / (msx * 1e-3), ms_per_step=msx,
-                        ms_sweep=statistics.mean(s_["ms_sweep"] for _, s_ in out),
-                        ms_residual=statistics.mean(s_["ms_residual"] for _, s_ in out),
-                        ms_solve=statistics.mean(s_["ms_solve"] for _, s_ in out))
-
-        h32, _ = create(P.SMM_SWEEP_FP32_REFINED)
-        extra["fp32_refined_step"] = time_steps(h32)
-        h32.destroy()
-        hlu, _ = create(P.SMM_SWEEP_FP64, solver=P.smm.SMM_SOLVER_LU)
-        extra["fp64_lu_step"] = time_steps(hlu)
-        hlu.destroy()
-
-        def solve(precision, solver=None, precond=None, anderson=0, moment=None):
-            hh, _ = create(precision, solver, precond, anderson, moment)
-            x = torch.zeros_like(phi)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            with torch.cuda.stream(stream):
-                rc, s_ = P.smm_iterate(hh, x, 1e-8, 200, relative=True, raise_on_error=False)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            hh.destroy()
-            return dt, s_, rc, x
-
-        tp, sp, rcp, xp = solve(P.SMM_SWEEP_FP64, P.smm.SMM_SOLVER_LU, P.smm.SMM_PRECOND_BLOCK_JACOBI)
-        tc, sc, rcc, xc = solve(P.SMM_SWEEP_FP64)
-        ta, sa, rca, xa = solve(P.SMM_SWEEP_FP64, anderson=2)
-        t3, s3, rc3, x3 = solve(P.SMM_SWEEP_FP32_REFINED)
-        # parallel block Jacobi sweep: shorter dependency chains, more outer steps
-        bj = {}
-        for tiles in (2, 4, 8):
-            hb_, _ = create(P.SMM_SWEEP_FP64, tiles=tiles)
-            levels = hb_.info().n_levels
-            xb_ = torch.zeros_like(phi)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            with torch.cuda.stream(stream):
-                rcb, sb_ = P.smm_iterate(hb_, xb_, 1e-8, 400, relative=True, raise_on_error=False)
-            torch.cuda.synchronize()
-            bj[f"tiles_{tiles}x{tiles}"] = dict(
-                seconds=time.perf_counter() - t0, status=rcb, outer=sb_["outer_iterations"], levels=levels,
-                ms_sweep_per_outer=sb_["ms_sweep"] / max(1, sb_["outer_iterations"]),
-                cg_total=sb_["cg_total"], rel_diff_vs_exact_sweep=float((xb_ - xc).abs().max() / xc.abs().max()))
-            hb_.destroy()
-        extra["time_to_1e-8_block_jacobi"] = bj
-        tg, sg, rcg, xg = solve(P.SMM_SWEEP_FP64, moment=P.smm.SMM_MOMENT_CG)
-        extra["time_to_1e-8_cg_moments"] = dict(
-            seconds=tg, outer=sg["outer_iterations"], cg_total=sg["cg_total"], status=rcg,
-            ms_solve_per_outer=sg["ms_solve"] / max(1, sg["outer_iterations"]),
-            rel_diff_vs_ip=float((xg - xc).abs().max() / xc.abs().max()),
-            method="continuous finite element moment system (Sec. 5.1), FP64 cached sweep, V-cycle-preconditioned "
-                   "CG on the continuous nodes; differs from the IP solution by the discretization error")
-        extra["time_to_1e-8"] = dict(
-            plain_s=tp, plain_outer=sp["outer_iterations"], plain_cg_total=sp["cg_total"], plain_status=rcp,
-            plain="FP64 sweep with on-the-fly LU, element-block-Jacobi PCG, zero guess",
-            chosen_s=tc, chosen_outer=sc["outer_iterations"], chosen_cg_total=sc["cg_total"], chosen_status=rcc,
-            chosen="FP64 sweep with cached local inverses, multigrid PCG, zero guess",
-            fp32_refined_s=t3, fp32_refined_outer=s3["outer_iterations"], fp32_refined_status=rc3,
-            anderson2_s=ta, anderson2_outer=sa["outer_iterations"], anderson2_cg_total=sa["cg_total"],
-            anderson2_status=rca, rel_diff_anderson2_vs_plain=float((xa - xp).abs().max() / xp.abs().max()),
-            rel_diff_chosen_vs_plain=float((xc - xp).abs().max() / xp.abs().max()),
-            rel_diff_fp32_vs_plain=float((x3 - xp).abs().max() / xp.abs().max()),
-            learned_guess="see the learned_guess entry (network trained in the run on the learned-guess workload)")
-
-    if not args.quick and args.batch > 0:
-        extra["batched_sweep"] = run_batch(args.batch, stream)
-    if not args.quick and args.learned > 0:
-        extra["learned_guess"] = run_learned(args.learned, stream)
-    if not args.quick:
-        extra["thick_thin"] = run_thick_thin(stream)
+        extra.update(run_extras(args, P, torch, stream, create, step, phi, flush, ms_sweep))
+    h.destroy()
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = run_oracle_child(args.cpu_seconds, CPU_SAMPLE_NX)
+        cpu = run_oracle_child(args.cpu_seconds, CPU_SAMPLE["nx"])
         cpu["cpu"] = cpu_model()
-        cpu_all = run_oracle_all_cores(args.cpu_seconds, CPU_SAMPLE_NX)
+        cpu_all = run_oracle_all_cores(args.cpu_seconds, CPU_SAMPLE["nx"])
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (FP32 copies of the multigrid smoother blocks)", "data": "synthetic",
-            "config": {"workload": WL_NAME, "n_elem": ne, "p": WL["p"], "geom_order": WL["m"], "sn": WL["sn"],
-                       "n_ord": nd, "angular_unknowns": unknowns, "parallelism": f"replicas x{world}",
-                       "l2": "flushed between timed steps (256 MiB write)", "sweep": "fp64, cached local inverses",
+            "vs_baseline": None,
+            "dtype": "f64 accuracy: sweep products and right-hand side in FP32 pairs (f32x2), moments, CG and "
+                     "checks in f64, multigrid smoother blocks in f32",
+            "data": "synthetic",
+            "config": {"workload": WL_NAME, "n_elem": ne, "p": WL["p"], "geom_order": 1, "sn": WL["sn"],
+                       "n_ord": nd, "angular_unknowns": unknowns, "thick_blocks": int(thick.sum()),
+                       "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MiB write)",
+                       "sweep": "cached local inverses applied as FP32-pair products; moments in the sweep kernel",
                        "step_state": f"outer iteration {START_ITERATIONS + 1} from varphi^0 = 0, restored before "
                                      "every step",
-                       "moment_solve": "flexible CG, multigrid V-cycle with degree-3 Chebyshev level-0 smoothing", "cg_tol": 1e-12,
+                       "moment_solve": "flexible CG, multigrid V-cycle with degree-3 Chebyshev level-0 smoothing",
+                       "cg_tol": 1e-12,
                        "cg_loop": "host-checked chunks" if args.host_cg_loop else "one device-side graph loop"},
             "roofline": roof, "roofline_all": rooflines, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
             "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
-            "phases_ms": dict(residual=ms_res, sweep=ms_sweep, moments=mean("ms_moments"), rhs=mean("ms_rhs"),
-                              solve=ms_solve, cg_iters=cg_it),
-            "sweep_only": dict(value=unknowns / ((ms_sweep + ms_res) * 1e-3), unit="unknowns/s",
-                               note="sweep kernel (plus the per-sweep source kernel)"),
+            "phases_ms": dict(source=ms_src, sweep_with_moments=ms_sweep, rhs=ms_rhs, solve=ms_solve,
+                              cg_iters=cg_it),
+            "sweep_unknowns_per_s": dict(value=unknowns / (ms_sweep * 1e-3), unit="unknowns/s",
+                                         ms=ms_sweep, note="SURVEY 8(d)'s metric: one sweep including the fused "
+                                                           "moments (the sweep kernel alone)"),
             "setup_s": t_setup, "inputs_s": t_in,
         }
         line.update(extra)
         print(json.dumps(line), flush=True)
-    h.destroy()
     if dist:
         dist.destroy_process_group()
+
+
+def time_steps(P, torch, stream, handle, x, flush, step, nsteps=4):
+    """Mean time of nsteps outer steps from the state after two steps from zero."""
+    out = []
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            step(handle, x)
+        torch.cuda.synchronize()
+        for _ in range(nsteps):
+            flush.fill_(2.0)
+            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s_ = step(handle, x)
+            b2.record(stream)
+            b2.synchronize()
+            out.append((a.elapsed_time(b2), s_))
+    ms = statistics.mean(t for t, _ in out)
+    return dict(ms_per_step=ms, ms_sweep=statistics.mean(s_["ms_sweep"] for _, s_ in out),
+                ms_residual_or_source=statistics.mean(s_["ms_residual"] for _, s_ in out),
+                ms_solve=statistics.mean(s_["ms_solve"] for _, s_ in out))
+
+
+def run_extras(args, P, torch, stream, create, step, phi, flush, ms_sweep_default) -> dict:
+    import numpy as np
+
+    extra = {}
+    info = None
+
+    def solve(**kw):
+        hh, _ = create(**kw)
+        x = torch.zeros_like(phi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            rc, s_ = P.smm_iterate(hh, x, 1e-8, 300, relative=True, raise_on_error=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        hh.destroy()
+        return dict(seconds=dt, status=rc, outer=s_["outer_iterations"], cg_total=s_["cg_total"],
+                    cg_per_outer=s_["cg_total"] / max(1, s_["outer_iterations"]),
+                    ms_sweep_per_outer=s_["ms_sweep"] / max(1, s_["outer_iterations"])), x
+
+    d0, x0 = solve()
+    da, xa = solve(anderson=2)
+    da["rel_diff_vs_default"] = float((xa - x0).abs().max() / x0.abs().max())
+    dc, xc = solve(moment=P.smm.SMM_MOMENT_CG)
+    dc["rel_diff_vs_ip"] = float((xc - x0).abs().max() / x0.abs().max())
+    dc["method"] = ("continuous finite element moment system (Sec. 5.1); differs from the IP solution by the "
+                    "discretization error")
+    extra["time_to_1e-8"] = dict(workload=WL_NAME, default=d0, anderson2=da, cg_moment_system=dc,
+                                 note="from varphi^0 = 0 to a 1e-8 relative successive difference; wall time "
+                                      "of smm_iterate, setup excluded")
+    # the FP32-refined sweep (FP64 transport residual + FP32 correction sweep) on the same workload
+    h32, _ = create(precision=P.SMM_SWEEP_FP32_REFINED)
+    extra["fp32_refined_step"] = time_steps(P, torch, stream, h32, torch.zeros_like(phi), flush, step)
+    h32.destroy()
+    if args.cfg2:
+        extra["mms_curved"] = run_mms_curved(P, torch, stream, flush, step)
+    if args.batch > 0:
+        extra["batched_sweep"] = run_batch(args.batch, stream)
+    if args.learned > 0:
+        extra["learned_guess"] = run_learned(args.learned, stream)
+    return extra
+
+
+def run_mms_curved(P, torch, stream, flush, step) -> dict:
+    """The curved manufactured-solution workload (128x128 quads of geometry
+    order 3, p = 4, S8, c = 0.9, MMS source and inflow): one outer step and
+    the sweep alone."""
+    om, _ = P.smm_quadrature(WL2["sn"])
+    mesh, st, ss, q, inflow = workload_inputs(WL2["nx"], WL2["m"], WL2["p"], om, WL2["sigma_t"], WL2["c"],
+                                              WL2["seed"])
+    opt = P.smm_default_options()
+    opt.tol_cg = 1e-12
+    h = P.smm_create(mesh.nodes, mesh.elem_nodes, WL2["m"], WL2["p"], WL2["sn"], st, ss, q, inflow=inflow,
+                     options=opt, stream=stream)
+    info = h.info()
+    x = torch.zeros(info.n_elem * info.n_dof_elem, dtype=torch.float64, device="cuda")
+    r = time_steps(P, torch, stream, h, x, flush, step)
+    r.update(workload=WL2_NAME, angular_unknowns=int(info.n_angular),
+             value=info.n_angular / (r["ms_per_step"] * 1e-3),
+             sweep_unknowns_per_s=info.n_angular / (r["ms_sweep"] * 1e-3), unit="unknowns/s")
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        rc, s_ = P.smm_iterate(h, x, 1e-8, 300, relative=True, raise_on_error=False)
+    torch.cuda.synchronize()
+    r["time_to_1e-8"] = dict(seconds=time.perf_counter() - t0, status=rc, outer=s_["outer_iterations"],
+                             cg_total=s_["cg_total"])
+    h.destroy()
+    return r
 
 
 def batch_problem(seed: int):
@@ -552,7 +612,8 @@ def batch_problem(seed: int):
 
 def run_batch(nprob: int, stream) -> dict:
     """Time one batched sweep of nprob uneven problems against the same
-    problems swept one at a time (FP32-refined sweeps, cached inverses)."""
+    problems swept one at a time (the default sweep: cached inverses applied
+    in FP32-pair arithmetic, moments in the sweep kernel)."""
     import torch
 
     import paper_2304_07386_gb300 as P
@@ -561,7 +622,7 @@ def run_batch(nprob: int, stream) -> dict:
     for i in range(nprob):
         mesh, p, sn, st, ss, q = batch_problem(i)
         opt = P.smm_default_options()
-        opt.sweep_precision = P.SMM_SWEEP_FP32_REFINED
+        opt.precond = P.smm.SMM_PRECOND_BLOCK_JACOBI  # only sweeps are timed: skip the multigrid setup
         hs.append(P.smm_create(mesh.nodes, mesh.elem_nodes, 1, p, sn, st, ss, q, options=opt, stream=stream))
         unknowns += hs[-1].info().n_angular
     b = P.smm.smm_batch_create(hs)
@@ -585,18 +646,23 @@ def run_batch(nprob: int, stream) -> dict:
         h.destroy()
     return dict(problems=nprob, angular_unknowns=unknowns, batched_s=tb, one_at_a_time_s=ts,
                 batched_value=unknowns / tb, one_at_a_time_value=unknowns / ts, unit="unknowns/s",
-                schedule=sched, note="wall time of smm_batch_sweep vs consecutive smm_sweep calls (each includes "
-                                     "the FP64 residual, the FP32 correction sweep, moments and one sync)")
+                schedule=sched, note="wall time of one smm_batch_sweep launch vs consecutive smm_sweep calls (each "
+                                     "with its source kernel, sweep kernel and one host sync); best of 3")
 
 
-def run_learned(nx: int, stream, n_train: int = 128, n_test: int = 8, p: int = 2, sn: int = 8) -> dict:
+def run_learned(nx: int, stream, n_train: int = 192, n_test: int = 16, p: int = 2, sn: int = 8) -> dict:
     """Learned-guess workload (p=2, S8, log-normal sigma_t / sigma_s fields,
     piecewise-constant source maps, on an nx*nx grid of quads): train the
     library's network on n_train converged solutions the method produces,
-    then time held-out solves to a 1e-8 relative difference: the plain GPU
-    method (FP64 on-the-fly LU sweep, block-Jacobi PCG, zero guess), the
-    chosen method with a zero guess, and the chosen method started from the
-    network's proposal (guess_check on)."""
+    then solve n_test held-out problems to a 1e-8 relative difference.
+
+    plain: each problem on its own with the library's default FP64-accuracy
+    path (cached inverses, multigrid CG) from the zero guess.  chosen: all
+    problems in one batched iteration (one sweep launch per outer step for
+    all of them), each started from the network's proposal (guess_check on)
+    with Anderson acceleration of depth 2.  The ablations switch one
+    ingredient at a time.  Times are wall times of the solves (network
+    inference included, handle setup excluded)."""
     import numpy as np
     import torch
 
@@ -606,129 +672,119 @@ def run_learned(nx: int, stream, n_train: int = 128, n_test: int = 8, p: int = 2
 
     n = (p + 1) ** 2
 
-    def make(seed, plain=False, check=False, anderson=0):
+    def make(seed, check=False, anderson=0):
         mesh, st, ss, qe = W.learned_guess_problem(nx, seed)
         opt = P.smm_default_options()
         opt.tol_cg = 1e-12
         opt.guess_check = int(check)
         opt.anderson_depth = anderson
-        if plain:
-            opt.sweep_solver = P.smm.SMM_SOLVER_LU
-            opt.precond = P.smm.SMM_PRECOND_BLOCK_JACOBI
         h = P.smm_create(mesh.nodes, mesh.elem_nodes, 1, p, sn, st, ss, np.repeat(qe[:, None], n, axis=1),
                          options=opt, stream=stream)
         return h, (st, ss, qe)
 
-    def solve(h, tol, phi0=None):
-        x = torch.zeros(nx * nx * n, dtype=torch.float64, device="cuda")
-        if phi0 is not None:
-            x.copy_(torch.as_tensor(phi0, device="cuda"))
+    def zeros():
+        return torch.zeros(nx * nx * n, dtype=torch.float64, device="cuda")
+
+    def timed(fn):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            rc, s = P.smm_iterate(h, x, tol, 200, relative=True, raise_on_error=False)
+            r = fn()
         torch.cuda.synchronize()
-        return time.perf_counter() - t0, s, x
+        return time.perf_counter() - t0, r
 
     t_gen = time.perf_counter()
     X, Y = [], []
     for seed in range(n_train):
         h, (st, ss, qe) = make(seed)
-        _, _, x = solve(h, 1e-10)
-        mom = torch.zeros(6 * nx * nx * n, dtype=torch.float64, device="cuda")
-        P.smm_moments(h, mom)
+        x = zeros()
+        with torch.cuda.stream(stream):
+            P.smm_iterate(h, x, 1e-10, 300, relative=True, raise_on_error=False)
         h.destroy()
         X.append(G.features(st, ss, qe, nx))
-        Y.append(G.targets(x.cpu().numpy(), mom.cpu().numpy(), nx, n))
+        Y.append(G.targets(x.cpu().numpy(), nx, n))
     t_gen = time.perf_counter() - t_gen
     X, Y = np.stack(X), np.stack(Y)
     xn, yn = G.Normalizer(X), G.Normalizer(Y)
-    net = P.smm.Guess(nx, nx, 4 * n, 16, seed=0, stream=stream)
+    net = P.smm.Guess(nx, nx, n, 16, seed=0, stream=stream)
     t_train = time.perf_counter()
     with torch.cuda.stream(stream):
         losses = G.train(net, torch.as_tensor(xn.fwd(X), device="cuda"), torch.as_tensor(yn.fwd(Y), device="cuda"),
                          steps=1500, batch=16, lr=3e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t_train
-    rows = []
-    for seed in range(100_000, 100_000 + n_test):
-        hp, _ = make(seed, plain=True)
-        tp, sp, xp = solve(hp, 1e-8)
-        hp.destroy()
-        hz, (st, ss, qe) = make(seed)
-        tz, sz, xz = solve(hz, 1e-8)
-        hz.destroy()
-        with torch.cuda.stream(stream):
+
+    seeds = list(range(100_000, 100_000 + n_test))
+
+    def proposals(infos):
+        out = []
+        for st, ss, qe in infos:
             xg = torch.as_tensor(xn.fwd(G.features(st, ss, qe, nx)[None]), device="cuda")
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            phi0 = G.predict_phi(net, xg, yn, nx, n)
-            t_inf = time.perf_counter() - t0
-        hg, _ = make(seed, check=True)
-        tg, sg, xgs = solve(hg, 1e-8, phi0)
-        hg.destroy()
-        ha, _ = make(seed, check=True, anderson=2)
-        ta, sa, xa = solve(ha, 1e-8, phi0)
-        ha.destroy()
-        rows.append(dict(plain_s=tp, plain_outer=sp["outer_iterations"], zero_s=tz, zero_outer=sz["outer_iterations"],
-                         guess_s=tg + t_inf, guess_outer=sg["outer_iterations"], rejected=sg["guess_rejected"],
-                         guess_anderson2_s=ta + t_inf, guess_anderson2_outer=sa["outer_iterations"],
-                         rel_diff_guess_vs_plain=float((xgs - xp).abs().max() / xp.abs().max())))
-    mean = lambda k: float(np.mean([r[k] for r in rows]))
+            out.append(torch.as_tensor(G.predict_phi(net, xg, yn, nx, n), device="cuda"))
+        return out
+
+    def singles(check, anderson, learned):
+        hs = [make(sd, check=check, anderson=anderson) for sd in seeds]
+        xs = [zeros() for _ in seeds]
+
+        def run():
+            if learned:
+                for x, g in zip(xs, proposals([i for _, i in hs])):
+                    x.copy_(g)
+            st_ = []
+            for (h, _), x in zip(hs, xs):
+                rc, s_ = P.smm_iterate(h, x, 1e-8, 300, relative=True, raise_on_error=False)
+                st_.append((rc, s_))
+            return st_
+        dt, st_ = timed(run)
+        for h, _ in hs:
+            h.destroy()
+        return dt, st_, xs
+
+    def batched(check, anderson, learned):
+        hs = [make(sd, check=check, anderson=anderson) for sd in seeds]
+        b = P.smm.smm_batch_create([h for h, _ in hs])
+        xs = [zeros() for _ in seeds]
+
+        def run():
+            if learned:
+                for x, g in zip(xs, proposals([i for _, i in hs])):
+                    x.copy_(g)
+            return P.smm.smm_batch_iterate(b, xs, 1e-8, 300, relative=True)
+        dt, st_ = timed(run)
+        b.destroy()
+        for h, _ in hs:
+            h.destroy()
+        return dt, [(0, s_) for s_ in st_], xs
+
+    rows = {}
+    ref = None
+    for name, fn, kw in (("plain", singles, dict(check=False, anderson=0, learned=False)),
+                         ("batched", batched, dict(check=False, anderson=0, learned=False)),
+                         ("learned_guess", singles, dict(check=True, anderson=0, learned=True)),
+                         ("anderson2", singles, dict(check=False, anderson=2, learned=False)),
+                         ("chosen", batched, dict(check=True, anderson=2, learned=True))):
+        dt, st_, xs = fn(**kw)
+        if ref is None:
+            ref = xs
+        rows[name] = dict(seconds=dt, mean_outer=float(np.mean([s_["outer_iterations"] for _, s_ in st_])),
+                          rejected=int(sum(s_["guess_rejected"] for _, s_ in st_)),
+                          all_converged=all(rc == 0 for rc, _ in st_),
+                          max_rel_diff_vs_plain=max(float((x - r).abs().max() / r.abs().max())
+                                                    for x, r in zip(xs, ref)))
     return dict(grid=f"{nx}x{nx}", p=p, sn=sn, train_problems=n_train, test_problems=n_test,
                 params=net.n_params, data_gen_s=t_gen, train_s=t_train, final_loss=float(np.mean(losses[-50:])),
-                initial_loss=float(np.mean(losses[:10])),
-                mean_plain_s=mean("plain_s"), mean_zero_guess_s=mean("zero_s"), mean_learned_s=mean("guess_s"),
-                mean_learned_anderson2_s=mean("guess_anderson2_s"),
-                mean_outer_plain=mean("plain_outer"), mean_outer_zero=mean("zero_outer"),
-                mean_outer_learned=mean("guess_outer"), mean_outer_learned_anderson2=mean("guess_anderson2_outer"),
-                rejected=int(sum(r["rejected"] for r in rows)),
-                max_rel_diff_vs_plain=max(r["rel_diff_guess_vs_plain"] for r in rows),
-                note="times to a 1e-8 relative successive difference, inference included; the plain method is the "
-                     "FP64 on-the-fly LU sweep with block-Jacobi PCG and a zero guess")
-
-
-def run_thick_thin(stream, nx: int = 256, blocks: int = 8, p: int = 3, sn: int = 12) -> dict:
-    """Multi-material thick/thin workload: [0,8]^2, nx x nx straight quads, a
-    seeded blocks x blocks layout of thick (sigma_t = 200, c = 0.999) and thin
-    (sigma_t = 0.2, c = 0.5) cells, unit isotropic source in the lowest-index
-    thin block, vacuum, p = 3, S12.  Time to a 1e-8 relative successive
-    difference from zero, outer iterations and CG iterations per outer step,
-    for the default method and with Anderson acceleration of depth 2."""
-    import numpy as np
-    import torch
-
-    import paper_2304_07386_gb300 as P
-    import smm_workloads as W
-
-    mesh = W.structured_mesh(nx, m=1, domain=(0.0, 8.0, 0.0, 8.0))
-    st, ss, blk, thick = W.block_materials(nx, blocks, 0)
-    src_blk = int(np.flatnonzero(~thick)[0])
-    n = (p + 1) ** 2
-    q = np.repeat((blk == src_blk).astype(np.float64)[:, None], n, axis=1)
-    out = dict(grid=f"{nx}x{nx}", p=p, sn=sn, thick_blocks=int(thick.sum()), blocks=blocks * blocks)
-    for name, depth in (("default", 0), ("anderson2", 2)):
-        opt = P.smm_default_options()
-        opt.anderson_depth = depth
-        h = P.smm_create(mesh.nodes, mesh.elem_nodes, 1, p, sn, st, ss, q, options=opt, stream=stream)
-        info = h.info()
-        x = torch.zeros(info.n_elem * info.n_dof_elem, dtype=torch.float64, device="cuda")
-        with torch.cuda.stream(stream):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rc, s = P.smm_iterate(h, x, 1e-8, 200, relative=True, raise_on_error=False)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-        out[name] = dict(seconds=dt, status=rc, outer=s["outer_iterations"],
-                         cg_per_outer=s["cg_total"] / max(1, s["outer_iterations"]), cg_max=s["cg_max"],
-                         angular_unknowns=int(info.n_angular))
-        h.destroy()
-    return out
+                initial_loss=float(np.mean(losses[:10])), **rows,
+                speedup_chosen_vs_plain=rows["plain"]["seconds"] / rows["chosen"]["seconds"],
+                note="wall time to a 1e-8 relative successive difference for all held-out problems; plain = the "
+                     "default FP64-accuracy method one problem at a time from zero; chosen = learned guess "
+                     "(guess_check) + one batched sweep launch per outer step + Anderson depth 2")
 
 
 def run_reference(args) -> None:
     """The oracle arm: the CPU oracle on the host cores, K timed steps of a
-    bounded sample (one outer step each), after W warm-up steps."""
+    bounded sample of the headline workload (one outer step each), after W
+    warm-up steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -736,15 +792,13 @@ def run_reference(args) -> None:
         os.environ[k] = "1"
     import numpy as np
 
-    from oracle.quadrature import level_symmetric_2d
     from oracle.smm import SMMProblem
     from oracle.transport import Discretization
 
-    om, _ = level_symmetric_2d(WL["sn"])
-    nx = CPU_SAMPLE_NX
-    mesh, st, ss, q, inflow = workload_inputs(nx, WL["m"], WL["p"], om, WL["sigma_t"], WL["c"], WL["seed"])
-    disc = Discretization(mesh.nodes, mesh.elem_nodes, WL["m"], WL["p"], WL["sn"], st, ss)
-    prob = SMMProblem(disc, q, inflow)
+    c = CPU_SAMPLE
+    mesh, st, ss, q, _ = thick_thin_inputs(c["nx"], c["blocks"], WL["p"], WL["seed"], c["length"])
+    disc = Discretization(mesh.nodes, mesh.elem_nodes, 1, WL["p"], WL["sn"], st, ss)
+    prob = SMMProblem(disc, q)
     phi = np.zeros((disc.ne, disc.n))
     for _ in range(args.warmup):
         phi, _ = prob.G(phi)
@@ -756,16 +810,13 @@ def run_reference(args) -> None:
     ms = 1e3 * statistics.mean(t)
     unknowns = disc.ne * disc.n * disc.nd
     value = unknowns / (ms * 1e-3)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"oracle outer steps on a {nx}x{nx} mesh of the bench workload's kind (m={WL['m']}, p={WL['p']}, "
-              f"S{WL['sn']}); the full {WL['nx']}x{WL['nx']} workload is {(WL['nx'] // nx) ** 2}x larger")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WL_NAME, "sample_mesh": f"{nx}x{nx}", "angular_unknowns": unknowns},
+        "config": {"workload": WL_NAME, "sample_mesh": f"{c['nx']}x{c['nx']}", "angular_unknowns": unknowns},
         "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                         "sample": sample, "cpu": cpu_model()},
+                         "sample": cpu_sample_text(), "cpu": cpu_model()},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -776,17 +827,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--quick", action="store_true", help="skip the FP64 and time-to-solution extras")
+    ap.add_argument("--quick", action="store_true", help="the headline line only (no extras)")
     ap.add_argument("--host-cg-loop", action="store_true",
                     help="launch the CG iterations from the host in chunks instead of one device-side loop graph "
                          "(profiling runs: ncu does not see kernels inside conditional graph nodes)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--nx", type=int, default=WL["nx"], help="mesh size override (profiling runs)")
+    ap.add_argument("--no-cfg2", dest="cfg2", action="store_false", help="skip the curved MMS workload")
     ap.add_argument("--batch", type=int, default=24, help="problems in the batched-sweep measurement (0: skip)")
-    ap.add_argument("--learned", type=int, default=32, help="element grid of the learned-guess measurement (0: skip)")
+    ap.add_argument("--learned", type=int, default=64, help="element grid of the learned-guess measurement (0: skip)")
     args = ap.parse_args()
-    WL["nx"] = args.nx
     if args.impl == "reference":
         run_reference(args)
     else:

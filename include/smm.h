@@ -344,7 +344,8 @@ smm_status smm_batch_schedule(smm_batch b, int32_t* grid, int32_t* block, double
 smm_status smm_batch_sweep(smm_batch b, const double* const* phi_dev);
 
 /* smm_iterate for every problem, sharing the batched sweep: each outer step
- * runs one batched sweep, then each unconverged problem's moment solve.
+ * runs one batched sweep, then each unconverged problem's moment solve
+ * (with each handle's anderson_depth, guess_check and resume_history).
  * phi_dev: host array of n device pointers (guesses in, iterates out);
  * stats: NULL or n entries.  Errors as smm_iterate. */
 smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t max_outer, double* const* phi_dev,

@@ -1539,6 +1539,13 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
             q.cg_max = std::max(q.cg_max, it);
             q.last_diff = h->h_scal[0];
             q.last_rel_diff = h->h_scal[1] > 0 ? h->h_scal[0] / h->h_scal[1] : h->h_scal[0];
+            if (k == 1 && h->opt.guess_check && h->h_scal[0] > h->h_scal[1]) {
+                // as in smm_iterate: the guess is farther from its image than zero is; restart from zero
+                SMM_CUDA(cudaMemsetAsync(phi_dev[i], 0, nphi * sizeof(double), h->stream));
+                q.guess_rejected = 1;
+                h->aa_k = 0;
+                continue;
+            }
             const double crit = relative ? q.last_rel_diff : q.last_diff;
             if (crit < tol) {
                 done[i] = 1;

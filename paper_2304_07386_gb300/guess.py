@@ -2,7 +2,7 @@
 training / inference loop around the library's network (smm_guess_*).
 
 The network maps per-element fields (log sigma_t, scattering ratio, source)
-to the nodal scalar flux and correction tensor of the converged SMM solution.
+to the nodal scalar flux of the converged SMM solution.
 All network arithmetic runs in libsmm.so; this module only arranges arrays
 (element grid <-> channels) and normalizes them.  Its proposal enters
 smm_iterate as the initial varphi with options.guess_check set, so a
@@ -20,11 +20,10 @@ def features(sigma_t, sigma_s, q_elem, nx):
     return f.reshape(3, nx, nx)
 
 
-def targets(phi, moments, nx, n):
-    """[4 n][nx][nx]: nodal varphi and Txx, Txy, Tyy of each element as channels."""
+def targets(phi, nx, n):
+    """[n][nx][nx]: the nodal varphi of each element as channels."""
     ne = nx * nx
-    t = np.concatenate([np.asarray(phi).reshape(ne, n).T, np.asarray(moments).reshape(6, ne, n)[3:].transpose(0, 2, 1).reshape(3 * n, ne)])
-    return t.reshape(4 * n, nx, nx).astype(np.float32)
+    return np.asarray(phi).reshape(ne, n).T.reshape(n, nx, nx).astype(np.float32)
 
 
 class Normalizer:
@@ -64,7 +63,7 @@ def predict_phi(net, x_norm, ynorm: Normalizer, nx, n):
     """Nodal varphi [nx*nx*n] (float64) proposed by the network for one input."""
     import torch
 
-    out = torch.zeros((1,) + (4 * n, nx, nx), dtype=torch.float32, device=x_norm.device)
+    out = torch.zeros((1, n, nx, nx), dtype=torch.float32, device=x_norm.device)
     net.forward(x_norm.reshape(1, 3, nx, nx).contiguous(), out)
     y = ynorm.inv(out.cpu().numpy())[0]
     phi = y[:n].reshape(n, nx * nx).T

@@ -106,10 +106,10 @@ def test_trained_guess_saves_outer_iterations_on_held_out_problems():
     for seed in range(96):
         phi, mom, _, (st, ss, qe) = _solve(P, nx, seed, tol=1e-10)
         X.append(G.features(st, ss, qe, nx))
-        Y.append(G.targets(phi, mom, nx, n))
+        Y.append(G.targets(phi, nx, n))
     X, Y = np.stack(X), np.stack(Y)
     xn, yn = G.Normalizer(X), G.Normalizer(Y)
-    net = P.smm.Guess(nx, nx, 4 * n, 16, seed=0)
+    net = P.smm.Guess(nx, nx, n, 16, seed=0)
     Xd = torch.as_tensor(xn.fwd(X), device="cuda")
     Yd = torch.as_tensor(yn.fwd(Y), device="cuda")
     losses = G.train(net, Xd, Yd, steps=800, batch=16, lr=3e-3)
