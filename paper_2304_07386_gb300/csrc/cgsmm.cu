@@ -243,9 +243,10 @@ int cgc_mg(const CGCPlan& c, const MGPlan& m, const double* r, double* z, const 
     na.out = c.res;
     cgc_node_kernel<NODE_RESIDUAL><<<nbg, kTPB, 0, s>>>(na);
     cgc_corner_kernel<<<blocks(c.ne * 4), kTPB, 0, s>>>(c.ne, c.n, c.gid, m.w4, c.minv, c.res, c.cres, ctl);
-    const float* xv = launch_coarse_cycle(m, c.cres, ctl, s);
+    int lc = 0;
+    const float* xv = launch_coarse_cycle(m, c.cres, ctl, s, &lc);
     cgc_prolong_kernel<<<nbg, kTPB, 0, s>>>(c.nglob, c.n, c.gown, m.vid, m.w4, xv, xa, ctl);
-    launches += 5;
+    launches += 4 + lc;
     for (int k = 0; k < c.nu; ++k) {
         elem_apply_n(c, xa, ctl, s);
         na.xin = xa;

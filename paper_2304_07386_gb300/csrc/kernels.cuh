@@ -236,8 +236,11 @@ struct MGPlan {
 int mg_coarse_cluster_size();
 // the coarse part of the V-cycle (vertex level from element-corner residual
 // sums cres [ne][4], aggregation levels, coarsest solve) as one cluster
-// launch; returns the vertex-level correction (device pointer, nvert floats)
-const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* ctl, cudaStream_t s);
+// launch, or, for a large vertex level, that level's stages as grid kernels
+// around a cluster launch for the levels below; returns the vertex-level
+// correction (device pointer, nvert floats); *launches = kernels launched
+const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* ctl, cudaStream_t s, int* launches);
+bool mg_split_vertex_level(const MGPlan& m);
 // z = V-cycle(r); returns the number of kernel launches; the kernels return at once when ctl[0]
 // (CG finished) is set
 int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s);

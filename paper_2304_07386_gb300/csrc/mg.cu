@@ -343,6 +343,8 @@ constexpr int kCoarseThreads = 512;   // 128 registers per thread: a row's loads
 
 struct CoarseArgs {
     int nvert, nlev;
+    int first;                                  // 1: the whole coarse cycle; 2: the vertex level runs as
+                                                // grid kernels around the launch, which starts with b_2 = R r_1
     int cap;                                    // floats of dynamic shared memory (staged vectors)
     const float* cres;                          // [ne][4] corner sums of the level-0 residual
     int vw; const int* vinc;                    // vertex incidences, k-major ELL with -1 padding
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
     // covers 32 consecutive rows (coalesced ELL loads)
     const int tid = (((int)threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x) * 32 + ((int)threadIdx.x & 31);
     // vertex-level right-hand side: sum of the corner sums of the elements at each vertex
-    {
+    if (a.first == 1) {
         float* b1 = a.lv[1].b;
         for (int v = tid; v < a.nvert; v += T) {
             float s = 0.0f;
@@ -456,8 +458,8 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
             }
             b1[v] = s;
         }
+        cl.sync();
     }
-    cl.sync();
     // Each stage below reads one vector written in the stage before (by any
     // CTA): it is first copied into every CTA's shared memory (when it fits)
     // so that the row gathers are shared-memory loads.
@@ -466,14 +468,16 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
     // out of one pass over b.
     for (int l = 1; l < a.nlev; ++l) {
         const MGLevelDev& L = a.lv[l];
-        const bool sb = stage_x(L.b, L.n, xs, a.cap);
-        for (int i = tid; i < L.n; i += T) {
-            const float bi = sb ? xs[i] : __ldcg(L.b + i);
-            const float si = ell_apply(sb, L.aw, L.n, L.Aci, L.Asv, L.b, xs, i);
-            L.r[i] = bi - si;
-            L.x[i] = L.omega * L.dinv[i] * bi;
+        if (l >= a.first) {
+            const bool sb = stage_x(L.b, L.n, xs, a.cap);
+            for (int i = tid; i < L.n; i += T) {
+                const float bi = sb ? xs[i] : __ldcg(L.b + i);
+                const float si = ell_apply(sb, L.aw, L.n, L.Aci, L.Asv, L.b, xs, i);
+                L.r[i] = bi - si;
+                L.x[i] = L.omega * L.dinv[i] * bi;
+            }
+            cl.sync();
         }
-        cl.sync();
         const MGLevelDev& Lc = a.lv[l + 1];
         const bool sr = stage_x(L.r, L.n, xs, a.cap);
         for (int i = tid; i < Lc.n; i += T) Lc.b[i] = ell_apply(sr, L.rw, Lc.n, L.Rci, L.Rv, L.r, xs, i);
@@ -507,7 +511,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
     cl.sync();
     // up: x += P x_{l+1} ; t = x + omega dinv (b - A x)
     const float* coarse_out = a.lv[a.nlev].x;
-    for (int l = a.nlev - 1; l >= 1; --l) {
+    for (int l = a.nlev - 1; l >= a.first; --l) {
         const MGLevelDev& L = a.lv[l];
         const bool sp = stage_x(coarse_out, a.lv[l + 1].n, xs, a.cap);
         for (int i = tid; i < L.n; i += T) {
@@ -524,6 +528,54 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cycle_kernel(CoarseArgs
         cl.sync();
         coarse_out = L.t;
     }
+}
+
+// The vertex level's stages on the whole GPU (a thread per vertex), for vertex
+// levels too large for the cluster's shared memory; the same arithmetic as the
+// cluster's stages.  b_1 = the corner sums of the elements at each vertex:
+__global__ void vertex_rhs_kernel(int nvert, int vw, const int* __restrict__ vinc, const float* __restrict__ cres,
+                                  float* __restrict__ b1, const int* ctl) {
+    if (cg_finished(ctl)) return;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvert) return;
+    float s = 0.0f;
+    for (int k0 = 0; k0 < vw; k0 += 8) {
+        int c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = k0 + k < vw ? vinc[(size_t)(k0 + k) * nvert + v] : -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += c[k] >= 0 ? __ldcg(cres + c[k]) : 0.0f;
+    }
+    b1[v] = s;
+}
+
+// x_1 = omega dinv b_1 ; r_1 = b_1 - A_1 x_1 (as b_1 - As_1 b_1)
+__global__ void vertex_down_kernel(MGLevelDev L, const int* ctl) {
+    if (cg_finished(ctl)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n) return;
+    const float bi = __ldcg(L.b + i);
+    const float si = ell_row<false>(L.aw, L.n, L.Aci, L.Asv, L.b, i);
+    L.r[i] = bi - si;
+    L.x[i] = L.omega * L.dinv[i] * bi;
+}
+
+// x_1 += P_1 x_2 (the coarse correction from level 2)
+__global__ void vertex_up_kernel(MGLevelDev L, const float* __restrict__ x2, const int* ctl) {
+    if (cg_finished(ctl)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n) return;
+    L.x[i] = __ldcg(L.x + i) + ell_row<false>(L.pw, L.n, L.Pci, L.Pv, x2, i);
+}
+
+// t_1 = x_1 + omega dinv (b_1 - A_1 x_1)
+__global__ void vertex_post_kernel(MGLevelDev L, const int* ctl) {
+    if (cg_finished(ctl)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n) return;
+    const float xi = __ldcg(L.x + i), bi = __ldcg(L.b + i), di = L.dinv[i];
+    const float si = ell_row<false>(L.aw, L.n, L.Aci, L.Av, L.x, i);
+    L.t[i] = xi + L.omega * di * (bi - si);
 }
 
 }  // namespace
@@ -561,14 +613,33 @@ int mg_coarse_cluster_size() {
     return chosen;
 }
 
-const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* ctl, cudaStream_t s) {
+// The vertex level goes to grid kernels when it has more rows than this (its
+// vectors then no longer fit the cluster's shared memory, and one cluster's 16
+// SMs take its passes alone) and a level below it exists.
+constexpr int kSplitVertexRows = 32768;
+
+bool mg_split_vertex_level(const MGPlan& m) { return m.nlev >= 2 && m.nvert > kSplitVertexRows; }
+
+// The coarse part of the V-cycle: one cluster launch, or, for a large vertex
+// level, the vertex level's stages as grid kernels around a cluster launch
+// that covers the levels below it.  Returns the vertex-level correction that
+// prolong_q1_kernel reads; *launches gets the kernels launched.
+const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* ctl, cudaStream_t s, int* launches) {
+    const bool split = mg_split_vertex_level(m);
+    const MGLevelDev& L1 = m.lv[1];
+    const int g1 = (m.nvert + 255) / 256;
+    if (split) {
+        vertex_rhs_kernel<<<g1, 256, 0, s>>>(m.nvert, m.vw, m.vinc, cres, L1.b, ctl);
+        vertex_down_kernel<<<g1, 256, 0, s>>>(L1, ctl);
+    }
     CoarseArgs ca{};
     ca.nvert = m.nvert; ca.nlev = m.nlev; ca.cres = cres; ca.vw = m.vw; ca.vinc = m.vinc;
+    ca.first = split ? 2 : 1;
     for (int l = 0; l <= m.nlev; ++l) ca.lv[l] = m.lv[l];
     ca.cinv = m.cinv;
-    // shared memory for the largest vector a stage stages (the vertex level), up to kCoarseSmemFloats
+    // shared memory for the largest vector a stage stages, up to kCoarseSmemFloats
     int vmax = 0;
-    for (int l = 1; l <= m.nlev; ++l) vmax = std::max(vmax, m.lv[l].n);
+    for (int l = ca.first; l <= m.nlev; ++l) vmax = std::max(vmax, m.lv[l].n);
     ca.cap = std::min(vmax, kCoarseSmemFloats);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
@@ -583,7 +654,14 @@ const float* launch_coarse_cycle(const MGPlan& m, const float* cres, const int* 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, coarse_cycle_kernel, ca, ctl);
-    return m.nlev > 1 ? m.lv[1].t : m.lv[1].x;
+    if (!split) {
+        *launches = 1;
+        return m.nlev > 1 ? m.lv[1].t : m.lv[1].x;
+    }
+    vertex_up_kernel<<<g1, 256, 0, s>>>(L1, m.nlev > 2 ? m.lv[2].t : m.lv[2].x, ctl);
+    vertex_post_kernel<<<g1, 256, 0, s>>>(L1, ctl);
+    *launches = 5;
+    return L1.t;
 }
 
 int mg_apply(const MGPlan& m, const double* r, double* z, const int* ctl, cudaStream_t s) {
@@ -661,11 +739,12 @@ int mg_apply_n(const MGPlan& m, const double* r, double* z, const int* ctl, cuda
     }
     bj_residual_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.WdT, r, st.cur, m.w4, m.res0,
                                                            m.coarse_pf, m.coarse_npf, ctl);
-    // vertex and aggregation levels and the coarsest solve (one cluster launch)
-    const float* coarse_out = launch_coarse_cycle(m, m.res0, ctl, s);
+    // vertex and aggregation levels and the coarsest solve
+    int lc = 0;
+    const float* coarse_out = launch_coarse_cycle(m, m.res0, ctl, s, &lc);
     const int rows0 = m.ne * N;
     prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, st.cur, ctl);
-    launches += 3;
+    launches += 2 + lc;
     // post-smoothing: the recurrence restarts from the corrected iterate
     st.prev = nullptr;
     for (int k = 0; k < m.nu0; ++k) {
@@ -710,10 +789,11 @@ int mg_cg_iteration_n(const MGPlan& m, const CGArgs& a, cudaStream_t s) {
     }
     bj_residual_kernel<N, kSmoothRows><<<nblkR, tpb, 0, s>>>(m.ne, m.A, m.WdT, a.r, st.cur, m.w4, m.res0,
                                                            m.coarse_pf, m.coarse_npf, a.ctl);
-    const float* coarse_out = launch_coarse_cycle(m, m.res0, a.ctl, s);
+    int lc = 0;
+    const float* coarse_out = launch_coarse_cycle(m, m.res0, a.ctl, s, &lc);
     const int rows0 = m.ne * N;
     prolong_q1_kernel<<<(rows0 + 255) / 256, 256, 0, s>>>(m.ne, N, m.vid, m.w4, coarse_out, st.cur, a.ctl);
-    launches += 3;
+    launches += 2 + lc;
     st.prev = nullptr;
     for (int k = 0; k < m.nu0; ++k) {
         if (k == m.nu0 - 1) {

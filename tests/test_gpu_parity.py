@@ -296,3 +296,22 @@ def test_moment_solve_from_smooth_moments_on_a_fine_curved_mesh():
         assert rel(phi.cpu().numpy(), x_o) < 1e-9, rel(phi.cpu().numpy(), x_o)
     finally:
         h.destroy()
+
+
+def test_multigrid_with_the_vertex_level_on_grid_kernels():
+    """A vertex level of more than 32,768 rows (here 201 x 201) runs its
+    stages as grid kernels around the cluster launch; the V-cycle must still
+    cut the CG iterations far below element-block Jacobi's and give the same
+    solution of the moment system."""
+    import paper_2304_07386_gb300 as P
+    prob = problem(200, 200, m=1, p=1, sn=4, kind="iso", c=0.9)
+    its, sols = [], []
+    for precond in (0, 1):
+        h = make_gpu(prob, tol_cg=1e-12, precond=precond)
+        P.smm_sweep(h, None)
+        phi = torch.zeros(prob["mesh"].n_elem * 4, dtype=torch.float64, device="cuda")
+        its.append(P.smm_moment_solve(h, phi))
+        sols.append(phi.cpu().numpy())
+        h.destroy()
+    assert its[1] < 40 and its[1] * 8 < its[0], its
+    assert rel(sols[1], sols[0]) < 1e-9
