@@ -53,9 +53,10 @@ typedef enum {
     SMM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
     SMM_ERR_OOM = 3,            /* device allocation failed */
     SMM_ERR_MESH = 4,           /* non-positive Jacobian, broken connectivity */
-    SMM_ERR_CYCLE = 5,          /* an ordinate's upwind graph has a cycle, or a
-                                   face is inflow at some points and outflow at
-                                   others (no lagging is done) */
+    SMM_ERR_CYCLE = 5,          /* an ordinate's upwind graph has a cycle (a face
+                                   that is inflow at some points and outflow at
+                                   others makes one) and options.cycle_lagging is
+                                   0, or the sweep mode cannot lag it */
     SMM_ERR_NONFINITE = 6,      /* NaN/Inf in an iterate */
     SMM_ERR_NOT_CONVERGED = 7,  /* iteration limit reached; the iterate is kept */
     SMM_ERR_DEVICE_TIMEOUT = 8  /* a bounded device-side wait expired */
@@ -181,11 +182,26 @@ typedef struct {
                                    checkpoint, takes the same steps as one
                                    uninterrupted call.  The caller passes the
                                    iterate the previous call returned. */
+    int32_t cycle_lagging;      /* nonzero (default): cycles of the ordinates'
+                                   upwind graphs are lagged, as the paper does on
+                                   its distorted mesh (Sec. "Thick Diffusion
+                                   Limit"): when no element is left whose upwind
+                                   neighbours are all swept, the lowest-numbered
+                                   remaining element is swept next and its
+                                   inflow from neighbours not yet swept is taken
+                                   from the previous sweep (zero before the
+                                   first).  A face that is inflow at some
+                                   quadrature points and outflow at others is
+                                   upwinded pointwise.  The iteration converges
+                                   to the same fixed point in more outer steps.
+                                   FP64 sweeps without the fixup only (else
+                                   SMM_ERR_CYCLE).  0: a cycle is SMM_ERR_CYCLE. */
 } smm_options;
 
 typedef struct {
     int32_t n_elem, p, m, n_dof_elem, n_ord, n_bface, n_fq, n_levels;
     int64_t n_angular;          /* n_elem * n_dof_elem * n_ord */
+    int64_t n_lagged;           /* (element, ordinate, face) inflows lagged to break cycles */
 } smm_info;
 
 typedef struct {

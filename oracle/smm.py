@@ -29,7 +29,8 @@ class SMMProblem:
         self.q = np.asarray(q, float)
         self.psibar = psibar
         self.fixup = fixup
-        # parallel block Jacobi sweep: tile ids and the previous sweep's psi (zero at first)
+        # parallel block Jacobi sweep: tile ids; the previous sweep's psi (zero at first) feeds
+        # lagged inflow (between tiles, or closing a cycle)
         self.block = disc.element_tiles(tiles) if tiles > 1 else None
         self.psi_prev = np.zeros((disc.nd, disc.ne, disc.n))
         self.A = ipsmm.assemble_lhs(disc, kappa_scale)
@@ -43,8 +44,7 @@ class SMMProblem:
 
     def G(self, varphi):
         """One application of the fixed-point map; returns (varphi_new, psi)."""
-        psi = self.disc.sweep(varphi, self.q, self.psibar, self.fixup, self.block,
-                              self.psi_prev if self.block is not None else None)
+        psi = self.disc.sweep(varphi, self.q, self.psibar, self.fixup, self.block, self.psi_prev)
         self.psi_prev = psi
         b = self.rhs_from_psi(psi)
         x = ipsmm.solve(self.A, b)
@@ -83,19 +83,20 @@ def source_iteration(disc: Discretization, q, psibar=None, tol=1e-10, max_iter=1
 def coupled_dense_solve(prob: SMMProblem):
     """Solve the coupled linear system {L psi = sigma_s/(4pi) varphi + q,
     D varphi = b(psi)} in one dense LU.  The maps varphi -> L^{-1}(...)
-    and psi -> b(psi) are affine; their matrices are built column by column
-    from unit vectors.  Tiny meshes only."""
+    (each ordinate's whole DG system solved at once, so cycles of the upwind
+    graph need no lagging) and psi -> b(psi) are affine; their matrices are
+    built column by column from unit vectors.  Tiny meshes only."""
     disc = prob.disc
     ne, n, nd = disc.ne, disc.n, disc.nd
     npsi, nphi = nd * ne * n, ne * n
     # affine transport map: psi = S varphi + s0
     zero_q = np.zeros_like(prob.q)
-    s0 = disc.sweep(None, prob.q, prob.psibar).ravel()
+    s0 = disc.solve_global(None, prob.q, prob.psibar).ravel()
     S = np.zeros((npsi, nphi))
     for j in range(nphi):
         e_j = np.zeros(nphi)
         e_j[j] = 1.0
-        S[:, j] = disc.sweep(e_j.reshape(ne, n), zero_q, None).ravel()
+        S[:, j] = disc.solve_global(e_j.reshape(ne, n), zero_q, None).ravel()
     # affine closure map: b = R psi + r0
     r0 = prob.rhs_from_psi(np.zeros((nd, ne, n)))
     R = np.zeros((nphi, npsi))

@@ -17,8 +17,13 @@ s_d = sigma_s/(4 pi) varphi + q_d (Eq. moment_coupled, first line).
 
 Elements are visited in a topological order of each ordinate's upwind
 graph (a neighbour is upwind if Omega_d . n < 0 at any point of the shared
-face); a cycle is an error (no lagging).  Each local system is solved by
-dense LU with partial pivoting.
+face, so a face that is inflow at some points and outflow at others makes
+its two elements depend on each other).  Cycles are lagged, as Sec. 6.2
+does on its distorted mesh: whenever no element is left whose upwind
+neighbours are all done, the lowest-numbered remaining element is taken
+next and its inflow from the neighbours not yet done comes from the
+previous sweep (psi_lag; zero if none is given).  Each local system is
+solved by dense LU with partial pivoting.
 """
 from __future__ import annotations
 
@@ -121,19 +126,66 @@ class Discretization:
         t = np.minimum(((corners - lo) / (hi - lo) * tiles).astype(int), tiles - 1)
         return t[:, 1] * tiles + t[:, 0]
 
-    def upwind_order(self, d: int, block=None):
-        """Topological order of the elements for ordinate d (smallest index
-        first among ready elements); with a tile array, upwind neighbours in
-        another tile are not dependencies (their values are lagged).  Raises
-        CycleError on a cycle."""
+    def upwind_order(self, d: int, block=None, lag_cycles=True):
+        """(order, lagged): a topological order of the elements for ordinate
+        d (smallest index first among ready elements) and the set of (e, f)
+        whose inflow is lagged.  With a tile array, upwind neighbours in
+        another tile are not dependencies (their values are lagged).  A cycle
+        is broken by taking the lowest-numbered remaining element and lagging
+        its pending inflow faces; with lag_cycles=False it raises CycleError."""
         if not hasattr(self, "_orders"):
             self._orders = {}
-        key = (d, None if block is None else tuple(block))
+        key = (d, None if block is None else tuple(block), lag_cycles)
         if key not in self._orders:
-            self._orders[key] = self._topological_order(d, block)
+            self._orders[key] = self._topological_order(d, block, lag_cycles)
         return self._orders[key]
 
-    def _topological_order(self, d: int, block=None):
+    def upwind_faces(self, e: int, d: int):
+        """Faces of element e through which ordinate d enters at some point
+        from a neighbour (the element's upwind dependencies)."""
+        out = []
+        for f in range(4):
+            nb = self.nbr[e][f]
+            if nb is not None and np.any(self.faces[e][f]["nds"] @ self.omega[d] < 0.0):
+                out.append((f, nb[0]))
+        return out
+
+    def _topological_order(self, d: int, block=None, lag_cycles=True):
+        lagged = set()
+        deps = [{} for _ in range(self.ne)]      # upwind neighbour -> faces of e toward it
+        for e in range(self.ne):
+            for f, u in self.upwind_faces(e, d):
+                if block is not None and block[u] != block[e]:
+                    lagged.add((e, f))
+                    continue
+                deps[e].setdefault(u, []).append(f)
+        indeg = [len(s) for s in deps]
+        down = [[] for _ in range(self.ne)]
+        for e in range(self.ne):
+            for u in deps[e]:
+                down[u].append(e)
+        ready = [e for e in range(self.ne) if indeg[e] == 0]
+        heapq.heapify(ready)
+        order, done = [], [False] * self.ne
+        while len(order) < self.ne:
+            if not ready:
+                if not lag_cycles:
+                    raise CycleError(f"upwind graph of ordinate {d} has a cycle")
+                v = min(e for e in range(self.ne) if not done[e])
+                for u, faces in deps[v].items():
+                    if not done[u]:
+                        lagged.update((v, f) for f in faces)
+                        down[u].remove(v)
+                indeg[v] = 0
+                heapq.heappush(ready, v)
+            u = heapq.heappop(ready)
+            done[u] = True
+            order.append(u)
+            for v in down[u]:
+                indeg[v] -= 1
+                if indeg[v] == 0:
+                    heapq.heappush(ready, v)
+        return order, lagged
         om = self.omega[d]
         deps = [set() for _ in range(self.ne)]
         for e in range(self.ne):
@@ -190,11 +242,15 @@ class Discretization:
         values of the total source for this ordinate; psibar: None (vacuum)
         or [nd][n_bface][p+1] face-node values.  fixup: apply the zero and
         scale negative flux fixup to every element solution before it is
-        passed downwind.  block/psi_lag: parallel block Jacobi sweep (Sec.
-        6.5) -- an upwind neighbour in another tile contributes its value
-        from psi_lag [ne][n] (the previous sweep) instead of this one."""
+        passed downwind.  psi_lag [ne][n] (the previous sweep; zero if None)
+        feeds the lagged faces: those that close a cycle, and, with a tile
+        array (parallel block Jacobi sweep, Sec. 6.5), those from another
+        tile."""
         psi = np.zeros((self.ne, self.n))
-        for e in self.upwind_order(d, block):
+        order, lagset = self.upwind_order(d, block)
+        if psi_lag is None:
+            psi_lag = np.zeros((self.ne, self.n))
+        for e in order:
             A = self.local_matrix(e, d)
             b = self.M[e] @ src[e]
             for f in range(4):
@@ -202,14 +258,18 @@ class Discretization:
                 a = fd["nds"] @ self.omega[d]
                 neg = np.minimum(a, 0.0)
                 if np.any(neg < 0.0):
-                    nb = self.nbr[e][f]
-                    lagged = block is not None and nb is not None and block[nb[0]] != block[e]
-                    up = self.upwind_values(e, f, d, psi_lag if lagged else psi, psibar)
+                    up = self.upwind_values(e, f, d, psi_lag if (e, f) in lagset else psi, psibar)
                     b = b - fd["V"].T @ (neg * up)
             psi[e] = np.linalg.solve(A, b)
             if fixup:
                 psi[e] = zero_and_scale(A, psi[e])
         return psi
+
+    def scattering_source(self, varphi):
+        """sigma_s/(4 pi) varphi per element node (zero for varphi None)."""
+        if varphi is None:
+            return np.zeros((self.ne, self.n))
+        return (self.sigma_s / (4.0 * math.pi))[:, None] * np.asarray(varphi, float)
 
     def sweep(self, varphi, q, psibar=None, fixup=False, block=None, psi_lag=None):
         """psi = L^{-1}(sigma_s/(4 pi) varphi + q) for all ordinates.
@@ -219,9 +279,7 @@ class Discretization:
         Returns psi [nd][ne][n]."""
         q = np.asarray(q, float)
         out = np.zeros((self.nd, self.ne, self.n))
-        scat = np.zeros((self.ne, self.n))
-        if varphi is not None:
-            scat = (self.sigma_s / (4.0 * math.pi))[:, None] * np.asarray(varphi, float)
+        scat = self.scattering_source(varphi)
         for d in range(self.nd):
             qd = q if q.ndim == 2 else q[d]
             out[d] = self.sweep_ordinate(d, scat + qd, psibar, fixup, block,
@@ -260,6 +318,20 @@ class Discretization:
                 up = self.upwind_values(e, f, d, zero, psibar)
                 b[e * n:(e + 1) * n] -= fd["V"].T @ (neg * up)
         return b
+
+    def solve_global(self, varphi, q, psibar=None):
+        """psi = L^{-1}(sigma_s/(4 pi) varphi + q) with each ordinate's whole
+        DG system (global_ordinate_matrix) solved by dense LU: the transport
+        solution the sweep computes when no inflow is lagged, and the fixed
+        point of lagged sweeps otherwise.  Tiny meshes only."""
+        q = np.asarray(q, float)
+        out = np.zeros((self.nd, self.ne, self.n))
+        scat = self.scattering_source(varphi)
+        for d in range(self.nd):
+            src = scat + (q if q.ndim == 2 else q[d])
+            A = self.global_ordinate_matrix(d)
+            out[d] = np.linalg.solve(A, self.global_ordinate_rhs(d, src, psibar)).reshape(self.ne, self.n)
+        return out
 
     # -- helpers --------------------------------------------------------------
     def interpolate(self, func):

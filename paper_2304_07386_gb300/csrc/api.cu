@@ -67,8 +67,13 @@ struct smm_ctx {
     float2 *ox2 = nullptr, *oy2 = nullptr, *Fx2 = nullptr, *Fy2 = nullptr, *inflow2 = nullptr;
     float2* psi2 = nullptr;
     float2* wq2 = nullptr;         // [6][nd] pairs of w_d (1, Ox, Oy, OxOx, OxOy, OyOy) for the pair moments
-    double* psi_lag = nullptr;     // block Jacobi sweep: previous sweep's psi (on-the-fly LU mode)
+    double* psi_lag = nullptr;     // lagged inflow: previous sweep's psi (on-the-fly LU mode)
     float2* psi2_lag = nullptr;    // ... and its pairs (cached-inverse mode)
+    bool lagging = false;          // some inflow is lagged (block Jacobi tiles or cycles)
+    int64_t n_lagged = 0;          // (element, ordinate, face) inflows lagged to break cycles
+    int32_t* fmix_id = nullptr;    // mixed faces: pointwise face matrices (see SweepArgs)
+    double* fmix = nullptr;
+    float2* fmix2 = nullptr;
     // negative flux fixup: column sums of M, Gx, Gy [ne][n] and of Fx, Fy over the test index [ne][4][p1]
     double *colM = nullptr, *colGx = nullptr, *colGy = nullptr, *colFx = nullptr, *colFy = nullptr;
     std::vector<int32_t> tasks_host, level_start;  // level-sorted task list (for batching)
@@ -227,6 +232,7 @@ void smm_default_options(smm_options* opt) {
     opt->mg_smoother = SMM_SMOOTHER_CHEBYSHEV;
     opt->cg_device_loop = 1;
     opt->resume_history = 0;
+    opt->cycle_lagging = 1;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -274,10 +280,15 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     in.kappa_scale = o.kappa_scale;
     in.moment_cg = o.moment_discretization == SMM_MOMENT_CG;
     in.sweep_tiles = o.sweep_tiles;
+    in.lag_cycles = o.cycle_lagging ? 1 : 0;
     smm::Setup s;
     std::string err;
     int rc = smm::build_setup(in, s, err);
     if (rc != 0) return fail((smm_status)rc, err);
+    if ((s.n_cycle_lagged > 0 || s.n_mixed > 0) &&
+        (o.sweep_precision != SMM_SWEEP_FP64 || o.negative_flux_fixup))
+        return fail(SMM_ERR_CYCLE, "the upwind graphs have cycles: cycle lagging needs the FP64 sweep without the "
+                                   "negative flux fixup");
 
     smm_ctx* h = new smm_ctx();
     h->opt = o;
@@ -369,7 +380,13 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
         h->psi = h->alloc<double>(nang);
         if (!h->psi) return bail(SMM_ERR_OOM, "device allocation failed");
     }
-    if (o.sweep_tiles > 1 && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) {
+    h->n_lagged = s.n_cycle_lagged;
+    h->lagging = o.sweep_tiles > 1 || s.n_cycle_lagged > 0;
+    if (!s.fmix.empty()) {
+        if (!upload(h, h->fmix_id, s.fmix_id) || !upload(h, h->fmix, s.fmix) || !upload(h, h->fmix2, to_pairs(s.fmix)))
+            return bail(SMM_ERR_OOM, "device allocation failed");
+    }
+    if (h->lagging && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) {
         h->psi_lag = h->alloc<double>(nang);
         if (!h->psi_lag) return bail(SMM_ERR_OOM, "device allocation failed");
     }
@@ -655,7 +672,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             if (!okp || !h->psi2) return bail(SMM_ERR_OOM, "device allocation failed");
             if (cudaMemsetAsync(h->psi2, 0, nang * sizeof(float2), h->stream) != cudaSuccess)
                 return bail(SMM_ERR_CUDA, "cudaMemsetAsync failed");
-            if (o.sweep_tiles > 1) {
+            if (h->lagging) {
                 h->psi2_lag = h->alloc<float2>(nang);
                 if (!h->psi2_lag) return bail(SMM_ERR_OOM, "device allocation failed");
             }
@@ -666,6 +683,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             smm::SweepArgs<float> a{};
             a.ne = s.ne; a.nd = s.nd; a.ntask = h->ntask; a.ox = h->ox; a.oy = h->oy; a.sigma_t = h->sigma_t;
             a.M = h->M32; a.Gx = h->Gx32; a.Gy = h->Gy32; a.Fx = h->Fx32; a.Fy = h->Fy32; a.fdir = h->fdir;
+            a.fmix_id = h->fmix_id; a.fmix = h->fmix;
             smm::launch_invert<float>(s.p, a, h->ainv32, h->stream);
         } else {
             h->ainv_df = h->alloc<float2>(ninv);
@@ -673,6 +691,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
             smm::SweepArgs<double> a{};
             a.ne = s.ne; a.nd = s.nd; a.ntask = h->ntask; a.ox = h->ox; a.oy = h->oy; a.sigma_t = h->sigma_t;
             a.M = h->M; a.Gx = h->Gx; a.Gy = h->Gy; a.Fx = h->Fx; a.Fy = h->Fy; a.fdir = h->fdir;
+            a.fmix_id = h->fmix_id; a.fmix = h->fmix;
             smm::launch_invert_df(s.p, a, h->ainv_df, h->stream);
         }
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -697,6 +716,7 @@ smm_status smm_get_info(smm_handle h, smm_info* info) {
     info->n_elem = h->ne; info->p = h->p; info->m = h->m; info->n_dof_elem = h->n; info->n_ord = h->nd;
     info->n_bface = h->nb; info->n_fq = h->nfq; info->n_levels = h->nlevels;
     info->n_angular = (int64_t)h->ne * h->n * h->nd;
+    info->n_lagged = h->n_lagged;
     return SMM_OK;
 }
 
@@ -726,6 +746,7 @@ smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) 
     a.ne = h->ne; a.nd = h->nd; a.ntask = h->ntask; a.p = h->p; a.tasks = h->tasks; a.ox = h->ox; a.oy = h->oy;
     a.sigma_t = h->sigma_t; a.sigma_s = h->sigma_s;
     a.fdir = h->fdir; a.nbr = h->nbr; a.nbr_face = h->nbr_face; a.nbr_flip = h->nbr_flip; a.bface_id = h->bface_id;
+    a.fmix_id = h->fmix_id; a.fmix = h->fmix; a.fmix2 = h->fmix2;
     a.done = h->done; a.epoch = h->epoch; a.ticket = h->ticket; a.err = h->err;
     a.timeout_ns = (long long)(h->opt.spin_timeout_s * 1e9);
     SMM_CUDA(cudaMemsetAsync(h->gate, 0, sizeof(unsigned), h->stream));
@@ -737,8 +758,8 @@ smm_status prepare_sweep(smm_handle h, const double* phi, smm::SweepArgs<T>& a) 
         a.fixup = h->opt.negative_flux_fixup ? 1 : 0;
         a.colM = h->colM; a.colGx = h->colGx; a.colGy = h->colGy; a.colFx = h->colFx; a.colFy = h->colFy;
         a.rhs = nullptr; a.psi = h->psi; a.psi_acc = nullptr;
-        if (h->opt.sweep_tiles > 1) {
-            // block Jacobi sweep: the previous sweep's psi feeds the faces between tiles
+        if (h->lagging) {
+            // lagged inflow (between tiles, or closing a cycle): the previous sweep's psi
             const size_t nang = (size_t)h->ne * h->nd * h->n;
             if (h->cached) {
                 SMM_CUDA(cudaMemcpyAsync(h->psi2_lag, h->psi2, nang * sizeof(float2), cudaMemcpyDeviceToDevice,

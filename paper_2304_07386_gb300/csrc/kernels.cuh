@@ -49,9 +49,16 @@ struct SweepArgs {
     const float2* Fy2;
     const float2* inflow2;
     float2* psi2;              // FP64 cached mode: psi as pairs (read by downwind tasks and the moments)
-    // block Jacobi sweep: the previous sweep's psi, read across tiles (fdir == -2)
+    // lagged inflow (fdir -2 or 3: across tiles of a block Jacobi sweep, or closing a cycle): the
+    // previous sweep's psi
     const T* psi_lag;
     const float2* psi2_lag;
+    // faces that are inflow at some quadrature points and outflow at others (fdir 2, or 3 when
+    // lagged): id [ne][nd][4] of their pointwise face matrices fmix[id][2][p1][p1] (outflow part,
+    // inflow part), FP64 and as FP32 pairs; nullptr when the mesh has none
+    const int32_t* fmix_id;
+    const double* fmix;
+    const float2* fmix2;
     // zero and scale negative flux fixup (source mode): column sums of M, Gx, Gy [ne][n] and of the
     // face matrices Fx, Fy over their test index [ne][4][p1]
     int fixup;

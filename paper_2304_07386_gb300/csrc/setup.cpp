@@ -591,9 +591,10 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
     }
     if (bad_jac) { err = "non-positive Jacobian at a quadrature point"; return 4; }
 
-    // ---- face direction per (e, d, f) and sign definiteness ----
+    // ---- face direction per (e, d, f): 1 outflow, -1 inflow, 2 inflow at some
+    //      quadrature points and outflow at others (mixed), 0 tangential ----
     s.fdir.assign((size_t)ne * nd * 4, 0);
-    int mixed = 0;
+    int64_t mixed = 0;
 #pragma omp parallel for schedule(static) reduction(+ : mixed)
     for (int e = 0; e < ne; ++e)
         for (int d = 0; d < nd; ++d)
@@ -606,11 +607,42 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
                     neg |= a < 0.0;
                 }
                 if (pos && neg) mixed += 1;
-                s.fdir[((size_t)e * nd + d) * 4 + f] = pos ? 1 : (neg ? -1 : 0);
+                s.fdir[((size_t)e * nd + d) * 4 + f] = pos && neg ? 2 : (pos ? 1 : (neg ? -1 : 0));
             }
-    if (mixed) {
+    if (mixed && !in.lag_cycles) {
         err = "a face is inflow at some quadrature points and outflow at others for some ordinate";
         return 5;
+    }
+    // pointwise face matrices of the mixed faces: their outflow part enters the
+    // local operator, their inflow part multiplies the upwind trace
+    s.n_mixed = mixed;
+    s.fmix_id.clear();
+    s.fmix.clear();
+    if (mixed) {
+        s.fmix_id.assign((size_t)ne * nd * 4, -1);
+        int32_t next = 0;
+        for (size_t k = 0; k < s.fdir.size(); ++k)
+            if (s.fdir[k] == 2) s.fmix_id[k] = next++;
+        s.fmix.assign((size_t)next * 2 * p1 * p1, 0.0);
+#pragma omp parallel for schedule(static)
+        for (int e = 0; e < ne; ++e)
+            for (int d = 0; d < nd; ++d)
+                for (int f = 0; f < 4; ++f) {
+                    const int32_t id = s.fmix_id[((size_t)e * nd + d) * 4 + f];
+                    if (id < 0) continue;
+                    double* fp = &s.fmix[(size_t)id * 2 * p1 * p1];
+                    double* fn = fp + p1 * p1;
+                    for (int q = 0; q < nfq; ++q) {
+                        const double* nds = &s.nds[(((size_t)e * 4 + f) * nfq + q) * 2];
+                        const double a = s.quad.ox[d] * nds[0] + s.quad.oy[d] * nds[1];
+                        for (int i = 0; i < p1; ++i)
+                            for (int j = 0; j < p1; ++j) {
+                                const double lab = s.L1[q * p1 + i] * s.L1[q * p1 + j];
+                                fp[i * p1 + j] += std::max(a, 0.0) * lab;
+                                fn[i * p1 + j] += std::min(a, 0.0) * lab;
+                            }
+                    }
+                }
     }
 
     // ---- parallel block Jacobi sweep (Sec. 6.5): tiles of the bounding box by
@@ -643,40 +675,68 @@ int build_setup(const Input& in, Setup& s, std::string& err) {
                 if (e2 < 0 || s.tile[e2] == s.tile[e]) continue;
                 for (int d = 0; d < nd; ++d) {
                     int8_t& fd = s.fdir[((size_t)e * nd + d) * 4 + f];
-                    if (fd < 0) fd = -2;
+                    if (fd == -1) fd = -2;
+                    else if (fd == 2) fd = 3;
                 }
             }
     }
 
-    // ---- upwind levels per ordinate (Kahn), task list sorted by (level, e, d) ----
+    // ---- upwind levels per ordinate (Kahn), task list sorted by (level, e, d).
+    //      An element depends on the neighbour across each face through which
+    //      the ordinate enters it (fdir -1 or 2).  When no element is ready but
+    //      some remain (a cycle), the lowest-numbered remaining element is taken
+    //      next and its faces toward neighbours not yet done are lagged (fdir
+    //      -1 -> -2, 2 -> 3: those values come from the previous sweep), the
+    //      cycle lagging of Sec. 6.2 ----
     s.level.assign((size_t)nd * ne, -1);
     int maxlev = 0;
+    int64_t lagged = 0;
     {
+        auto pending = [&](int e, int d, int f) {  // face f of e is an unlagged inflow face from a neighbour
+            const int8_t c = s.fdir[((size_t)e * nd + d) * 4 + f];
+            return s.nbr[e * 4 + f] >= 0 && (c == -1 || c == 2);
+        };
         std::vector<int> indeg(ne), queue(ne);
+        std::vector<char> done(ne);
         for (int d = 0; d < nd; ++d) {
             int* lev = &s.level[(size_t)d * ne];
-            int head = 0, tail = 0;
+            int head = 0, tail = 0, low = 0;
+            std::fill(done.begin(), done.end(), 0);
             for (int e = 0; e < ne; ++e) {
                 int c = 0;
-                for (int f = 0; f < 4; ++f)
-                    if (s.nbr[e * 4 + f] >= 0 && s.fdir[((size_t)e * nd + d) * 4 + f] == -1) ++c;
+                for (int f = 0; f < 4; ++f) c += pending(e, d, f) ? 1 : 0;
                 indeg[e] = c;
                 if (c == 0) { lev[e] = 0; queue[tail++] = e; }
             }
-            while (head < tail) {
-                int u = queue[head++];
+            while (tail < ne || head < tail) {
+                if (head == tail) {
+                    if (!in.lag_cycles) { err = "an ordinate's upwind graph has a cycle"; return 5; }
+                    while (done[low] || indeg[low] == 0) ++low;  // the lowest-numbered remaining element
+                    const int v = low;
+                    for (int f = 0; f < 4; ++f) {
+                        const int u = s.nbr[v * 4 + f];
+                        if (!pending(v, d, f) || done[u]) continue;
+                        int8_t& c = s.fdir[((size_t)v * nd + d) * 4 + f];
+                        c = c == -1 ? -2 : 3;
+                        lagged += 1;
+                    }
+                    indeg[v] = 0;
+                    lev[v] = std::max(lev[v], 0);
+                    queue[tail++] = v;
+                }
+                const int u = queue[head++];
+                done[u] = 1;
                 for (int f = 0; f < 4; ++f) {
-                    int v = s.nbr[u * 4 + f];
-                    if (v < 0 || s.fdir[((size_t)u * nd + d) * 4 + f] <= 0) continue;  // u -> v through u's outflow face
-                    if (s.tile[v] != s.tile[u]) continue;                                // lagged across tiles
+                    const int v = s.nbr[u * 4 + f];
+                    if (v < 0 || !pending(v, d, s.nbr_face[u * 4 + f])) continue;  // v takes inflow from u
                     lev[v] = std::max(lev[v], lev[u] + 1);
                     if (--indeg[v] == 0) queue[tail++] = v;
                 }
             }
-            if (tail != ne) { err = "an ordinate's upwind graph has a cycle"; return 5; }
             for (int e = 0; e < ne; ++e) maxlev = std::max(maxlev, lev[e]);
         }
     }
+    s.n_cycle_lagged = lagged;
     s.nlevels = maxlev + 1;
     {
         std::vector<int64_t> cnt(s.nlevels + 1, 0);

@@ -38,6 +38,7 @@ struct Input {
     double kappa_scale = 1.0;
     int moment_cg = 0;                   // also build the continuous (CG) moment system
     int sweep_tiles = 1;                 // parallel block Jacobi sweep over tiles x tiles tiles (1: exact)
+    int lag_cycles = 1;                  // lag cycles of the upwind graphs (0: a cycle is an error)
 };
 
 struct Setup {
@@ -51,6 +52,14 @@ struct Setup {
     std::vector<double> sigma_t, sigma_s;
     std::vector<double> M, Gx, Gy;                // [ne][n][n], row = test function
     std::vector<double> Fx, Fy;                   // [ne][4][p1][p1]
+    // faces that are inflow at some quadrature points and outflow at others for
+    // an ordinate (fdir 2, or 3 when lagged): the id of their pair of pointwise
+    // face matrices [ne][nd][4] (-1 for other faces), and the pairs
+    // fmix[id][0][a][b] = sum_q max(Omega.n ds w, 0) l_a l_b (outflow part, in A)
+    // and fmix[id][1][a][b] = the same with min (inflow part, on the upwind trace)
+    std::vector<int32_t> fmix_id;
+    std::vector<double> fmix;
+    int64_t n_mixed = 0, n_cycle_lagged = 0;     // (element, ordinate, face) counts
     std::vector<int8_t> fdir;                     // [ne][nd][4]: +1 out, -1 in, -2 in from another tile
                                                   // (lagged: previous sweep's values), 0 none
     std::vector<int32_t> tile;                    // [ne] tile of the block Jacobi sweep (all 0: exact sweep)

@@ -283,8 +283,9 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
             const int f = lane;
             const int df = f == 0 ? dir[0] : (f == 1 ? dir[1] : (f == 2 ? dir[2] : dir[3]));
             const int nb = a.nbr[e * 4 + f];
-            // (-2: inflow from another tile of a block Jacobi sweep, taken from the previous sweep)
-            if (df == -1 && nb >= 0) ok = wait_epoch(a.done + (size_t)nb * nd + d, a.epoch, a.timeout_ns, a.err);
+            // (-2, 3: lagged inflow, taken from the previous sweep)
+            if ((df == -1 || (EXT && df == 2)) && nb >= 0)
+                ok = wait_epoch(a.done + (size_t)nb * nd + d, a.epoch, a.timeout_ns, a.err);
         }
         ok = __all_sync(FULL, ok);
         if (!ok) {
@@ -324,34 +325,44 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
             const bool on = (f == 0 && iy == 0) || (f == 1 && ix == P) || (f == 2 && iy == P) || (f == 3 && ix == 0);
             const int fa = (f == 0 || f == 2) ? ix : iy;  // position of this row on face f
             const size_t fo = (((size_t)e * 4 + f) * P1 + fa) * P1;
-            if (!INV && df > 0 && on) {
+            if (!INV && (df == 1 || (EXT && df >= 2)) && on) {
+                const double* fm =
+                    EXT && df >= 2 ? a.fmix + ((size_t)a.fmix_id[((size_t)e * nd + d) * 4 + f] * 2 * P1 + fa) * P1
+                                   : nullptr;
 #pragma unroll
                 for (int c = 0; c < P1; ++c) {
-                    const T v = ox * a.Fx[fo + c] + oy * a.Fy[fo + c];
+                    const T v = fm ? (T)fm[c] : ox * a.Fx[fo + c] + oy * a.Fy[fo + c];
 #pragma unroll
                     for (int j = 0; j < (INV ? 1 : N); ++j)
                         if (j == face_node<P>(f, c)) A[j] += v;
                 }
-            } else if (DF && df < 0) {
+            }
+            if (DF && (df < 0 || (EXT && df >= 2))) {
                 // inflow face in pairs: lane (a, c) forms coef[a][c] u[c] with
                 // coef = Omega_x Fx + Omega_y Fy, the p+1 lanes of group a sum
                 // over c, and every row adds -A^{-1}[row][node(f, a)] v_a
                 const int la = lane / P1, lc = lane - (lane / P1) * P1;
                 float ts = 0.0f, tc = 0.0f;
                 if (lane < P1 * P1) {
-                    const size_t fo2 = ((size_t)e * 4 + f) * P1 * P1 + la * P1 + lc;
-                    const float2 fx = a.Fx2[fo2], fy = a.Fy2[fo2], o2x = a.ox2[d], o2y = a.oy2[d];
-                    float cs = 0.0f, cc = 0.0f;
-                    df_acc(cs, cc, o2x.x, o2x.y, fx.x, fx.y);
-                    df_acc(cs, cc, o2y.x, o2y.y, fy.x, fy.y);
-                    const float2 coef = df_norm(cs, cc);
+                    float2 coef;
+                    if (EXT && df >= 2) {
+                        // mixed face: the inflow part of its pointwise face matrix
+                        coef = a.fmix2[((size_t)a.fmix_id[((size_t)e * nd + d) * 4 + f] * 2 + 1) * P1 * P1 + la * P1 + lc];
+                    } else {
+                        const size_t fo2 = ((size_t)e * 4 + f) * P1 * P1 + la * P1 + lc;
+                        const float2 fx = a.Fx2[fo2], fy = a.Fy2[fo2], o2x = a.ox2[d], o2y = a.oy2[d];
+                        float cs = 0.0f, cc = 0.0f;
+                        df_acc(cs, cc, o2x.x, o2x.y, fx.x, fx.y);
+                        df_acc(cs, cc, o2y.x, o2y.y, fy.x, fy.y);
+                        coef = df_norm(cs, cc);
+                    }
                     const int nb = a.nbr[e * 4 + f];
                     float2 u = make_float2(0.0f, 0.0f);
                     if (nb >= 0) {
                         const int f2 = a.nbr_face[e * 4 + f];
                         const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
                         const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
-                        u = __ldcg((EXT && df == -2 ? a.psi2_lag : a.psi2) + ((size_t)nb * nd + d) * N + node);
+                        u = __ldcg((EXT && (df == -2 || df == 3) ? a.psi2_lag : a.psi2) + ((size_t)nb * nd + d) * N + node);
                     } else if (MODE == SWEEP_SOURCE && a.inflow2) {
                         const int bi = a.bface_id[e * 4 + f];
                         u = a.inflow2[((size_t)bi * nd + d) * P1 + lc];
@@ -369,7 +380,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                     const float2 col = Adf[face_node<P>(f, aa)];
                     df_acc(ys, yc, -col.x, -col.y, __shfl_sync(FULL, v.x, aa * P1), __shfl_sync(FULL, v.y, aa * P1));
                 }
-            } else if (df < 0) {
+            } else if (df < 0 || (EXT && df >= 2)) {
                 // inflow face (warp-uniform branch): the (p+1)^2 products
                 // coef[a][c] * psi_up[c] are spread over lanes (a, c), summed
                 // over c within each group of p+1 lanes, and handed to the lane
@@ -378,14 +389,17 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                 T term = 0;
                 if (lane < P1 * P1) {
                     const size_t fo2 = ((size_t)e * 4 + f) * P1 * P1 + la * P1 + lc;
-                    const T coef = ox * a.Fx[fo2] + oy * a.Fy[fo2];
+                    const T coef = EXT && df >= 2
+                                       ? (T)a.fmix[((size_t)a.fmix_id[((size_t)e * nd + d) * 4 + f] * 2 + 1) * P1 * P1 +
+                                                   la * P1 + lc]
+                                       : ox * a.Fx[fo2] + oy * a.Fy[fo2];
                     const int nb = a.nbr[e * 4 + f];
                     T upv = 0;
                     if (nb >= 0) {
                         const int f2 = a.nbr_face[e * 4 + f];
                         const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
                         const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
-                        upv = ldg_cg((EXT && df == -2 ? a.psi_lag : a.psi) + ((size_t)nb * nd + d) * N + node);
+                        upv = ldg_cg((EXT && (df == -2 || df == 3) ? a.psi_lag : a.psi) + ((size_t)nb * nd + d) * N + node);
                     } else if (MODE == SWEEP_SOURCE && a.inflow) {
                         const int bi = a.bface_id[e * 4 + f];
                         upv = (T)a.inflow[((size_t)bi * nd + d) * P1 + lc];
@@ -639,9 +653,12 @@ __global__ void __launch_bounds__(256) invert_kernel(SweepArgs<T> a, T* __restri
             if (dir[f] > 0 && on) {
                 const int fa = (f == 0 || f == 2) ? ix : iy;
                 const size_t fo = (((size_t)e * 4 + f) * P1 + fa) * P1;
+                // mixed face: the outflow part of its pointwise face matrix
+                const double* fm =
+                    dir[f] >= 2 ? a.fmix + ((size_t)a.fmix_id[(size_t)task * 4 + f] * 2 * P1 + fa) * P1 : nullptr;
 #pragma unroll
                 for (int c = 0; c < P1; ++c) {
-                    const T v = ox * a.Fx[fo + c] + oy * a.Fy[fo + c];
+                    const T v = fm ? (T)fm[c] : ox * a.Fx[fo + c] + oy * a.Fy[fo + c];
 #pragma unroll
                     for (int j = 0; j < N; ++j)
                         if (j == face_node<P>(f, c)) A[j] += v;
@@ -728,7 +745,7 @@ static void launch_p(int mode, const SweepArgs<T>& a, int grid, cudaStream_t s) 
     const bool inv = a.ainv != nullptr || a.ainv_df != nullptr;
     if (mode == SWEEP_SOURCE) {
         if constexpr (sizeof(T) == 8) {
-            if (a.fixup || a.psi_lag || a.psi2_lag) {
+            if (a.fixup || a.psi_lag || a.psi2_lag || a.fmix_id) {
                 if (inv) launch_one<T, P, SWEEP_SOURCE, true, true>(a, grid, s);
                 else launch_one<T, P, SWEEP_SOURCE, false, true>(a, grid, s);
                 return;

@@ -39,13 +39,13 @@ class smm_options(C.Structure):
                 ("sweep_solver", C.c_int32), ("anderson_depth", C.c_int32), ("guess_check", C.c_int32),
                 ("mg_smooth_steps", C.c_int32), ("moment_discretization", C.c_int32),
                 ("negative_flux_fixup", C.c_int32), ("sweep_tiles", C.c_int32), ("mg_smoother", C.c_int32),
-                ("cg_device_loop", C.c_int32), ("resume_history", C.c_int32)]
+                ("cg_device_loop", C.c_int32), ("resume_history", C.c_int32), ("cycle_lagging", C.c_int32)]
 
 
 class smm_info(C.Structure):
     _fields_ = [("n_elem", C.c_int32), ("p", C.c_int32), ("m", C.c_int32), ("n_dof_elem", C.c_int32),
                 ("n_ord", C.c_int32), ("n_bface", C.c_int32), ("n_fq", C.c_int32), ("n_levels", C.c_int32),
-                ("n_angular", C.c_int64)]
+                ("n_angular", C.c_int64), ("n_lagged", C.c_int64)]
 
 
 class smm_stats(C.Structure):

@@ -105,31 +105,34 @@ class StructuredMesh:
         return xm, ym
 
 
-def _perturbation(seed: int, lx: float, ly: float, amplitude: float):
+def _perturbation(seed: int, lx: float, ly: float, amplitude: float, wave_max: int = 2, scale_by_k: bool = True):
     """Seeded sinusoidal perturbation parameters.
 
-    Wave numbers are drawn from {1, 2}; the amplitude of each component is
-    ``amplitude * L / max(k)`` with a random sign, so that the largest face
-    tilt stays at about ``amplitude * pi`` radians whatever the draw.
+    Wave numbers are drawn from {1, ..., wave_max}; the amplitude of each
+    component is ``amplitude * L / max(k)`` (scale_by_k, so that the largest
+    face tilt stays at about ``amplitude * pi`` radians whatever the draw) or
+    ``amplitude * L``, with a random sign.
     """
     rng = np.random.default_rng(seed)
-    k = rng.integers(1, 3, size=4)
+    k = rng.integers(1, wave_max + 1, size=4)
     s = rng.choice([-1.0, 1.0], size=2)
-    ax = s[0] * amplitude * lx / max(k[0], k[1])
-    ay = s[1] * amplitude * ly / max(k[2], k[3])
+    ax = s[0] * amplitude * lx / (max(k[0], k[1]) if scale_by_k else 1)
+    ay = s[1] * amplitude * ly / (max(k[2], k[3]) if scale_by_k else 1)
     return ((float(ax), int(k[0]), int(k[1])), (float(ay), int(k[2]), int(k[3])))
 
 
 def structured_mesh(nx: int, ny: int | None = None, m: int = 1,
                     domain=(0.0, 1.0, 0.0, 1.0), *, perturb_seed: int | None = None,
-                    amplitude: float = 0.05) -> StructuredMesh:
+                    amplitude: float = 0.05, wave_max: int = 2, scale_by_k: bool = True) -> StructuredMesh:
     """Structured quad mesh with control points on GLL nodes of order ``m``.
 
     With ``perturb_seed`` the straight grid is moved by the seeded
     sinusoidal map x' = x + a_x sin(pi k1 x~) sin(pi k2 y~),
     y' = y + a_y sin(pi k3 x~) sin(pi k4 y~) (x~, y~ scaled to [0,1]), which
     leaves the domain boundary in place.  Shared control points make the
-    mesh continuous.
+    mesh continuous.  wave_max = 3, scale_by_k = False gives wave numbers in
+    {1, 2, 3} at amplitude a_x = amplitude * (x1 - x0), whose tilted faces can
+    be inflow at some points and outflow at others for grazing ordinates.
     """
     ny = nx if ny is None else ny
     x0, x1, y0, y1 = map(float, domain)
@@ -145,7 +148,8 @@ def structured_mesh(nx: int, ny: int | None = None, m: int = 1,
     ys = y0 + (ey + g[ay_]) * hy
     xs[-1], ys[-1] = x1, y1
     X, Y = np.meshgrid(xs, ys, indexing="xy")  # [nyn][nxn]
-    pert = _perturbation(perturb_seed, x1 - x0, y1 - y0, amplitude) if perturb_seed is not None else ()
+    pert = (_perturbation(perturb_seed, x1 - x0, y1 - y0, amplitude, wave_max, scale_by_k)
+            if perturb_seed is not None else ())
     mesh = StructuredMesh(nx, ny, m, x0, x1, y0, y1, np.zeros((0, 2)), np.zeros((0, 0), np.int32), pert)
     Xm, Ym = mesh.map(X, Y)
     nodes = np.stack([Xm.ravel(), Ym.ravel()], axis=1).astype(np.float64)

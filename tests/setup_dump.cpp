@@ -3,6 +3,7 @@
 // with the oracle.  Usage: setup_dump DIR NE NNODES M P
 //   in:  DIR/nodes.f64 [nnodes][2], DIR/elem.i32 [ne][(m+1)^2], DIR/sigma_t.f64 [ne],
 //        DIR/q.f64 [ne][n] isotropic source per steradian (sigma_s = sigma_t / 2)
+//   a sixth argument "nolag" turns cycle lagging off
 //   out: DIR/dims.txt (n nfq nd nlevels), DIR/{Kxx,Ks,Kyy,Dfx,Dfy,nds,M,Gx,Gy,Adiag,Aoff,Pinv,bfixed,
 //        ox,oy,w}.f64, DIR/{nbr,level,tasks,level_start}.i32, DIR/fdir.i8 [ne][nd][4]
 //   A setup error is printed on stderr and gives exit status 4.
@@ -51,8 +52,9 @@ static int size_check(int ne, int m, int p, int sn) {
 int main(int argc, char** argv) {
     if (argc == 6 && std::string(argv[1]) == "--size-check")
         return size_check(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]));
-    if (argc != 6) return 2;
+    if (argc != 6 && argc != 7) return 2;
     const std::string dir = argv[1];
+    const bool lag = !(argc == 7 && std::string(argv[6]) == "nolag");
     const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
     const int n = (p + 1) * (p + 1);
     std::vector<double> nodes((size_t)nn * 2), st(ne), ss(ne), q((size_t)ne * n, 0.0);
@@ -65,6 +67,7 @@ int main(int argc, char** argv) {
     in.ne = ne; in.m = m; in.p = p; in.sn = 4; in.n_nodes = nn;
     in.nodes = nodes.data(); in.elem_nodes = elem.data(); in.sigma_t = st.data(); in.sigma_s = ss.data();
     in.q = q.data();
+    in.lag_cycles = lag ? 1 : 0;
     smm::Setup s;
     std::string err;
     if (smm::build_setup(in, s, err)) {

@@ -24,11 +24,15 @@
 // stopped.  It then sweeps again with the next flag epoch and the whole list,
 // as the library's next sweep does, and that sweep's flux is the output.  The
 // error words of both runs go to DIR/timeout_err.txt.
+// MODE lag runs the kernels with the optional parts compiled in on a mesh whose
+// upwind graphs have cycles: the faces the setup lagged read DIR/psi_lag.f64
+// ([ne][nd][n], the previous sweep's flux), the faces that are inflow at some
+// points and outflow at others use their pointwise face matrices.
 // Usage: sweep_emu DIR NE NNODES M P SN ANGULAR INFLOW MODE K   (one problem)
 //        sweep_emu --batch DIR COUNT                          (see run_batch)
 //   in:  DIR/nodes.f64, elem.i32, sigma_t.f64, sigma_s.f64, phi.f64 [ne][n],
 //        q.f64 ([ne][n], or [nd][ne][n] if ANGULAR), inflow.f64 [nd][n_bface][p+1] if INFLOW,
-//        nbface.txt (the boundary face count); MODE plain | fixup | refine | timeout, K sweeps (refine)
+//        nbface.txt (the boundary face count); MODE plain | fixup | refine | timeout | lag, K sweeps (refine)
 //   out: DIR/dims.txt (n nd n_bface nlevels), DIR/psi_lu.f64, DIR/psi_inv.f64 and (FP64 modes)
 //        DIR/psi2_inv.f64 (the pair copy as hi + lo) [ne][nd][n], the moments the sweep forms
 //        DIR/mom_lu.f64, DIR/mom_inv.f64 [6][ne][n] and beta DIR/beta_lu.f64, DIR/beta_inv.f64
@@ -132,6 +136,11 @@ static smm::SweepArgs<double> base_args(const smm::Setup& s, const std::vector<d
     done.assign((size_t)s.ne * s.nd, 0u);
     a.done = done.data(); a.epoch = 1; a.err = &err;
     a.timeout_ns = 60LL * 1000 * 1000 * 1000;
+    if (!s.fmix.empty()) {
+        static thread_local std::vector<float2> fmix2;
+        fmix2 = to_pairs(s.fmix);
+        a.fmix_id = s.fmix_id.data(); a.fmix = s.fmix.data(); a.fmix2 = fmix2.data();
+    }
     return a;
 }
 
@@ -244,17 +253,22 @@ static void run_refined(const smm::Setup& s, const std::vector<double>& phi, boo
 }
 
 template <int P>
-static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow, bool fixup, Run& lu, Run& inv) {
+static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow, bool fixup, Run& lu, Run& inv,
+                const std::vector<double>* lag = nullptr) {
     const int ne = s.ne, nd = s.nd, n = s.n;
     const size_t nang = (size_t)ne * nd * n;
     const ColSums cols(s);
+    const std::vector<float2> lag2 = lag ? to_pairs(*lag) : std::vector<float2>();
     {  // in-register LU
         std::vector<unsigned> done;
         smm::SweepArgs<double> a = base_args(s, phi, inflow, done, lu.err);
         lu.psi.assign(nang, 0.0);
         a.psi = lu.psi.data();
         moment_args(s, a, lu, lu.psi.data());
-        if (fixup) {
+        if (lag) {
+            a.psi_lag = lag->data();
+            emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, true>(a); });
+        } else if (fixup) {
             cols.fill(a);
             emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, false, true>(a); });
         } else {
@@ -269,7 +283,10 @@ static void run(const smm::Setup& s, const std::vector<double>& phi, bool inflow
         inv.psi2.assign(nang, make_float2(0.0f, 0.0f));
         a.psi = nullptr; a.psi2 = inv.psi2.data();
         moment_args(s, a, inv, nullptr);
-        if (fixup) {
+        if (lag) {
+            a.psi2_lag = lag2.data();
+            emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, true>(a); });
+        } else if (fixup) {
             cols.fill(a);
             emu_launch(1, 256, 0, [&] { smm::sweep_kernel<double, P, smm::SWEEP_SOURCE, true, true>(a); });
         } else {
@@ -454,7 +471,7 @@ int main(int argc, char** argv) {
     if (argc != 11) return 2;
     const std::string mode = argv[9];
     const int K = std::atoi(argv[10]);
-    if (mode != "plain" && mode != "fixup" && mode != "refine" && mode != "timeout") return 2;
+    if (mode != "plain" && mode != "fixup" && mode != "refine" && mode != "timeout" && mode != "lag") return 2;
     const std::string dir = argv[1];
     const int ne = std::atoi(argv[2]), nn = std::atoi(argv[3]), m = std::atoi(argv[4]), p = std::atoi(argv[5]);
     const int sn = std::atoi(argv[6]), angular = std::atoi(argv[7]), inflow = std::atoi(argv[8]);
@@ -482,11 +499,17 @@ int main(int argc, char** argv) {
             default: run_refined<4>(s, pr.phi, pr.inflow, K, lu, inv); break;
         }
     } else {
+        std::vector<double> lagv;
+        if (mode == "lag") {
+            lagv.resize((size_t)s.ne * s.nd * s.n);
+            if (!read_file(dir + "/psi_lag.f64", lagv)) return 3;
+        }
+        const std::vector<double>* lag = mode == "lag" ? &lagv : nullptr;
         switch (p) {
-            case 1: run<1>(s, pr.phi, pr.inflow, fix, lu, inv); break;
-            case 2: run<2>(s, pr.phi, pr.inflow, fix, lu, inv); break;
-            case 3: run<3>(s, pr.phi, pr.inflow, fix, lu, inv); break;
-            default: run<4>(s, pr.phi, pr.inflow, fix, lu, inv); break;
+            case 1: run<1>(s, pr.phi, pr.inflow, fix, lu, inv, lag); break;
+            case 2: run<2>(s, pr.phi, pr.inflow, fix, lu, inv, lag); break;
+            case 3: run<3>(s, pr.phi, pr.inflow, fix, lu, inv, lag); break;
+            default: run<4>(s, pr.phi, pr.inflow, fix, lu, inv, lag); break;
         }
     }
     return write_outputs(dir, s, lu, inv) ? 0 : 5;

@@ -169,15 +169,22 @@ def test_thick_diffusion_limit_counts_match_oracle():
         assert rel(phi.cpu().numpy(), phi_o.ravel()) < 1e-8
 
 
-def test_cycle_rejected():
+def test_cycle_rejected_without_lagging():
+    """A bowed shared face that is inflow at some points and outflow at others
+    for some S8 ordinates: with cycle lagging off it is SMM_ERR_CYCLE, with
+    lagging (the default) the handle lags it."""
     import paper_2304_07386_gb300 as P
     mesh = W.structured_mesh(2, 1, m=2, domain=(0.0, 2.0, 0.0, 1.0))
     nodes = mesh.nodes.copy()
     k = np.argmin(np.hypot(nodes[:, 0] - 1.0, nodes[:, 1] - 0.5))
     nodes[k, 0] = 1.2
+    opt = P.smm_default_options()
+    opt.cycle_lagging = 0
     with pytest.raises(P.SMMError) as ei:
-        P.smm_create(nodes, mesh.elem_nodes, 2, 1, 8, np.ones(2), np.zeros(2), np.ones((2, 4)))
+        P.smm_create(nodes, mesh.elem_nodes, 2, 1, 8, np.ones(2), np.zeros(2), np.ones((2, 4)), options=opt)
     assert ei.value.status == 5
+    h = P.smm_create(nodes, mesh.elem_nodes, 2, 1, 8, np.ones(2), np.zeros(2), np.ones((2, 4)))
+    assert h.info().n_lagged > 0
 
 
 def test_multigrid_cuts_cg_iterations():

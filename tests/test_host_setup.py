@@ -63,10 +63,13 @@ def write_inputs(tmp_path, mesh, p):
     return st, q
 
 
-def run_setup(driver, tmp_path, case):
-    """Run the host setup on a seeded curved mesh; returns (mesh, sigma_t, q, loader, dims)."""
+def run_setup(driver, tmp_path, case, strong=False):
+    """Run the host setup on a seeded curved mesh (strong: wave numbers up to 3
+    at amplitude 0.05, whose upwind graphs have cycles); returns (mesh,
+    sigma_t, q, loader, dims)."""
     nx, ny, m, p, seed = case
-    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed)
+    mesh = (W.structured_mesh(nx, ny, m=m, perturb_seed=seed, wave_max=3, scale_by_k=False) if strong
+            else W.structured_mesh(nx, ny, m=m, perturb_seed=seed))
     st, q = write_inputs(tmp_path, mesh, p)
     subprocess.run([driver, str(tmp_path), str(mesh.n_elem), str(len(mesh.nodes)), str(m), str(p)], check=True)
     n, nfq, nd, nlevels = map(int, open(tmp_path / "dims.txt").read().split())
@@ -149,15 +152,20 @@ def test_sweep_and_moment_operators_match_oracle(driver, tmp_path, case):
     assert np.max(np.abs(bfixed.ravel() - b)) <= 1e-12 * np.max(np.abs(b))
 
 
-@pytest.mark.parametrize("case", CASES + [(6, 5, 2, 1, 9)], ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4])
-def test_sweep_ordering_matches_oracle_upwind_graph(driver, tmp_path, case):
-    """Face directions from the sign of Omega_d . n at every face point; level
-    of (e, d) = 0 without upwind neighbours, else 1 + the largest level of its
-    upwind neighbours (longest path, unique); tasks = all (e, d) sorted by
-    (level, e, d), level_start the first task of each level."""
+@pytest.mark.parametrize("case,strong", [(c, False) for c in CASES + [(6, 5, 2, 1, 9)]] +
+                         [((5, 5, 2, 1, 1), True), ((6, 4, 2, 2, 4), True)],
+                         ids=lambda c: "nx%d_ny%d_m%d_p%d" % c[:4] if isinstance(c, tuple) else ("cycles" if c else "dag"))
+def test_sweep_ordering_matches_oracle_upwind_graph(driver, tmp_path, case, strong):
+    """Face directions from the sign of Omega_d . n at every face point (1
+    outflow, -1 inflow, 2 both; -2 and 3 when the inflow is lagged); the
+    faces lagged to break cycles are the oracle's (the same rule, stated in
+    oracle/transport.py); level of (e, d) = 0 without unlagged upwind
+    neighbours, else 1 + the largest level of those (longest path, unique);
+    tasks = all (e, d) sorted by (level, e, d), level_start the first task of
+    each level."""
     from oracle.transport import Discretization
     m, p = case[2], case[3]
-    mesh, st, _, load, dims = run_setup(driver, tmp_path, case)
+    mesh, st, _, load, dims = run_setup(driver, tmp_path, case, strong)
     ne, nd, nfq, nlev = mesh.n_elem, dims["nd"], dims["nfq"], dims["nlevels"]
     disc = Discretization(mesh.nodes, mesh.elem_nodes, m, p, 4, st, 0.5 * st)
     assert nd == disc.nd
@@ -167,18 +175,25 @@ def test_sweep_ordering_matches_oracle_upwind_graph(driver, tmp_path, case):
     level = load("level", (nd, ne), np.int32)
     tasks = load("tasks", (ne * nd,), np.int32)
     start = load("level_start", (nlev + 1,), np.int32)
+    n_lagged = 0
     for d in range(nd):
+        order, lagged = disc.upwind_order(d)
+        n_lagged += len(lagged)
         deps = [[] for _ in range(ne)]
         for e in range(ne):
             for f in range(4):
                 a = disc.faces[e][f]["nds"] @ disc.omega[d]
-                want = 1 if np.any(a > 0) else (-1 if np.any(a < 0) else 0)
+                pos, neg = np.any(a > 0), np.any(a < 0)
+                want = 2 if pos and neg else (1 if pos else (-1 if neg else 0))
+                if (e, f) in lagged:
+                    want = {-1: -2, 2: 3}[want]
                 assert fdir[e, d, f] == want, (e, d, f)
-                if disc.nbr[e][f] is not None and np.any(a < 0):
+                if disc.nbr[e][f] is not None and neg and (e, f) not in lagged:
                     deps[e].append(disc.nbr[e][f][0])
-        for e in disc.upwind_order(d):  # upwind neighbours first
+        for e in order:  # unlagged upwind neighbours first
             want = 1 + max(level[d, u] for u in deps[e]) if deps[e] else 0
             assert level[d, e] == want, (e, d)
+    assert (n_lagged > 0) == strong
     assert nlev == level.max() + 1
     assert np.array_equal(np.sort(tasks), np.arange(ne * nd))
     e_of, d_of = tasks // nd, tasks % nd
@@ -189,11 +204,12 @@ def test_sweep_ordering_matches_oracle_upwind_graph(driver, tmp_path, case):
         assert np.all(key[start[lv]:start[lv + 1], 0] == lv)
 
 
-def test_sign_indefinite_face_is_rejected(driver, tmp_path):
+def test_sign_indefinite_face_is_rejected_without_lagging(driver, tmp_path):
     """Two elements sharing a bowed quadratic face: its normal turns through
     the direction of some S4 ordinate, which then flows in at some face points
-    and out at others, which is not lagged but rejected: setup fails
-    with that error."""
+    and out at others.  With cycle lagging off (the driver's fourth mode
+    argument) setup fails with that error, and the oracle's ordering without
+    lagging rejects it too."""
     nodes = np.array([[0, 0], [0.5, 0], [1, 0], [0, 0.5], [0.5, 0.5], [1, 0.5], [0, 1], [0.5, 1], [1, 1],
                       [1.5, 0], [2, 0], [1.5, 0.5], [2, 0.5], [1.5, 1], [2, 1]], float)
     nodes[5] = [1.25, 0.5]  # middle node of the shared face, pushed to the right
@@ -205,15 +221,19 @@ def test_sign_indefinite_face_is_rejected(driver, tmp_path):
     mesh = Mesh()
     mesh.nodes, mesh.elem_nodes = nodes, elem
     write_inputs(tmp_path, mesh, 1)
-    r = subprocess.run([driver, str(tmp_path), "2", str(len(nodes)), "2", "1"], capture_output=True, text=True)
+    r = subprocess.run([driver, str(tmp_path), "2", str(len(nodes)), "2", "1", "nolag"], capture_output=True, text=True)
     assert r.returncode == 4
     assert "inflow at some quadrature points and outflow at others" in r.stderr
-    # the oracle rejects it too: across a mixed face each element is upwind of the other
+    # the oracle rejects it too without lagging: across a mixed face each element is upwind of the other
     from oracle.transport import CycleError, Discretization
     disc = Discretization(nodes, elem, 2, 1, 4, np.ones(2), 0.5 * np.ones(2))
     with pytest.raises(CycleError):
         for d in range(disc.nd):
-            disc.upwind_order(d)
+            disc.upwind_order(d, lag_cycles=False)
+    # with lagging both accept it
+    r = subprocess.run([driver, str(tmp_path), "2", str(len(nodes)), "2", "1"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert sum(len(disc.upwind_order(d)[1]) for d in range(disc.nd)) > 0
 
 
 @pytest.mark.parametrize("ne,m,p,sn", [

@@ -42,12 +42,15 @@ MUTATIONS = [
      'A = A + fd["V"].T @ (np.minimum(a, 0.0)[:, None] * fd["V"])', T_SWEEP),
     ("upwind_trace_of_own_element", TR, "return self.Vnb[e][f] @ psi[nb[0]]", "return self.Vnb[e][f] @ psi[e]",
      T_SWEEP),
-    ("scattering_over_2pi", TR, "scat = (self.sigma_s / (4.0 * math.pi))", "scat = (self.sigma_s / (2.0 * math.pi))",
+    ("scattering_over_2pi", TR, "return (self.sigma_s / (4.0 * math.pi))", "return (self.sigma_s / (2.0 * math.pi))",
      ["tests/test_oracle_smm.py::test_linear_fixed_point_on_curved_mesh",
       "tests/test_oracle_smm.py::test_iteration_converges_to_coupled_dense_solution"]),
     ("fixup_without_rescale", TR, "return (t / tp) * pos", "return pos", ["tests/test_oracle_fixup.py"]),
-    ("block_jacobi_not_lagged", TR, "up = self.upwind_values(e, f, d, psi_lag if lagged else psi, psibar)",
-     "up = self.upwind_values(e, f, d, psi, psibar)", ["tests/test_oracle_block_jacobi.py"]),
+    ("lagged_inflow_not_lagged", TR, "up = self.upwind_values(e, f, d, psi_lag if (e, f) in lagset else psi, psibar)",
+     "up = self.upwind_values(e, f, d, psi, psibar)",
+     ["tests/test_oracle_block_jacobi.py", "tests/test_oracle_lagging.py"]),
+    ("cycle_lagging_wrong_faces", TR, "lagged.update((v, f) for f in faces)", "lagged.update((u, f) for f in faces)",
+     ["tests/test_oracle_lagging.py"]),
     ("tensor_trace_half", CL, "pxx - phi / 3.0, pxy", "pxx - phi / 2.0, pxy", T_CLOS),
     ("beta_sign", CL, 'out[b] = B[b] - eb0(disc, nhat) * (fd["V"] @ phi[e])',
      'out[b] = B[b] + eb0(disc, nhat) * (fd["V"] @ phi[e])', T_CLOS),
