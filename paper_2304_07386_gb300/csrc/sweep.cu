@@ -523,13 +523,13 @@ __global__ void __launch_bounds__(256, INV ? (P <= 3 ? 4 : 3) : 1) sweep_kernel(
 // sorted by each problem's own upwind level, and each task dispatches on its
 // problem's order p.  The same schedule argument holds: a task's upwind tasks
 // belong to its problem, sit at lower levels and so earlier in the list.
-template <typename T, int MODE, bool INV>
+template <typename T, int MODE, bool INV, bool EXT>
 __global__ void __launch_bounds__(256, INV ? 3 : 1) batch_sweep_kernel(const SweepArgs<T>* __restrict__ args,
                                                           const int2* __restrict__ tasks, int ntask,
                                                           const int2* __restrict__ elems, int nelem) {
     const int W = (gridDim.x * blockDim.x) >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    constexpr bool EXT = sizeof(T) == 8 && MODE == SWEEP_SOURCE;  // problems may use fixup or tiles
+    // EXT: some problem uses the fixup, tiles or lagged / mixed faces
     constexpr bool DF = INV && sizeof(T) == 8;
     bool ok = true;
     for (int t = gw; t < ntask && ok; t += W) {
@@ -781,47 +781,37 @@ static int residual_grid(long long ntask) {
     return grid < 1 ? 1 : grid;
 }
 
-template <typename T, int MODE, bool INV>
-static cudaError_t launch_batch_one(const SweepArgs<T>* args, const int2* tasks, int ntask, const int2* elems,
-                                   int nelem, int grid, int block, cudaStream_t s) {
-    void* params[] = {(void*)&args, (void*)&tasks, (void*)&ntask, (void*)&elems, (void*)&nelem};
-    return cudaLaunchCooperativeKernel((const void*)batch_sweep_kernel<T, MODE, INV>, dim3(grid), dim3(block),
-                                       params, 0, s);
+// the kernel of a batch: the optional parts only when a problem uses them (FP64 source mode)
+template <typename T>
+static const void* batch_kernel_of(int mode, bool cached, bool ext) {
+    if (mode == SWEEP_SOURCE) {
+        if constexpr (sizeof(T) == 8) {
+            if (ext)
+                return cached ? (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, true, true>
+                              : (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, false, true>;
+        }
+        return cached ? (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, true, false>
+                      : (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, false, false>;
+    }
+    return cached ? (const void*)batch_sweep_kernel<T, SWEEP_RESIDUAL, true, false>
+                  : (const void*)batch_sweep_kernel<T, SWEEP_RESIDUAL, false, false>;
 }
 
 template <typename T>
-cudaError_t launch_batch_sweep(int mode, bool cached, const SweepArgs<T>* args, const int2* tasks, int ntask,
+cudaError_t launch_batch_sweep(int mode, bool cached, bool ext, const SweepArgs<T>* args, const int2* tasks, int ntask,
                                const int2* elems, int nelem, int grid, int block, cudaStream_t s) {
-    if (mode == SWEEP_SOURCE)
-        return cached ? launch_batch_one<T, SWEEP_SOURCE, true>(args, tasks, ntask, elems, nelem, grid, block, s)
-                      : launch_batch_one<T, SWEEP_SOURCE, false>(args, tasks, ntask, elems, nelem, grid, block, s);
-    return cached ? launch_batch_one<T, SWEEP_RESIDUAL, true>(args, tasks, ntask, elems, nelem, grid, block, s)
-                  : launch_batch_one<T, SWEEP_RESIDUAL, false>(args, tasks, ntask, elems, nelem, grid, block, s);
+    void* params[] = {(void*)&args, (void*)&tasks, (void*)&ntask, (void*)&elems, (void*)&nelem};
+    return cudaLaunchCooperativeKernel(batch_kernel_of<T>(mode, cached, ext), dim3(grid), dim3(block), params, 0, s);
 }
 
-template cudaError_t launch_batch_sweep<double>(int, bool, const SweepArgs<double>*, const int2*, int, const int2*,
-                                                int, int, int, cudaStream_t);
-template cudaError_t launch_batch_sweep<float>(int, bool, const SweepArgs<float>*, const int2*, int, const int2*, int,
-                                               int, int, cudaStream_t);
+template cudaError_t launch_batch_sweep<double>(int, bool, bool, const SweepArgs<double>*, const int2*, int,
+                                                const int2*, int, int, int, cudaStream_t);
+template cudaError_t launch_batch_sweep<float>(int, bool, bool, const SweepArgs<float>*, const int2*, int,
+                                               const int2*, int, int, int, cudaStream_t);
 
-int batch_blocks_per_sm(int mode, bool fp32, bool cached, int block) {
+int batch_blocks_per_sm(int mode, bool fp32, bool cached, bool ext, int block) {
     int nb = 0;
-    const void* f = nullptr;
-    if (fp32) {
-        if (mode == SWEEP_SOURCE)
-            f = cached ? (const void*)batch_sweep_kernel<float, SWEEP_SOURCE, true>
-                       : (const void*)batch_sweep_kernel<float, SWEEP_SOURCE, false>;
-        else
-            f = cached ? (const void*)batch_sweep_kernel<float, SWEEP_RESIDUAL, true>
-                       : (const void*)batch_sweep_kernel<float, SWEEP_RESIDUAL, false>;
-    } else {
-        if (mode == SWEEP_SOURCE)
-            f = cached ? (const void*)batch_sweep_kernel<double, SWEEP_SOURCE, true>
-                       : (const void*)batch_sweep_kernel<double, SWEEP_SOURCE, false>;
-        else
-            f = cached ? (const void*)batch_sweep_kernel<double, SWEEP_RESIDUAL, true>
-                       : (const void*)batch_sweep_kernel<double, SWEEP_RESIDUAL, false>;
-    }
+    const void* f = fp32 ? batch_kernel_of<float>(mode, cached, false) : batch_kernel_of<double>(mode, cached, ext);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, 0);
     return nb;
 }
