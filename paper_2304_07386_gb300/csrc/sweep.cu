@@ -277,6 +277,51 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
             }
         }
 
+        // ---- DF: each inflow face's coefficient entry (lane (a, c)) and the
+        //      index of its upwind value, formed before the wait; boundary
+        //      faces are finished here (ui = -2: cf holds coef * inflow) ----
+        float2 cf[4];
+        int ui[4];
+        unsigned lagm = 0;
+        if constexpr (DF) {
+            const int la = lane / P1, lc = lane - (lane / P1) * P1;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const int df = dir[f];
+                cf[f] = make_float2(0.0f, 0.0f);
+                ui[f] = -1;
+                if ((df < 0 || (EXT && df >= 2)) && lane < P1 * P1) {
+                    float2 coef;
+                    if (EXT && df >= 2) {
+                        coef = a.fmix2[((size_t)a.fmix_id[((size_t)e * nd + d) * 4 + f] * 2 + 1) * P1 * P1 + la * P1 + lc];
+                    } else {
+                        const size_t fo2 = ((size_t)e * 4 + f) * P1 * P1 + la * P1 + lc;
+                        const float2 fx = a.Fx2[fo2], fy = a.Fy2[fo2], o2x = a.ox2[d], o2y = a.oy2[d];
+                        float cs = 0.0f, cc = 0.0f;
+                        df_acc(cs, cc, o2x.x, o2x.y, fx.x, fx.y);
+                        df_acc(cs, cc, o2y.x, o2y.y, fy.x, fy.y);
+                        coef = df_norm(cs, cc);
+                    }
+                    cf[f] = coef;
+                    const int nb = a.nbr[e * 4 + f];
+                    if (nb >= 0) {
+                        const int f2 = a.nbr_face[e * 4 + f];
+                        const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
+                        const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
+                        ui[f] = (int)(((size_t)nb * nd + d) * N + node);
+                        if (EXT && (df == -2 || df == 3)) lagm |= 1u << f;
+                    } else if (MODE == SWEEP_SOURCE && a.inflow2) {
+                        const int bi = a.bface_id[e * 4 + f];
+                        const float2 u = a.inflow2[((size_t)bi * nd + d) * P1 + lc];
+                        float ts = 0.0f, tc = 0.0f;
+                        df_acc(ts, tc, coef.x, coef.y, u.x, u.y);
+                        cf[f] = df_norm(ts, tc);
+                        ui[f] = -2;
+                    }
+                }
+            }
+        }
+
         // ---- wait for the upwind neighbours (lane f waits on face f) ----
         bool ok = true;
         if (lane < 4) {
@@ -319,6 +364,14 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
             b = (T)a.rhs[((size_t)e * nd + d) * N + row];
         }
 
+        // DF: every inflow face's upwind value, loaded together
+        float2 up[4];
+        if constexpr (DF) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                up[f] = ui[f] >= 0 ? __ldcg((EXT && ((lagm >> f) & 1u) ? a.psi2_lag : a.psi2) + ui[f])
+                                   : make_float2(0.0f, 0.0f);
+        }
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             const int df = dir[f];
@@ -338,38 +391,17 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                 }
             }
             if (DF && (df < 0 || (EXT && df >= 2))) {
-                // inflow face in pairs: lane (a, c) forms coef[a][c] u[c] with
-                // coef = Omega_x Fx + Omega_y Fy, the p+1 lanes of group a sum
-                // over c, and every row adds -A^{-1}[row][node(f, a)] v_a
-                const int la = lane / P1, lc = lane - (lane / P1) * P1;
-                float ts = 0.0f, tc = 0.0f;
-                if (lane < P1 * P1) {
-                    float2 coef;
-                    if (EXT && df >= 2) {
-                        // mixed face: the inflow part of its pointwise face matrix
-                        coef = a.fmix2[((size_t)a.fmix_id[((size_t)e * nd + d) * 4 + f] * 2 + 1) * P1 * P1 + la * P1 + lc];
-                    } else {
-                        const size_t fo2 = ((size_t)e * 4 + f) * P1 * P1 + la * P1 + lc;
-                        const float2 fx = a.Fx2[fo2], fy = a.Fy2[fo2], o2x = a.ox2[d], o2y = a.oy2[d];
-                        float cs = 0.0f, cc = 0.0f;
-                        df_acc(cs, cc, o2x.x, o2x.y, fx.x, fx.y);
-                        df_acc(cs, cc, o2y.x, o2y.y, fy.x, fy.y);
-                        coef = df_norm(cs, cc);
-                    }
-                    const int nb = a.nbr[e * 4 + f];
-                    float2 u = make_float2(0.0f, 0.0f);
-                    if (nb >= 0) {
-                        const int f2 = a.nbr_face[e * 4 + f];
-                        const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
-                        const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
-                        u = __ldcg((EXT && (df == -2 || df == 3) ? a.psi2_lag : a.psi2) + ((size_t)nb * nd + d) * N + node);
-                    } else if (MODE == SWEEP_SOURCE && a.inflow2) {
-                        const int bi = a.bface_id[e * 4 + f];
-                        u = a.inflow2[((size_t)bi * nd + d) * P1 + lc];
-                    }
-                    df_acc(ts, tc, coef.x, coef.y, u.x, u.y);
+                // inflow face in pairs: lane (a, c) forms coef[a][c] u[c], the
+                // p+1 lanes of group a sum over c, and every row adds
+                // -A^{-1}[row][node(f, a)] v_a
+                float2 t;
+                if (ui[f] == -2) {
+                    t = cf[f];
+                } else {
+                    float ts = 0.0f, tc = 0.0f;
+                    df_acc(ts, tc, cf[f].x, cf[f].y, up[f].x, up[f].y);
+                    t = df_norm(ts, tc);
                 }
-                const float2 t = df_norm(ts, tc);
                 float vs = t.x, vc = t.y;
 #pragma unroll
                 for (int k = 1; k < P1; ++k)
@@ -491,7 +523,9 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
             else a.psi[o] = x;
             if (MODE == SWEEP_RESIDUAL) a.psi_acc[o] += (double)x;
         }
-        __threadfence();  // one warp-wide fence instruction orders every lane's stores
+        // the warp barrier orders every lane's stores before lane 0's release
+        // store, whose release semantics make them visible to whoever acquires
+        // the flag (no separate full fence: it cost 8 % of the sweep)
         __syncwarp();
         if (lane == 0) st_release(a.done + task, a.epoch);
     }
