@@ -235,17 +235,28 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         //      loaded before the wait, so HBM latency overlaps the wavefront ----
         // FP64 cached mode keeps the inverse as FP32 pairs and forms
         // y0 = A^{-1} b_pre (the part of the solution without upwind data)
-        // before the wait; after it only the inflow-face columns are added
+        // before the wait; after it only the inflow-face columns are added.
+        // With n <= 16 the warp's lanes form KG = 32 / n groups of n rows;
+        // group g holds columns [g CPG, (g + 1) CPG) of its row of A^{-1} and
+        // accumulates their terms, and the groups' partial sums are added in
+        // group order at the end (p = 4: one group, the plain row per lane).
         constexpr bool DF = INV && sizeof(T) == 8;
+        constexpr int KG = DF ? 32 / N : 1, CPG = (N + KG - 1) / KG;
+        // one group: lanes >= n shadow row 0, as in the other modes
+        const int dgrp = KG == 1 ? 0 : (lane < KG * N ? lane / N : KG);  // KG: no columns
+        const int drow = KG == 1 ? row : (lane < KG * N ? lane - (lane / N) * N : 0);
         T Ainv[(INV && !DF) ? N : 1];
-        float2 Adf[DF ? N : 1];
+        float2 Adf[DF ? CPG : 1];
         T bpre = 0;
-        float ys = 0.0f, yc = 0.0f;  // DF: running pair sum of x
+        float ys = 0.0f, yc = 0.0f;  // DF: running pair sum of this lane's columns' terms
         if (INV) {
             if constexpr (DF) {
-                const float2* Ai = a.ainv_df + (size_t)task * N * N + row;
+                const float2* Ai = a.ainv_df + (size_t)task * N * N + drow;
 #pragma unroll
-                for (int j = 0; j < N; ++j) Adf[j] = Ai[(size_t)j * N];
+                for (int jj = 0; jj < CPG; ++jj) {
+                    const int j = dgrp * CPG + jj;
+                    Adf[jj] = KG == 1 || j < N ? Ai[(size_t)j * N] : make_float2(0.0f, 0.0f);
+                }
             } else {
                 const T* Ai = a.ainv + (size_t)task * N * N + row;
 #pragma unroll
@@ -265,9 +276,12 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                 } else {
                     bp = make_float2(a.rhs[((size_t)e * nd + d) * N + row], 0.0f);
                 }
+                // (a zero entry adds an exact zero: the sums are unchanged)
 #pragma unroll
-                for (int j = 0; j < N; ++j)
-                    df_acc(ys, yc, Adf[j].x, Adf[j].y, __shfl_sync(FULL, bp.x, j), __shfl_sync(FULL, bp.y, j));
+                for (int jj = 0; jj < CPG; ++jj) {
+                    const int j = KG == 1 ? jj : min(dgrp * CPG + jj, N - 1);
+                    df_acc(ys, yc, Adf[jj].x, Adf[jj].y, __shfl_sync(FULL, bp.x, j), __shfl_sync(FULL, bp.y, j));
+                }
             } else if (MODE == SWEEP_SOURCE) {
                 double bs = a.msrc[(size_t)e * N + row];
                 if (a.mq) bs += a.mq[((size_t)e * nd + d) * N + row];
@@ -409,7 +423,9 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                 const float2 v = df_norm(vs, vc);
 #pragma unroll
                 for (int aa = 0; aa < P1; ++aa) {
-                    const float2 col = Adf[face_node<P>(f, aa)];
+                    const int cn = face_node<P>(f, aa);
+                    const float2 col =
+                        KG == 1 ? Adf[cn] : (cn / CPG == dgrp ? Adf[cn % CPG] : make_float2(0.0f, 0.0f));
                     df_acc(ys, yc, -col.x, -col.y, __shfl_sync(FULL, v.x, aa * P1), __shfl_sync(FULL, v.y, aa * P1));
                 }
             } else if (df < 0 || (EXT && df >= 2)) {
@@ -449,6 +465,15 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         T x = 0;
         if (INV) {
             if constexpr (DF) {
+                if constexpr (KG > 1) {
+                    // the row's full sum: its groups' partial sums in group order
+                    float ts = __shfl_sync(FULL, ys, drow), tc = __shfl_sync(FULL, yc, drow);
+#pragma unroll
+                    for (int g = 1; g < KG; ++g)
+                        df_add(ts, tc, __shfl_sync(FULL, ys, drow + g * N), __shfl_sync(FULL, yc, drow + g * N));
+                    ys = ts;
+                    yc = tc;
+                }
                 x = (T)((double)ys + (double)yc);
             } else {
                 // ---- cached inverse: x = A^{-1} b ----
@@ -536,13 +561,13 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
 // t mod W, so each warp meets its tasks in level order; with every warp
 // co-resident (cooperative launch) the task a warp waits for is owned by a
 // running warp that reaches it after finishing only earlier-level tasks.
-// Cached-inverse sweeps: at least three blocks per SM (four for p <= 3, whose
-// tasks hold fewer inverse entries per lane).  They are bound by the latency
+// Cached-inverse sweeps: at least three blocks per SM (five for p <= 3, whose
+// lanes hold at most eight inverse entries each in column groups).  They are bound by the latency
 // of each task's chain of dependent loads, so resident warps set their
 // throughput; the moment reduction after the tasks takes any register spills.
 // (The in-register LU keeps its registers: it is bound by its FP64 arithmetic.)
 template <typename T, int P, int MODE, bool INV, bool EXT>
-__global__ void __launch_bounds__(256, INV ? (P <= 3 ? 4 : 3) : 1) sweep_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(256, INV ? (P <= 3 ? 5 : 3) : 1) sweep_kernel(SweepArgs<T> a) {
     constexpr bool DF = INV && sizeof(T) == 8;
     const int W = (gridDim.x * blockDim.x) >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
