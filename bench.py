@@ -470,6 +470,8 @@ def run_ours(args) -> None:
     if not args.quick:
         extra.update(run_extras(args, P, torch, stream, create, step, phi, flush, ms_sweep))
     h.destroy()
+    if args.batch_full > 0:
+        extra["batched_full"] = run_batch_full(stream, args.batch_full)
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -690,6 +692,90 @@ def run_batch(nprob: int, stream) -> dict:
                                      "with its source kernel, sweep kernel and one host sync); best of 3")
 
 
+def batch_full_problem(seed: int):
+    """One problem of the uneven batched-instances workload at its full size:
+    n ~ U{32..192}, p ~ U{1..4}, S_N ~ U{4,6,8,10,12}, sigma_t = 10 exp(1.5 g)
+    with g a unit Gaussian random field (correlation length 0.1), c ~
+    U[0.5, 0.99], q = 1 per steradian, vacuum, straight mesh."""
+    import numpy as np
+
+    import smm_workloads as W
+
+    rng = np.random.default_rng(5000 + seed)
+    nx = int(rng.integers(32, 193))
+    p = int(rng.integers(1, 5))
+    sn = int(rng.choice([4, 6, 8, 10, 12]))
+    c = float(rng.uniform(0.5, 0.99))
+    mesh = W.structured_mesh(nx, m=1)
+    st = 10.0 * np.exp(1.5 * W.gaussian_random_field(nx, 0.1, 5000 + seed))
+    return mesh, p, sn, st, c * st, np.ones((mesh.n_elem, (p + 1) ** 2))
+
+
+def run_batch_full(stream, nprob: int = 256, wave_bytes: float = 150e9) -> dict:
+    """All nprob uneven problems solved to a 1e-8 relative successive
+    difference with the default FP64-accuracy method (cached pair inverses,
+    multigrid CG).  Their cached inverses together exceed the GPU's memory, so
+    the problems go in waves whose estimated device footprint stays below
+    wave_bytes; each wave is created, iterated as one batch (one sweep launch
+    per outer step for all its problems) and destroyed."""
+    import numpy as np
+    import torch
+
+    import paper_2304_07386_gb300 as P
+
+    def footprint(nx, p, sn):
+        n, nd, ne = (p + 1) ** 2, sn * (sn + 2) // 2, nx * nx
+        return ne * nd * (8 * n * n + 8 * n + 16) + ne * 48 * 1024
+
+    specs = []
+    for i in range(nprob):
+        rng = np.random.default_rng(5000 + i)
+        nx, p = int(rng.integers(32, 193)), int(rng.integers(1, 5))
+        sn = int(rng.choice([4, 6, 8, 10, 12]))
+        specs.append((i, footprint(nx, p, sn)))
+    waves, cur, used = [], [], 0.0
+    for i, b in specs:
+        if cur and used + b > wave_bytes:
+            waves.append(cur)
+            cur, used = [], 0.0
+        cur.append(i)
+        used += b
+    waves.append(cur)
+    total_unknowns, t_setup, t_iter, outer, converged = 0, 0.0, 0.0, [], 0
+    for wave in waves:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs = []
+        for i in wave:
+            mesh, p, sn, st, ss, q = batch_full_problem(i)
+            opt = P.smm_default_options()
+            opt.tol_cg = 1e-12
+            hs.append(P.smm_create(mesh.nodes, mesh.elem_nodes, 1, p, sn, st, ss, q, options=opt, stream=stream))
+        b = P.smm.smm_batch_create(hs)
+        phis = [torch.zeros(h.info().n_elem * h.info().n_dof_elem, dtype=torch.float64, device="cuda") for h in hs]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            rc, stats = P.smm.smm_batch_iterate(b, phis, 1e-8, 300, relative=True)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        t_setup += t1 - t0
+        t_iter += t2 - t1
+        for h, s_ in zip(hs, stats):
+            total_unknowns += h.info().n_angular
+            outer.append(s_["outer_iterations"])
+            converged += int(s_["last_rel_diff"] <= 1e-8)
+        b.destroy()
+        for h in hs:
+            h.destroy()
+        del phis
+        torch.cuda.empty_cache()
+    return dict(problems=nprob, waves=len(waves), problems_per_wave=[len(w) for w in waves],
+                angular_unknowns_per_sweep=total_unknowns, setup_s=t_setup, iterate_s=t_iter,
+                outer_mean=float(np.mean(outer)), outer_max=int(max(outer)), converged=converged,
+                note="time to a 1e-8 relative difference for every problem, batched per wave (setup excluded)")
+
+
 def run_learned(nx: int, stream, n_train: int = 192, n_test: int = 16, p: int = 2, sn: int = 8) -> dict:
     """Learned-guess workload (p=2, S8, log-normal sigma_t / sigma_s fields,
     piecewise-constant source maps, on an nx*nx grid of quads): train the
@@ -877,6 +963,9 @@ def main():
     ap.add_argument("--no-cfg2", dest="cfg2", action="store_false", help="skip the curved MMS workload")
     ap.add_argument("--batch", type=int, default=24, help="problems in the batched-sweep measurement (0: skip)")
     ap.add_argument("--learned", type=int, default=64, help="element grid of the learned-guess measurement (0: skip)")
+    ap.add_argument("--batch-full", type=int, default=0,
+                    help="problems of the full-size uneven batched workload solved to 1e-8 in memory-sized waves "
+                         "(opt-in: about ten minutes for 256)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
