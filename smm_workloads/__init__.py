@@ -88,6 +88,7 @@ class StructuredMesh:
     nodes: np.ndarray            # [n_nodes][2] float64
     elem_nodes: np.ndarray       # [n_elem][(m+1)^2] int32
     perturb: tuple = field(default=())  # ((ax,k1,k2),(ay,k3,k4)) or ()
+    fan: float = 0.0             # x spread factor at the top edge (see structured_mesh)
 
     @property
     def n_elem(self) -> int:
@@ -95,13 +96,17 @@ class StructuredMesh:
 
     def map(self, x: np.ndarray, y: np.ndarray):
         """The analytic node map applied to straight-grid positions."""
-        if not self.perturb:
-            return x, y
-        (ax, k1, k2), (ay, k3, k4) = self.perturb
         xt = (x - self.x0) / (self.x1 - self.x0)
         yt = (y - self.y0) / (self.y1 - self.y0)
-        xm = x + ax * np.sin(math.pi * k1 * xt) * np.sin(math.pi * k2 * yt)
-        ym = y + ay * np.sin(math.pi * k3 * xt) * np.sin(math.pi * k4 * yt)
+        if self.perturb:
+            (ax, k1, k2), (ay, k3, k4) = self.perturb
+            xm = x + ax * np.sin(math.pi * k1 * xt) * np.sin(math.pi * k2 * yt)
+            ym = y + ay * np.sin(math.pi * k3 * xt) * np.sin(math.pi * k4 * yt)
+        else:
+            xm, ym = x, y
+        if self.fan:
+            xc = 0.5 * (self.x0 + self.x1)
+            xm = xc + (xm - xc) * (1.0 + self.fan * yt)
         return xm, ym
 
 
@@ -123,7 +128,8 @@ def _perturbation(seed: int, lx: float, ly: float, amplitude: float, wave_max: i
 
 def structured_mesh(nx: int, ny: int | None = None, m: int = 1,
                     domain=(0.0, 1.0, 0.0, 1.0), *, perturb_seed: int | None = None,
-                    amplitude: float = 0.05, wave_max: int = 2, scale_by_k: bool = True) -> StructuredMesh:
+                    amplitude: float = 0.05, wave_max: int = 2, scale_by_k: bool = True,
+                    fan: float = 0.0) -> StructuredMesh:
     """Structured quad mesh with control points on GLL nodes of order ``m``.
 
     With ``perturb_seed`` the straight grid is moved by the seeded
@@ -133,6 +139,10 @@ def structured_mesh(nx: int, ny: int | None = None, m: int = 1,
     mesh continuous.  wave_max = 3, scale_by_k = False gives wave numbers in
     {1, 2, 3} at amplitude a_x = amplitude * (x1 - x0), whose tilted faces can
     be inflow at some points and outflow at others for grazing ordinates.
+    fan > 0 then spreads the columns as y grows, x' = x_c + (x - x_c)(1 + fan y~)
+    (x_c the centre; bilinear, so exact at any geometry order): the elements
+    become trapezoids that widen upwards, and an ordinate pointing up enters
+    them through three straight faces.
     """
     ny = nx if ny is None else ny
     x0, x1, y0, y1 = map(float, domain)
@@ -150,7 +160,7 @@ def structured_mesh(nx: int, ny: int | None = None, m: int = 1,
     X, Y = np.meshgrid(xs, ys, indexing="xy")  # [nyn][nxn]
     pert = (_perturbation(perturb_seed, x1 - x0, y1 - y0, amplitude, wave_max, scale_by_k)
             if perturb_seed is not None else ())
-    mesh = StructuredMesh(nx, ny, m, x0, x1, y0, y1, np.zeros((0, 2)), np.zeros((0, 0), np.int32), pert)
+    mesh = StructuredMesh(nx, ny, m, x0, x1, y0, y1, np.zeros((0, 2)), np.zeros((0, 0), np.int32), pert, float(fan))
     Xm, Ym = mesh.map(X, Y)
     nodes = np.stack([Xm.ravel(), Ym.ravel()], axis=1).astype(np.float64)
     en = np.empty((nx * ny, (m + 1) ** 2), dtype=np.int32)

@@ -11,9 +11,10 @@ import numpy as np
 import smm_workloads as W
 
 
-def problem(nx, ny=None, m=1, p=1, sn=4, seed=None, sigt=1.0, c=0.5, kind="mms", domain=(0.0, 1.0, 0.0, 1.0)):
+def problem(nx, ny=None, m=1, p=1, sn=4, seed=None, sigt=1.0, c=0.5, kind="mms", domain=(0.0, 1.0, 0.0, 1.0),
+            fan=0.0):
     ny = nx if ny is None else ny
-    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed, domain=domain)
+    mesh = W.structured_mesh(nx, ny, m=m, perturb_seed=seed, domain=domain, fan=fan)
     ne = mesh.n_elem
     st = np.broadcast_to(np.asarray(sigt, float), (ne,)).copy()
     ss = st * c

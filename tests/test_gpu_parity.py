@@ -95,6 +95,34 @@ def test_sweep_and_moments_fp64(case, solver):
     assert np.max(np.abs(beta.cpu().numpy().reshape(beta_o.shape) - beta_o)) < 1e-11 * np.max(np.abs(mom_o[0]))
 
 
+@pytest.mark.parametrize("solver", [0, 1], ids=["lu", "cached_inverse"])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_sweep_with_three_inflow_faces_on_a_fan_mesh(p, solver):
+    """Trapezoids widening upwards: ordinates pointing up enter some elements
+    through three faces.  Flux and moments against the oracle at 1e-11, as
+    above."""
+    import paper_2304_07386_gb300 as P
+    from oracle import closures
+    prob = problem(5, 4, m=1, p=p, sn=8, kind="mms", c=0.6, fan=1.5)
+    h = make_gpu(prob, sweep_solver=solver)
+    disc, op, q, inflow = make_oracle(prob)
+    assert any(sum(bool(np.all(disc.faces[e][f]["nds"] @ disc.omega[d] < 0.0)) for f in range(4)) == 3
+               for e in range(disc.ne) for d in range(disc.nd))
+    phi = W.mms_phi(prob["pos"][:, :, 0], prob["pos"][:, :, 1])
+    P.smm_sweep(h, dev(phi))
+    info = h.info()
+    psi_g = torch.zeros(info.n_elem * info.n_ord * info.n_dof_elem, dtype=torch.float64, device="cuda")
+    P.smm_get_psi(h, psi_g)
+    psi_g = psi_g.cpu().numpy().reshape(info.n_elem, info.n_ord, info.n_dof_elem).transpose(1, 0, 2)
+    psi_o = disc.sweep(phi, q, inflow)
+    assert rel(psi_g, psi_o) < 1e-11
+    mom = torch.zeros(6 * info.n_elem * info.n_dof_elem, dtype=torch.float64, device="cuda")
+    P.smm_moments(h, mom)
+    mom_o = closures.nodal_moments(disc, psi_o)
+    assert np.max(np.abs(mom.cpu().numpy().reshape(6, info.n_elem, -1) - mom_o)) < 1e-11 * np.max(np.abs(mom_o[0]))
+    h.destroy()
+
+
 @pytest.mark.parametrize("precond", [0, 1], ids=["block_jacobi", "multigrid"])
 @pytest.mark.parametrize("case", CASES[:4] + [(12, 9, 2, 2, 4, 4, "mms")], ids=lambda c: "x".join(map(str, c[:5])))
 def test_moment_solve_fp64(case, precond):

@@ -237,14 +237,14 @@ SWEEP_CASES = [(3, 2, 1, 1, 4, None, "iso"), (2, 3, 2, 2, 4, 4, "mms"), (3, 3, 3
                (2, 2, 3, 4, 4, 2, "mms"), (1, 1, 1, 2, 8, None, "iso"), (5, 1, 2, 1, 8, 3, "mms")]
 
 
-def _sweep_problem(case, sig=None, strip_light=False, strong=False):
+def _sweep_problem(case, sig=None, strip_light=False, strong=False, fan=0.0):
     """Mesh, cross sections, the oracle's discretization, varphi, q and inflow
     of one sweep case (isotropic q with vacuum boundaries, or the manufactured
     angular source with its inflow, or a strip lit from the left face)."""
     from oracle.transport import Discretization
     nx, ny, m, p, sn, seed, kind = case
     mesh = (W.structured_mesh(nx, ny, m=m, perturb_seed=seed, wave_max=3, scale_by_k=False) if strong
-            else W.structured_mesh(nx, ny, m=m, perturb_seed=seed))
+            else W.structured_mesh(nx, ny, m=m, perturb_seed=seed, fan=fan))
     ne, n = mesh.n_elem, (p + 1) ** 2
     st = np.full(ne, sig) if sig is not None else 1.0 + 0.5 * (np.arange(ne) % 3)
     ss = (0.0 if strip_light else 0.6) * st
@@ -312,6 +312,25 @@ def test_sweep_kernel_matches_oracle(sweep_emu, tmp_path, case):
     disc, phi, q, inflow, got = _run_sweep_emu(sweep_emu, tmp_path, case)
     ref_nd = disc.sweep(phi, q, inflow)
     ref = ref_nd.transpose(1, 0, 2)   # [ne][nd][n], the device layout
+    scale = np.max(np.abs(ref))
+    for name, psi in got.items():
+        assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
+    _check_fused_moments(disc, ref_nd)
+
+
+@pytest.mark.parametrize("case", [(4, 3, 1, 1, 8, None, "mms"), (3, 3, 2, 2, 12, None, "mms"),
+                                  (4, 2, 1, 3, 8, None, "iso")], ids=lambda c: "nx%d_ny%d_m%d_p%d_S%d_%s" % (c[:5] + c[6:]))
+def test_sweep_kernel_takes_three_inflow_faces(sweep_emu, tmp_path, case):
+    """On a fan mesh (trapezoids that widen upwards) an ordinate pointing up
+    enters some elements through three straight faces (two is the rule on
+    meshes of nearly parallel faces); the sweep and its moments must still
+    equal the oracle's."""
+    disc, phi, q, inflow, got = _run_sweep_emu(sweep_emu, tmp_path, case, fan=1.5)
+    three = sum(1 for e in range(disc.ne) for d in range(disc.nd)
+                if sum(bool(np.all(disc.faces[e][f]["nds"] @ disc.omega[d] < 0.0)) for f in range(4)) == 3)
+    assert three > 0
+    ref_nd = disc.sweep(phi, q, inflow)
+    ref = ref_nd.transpose(1, 0, 2)
     scale = np.max(np.abs(ref))
     for name, psi in got.items():
         assert np.max(np.abs(psi - ref)) <= 1e-12 * scale, (name, np.max(np.abs(psi - ref)) / scale)
