@@ -741,7 +741,7 @@ def run_batch_full(stream, nprob: int = 256, wave_bytes: float = 150e9) -> dict:
         cur.append(i)
         used += b
     waves.append(cur)
-    total_unknowns, t_setup, t_iter, outer, converged = 0, 0.0, 0.0, [], 0
+    total_unknowns, t_setup, t_iter, outer, converged, statuses = 0, 0.0, 0.0, [], 0, []
     for wave in waves:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -755,14 +755,20 @@ def run_batch_full(stream, nprob: int = 256, wave_bytes: float = 150e9) -> dict:
         phis = [torch.zeros(h.info().n_elem * h.info().n_dof_elem, dtype=torch.float64, device="cuda") for h in hs]
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            rc, stats = P.smm.smm_batch_iterate(b, phis, 1e-8, 300, relative=True)
+        status = 0
+        try:
+            with torch.cuda.stream(stream):
+                stats = P.smm.smm_batch_iterate(b, phis, 1e-8, 300, relative=True)
+        except P.smm.SMMError as ex:  # e.g. a problem not converged in 300 steps
+            status, stats = ex.status, []
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         t_setup += t1 - t0
         t_iter += t2 - t1
-        for h, s_ in zip(hs, stats):
+        statuses.append(status)
+        for h in hs:
             total_unknowns += h.info().n_angular
+        for s_ in stats:
             outer.append(s_["outer_iterations"])
             converged += int(s_["last_rel_diff"] <= 1e-8)
         b.destroy()
@@ -772,7 +778,8 @@ def run_batch_full(stream, nprob: int = 256, wave_bytes: float = 150e9) -> dict:
         torch.cuda.empty_cache()
     return dict(problems=nprob, waves=len(waves), problems_per_wave=[len(w) for w in waves],
                 angular_unknowns_per_sweep=total_unknowns, setup_s=t_setup, iterate_s=t_iter,
-                outer_mean=float(np.mean(outer)), outer_max=int(max(outer)), converged=converged,
+                outer_mean=float(np.mean(outer)) if outer else None, outer_max=max(outer) if outer else None,
+                converged=converged, wave_status=statuses,
                 note="time to a 1e-8 relative difference for every problem, batched per wave (setup excluded)")
 
 
