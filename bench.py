@@ -572,7 +572,7 @@ def run_extras(args, P, torch, stream, create, step, phi, flush, ms_sweep_defaul
     if args.batch > 0:
         extra["batched_sweep"] = run_batch(args.batch, stream)
     if args.learned > 0:
-        extra["learned_guess"] = run_learned(args.learned, stream)
+        extra["learned_guess"] = run_learned(args.learned, stream, args.learned_train, args.learned_test)
     return extra
 
 
@@ -970,6 +970,8 @@ def main():
     ap.add_argument("--no-cfg2", dest="cfg2", action="store_false", help="skip the curved MMS workload")
     ap.add_argument("--batch", type=int, default=24, help="problems in the batched-sweep measurement (0: skip)")
     ap.add_argument("--learned", type=int, default=64, help="element grid of the learned-guess measurement (0: skip)")
+    ap.add_argument("--learned-train", type=int, default=192, help="training problems of the learned guess")
+    ap.add_argument("--learned-test", type=int, default=16, help="held-out problems of the learned guess")
     ap.add_argument("--batch-full", type=int, default=0,
                     help="problems of the full-size uneven batched workload solved to 1e-8 in memory-sized waves "
                          "(opt-in: about ten minutes for 256)")
