@@ -1366,6 +1366,7 @@ struct smm_batch_ctx {
     int2* tasks = nullptr;
     int2* elems = nullptr;          // (problem, element) of every element of every problem
     bool ext = false;               // some problem uses the fixup, tiles or lagged / mixed faces
+    int pmax = 1;                   // the largest order p of the batch
     void* args_dev = nullptr;
     void* args_host = nullptr;  // pinned
     size_t args_bytes = 0;
@@ -1397,7 +1398,7 @@ smm_status batch_enqueue(smm_batch b, const double* const* phis) {
         host[i].gate = b->gate;  // one gate for the whole launch
     }
     SMM_CUDA(cudaMemcpyAsync(b->args_dev, b->args_host, b->args_bytes, cudaMemcpyHostToDevice, b->stream));
-    SMM_CUDA(smm::launch_batch_sweep<T>(b->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE, b->cached, b->ext,
+    SMM_CUDA(smm::launch_batch_sweep<T>(b->fp32 ? smm::SWEEP_RESIDUAL : smm::SWEEP_SOURCE, b->cached, b->ext, b->pmax,
                                          static_cast<const smm::SweepArgs<T>*>(b->args_dev), b->tasks, b->ntask,
                                          b->elems, b->nelem, b->grid, b->block, b->stream));
     b->hs[0]->launches += 1;
@@ -1439,8 +1440,10 @@ smm_status smm_batch_create(int32_t n, const smm_handle* handles, smm_batch* out
     auto* b = new smm_batch_ctx();
     auto bail = [&](smm_status st, const std::string& msg) { delete b; return fail(st, msg); };
     b->hs.assign(handles, handles + n);
-    for (smm_handle h : b->hs)
+    for (smm_handle h : b->hs) {
         b->ext |= h->opt.negative_flux_fixup || h->lagging || h->fmix_id != nullptr;
+        b->pmax = std::max(b->pmax, h->p);
+    }
     b->fp32 = h0->fp32;
     b->cached = h0->cached;
     b->stream = h0->stream;
@@ -1480,7 +1483,7 @@ smm_status smm_batch_create(int32_t n, const smm_handle* handles, smm_batch* out
     double best = 1e300;
     int best_grid = 1, best_block = 256;
     for (int block : {256, 128}) {
-        const int bps = smm::batch_blocks_per_sm(mode, b->fp32, b->cached, b->ext, block);
+        const int bps = smm::batch_blocks_per_sm(mode, b->fp32, b->cached, b->ext, b->pmax, block);
         if (bps < 1) continue;
         for (int frac : {1, 2}) {
             const long long want = ((long long)b->ntask * 32 + block - 1) / block;

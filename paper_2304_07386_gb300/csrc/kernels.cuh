@@ -122,10 +122,11 @@ void launch_sweep(int p, int mode, const SweepArgs<T>& a, int grid, cudaStream_t
 // many problems in one cooperative launch; tasks: (problem, task) pairs sorted by level; elems:
 // (problem, element) of every element of every problem
 // ext: some problem uses the fixup, tiles or lagged / mixed faces (the kernel with those parts compiled in)
+// pmax: the largest order p among the batch's problems
 template <typename T>
-cudaError_t launch_batch_sweep(int mode, bool cached, bool ext, const SweepArgs<T>* args, const int2* tasks, int ntask,
-                               const int2* elems, int nelem, int grid, int block, cudaStream_t s);
-int batch_blocks_per_sm(int mode, bool fp32, bool cached, bool ext, int block);
+cudaError_t launch_batch_sweep(int mode, bool cached, bool ext, int pmax, const SweepArgs<T>* args, const int2* tasks,
+                               int ntask, const int2* elems, int nelem, int grid, int block, cudaStream_t s);
+int batch_blocks_per_sm(int mode, bool fp32, bool cached, bool ext, int pmax, int block);
 // form every local inverse A_{K,d}^{-1} (column-major, type T) in ainv_out
 template <typename T>
 void launch_invert(int p, const SweepArgs<T>& a, T* ainv_out, cudaStream_t s);

@@ -582,8 +582,10 @@ __global__ void __launch_bounds__(256, INV ? (P <= 3 ? 5 : 3) : 1) sweep_kernel(
 // sorted by each problem's own upwind level, and each task dispatches on its
 // problem's order p.  The same schedule argument holds: a task's upwind tasks
 // belong to its problem, sit at lower levels and so earlier in the list.
-template <typename T, int MODE, bool INV, bool EXT>
-__global__ void __launch_bounds__(256, INV ? 3 : 1) batch_sweep_kernel(const SweepArgs<T>* __restrict__ args,
+// PMAX: the largest order in the batch (3: the p = 4 path is not compiled in,
+// so the kernel takes the registers of p <= 3 and five blocks per SM).
+template <typename T, int MODE, bool INV, bool EXT, int PMAX>
+__global__ void __launch_bounds__(256, INV ? (PMAX <= 3 ? 5 : 3) : 1) batch_sweep_kernel(const SweepArgs<T>* __restrict__ args,
                                                           const int2* __restrict__ tasks, int ntask,
                                                           const int2* __restrict__ elems, int nelem) {
     const int W = (gridDim.x * blockDim.x) >> 5;
@@ -598,7 +600,9 @@ __global__ void __launch_bounds__(256, INV ? 3 : 1) batch_sweep_kernel(const Swe
             case 1: ok = sweep_task<T, 1, MODE, INV, EXT>(a, it.y); break;
             case 2: ok = sweep_task<T, 2, MODE, INV, EXT>(a, it.y); break;
             case 3: ok = sweep_task<T, 3, MODE, INV, EXT>(a, it.y); break;
-            default: ok = sweep_task<T, 4, MODE, INV, EXT>(a, it.y); break;
+            default:
+                if constexpr (PMAX >= 4) ok = sweep_task<T, 4, MODE, INV, EXT>(a, it.y);
+                break;
         }
     }
     if (!args[0].mom) return;
@@ -611,7 +615,9 @@ __global__ void __launch_bounds__(256, INV ? 3 : 1) batch_sweep_kernel(const Swe
             case 1: element_moments<T, 1, DF>(b, pe.y); break;
             case 2: element_moments<T, 2, DF>(b, pe.y); break;
             case 3: element_moments<T, 3, DF>(b, pe.y); break;
-            default: element_moments<T, 4, DF>(b, pe.y); break;
+            default:
+                if constexpr (PMAX >= 4) element_moments<T, 4, DF>(b, pe.y);
+                break;
         }
     }
 }
@@ -840,37 +846,45 @@ static int residual_grid(long long ntask) {
     return grid < 1 ? 1 : grid;
 }
 
-// the kernel of a batch: the optional parts only when a problem uses them (FP64 source mode)
-template <typename T>
-static const void* batch_kernel_of(int mode, bool cached, bool ext) {
+// the kernel of a batch: the optional parts only when a problem uses them (FP64 source mode), the p = 4
+// path only when a problem has p = 4
+template <typename T, int PMAX>
+static const void* batch_kernel_pm(int mode, bool cached, bool ext) {
     if (mode == SWEEP_SOURCE) {
         if constexpr (sizeof(T) == 8) {
             if (ext)
-                return cached ? (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, true, true>
-                              : (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, false, true>;
+                return cached ? (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, true, true, PMAX>
+                              : (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, false, true, PMAX>;
         }
-        return cached ? (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, true, false>
-                      : (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, false, false>;
+        return cached ? (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, true, false, PMAX>
+                      : (const void*)batch_sweep_kernel<T, SWEEP_SOURCE, false, false, PMAX>;
     }
-    return cached ? (const void*)batch_sweep_kernel<T, SWEEP_RESIDUAL, true, false>
-                  : (const void*)batch_sweep_kernel<T, SWEEP_RESIDUAL, false, false>;
+    return cached ? (const void*)batch_sweep_kernel<T, SWEEP_RESIDUAL, true, false, PMAX>
+                  : (const void*)batch_sweep_kernel<T, SWEEP_RESIDUAL, false, false, PMAX>;
 }
 
 template <typename T>
-cudaError_t launch_batch_sweep(int mode, bool cached, bool ext, const SweepArgs<T>* args, const int2* tasks, int ntask,
-                               const int2* elems, int nelem, int grid, int block, cudaStream_t s) {
-    void* params[] = {(void*)&args, (void*)&tasks, (void*)&ntask, (void*)&elems, (void*)&nelem};
-    return cudaLaunchCooperativeKernel(batch_kernel_of<T>(mode, cached, ext), dim3(grid), dim3(block), params, 0, s);
+static const void* batch_kernel_of(int mode, bool cached, bool ext, int pmax) {
+    return pmax <= 3 ? batch_kernel_pm<T, 3>(mode, cached, ext) : batch_kernel_pm<T, 4>(mode, cached, ext);
 }
 
-template cudaError_t launch_batch_sweep<double>(int, bool, bool, const SweepArgs<double>*, const int2*, int,
+template <typename T>
+cudaError_t launch_batch_sweep(int mode, bool cached, bool ext, int pmax, const SweepArgs<T>* args, const int2* tasks,
+                               int ntask, const int2* elems, int nelem, int grid, int block, cudaStream_t s) {
+    void* params[] = {(void*)&args, (void*)&tasks, (void*)&ntask, (void*)&elems, (void*)&nelem};
+    return cudaLaunchCooperativeKernel(batch_kernel_of<T>(mode, cached, ext, pmax), dim3(grid), dim3(block), params,
+                                       0, s);
+}
+
+template cudaError_t launch_batch_sweep<double>(int, bool, bool, int, const SweepArgs<double>*, const int2*, int,
                                                 const int2*, int, int, int, cudaStream_t);
-template cudaError_t launch_batch_sweep<float>(int, bool, bool, const SweepArgs<float>*, const int2*, int,
+template cudaError_t launch_batch_sweep<float>(int, bool, bool, int, const SweepArgs<float>*, const int2*, int,
                                                const int2*, int, int, int, cudaStream_t);
 
-int batch_blocks_per_sm(int mode, bool fp32, bool cached, bool ext, int block) {
+int batch_blocks_per_sm(int mode, bool fp32, bool cached, bool ext, int pmax, int block) {
     int nb = 0;
-    const void* f = fp32 ? batch_kernel_of<float>(mode, cached, false) : batch_kernel_of<double>(mode, cached, ext);
+    const void* f = fp32 ? batch_kernel_of<float>(mode, cached, false, pmax)
+                         : batch_kernel_of<double>(mode, cached, ext, pmax);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, 0);
     return nb;
 }

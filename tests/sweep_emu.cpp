@@ -450,12 +450,12 @@ static int run_batch(const std::string& dir, int count) {
         const int nelem = (int)elems.size();
         if (form == 0)
             emu_launch(1, 256, 0, [&] {
-                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, false, false>(args.data(), merged.data(), ntask,
+                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, false, false, 4>(args.data(), merged.data(), ntask,
                                                                           elems.data(), nelem);
             });
         else
             emu_launch(1, 256, 0, [&] {
-                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, true, false>(args.data(), merged.data(), ntask,
+                smm::batch_sweep_kernel<double, smm::SWEEP_SOURCE, true, false, 4>(args.data(), merged.data(), ntask,
                                                                          elems.data(), nelem);
             });
     }

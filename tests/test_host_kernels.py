@@ -217,7 +217,7 @@ def sweep_emu(tmp_path_factory):
                      extract(sweep, "__device__ bool sweep_gate("),
                      extract(sweep, "__device__ __forceinline__ bool sweep_task("),
                      extract(sweep, "__global__ void __launch_bounds__(256, INV ? (P <= 3 ? 5 : 3) : 1) sweep_kernel("),
-                     extract(sweep, "__global__ void __launch_bounds__(256, INV ? 3 : 1) batch_sweep_kernel("),
+                     extract(sweep, "__global__ void __launch_bounds__(256, INV ? (PMAX <= 3 ? 5 : 3) : 1) batch_sweep_kernel("),
                      extract(sweep, "__global__ void __launch_bounds__(256) invert_kernel("),
                      extract(sweep, "__global__ void __launch_bounds__(256) residual_kernel("),
                      extract(sweep, "__global__ void mass_apply_kernel("),
