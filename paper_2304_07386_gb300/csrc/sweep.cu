@@ -72,9 +72,10 @@ template <typename T> __device__ __forceinline__ T ldg_cg(const T* p) { return _
 // bdr_correction_factor_disc), formed after the sweep's last task:
 //   phi = sum_d w_d psi_d, J = sum_d w_d Omega_d psi_d,
 //   T = sum_d w_d Omega_d Omega_d psi_d - phi/3 I        (lane = node),
-// accumulated over the ordinates in their order (so the result does not
+// accumulated over the ordinates in a fixed order (so the result does not
 // depend on which warp forms it), as FP32 pairs against the pair weights in
-// FP64 cached mode and in FP64 otherwise; then, at the Gauss points of each
+// FP64 cached mode (split over lane groups for n <= 16) and in FP64 otherwise
+// (index order); then, at the Gauss points of each
 // boundary face, beta = sum_d w_d |Omega_d . n| psi_d - E_b0 phi (lanes over
 // the ordinates, a fixed-order butterfly sum).  The flux loads are issued
 // eight ordinates at a time.
@@ -89,20 +90,59 @@ __device__ __noinline__ void element_moments(const SweepArgs<T>& a, const int e)
     constexpr int B = 8;  // ordinates whose loads are in flight together
     double phi;
     if constexpr (DF) {
+        // with n <= 16 the lanes form KG = 32 / n groups of n rows; group g sums
+        // the ordinates d = g (mod KG) and the groups' partial sums are added in
+        // group order (p = 4: one group, every ordinate in index order)
+        constexpr int KG = 32 / N;
+        const int g = KG == 1 ? 0 : (lane < KG * N ? lane / N : KG);
+        const int r = KG == 1 ? row : (lane < KG * N ? lane - (lane / N) * N : 0);
         float s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
-        const float2* ps = a.psi2 + (size_t)e * nd * N + row;
-        for (int d0 = 0; d0 < nd; d0 += B) {
-            float2 v[B];
+        const float2* ps = a.psi2 + (size_t)e * nd * N + r;
+        if constexpr (KG == 1) {
+            for (int d0 = 0; d0 < nd; d0 += B) {
+                float2 v[B];
 #pragma unroll
-            for (int k = 0; k < B; ++k) v[k] = d0 + k < nd ? __ldcg(ps + (size_t)(d0 + k) * N) : make_float2(0.f, 0.f);
+                for (int k = 0; k < B; ++k)
+                    v[k] = d0 + k < nd ? __ldcg(ps + (size_t)(d0 + k) * N) : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < B; ++k) {
-                if (d0 + k >= nd) break;
+                for (int k = 0; k < B; ++k) {
+                    if (d0 + k >= nd) break;
 #pragma unroll
-                for (int m = 0; m < 6; ++m) {
-                    const float2 wk = a.wq2[m * nd + d0 + k];
-                    df_acc(s[m], c[m], wk.x, wk.y, v[k].x, v[k].y);
+                    for (int m = 0; m < 6; ++m) {
+                        const float2 wk = a.wq2[m * nd + d0 + k];
+                        df_acc(s[m], c[m], wk.x, wk.y, v[k].x, v[k].y);
+                    }
                 }
+            }
+        } else {
+            for (int d0 = 0; d0 < nd; d0 += B * KG) {
+                float2 v[B];
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const int d = d0 + k * KG + g;
+                    v[k] = g < KG && d < nd ? __ldcg(ps + (size_t)d * N) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const int d = d0 + k * KG + g;
+                    if (g >= KG || d >= nd) continue;
+#pragma unroll
+                    for (int m = 0; m < 6; ++m) {
+                        const float2 wk = a.wq2[m * nd + d];
+                        df_acc(s[m], c[m], wk.x, wk.y, v[k].x, v[k].y);
+                    }
+                }
+            }
+        }
+        if constexpr (KG > 1) {
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                float ts = __shfl_sync(FULL, s[m], r), tc = __shfl_sync(FULL, c[m], r);
+#pragma unroll
+                for (int gg = 1; gg < KG; ++gg)
+                    df_add(ts, tc, __shfl_sync(FULL, s[m], r + gg * N), __shfl_sync(FULL, c[m], r + gg * N));
+                s[m] = ts;
+                c[m] = tc;
             }
         }
         phi = df_to_double(s[0], c[0]);
