@@ -334,10 +334,14 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
         // ---- DF: each inflow face's coefficient entry (lane (a, c)) and the
         //      index of its upwind value, formed before the wait; boundary
         //      faces are finished here (ui = -2: cf holds coef * inflow) ----
+        //      (p = 4 and the kernel with the optional parts; p <= 3 otherwise packs
+        //      its inflow faces below)
+        constexpr int FG = 32 / (P1 * P1);            // faces whose lanes fit the warp at once
+        constexpr bool FPK = DF && !EXT && FG >= 2;
         float2 cf[4];
         int ui[4];
         unsigned lagm = 0;
-        if constexpr (DF) {
+        if constexpr (DF && !FPK) {
             const int la = lane / P1, lc = lane - (lane / P1) * P1;
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
@@ -371,6 +375,53 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                         df_acc(ts, tc, coef.x, coef.y, u.x, u.y);
                         cf[f] = df_norm(ts, tc);
                         ui[f] = -2;
+                    }
+                }
+            }
+        }
+
+        // ---- packed inflow faces (FP64 cached mode, p <= 3, no optional parts):
+        //      the task's inflow faces (at most three) are dealt to the FG lane
+        //      groups of (p+1)^2 lanes, one face per group and round; lane
+        //      (h, a, c) of group h forms face f_h's coefficient coef[a][c] and
+        //      the index of its upwind value, so all faces' products and sums
+        //      over c run in the same instructions ----
+        constexpr int RMAX = FPK ? (3 + FG - 1) / FG : 1;
+        unsigned flist = 0;  // the inflow faces in order, two bits each
+        int nin = 0;
+        float2 cfp[RMAX];
+        int uip[RMAX];
+        if constexpr (FPK) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                if (dir[f] == -1) flist |= (unsigned)f << (2 * nin++);
+            const int h = lane / (P1 * P1), la = (lane % (P1 * P1)) / P1, lc = lane % P1;
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+                const int sl = r * FG + h;
+                cfp[r] = make_float2(0.0f, 0.0f);
+                uip[r] = -1;
+                if (h < FG && sl < nin) {
+                    const int f = (flist >> (2 * sl)) & 3;
+                    const size_t fo2 = ((size_t)e * 4 + f) * P1 * P1 + la * P1 + lc;
+                    const float2 fx = a.Fx2[fo2], fy = a.Fy2[fo2], o2x = a.ox2[d], o2y = a.oy2[d];
+                    float cs = 0.0f, cc = 0.0f;
+                    df_acc(cs, cc, o2x.x, o2x.y, fx.x, fx.y);
+                    df_acc(cs, cc, o2y.x, o2y.y, fy.x, fy.y);
+                    const float2 coef = df_norm(cs, cc);
+                    cfp[r] = coef;
+                    const int nb = a.nbr[e * 4 + f];
+                    if (nb >= 0) {
+                        const int f2 = a.nbr_face[e * 4 + f];
+                        const int c2 = a.nbr_flip[e * 4 + f] ? P - lc : lc;
+                        const int node = f2 == 0 ? c2 : (f2 == 1 ? c2 * P1 + P : (f2 == 2 ? P * P1 + c2 : c2 * P1));
+                        uip[r] = (int)(((size_t)nb * nd + d) * N + node);
+                    } else if (MODE == SWEEP_SOURCE && a.inflow2) {
+                        const float2 u = a.inflow2[((size_t)a.bface_id[e * 4 + f] * nd + d) * P1 + lc];
+                        float ts = 0.0f, tc = 0.0f;
+                        df_acc(ts, tc, coef.x, coef.y, u.x, u.y);
+                        cfp[r] = df_norm(ts, tc);
+                        uip[r] = -2;
                     }
                 }
             }
@@ -418,9 +469,48 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
             b = (T)a.rhs[((size_t)e * nd + d) * N + row];
         }
 
+        if constexpr (FPK) {
+            // every round's upwind values, loaded together; per round the
+            // product, the sum over c within each group of p+1 lanes (valid at
+            // lane (h, a, 0)), then every row adds -A^{-1}[row][node(f, a)] v_a
+            float2 upp[RMAX], vr[RMAX];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) upp[r] = uip[r] >= 0 ? __ldcg(a.psi2 + uip[r]) : make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+                float2 t;
+                if (uip[r] == -2) {
+                    t = cfp[r];
+                } else {
+                    float ts = 0.0f, tc = 0.0f;
+                    df_acc(ts, tc, cfp[r].x, cfp[r].y, upp[r].x, upp[r].y);
+                    t = df_norm(ts, tc);
+                }
+                float vs = t.x, vc = t.y;
+#pragma unroll
+                for (int k = 1; k < P1; ++k)
+                    df_add(vs, vc, __shfl_down_sync(FULL, t.x, k), __shfl_down_sync(FULL, t.y, k));
+                vr[r] = df_norm(vs, vc);
+            }
+            int sl = 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (dir[f] != -1) continue;
+                const int base = (sl % FG) * P1 * P1;
+                const float2 v = sl < FG ? vr[0] : vr[RMAX - 1];
+#pragma unroll
+                for (int aa = 0; aa < P1; ++aa) {
+                    const int cn = face_node<P>(f, aa);
+                    const float2 col = cn / CPG == dgrp ? Adf[cn % CPG] : make_float2(0.0f, 0.0f);
+                    df_acc(ys, yc, -col.x, -col.y, __shfl_sync(FULL, v.x, base + aa * P1),
+                           __shfl_sync(FULL, v.y, base + aa * P1));
+                }
+                ++sl;
+            }
+        }
         // DF: every inflow face's upwind value, loaded together
         float2 up[4];
-        if constexpr (DF) {
+        if constexpr (DF && !FPK) {
 #pragma unroll
             for (int f = 0; f < 4; ++f)
                 up[f] = ui[f] >= 0 ? __ldcg((EXT && ((lagm >> f) & 1u) ? a.psi2_lag : a.psi2) + ui[f])
@@ -444,7 +534,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                         if (j == face_node<P>(f, c)) A[j] += v;
                 }
             }
-            if (DF && (df < 0 || (EXT && df >= 2))) {
+            if (DF && !FPK && (df < 0 || (EXT && df >= 2))) {
                 // inflow face in pairs: lane (a, c) forms coef[a][c] u[c], the
                 // p+1 lanes of group a sum over c, and every row adds
                 // -A^{-1}[row][node(f, a)] v_a
@@ -468,7 +558,7 @@ __device__ __forceinline__ bool sweep_task(const SweepArgs<T>& a, const int task
                         KG == 1 ? Adf[cn] : (cn / CPG == dgrp ? Adf[cn % CPG] : make_float2(0.0f, 0.0f));
                     df_acc(ys, yc, -col.x, -col.y, __shfl_sync(FULL, v.x, aa * P1), __shfl_sync(FULL, v.y, aa * P1));
                 }
-            } else if (df < 0 || (EXT && df >= 2)) {
+            } else if (!DF && (df < 0 || (EXT && df >= 2))) {
                 // inflow face (warp-uniform branch): the (p+1)^2 products
                 // coef[a][c] * psi_up[c] are spread over lanes (a, c), summed
                 // over c within each group of p+1 lanes, and handed to the lane
