@@ -196,6 +196,16 @@ typedef struct {
                                    to the same fixed point in more outer steps.
                                    FP64 sweeps without the fixup only (else
                                    SMM_ERR_CYCLE).  0: a cycle is SMM_ERR_CYCLE. */
+    double cg_tol_adaptive;     /* smm_iterate / smm_batch_iterate: eta > 0 solves
+                                   the moment system of outer step k only to
+                                   ||r||_2 <= max(tol_cg, eta d_{k-1}) ||b||_2,
+                                   d_{k-1} the previous step's relative
+                                   successive difference (1 before the first):
+                                   an inexact inner solve that tightens as the
+                                   outer iteration converges (the paper's
+                                   crooked-pipe runs solve the moment system
+                                   to 1e-8 for an outer tolerance of 1e-6).
+                                   Default 0: every solve to tol_cg. */
 } smm_options;
 
 typedef struct {

@@ -233,6 +233,7 @@ void smm_default_options(smm_options* opt) {
     opt->cg_device_loop = 1;
     opt->resume_history = 0;
     opt->cycle_lagging = 1;
+    opt->cg_tol_adaptive = 0.0;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -263,7 +264,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     if (opt) o = *opt;
     if (o.sweep_precision != SMM_SWEEP_FP64 && o.sweep_precision != SMM_SWEEP_FP32_REFINED)
         return fail(SMM_ERR_INVALID_ARG, "bad sweep precision");
-    if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0) ||
+    if (!(o.tol_cg > 0) || o.max_cg < 1 || !(o.kappa_scale > 0) || !(o.spin_timeout_s > 0) || !(o.cg_tol_adaptive >= 0) ||
         (o.precond != SMM_PRECOND_BLOCK_JACOBI && o.precond != SMM_PRECOND_MULTIGRID) ||
         (o.sweep_solver != SMM_SOLVER_LU && o.sweep_solver != SMM_SOLVER_CACHED_INVERSE) || o.anderson_depth < 0 ||
         o.anderson_depth > 5 || o.mg_smooth_steps < 1 || o.mg_smooth_steps > 4 ||
@@ -936,8 +937,8 @@ smm_status check_device_error(smm_handle h) {
     return SMM_OK;
 }
 
-// CG from the guess in x; host reads the control word every `chunk` iterations
-smm_status run_cg(smm_handle h, double* x, int* iters) {
+// CG from the guess in x to ||r||_2 <= tol ||b||_2; host reads the control word every `chunk` iterations
+smm_status run_cg(smm_handle h, double* x, int* iters, double tol) {
     const bool cgm = h->cgc.enabled;
     const bool mg = h->mg.enabled;
     const size_t nphi = (size_t)h->ne * h->n;
@@ -947,12 +948,12 @@ smm_status run_cg(smm_handle h, double* x, int* iters) {
         // continuous system: b = P^T b_IP, initial guess from the DG iterate
         smm::cgc_gather(h->cgc, h->rhs, h->bc, h->stream);
         smm::cgc_pick(h->cgc, x, h->xc, h->stream);
-        h->launches += 2 + smm::cgc_start(a, h->cgc, h->mg, h->opt.tol_cg, h->opt.max_cg, h->stream);
+        h->launches += 2 + smm::cgc_start(a, h->cgc, h->mg, tol, h->opt.max_cg, h->stream);
     } else if (mg) {
         SMM_CUDA(cudaMemcpyAsync(h->xcg, x, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-        h->launches += smm::cgx_start(a, h->opt.tol_cg, h->opt.max_cg, h->mg, h->stream);
+        h->launches += smm::cgx_start(a, tol, h->opt.max_cg, h->mg, h->stream);
     } else {
-        smm::cg_start(a, h->opt.tol_cg, h->opt.max_cg, h->stream);
+        smm::cg_start(a, tol, h->opt.max_cg, h->stream);
         h->launches += 2;
     }
     SMM_CUDA(cudaGetLastError());
@@ -1126,7 +1127,7 @@ smm_status smm_moment_solve(smm_handle h, double* phi_dev, int32_t* cg_iters) {
     smm_status st = enqueue_rhs(h);
     if (st != SMM_OK) return st;
     int it = 0;
-    st = run_cg(h, phi_dev, &it);
+    st = run_cg(h, phi_dev, &it, h->opt.tol_cg);
     if (cg_iters) *cg_iters = it;
     return st;
 }
@@ -1145,6 +1146,13 @@ bool is_host_pointer(const void* p) {
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
+// the moment solve's tolerance in an outer step whose predecessor changed
+// varphi by prev_rel (relative max-norm): options.cg_tol_adaptive
+double inner_tol(smm_handle h, double prev_rel) {
+    const double eta = h->opt.cg_tol_adaptive;
+    return eta > 0 ? std::max(h->opt.tol_cg, eta * prev_rel) : h->opt.tol_cg;
+}
+
 smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t max_outer, double* phi_dev,
                           smm_stats* stats) {
     smm_stats local{};
@@ -1153,6 +1161,7 @@ smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t ma
     const size_t nphi = (size_t)h->ne * h->n;
     smm_status result = SMM_ERR_NOT_CONVERGED;
     if (!h->opt.resume_history) h->aa_k = 0;
+    double prev_rel = 1.0;  // the previous step's relative difference (adaptive inner tolerance)
     for (int k = 1; k <= max_outer; ++k) {
         SMM_CUDA(cudaMemcpyAsync(h->phi_prev, phi_dev, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         SMM_CUDA(cudaEventRecord(h->ev[0], h->stream));
@@ -1164,7 +1173,7 @@ smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t ma
         if (st != SMM_OK) return st;
         SMM_CUDA(cudaEventRecord(h->ev[3], h->stream));
         int it = 0;
-        st = run_cg(h, phi_dev, &it);
+        st = run_cg(h, phi_dev, &it, inner_tol(h, prev_rel));
         if (st != SMM_OK && st != SMM_ERR_NOT_CONVERGED) return st;
         SMM_CUDA(cudaEventRecord(h->ev[4], h->stream));
         SMM_CUDA(cudaMemsetAsync(h->nonfinite, 0, sizeof(int), h->stream));
@@ -1195,6 +1204,7 @@ smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t ma
         const double diff = h->h_scal[0], mx = h->h_scal[1];
         local.last_diff = diff;
         local.last_rel_diff = mx > 0 ? diff / mx : diff;
+        prev_rel = local.last_rel_diff;
         if (h->h_int[4]) {
             h->aa_k = 0;
             if (stats) *stats = local;
@@ -1550,7 +1560,7 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
             s = enqueue_rhs(h);
             if (s != SMM_OK) return s;
             int it = 0;
-            s = run_cg(h, phi_dev[i], &it);
+            s = run_cg(h, phi_dev[i], &it, inner_tol(h, k == 1 ? 1.0 : st[i].last_rel_diff));
             if (s != SMM_OK && s != SMM_ERR_NOT_CONVERGED) return s;
             const size_t nphi = (size_t)h->ne * h->n;
             SMM_CUDA(cudaMemsetAsync(h->nonfinite, 0, sizeof(int), h->stream));

@@ -250,6 +250,34 @@ def test_anderson_reaches_oracle_fixed_point(depth):
     assert its[1] <= its[0], its
 
 
+@pytest.mark.parametrize("anderson", [0, 2])
+def test_adaptive_inner_tolerance_reaches_oracle_fixed_point(anderson):
+    """Moment solves to max(tol_cg, 1e-2 d_{k-1}) (d the previous step's
+    relative difference) instead of tol_cg: the same fixed point as the
+    oracle's, in fewer CG iterations than every solve to tol_cg; and the
+    batched iterate with the same option matches the single iterate."""
+    import paper_2304_07386_gb300 as P
+    prob = problem(6, 5, m=2, p=2, sn=4, seed=2, kind="mms", c=0.95)
+    disc, op, q, inflow = make_oracle(prob)
+    phi_o, _, _ = op.iterate(tol=1e-13)
+    cg = []
+    for eta in (0.0, 1e-2):
+        h = make_gpu(prob, tol_cg=1e-14, anderson_depth=anderson, cg_tol_adaptive=eta)
+        phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+        rc, st = P.smm_iterate(h, phi, 1e-11, 200, relative=True)
+        assert rel(phi.cpu().numpy(), phi_o.ravel()) < 1e-9
+        cg.append(st["cg_total"])
+        h.destroy()
+    assert cg[1] < cg[0], cg
+    hb = make_gpu(prob, tol_cg=1e-14, anderson_depth=anderson, cg_tol_adaptive=1e-2)
+    b = P.smm.smm_batch_create([hb])
+    xb = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+    P.smm.smm_batch_iterate(b, [xb], 1e-11, 200, relative=True)
+    assert rel(xb.cpu().numpy(), phi_o.ravel()) < 1e-9
+    b.destroy()
+    hb.destroy()
+
+
 BATCH = [
     # (nx, ny, m, p, sn, seed)
     (4, 4, 1, 1, 4, None),
