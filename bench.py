@@ -242,7 +242,7 @@ class ClockSampler:
 # on the 128x128 piece of the headline workload (a quarter of its elements, to keep the capture small)
 # and scaled x4, every kernel's bytes being proportional to the element count; a key is dropped
 # whenever the kernels it covers change.
-NCU_TRAFFIC: dict = {"cg_iteration": 4 * 332885248}
+NCU_TRAFFIC: dict = {"cg_iteration": 4 * 332872960, "sweep_kernel": 4 * 3268649728}
 
 # a timed step is outer iteration START_ITERATIONS + 1 from varphi^0 = 0
 START_ITERATIONS = 3
