@@ -349,6 +349,28 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;  // valid in thread 0
 }
 
+// two block sums in one pass (one pair of barriers); each is summed in the
+// same order as block_sum (warp sums, then the warps in order); valid in
+// thread 0; blocks of at most 512 threads, sh at least 32 words
+__device__ __forceinline__ void block_sum2(double a, double b, double* sh, double& sa, double& sb) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    __syncthreads();
+    if (l == 0) {
+        sh[w] = a;
+        sh[16 + w] = b;
+    }
+    __syncthreads();
+    sa = 0.0;
+    sb = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) {
+            sa += sh[i];
+            sb += sh[16 + i];
+        }
+}
+
 // sum over partials written by other blocks of the running kernel (read
 // through L2, four loads in flight per thread); deterministic order
 __device__ __forceinline__ double sum_partials_cg(const double* part, int nblk, double* sh) {

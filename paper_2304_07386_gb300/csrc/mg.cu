@@ -297,8 +297,8 @@ __global__ void __launch_bounds__(256) bj_last_dots_kernel(CGArgs a, FaceOp<floa
             dz += (rd[k] - a.rold[o]) * zd;
         }
     }
-    const double s1 = block_sum(rz, sh);
-    const double s2 = block_sum(dz, sh);
+    double s1, s2;
+    block_sum2(rz, dz, sh, s1, s2);
     if (threadIdx.x == 0) {
         a.part[2 * a.nblk + blockIdx.x] = s1;
         a.part[3 * a.nblk + blockIdx.x] = s2;
