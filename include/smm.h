@@ -175,7 +175,9 @@ typedef struct {
                                    arithmetic either way. */
     int32_t resume_history;     /* smm_iterate / smm_batch_iterate: 0 (default)
                                    starts every call with an empty Anderson
-                                   history; nonzero continues the history that
+                                   history (and no extrapolation history, see
+                                   cg_guess_extrapolate); nonzero continues the
+                                   history that
                                    the previous call on the handle left (or that
                                    smm_set_state restored), so that an iteration
                                    split over several calls, or restarted from a
@@ -206,6 +208,18 @@ typedef struct {
                                    crooked-pipe runs solve the moment system
                                    to 1e-8 for an outer tolerance of 1e-6).
                                    Default 0: every solve to tol_cg. */
+    int32_t cg_guess_extrapolate; /* smm_iterate / smm_batch_iterate without
+                                   Anderson acceleration: nonzero (default)
+                                   starts the moment solve of outer step k
+                                   from varphi_k + rho (varphi_k - varphi_{k-1}),
+                                   rho = d_{k-1} / d_{k-2} (the ratio of the last
+                                   two successive differences, clamped to
+                                   [0, 0.9]) instead of from varphi_k, once two
+                                   steps of this call (or, with resume_history,
+                                   of earlier calls) exist: the outer iteration
+                                   converges linearly, so the extrapolation
+                                   starts the CG closer to its solution.  The
+                                   same fixed point; 0: start from varphi_k. */
 } smm_options;
 
 typedef struct {
@@ -331,8 +345,9 @@ smm_status smm_set_spin_timeout(smm_handle h, double seconds);
  * The state a later call depends on besides its arguments: the angular flux
  * of the last sweep (which the next FP32-refined sweep corrects and a block
  * Jacobi sweep lags), the moments and boundary correction (the next moment
- * solve's closures), the previous iterate and the Anderson history with its
- * length.  Restoring it into a handle created with the same mesh, data and
+ * solve's closures), the previous iterate, the Anderson history with its
+ * length and the extrapolated CG start's history (the input of the step
+ * before and the last two successive differences).  Restoring it into a handle created with the same mesh, data and
  * options makes the following calls return bit for bit what they would have
  * returned on the saved handle.  The buffer is opaque (a 256-byte header,
  * then the arrays), host or device memory alike, owned by the caller.

@@ -59,6 +59,10 @@ struct smm_ctx {
     double *src = nullptr, *inflow = nullptr;
     bool cached = false;
     float2* ainv_df = nullptr;     // cached local inverses (FP64 sweep), FP32 pairs hi + lo
+    // extrapolated CG start (options.cg_guess_extrapolate): the previous outer
+    // step's input and the last two successive differences (0: not yet)
+    double* phi_old = nullptr;
+    double dl1 = 0.0, dl2 = 0.0;
     float* ainv32 = nullptr;       // cached local inverses (FP32 correction sweep)
     // FP64 cached sweep, FP32-pair inputs: M (sigma_s/(4pi) phi + q_iso) of the current sweep [ne][n],
     // M q_d [ne][nd][n] (angular sources), cosines [nd], face matrices, inflow; psi as pairs
@@ -234,6 +238,7 @@ void smm_default_options(smm_options* opt) {
     opt->resume_history = 0;
     opt->cycle_lagging = 1;
     opt->cg_tol_adaptive = 0.0;
+    opt->cg_guess_extrapolate = 1;
 }
 
 const char* smm_last_error(void) { return g_err.c_str(); }
@@ -411,6 +416,7 @@ smm_status smm_create(const smm_mesh* mesh, int32_t p, int32_t sn_order, const d
     h->qv = h->alloc<double>(nphi);
     h->p2 = h->alloc<float2>(nphi);
     h->phi_prev = h->alloc<double>(nphi);
+    h->phi_old = h->alloc<double>(nphi);
     h->phi_io = h->alloc<double>(nphi);
     const int epb = smm::cg_threads_per_block(s.n) / s.n;
     h->cg_nblk = (s.ne + epb - 1) / epb;
@@ -1153,6 +1159,28 @@ double inner_tol(smm_handle h, double prev_rel) {
     return eta > 0 ? std::max(h->opt.tol_cg, eta * prev_rel) : h->opt.tol_cg;
 }
 
+// the moment solve's starting point: phi_dev holds varphi_k (also in
+// phi_prev); with two earlier steps known it becomes varphi_k + rho (varphi_k
+// - varphi_{k-1}), rho = d_{k-1} / d_{k-2} clamped to [0, 0.9]
+smm_status extrapolate_start(smm_handle h, double* phi_dev) {
+    if (!h->opt.cg_guess_extrapolate || h->opt.anderson_depth > 0 || !(h->dl2 > 0.0)) return SMM_OK;
+    const double rho = std::min(0.9, std::max(0.0, h->dl1 / h->dl2));
+    smm::launch_axpby(h->ne * h->n, 1.0 + rho, h->phi_prev, -rho, h->phi_old, phi_dev, h->stream);
+    h->launches += 1;
+    SMM_CUDA(cudaGetLastError());
+    return SMM_OK;
+}
+
+// after an outer step whose input is in phi_prev and whose successive
+// difference is diff: shift the extrapolation history
+smm_status record_step(smm_handle h, double diff) {
+    h->dl2 = h->dl1;
+    h->dl1 = diff;
+    SMM_CUDA(cudaMemcpyAsync(h->phi_old, h->phi_prev, (size_t)h->ne * h->n * sizeof(double),
+                             cudaMemcpyDeviceToDevice, h->stream));
+    return SMM_OK;
+}
+
 smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t max_outer, double* phi_dev,
                           smm_stats* stats) {
     smm_stats local{};
@@ -1160,7 +1188,10 @@ smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t ma
     const long long launches0 = h->launches;
     const size_t nphi = (size_t)h->ne * h->n;
     smm_status result = SMM_ERR_NOT_CONVERGED;
-    if (!h->opt.resume_history) h->aa_k = 0;
+    if (!h->opt.resume_history) {
+        h->aa_k = 0;
+        h->dl1 = h->dl2 = 0.0;
+    }
     double prev_rel = 1.0;  // the previous step's relative difference (adaptive inner tolerance)
     for (int k = 1; k <= max_outer; ++k) {
         SMM_CUDA(cudaMemcpyAsync(h->phi_prev, phi_dev, nphi * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -1173,6 +1204,8 @@ smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t ma
         if (st != SMM_OK) return st;
         SMM_CUDA(cudaEventRecord(h->ev[3], h->stream));
         int it = 0;
+        st = extrapolate_start(h, phi_dev);
+        if (st != SMM_OK) return st;
         st = run_cg(h, phi_dev, &it, inner_tol(h, prev_rel));
         if (st != SMM_OK && st != SMM_ERR_NOT_CONVERGED) return st;
         SMM_CUDA(cudaEventRecord(h->ev[4], h->stream));
@@ -1205,6 +1238,8 @@ smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t ma
         local.last_diff = diff;
         local.last_rel_diff = mx > 0 ? diff / mx : diff;
         prev_rel = local.last_rel_diff;
+        st = record_step(h, diff);
+        if (st != SMM_OK) return st;
         if (h->h_int[4]) {
             h->aa_k = 0;
             if (stats) *stats = local;
@@ -1217,6 +1252,8 @@ smm_status iterate_device(smm_handle h, double tol, int32_t relative, int32_t ma
             SMM_CUDA(cudaMemsetAsync(phi_dev, 0, nphi * sizeof(double), h->stream));
             local.guess_rejected = 1;
             h->aa_k = 0;
+            h->dl1 = h->dl2 = 0.0;
+            prev_rel = 1.0;
             continue;
         }
         const double crit = relative ? local.last_rel_diff : diff;
@@ -1263,7 +1300,7 @@ namespace {
 // Checkpoint layout: a header of 16 int64 words, then the handle's state
 // arrays, each starting on a 256-byte boundary.
 constexpr int64_t kStateMagic = 0x534d4d5354415445LL;  // "SMMSTATE"
-constexpr int64_t kStateVersion = 1;
+constexpr int64_t kStateVersion = 2;
 
 struct StateSection {
     void* dev;
@@ -1278,6 +1315,7 @@ std::vector<StateSection> state_sections(smm_handle h) {
     v.push_back({h->mom, 6 * nphi * sizeof(double)});
     v.push_back({h->beta, (size_t)h->nb * h->nfq * sizeof(double)});
     v.push_back({h->phi_prev, nphi * sizeof(double)});
+    v.push_back({h->phi_old, nphi * sizeof(double)});
     for (size_t k = 0; k < h->aaG.size(); ++k) {
         v.push_back({h->aaG[k], nphi * sizeof(double)});
         v.push_back({h->aaF[k], nphi * sizeof(double)});
@@ -1302,6 +1340,8 @@ void state_header(smm_handle h, int64_t* hdr) {
     hdr[8] = h->opt.anderson_depth;
     hdr[9] = h->aa_k;
     hdr[10] = state_bytes(h);
+    std::memcpy(&hdr[11], &h->dl1, sizeof(double));  // the extrapolation history's differences
+    std::memcpy(&hdr[12], &h->dl2, sizeof(double));
 }
 
 }  // namespace
@@ -1358,6 +1398,8 @@ smm_status smm_set_state(smm_handle h, const void* buf, int64_t bytes) {
     }
     SMM_CUDA(cudaStreamSynchronize(h->stream));
     h->aa_k = aa_k;
+    std::memcpy(&h->dl1, &hdr[11], sizeof(double));
+    std::memcpy(&h->dl2, &hdr[12], sizeof(double));
     return SMM_OK;
 }
 
@@ -1544,7 +1586,10 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
     for (auto& s : st) s.cg_min = 1 << 30;
     std::vector<const double*> phis(phi_dev, phi_dev + n);
     for (smm_handle h : b->hs)
-        if (!h->opt.resume_history) h->aa_k = 0;
+        if (!h->opt.resume_history) {
+            h->aa_k = 0;
+            h->dl1 = h->dl2 = 0.0;
+        }
     int remaining = n;
     for (int k = 1; k <= max_outer && remaining > 0; ++k) {
         for (int i = 0; i < n; ++i) {
@@ -1560,6 +1605,8 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
             s = enqueue_rhs(h);
             if (s != SMM_OK) return s;
             int it = 0;
+            s = extrapolate_start(h, phi_dev[i]);
+            if (s != SMM_OK) return s;
             s = run_cg(h, phi_dev[i], &it, inner_tol(h, k == 1 ? 1.0 : st[i].last_rel_diff));
             if (s != SMM_OK && s != SMM_ERR_NOT_CONVERGED) return s;
             const size_t nphi = (size_t)h->ne * h->n;
@@ -1576,11 +1623,14 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
             q.cg_max = std::max(q.cg_max, it);
             q.last_diff = h->h_scal[0];
             q.last_rel_diff = h->h_scal[1] > 0 ? h->h_scal[0] / h->h_scal[1] : h->h_scal[0];
+            s = record_step(h, q.last_diff);
+            if (s != SMM_OK) return s;
             if (k == 1 && h->opt.guess_check && h->h_scal[0] > h->h_scal[1]) {
                 // as in smm_iterate: the guess is farther from its image than zero is; restart from zero
                 SMM_CUDA(cudaMemsetAsync(phi_dev[i], 0, nphi * sizeof(double), h->stream));
                 q.guess_rejected = 1;
                 h->aa_k = 0;
+                h->dl1 = h->dl2 = 0.0;
                 continue;
             }
             const double crit = relative ? q.last_rel_diff : q.last_diff;

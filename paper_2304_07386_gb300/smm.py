@@ -40,7 +40,7 @@ class smm_options(C.Structure):
                 ("mg_smooth_steps", C.c_int32), ("moment_discretization", C.c_int32),
                 ("negative_flux_fixup", C.c_int32), ("sweep_tiles", C.c_int32), ("mg_smoother", C.c_int32),
                 ("cg_device_loop", C.c_int32), ("resume_history", C.c_int32), ("cycle_lagging", C.c_int32),
-                ("cg_tol_adaptive", C.c_double)]
+                ("cg_tol_adaptive", C.c_double), ("cg_guess_extrapolate", C.c_int32)]
 
 
 class smm_info(C.Structure):

@@ -102,15 +102,17 @@ def test_iterate_on_a_host_array_equals_the_device_run():
     assert rc == 7 and st["outer_iterations"] == 2 and np.max(np.abs(x3)) > 0
 
 
-@pytest.mark.parametrize("mode", ["fp32_refined", "anderson2", "tiles"])
+@pytest.mark.parametrize("mode", ["fp32_refined", "anderson2", "tiles", "extrapolate"])
 def test_restored_state_reproduces_the_next_iterates_bit_for_bit(mode):
     """A state saved after three outer steps and restored into a fresh handle
     built from the same data gives, bit for bit, the next two iterates of the
     saved handle -- for each mode whose next step reads the state: the
     FP32-refined sweep (it corrects the stored angular flux), Anderson depth 2
     with resume_history (the history ring and its length), the block Jacobi
-    sweep (it lags the stored flux across tile borders).  Without the restore
-    the fresh handle's steps differ, so the state is what carries them."""
+    sweep (it lags the stored flux across tile borders), the extrapolated CG
+    start with resume_history (the previous input and the last two
+    differences).  Without the restore the fresh handle's steps differ, so
+    the state is what carries them."""
     import paper_2304_07386_gb300 as P
     prob = problem(6, 5, m=2, p=2, sn=4, seed=2, kind="mms", c=0.95)
     kw = dict(tol_cg=1e-14)
@@ -118,6 +120,8 @@ def test_restored_state_reproduces_the_next_iterates_bit_for_bit(mode):
         kw["sweep_precision"] = 1
     elif mode == "anderson2":
         kw.update(anderson_depth=2, resume_history=1)
+    elif mode == "extrapolate":
+        kw.update(cg_guess_extrapolate=1, resume_history=1)
     else:
         kw["sweep_tiles"] = 2
     n_phi = prob["mesh"].n_elem * 9
@@ -142,7 +146,7 @@ def test_restored_state_reproduces_the_next_iterates_bit_for_bit(mode):
     y = x3.clone()
     P.smm_iterate(c, y, 1e-30, 2, raise_on_error=False)
     assert not np.array_equal(y.cpu().numpy(), x5)
-    if mode == "anderson2":
+    if mode in ("anderson2", "extrapolate"):
         # with resume_history a run split 3 + 2 takes the steps of one 5-step run
         d = make_gpu(prob, **kw)
         z = zeros(n_phi)

@@ -278,6 +278,32 @@ def test_adaptive_inner_tolerance_reaches_oracle_fixed_point(anderson):
     hb.destroy()
 
 
+def test_extrapolated_cg_start_reaches_oracle_fixed_point_in_fewer_cg_iterations():
+    """Each outer step's CG started from varphi_k + rho (varphi_k - varphi_{k-1})
+    (the default) instead of varphi_k: the oracle's fixed point, the same
+    outer steps within one, fewer CG iterations; the batched iterate too."""
+    import paper_2304_07386_gb300 as P
+    prob = problem(6, 5, m=2, p=2, sn=4, seed=2, kind="mms", c=0.95)
+    disc, op, q, inflow = make_oracle(prob)
+    phi_o, _, _ = op.iterate(tol=1e-13)
+    res = []
+    for ex in (0, 1):
+        h = make_gpu(prob, tol_cg=1e-14, cg_guess_extrapolate=ex)
+        phi = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+        rc, st = P.smm_iterate(h, phi, 1e-11, 200, relative=True)
+        assert rel(phi.cpu().numpy(), phi_o.ravel()) < 1e-9
+        res.append((st["outer_iterations"], st["cg_total"]))
+        h.destroy()
+    assert abs(res[1][0] - res[0][0]) <= 1 and res[1][1] < res[0][1], res
+    hb = make_gpu(prob, tol_cg=1e-14, cg_guess_extrapolate=1)
+    b = P.smm.smm_batch_create([hb])
+    xb = torch.zeros(disc.ne * disc.n, dtype=torch.float64, device="cuda")
+    stats = P.smm.smm_batch_iterate(b, [xb], 1e-11, 200, relative=True)
+    assert rel(xb.cpu().numpy(), phi_o.ravel()) < 1e-9 and stats[0]["cg_total"] < res[0][1]
+    b.destroy()
+    hb.destroy()
+
+
 BATCH = [
     # (nx, ny, m, p, sn, seed)
     (4, 4, 1, 1, 4, None),

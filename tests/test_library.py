@@ -90,7 +90,7 @@ def test_default_options(lib):
     assert o.mg_smoother == S.SMM_SMOOTHER_CHEBYSHEV and o.mg_smooth_steps == 3
     assert o.cg_device_loop == 1 and o.sweep_tiles == 1 and o.negative_flux_fixup == 0
     assert o.moment_discretization == S.SMM_MOMENT_IP
-    assert o.cg_tol_adaptive == 0.0 and o.cycle_lagging == 1
+    assert o.cg_tol_adaptive == 0.0 and o.cycle_lagging == 1 and o.cg_guess_extrapolate == 1
 
 
 class _FakeDeviceBuffer:
