@@ -16,7 +16,9 @@ all, so the device must reproduce the oracle exactly:
   multiple of 2^-8, and certify() checks that each backward sum (input,
   weight and bias gradients of every layer) has sum |terms| < 2^15: every
   FP32 partial sum of it is then exact in any order;
-- the loss's sum of squares is an integer below 2^24.
+- the loss's sum of squares is an integer below 2^24;
+- a few targets are large odd integers, so some output gradients are not
+  BF16 numbers and the rounding of the stored gradients is exercised.
 
 The inputs come from a seeded generator here; certify() reads only the
 oracle's values.
@@ -40,6 +42,11 @@ def case(seed):
         parts.append(rng.integers(-1, 2, size=co).astype(float))
     x = rng.integers(0, 3, size=(B, 3, H, W)).astype(float)
     t = rng.integers(-8, 9, size=(B, N_OUT, H, W)).astype(float)
+    # a few large odd targets: their output gradients 2 (y - t) / n need more
+    # than BF16's 8 significant bits, so the rounding of the stored gradient
+    # is exercised
+    pos = rng.choice(t.size, size=6, replace=False)
+    t.ravel()[pos] = rng.choice([-1.0, 1.0], size=6) * (2 * rng.integers(150, 250, size=6) + 1)
     return np.concatenate(parts), x, t, N_OUT
 
 

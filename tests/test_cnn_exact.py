@@ -1,7 +1,8 @@
 """CPU checks of the exact network cases (tests/cnn_exact.py) that the GPU
 network test compares bit for bit: the exactness certificate holds for the
 seeds the GPU test uses; an evaluation in the library's arithmetic (BF16
-weights and stored activations, FP32 accumulation), written here in NumPy
+weights, stored activations and stored backward gradients, FP32
+accumulation), written here in NumPy
 float32 with its own summation order, reproduces the oracle exactly on them;
 and plausible mistakes planted in that evaluation -- one per kind of layer
 (the 1x1 head, the skip concatenation, the stride-2 convolution, the
@@ -71,26 +72,29 @@ def _emulate(params, x, t, n_out, mistake=None):
     r = (y - t.astype(np.float32)).astype(np.float32)
     loss = float(np.sum(r * r, dtype=np.float32)) / r.size
     gy = (np.float32(2.0) * r / np.float32(r.size)).astype(np.float32)
+    if mistake != "gradient_kept_in_fp32":
+        gy = _bf(gy)
     gu5, gw5, gb5 = _conv_grads32(a5, L[5][0], 1, gy)
     if mistake == "head_bias_misses_a_sample":
         gb5 = gy[:-1].sum(axis=(0, 2, 3), dtype=np.float32)
-    g5 = gu5 if mistake == "a5_mask_dropped" else gu5 * (a5 > 0)
+    g5 = _bf(gu5 if mistake == "a5_mask_dropped" else gu5 * (a5 > 0))
     gcat, gw4, gb4 = _conv_grads32(cat, L[4][0], 1, g5)
     C1 = cnn.C1
-    g4 = gcat[:, :C1] * (a4 > 0)
+    g4 = _bf(gcat[:, :C1] * (a4 > 0))
     g1_skip = gcat[:, C1:] * (a1 > 0)
     gu3, gw3, gb3 = _conv_grads32(u3, L[3][0], 1, g4)
     if mistake == "upsampling_backward_takes_one_of_four":
         gs3 = 4.0 * gu3[:, :, ::2, ::2]
     else:
         gs3 = gu3.reshape(gu3.shape[0], gu3.shape[1], gu3.shape[2] // 2, 2, gu3.shape[3] // 2, 2).sum(axis=(3, 5))
-    g3 = gs3 * (a3 > 0)
+    g3 = _bf(gs3 * (a3 > 0))
     gu2, gw2, gb2 = _conv_grads32(a2, L[2][0], 1, g3)
-    g2 = gu2 * (a2 > 0)
+    g2 = _bf(gu2 * (a2 > 0))
     gu1, gw1, gb1 = _conv_grads32(a1, L[1][0], 2, g2, wrong_stride=mistake == "stride2_weight_grad_at_stride1")
     g1 = gu1 * (a1 > 0)
     if mistake != "skip_gradient_dropped":
         g1 = (g1 + g1_skip).astype(np.float32)
+    g1 = _bf(g1)
     _, gw0, gb0 = _conv_grads32(x0, L[0][0], 1, g1)
     g = np.concatenate([v.ravel() for v in (gw0, gb0, gw1, gb1, gw2, gb2, gw3, gb3, gw4, gb4, gw5, gb5)])
     return y, loss, g
@@ -108,7 +112,7 @@ def test_certified_cases_are_reproduced_exactly_in_any_order(seed):
         assert np.count_nonzero(g_o[sl]) > 0, name
 
 
-@pytest.mark.parametrize("mistake", ["conv3_bias_dropped", "head_bias_misses_a_sample", "a5_mask_dropped",
+@pytest.mark.parametrize("mistake", ["gradient_kept_in_fp32", "conv3_bias_dropped", "head_bias_misses_a_sample", "a5_mask_dropped",
                                      "upsampling_backward_takes_one_of_four", "stride2_weight_grad_at_stride1",
                                      "skip_gradient_dropped"])
 def test_planted_mistakes_change_the_exact_results(mistake):

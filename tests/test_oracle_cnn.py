@@ -1,6 +1,7 @@
 """Pins for the NumPy reference of the learned-guess network: gradients
 against central finite differences (FP64), BF16 rounding, shapes."""
 import numpy as np
+import pytest
 
 from oracle import cnn
 
@@ -13,20 +14,31 @@ def test_bf16_rounding():
     assert abs(r[3] + 3.140625) < 1e-12 and r[4] == 0.0
 
 
-def test_gradients_match_finite_differences():
+@pytest.mark.parametrize("c1,c2", [(cnn.C1, cnn.C2), (16, 48)])
+def test_gradients_match_finite_differences(c1, c2):
     rng = np.random.default_rng(0)
     n_out = 4
-    npar = cnn.num_params(n_out)
+    npar = cnn.num_params(n_out, c1, c2)
     p = rng.standard_normal(npar) * 0.2
     x = rng.standard_normal((2, 3, 6, 4))
     t = rng.standard_normal((2, n_out, 6, 4))
-    loss, g = cnn.loss_and_grad(p, x, t, n_out)
-    y, _ = cnn.forward(p, x, n_out)
+    loss, g = cnn.loss_and_grad(p, x, t, n_out, c1=c1, c2=c2)
+    y, _ = cnn.forward(p, x, n_out, c1=c1, c2=c2)
     assert y.shape == (2, n_out, 6, 4)
     idx = rng.choice(npar, 40, replace=False)
     h = 1e-6
     for i in idx:
         e = np.zeros(npar)
         e[i] = h
-        fd = (cnn.loss_and_grad(p + e, x, t, n_out)[0] - cnn.loss_and_grad(p - e, x, t, n_out)[0]) / (2 * h)
+        fd = (cnn.loss_and_grad(p + e, x, t, n_out, c1=c1, c2=c2)[0] -
+              cnn.loss_and_grad(p - e, x, t, n_out, c1=c1, c2=c2)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_widths_set_the_parameter_count():
+    """Two million parameters at c1 = 64, c2 = 384 (9 (3 c1 + c1 c2 + c2^2 + c2 c1 + 2 c1^2) weights of the 3x3
+    layers, c1 n_out of the head, and one bias per output channel)."""
+    n_out, c1, c2 = 9, 64, 384
+    w = 9 * (3 * c1 + c1 * c2 + c2 * c2 + c2 * c1 + 2 * c1 * c1) + c1 * n_out
+    b = c1 + c2 + c2 + c1 + c1 + n_out
+    assert cnn.num_params(n_out, c1, c2) == w + b == 1_846_473
