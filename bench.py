@@ -322,6 +322,15 @@ def load_peaks() -> tuple:
     return hbm, src
 
 
+def load_tensor_peak() -> tuple:
+    """(dense BF16 TFLOP/s burst, 'measured' | 'fallback')"""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    return float(peaks.get("bf16_tflops", 1900.0)), ("measured" if "bf16_tflops" in peaks else "fallback")
+
+
 # FP32 instruction issue of the whole GPU at the maximum SM clock: 152 SMs x 128 FP32 lanes x 2.07 GHz
 FP32_ISSUE_PEAK = 152 * 128 * 2.07e9
 
@@ -581,6 +590,10 @@ def run_extras(args, P, torch, stream, create, step, phi, flush, ms_sweep_defaul
         extra["batched_sweep"] = run_batch(args.batch, stream)
     if args.learned > 0:
         extra["learned_guess"] = run_learned(args.learned, stream, args.learned_train, args.learned_test)
+    if args.learned_full:
+        # the two-million-parameter network on 128 x 128 problems: 2000 training and 200 held-out solutions
+        extra["learned_guess_full"] = run_learned(128, stream, 2000, 200, widths=(64, 384), steps=args.learned_steps,
+                                                  configs=("plain", "learned_guess", "adaptive_inner_tol", "chosen"))
     return extra
 
 
@@ -796,7 +809,17 @@ def run_batch_full(stream, nprob: int = 256, wave_bytes: float = 150e9) -> dict:
                 note="time to a 1e-8 relative difference for every problem, batched per wave (setup excluded)")
 
 
-def run_learned(nx: int, stream, n_train: int = 192, n_test: int = 16, p: int = 2, sn: int = 8) -> dict:
+def network_flops(nx: int, n_out: int, c1: int, c2: int) -> float:
+    """Algorithmic FLOPs of one sample's forward pass (2 per multiply-add over
+    the real channels of every layer; the half-resolution layers on nx/2)."""
+    full, half = nx * nx, (nx // 2) ** 2
+    macs = 9 * 3 * c1 * full + 9 * c1 * c2 * half + 9 * c2 * c2 * half + 9 * c2 * c1 * full + \
+        9 * 2 * c1 * c1 * full + c1 * n_out * full
+    return 2.0 * macs
+
+
+def run_learned(nx: int, stream, n_train: int = 192, n_test: int = 16, p: int = 2, sn: int = 8,
+                widths=(24, 32), steps: int = 1500, configs=None) -> dict:
     """Learned-guess workload (p=2, S8, log-normal sigma_t / sigma_s fields,
     piecewise-constant source maps, on an nx*nx grid of quads): train the
     library's network on n_train converged solutions the method produces,
@@ -854,13 +877,45 @@ def run_learned(nx: int, stream, n_train: int = 192, n_test: int = 16, p: int = 
     t_gen = time.perf_counter() - t_gen
     X, Y = np.stack(X), np.stack(Y)
     xn, yn = G.Normalizer(X), G.Normalizer(Y)
-    net = P.smm.Guess(nx, nx, n, 16, seed=0, stream=stream)
+    c1, c2 = widths
+    net = P.smm.Guess(nx, nx, n, 16, seed=0, stream=stream, c1=c1, c2=c2)
+    Xd, Yd = torch.as_tensor(xn.fwd(X), device="cuda"), torch.as_tensor(yn.fwd(Y), device="cuda")
     t_train = time.perf_counter()
     with torch.cuda.stream(stream):
-        losses = G.train(net, torch.as_tensor(xn.fwd(X), device="cuda"), torch.as_tensor(yn.fwd(Y), device="cuda"),
-                         steps=1500, batch=16, lr=3e-3)
+        losses = G.train(net, Xd, Yd, steps=steps, batch=16, lr=3e-3 if c2 <= 64 else 1e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t_train
+    # the network's passes alone on a resident batch of 16 (CUDA events on the network's stream):
+    # forward, and forward + backward (gradients, no update)
+    fl = network_flops(nx, n, c1, c2)
+    xb, yb = Xd[:16].contiguous(), Yd[:16].contiguous()
+    out = torch.zeros((16, n, nx, nx), dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            net.forward(xb, out)
+        ev[0].record(stream)
+        for _ in range(10):
+            net.forward(xb, out)
+        ev[1].record(stream)
+        for _ in range(3):
+            net.gradients(xb, yb)
+        ev[2].record(stream)
+        for _ in range(10):
+            net.gradients(xb, yb)
+        ev[3].record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = ev[0].elapsed_time(ev[1]) / 10
+    ms_fb = ev[2].elapsed_time(ev[3]) / 10
+    peak_tensor, peak_src = load_tensor_peak()
+    network = dict(widths=[c1, c2], params=net.n_params, batch=16, forward_ms=ms_fwd, forward_backward_ms=ms_fb,
+                   forward_tflops=16 * fl / ms_fwd * 1e-9, forward_backward_tflops=16 * 3 * fl / ms_fb * 1e-9,
+                   train_steps=steps, train_step_tflops_wall=steps * 16 * 3 * fl / t_train * 1e-12,
+                   roofline=dict(bound="tensor", achieved=16 * 3 * fl / ms_fb * 1e-9, peak=peak_tensor,
+                                 unit="TFLOP/s", frac=16 * 3 * fl / ms_fb * 1e-9 / peak_tensor, peak_source=peak_src,
+                                 note="algorithmic FLOPs (real channels, forward x 3 for forward + backward) of the "
+                                      "mma.sync BF16 implicit-GEMM passes over their measured time (loss, "
+                                      "repacking and reductions included), against the measured cuBLAS BF16 peak"))
 
     seeds = list(range(100_000, 100_000 + n_test))
 
@@ -913,6 +968,8 @@ def run_learned(nx: int, stream, n_train: int = 192, n_test: int = 16, p: int = 
                          ("anderson2", singles, dict(check=False, anderson=2, learned=False)),
                          ("adaptive_inner_tol", singles, dict(check=False, anderson=0, learned=False, adaptive=1e-2)),
                          ("chosen", batched, dict(check=True, anderson=2, learned=True, adaptive=1e-2))):
+        if configs is not None and name not in configs:
+            continue
         dt, st_, xs = fn(**kw)
         if ref is None:
             ref = xs
@@ -922,9 +979,11 @@ def run_learned(nx: int, stream, n_train: int = 192, n_test: int = 16, p: int = 
                           max_rel_diff_vs_plain=max(float((x - r).abs().max() / r.abs().max())
                                                     for x, r in zip(xs, ref)))
     return dict(grid=f"{nx}x{nx}", p=p, sn=sn, train_problems=n_train, test_problems=n_test,
-                params=net.n_params, data_gen_s=t_gen, train_s=t_train, final_loss=float(np.mean(losses[-50:])),
+                params=net.n_params, network=network, data_gen_s=t_gen, train_s=t_train,
+                final_loss=float(np.mean(losses[-50:])),
                 initial_loss=float(np.mean(losses[:10])), **rows,
-                speedup_chosen_vs_plain=rows["plain"]["seconds"] / rows["chosen"]["seconds"],
+                speedup_chosen_vs_plain=(rows["plain"]["seconds"] / rows["chosen"]["seconds"]
+                                         if "plain" in rows and "chosen" in rows else None),
                 note="wall time to a 1e-8 relative successive difference for all held-out problems; plain = the "
                      "default FP64-accuracy method one problem at a time from zero; chosen = learned guess "
                      "(guess_check) + one batched sweep launch per outer step + Anderson depth 2 + moment "
@@ -989,6 +1048,10 @@ def main():
     ap.add_argument("--learned", type=int, default=64, help="element grid of the learned-guess measurement (0: skip)")
     ap.add_argument("--learned-train", type=int, default=192, help="training problems of the learned guess")
     ap.add_argument("--learned-test", type=int, default=16, help="held-out problems of the learned guess")
+    ap.add_argument("--learned-full", action="store_true",
+                    help="the learned guess at full size (128x128, p = 2, S8, 2000 training and 200 held-out "
+                         "problems, the two-million-parameter network; opt-in: about a quarter of an hour)")
+    ap.add_argument("--learned-steps", type=int, default=3000, help="training steps of --learned-full")
     ap.add_argument("--batch-full", type=int, default=0,
                     help="problems of the full-size uneven batched workload solved to 1e-8 in memory-sized waves "
                          "(opt-in: about ten minutes for 256)")

@@ -395,20 +395,30 @@ smm_status smm_batch_iterate(smm_batch b, double tol, int32_t relative, int32_t 
 smm_status smm_batch_destroy(smm_batch b);
 
 /* ---- Learned initial guess (not part of the paper's method) ----
- * A small convolutional encoder-decoder on an H x W element grid (H, W even)
+ * A convolutional encoder-decoder on an H x W element grid (H, W even)
  * mapping 3 input channels (normalized sigma_t, scattering ratio, source) to
- * n_out output channels (normalized varphi and correction-tensor nodal
- * values), trained and evaluated by the library's own kernels: BF16 weights
- * and activations, FP32 accumulation, FP32 master weights, Adam, mean squared
- * error.  Layouts: inputs dev [batch][3][H][W] FP32, outputs and targets dev
- * [batch][n_out][H][W] FP32.  The network only proposes a starting point:
- * smm_iterate still runs to the same tolerance, and options.guess_check makes
- * it fall back to the zero guess when the proposal raises the first residual. */
+ * n_out output channels (normalized nodal varphi), trained and evaluated by
+ * the library's own tensor-core kernels: BF16 weights, activations and stored
+ * gradients, FP32 accumulation, FP32 master weights, Adam, mean squared
+ * error.  Layers: a1 = relu(conv3x3(x, 3 -> c1)), a2 = relu(conv3x3 stride 2
+ * (a1, c1 -> c2)), a3 = relu(conv3x3(a2, c2 -> c2)), a4 = relu(conv3x3(up2(a3),
+ * c2 -> c1)), a5 = relu(conv3x3([a4, a1], 2 c1 -> c1)), y = conv1x1(a5, c1 ->
+ * n_out); parameters flat, layer by layer: weights [cout][cin][ky][kx], then
+ * biases [cout].  Layouts: inputs dev [batch][3][H][W] FP32, outputs and
+ * targets dev [batch][n_out][H][W] FP32.  The network only proposes a starting
+ * point: smm_iterate still runs to the same tolerance, and options.guess_check
+ * makes it fall back to the zero guess when the proposal raises the first
+ * residual. */
 typedef struct smm_guess_ctx* smm_guess;
 
-/* max_batch: largest batch of later calls; seed: weight initialization. */
-smm_status smm_guess_create(int32_t height, int32_t width, int32_t n_out, int32_t max_batch, uint64_t seed,
-                            void* cuda_stream, smm_guess* out);
+/* c1, c2: the widths (24 / 32 for a small network, 64 / 384 for about two
+ * million parameters); max_batch: largest batch of later calls (the
+ * activations of max_batch samples are allocated here); seed: weight
+ * initialization.  SMM_ERR_INVALID_ARG for odd or tiny grids, widths outside
+ * 1..1024, or max_batch x H x W x width beyond 2^31; SMM_ERR_OOM when the
+ * device allocations fail. */
+smm_status smm_guess_create(int32_t height, int32_t width, int32_t n_out, int32_t c1, int32_t c2, int32_t max_batch,
+                            uint64_t seed, void* cuda_stream, smm_guess* out);
 smm_status smm_guess_num_params(smm_guess g, int64_t* n);
 smm_status smm_guess_forward(smm_guess g, int32_t batch, const float* in_dev, float* out_dev);
 /* One Adam step (learning rate lr) on the batch; loss_host (may be NULL) gets the batch loss before the step. */

@@ -1,6 +1,7 @@
-// Learned initial guess: a small convolutional encoder-decoder on the element
-// grid, trained and run with this file's own kernels (BF16 weights and
-// activations, FP32 accumulation, FP32 master weights and Adam state).
+// Learned initial guess: a convolutional encoder-decoder on the element grid,
+// trained and run with this file's own kernels (BF16 weights, activations and
+// stored gradients, FP32 accumulation on the tensor cores, FP32 master weights
+// and Adam state).
 //
 // Network (all convolutions 3x3, zero padding 1, except the last 1x1):
 //   a1 = relu(conv(x, 3 -> C1))                 full resolution
@@ -9,11 +10,27 @@
 //   a4 = relu(conv(up2(a3), C2 -> C1))          full resolution (nearest up-sampling)
 //   a5 = relu(conv([a4, a1], 2 C1 -> C1))       skip connection by channel concatenation
 //   y  = conv1x1(a5, C1 -> n_out)
-// with C1 = 24, C2 = 32.  Loss: mean squared error against the targets.
+// with widths C1, C2 chosen at create (24 / 32 for the small network, 64 / 384
+// for about two million parameters).  Loss: mean squared error.
+//
+// Every convolution pass is an implicit GEMM on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulators): activations and
+// gradients live in HBM as [batch][y][x][channel] with the channel count
+// padded to a multiple of 16 (pad channels hold zero), so that 8 consecutive
+// reduction indices (one tap, 8 channels) are one 16-byte load.
+//   forward      out[pixel][co]  = sum_{tap, c} in[pixel + tap][c] Wf[co][tap, c]
+//   input grad   gin[pixel][c]   = sum_{tap, co} gout[pixel - tap][co] Wb[c][tap, co]
+//   weight grad  gw[co][tap, c]  = sum_{pixel} gout[pixel][co] in[pixel + tap][c]
+// The first two gather their A rows (pixels) and read the repacked BF16
+// weights (Wf, Wb, rebuilt from the FP32 masters after every update); the
+// third reduces over pixels in split chunks whose FP32 partials are summed in
+// a fixed order, so every result is deterministic.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <random>
 #include <string>
@@ -24,169 +41,316 @@
 
 namespace {
 
-constexpr int kC1 = 24, kC2 = 32, kIn = 3;
+constexpr int kIn = 3;
+constexpr int kBM = 64, kBN = 64, kBK = 32, kLds = kBK + 8;  // block tile; smem row of kLds BF16
+constexpr int kGemmThreads = 128;                          // four warps, each a 32 x 32 piece
 
 smm_status fail(smm_status s, const std::string& msg) {
     smm::set_last_error(msg.c_str());
     return s;
 }
 
-struct ConvDesc {
-    int cin1, cin2, cout, k, stride;  // input channels split over two tensors (concatenation)
-    size_t w_off, b_off;              // offsets into the parameter vector
+inline int pad16(int c) { return (c + 15) / 16 * 16; }
+
+// A convolution pass as the GEMM kernel sees it.  Input channels come from up
+// to two tensors (the skip concatenation): part a has ca real channels stored
+// with Ka (padded) per pixel, part b cb / Kb; Kc = Ka + Kb.  Output channels:
+// cout real, Np = pad16(cout) stored.
+struct ConvGeom {
+    int B, Hin, Win, Hout, Wout;
+    int ksz, stride, pad, taps;
+    int ca, Ka, cb, Kb, Kc, cout, Np;
 };
+
+// Epilogue of an input-gradient pass for the channels of one input part:
+// v = acc; v *= (act > 0) if act; v += add if add; stored to out_bf (BF16) or
+// out_f (FP32), ld channels per pixel.
+struct GradPart {
+    const __nv_bfloat16* act;
+    const float* add;
+    __nv_bfloat16* out_bf;
+    float* out_f;
+    int ld;
+};
+
+struct GemmArgs {
+    ConvGeom g;
+    int M, N, K;
+    const __nv_bfloat16* in_a;  // forward / weight grad: the input parts
+    const __nv_bfloat16* in_b;
+    const __nv_bfloat16* gout;  // input / weight grad: the output gradient (Np channels)
+    const __nv_bfloat16* wt;    // forward: Wf [Np][taps*Kc]; input grad: Wb [Kc][taps*Np]
+    // forward epilogue
+    const float* bias;
+    int relu;
+    __nv_bfloat16* out_bf;  // [pixel][Np]
+    float* out_nchw;        // [b][cout][y][x] (the head)
+    // input-grad epilogue
+    GradPart part[2];
+    // weight grad: FP32 partials [split][Np][taps*Kc], kchunk pixels per split
+    float* wpart;
+    int kchunk;
+};
+
+enum { kFwd = 0, kBwdData = 1, kBwdWeight = 2 };
+
+// D += A B on a 16 x 8 x 16 tile: A row-major BF16 pairs, B column-major BF16
+// pairs, FP32 accumulators (the register layout of mma.sync.m16n8k16).
+__device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
 
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
-// out[b][co][y][x] = bias[co] + sum w[co][ci][ky][kx] in[b][ci][y*s+ky-pad][x*s+kx-pad]
-__global__ void conv_fwd_kernel(int B, int Hin, int Win, int Hout, int Wout, ConvDesc d,
-                                const __nv_bfloat16* __restrict__ in1, const __nv_bfloat16* __restrict__ in2,
-                                const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias, int relu,
-                                __nv_bfloat16* __restrict__ out_bf, float* __restrict__ out_f) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tot = (long long)B * d.cout * Hout * Wout;
-    if (t >= tot) return;
-    const int x = (int)(t % Wout), y = (int)((t / Wout) % Hout), co = (int)((t / ((long long)Wout * Hout)) % d.cout);
-    const int b = (int)(t / ((long long)Wout * Hout * d.cout));
-    const int pad = d.k / 2, cin = d.cin1 + d.cin2;
-    float acc = bias[co];
-    for (int ci = 0; ci < cin; ++ci) {
-        const __nv_bfloat16* src = ci < d.cin1 ? in1 + ((size_t)b * d.cin1 + ci) * Hin * Win
-                                              : in2 + ((size_t)b * d.cin2 + (ci - d.cin1)) * Hin * Win;
-        const __nv_bfloat16* wk = w + ((size_t)co * cin + ci) * d.k * d.k;
-        for (int ky = 0; ky < d.k; ++ky) {
-            const int iy = y * d.stride + ky - pad;
-            if (iy < 0 || iy >= Hin) continue;
-            for (int kx = 0; kx < d.k; ++kx) {
-                const int ix = x * d.stride + kx - pad;
-                if (ix < 0 || ix >= Win) continue;
-                acc = fmaf(bf(wk[ky * d.k + kx]), bf(src[(size_t)iy * Win + ix]), acc);
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// One 64 x 64 tile of a convolution pass per block (blockIdx.z: the weight
+// gradient's pixel split).  The reduction runs in steps of 32 through two
+// shared-memory buffers: each thread issues its 16-byte global loads of the
+// next step before the current step's products and stores them to the other
+// buffer after them; one barrier per step.
+template <int MODE>
+__global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs args) {
+    __shared__ __align__(16) __nv_bfloat16 sA[2][kBM * kLds];
+    __shared__ __align__(16) __nv_bfloat16 sB[2][kBN * kLds];
+    const ConvGeom& g = args.g;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+    int k_begin = 0, k_end = args.K;
+    if (MODE == kBwdWeight) {
+        k_begin = blockIdx.z * args.kchunk;
+        k_end = min(args.K, k_begin + args.kchunk);
+    }
+    const int hw_out = g.Hout * g.Wout, hw_in = g.Hin * g.Win;
+
+    // forward / input grad: the two A rows (pixels) of this thread's chunks
+    int rb_[2] = {0, 0}, ry_[2] = {0, 0}, rx_[2] = {0, 0};
+    bool rok[2] = {false, false};
+    if (MODE != kBwdWeight) {
+        #pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int m = m0 + ((tid + i * kGemmThreads) >> 2);
+            rok[i] = m < args.M;
+            const int hw = MODE == kFwd ? hw_out : hw_in, wd = MODE == kFwd ? g.Wout : g.Win;
+            rb_[i] = m / hw;
+            ry_[i] = (m % hw) / wd;
+            rx_[i] = m % wd;
+        }
+    }
+
+    uint4 ra[2], rbv[2];
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    // global -> registers for the reduction step starting at k0
+    auto load = [&](int k0) {
+        #pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = tid + i * kGemmThreads;
+            ra[i] = zero;
+            rbv[i] = zero;
+            if (MODE != kBwdWeight) {
+                const int kc = (q & 3) * 8, r = q >> 2, k = k0 + kc;
+                if (k < k_end) {
+                    if (MODE == kFwd) {
+                        const int tap = k / g.Kc, c = k - tap * g.Kc, ky = tap / g.ksz, kx = tap - ky * g.ksz;
+                        const int iy = ry_[i] * g.stride + ky - g.pad, ix = rx_[i] * g.stride + kx - g.pad;
+                        if (rok[i] && iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win) {
+                            const size_t pix = ((size_t)rb_[i] * g.Hin + iy) * g.Win + ix;
+                            const __nv_bfloat16* src =
+                                c < g.Ka ? args.in_a + pix * g.Ka + c : args.in_b + pix * g.Kb + (c - g.Ka);
+                            ra[i] = *reinterpret_cast<const uint4*>(src);
+                        }
+                    } else {
+                        const int tap = k / g.Np, co = k - tap * g.Np, ky = tap / g.ksz, kx = tap - ky * g.ksz;
+                        const int ny = ry_[i] + g.pad - ky, nx = rx_[i] + g.pad - kx;
+                        if (rok[i] && ny >= 0 && nx >= 0 && ny % g.stride == 0 && nx % g.stride == 0) {
+                            const int oy = ny / g.stride, ox = nx / g.stride;
+                            if (oy < g.Hout && ox < g.Wout) {
+                                const size_t pix = ((size_t)rb_[i] * g.Hout + oy) * g.Wout + ox;
+                                ra[i] = *reinterpret_cast<const uint4*>(args.gout + pix * g.Np + co);
+                            }
+                        }
+                    }
+                    const int n = n0 + r;
+                    if (n < args.N) rbv[i] = *reinterpret_cast<const uint4*>(args.wt + (size_t)n * args.K + k);
+                }
+            } else {
+                const int p = q & 31, j8 = (q >> 5) * 8, kk = k0 + p;
+                if (kk < k_end) {
+                    const int co = m0 + j8;
+                    if (co < args.M) ra[i] = *reinterpret_cast<const uint4*>(args.gout + (size_t)kk * g.Np + co);
+                    const int n = n0 + j8;
+                    if (n < args.N) {
+                        const int tap = n / g.Kc, c = n - tap * g.Kc, ky = tap / g.ksz, kx = tap - ky * g.ksz;
+                        const int b = kk / hw_out, oy = (kk % hw_out) / g.Wout, ox = kk % g.Wout;
+                        const int iy = oy * g.stride + ky - g.pad, ix = ox * g.stride + kx - g.pad;
+                        if (iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win) {
+                            const size_t pix = ((size_t)b * g.Hin + iy) * g.Win + ix;
+                            const __nv_bfloat16* src =
+                                c < g.Ka ? args.in_a + pix * g.Ka + c : args.in_b + pix * g.Kb + (c - g.Ka);
+                            rbv[i] = *reinterpret_cast<const uint4*>(src);
+                        }
+                    }
+                }
             }
         }
-    }
-    if (relu) acc = fmaxf(acc, 0.0f);
-    if (out_bf) out_bf[t] = __float2bfloat16(acc);
-    if (out_f) out_f[t] = acc;
-}
-
-// gin[b][ci][iy][ix] = sum_{co,ky,kx} w[co][ci][ky][kx] gout[b][co][oy][ox], iy = oy*s+ky-pad;
-// ci ranges over the part [c0, c0 + cn) of the concatenated input; gin may be scaled by
-// the ReLU mask of that input (act != nullptr)
-__global__ void conv_bwd_data_kernel(int B, int Hin, int Win, int Hout, int Wout, ConvDesc d, int c0, int cn,
-                                     const __nv_bfloat16* __restrict__ w, const float* __restrict__ gout,
-                                     const __nv_bfloat16* __restrict__ act, float* __restrict__ gin) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tot = (long long)B * cn * Hin * Win;
-    if (t >= tot) return;
-    const int ix = (int)(t % Win), iy = (int)((t / Win) % Hin), cl = (int)((t / ((long long)Win * Hin)) % cn);
-    const int b = (int)(t / ((long long)Win * Hin * cn));
-    const int ci = c0 + cl, cin = d.cin1 + d.cin2, pad = d.k / 2;
-    float acc = 0.0f;
-    for (int co = 0; co < d.cout; ++co) {
-        const float* go = gout + ((size_t)b * d.cout + co) * Hout * Wout;
-        const __nv_bfloat16* wk = w + ((size_t)co * cin + ci) * d.k * d.k;
-        for (int ky = 0; ky < d.k; ++ky) {
-            const int ny = iy + pad - ky;
-            if (ny < 0 || ny % d.stride) continue;
-            const int oy = ny / d.stride;
-            if (oy >= Hout) continue;
-            for (int kx = 0; kx < d.k; ++kx) {
-                const int nx = ix + pad - kx;
-                if (nx < 0 || nx % d.stride) continue;
-                const int ox = nx / d.stride;
-                if (ox >= Wout) continue;
-                acc = fmaf(bf(wk[ky * d.k + kx]), go[(size_t)oy * Wout + ox], acc);
+    };
+    // registers -> shared buffer s (the weight grad transposes: rows = channels, columns = pixels)
+    auto store = [&](int s) {
+        #pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = tid + i * kGemmThreads;
+            if (MODE != kBwdWeight) {
+                const int kc = (q & 3) * 8, r = q >> 2;
+                *reinterpret_cast<uint4*>(&sA[s][r * kLds + kc]) = ra[i];
+                *reinterpret_cast<uint4*>(&sB[s][r * kLds + kc]) = rbv[i];
+            } else {
+                const int p = q & 31, j8 = (q >> 5) * 8;
+                const __nv_bfloat16* ea = reinterpret_cast<const __nv_bfloat16*>(&ra[i]);
+                const __nv_bfloat16* eb = reinterpret_cast<const __nv_bfloat16*>(&rbv[i]);
+                #pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    sA[s][(j8 + e) * kLds + p] = ea[e];
+                    sB[s][(j8 + e) * kLds + p] = eb[e];
+                }
             }
         }
-    }
-    if (act && !(bf(act[t]) > 0.0f)) acc = 0.0f;
-    gin[t] = acc;
-}
+    };
 
-// gw[co][ci][ky][kx] = sum_{b,y,x} gout[b][co][y][x] in[b][ci][y*s+ky-pad][x*s+kx-pad]; one block per weight;
-// blocks with index >= nweights compute the bias gradients
-__global__ void conv_bwd_weight_kernel(int B, int Hin, int Win, int Hout, int Wout, ConvDesc d,
-                                       const __nv_bfloat16* __restrict__ in1, const __nv_bfloat16* __restrict__ in2,
-                                       const float* __restrict__ gout, float* __restrict__ gw, float* __restrict__ gb) {
-    __shared__ float sh[256];
-    const int cin = d.cin1 + d.cin2, kk = d.k * d.k;
-    const int nw = d.cout * cin * kk;
-    const int widx = blockIdx.x;
-    const int n = B * Hout * Wout, pad = d.k / 2;
-    float acc = 0.0f;
-    if (widx < nw) {
-        const int kx = widx % d.k, ky = (widx / d.k) % d.k, ci = (widx / kk) % cin, co = widx / (kk * cin);
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            const int x = t % Wout, y = (t / Wout) % Hout, b = t / (Wout * Hout);
-            const int iy = y * d.stride + ky - pad, ix = x * d.stride + kx - pad;
-            if (iy < 0 || iy >= Hin || ix < 0 || ix >= Win) continue;
-            const __nv_bfloat16* src = ci < d.cin1 ? in1 + ((size_t)b * d.cin1 + ci) * Hin * Win
-                                                  : in2 + ((size_t)b * d.cin2 + (ci - d.cin1)) * Hin * Win;
-            acc = fmaf(gout[((size_t)b * d.cout + co) * Hout * Wout + (size_t)y * Wout + x], bf(src[(size_t)iy * Win + ix]),
-                       acc);
-        }
-    } else {
-        const int co = widx - nw;
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            const int x = t % Wout, y = (t / Wout) % Hout, b = t / (Wout * Hout);
-            acc += gout[((size_t)b * d.cout + co) * Hout * Wout + (size_t)y * Wout + x];
-        }
+    float acc[2][4][4];
+    #pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+        #pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+            #pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.0f;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32, gq = lane >> 2, tq = lane & 3;
+
+    const int nsteps = k_end > k_begin ? (k_end - k_begin + kBK - 1) / kBK : 0;
+    if (nsteps > 0) {
+        load(k_begin);
+        store(0);
     }
-    sh[threadIdx.x] = acc;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    for (int st = 0; st < nsteps; ++st) {
+        const int cur = st & 1;
+        if (st + 1 < nsteps) load(k_begin + (st + 1) * kBK);
+        #pragma unroll
+        for (int ks = 0; ks < kBK; ks += 16) {
+            uint32_t af[2][4], bq[4][2];
+            #pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const __nv_bfloat16* pa = &sA[cur][(wm + mi * 16 + gq) * kLds + ks + 2 * tq];
+                af[mi][0] = lds32(pa);
+                af[mi][1] = lds32(pa + 8 * kLds);
+                af[mi][2] = lds32(pa + 8);
+                af[mi][3] = lds32(pa + 8 * kLds + 8);
+            }
+            #pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                const __nv_bfloat16* pb = &sB[cur][(wn + ni * 8 + gq) * kLds + ks + 2 * tq];
+                bq[ni][0] = lds32(pb);
+                bq[ni][1] = lds32(pb + 8);
+            }
+            #pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+                #pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], af[mi], bq[ni]);
+        }
+        if (st + 1 < nsteps) store(cur ^ 1);
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        if (widx < nw) gw[widx] = sh[0];
-        else gb[widx - nw] = sh[0];
-    }
+
+    // epilogue: accumulator e of tile (mi, ni) is row gq + 8 (e >> 1), column 2 tq + (e & 1)
+    #pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+        #pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+            #pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int row = m0 + wm + mi * 16 + gq + 8 * (e >> 1);
+                const int col = n0 + wn + ni * 8 + 2 * tq + (e & 1);
+                if (row >= args.M || col >= args.N) continue;
+                float v = acc[mi][ni][e];
+                if (MODE == kFwd) {
+                    if (col < g.cout) v += args.bias[col];
+                    if (args.relu) v = fmaxf(v, 0.0f);
+                    if (args.out_bf) args.out_bf[(size_t)row * g.Np + col] = __float2bfloat16(v);
+                    if (args.out_nchw && col < g.cout) {
+                        const int b = row / hw_out, rem = row - b * hw_out;
+                        args.out_nchw[((size_t)b * g.cout + col) * hw_out + rem] = v;
+                    }
+                } else if (MODE == kBwdData) {
+                    const int pi = col < g.Ka ? 0 : 1, lc = pi ? col - g.Ka : col;
+                    const GradPart& P = args.part[pi];
+                    const size_t idx = (size_t)row * P.ld + lc;
+                    if (P.act && !(bf(P.act[idx]) > 0.0f)) v = 0.0f;
+                    if (P.add) v += P.add[idx];
+                    if (P.out_bf) P.out_bf[idx] = __float2bfloat16(v);
+                    if (P.out_f) P.out_f[idx] = v;
+                } else {
+                    args.wpart[((size_t)blockIdx.z * g.Np + row) * args.N + col] = v;
+                }
+            }
 }
 
-__global__ void upsample_kernel(int B, int C, int H, int W, const __nv_bfloat16* __restrict__ in,
+// x [b][3][y][x] FP32 -> [b][y][x][16] BF16 (channels 3..15 zero)
+__global__ void pack_input_kernel(int B, int H, int W, const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long hw = (long long)H * W, tot = (long long)B * hw * 16;
+    if (t >= tot) return;
+    const int c = (int)(t & 15);
+    const long long pix = t >> 4, b = pix / hw, rem = pix - b * hw;
+    out[t] = __float2bfloat16(c < kIn ? in[(b * kIn + c) * hw + rem] : 0.0f);
+}
+
+// nearest up-sampling of [b][h][w][C] to [b][2h][2w][C], 8 channels per thread
+__global__ void upsample_kernel(int B, int H, int W, int C, const __nv_bfloat16* __restrict__ in,
                                 __nv_bfloat16* __restrict__ out) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tot = (long long)B * C * 2 * H * 2 * W;
+    const int c8 = C / 8;
+    const long long tot = (long long)B * 4 * H * W * c8;
     if (t >= tot) return;
-    const int x = (int)(t % (2 * W)), y = (int)((t / (2 * W)) % (2 * H));
-    const long long bc = t / (4LL * H * W);
-    out[t] = in[bc * H * W + (size_t)(y / 2) * W + x / 2];
+    const int j = (int)(t % c8);
+    const long long pix = t / c8;
+    const int x = (int)(pix % (2 * W)), y = (int)((pix / (2 * W)) % (2 * H));
+    const long long b = pix / (4LL * H * W);
+    reinterpret_cast<uint4*>(out)[t] =
+        reinterpret_cast<const uint4*>(in)[((b * H + y / 2) * W + x / 2) * c8 + j];
 }
 
-// g_in[b][c][y][x] = relu'(a) * sum of the four up-sampled gradients
-__global__ void upsample_bwd_kernel(int B, int C, int H, int W, const float* __restrict__ gup,
-                                    const __nv_bfloat16* __restrict__ act, float* __restrict__ gin) {
+// g[b][y][x][c] = bf16((a[b][y][x][c] > 0) * sum of the four up-sampled gradients gup[b][2y+i][2x+j][c])
+__global__ void upsample_bwd_kernel(int B, int H, int W, int C, const float* __restrict__ gup,
+                                    const __nv_bfloat16* __restrict__ act, __nv_bfloat16* __restrict__ g) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tot = (long long)B * C * H * W;
+    const long long tot = (long long)B * H * W * C;
     if (t >= tot) return;
-    const int x = (int)(t % W), y = (int)((t / W) % H);
-    const long long bc = t / ((long long)H * W);
-    const float* g = gup + bc * 4LL * H * W;
-    float s = g[(size_t)(2 * y) * 2 * W + 2 * x] + g[(size_t)(2 * y) * 2 * W + 2 * x + 1] +
-              g[(size_t)(2 * y + 1) * 2 * W + 2 * x] + g[(size_t)(2 * y + 1) * 2 * W + 2 * x + 1];
+    const int c = (int)(t % C);
+    const long long pix = t / C;
+    const int x = (int)(pix % W), y = (int)((pix / W) % H);
+    const long long b = pix / ((long long)H * W);
+    const float* r0 = gup + ((b * 2 * H + 2 * y) * 2 * W + 2 * x) * C + c;
+    const float* r1 = r0 + (size_t)2 * W * C;
+    float s = (r0[0] + r0[C]) + (r1[0] + r1[C]);
     if (!(bf(act[t]) > 0.0f)) s = 0.0f;
-    gin[t] = s;
+    g[t] = __float2bfloat16(s);
 }
 
-__global__ void add_f32_kernel(long long n, float* __restrict__ a, const float* __restrict__ b) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) a[t] += b[t];
-}
-
-__global__ void to_bf16_kernel(long long n, const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) out[t] = __float2bfloat16(in[t]);
-}
-
-// d = 2 (y - target) / count ; partial sums of (y - target)^2 per block
-__global__ void mse_kernel(long long n, const float* __restrict__ y, const float* __restrict__ tgt,
-                           float* __restrict__ g, float* __restrict__ part) {
+// gy[b][y][x][co] = bf16(2 (y - target) / count) (layouts: y, target [b][n_out][y][x]; gy with ld
+// channels per pixel); partial sums of (y - target)^2 per block
+__global__ void mse_kernel(int B, int nout, int hw, int ld, const float* __restrict__ y, const float* __restrict__ tgt,
+                           __nv_bfloat16* __restrict__ gy, float* __restrict__ part) {
     __shared__ float sh[256];
+    const long long n = (long long)B * nout * hw;
     float acc = 0.0f;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const float r = y[t] - tgt[t];
-        g[t] = 2.0f * r / (float)n;
+        const long long b = t / ((long long)nout * hw), rem = t % hw;
+        const int co = (int)((t / hw) % nout);
+        gy[(b * hw + rem) * ld + co] = __float2bfloat16(2.0f * r / (float)n);
         acc += r * r;
     }
     sh[threadIdx.x] = acc;
@@ -198,9 +362,65 @@ __global__ void mse_kernel(long long n, const float* __restrict__ y, const float
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// real input channel of padded channel c (or -1 for a pad channel)
+__device__ __forceinline__ int real_channel(const ConvGeom& g, int c) {
+    if (c < g.Ka) return c < g.ca ? c : -1;
+    const int cb = c - g.Ka;
+    return cb < g.cb ? g.ca + cb : -1;
+}
+
+// Wf[n][tap*Kc + c] and Wb[c][tap*Np + n] in BF16 from the FP32 master w[co][ci][tap] (zero where n or c pads)
+__global__ void repack_kernel(ConvGeom g, const float* __restrict__ w, __nv_bfloat16* __restrict__ wf,
+                              __nv_bfloat16* __restrict__ wb) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)g.Np * g.taps * g.Kc;
+    if (t >= tot) return;
+    const int c = (int)(t % g.Kc), tap = (int)((t / g.Kc) % g.taps), n = (int)(t / ((long long)g.Kc * g.taps));
+    const int ci = real_channel(g, c), cin = g.ca + g.cb;
+    const float v = (n < g.cout && ci >= 0) ? w[((size_t)n * cin + ci) * g.taps + tap] : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16(v);
+    wf[t] = h;
+    wb[((size_t)c * g.taps + tap) * g.Np + n] = h;
+}
+
+// bias-gradient partials: part[chunk][c] = sum of gout[pixel][c] over the chunk's pixels (64 channels per block)
+__global__ void bias_partial_kernel(int npix, int np, int chunk, const __nv_bfloat16* __restrict__ gout,
+                                    float* __restrict__ part) {
+    __shared__ float sh[4][64];
+    const int cl = threadIdx.x & 63, grp = threadIdx.x >> 6, c = blockIdx.x * 64 + cl;
+    const int p0 = blockIdx.y * chunk, p1 = min(npix, p0 + chunk);
+    float acc = 0.0f;
+    if (c < np)
+        for (int p = p0 + grp; p < p1; p += 4) acc += bf(gout[(size_t)p * np + c]);
+    sh[grp][cl] = acc;
+    __syncthreads();
+    if (grp == 0 && c < np) part[(size_t)blockIdx.y * np + c] = ((sh[0][cl] + sh[1][cl]) + sh[2][cl]) + sh[3][cl];
+}
+
+// weight and bias gradients in the flat layout (w[co][ci][ky][kx], then b[co]) from the split partials,
+// each sum over the splits in split order
+__global__ void grad_reduce_kernel(ConvGeom g, int wsplits, const float* __restrict__ wpart, int bsplits,
+                                   const float* __restrict__ bpart, float* __restrict__ gw, float* __restrict__ gb) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cin = g.ca + g.cb;
+    const long long nw = (long long)g.cout * cin * g.taps;
+    if (t < nw) {
+        const int tap = (int)(t % g.taps), ci = (int)((t / g.taps) % cin), co = (int)(t / ((long long)g.taps * cin));
+        const int c = ci < g.ca ? ci : g.Ka + (ci - g.ca);
+        const long long N = (long long)g.taps * g.Kc, col = (long long)tap * g.Kc + c;
+        float s = 0.0f;
+        for (int k = 0; k < wsplits; ++k) s += wpart[((long long)k * g.Np + co) * N + col];
+        gw[t] = s;
+    } else if (t < nw + g.cout) {
+        const int co = (int)(t - nw);
+        float s = 0.0f;
+        for (int k = 0; k < bsplits; ++k) s += bpart[(size_t)k * g.Np + co];
+        gb[co] = s;
+    }
+}
+
 __global__ void adam_kernel(long long n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                            const float* __restrict__ g, __nv_bfloat16* __restrict__ pbf, float lr, float b1, float b2,
-                            float c1, float c2, float eps) {
+                            const float* __restrict__ g, float lr, float b1, float b2, float c1, float c2, float eps) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const float gi = g[t];
@@ -208,9 +428,7 @@ __global__ void adam_kernel(long long n, float* __restrict__ p, float* __restric
     const float vi = b2 * v[t] + (1.0f - b2) * gi * gi;
     m[t] = mi;
     v[t] = vi;
-    const float pi = p[t] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    p[t] = pi;
-    pbf[t] = __float2bfloat16(pi);
+    p[t] = p[t] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
 inline unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -218,22 +436,28 @@ inline unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1)
 }  // namespace
 
 struct smm_guess_ctx {
-    int H = 0, W = 0, nout = 0, maxb = 0;
+    int H = 0, W = 0, nout = 0, maxb = 0, c1 = 0, c2 = 0, P1 = 0, P2 = 0, Po = 0;
     cudaStream_t stream = nullptr;
-    ConvDesc L[6];
+    ConvGeom L[6];                   // per layer, B filled in per call
+    size_t w_off[6], b_off[6];       // offsets of each layer's weights and biases in the flat vector
+    __nv_bfloat16 *wf[6], *wb[6];    // repacked BF16 weights of each layer
     size_t nparam = 0;
     float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // FP32 master, Adam moments, gradients
-    __nv_bfloat16* pb = nullptr;                                       // BF16 copy used by the kernels
     long long step = 0;
-    // activations (BF16) and gradients (FP32) for up to maxb samples
-    __nv_bfloat16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *u3 = nullptr, *a4 = nullptr, *a5 = nullptr;
-    float *y = nullptr, *gy = nullptr, *g5 = nullptr, *g4a = nullptr, *g1 = nullptr, *gu = nullptr, *g3 = nullptr,
-          *g2 = nullptr, *g1b = nullptr, *part = nullptr;
+    // activations and gradients ([b][y][x][channels padded to 16]) for up to maxb samples
+    __nv_bfloat16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *u3 = nullptr, *a4 = nullptr,
+                  *a5 = nullptr, *gy = nullptr, *g5 = nullptr, *g4 = nullptr, *g3 = nullptr, *g2 = nullptr,
+                  *g1 = nullptr;
+    float *y = nullptr, *g1s = nullptr, *gu = nullptr, *wpart = nullptr, *bpart = nullptr, *part = nullptr;
     std::vector<void*> allocs;
+    bool alloc_failed = false;
     template <class T>
     T* alloc(size_t n) {
         void* q = nullptr;
-        if (cudaMalloc(&q, (n ? n : 1) * sizeof(T)) != cudaSuccess) return nullptr;
+        if (cudaMalloc(&q, (n ? n : 1) * sizeof(T)) != cudaSuccess) {
+            alloc_failed = true;
+            return nullptr;
+        }
         allocs.push_back(q);
         return (T*)q;
     }
@@ -244,28 +468,102 @@ struct smm_guess_ctx {
 
 namespace {
 
+constexpr int kBiasChunk = 1024;  // pixels per bias-gradient partial
+
+ConvGeom geom(const smm_guess_ctx* c, int l, int B) {
+    ConvGeom g = c->L[l];
+    g.B = B;
+    return g;
+}
+
+// pixel splits of a weight-gradient pass: about four blocks per SM in total, chunks a multiple of the step
+void weight_splits(long long K, long long tiles, int* splits, int* kchunk) {
+    long long want = std::max(1LL, (4LL * 152 + tiles - 1) / tiles);
+    want = std::min(want, std::max(1LL, (K + kBK - 1) / kBK));
+    long long ch = (K + want - 1) / want;
+    ch = std::max<long long>(kBK, (ch + kBK - 1) / kBK * kBK);
+    *kchunk = (int)ch;
+    *splits = (int)std::max(1LL, (K + ch - 1) / ch);
+}
+
+void launch_fwd(smm_guess g, int l, int B, const __nv_bfloat16* ia, const __nv_bfloat16* ib, int relu,
+                __nv_bfloat16* out_bf, float* out_nchw) {
+    GemmArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = geom(g, l, B);
+    a.M = B * a.g.Hout * a.g.Wout;
+    a.N = a.g.Np;
+    a.K = a.g.taps * a.g.Kc;
+    a.in_a = ia;
+    a.in_b = ib;
+    a.wt = g->wf[l];
+    a.bias = g->p + g->b_off[l];
+    a.relu = relu;
+    a.out_bf = out_bf;
+    a.out_nchw = out_nchw;
+    dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN);
+    conv_gemm_kernel<kFwd><<<grid, kGemmThreads, 0, g->stream>>>(a);
+}
+
+void launch_bwd_data(smm_guess g, int l, int B, const __nv_bfloat16* gout, GradPart p0, GradPart p1) {
+    GemmArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = geom(g, l, B);
+    a.M = B * a.g.Hin * a.g.Win;
+    a.N = a.g.Kc;
+    a.K = a.g.taps * a.g.Np;
+    a.gout = gout;
+    a.wt = g->wb[l];
+    a.part[0] = p0;
+    a.part[1] = p1;
+    dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN);
+    conv_gemm_kernel<kBwdData><<<grid, kGemmThreads, 0, g->stream>>>(a);
+}
+
+void launch_bwd_weight(smm_guess g, int l, int B, const __nv_bfloat16* ia, const __nv_bfloat16* ib,
+                       const __nv_bfloat16* gout) {
+    GemmArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = geom(g, l, B);
+    a.M = a.g.Np;
+    a.N = a.g.taps * a.g.Kc;
+    a.K = B * a.g.Hout * a.g.Wout;
+    a.in_a = ia;
+    a.in_b = ib;
+    a.gout = gout;
+    a.wpart = g->wpart;
+    const long long tiles = (long long)((a.M + kBM - 1) / kBM) * ((a.N + kBN - 1) / kBN);
+    int splits = 1;
+    weight_splits(a.K, tiles, &splits, &a.kchunk);
+    dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN, splits);
+    conv_gemm_kernel<kBwdWeight><<<grid, kGemmThreads, 0, g->stream>>>(a);
+    const int bsplits = (a.K + kBiasChunk - 1) / kBiasChunk;
+    bias_partial_kernel<<<dim3((a.g.Np + 63) / 64, bsplits), 256, 0, g->stream>>>(a.K, a.g.Np, kBiasChunk, gout,
+                                                                                    g->bpart);
+    const long long nw = (long long)a.g.cout * (a.g.ca + a.g.cb) * a.g.taps;
+    grad_reduce_kernel<<<blocks(nw + a.g.cout), 256, 0, g->stream>>>(a.g, splits, g->wpart, bsplits, g->bpart,
+                                                                     g->g + g->w_off[l], g->g + g->b_off[l]);
+}
+
+void repack_all(smm_guess g) {
+    for (int l = 0; l < 6; ++l) {
+        const ConvGeom& d = g->L[l];
+        const long long tot = (long long)d.Np * d.taps * d.Kc;
+        repack_kernel<<<blocks(tot), 256, 0, g->stream>>>(d, g->p + g->w_off[l], g->wf[l], g->wb[l]);
+    }
+}
+
 smm_status guess_forward(smm_guess g, int B, const float* in) {
     const int H = g->H, W = g->W, H2 = H / 2, W2 = W / 2;
-    const long long nin = (long long)B * kIn * H * W;
     cudaStream_t s = g->stream;
-    to_bf16_kernel<<<blocks(nin), 256, 0, s>>>(nin, in, g->x);
-    const __nv_bfloat16* P = g->pb;
-    const float* Pf = g->p;
-    auto conv = [&](int l, int Hin, int Win, int Hout, int Wout, const __nv_bfloat16* i1, const __nv_bfloat16* i2,
-                    int relu, __nv_bfloat16* ob, float* of) {
-        const ConvDesc& d = g->L[l];
-        const long long tot = (long long)B * d.cout * Hout * Wout;
-        conv_fwd_kernel<<<blocks(tot), 256, 0, s>>>(B, Hin, Win, Hout, Wout, d, i1, i2, P + d.w_off, Pf + d.b_off, relu,
-                                                     ob, of);
-    };
-    conv(0, H, W, H, W, g->x, nullptr, 1, g->a1, nullptr);
-    conv(1, H, W, H2, W2, g->a1, nullptr, 1, g->a2, nullptr);
-    conv(2, H2, W2, H2, W2, g->a2, nullptr, 1, g->a3, nullptr);
-    const long long nup = (long long)B * kC2 * H * W;
-    upsample_kernel<<<blocks(nup), 256, 0, s>>>(B, kC2, H2, W2, g->a3, g->u3);
-    conv(3, H, W, H, W, g->u3, nullptr, 1, g->a4, nullptr);
-    conv(4, H, W, H, W, g->a4, g->a1, 1, g->a5, nullptr);
-    conv(5, H, W, H, W, g->a5, nullptr, 0, nullptr, g->y);
+    pack_input_kernel<<<blocks((long long)B * H * W * 16), 256, 0, s>>>(B, H, W, in, g->x);
+    launch_fwd(g, 0, B, g->x, nullptr, 1, g->a1, nullptr);
+    launch_fwd(g, 1, B, g->a1, nullptr, 1, g->a2, nullptr);
+    launch_fwd(g, 2, B, g->a2, nullptr, 1, g->a3, nullptr);
+    upsample_kernel<<<blocks((long long)B * H * W * (g->P2 / 8)), 256, 0, s>>>(B, H2, W2, g->P2, g->a3, g->u3);
+    launch_fwd(g, 3, B, g->u3, nullptr, 1, g->a4, nullptr);
+    launch_fwd(g, 4, B, g->a4, g->a1, 1, g->a5, nullptr);
+    launch_fwd(g, 5, B, g->a5, nullptr, 0, nullptr, g->y);
     if (cudaGetLastError() != cudaSuccess) return fail(SMM_ERR_CUDA, "guess forward launch failed");
     return SMM_OK;
 }
@@ -275,48 +573,30 @@ smm_status guess_backward(smm_guess g, int B, const float* target, float* loss) 
     const int H = g->H, W = g->W, H2 = H / 2, W2 = W / 2;
     cudaStream_t s = g->stream;
     const long long ny = (long long)B * g->nout * H * W;
-    mse_kernel<<<256, 256, 0, s>>>(ny, g->y, target, g->gy, g->part);
-    const __nv_bfloat16* P = g->pb;
-    auto bw = [&](int l, int Hin, int Win, int Hout, int Wout, const __nv_bfloat16* i1, const __nv_bfloat16* i2,
-                  const float* gout) {
-        const ConvDesc& d = g->L[l];
-        const int nw = d.cout * (d.cin1 + d.cin2) * d.k * d.k;
-        conv_bwd_weight_kernel<<<nw + d.cout, 256, 0, s>>>(B, Hin, Win, Hout, Wout, d, i1, i2, gout, g->g + d.w_off,
-                                                            g->g + d.b_off);
-    };
-    auto bd = [&](int l, int Hin, int Win, int Hout, int Wout, int c0, int cn, const float* gout,
-                  const __nv_bfloat16* act, float* gin) {
-        const ConvDesc& d = g->L[l];
-        const long long tot = (long long)B * cn * Hin * Win;
-        conv_bwd_data_kernel<<<blocks(tot), 256, 0, s>>>(B, Hin, Win, Hout, Wout, d, c0, cn, P + d.w_off, gout, act,
-                                                          gin);
-    };
+    mse_kernel<<<256, 256, 0, s>>>(B, g->nout, H * W, g->Po, g->y, target, g->gy, g->part);
+    const GradPart none{nullptr, nullptr, nullptr, nullptr, 0};
     // y = conv1x1(a5)
-    bw(5, H, W, H, W, g->a5, nullptr, g->gy);
-    bd(5, H, W, H, W, 0, kC1, g->gy, g->a5, g->g5);                 // g5 = dL/d(pre-activation of a5)
+    launch_bwd_weight(g, 5, B, g->a5, nullptr, g->gy);
+    launch_bwd_data(g, 5, B, g->gy, GradPart{g->a5, nullptr, g->g5, nullptr, g->P1}, none);
     // a5 = relu(conv([a4, a1]))
-    bw(4, H, W, H, W, g->a4, g->a1, g->g5);
-    bd(4, H, W, H, W, 0, kC1, g->g5, g->a4, g->g4a);                // through a4's ReLU
-    bd(4, H, W, H, W, kC1, kC1, g->g5, g->a1, g->g1b);              // skip path into a1 (ReLU of a1)
-    // a4 = relu(conv(u3))
-    bw(3, H, W, H, W, g->u3, nullptr, g->g4a);
-    bd(3, H, W, H, W, 0, kC2, g->g4a, nullptr, g->gu);              // gradient w.r.t. u3
-    const long long n3 = (long long)B * kC2 * H2 * W2;
-    upsample_bwd_kernel<<<blocks(n3), 256, 0, s>>>(B, kC2, H2, W2, g->gu, g->a3, g->g3);
+    launch_bwd_weight(g, 4, B, g->a4, g->a1, g->g5);
+    launch_bwd_data(g, 4, B, g->g5, GradPart{g->a4, nullptr, g->g4, nullptr, g->P1},
+                    GradPart{g->a1, nullptr, nullptr, g->g1s, g->P1});
+    // a4 = relu(conv(u3)), u3 = up2(a3)
+    launch_bwd_weight(g, 3, B, g->u3, nullptr, g->g4);
+    launch_bwd_data(g, 3, B, g->g4, GradPart{nullptr, nullptr, nullptr, g->gu, g->P2}, none);
+    upsample_bwd_kernel<<<blocks((long long)B * H2 * W2 * g->P2), 256, 0, s>>>(B, H2, W2, g->P2, g->gu, g->a3, g->g3);
     // a3 = relu(conv(a2))
-    bw(2, H2, W2, H2, W2, g->a2, nullptr, g->g3);
-    bd(2, H2, W2, H2, W2, 0, kC2, g->g3, g->a2, g->g2);
-    // a2 = relu(conv_s2(a1))
-    bw(1, H, W, H2, W2, g->a1, nullptr, g->g2);
-    bd(1, H, W, H2, W2, 0, kC1, g->g2, g->a1, g->g1);
-    // a1 gradient = main path + skip path; a1 = relu(conv(x))
-    {
-        const long long n1 = (long long)B * kC1 * H * W;
-        add_f32_kernel<<<blocks(n1), 256, 0, s>>>(n1, g->g1, g->g1b);
-    }
-    bw(0, H, W, H, W, g->x, nullptr, g->g1);
+    launch_bwd_weight(g, 2, B, g->a2, nullptr, g->g3);
+    launch_bwd_data(g, 2, B, g->g3, GradPart{g->a2, nullptr, g->g2, nullptr, g->P2}, none);
+    // a2 = relu(conv_s2(a1)); a1's gradient = main path + skip path
+    launch_bwd_weight(g, 1, B, g->a1, nullptr, g->g2);
+    launch_bwd_data(g, 1, B, g->g2, GradPart{g->a1, g->g1s, g->g1, nullptr, g->P1}, none);
+    // a1 = relu(conv(x))
+    launch_bwd_weight(g, 0, B, g->x, nullptr, g->g1);
     std::vector<float> part(256);
-    if (cudaMemcpyAsync(part.data(), g->part, 256 * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(part.data(), g->part, 256 * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(SMM_ERR_CUDA, "guess backward failed");
     double sum = 0.0;
@@ -329,24 +609,43 @@ smm_status guess_backward(smm_guess g, int B, const float* target, float* loss) 
 
 extern "C" {
 
-smm_status smm_guess_create(int32_t height, int32_t width, int32_t n_out, int32_t max_batch, uint64_t seed,
-                            void* cuda_stream, smm_guess* out) {
-    if (!out || height < 2 || width < 2 || (height & 1) || (width & 1) || n_out < 1 || max_batch < 1)
-        return fail(SMM_ERR_INVALID_ARG, "smm_guess_create: bad sizes (height and width must be even)");
+smm_status smm_guess_create(int32_t height, int32_t width, int32_t n_out, int32_t c1, int32_t c2, int32_t max_batch,
+                            uint64_t seed, void* cuda_stream, smm_guess* out) {
+    if (!out || height < 2 || width < 2 || (height & 1) || (width & 1) || n_out < 1 || n_out > 1024 || max_batch < 1 ||
+        c1 < 1 || c1 > 1024 || c2 < 1 || c2 > 1024)
+        return fail(SMM_ERR_INVALID_ARG,
+                    "smm_guess_create: bad sizes (height and width even, 1 <= n_out, c1, c2 <= 1024)");
+    const long long pix = (long long)max_batch * height * width;
+    if (pix * pad16(c1 > c2 ? c1 : c2) > (1LL << 31) || pix > (1LL << 30))
+        return fail(SMM_ERR_INVALID_ARG, "smm_guess_create: max_batch x height x width x width of a layer too large");
     *out = nullptr;
     auto* g = new smm_guess_ctx();
-    auto bail = [&](smm_status st, const std::string& m) { delete g; return fail(st, m); };
-    g->H = height; g->W = width; g->nout = n_out; g->maxb = max_batch;
+    auto bail = [&](smm_status st, const std::string& msg) {
+        delete g;
+        return fail(st, msg);
+    };
+    g->H = height; g->W = width; g->nout = n_out; g->maxb = max_batch; g->c1 = c1; g->c2 = c2;
+    g->P1 = pad16(c1); g->P2 = pad16(c2); g->Po = pad16(n_out);
     g->stream = (cudaStream_t)cuda_stream;
-    const int spec[6][5] = {{kIn, 0, kC1, 3, 1}, {kC1, 0, kC2, 3, 2}, {kC2, 0, kC2, 3, 1},
-                            {kC2, 0, kC1, 3, 1}, {kC1, kC1, kC1, 3, 1}, {kC1, 0, n_out, 1, 1}};
+    const int H = height, W = width, H2 = H / 2, W2 = W / 2;
+    // per layer: input size, output size, kernel, stride, parts (real, padded), cout
+    const int spec[6][11] = {{H, W, H, W, 3, 1, kIn, 16, 0, 0, c1},
+                             {H, W, H2, W2, 3, 2, c1, g->P1, 0, 0, c2},
+                             {H2, W2, H2, W2, 3, 1, c2, g->P2, 0, 0, c2},
+                             {H, W, H, W, 3, 1, c2, g->P2, 0, 0, c1},
+                             {H, W, H, W, 3, 1, c1, g->P1, c1, g->P1, c1},
+                             {H, W, H, W, 1, 1, c1, g->P1, 0, 0, n_out}};
     size_t off = 0;
     for (int l = 0; l < 6; ++l) {
-        ConvDesc& d = g->L[l];
-        d.cin1 = spec[l][0]; d.cin2 = spec[l][1]; d.cout = spec[l][2]; d.k = spec[l][3]; d.stride = spec[l][4];
-        d.w_off = off;
-        off += (size_t)d.cout * (d.cin1 + d.cin2) * d.k * d.k;
-        d.b_off = off;
+        ConvGeom& d = g->L[l];
+        const int* s = spec[l];
+        d.B = 0; d.Hin = s[0]; d.Win = s[1]; d.Hout = s[2]; d.Wout = s[3];
+        d.ksz = s[4]; d.stride = s[5]; d.pad = s[4] / 2; d.taps = s[4] * s[4];
+        d.ca = s[6]; d.Ka = s[7]; d.cb = s[8]; d.Kb = s[9]; d.Kc = d.Ka + d.Kb;
+        d.cout = s[10]; d.Np = pad16(d.cout);
+        g->w_off[l] = off;
+        off += (size_t)d.cout * (d.ca + d.cb) * d.taps;
+        g->b_off[l] = off;
         off += d.cout;
     }
     g->nparam = off;
@@ -354,39 +653,57 @@ smm_status smm_guess_create(int32_t height, int32_t width, int32_t n_out, int32_
     std::vector<float> host(off, 0.0f);
     std::mt19937_64 rng(seed);
     for (int l = 0; l < 6; ++l) {
-        const ConvDesc& d = g->L[l];
-        const int fan_in = (d.cin1 + d.cin2) * d.k * d.k;
+        const ConvGeom& d = g->L[l];
+        const int fan_in = (d.ca + d.cb) * d.taps;
         const float a = std::sqrt(6.0f / (float)fan_in) * (l == 5 ? 0.5f : 1.0f);
         std::uniform_real_distribution<float> U(-a, a);
-        for (size_t i = d.w_off; i < d.b_off; ++i) host[i] = U(rng);
+        for (size_t i = g->w_off[l]; i < g->b_off[l]; ++i) host[i] = U(rng);
     }
-    const size_t H = height, W = width, B = max_batch;
+    // split partials of the weight and bias gradients at the largest batch
+    size_t wmax = 1, bmax = 1;
+    for (int l = 0; l < 6; ++l) {
+        const ConvGeom& d = g->L[l];
+        const long long K = pix / ((long long)(H / d.Hout) * (W / d.Wout)), N = (long long)d.taps * d.Kc;
+        const long long tiles = (long long)((d.Np + kBM - 1) / kBM) * ((N + kBN - 1) / kBN);
+        // weight_splits never gives more splits than min(ceil(608 / tiles), ceil(K / kBK)), which is
+        // largest at the largest batch
+        const long long bound =
+            std::max(1LL, std::min((4LL * 152 + tiles - 1) / tiles, (K + kBK - 1) / kBK));
+        wmax = std::max(wmax, (size_t)bound * (size_t)d.Np * (size_t)N);
+        bmax = std::max(bmax, (size_t)((K + kBiasChunk - 1) / kBiasChunk) * d.Np);
+    }
+    const size_t HW = (size_t)H * W, B = max_batch;
     g->p = g->alloc<float>(off); g->m = g->alloc<float>(off); g->v = g->alloc<float>(off); g->g = g->alloc<float>(off);
-    g->pb = g->alloc<__nv_bfloat16>(off);
-    g->x = g->alloc<__nv_bfloat16>(B * kIn * H * W);
-    g->a1 = g->alloc<__nv_bfloat16>(B * kC1 * H * W);
-    g->a2 = g->alloc<__nv_bfloat16>(B * kC2 * H * W / 4);
-    g->a3 = g->alloc<__nv_bfloat16>(B * kC2 * H * W / 4);
-    g->u3 = g->alloc<__nv_bfloat16>(B * kC2 * H * W);
-    g->a4 = g->alloc<__nv_bfloat16>(B * kC1 * H * W);
-    g->a5 = g->alloc<__nv_bfloat16>(B * kC1 * H * W);
-    g->y = g->alloc<float>(B * n_out * H * W);
-    g->gy = g->alloc<float>(B * n_out * H * W);
-    g->g5 = g->alloc<float>(B * kC1 * H * W);
-    g->g4a = g->alloc<float>(B * kC1 * H * W);
-    g->g1 = g->alloc<float>(B * kC1 * H * W);
-    g->g1b = g->alloc<float>(B * kC1 * H * W);
-    g->gu = g->alloc<float>(B * kC2 * H * W);
-    g->g3 = g->alloc<float>(B * kC2 * H * W / 4);
-    g->g2 = g->alloc<float>(B * kC2 * H * W / 4);
+    for (int l = 0; l < 6; ++l) {
+        const ConvGeom& d = g->L[l];
+        g->wf[l] = g->alloc<__nv_bfloat16>((size_t)d.Np * d.taps * d.Kc);
+        g->wb[l] = g->alloc<__nv_bfloat16>((size_t)d.Np * d.taps * d.Kc);
+    }
+    g->x = g->alloc<__nv_bfloat16>(B * HW * 16);
+    g->a1 = g->alloc<__nv_bfloat16>(B * HW * g->P1);
+    g->a2 = g->alloc<__nv_bfloat16>(B * HW / 4 * g->P2);
+    g->a3 = g->alloc<__nv_bfloat16>(B * HW / 4 * g->P2);
+    g->u3 = g->alloc<__nv_bfloat16>(B * HW * g->P2);
+    g->a4 = g->alloc<__nv_bfloat16>(B * HW * g->P1);
+    g->a5 = g->alloc<__nv_bfloat16>(B * HW * g->P1);
+    g->y = g->alloc<float>(B * HW * n_out);
+    g->gy = g->alloc<__nv_bfloat16>(B * HW * g->Po);
+    g->g5 = g->alloc<__nv_bfloat16>(B * HW * g->P1);
+    g->g4 = g->alloc<__nv_bfloat16>(B * HW * g->P1);
+    g->g1s = g->alloc<float>(B * HW * g->P1);
+    g->gu = g->alloc<float>(B * HW * g->P2);
+    g->g3 = g->alloc<__nv_bfloat16>(B * HW / 4 * g->P2);
+    g->g2 = g->alloc<__nv_bfloat16>(B * HW / 4 * g->P2);
+    g->g1 = g->alloc<__nv_bfloat16>(B * HW * g->P1);
+    g->wpart = g->alloc<float>(wmax);
+    g->bpart = g->alloc<float>(bmax);
     g->part = g->alloc<float>(256);
-    for (void* q : g->allocs)
-        if (!q) return bail(SMM_ERR_OOM, "smm_guess_create: device allocation failed");
-    if (g->allocs.size() < 22) return bail(SMM_ERR_OOM, "smm_guess_create: device allocation failed");
+    if (g->alloc_failed) return bail(SMM_ERR_OOM, "smm_guess_create: device allocation failed");
     if (cudaMemcpy(g->p, host.data(), off * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(g->m, 0, off * sizeof(float)) != cudaSuccess || cudaMemset(g->v, 0, off * sizeof(float)) != cudaSuccess)
+        cudaMemset(g->m, 0, off * sizeof(float)) != cudaSuccess || cudaMemset(g->v, 0, off * sizeof(float)) != cudaSuccess ||
+        cudaMemset(g->gy, 0, B * HW * g->Po * sizeof(__nv_bfloat16)) != cudaSuccess)
         return bail(SMM_ERR_CUDA, "smm_guess_create: upload failed");
-    to_bf16_kernel<<<blocks((long long)off), 256, 0, g->stream>>>((long long)off, g->p, g->pb);
+    repack_all(g);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) return bail(SMM_ERR_CUDA, "smm_guess_create: init failed");
     *out = g;
     return SMM_OK;
@@ -432,8 +749,9 @@ smm_status smm_guess_train_step(smm_guess g, int32_t batch, const float* in_dev,
     g->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - std::pow(b1, (float)g->step), c2 = 1.0f - std::pow(b2, (float)g->step);
-    adam_kernel<<<blocks((long long)g->nparam), 256, 0, g->stream>>>((long long)g->nparam, g->p, g->m, g->v, g->g, g->pb,
-                                                                      lr, b1, b2, c1, c2, 1e-8f);
+    adam_kernel<<<blocks((long long)g->nparam), 256, 0, g->stream>>>((long long)g->nparam, g->p, g->m, g->v, g->g, lr,
+                                                                      b1, b2, c1, c2, 1e-8f);
+    repack_all(g);
     if (cudaGetLastError() != cudaSuccess) return fail(SMM_ERR_CUDA, "adam launch failed");
     return SMM_OK;
 }
@@ -449,7 +767,7 @@ smm_status smm_guess_set_params(smm_guess g, const float* host) {
     if (!g || !host) return fail(SMM_ERR_INVALID_ARG, "NULL argument");
     if (cudaMemcpy(g->p, host, g->nparam * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(SMM_ERR_CUDA, "parameter copy failed");
-    to_bf16_kernel<<<blocks((long long)g->nparam), 256, 0, g->stream>>>((long long)g->nparam, g->p, g->pb);
+    repack_all(g);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) return fail(SMM_ERR_CUDA, "parameter upload failed");
     return SMM_OK;
 }

@@ -105,7 +105,8 @@ def load_library(path: str | None = None):
     for name in ("smm_batch_create", "smm_batch_schedule", "smm_batch_sweep", "smm_batch_iterate", "smm_batch_destroy"):
         getattr(lib, name).restype = C.c_int
     fp = C.POINTER(C.c_float)
-    lib.smm_guess_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, vp, C.POINTER(vp)]
+    lib.smm_guess_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, vp,
+                                     C.POINTER(vp)]
     lib.smm_guess_num_params.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.smm_guess_forward.argtypes = [vp, C.c_int32, vp, vp]
     lib.smm_guess_train_step.argtypes = [vp, C.c_int32, vp, vp, C.c_float, fp]
@@ -424,16 +425,17 @@ def _fdev(t, count=None, what="buffer"):
 class Guess:
     """Owns an smm_guess network; methods mirror the C calls."""
 
-    def __init__(self, height, width, n_out, max_batch, seed=0, stream=None):
+    def __init__(self, height, width, n_out, max_batch, seed=0, stream=None, c1=24, c2=32):
         import torch
 
         self.shape = (height, width, n_out)
+        self.widths = (c1, c2)
         self.max_batch = max_batch
         s = stream if stream is not None else torch.cuda.current_stream()
         self._stream = s
         self.ptr = C.c_void_p()
-        _check(load_library().smm_guess_create(height, width, n_out, max_batch, seed, C.c_void_p(s.cuda_stream),
-                                               C.byref(self.ptr)))
+        _check(load_library().smm_guess_create(height, width, n_out, c1, c2, max_batch, seed,
+                                               C.c_void_p(s.cuda_stream), C.byref(self.ptr)))
         n = C.c_int64(0)
         _check(load_library().smm_guess_num_params(self.ptr, C.byref(n)))
         self.n_params = n.value

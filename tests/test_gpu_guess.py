@@ -81,6 +81,47 @@ def test_network_forward_and_gradients_match_oracle_elementwise():
             assert np.all(np.abs(g[sl] - g_ref[sl]) <= 1e-2 * np.max(np.abs(g_ref[sl]))), name
 
 
+def test_two_million_parameter_network_matches_oracle_elementwise():
+    """The network at the widths of the two-million-parameter configuration
+    (c1 = 64, c2 = 384: 1,846,473 parameters), He-initialized by the library
+    with non-zero biases, on a 12 x 10 grid: forward output and every gradient
+    entry against the oracle (bf=True) as in the test above.  Its reductions
+    have up to 3,456 terms (9 taps x 384 channels) per output and span several
+    64 x 64 tiles of the tensor-core passes in both the pixel and channel
+    directions."""
+    import paper_2304_07386_gb300 as P
+    from oracle import cnn
+    H, Wd, n_out, B, c1, c2 = 12, 10, 9, 3, 64, 384
+    net = P.smm.Guess(H, Wd, n_out, B, seed=5, c1=c1, c2=c2)
+    assert net.n_params == cnn.num_params(n_out, c1, c2) == 1_846_473
+    rng = np.random.default_rng(7)
+    params = net.get_params()
+    off = 0
+    for ci, co, k, _ in cnn.layer_specs(n_out, c1, c2):
+        off += co * ci * k * k
+        params[off:off + co] = rng.standard_normal(co).astype(np.float32) * 0.1
+        off += co
+    net.set_params(params)
+    x = rng.standard_normal((B, 3, H, Wd)).astype(np.float32)
+    t = rng.standard_normal((B, n_out, H, Wd)).astype(np.float32)
+    xd, td = torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda")
+    y = torch.zeros((B, n_out, H, Wd), dtype=torch.float32, device="cuda")
+    net.forward(xd, y)
+    p64 = params.astype(np.float64)
+    y_ref, _ = cnn.forward(p64, x.astype(np.float64), n_out, bf=True, c1=c1, c2=c2)
+    scale = np.max(np.abs(y_ref), axis=(0, 2, 3), keepdims=True)
+    assert np.all(np.abs(y.cpu().numpy() - y_ref) <= 1e-2 * scale)
+    loss, g = net.gradients(xd, td)
+    loss_ref, g_ref = cnn.loss_and_grad(p64, x.astype(np.float64), t.astype(np.float64), n_out, bf=True, c1=c1, c2=c2)
+    assert abs(loss - loss_ref) < 1e-3 * loss_ref
+    off = 0
+    for i, (ci, co, k, _) in enumerate(cnn.layer_specs(n_out, c1, c2)):
+        for name, n in (("weights", co * ci * k * k), ("bias", co)):
+            sl = slice(off, off + n)
+            off += n
+            assert np.all(np.abs(g[sl] - g_ref[sl]) <= 1e-2 * np.max(np.abs(g_ref[sl]))), (i, name)
+
+
 def _solve(P, nx, seed, phi0=None, check=False, p=2, sn=4, tol=1e-8):
     mesh, st, ss, qe = W.learned_guess_problem(nx, seed)
     n = (p + 1) ** 2
