@@ -480,6 +480,10 @@ def run_ours(args) -> None:
     if not args.quick:
         extra.update(run_extras(args, P, torch, stream, create, step, phi, flush, ms_sweep))
     h.destroy()
+    if args.learned_full:
+        # the two-million-parameter network on 128 x 128 problems: 2000 training and 200 held-out solutions
+        extra["learned_guess_full"] = run_learned(128, stream, 2000, 200, widths=(64, 384), steps=args.learned_steps,
+                                                  configs=("plain", "learned_guess", "adaptive_inner_tol", "chosen"))
     if args.batch_full > 0:
         extra["batched_full"] = run_batch_full(stream, args.batch_full)
 
@@ -590,10 +594,6 @@ def run_extras(args, P, torch, stream, create, step, phi, flush, ms_sweep_defaul
         extra["batched_sweep"] = run_batch(args.batch, stream)
     if args.learned > 0:
         extra["learned_guess"] = run_learned(args.learned, stream, args.learned_train, args.learned_test)
-    if args.learned_full:
-        # the two-million-parameter network on 128 x 128 problems: 2000 training and 200 held-out solutions
-        extra["learned_guess_full"] = run_learned(128, stream, 2000, 200, widths=(64, 384), steps=args.learned_steps,
-                                                  configs=("plain", "learned_guess", "adaptive_inner_tol", "chosen"))
     return extra
 
 
@@ -1050,7 +1050,8 @@ def main():
     ap.add_argument("--learned-test", type=int, default=16, help="held-out problems of the learned guess")
     ap.add_argument("--learned-full", action="store_true",
                     help="the learned guess at full size (128x128, p = 2, S8, 2000 training and 200 held-out "
-                         "problems, the two-million-parameter network; opt-in: about a quarter of an hour)")
+                         "problems, the two-million-parameter network; opt-in: about a quarter of an hour; also "
+                         "with --quick)")
     ap.add_argument("--learned-steps", type=int, default=3000, help="training steps of --learned-full")
     ap.add_argument("--batch-full", type=int, default=0,
                     help="problems of the full-size uneven batched workload solved to 1e-8 in memory-sized waves "
