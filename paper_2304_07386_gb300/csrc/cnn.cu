@@ -43,6 +43,7 @@ namespace {
 
 constexpr int kIn = 3;
 constexpr int kBM = 64, kBN = 64, kBK = 32, kLds = kBK + 8;  // block tile; smem row of kLds BF16
+constexpr int kLdt = kBM + 8;  // weight grad: smem row (one pixel) of kLdt BF16 channels
 constexpr int kGemmThreads = 128;                          // four warps, each a 32 x 32 piece
 
 smm_status fail(smm_status s, const std::string& msg) {
@@ -104,15 +105,33 @@ __device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, cons
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+// Four 8 x 8 BF16 matrices from shared memory: lane l gives the address of row
+// l % 8 of matrix l / 8 (16 contiguous bytes); register j of lane t receives
+// row t / 4, columns 2 (t % 4) and 2 (t % 4) + 1 of matrix j (ldmatrix.x4), or
+// with .trans rows 2 (t % 4), 2 (t % 4) + 1 of column t / 4.
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const __nv_bfloat16* p) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const __nv_bfloat16* p) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
 
-__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
 // One 64 x 64 tile of a convolution pass per block (blockIdx.z: the weight
 // gradient's pixel split).  The reduction runs in steps of 32 through two
 // shared-memory buffers: each thread issues its 16-byte global loads of the
 // next step before the current step's products and stores them to the other
-// buffer after them; one barrier per step.
+// buffer after them; one barrier per step.  Forward and input gradient keep
+// both operands as rows of 32 reduction indices ([m][k], [n][k]); the weight
+// gradient, whose reduction index is the pixel, keeps them as rows of
+// channels ([k][m], [k][n]) and reads its fragments transposed.
 template <int MODE>
 __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs args) {
     __shared__ __align__(16) __nv_bfloat16 sA[2][kBM * kLds];
@@ -131,7 +150,7 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
     int rb_[2] = {0, 0}, ry_[2] = {0, 0}, rx_[2] = {0, 0};
     bool rok[2] = {false, false};
     if (MODE != kBwdWeight) {
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int m = m0 + ((tid + i * kGemmThreads) >> 2);
             rok[i] = m < args.M;
@@ -146,7 +165,7 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
     // global -> registers for the reduction step starting at k0
     auto load = [&](int k0) {
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int q = tid + i * kGemmThreads;
             ra[i] = zero;
@@ -200,7 +219,7 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
     };
     // registers -> shared buffer s (the weight grad transposes: rows = channels, columns = pixels)
     auto store = [&](int s) {
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int q = tid + i * kGemmThreads;
             if (MODE != kBwdWeight) {
@@ -209,23 +228,18 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
                 *reinterpret_cast<uint4*>(&sB[s][r * kLds + kc]) = rbv[i];
             } else {
                 const int p = q & 31, j8 = (q >> 5) * 8;
-                const __nv_bfloat16* ea = reinterpret_cast<const __nv_bfloat16*>(&ra[i]);
-                const __nv_bfloat16* eb = reinterpret_cast<const __nv_bfloat16*>(&rbv[i]);
-                #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    sA[s][(j8 + e) * kLds + p] = ea[e];
-                    sB[s][(j8 + e) * kLds + p] = eb[e];
-                }
+                *reinterpret_cast<uint4*>(&sA[s][p * kLdt + j8]) = ra[i];
+                *reinterpret_cast<uint4*>(&sB[s][p * kLdt + j8]) = rbv[i];
             }
         }
     };
 
     float acc[2][4][4];
-    #pragma unroll
+#pragma unroll
     for (int mi = 0; mi < 2; ++mi)
-        #pragma unroll
+#pragma unroll
         for (int ni = 0; ni < 4; ++ni)
-            #pragma unroll
+#pragma unroll
             for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.0f;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32, gq = lane >> 2, tq = lane & 3;
 
@@ -238,26 +252,34 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
     for (int st = 0; st < nsteps; ++st) {
         const int cur = st & 1;
         if (st + 1 < nsteps) load(k_begin + (st + 1) * kBK);
-        #pragma unroll
+#pragma unroll
         for (int ks = 0; ks < kBK; ks += 16) {
+            // A of rows wm + 16 mi: matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15) in the order a0..a3;
+            // B of columns wn + 8 nj, two n8 tiles per load: (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, ...)
             uint32_t af[2][4], bq[4][2];
-            #pragma unroll
+            const int r8 = lane & 7, j1 = (lane >> 3) & 1, j2 = lane >> 4;
+#pragma unroll
             for (int mi = 0; mi < 2; ++mi) {
-                const __nv_bfloat16* pa = &sA[cur][(wm + mi * 16 + gq) * kLds + ks + 2 * tq];
-                af[mi][0] = lds32(pa);
-                af[mi][1] = lds32(pa + 8 * kLds);
-                af[mi][2] = lds32(pa + 8);
-                af[mi][3] = lds32(pa + 8 * kLds + 8);
+                if (MODE != kBwdWeight)
+                    ldsm_x4(af[mi], &sA[cur][(wm + mi * 16 + r8 + 8 * j1) * kLds + ks + 8 * j2]);
+                else
+                    ldsm_x4_trans(af[mi], &sA[cur][(ks + 8 * j2 + r8) * kLdt + wm + mi * 16 + 8 * j1]);
             }
-            #pragma unroll
-            for (int ni = 0; ni < 4; ++ni) {
-                const __nv_bfloat16* pb = &sB[cur][(wn + ni * 8 + gq) * kLds + ks + 2 * tq];
-                bq[ni][0] = lds32(pb);
-                bq[ni][1] = lds32(pb + 8);
+#pragma unroll
+            for (int nj = 0; nj < 4; nj += 2) {
+                uint32_t r[4];
+                if (MODE != kBwdWeight)
+                    ldsm_x4(r, &sB[cur][(wn + nj * 8 + r8 + 8 * j2) * kLds + ks + 8 * j1]);
+                else
+                    ldsm_x4_trans(r, &sB[cur][(ks + 8 * j1 + r8) * kLdt + wn + nj * 8 + 8 * j2]);
+                bq[nj][0] = r[0];
+                bq[nj][1] = r[1];
+                bq[nj + 1][0] = r[2];
+                bq[nj + 1][1] = r[3];
             }
-            #pragma unroll
+#pragma unroll
             for (int mi = 0; mi < 2; ++mi)
-                #pragma unroll
+#pragma unroll
                 for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], af[mi], bq[ni]);
         }
         if (st + 1 < nsteps) store(cur ^ 1);
@@ -265,11 +287,11 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
     }
 
     // epilogue: accumulator e of tile (mi, ni) is row gq + 8 (e >> 1), column 2 tq + (e & 1)
-    #pragma unroll
+#pragma unroll
     for (int mi = 0; mi < 2; ++mi)
-        #pragma unroll
+#pragma unroll
         for (int ni = 0; ni < 4; ++ni)
-            #pragma unroll
+#pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int row = m0 + wm + mi * 16 + gq + 8 * (e >> 1);
                 const int col = n0 + wn + ni * 8 + 2 * tq + (e & 1);

@@ -3,8 +3,9 @@
 // gradients, weight repacking), compiled for the host with the shim of
 // host_kernel_shim.h.  The kernels come from cnn.cu (conv_kernels.inc, written
 // by the test); BF16 is emulated here with round-to-nearest-even, and
-// mma.sync.m16n8k16 (BF16 in, FP32 accumulate) by an exchange of every lane's
-// fragments in the register layout the PTX ISA documents for that shape:
+// mma.sync.m16n8k16 (BF16 in, FP32 accumulate) and ldmatrix.x4 by exchanges
+// between the lanes of a warp, in the register layouts the PTX ISA documents
+// (the mma's, below; ldmatrix's, at emu_ldsm):
 //   A (16 x 16, row): lane 4 (r % 8) + (k % 8) / 2, register (r >= 8) + 2 (k >= 8), half k % 2
 //   B (16 x 8, col):  lane 4 n + (k % 8) / 2,       register (k >= 8),             half k % 2
 //   C (16 x 8):       lane 4 (r % 8) + n / 2,       register 2 (r >= 8) + n % 2
@@ -72,6 +73,28 @@ inline void mma_bf16_16816(float* c, const uint32_t* a, const uint32_t* b) {
     for (int e = 0; e < 4; ++e) c[e] = out[e];
 }
 
+// ldmatrix.x4 (and .trans): lane l names row l % 8 of matrix l / 8; register j of
+// lane t gets row t / 4, columns 2 (t % 4), 2 (t % 4) + 1 of matrix j (low half
+// first), or with .trans rows 2 (t % 4), 2 (t % 4) + 1 of column t / 4
+inline std::vector<const void*>* emu_rows = nullptr;
+
+inline void emu_ldsm(uint32_t* r, const __nv_bfloat16* p, bool trans) {
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    (*emu_rows)[t] = p;
+    __syncwarp();
+    for (int j = 0; j < 4; ++j) {
+        uint16_t h[2];
+        for (int e = 0; e < 2; ++e) {
+            const int row = trans ? 2 * (lane % 4) + e : lane / 4, col = trans ? lane / 4 : 2 * (lane % 4) + e;
+            h[e] = static_cast<const __nv_bfloat16*>((*emu_rows)[w * 32 + 8 * j + row])[col].x;
+        }
+        r[j] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+    }
+    __syncwarp();
+}
+inline void ldsm_x4(uint32_t* r, const __nv_bfloat16* p) { emu_ldsm(r, p, false); }
+inline void ldsm_x4_trans(uint32_t* r, const __nv_bfloat16* p) { emu_ldsm(r, p, true); }
+
 #include "conv_kernels.inc"
 
 template <class T>
@@ -96,7 +119,9 @@ void save(const std::string& path, const std::vector<T>& v) {
 template <class F>
 void launch3(int gx, int gy, int gz, int threads, F body) {
     std::vector<uint32_t> frag((size_t)threads * 6, 0u);
+    std::vector<const void*> rows((size_t)threads, nullptr);
     emu_frag = &frag;
+    emu_rows = &rows;
     for (int z = 0; z < gz; ++z)
         for (int y = 0; y < gy; ++y) {
             blockIdx.y = y;

@@ -1,7 +1,7 @@
 """CPU test of the learned-guess network's tensor-core kernels (cnn.cu),
-compiled for the host with tests/host_kernel_shim.h and an emulation of
-mma.sync.m16n8k16 in the register layout the PTX ISA documents
-(tests/conv_emu.cpp).  One convolution layer per case -- the first layer's
+compiled for the host with tests/host_kernel_shim.h and emulations of
+mma.sync.m16n8k16 and ldmatrix.x4 (plain and transposed) in the register
+layouts the PTX ISA documents (tests/conv_emu.cpp).  One convolution layer per case -- the first layer's
 3 padded input channels, a stride-2 layer, the skip concatenation, the 1x1
 head, several output tiles, ragged pixel counts -- through the forward pass
 (with and without ReLU), the input gradient (ReLU masks, an FP32 addend,
@@ -52,7 +52,6 @@ def conv_emu(tmp_path_factory):
              extract(src, "struct GemmArgs {") + ";",
              "enum { kFwd = 0, kBwdData = 1, kBwdWeight = 2 };",
              extract(src, "__device__ __forceinline__ float bf("),
-             extract(src, "__device__ __forceinline__ uint32_t lds32("),
              extract(src, "__global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel("),
              extract(src, "__device__ __forceinline__ int real_channel("),
              extract(src, "__global__ void repack_kernel("),

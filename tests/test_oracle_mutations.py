@@ -81,7 +81,7 @@ MUTATIONS = [
     ("source_current_components_swapped", CL, 'np.einsum("d,den->en", disc.wq * disc.omega[:, 0], q)',
      'np.einsum("d,den->en", disc.wq * disc.omega[:, 1], q)', T_IP + ["tests/test_oracle_smm.py"]),
     ("cnn_upsampling_adjoint", CNN, ".sum(axis=(3, 5))", ".mean(axis=(3, 5))", ["tests/test_oracle_cnn.py"]),
-    ("cnn_relu_mask", CNN, 'g5 = gu5 * (c["a5"] > 0)', 'g5 = gu5 * (c["a4"].mean() > 0)',
+    ("cnn_relu_mask", CNN, 'g5 = q(gu5 * (c["a5"] > 0))', 'g5 = q(gu5 * (c["a4"].mean() > 0))',
      ["tests/test_oracle_cnn.py"]),
     ("cg_rhs_wrong_element_sigma", CG, 'np.add.at(b, gid[e2], 0.5 * np.einsum("qic,qc->i", G2, tj) / st[e2])',
      'np.add.at(b, gid[e2], 0.5 * np.einsum("qic,qc->i", G2, tj) / st[e])', ["tests/test_oracle_cgsmm.py"]),
