@@ -990,6 +990,46 @@ def run_learned(nx: int, stream, n_train: int = 192, n_test: int = 16, p: int = 
                      "solves to max(1e-12, 1e-2 x the previous relative difference)")
 
 
+def run_network_passes(batch: int, nx: int = 128, n_out: int = 9, widths=(64, 384)) -> None:
+    """The learned guess's network alone (the two-million-parameter widths on
+    nx x nx grids): forward, forward + backward (gradients), and a training
+    step (gradients + Adam), each 3 warm-up and 10 timed calls with CUDA events
+    on the network's stream, on seeded normal inputs and targets resident on
+    the GPU.  Prints one JSON line."""
+    import torch
+
+    import paper_2304_07386_gb300 as P
+    from paper_2304_07386_gb300 import build as B
+    B.build()
+    c1, c2 = widths
+    stream = torch.cuda.current_stream()
+    net = P.smm.Guess(nx, nx, n_out, batch, seed=0, stream=stream, c1=c1, c2=c2)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(batch, 3, nx, nx, device="cuda", generator=gen)
+    t = torch.randn(batch, n_out, nx, nx, device="cuda", generator=gen)
+    out = torch.zeros(batch, n_out, nx, nx, device="cuda")
+    fl = network_flops(nx, n_out, c1, c2)
+    peak, src = load_tensor_peak()
+    res = dict(grid=f"{nx}x{nx}", batch=batch, widths=[c1, c2], params=net.n_params)
+    for name, fn, mult in (("forward", lambda: net.forward(x, out), 1),
+                           ("forward_backward", lambda: net.gradients(x, t), 3),
+                           ("train_step", lambda: net.train_step(x, t, 1e-4), 3)):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        tf = batch * mult * fl / ms * 1e-9
+        res[name] = dict(ms=ms, tflops=tf, frac_of_bf16_peak=tf / peak)
+    res["peak_tflops"] = peak
+    res["peak_source"] = src
+    print(json.dumps({"network_passes": res}))
+
+
 def run_reference(args) -> None:
     """The oracle arm: the CPU oracle on the host cores, K timed steps of a
     bounded sample of the headline workload (one outer step each), after W
@@ -1056,8 +1096,13 @@ def main():
     ap.add_argument("--batch-full", type=int, default=0,
                     help="problems of the full-size uneven batched workload solved to 1e-8 in memory-sized waves "
                          "(opt-in: about ten minutes for 256)")
+    ap.add_argument("--network-passes", type=int, default=0,
+                    help="time only the learned guess's two-million-parameter network on 128x128 grids at this "
+                         "batch (forward, forward + backward, training step) and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.network_passes > 0:
+        run_network_passes(args.network_passes)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -133,7 +133,7 @@ __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162f
 // gradient, whose reduction index is the pixel, keeps them as rows of
 // channels ([k][m], [k][n]) and reads its fragments transposed.
 template <int MODE>
-__global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs args) {
+__global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmArgs args) {
     __shared__ __align__(16) __nv_bfloat16 sA[2][kBM * kLds];
     __shared__ __align__(16) __nv_bfloat16 sB[2][kBN * kLds];
     const ConvGeom& g = args.g;
@@ -146,9 +146,18 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
     }
     const int hw_out = g.Hout * g.Wout, hw_in = g.Hin * g.Win;
 
-    // forward / input grad: the two A rows (pixels) of this thread's chunks
+    // The reduction index of this thread's chunks advances by kBK per step; its decomposition is kept
+    // up to date without divisions.  Forward / input grad: every chunk of the thread has k = k0 + 8 (tid % 4),
+    // split into (tap, channel c < Kd) with tap = ky ksz + kx; the two A rows (pixels) are fixed.  Weight
+    // grad: both chunks have pixel kk = k0 + tid % 32, split into (b, oy, ox); the channels of the two B
+    // chunks (tap, c) are fixed.
+    const int Kd = MODE == kFwd ? g.Kc : g.Np;
     int rb_[2] = {0, 0}, ry_[2] = {0, 0}, rx_[2] = {0, 0};
     bool rok[2] = {false, false};
+    int cc = 0, cky = 0, ckx = 0;                  // forward / input grad: channel and tap of k
+    int pb = 0, poy = 0, pox = 0;                  // weight grad: pixel kk
+    int nky[2] = {0, 0}, nkx[2] = {0, 0}, nc[2] = {0, 0};
+    bool nok[2] = {false, false};
     if (MODE != kBwdWeight) {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -159,61 +168,94 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
             ry_[i] = (m % hw) / wd;
             rx_[i] = m % wd;
         }
+        const int k = k_begin + (tid & 3) * 8, tap = k / Kd;
+        cc = k - tap * Kd;
+        cky = tap / g.ksz;
+        ckx = tap - cky * g.ksz;
+    } else {
+        const int kk = k_begin + (tid & 31), rem = kk % hw_out;
+        pb = kk / hw_out;
+        poy = rem / g.Wout;
+        pox = rem - poy * g.Wout;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int n = n0 + ((tid + i * kGemmThreads) >> 5) * 8, tap = n / g.Kc;
+            nok[i] = n < args.N;
+            nc[i] = n - tap * g.Kc;
+            nky[i] = tap / g.ksz;
+            nkx[i] = tap - nky[i] * g.ksz;
+        }
     }
+    auto advance = [&]() {
+        if (MODE != kBwdWeight) {
+            cc += kBK;
+            while (cc >= Kd) {
+                cc -= Kd;
+                if (++ckx == g.ksz) {
+                    ckx = 0;
+                    ++cky;
+                }
+            }
+        } else {
+            pox += kBK;
+            while (pox >= g.Wout) {
+                pox -= g.Wout;
+                if (++poy == g.Hout) {
+                    poy = 0;
+                    ++pb;
+                }
+            }
+        }
+    };
+    auto src_of = [&](size_t pix, int c) {
+        return c < g.Ka ? args.in_a + pix * g.Ka + c : args.in_b + pix * g.Kb + (c - g.Ka);
+    };
 
     uint4 ra[2], rbv[2];
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-    // global -> registers for the reduction step starting at k0
+    // global -> registers for the reduction step starting at k0 (the state above describes k0)
     auto load = [&](int k0) {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-            const int q = tid + i * kGemmThreads;
             ra[i] = zero;
             rbv[i] = zero;
-            if (MODE != kBwdWeight) {
-                const int kc = (q & 3) * 8, r = q >> 2, k = k0 + kc;
-                if (k < k_end) {
-                    if (MODE == kFwd) {
-                        const int tap = k / g.Kc, c = k - tap * g.Kc, ky = tap / g.ksz, kx = tap - ky * g.ksz;
-                        const int iy = ry_[i] * g.stride + ky - g.pad, ix = rx_[i] * g.stride + kx - g.pad;
-                        if (rok[i] && iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win) {
-                            const size_t pix = ((size_t)rb_[i] * g.Hin + iy) * g.Win + ix;
-                            const __nv_bfloat16* src =
-                                c < g.Ka ? args.in_a + pix * g.Ka + c : args.in_b + pix * g.Kb + (c - g.Ka);
-                            ra[i] = *reinterpret_cast<const uint4*>(src);
-                        }
-                    } else {
-                        const int tap = k / g.Np, co = k - tap * g.Np, ky = tap / g.ksz, kx = tap - ky * g.ksz;
-                        const int ny = ry_[i] + g.pad - ky, nx = rx_[i] + g.pad - kx;
-                        if (rok[i] && ny >= 0 && nx >= 0 && ny % g.stride == 0 && nx % g.stride == 0) {
-                            const int oy = ny / g.stride, ox = nx / g.stride;
-                            if (oy < g.Hout && ox < g.Wout) {
-                                const size_t pix = ((size_t)rb_[i] * g.Hout + oy) * g.Wout + ox;
-                                ra[i] = *reinterpret_cast<const uint4*>(args.gout + pix * g.Np + co);
-                            }
-                        }
+        }
+        if (MODE != kBwdWeight) {
+            const int kc = (tid & 3) * 8, k = k0 + kc;
+            if (k >= k_end) return;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (MODE == kFwd) {
+                    const int iy = ry_[i] * g.stride + cky - g.pad, ix = rx_[i] * g.stride + ckx - g.pad;
+                    if (rok[i] && iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win)
+                        ra[i] = *reinterpret_cast<const uint4*>(
+                            src_of(((size_t)rb_[i] * g.Hin + iy) * g.Win + ix, cc));
+                } else {
+                    int oy = ry_[i] + g.pad - cky, ox = rx_[i] + g.pad - ckx;
+                    bool ok = rok[i] && oy >= 0 && ox >= 0;
+                    if (g.stride != 1) {
+                        ok = ok && oy % g.stride == 0 && ox % g.stride == 0;
+                        oy /= g.stride;
+                        ox /= g.stride;
                     }
-                    const int n = n0 + r;
-                    if (n < args.N) rbv[i] = *reinterpret_cast<const uint4*>(args.wt + (size_t)n * args.K + k);
+                    if (ok && oy < g.Hout && ox < g.Wout)
+                        ra[i] = *reinterpret_cast<const uint4*>(
+                            args.gout + (((size_t)rb_[i] * g.Hout + oy) * g.Wout + ox) * g.Np + cc);
                 }
-            } else {
-                const int p = q & 31, j8 = (q >> 5) * 8, kk = k0 + p;
-                if (kk < k_end) {
-                    const int co = m0 + j8;
-                    if (co < args.M) ra[i] = *reinterpret_cast<const uint4*>(args.gout + (size_t)kk * g.Np + co);
-                    const int n = n0 + j8;
-                    if (n < args.N) {
-                        const int tap = n / g.Kc, c = n - tap * g.Kc, ky = tap / g.ksz, kx = tap - ky * g.ksz;
-                        const int b = kk / hw_out, oy = (kk % hw_out) / g.Wout, ox = kk % g.Wout;
-                        const int iy = oy * g.stride + ky - g.pad, ix = ox * g.stride + kx - g.pad;
-                        if (iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win) {
-                            const size_t pix = ((size_t)b * g.Hin + iy) * g.Win + ix;
-                            const __nv_bfloat16* src =
-                                c < g.Ka ? args.in_a + pix * g.Ka + c : args.in_b + pix * g.Kb + (c - g.Ka);
-                            rbv[i] = *reinterpret_cast<const uint4*>(src);
-                        }
-                    }
-                }
+                const int n = n0 + ((tid + i * kGemmThreads) >> 2);
+                if (n < args.N) rbv[i] = *reinterpret_cast<const uint4*>(args.wt + (size_t)n * args.K + k);
+            }
+        } else {
+            const int kk = k0 + (tid & 31);
+            if (kk >= k_end) return;
+            const __nv_bfloat16* grow = args.gout + (size_t)kk * g.Np;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int j8 = ((tid + i * kGemmThreads) >> 5) * 8;
+                if (m0 + j8 < args.M) ra[i] = *reinterpret_cast<const uint4*>(grow + m0 + j8);
+                const int iy = poy * g.stride + nky[i] - g.pad, ix = pox * g.stride + nkx[i] - g.pad;
+                if (nok[i] && iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win)
+                    rbv[i] = *reinterpret_cast<const uint4*>(src_of(((size_t)pb * g.Hin + iy) * g.Win + ix, nc[i]));
             }
         }
     };
@@ -251,7 +293,10 @@ __global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel(const GemmArgs 
     __syncthreads();
     for (int st = 0; st < nsteps; ++st) {
         const int cur = st & 1;
-        if (st + 1 < nsteps) load(k_begin + (st + 1) * kBK);
+        if (st + 1 < nsteps) {
+            advance();
+            load(k_begin + (st + 1) * kBK);
+        }
 #pragma unroll
         for (int ks = 0; ks < kBK; ks += 16) {
             // A of rows wm + 16 mi: matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15) in the order a0..a3;

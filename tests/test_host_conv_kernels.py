@@ -52,7 +52,7 @@ def conv_emu(tmp_path_factory):
              extract(src, "struct GemmArgs {") + ";",
              "enum { kFwd = 0, kBwdData = 1, kBwdWeight = 2 };",
              extract(src, "__device__ __forceinline__ float bf("),
-             extract(src, "__global__ void __launch_bounds__(kGemmThreads) conv_gemm_kernel("),
+             extract(src, "__global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel("),
              extract(src, "__device__ __forceinline__ int real_channel("),
              extract(src, "__global__ void repack_kernel("),
              extract(src, "__global__ void bias_partial_kernel("),
