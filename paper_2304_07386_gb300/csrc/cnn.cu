@@ -45,6 +45,7 @@ constexpr int kIn = 3;
 constexpr int kBM = 64, kBN = 64, kBK = 32, kLds = kBK + 8;  // block tile; smem row of kLds BF16
 constexpr int kLdt = kBM + 8;  // weight grad: smem row (one pixel) of kLdt BF16 channels
 constexpr int kGemmThreads = 128;                          // four warps, each a 32 x 32 piece
+constexpr int kStages = 3;                                 // shared-memory stages of the copy pipeline
 
 smm_status fail(smm_status s, const std::string& msg) {
     smm::set_last_error(msg.c_str());
@@ -122,20 +123,35 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const __nv_bfloat16* 
                  : "r"(a));
 }
 
+// 16 bytes global -> shared without a register stop (cp.async, L2 only); with valid == false nothing is
+// read and the 16 bytes are zero-filled (src must still be a valid global address).  The copies of one
+// thread form groups (commit); wait_group<N> returns once at most N of its newest groups are pending.
+__device__ __forceinline__ void cp_async16(__nv_bfloat16* dst, const __nv_bfloat16* src, bool valid) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
 // One 64 x 64 tile of a convolution pass per block (blockIdx.z: the weight
-// gradient's pixel split).  The reduction runs in steps of 32 through two
-// shared-memory buffers: each thread issues its 16-byte global loads of the
-// next step before the current step's products and stores them to the other
-// buffer after them; one barrier per step.  Forward and input gradient keep
+// gradient's pixel split).  The reduction runs in steps of 32 through a
+// pipeline of kStages shared-memory stages: each thread copies its 16-byte
+// pieces of step st + kStages - 1 with cp.async (zero-filled at the image
+// border and past the end) while the products of step st run; one barrier
+// per step.  Forward and input gradient keep
 // both operands as rows of 32 reduction indices ([m][k], [n][k]); the weight
 // gradient, whose reduction index is the pixel, keeps them as rows of
 // channels ([k][m], [k][n]) and reads its fragments transposed.
 template <int MODE>
 __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmArgs args) {
-    __shared__ __align__(16) __nv_bfloat16 sA[2][kBM * kLds];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][kBN * kLds];
+    __shared__ __align__(16) __nv_bfloat16 sA[kStages][kBM * kLds];
+    __shared__ __align__(16) __nv_bfloat16 sB[kStages][kBN * kLds];
     const ConvGeom& g = args.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
@@ -211,67 +227,50 @@ __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmAr
         return c < g.Ka ? args.in_a + pix * g.Ka + c : args.in_b + pix * g.Kb + (c - g.Ka);
     };
 
-    uint4 ra[2], rbv[2];
-    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-    // global -> registers for the reduction step starting at k0 (the state above describes k0)
-    auto load = [&](int k0) {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            ra[i] = zero;
-            rbv[i] = zero;
-        }
+    // copies of the reduction step starting at k0 (the state above describes k0) into stage sg
+    auto load = [&](int k0, int sg) {
+        const __nv_bfloat16* any = args.wt ? args.wt : args.gout;  // a valid address for zero-filled pieces
         if (MODE != kBwdWeight) {
             const int kc = (tid & 3) * 8, k = k0 + kc;
-            if (k >= k_end) return;
+            const bool kin = k < k_end;
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
+                const int r = (tid + i * kGemmThreads) >> 2;
+                const __nv_bfloat16* src = any;
+                bool ok = false;
                 if (MODE == kFwd) {
                     const int iy = ry_[i] * g.stride + cky - g.pad, ix = rx_[i] * g.stride + ckx - g.pad;
-                    if (rok[i] && iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win)
-                        ra[i] = *reinterpret_cast<const uint4*>(
-                            src_of(((size_t)rb_[i] * g.Hin + iy) * g.Win + ix, cc));
+                    ok = kin && rok[i] && iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win;
+                    if (ok) src = src_of(((size_t)rb_[i] * g.Hin + iy) * g.Win + ix, cc);
                 } else {
                     int oy = ry_[i] + g.pad - cky, ox = rx_[i] + g.pad - ckx;
-                    bool ok = rok[i] && oy >= 0 && ox >= 0;
+                    ok = kin && rok[i] && oy >= 0 && ox >= 0;
                     if (g.stride != 1) {
                         ok = ok && oy % g.stride == 0 && ox % g.stride == 0;
                         oy /= g.stride;
                         ox /= g.stride;
                     }
-                    if (ok && oy < g.Hout && ox < g.Wout)
-                        ra[i] = *reinterpret_cast<const uint4*>(
-                            args.gout + (((size_t)rb_[i] * g.Hout + oy) * g.Wout + ox) * g.Np + cc);
+                    ok = ok && oy < g.Hout && ox < g.Wout;
+                    if (ok) src = args.gout + (((size_t)rb_[i] * g.Hout + oy) * g.Wout + ox) * g.Np + cc;
                 }
-                const int n = n0 + ((tid + i * kGemmThreads) >> 2);
-                if (n < args.N) rbv[i] = *reinterpret_cast<const uint4*>(args.wt + (size_t)n * args.K + k);
+                cp_async16(&sA[sg][r * kLds + kc], src, ok);
+                const int n = n0 + r;
+                const bool nok_ = kin && n < args.N;
+                cp_async16(&sB[sg][r * kLds + kc], nok_ ? args.wt + (size_t)n * args.K + k : any, nok_);
             }
         } else {
-            const int kk = k0 + (tid & 31);
-            if (kk >= k_end) return;
-            const __nv_bfloat16* grow = args.gout + (size_t)kk * g.Np;
+            const int p = tid & 31, kk = k0 + p;
+            const bool kin = kk < k_end;
+            const __nv_bfloat16* grow = args.gout + (size_t)(kin ? kk : 0) * g.Np;
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int j8 = ((tid + i * kGemmThreads) >> 5) * 8;
-                if (m0 + j8 < args.M) ra[i] = *reinterpret_cast<const uint4*>(grow + m0 + j8);
+                const bool aok = kin && m0 + j8 < args.M;
+                cp_async16(&sA[sg][p * kLdt + j8], aok ? grow + m0 + j8 : any, aok);
                 const int iy = poy * g.stride + nky[i] - g.pad, ix = pox * g.stride + nkx[i] - g.pad;
-                if (nok[i] && iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win)
-                    rbv[i] = *reinterpret_cast<const uint4*>(src_of(((size_t)pb * g.Hin + iy) * g.Win + ix, nc[i]));
-            }
-        }
-    };
-    // registers -> shared buffer s (the weight grad transposes: rows = channels, columns = pixels)
-    auto store = [&](int s) {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int q = tid + i * kGemmThreads;
-            if (MODE != kBwdWeight) {
-                const int kc = (q & 3) * 8, r = q >> 2;
-                *reinterpret_cast<uint4*>(&sA[s][r * kLds + kc]) = ra[i];
-                *reinterpret_cast<uint4*>(&sB[s][r * kLds + kc]) = rbv[i];
-            } else {
-                const int p = q & 31, j8 = (q >> 5) * 8;
-                *reinterpret_cast<uint4*>(&sA[s][p * kLdt + j8]) = ra[i];
-                *reinterpret_cast<uint4*>(&sB[s][p * kLdt + j8]) = rbv[i];
+                const bool bok = kin && nok[i] && iy >= 0 && iy < g.Hin && ix >= 0 && ix < g.Win;
+                cp_async16(&sB[sg][p * kLdt + j8],
+                           bok ? src_of(((size_t)pb * g.Hin + iy) * g.Win + ix, nc[i]) : any, bok);
             }
         }
     };
@@ -286,16 +285,26 @@ __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmAr
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32, gq = lane >> 2, tq = lane & 3;
 
     const int nsteps = k_end > k_begin ? (k_end - k_begin + kBK - 1) / kBK : 0;
-    if (nsteps > 0) {
-        load(k_begin);
-        store(0);
+    // prologue: steps 0 .. kStages - 2 in flight (one commit group per step, empty past the end)
+#pragma unroll
+    for (int sg = 0; sg < kStages - 1; ++sg) {
+        if (sg < nsteps) {
+            if (sg > 0) advance();
+            load(k_begin + sg * kBK, sg);
+        }
+        cp_async_commit();
     }
-    __syncthreads();
     for (int st = 0; st < nsteps; ++st) {
-        const int cur = st & 1;
-        if (st + 1 < nsteps) {
-            advance();
-            load(k_begin + (st + 1) * kBK);
+        const int cur = st % kStages;
+        cp_async_wait<kStages - 2>();  // this thread's pieces of step st have landed
+        __syncthreads();               // everyone's have; everyone is done with step st - 1's stage
+        {
+            const int nx = st + kStages - 1;
+            if (nx < nsteps) {
+                advance();
+                load(k_begin + nx * kBK, nx % kStages);
+            }
+            cp_async_commit();
         }
 #pragma unroll
         for (int ks = 0; ks < kBK; ks += 16) {
@@ -327,9 +336,8 @@ __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmAr
 #pragma unroll
                 for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], af[mi], bq[ni]);
         }
-        if (st + 1 < nsteps) store(cur ^ 1);
-        __syncthreads();
     }
+    cp_async_wait<0>();
 
     // epilogue: accumulator e of tile (mi, ni) is row gq + 8 (e >> 1), column 2 tq + (e & 1)
 #pragma unroll

@@ -95,6 +95,16 @@ inline void emu_ldsm(uint32_t* r, const __nv_bfloat16* p, bool trans) {
 inline void ldsm_x4(uint32_t* r, const __nv_bfloat16* p) { emu_ldsm(r, p, false); }
 inline void ldsm_x4_trans(uint32_t* r, const __nv_bfloat16* p) { emu_ldsm(r, p, true); }
 
+// cp.async: the copy (or the zero fill) happens at once, so commit and wait have nothing to do; the
+// pipeline's group accounting is checked on the GPU, its addresses and predicates here
+inline void cp_async16(__nv_bfloat16* dst, const __nv_bfloat16* src, bool valid) {
+    if (valid) std::memcpy(dst, src, 16);
+    else std::memset(dst, 0, 16);
+}
+inline void cp_async_commit() {}
+template <int N>
+inline void cp_async_wait() {}
+
 #include "conv_kernels.inc"
 
 template <class T>

@@ -1,7 +1,8 @@
 """CPU test of the learned-guess network's tensor-core kernels (cnn.cu),
 compiled for the host with tests/host_kernel_shim.h and emulations of
 mma.sync.m16n8k16 and ldmatrix.x4 (plain and transposed) in the register
-layouts the PTX ISA documents (tests/conv_emu.cpp).  One convolution layer per case -- the first layer's
+layouts the PTX ISA documents, and of cp.async as an immediate copy or zero
+fill (tests/conv_emu.cpp).  One convolution layer per case -- the first layer's
 3 padded input channels, a stride-2 layer, the skip concatenation, the 1x1
 head, several output tiles, ragged pixel counts -- through the forward pass
 (with and without ReLU), the input gradient (ReLU masks, an FP32 addend,
