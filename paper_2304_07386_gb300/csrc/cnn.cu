@@ -46,6 +46,7 @@ constexpr int kBM = 64, kBN = 64, kBK = 32, kLds = kBK + 8;  // block tile; smem
 constexpr int kLdt = kBM + 8;  // weight grad: smem row (one pixel) of kLdt BF16 channels
 constexpr int kGemmThreads = 128;                          // four warps, each a 32 x 32 piece
 constexpr int kStages = 3;                                 // shared-memory stages of the copy pipeline
+constexpr int kWgradBlocks = 2 * 5 * 152;                  // weight grad: two waves of five CTAs per SM
 
 smm_status fail(smm_status s, const std::string& msg) {
     smm::set_last_error(msg.c_str());
@@ -551,9 +552,9 @@ ConvGeom geom(const smm_guess_ctx* c, int l, int B) {
     return g;
 }
 
-// pixel splits of a weight-gradient pass: about four blocks per SM in total, chunks a multiple of the step
+// pixel splits of a weight-gradient pass: about kWgradBlocks CTAs in total, chunks a multiple of the step
 void weight_splits(long long K, long long tiles, int* splits, int* kchunk) {
-    long long want = std::max(1LL, (4LL * 152 + tiles - 1) / tiles);
+    long long want = std::max(1LL, (kWgradBlocks + tiles - 1) / tiles);
     want = std::min(want, std::max(1LL, (K + kBK - 1) / kBK));
     long long ch = (K + want - 1) / want;
     ch = std::max<long long>(kBK, (ch + kBK - 1) / kBK * kBK);
@@ -740,10 +741,10 @@ smm_status smm_guess_create(int32_t height, int32_t width, int32_t n_out, int32_
         const ConvGeom& d = g->L[l];
         const long long K = pix / ((long long)(H / d.Hout) * (W / d.Wout)), N = (long long)d.taps * d.Kc;
         const long long tiles = (long long)((d.Np + kBM - 1) / kBM) * ((N + kBN - 1) / kBN);
-        // weight_splits never gives more splits than min(ceil(608 / tiles), ceil(K / kBK)), which is
+        // weight_splits never gives more splits than min(ceil(kWgradBlocks / tiles), ceil(K / kBK)), which is
         // largest at the largest batch
         const long long bound =
-            std::max(1LL, std::min((4LL * 152 + tiles - 1) / tiles, (K + kBK - 1) / kBK));
+            std::max(1LL, std::min((kWgradBlocks + tiles - 1) / tiles, (K + kBK - 1) / kBK));
         wmax = std::max(wmax, (size_t)bound * (size_t)d.Np * (size_t)N);
         bmax = std::max(bmax, (size_t)((K + kBiasChunk - 1) / kBiasChunk) * d.Np);
     }
