@@ -92,3 +92,18 @@ def test_oracle_on_every_core_sums_independent_copies():
     assert "error" not in both, both
     assert both["cores"] == 2 and both["kind"] == "oracle" and both["unit"] == one["unit"]
     assert both["value"] > 0 and isinstance(both["cpu"], str)
+
+
+def test_network_flop_count_matches_the_layer_list():
+    """The learned-guess roofline's numerator: 2 x the multiply-adds of every layer of the oracle's layer
+    list over real channels (the stride-2 layer and the one after it on the half-resolution grid), at both
+    sets of widths."""
+    import bench
+    from oracle import cnn
+    for nx, n_out, c1, c2 in ((128, 9, 64, 384), (64, 9, 24, 32), (16, 4, 16, 48)):
+        macs = 0
+        for i, (ci, co, k, _) in enumerate(cnn.layer_specs(n_out, c1, c2)):
+            side = nx // 2 if i in (1, 2) else nx
+            macs += co * ci * k * k * side * side
+        assert bench.network_flops(nx, n_out, c1, c2) == 2.0 * macs
+    assert abs(bench.network_flops(128, 9, 64, 384) - 22.42e9) < 0.01e9
