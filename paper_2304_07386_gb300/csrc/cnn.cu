@@ -93,6 +93,13 @@ struct GemmArgs {
     // weight grad: FP32 partials [split][Np][taps*Kc], kchunk pixels per split
     float* wpart;
     int kchunk;
+    // row length of wt (taps * Kc or taps * Np)
+    int wt_ld;
+    // input grad of a strided layer, one launch per parity class of input pixels: rows are the pixels
+    // (b, stride qy + py, stride qx + px), the reduction runs over the ntap taps tapk[] that reach an
+    // output pixel from that class (K = ntap * Np).  cls = 0: every pixel and every tap.
+    int cls, py, px, ntap;
+    int tapk[9];
 };
 
 enum { kFwd = 0, kBwdData = 1, kBwdWeight = 2 };
@@ -165,13 +172,14 @@ __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmAr
 
     // The reduction index of this thread's chunks advances by kBK per step; its decomposition is kept
     // up to date without divisions.  Forward / input grad: every chunk of the thread has k = k0 + 8 (tid % 4),
-    // split into (tap, channel c < Kd) with tap = ky ksz + kx; the two A rows (pixels) are fixed.  Weight
-    // grad: both chunks have pixel kk = k0 + tid % 32, split into (b, oy, ox); the channels of the two B
-    // chunks (tap, c) are fixed.
+    // split into (tap ti of the launch's taps, channel c < Kd); ctap = ky ksz + kx is the tap itself (ti, or
+    // tapk[ti] for a parity class); the two A rows (pixels) are fixed.  Weight grad: both chunks have pixel
+    // kk = k0 + tid % 32, split into (b, oy, ox); the channels of the two B chunks (tap, c) are fixed.
     const int Kd = MODE == kFwd ? g.Kc : g.Np;
+    const bool cls = MODE == kBwdData && args.cls;
     int rb_[2] = {0, 0}, ry_[2] = {0, 0}, rx_[2] = {0, 0};
     bool rok[2] = {false, false};
-    int cc = 0, cky = 0, ckx = 0;                  // forward / input grad: channel and tap of k
+    int cc = 0, ti = 0, ctap = 0, cky = 0, ckx = 0;  // forward / input grad: channel and tap of k
     int pb = 0, poy = 0, pox = 0;                  // weight grad: pixel kk
     int nky[2] = {0, 0}, nkx[2] = {0, 0}, nc[2] = {0, 0};
     bool nok[2] = {false, false};
@@ -180,15 +188,24 @@ __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmAr
         for (int i = 0; i < 2; ++i) {
             const int m = m0 + ((tid + i * kGemmThreads) >> 2);
             rok[i] = m < args.M;
-            const int hw = MODE == kFwd ? hw_out : hw_in, wd = MODE == kFwd ? g.Wout : g.Win;
-            rb_[i] = m / hw;
-            ry_[i] = (m % hw) / wd;
-            rx_[i] = m % wd;
+            if (cls) {
+                const int wd = g.Win / g.stride, hw = (g.Hin / g.stride) * wd;
+                rb_[i] = m / hw;
+                ry_[i] = (m % hw) / wd * g.stride + args.py;
+                rx_[i] = m % wd * g.stride + args.px;
+            } else {
+                const int hw = MODE == kFwd ? hw_out : hw_in, wd = MODE == kFwd ? g.Wout : g.Win;
+                rb_[i] = m / hw;
+                ry_[i] = (m % hw) / wd;
+                rx_[i] = m % wd;
+            }
         }
-        const int k = k_begin + (tid & 3) * 8, tap = k / Kd;
-        cc = k - tap * Kd;
-        cky = tap / g.ksz;
-        ckx = tap - cky * g.ksz;
+        const int k = k_begin + (tid & 3) * 8;
+        ti = k / Kd;
+        cc = k - ti * Kd;
+        ctap = cls ? args.tapk[ti < args.ntap ? ti : 0] : ti;
+        cky = ctap / g.ksz;
+        ckx = ctap - cky * g.ksz;
     } else {
         const int kk = k_begin + (tid & 31), rem = kk % hw_out;
         pb = kk / hw_out;
@@ -208,9 +225,17 @@ __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmAr
             cc += kBK;
             while (cc >= Kd) {
                 cc -= Kd;
-                if (++ckx == g.ksz) {
-                    ckx = 0;
-                    ++cky;
+                ++ti;
+                if (cls) {
+                    ctap = args.tapk[ti < args.ntap ? ti : 0];
+                    cky = ctap / g.ksz;
+                    ckx = ctap - cky * g.ksz;
+                } else {
+                    ++ctap;
+                    if (++ckx == g.ksz) {
+                        ckx = 0;
+                        ++cky;
+                    }
                 }
             }
         } else {
@@ -257,7 +282,8 @@ __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmAr
                 cp_async16(&sA[sg][r * kLds + kc], src, ok);
                 const int n = n0 + r;
                 const bool nok_ = kin && n < args.N;
-                cp_async16(&sB[sg][r * kLds + kc], nok_ ? args.wt + (size_t)n * args.K + k : any, nok_);
+                cp_async16(&sB[sg][r * kLds + kc], nok_ ? args.wt + (size_t)n * args.wt_ld + ctap * Kd + cc : any,
+                           nok_);
             }
         } else {
             const int p = tid & 31, kk = k0 + p;
@@ -362,7 +388,13 @@ __global__ void __launch_bounds__(kGemmThreads, 5) conv_gemm_kernel(const GemmAr
                 } else if (MODE == kBwdData) {
                     const int pi = col < g.Ka ? 0 : 1, lc = pi ? col - g.Ka : col;
                     const GradPart& P = args.part[pi];
-                    const size_t idx = (size_t)row * P.ld + lc;
+                    size_t pix = (size_t)row;
+                    if (cls) {
+                        const int wd = g.Win / g.stride, hw = (g.Hin / g.stride) * wd;
+                        const int b = row / hw, qy = (row % hw) / wd, qx = row % wd;
+                        pix = ((size_t)b * g.Hin + qy * g.stride + args.py) * g.Win + qx * g.stride + args.px;
+                    }
+                    const size_t idx = pix * P.ld + lc;
                     if (P.act && !(bf(P.act[idx]) > 0.0f)) v = 0.0f;
                     if (P.add) v += P.add[idx];
                     if (P.out_bf) P.out_bf[idx] = __float2bfloat16(v);
@@ -562,6 +594,17 @@ void weight_splits(long long K, long long tiles, int* splits, int* kchunk) {
     *splits = (int)std::max(1LL, (K + ch - 1) / ch);
 }
 
+// taps of a strided layer that reach an output pixel from the input pixels of parity (py, px)
+int class_taps(const ConvGeom& g, int py, int px, int* tapk) {
+    int n = 0;
+    for (int ky = 0; ky < g.ksz; ++ky)
+        for (int kx = 0; kx < g.ksz; ++kx)
+            if (((py + g.pad - ky) % g.stride + g.stride) % g.stride == 0 &&
+                ((px + g.pad - kx) % g.stride + g.stride) % g.stride == 0)
+                tapk[n++] = ky * g.ksz + kx;
+    return n;
+}
+
 void launch_fwd(smm_guess g, int l, int B, const __nv_bfloat16* ia, const __nv_bfloat16* ib, int relu,
                 __nv_bfloat16* out_bf, float* out_nchw) {
     GemmArgs a;
@@ -577,6 +620,7 @@ void launch_fwd(smm_guess g, int l, int B, const __nv_bfloat16* ia, const __nv_b
     a.relu = relu;
     a.out_bf = out_bf;
     a.out_nchw = out_nchw;
+    a.wt_ld = a.K;
     dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN);
     conv_gemm_kernel<kFwd><<<grid, kGemmThreads, 0, g->stream>>>(a);
 }
@@ -590,10 +634,26 @@ void launch_bwd_data(smm_guess g, int l, int B, const __nv_bfloat16* gout, GradP
     a.K = a.g.taps * a.g.Np;
     a.gout = gout;
     a.wt = g->wb[l];
+    a.wt_ld = a.K;
     a.part[0] = p0;
     a.part[1] = p1;
-    dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN);
-    conv_gemm_kernel<kBwdData><<<grid, kGemmThreads, 0, g->stream>>>(a);
+    if (a.g.stride == 1) {
+        dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN);
+        conv_gemm_kernel<kBwdData><<<grid, kGemmThreads, 0, g->stream>>>(a);
+        return;
+    }
+    // strided: one launch per parity class of the input pixels, over the taps that reach an output pixel
+    a.cls = 1;
+    a.M = B * (a.g.Hin / a.g.stride) * (a.g.Win / a.g.stride);
+    for (int py = 0; py < a.g.stride; ++py)
+        for (int px = 0; px < a.g.stride; ++px) {
+            a.py = py;
+            a.px = px;
+            a.ntap = class_taps(a.g, py, px, a.tapk);
+            a.K = a.ntap * a.g.Np;
+            dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN);
+            conv_gemm_kernel<kBwdData><<<grid, kGemmThreads, 0, g->stream>>>(a);
+        }
 }
 
 void launch_bwd_weight(smm_guess g, int l, int B, const __nv_bfloat16* ia, const __nv_bfloat16* ib,

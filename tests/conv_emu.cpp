@@ -174,6 +174,7 @@ int main(int argc, char** argv) {
         a.g = g;
         a.M = (int)pout; a.N = g.Np; a.K = g.taps * g.Kc;
         a.in_a = in_a.data(); a.in_b = cb ? in_b.data() : nullptr; a.wt = wf.data(); a.bias = bias.data();
+        a.wt_ld = a.K;
         a.relu = 1; a.out_bf = fwd.data();
         launch3((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN, 1, kGemmThreads, [&] { conv_gemm_kernel<kFwd>(a); });
         a.relu = 0; a.out_bf = nullptr; a.out_nchw = fwd_nchw.data();
@@ -187,10 +188,27 @@ int main(int argc, char** argv) {
         std::memset(&a, 0, sizeof(a));
         a.g = g;
         a.M = (int)pin; a.N = g.Kc; a.K = g.taps * g.Np;
-        a.gout = gout.data(); a.wt = wb.data();
+        a.gout = gout.data(); a.wt = wb.data(); a.wt_ld = a.K;
         a.part[0] = GradPart{act_a.data(), add_a.data(), gin_a.data(), nullptr, g.Ka};
         if (cb) a.part[1] = GradPart{act_b.data(), nullptr, nullptr, gin_b.data(), g.Kb};
-        launch3((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN, 1, kGemmThreads, [&] { conv_gemm_kernel<kBwdData>(a); });
+        if (stride == 1) {
+            launch3((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN, 1, kGemmThreads,
+                    [&] { conv_gemm_kernel<kBwdData>(a); });
+        } else {
+            // as the library launches a strided layer's input gradient: one launch per parity class
+            a.cls = 1;
+            a.M = B * (Hin / stride) * (Win / stride);
+            for (int py = 0; py < stride; ++py)
+                for (int px = 0; px < stride; ++px) {
+                    a.py = py;
+                    a.px = px;
+                    a.ntap = class_taps(g, py, px, a.tapk);
+                    a.K = a.ntap * g.Np;
+                    std::printf("class (%d, %d): %d taps\n", py, px, a.ntap);
+                    launch3((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN, 1, kGemmThreads,
+                            [&] { conv_gemm_kernel<kBwdData>(a); });
+                }
+        }
     }
     // weight and bias gradients through the split partials
     std::vector<float> gw((size_t)cout * cin * g.taps), gb(cout);

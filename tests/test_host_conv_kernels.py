@@ -6,7 +6,8 @@ fill (tests/conv_emu.cpp).  One convolution layer per case -- the first layer's
 3 padded input channels, a stride-2 layer, the skip concatenation, the 1x1
 head, several output tiles, ragged pixel counts -- through the forward pass
 (with and without ReLU), the input gradient (ReLU masks, an FP32 addend,
-BF16 and FP32 outputs), and the weight and bias gradients through their
+BF16 and FP32 outputs; for a stride-2 layer one launch per parity class of
+input pixels over the taps that reach an output pixel, as the library does), and the weight and bias gradients through their
 split partials, against the oracle's convolution and its gradients.  The
 values are small integers and multiples of 2^-8, so every sum is exact in
 any order and the comparison is exact."""
@@ -58,7 +59,8 @@ def conv_emu(tmp_path_factory):
              extract(src, "__global__ void repack_kernel("),
              extract(src, "__global__ void bias_partial_kernel("),
              extract(src, "__global__ void grad_reduce_kernel("),
-             extract(src, "void weight_splits(")]
+             extract(src, "void weight_splits("),
+             extract(src, "int class_taps(")]
     (d / "conv_kernels.inc").write_text("\n\n".join(parts))
     exe = d / "conv_emu"
     subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-pthread", "-I", str(d), "-I",
