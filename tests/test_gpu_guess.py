@@ -50,8 +50,9 @@ def test_network_forward_and_gradients_match_oracle_elementwise():
     """General inputs (weights ~ N(0, 0.2^2), normal inputs and targets): the
     library's FP32 sums round differently from the oracle's FP64 ones, by about
     2^-24 K of a sum of K terms, and where such a difference crosses a BF16
-    rounding boundary a stored activation moves by one BF16 unit (at most
-    2^-7 of its value), moving what follows it by about that fraction.  So
+    rounding boundary a stored activation or stored gradient moves by one
+    BF16 unit (at most 2^-7 of its value), moving what follows it by about
+    that fraction.  So
     every output value is checked against 1e-2 of its channel's largest
     magnitude, and every gradient entry against 1e-2 of its layer block's
     (weights and bias of each layer separately); the loss to 1e-3."""
