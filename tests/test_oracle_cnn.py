@@ -42,3 +42,22 @@ def test_widths_set_the_parameter_count():
     w = 9 * (3 * c1 + c1 * c2 + c2 * c2 + c2 * c1 + 2 * c1 * c1) + c1 * n_out
     b = c1 + c2 + c2 + c1 + c1 + n_out
     assert cnn.num_params(n_out, c1, c2) == w + b == 1_846_473
+
+
+def test_outputs_depend_only_on_nearby_inputs():
+    """The receptive field behind the full-size GPU network test's crops: the
+    forward pass on a crop at an even offset equals the full image's on every
+    pixel at least 6 pixels from an interior crop edge, and not at 5 (so the
+    test's margin of 8 is a real bound, not a coincidence of the data)."""
+    rng = np.random.default_rng(0)
+    n_out, c1, c2, S = 4, 16, 32, 48
+    p = rng.standard_normal(cnn.num_params(n_out, c1, c2)) * 0.3
+    x = rng.standard_normal((1, 3, 64, 64))
+    full, _ = cnn.forward(p, x, n_out, c1=c1, c2=c2)
+    for oy, ox in ((0, 0), (8, 8), (16, 16)):
+        crop, _ = cnn.forward(p, x[:, :, oy:oy + S, ox:ox + S], n_out, c1=c1, c2=c2)
+        for m, exact in ((8, True), (6, True), (5, False)):
+            y0, x0 = (0 if oy == 0 else m), (0 if ox == 0 else m)
+            y1, x1 = (S if oy + S == 64 else S - m), (S if ox + S == 64 else S - m)
+            same = np.array_equal(crop[0, :, y0:y1, x0:x1], full[0, :, oy + y0:oy + y1, ox + x0:ox + x1])
+            assert same == exact, (oy, ox, m)
